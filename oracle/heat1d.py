@@ -1,0 +1,99 @@
+"""1D random-diffusion problem and backward-Euler propagators (oracle).
+
+PDE (eq. psys with f(u) = (a u_x)_x - c u + f0): on (0, 1) with zero Dirichlet
+boundary values, u_t = (a(x; xi) u_x)_x - c u + f0.  Finite differences on
+Nx interior points x_i = i h, h = 1/(Nx+1), coefficient sampled at the faces
+x_{i+1/2}:
+
+  (A u)_i = -[a_{i+1/2}(u_{i+1} - u_i) - a_{i-1/2}(u_i - u_{i-1})] / h^2 + c u_i
+
+so the semi-discrete system reads u' + A u = f0 (eq. ODE of Section 4.1).
+
+Propagators (Section 3.1, both backward Euler in every experiment of
+Section 5):
+  G(v)  one step of Delta T:       (I + dT A) v' = v + dT f0
+  F(v)  J steps of dt = dT / J:    (I + dt A) v_{j+1} = v_j + dt f0
+Every linear solve is a banded LAPACK solve (scipy.linalg.solve_banded).
+
+The reference ("fine-grid") solution of the paper (Section 2, remark after
+eq. psys) is the sequential fine solution U*_n, n = 1..N.
+"""
+from __future__ import annotations
+
+import numpy as np
+from scipy.linalg import solve_banded
+
+
+class Heat1D:
+    def __init__(self, a_faces: np.ndarray, reaction: float = 0.0,
+                 forcing: float = 0.0):
+        a_faces = np.asarray(a_faces, dtype=np.float64)
+        self.nx = a_faces.shape[0] - 1
+        self.h = 1.0 / (self.nx + 1)
+        w = a_faces / self.h ** 2
+        self.diag = w[:-1] + w[1:] + reaction      # A_ii
+        self.off = -w[1:-1]                         # A_{i,i+1} = A_{i+1,i}
+        self.forcing = float(forcing)
+        self.reaction = float(reaction)
+
+    @property
+    def n(self) -> int:
+        return self.nx
+
+    def grid(self) -> np.ndarray:
+        return np.arange(1, self.nx + 1) * self.h
+
+    def apply(self, V: np.ndarray) -> np.ndarray:
+        """A V along the last axis."""
+        V = np.asarray(V)
+        out = self.diag * V
+        out[..., :-1] += self.off * V[..., 1:]
+        out[..., 1:] += self.off * V[..., :-1]
+        return out
+
+    def dense(self) -> np.ndarray:
+        return (np.diag(self.diag) + np.diag(self.off, 1) + np.diag(self.off, -1))
+
+    def shifted_solve(self, shift, scale: float, R: np.ndarray) -> np.ndarray:
+        """Solve (shift I + scale A) X = R along the last axis of R."""
+        R = np.asarray(R)
+        dt = np.result_type(R.dtype, np.asarray(shift).dtype, np.float64)
+        ab = np.zeros((3, self.nx), dtype=dt)
+        ab[0, 1:] = scale * self.off
+        ab[1, :] = shift + scale * self.diag
+        ab[2, :-1] = scale * self.off
+        X = solve_banded((1, 1), ab, np.moveaxis(R, -1, 0))
+        return np.moveaxis(X, 0, -1)
+
+    def be_step(self, V: np.ndarray, dt: float) -> np.ndarray:
+        """One backward-Euler step (I + dt A) V' = V + dt f0."""
+        return self.shifted_solve(1.0, dt, V + dt * self.forcing)
+
+
+def u0_sine(nx: int) -> np.ndarray:
+    h = 1.0 / (nx + 1)
+    return np.sin(np.pi * np.arange(1, nx + 1) * h)
+
+
+def G(op, V: np.ndarray, dT: float) -> np.ndarray:
+    """Coarse propagator: one backward-Euler step of size dT."""
+    return op.be_step(V, dT)
+
+
+def F(op, V: np.ndarray, dT: float, J: int) -> np.ndarray:
+    """Fine propagator: J backward-Euler steps of size dT/J."""
+    dt = dT / J
+    for _ in range(J):
+        V = op.be_step(V, dt)
+    return V
+
+
+def fine_sequential(op, u0: np.ndarray, N: int, J: int, T: float) -> np.ndarray:
+    """Reference solution U*_n at T_n = n T/N, n = 1..N, shape [N, nx]."""
+    dT = T / N
+    out = np.empty((N, op.n))
+    v = np.asarray(u0, dtype=np.float64)
+    for n in range(N):
+        v = F(op, v, dT, J)
+        out[n] = v
+    return out

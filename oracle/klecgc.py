@@ -1,0 +1,82 @@
+"""End-to-end KLE-PCGC on a workload (oracle): setup + per-sample solves.
+
+setup(w, xi_train)  input-KL basis at the faces, sequential fine snapshots of
+                    the training set, surrogate (Algorithm 3 offline part)
+solve_sample(...)   Algorithm 2 from the surrogate guess (Algorithm 3 online)
+error metrics       relative L2 error vs U* per sample; the paper's mean
+                    infinity-norm error per coarse point (Section 5).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+from . import kl_input, heat1d, pcgc
+from .surrogate import build_surrogate
+
+
+def _reference_worker(args):
+    w, xi = args
+    st = Setup1D(w, build=False)
+    return st.reference(xi).reshape(-1)
+
+
+class Setup1D:
+    def __init__(self, w, xi_train=None, build=True, processes=1):
+        from synth import draw_train
+        self.w = w
+        nx = w.nx
+        h = 1.0 / (nx + 1)
+        self.faces = (np.arange(nx + 1) + 0.5) * h
+        self.basis = kl_input.field_basis_1d(w.sigma, w.corr_len, w.M, self.faces)
+        self.u0 = heat1d.u0_sine(nx) if w.u0_kind == 0 else np.zeros(nx)
+        self.dT = w.T / w.N
+        if xi_train is None:
+            xi_train = draw_train(w)
+        self.xi_train = xi_train
+        self.sur = None
+        if build:
+            snaps = self.references(xi_train, processes)
+            self.sur = build_surrogate(snaps.reshape(len(xi_train), -1), xi_train,
+                                       w.gpc_degree, w.eps_kl)
+
+    def references(self, xis, processes=1) -> np.ndarray:
+        """U*(xi) for each row of xis, [S, N, nx]; optional spawn process pool."""
+        if processes <= 1 or len(xis) < 2:
+            return np.stack([self.reference(x) for x in xis])
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn")) as ex:
+            out = list(ex.map(_reference_worker, [(self.w, x) for x in xis],
+                              chunksize=max(1, len(xis) // (4 * processes))))
+        return np.stack(out).reshape(len(xis), self.w.N, self.w.nx)
+
+    def operator(self, xi) -> heat1d.Heat1D:
+        a = np.exp(kl_input.log_coefficient_1d(xi, self.basis))
+        return heat1d.Heat1D(a, self.w.reaction, self.w.forcing)
+
+    def reference(self, xi) -> np.ndarray:
+        """U*(xi): sequential fine solution, [N, nx]."""
+        return heat1d.fine_sequential(self.operator(xi), self.u0, self.w.N,
+                                      self.w.J, self.w.T)
+
+    def guess(self, xi) -> np.ndarray:
+        return self.sur.guess(np.atleast_2d(xi)).reshape(-1, self.w.N, self.w.nx)
+
+    def solve_sample(self, xi, U0=None, kmax=None, history=False):
+        w = self.w
+        if U0 is None:
+            U0 = self.guess(xi)[0]
+        op = self.operator(xi)
+        return pcgc.pcgc_solve(op, self.u0, U0, self.dT, w.J, w.alpha, w.tol,
+                               kmax or w.kmax, history=history)
+
+
+def rel_l2(U, Uref) -> float:
+    return float(np.linalg.norm(np.ravel(U) - np.ravel(Uref)) /
+                 np.linalg.norm(np.ravel(Uref)))
+
+
+def mean_inf_error(Uref_batch, U_batch) -> np.ndarray:
+    """e_n = (1/S) sum_i ||u_n(xi_i) - U_n(xi_i)||_inf, n = 1..N (Section 5)."""
+    d = np.abs(np.asarray(Uref_batch) - np.asarray(U_batch))
+    return d.max(axis=-1).mean(axis=0)

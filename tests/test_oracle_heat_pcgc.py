@@ -1,0 +1,175 @@
+"""Pins of the oracle's operator, propagators and parareal iterations against
+closed forms, dense brute force and the paper's error-propagation matrices."""
+import math
+
+import numpy as np
+import pytest
+
+from oracle import contraction, heat1d, pcgc
+
+
+def _op(nx, seed=0, reaction=0.0, forcing=0.0, const=False):
+    rng = np.random.default_rng(seed)
+    a = np.ones(nx + 1) if const else np.exp(0.5 * rng.standard_normal(nx + 1))
+    return heat1d.Heat1D(a, reaction, forcing)
+
+
+def test_operator_eigenvalues_constant_coefficient():
+    # a == 1: textbook spectrum mu_k = (4/h^2) sin^2(k pi h / 2), eigvecs sin(k pi x)
+    nx = 31
+    op = _op(nx, const=True, reaction=0.7)
+    h = op.h
+    mu = 4 / h ** 2 * np.sin(np.arange(1, nx + 1) * np.pi * h / 2) ** 2 + 0.7
+    ev = np.sort(np.linalg.eigvalsh(op.dense()))
+    assert np.allclose(ev, mu, rtol=1e-12)
+    x = op.grid()
+    for k in (1, 5):
+        v = np.sin(k * np.pi * x)
+        assert np.allclose(op.apply(v), mu[k - 1] * v, rtol=1e-11, atol=1e-9)
+
+
+def test_sequential_fine_solution_closed_form_a_const():
+    # a == 1, u0 = sin(pi x): U*_n = (1 + dt mu_1)^(-nJ) sin(pi x_i) exactly
+    nx, N, J, T = 63, 16, 16, 1.0
+    op = _op(nx, const=True)
+    u0 = heat1d.u0_sine(nx)
+    U = heat1d.fine_sequential(op, u0, N, J, T)
+    mu1 = 4 / op.h ** 2 * math.sin(math.pi * op.h / 2) ** 2
+    dt = T / N / J
+    n = np.arange(1, N + 1)
+    exact = (1 + dt * mu1) ** (-(n * J))[:, None] * u0[None, :]
+    assert np.allclose(U, exact, rtol=1e-12, atol=1e-15)
+    # coarse propagator multiplies by 1 / (1 + dT mu_1)
+    assert np.allclose(heat1d.G(op, u0, T / N), u0 / (1 + T / N * mu1), rtol=1e-13)
+
+
+def test_forcing_steady_state_is_discrete_parabola():
+    # a == 1, f0 = 1: the 3-point scheme is exact on x(1-x)/2, the steady state of BE
+    nx = 31
+    op = _op(nx, const=True, forcing=1.0)
+    v = np.zeros(nx)
+    for _ in range(400):
+        v = op.be_step(v, 0.05)
+    x = op.grid()
+    assert np.allclose(v, x * (1 - x) / 2, rtol=1e-10, atol=1e-13)
+
+
+def test_diagonalization_corrected_and_printed_orientation():
+    for N, alpha in ((2, 0.3), (8, 1e-3), (16, 1e-4)):
+        C = pcgc.calpha(N, alpha)
+        V, lam = pcgc.diag_factors(N, alpha)
+        assert np.linalg.norm(C @ V - V @ np.diag(lam)) <= 1e-12 * np.linalg.norm(V)
+        Vp, _ = pcgc.diag_factors(N, alpha, printed=True)
+        assert np.linalg.norm(C @ Vp - Vp @ np.diag(lam)) > 1e-3 * np.linalg.norm(Vp)
+        # eigenvalues printed as 1 - alpha^(1/N) omega^-(n-1) are the true ones
+        ev = np.linalg.eigvals(C)
+        for l in lam:
+            assert np.min(np.abs(ev - l)) < 1e-10
+
+
+@pytest.mark.parametrize("N,nx,alpha", [(4, 8, 0.1), (6, 5, 1e-3), (8, 7, 1e-2)])
+def test_three_step_solve_equals_dense_kron_solve(N, nx, alpha):
+    op = _op(nx, seed=N, reaction=0.3)
+    r = np.random.default_rng(1).standard_normal((N, nx))
+    dT = 1.0 / N
+    u1 = pcgc.cgc_diagonalized(op, r, dT, alpha)
+    u2 = pcgc.cgc_dense(op, r, dT, alpha)
+    assert np.allclose(u1, u2, rtol=1e-11, atol=1e-12 * np.abs(u2).max())
+
+
+def test_dft_of_real_data_is_hermitian():
+    N = 16
+    r = np.random.default_rng(3).standard_normal((N, 5))
+    p = pcgc.dft_matrix(N).conj().T @ r
+    for k in range(1, N):
+        assert np.allclose(p[N - k], p[k].conj(), atol=1e-13)
+
+
+def test_alpha_limit_is_sequential_cgc():
+    # CGC_alpha - CGC_seq = O(alpha) (the alpha-system tends to the sequential one)
+    N, nx = 8, 9
+    op = _op(nx, seed=5)
+    r = np.random.default_rng(2).standard_normal((N, nx))
+    dT = 1 / N
+    useq = pcgc.cgc_sequential(op, r, dT)
+    ratios = []
+    for alpha in (1e-2, 1e-3, 1e-4, 1e-5):
+        ratios.append(np.linalg.norm(pcgc.cgc_diagonalized(op, r, dT, alpha) - useq) / alpha)
+    assert max(ratios) / min(ratios) < 1.1
+    assert ratios[0] > 1e-8
+
+
+def test_classical_parareal_terminates_after_N_iterations():
+    nx, N, J = 11, 6, 5
+    op = _op(nx, seed=7, reaction=0.2, forcing=0.5)
+    u0 = heat1d.u0_sine(nx)
+    Ustar = heat1d.fine_sequential(op, u0, N, J, 1.0)
+    U0 = np.random.default_rng(0).standard_normal((N, nx))
+    its = pcgc.parareal_classical(op, u0, U0, 1.0 / N, J, N)
+    assert np.allclose(its[N], Ustar, rtol=1e-12, atol=1e-13)
+    # and after k iterations the first k points are already exact
+    for k in range(1, N):
+        assert np.allclose(its[k][:k], Ustar[:k], rtol=1e-12, atol=1e-13)
+
+
+def test_cgc_rhs_newton_form_equals_jump_form():
+    # r of eq. three steps at l=0 equals (I + dT A) b + dT f0 for linear f
+    N, nx = 5, 7
+    op = _op(nx, seed=9, reaction=0.4, forcing=0.8)
+    rng = np.random.default_rng(4)
+    Uk, b = rng.standard_normal((2, N, nx))
+    dT = 0.2
+    r = pcgc.cgc_rhs(op, Uk, b, dT)
+    assert np.allclose(r, b + dT * op.apply(b) + dT * 0.8, rtol=1e-13, atol=1e-13)
+
+
+def _scalar_setup(N=12, J=8, alpha=1e-2, nx=15, T=1.0):
+    op = _op(nx, const=True)
+    u0 = heat1d.u0_sine(nx)
+    mu1 = 4 / op.h ** 2 * math.sin(math.pi * op.h / 2) ** 2
+    return op, u0, mu1, N, J, alpha, T
+
+
+def test_error_propagation_matches_lemma_matrices():
+    # a == 1, every iterate is a multiple of sin(pi x); the error vector obeys
+    # e^{k+1} = G(z)^{-1} (G(z) - F(z)) e^k exactly (Lemma lem1), z = dT mu_1
+    op, u0, mu1, N, J, alpha, T = _scalar_setup()
+    dT = T / N
+    z = dT * mu1
+    Ustar = heat1d.fine_sequential(op, u0, N, J, T)
+    rng = np.random.default_rng(0)
+    U = rng.standard_normal(N)[:, None] * u0[None, :]
+    Gm, Fm = contraction.lemma_matrices(z, J, N, alpha)
+    Mit = np.linalg.solve(Gm, Gm - Fm)
+    e = (U - Ustar)[:, 0] / u0[0]
+    for _ in range(5):
+        U = pcgc.pcgc_iteration(op, u0, U, dT, J, alpha)
+        e_new = (U - Ustar)[:, 0] / u0[0]
+        # alpha-twisted G couples e_1 to alpha e_N; the fixed point is U*
+        assert np.allclose(e_new, Mit @ e, rtol=1e-9, atol=1e-12)
+        assert np.max(np.abs(e_new)) <= contraction.k_alpha(z, J, alpha) * np.max(np.abs(e)) + 1e-14
+        e = e_new
+
+
+def test_contraction_factor_sup_is_below_one_third():
+    # BE/BE: sup_z K_cla(z, J) -> sup (e^-z - 1/(1+z)) (1+z)/z ~ 0.2984 (paper quotes ~1/3)
+    z = np.logspace(-3, 3, 20001)
+    kc = contraction.k_cla(z, 10 ** 6)
+    zz = z
+    limit = np.abs(np.exp(-zz) - 1 / (1 + zz)) / (1 - 1 / (1 + zz))
+    assert abs(kc.max() - limit.max()) < 1e-5
+    assert 0.29 < kc.max() < 1 / 3
+    # finite J stays below the J -> infinity envelope
+    assert contraction.k_cla(z, 16).max() <= kc.max() + 1e-12
+
+
+def test_pcgc_converges_to_fine_solution():
+    # fixed point of Algorithm 2 is U* (F starts from u0 on the first interval)
+    nx, N, J = 15, 8, 6
+    op = _op(nx, seed=11, reaction=0.1, forcing=0.3)
+    u0 = heat1d.u0_sine(nx)
+    Ustar = heat1d.fine_sequential(op, u0, N, J, 1.0)
+    U0 = pcgc.coarse_guess(op, u0, N, 1.0 / N)
+    U, its, _ = pcgc.pcgc_solve(op, u0, U0, 1.0 / N, J, 1e-3, 1e-12, 60)
+    assert its > 0
+    assert np.max(np.abs(U - Ustar)) < 1e-11
