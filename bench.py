@@ -1,0 +1,400 @@
+"""Benchmark: converged samples/s of KLE-PCGC on the Nx=1023 / N=64 / J=64 heat workload.
+
+One step = one klecgc_solve over the whole batch (4096 samples): coefficient
+field and factorizations, surrogate guess, then parareal iterations with the
+diagonalized CGC until every sample meets tol.  A sample counts as converged
+when it reached tol and its relative L2 distance to the FP64 sequential fine
+solution U* is <= 1e-6 (U* from the library's FP64 reference kernel, which the
+test-suite pins to the CPU oracle).
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed_defect]
+  python bench.py --impl reference      (the CPU oracle on the host cores)
+
+Under torchrun (N > 1) every rank solves its own batch (different seed):
+weak scaling, no collective on the data path.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+METRIC = "converged samples/sec at rel err ≤1e-6 vs FP64 oracle; mean parareal iters"
+PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_defect": 2}
+DTYPES = {"fp64": "f64", "mixed": "f32+f64", "mixed_defect": "f32+f64"}
+FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA x max clock
+FP64_ALU_PEAK = 1.25                              # TFLOP/s, GB300 nominal FP64
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return d.get("hbm_gbs", 6800.0), "measured"
+    return 6800.0, "fallback"
+
+
+def workload_desc(w, S, precision):
+    return {"workload": f"{w.name}: 1D u_t=(a u_x)_x, a=exp(KL, M={w.M}), Nx={w.nx}, N={w.N}, "
+                        f"J={w.J}, gPC p={w.gpc_degree}, alpha={w.alpha}, tol={w.tol}",
+            "samples_per_gpu": S, "nx": w.nx, "N": w.N, "J": w.J, "M": w.M,
+            "gpc_degree": w.gpc_degree, "n_train": w.n_train, "alpha": w.alpha, "tol": w.tol,
+            "precision": precision,
+            "l2": "inputs larger than L2: per-step working set ~12 GB (U, r, p, factors)",
+            "parallelism": "sample shards per GPU, no collective"}
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle samples while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_id):
+        self.proc = None
+        self.path = None
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", gpu_id, f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        time.sleep(0.3)
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        rows = []
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) >= 9 and parts[1].replace(".", "").isdigit():
+                rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({n for r in rows for n, v in zip(names, r[5:9]) if v == "Active"})
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": float(rows[0][2]),
+                "power_w_max": max(float(r[3]) for r in rows if r[3].replace(".", "").isdigit()),
+                "samples": len(rows), "reasons": reasons}
+
+
+# ---------------------------------------------------------------- oracle (CPU)
+_ORACLE = None
+
+
+def _oracle_init(setup):
+    global _ORACLE
+    _ORACLE = setup
+
+
+def _oracle_solve(xi):
+    U, k, _ = _ORACLE.solve_sample(xi)
+    return U, k
+
+
+def oracle_pool(w, cores):
+    """Oracle set-up (snapshots on all cores) and a spawn pool holding it.
+
+    Worker processes run single-threaded BLAS so that `cores` processes use
+    `cores` hardware threads."""
+    import multiprocessing as mp
+    from oracle.klecgc import Setup1D
+    saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
+                                            "MKL_NUM_THREADS")}
+    for k in saved:
+        os.environ[k] = "1"
+    try:
+        setup = Setup1D(w, processes=cores)
+        pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_init, initargs=(setup,))
+    finally:
+        for k, v in saved.items():
+            if v is None:
+                os.environ.pop(k, None)
+            else:
+                os.environ[k] = v
+    return setup, pool
+
+
+def oracle_step(pool, xi):
+    t = time.perf_counter()
+    out = pool.map(_oracle_solve, list(xi), chunksize=1)
+    return time.perf_counter() - t, out
+
+
+def run_reference(args, w):
+    """--impl reference: the CPU oracle on the host cores, same metric."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    n_sub = max(16, cores)
+    from synth import draw_xi
+    xi = draw_xi(n_sub, w.M, w.seed)
+    setup, pool = oracle_pool(w, cores)
+    with pool:
+        for _ in range(args.warmup):
+            oracle_step(pool, xi[: min(n_sub, cores)])
+        times, outs = [], None
+        for _ in range(args.steps):
+            dt, outs = oracle_step(pool, xi)
+            times.append(dt)
+    iters = [k for _, k in outs]
+    t = float(np.mean(times))
+    value = n_sub / t
+    sample = (f"{n_sub} of the {w.S} samples of {w.name} per step, Algorithm 2 from the "
+              f"oracle's own surrogate (set-up not timed)")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_desc(w, n_sub, "fp64"), "mean_iters": float(np.mean(iters)),
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores,
+                             "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------- GPU arm
+def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
+    """Algorithmic work of kernel class `cls` over the timed region."""
+    if ms <= 0:
+        return None
+    row_steps = units["row_steps"]
+    pts = units["points"]
+    if cls == "fine":
+        if prec == "fp64":
+            flops = 5.0 * row_steps          # forward FMA; backward FMA + multiply
+            peak, unit = FP64_ALU_PEAK, "TFLOP/s"
+        else:
+            flops = 11.0 * row_steps         # flux rhs 5, forward 2, backward 3, update 1
+            peak, unit = FP32_ALU_PEAK, "TFLOP/s"
+        ach = flops / (ms / 1e3) / 1e12
+        return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": peak, "unit": unit,
+                "frac": ach / peak, "traffic": None,
+                "peak_source": "derived: 152 SMs x lanes x 2 x 2070 MHz" if prec != "fp64"
+                else "nominal GB300 FP64 1.25 TFLOP/s",
+                "work": f"{flops / max(launches, 1):.3e} flop per launch"}
+    K = w.N // 2 + 1
+    cb = 16 if prec != "mixed_defect" else 8      # complex value bytes
+    rb = 8 if prec != "mixed_defect" else 4       # r / d bytes
+    per_pt = {"cgc_fwd": rb + cb * K / w.N,
+              "cgc_solve": (2 * cb + 2 * cb) * K / w.N,
+              "cgc_inv": cb * K / w.N + 16}[cls] if cls in ("cgc_fwd", "cgc_solve", "cgc_inv") else None
+    if per_pt is None:
+        return None
+    byts = per_pt * pts
+    ach = byts / (ms / 1e3) / 1e9
+    return {"kernel": cls, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
+            "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_kind,
+            "work": f"{byts / max(launches, 1):.3e} bytes per launch"}
+
+
+def run_gpu(args, w):
+    import torch
+    import torch.distributed as dist
+    import __graft_entry__ as g
+    g.build()
+    import paper_2510_26180_gb300 as pkg
+    from synth import draw_train, draw_xi
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+
+    prec = args.precision
+    S = args.samples or w.S
+    cores = os.cpu_count() or 1
+    do_cpu = (not args.no_cpu_baseline) and world == 1 and rank == 0
+    pool = osetup = None
+    if do_cpu:
+        # spawn pool and oracle set-up before the first CUDA call of the library
+        osetup, pool = oracle_pool(w, cores)
+
+    solver = pkg.Solver(pkg.Problem.from_workload(w), draw_train(w))
+    info = solver.info()
+    xi_h = draw_xi(S, w.M, w.seed + 1000 * rank)
+    xi = torch.from_numpy(xi_h).to(dev)
+    U = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev)
+    it = torch.empty(S, dtype=torch.int32, device=dev)
+    stt = torch.empty(S, dtype=torch.int32, device=dev)
+    dT = w.T / w.N
+    code = lambda p: PRECISIONS[p]  # noqa: E731
+
+    def step(p=prec, xin=xi, Uo=U, ito=it, sto=stt):
+        return solver.solve(xin, S, dT, w.J, w.N, w.alpha, w.tol, w.kmax, code(p), pkg.GUESS_GPC,
+                            Uo, ito, sto)
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid is not None else str(local))
+    solver.profile_enable(True)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    prof = solver.profile_read()
+    solver.profile_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+
+    # accuracy of the last timed step against U* (FP64 reference kernel)
+    Uref = torch.empty_like(U)
+    solver.reference(xi, S, w.N, w.J, Uref)
+    err = ((U - Uref).flatten(1).norm(dim=1) / Uref.flatten(1).norm(dim=1)).cpu().numpy()
+    iters = it.cpu().numpy()
+    status = stt.cpu().numpy()
+    ok = (status == 0) & (err <= 1e-6)
+    n_ok = int(ok.sum())
+    row_steps = float(np.clip(iters, 0, None).sum()) * w.N * w.nx * w.J * args.steps
+    points = float(np.clip(iters, 0, None).sum()) * w.N * w.nx * args.steps
+
+    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
+    nok_t = torch.tensor([float(n_ok)], dtype=torch.float64, device=dev)
+    if world > 1:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+        dist.all_reduce(nok_t, op=dist.ReduceOp.SUM)
+    ms_max = float(ms_t.item())
+    value = float(nok_t.item()) / (ms_max / 1e3)
+
+    # end-to-end through the C ABI with pinned host buffers (copies timed)
+    xi_pin = torch.from_numpy(xi_h).pin_memory()
+    U_pin = torch.empty((S, w.N, w.nx), dtype=torch.float64).pin_memory()
+    it_pin = torch.empty(S, dtype=torch.int32).pin_memory()
+    st_pin = torch.empty(S, dtype=torch.int32).pin_memory()
+    step(xin=xi_pin, Uo=U_pin, ito=it_pin, sto=st_pin)
+    e_steps = max(1, min(args.steps, 3))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(e_steps):
+        step(xin=xi_pin, Uo=U_pin, ito=it_pin, sto=st_pin)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e_steps
+    e2e_ok = int(((st_pin.numpy() == 0) & (np.linalg.norm((U_pin.numpy() - Uref.cpu().numpy())
+                                                           .reshape(S, -1), axis=1)
+                                            / np.linalg.norm(Uref.cpu().numpy().reshape(S, -1),
+                                                             axis=1) <= 1e-6)).sum())
+    e2e = {"value": e2e_ok * world / e2e_s, "unit": "samples/s",
+           "h2d_bytes_per_step": int(xi_h.nbytes),
+           "d2h_bytes_per_step": int(U_pin.numel() * 8 + 2 * 4 * S)}
+
+    # plain FP64 path on the same batch (the >= 5x comparison of the method's
+    # precision variants)
+    fp64 = None
+    if prec != "fp64" and not args.skip_fp64:
+        U64 = torch.empty_like(U)
+        it64 = torch.empty_like(it)
+        st64 = torch.empty_like(stt)
+        step("fp64", Uo=U64, ito=it64, sto=st64)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        step("fp64", Uo=U64, ito=it64, sto=st64)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        ms64 = f0.elapsed_time(f1)
+        err64 = ((U64 - Uref).flatten(1).norm(dim=1) / Uref.flatten(1).norm(dim=1)).cpu().numpy()
+        ok64 = int(((st64.cpu().numpy() == 0) & (err64 <= 1e-6)).sum())
+        fp64 = {"value": ok64 / (ms64 / 1e3), "ms_per_step": ms64,
+                "mean_iters": float(it64.cpu().numpy().mean()), "max_rel_err": float(err64.max()),
+                "speedup_of_headline": value / (ok64 * world / (ms64 / 1e3)) if ok64 else None}
+
+    hbm_peak, peak_kind = peaks()
+    units = {"row_steps": row_steps, "points": points}
+    kernels = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}
+    tot_ms = sum(v["ms"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = v["ms"] / tot_ms
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    roof = roofline_entry(dom, kernels[dom]["ms"], kernels[dom]["launches"], units, prec, w,
+                          hbm_peak, peak_kind)
+    launches = int(sum(v["launches"] for v in kernels.values()))
+
+    cpu = None
+    if do_cpu:
+        n_sub = max(16, cores)
+        sub = xi_h[:n_sub]
+        with pool:
+            dt, outs = oracle_step(pool, sub)
+        Ug = U[:n_sub].cpu().numpy()
+        d = [float(np.linalg.norm(Ug[i] - outs[i][0]) / np.linalg.norm(outs[i][0]))
+             for i in range(n_sub)]
+        same_it = int(sum(int(iters[i]) == outs[i][1] for i in range(n_sub)))
+        cpu = {"value": n_sub / dt, "unit": "samples/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {n_sub} of the {S} samples, Algorithm 2 from the oracle's own "
+                         f"surrogate (set-up not timed)",
+               "gpu_vs_oracle_max_rel": max(d), "equal_iters": f"{same_it}/{n_sub}"}
+
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[prec], "data": "synthetic", "config": workload_desc(w, S, prec),
+            "mean_iters": float(iters.mean()), "converged": n_ok, "samples": S,
+            "max_rel_err": float(err.max()), "MQ": info.MQ, "P": info.P,
+            "fp64_path": fp64, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,
+            "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    solver.close()
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="heat1d_nx1023")
+    ap.add_argument("--precision", default="mixed_defect", choices=list(PRECISIONS))
+    ap.add_argument("--samples", type=int, default=0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--skip-fp64", action="store_true")
+    args = ap.parse_args()
+    from synth import workload
+    w = workload(args.workload)
+    if args.impl == "reference":
+        return run_reference(args, w)
+    return run_gpu(args, w)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,239 @@
+/*
+ * klecgc.h - C ABI of the GB300 (sm_103a) KLE-PCGC solver.
+ *
+ * The library evaluates, for a batch of random-input samples xi, the online
+ * part of Algorithm 3 of "A parallel solver for random input problems via
+ * Karhunen-Loeve expansion and diagonalized coarse grid correction"
+ * (arXiv 2510.26180): the KL/gPC surrogate initial guess (Algorithm 3,
+ * step 6), then parareal iterations with the alpha-circulant diagonalized
+ * coarse grid correction (Algorithm 2; Section 3.2, eqs. PGC_step1,
+ * PGC_step2, matrix_NT, Newton2, three steps).
+ *
+ * Problem (eq. psys with f(u) = div(a grad u) - c u + f0, Section 4.1
+ * eq. ODE): zero Dirichlet data on (0,1)^dim, a(x; xi) = exp(g(x; xi)),
+ * g = sum_m sqrt(lambda_m) phi_m(x) xi_m the KL expansion of a Gaussian
+ * field with covariance sigma^2 exp(-|x - y| / corr_len).  Both propagators
+ * are backward Euler (Section 5): G with step dT, F with J steps dT/J.
+ *
+ * Conventions shared by every entry point
+ *  - Every array is owned by the caller.  The library owns the context and
+ *    the device tables and scratch it allocates inside it.
+ *  - Array arguments may be host or device pointers (CUDA unified
+ *    addressing decides which); host arrays are staged through the
+ *    library's device scratch on the given stream.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Work is
+ *    enqueued on it; every entry point returns after that work has
+ *    completed, so the returned status is final.
+ *  - Layouts are row-major.  A solution batch U has shape [S][N][nx^dim]:
+ *    U[s][n][i] approximates u(x_i, T_{n+1}) for n = 0..N-1 (U_1..U_N of the
+ *    paper), x_i the interior grid points in lexicographic order.
+ *  - No exception crosses the ABI and no device trap is used: every error
+ *    is a status code; klecgc_last_error() returns a one-line detail for
+ *    the calling thread.
+ */
+#ifndef KLECGC_H
+#define KLECGC_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct klecgc_ctx klecgc_ctx;
+
+typedef enum {
+    KLECGC_OK = 0,
+    KLECGC_E_INVALID_ARG = 1,   /* an argument is out of range or inconsistent */
+    KLECGC_E_OUT_OF_MEMORY = 2, /* a device allocation failed */
+    KLECGC_E_NOT_CONVERGED = 3, /* some sample did not reach tol in kmax iterations */
+    KLECGC_E_NONFINITE = 4,     /* NaN/Inf in an input or an iterate */
+    KLECGC_E_CUDA = 5,          /* a CUDA runtime call failed */
+    KLECGC_E_UNSUPPORTED = 6    /* valid, but not implemented (e.g. N not a power of 2) */
+} klecgc_status;
+
+/* Arithmetic of klecgc_solve. */
+enum {
+    /* Everything in FP64. */
+    KLECGC_FP64 = 0,
+    /* Fine propagator in FP32 (increment form, see below); jump, CGC,
+       update and convergence norm in FP64. */
+    KLECGC_MIXED = 1,
+    /* Fine propagator in FP32 (increment form); the CGC is applied in FP32 to
+       the FP64 defect F(U^k) - U^k (defect-correction form of Algorithm 2,
+       algebraically identical); update and convergence norm in FP64. */
+    KLECGC_MIXED_DEFECT = 2
+};
+
+/* Initial guess U^0 of klecgc_solve. */
+enum {
+    KLECGC_GUESS_GPC = 0,   /* KL + gPC surrogate (Algorithm 3, step 6) */
+    KLECGC_GUESS_ZERO = 1,  /* U^0 = 0 */
+    KLECGC_GUESS_USER = 2,  /* U^0 given by the caller in U_guess */
+    KLECGC_GUESS_COARSE = 3 /* U^0_n = G(U^0_{n-1}), U^0_0 = u0 (Section 3.1) */
+};
+
+typedef struct {
+    int32_t dim;          /* space dimension: 1 (2 is reserved) */
+    int32_t nx;           /* interior points per direction, h = 1/(nx+1) */
+    double T;             /* final time */
+    double sigma;         /* std-dev of the Gaussian log-coefficient g */
+    double corr_len;      /* correlation length of exp(-|x-y|/corr_len) */
+    int32_t M;            /* input KL terms (length of xi) */
+    int32_t gpc_degree;   /* total degree p of the Hermite gPC basis */
+    int32_t n_train;      /* |Xi_t|, training samples of the surrogate */
+    double eps_kl;        /* snapshot-KL energy tolerance eps^KL */
+    int32_t N;            /* coarse intervals of the surrogate's time grid */
+    int32_t J;            /* fine steps per interval used for the snapshots */
+    double reaction;      /* c >= 0 in div(a grad u) - c u + f0 */
+    double forcing;       /* f0 (constant source) */
+    int32_t u0_kind;      /* 0: u0 = sin(pi x) (product of sines in 2D); 1: u0 = 0 */
+} klecgc_problem;
+
+typedef struct {
+    int32_t nx, N, J, M, P;   /* P = number of gPC basis functions */
+    int32_t MQ;               /* retained snapshot-KL modes (Algorithm 3, step 2) */
+    double lambda_sum;        /* sum of all snapshot-KL eigenvalues */
+    double lambda_kept;       /* sum of the retained ones */
+    int32_t n_unknowns;       /* nx^dim */
+    int32_t device;           /* CUDA device of the context */
+} klecgc_info_t;
+
+/*
+ * klecgc_setup - offline part of Algorithm 3 (steps 1-6).
+ *   1. input-field KL eigenpairs of the exponential covariance (roots of
+ *      the transcendental equations), coefficient field at the cell faces;
+ *   2. snapshots: the sequential fine solution (the paper's reference
+ *      solution) at the N coarse times for every xi in Xi_t;
+ *   3. snapshot mean, covariance C (Section 2.1), its eigenpairs and M_Q:
+ *      the smallest M_Q capturing a fraction >= 1 - eps_kl of the energy
+ *      (Algorithm 3 step 2 prints "<="; read as ">="), at most n_train-1;
+ *   4. modes g_k (eq. KLE basis) and coefficients zeta_k (eq. KLE parameter);
+ *   5. least squares h = argmin ||B h - D|| per mode (eq. least square
+ *      problem) with the total-degree Hermite basis (eq. complete);
+ *   6. stores ubar and W = (H diag(sqrt(lambda))) G so that the surrogate
+ *      U^0(xi) = ubar + psi(xi) W (step 6's double sum, regrouped).
+ * xi_train: [n_train][M] FP64, host or device.  Runs on the current CUDA
+ * device.  On success *out owns the context (free with klecgc_free).
+ * Errors: INVALID_ARG (bad problem fields, NULL pointers),
+ * OUT_OF_MEMORY, NONFINITE (xi_train), CUDA, UNSUPPORTED (dim != 1).
+ */
+klecgc_status klecgc_setup(const klecgc_problem* problem, const double* xi_train,
+                           klecgc_ctx** out, void* stream);
+
+/*
+ * klecgc_solve - online part of Algorithm 3 for S samples.
+ *   xi:        [S][M] FP64 KL coefficients (host or device).
+ *   dT, J, N:  coarse step, fine steps per interval, intervals; N*dT must
+ *              equal T to 1e-12 relative; N a power of two in [2, 64] and,
+ *              for the gPC guess, equal to the setup's N.
+ *   alpha:     twist of the coarse problem u(0) = alpha u(T), 0 < alpha < 1.
+ *   tol:       a sample stops after the first iteration k with
+ *              max_n ||U^{k}_n - U^{k-1}_n||_inf <= tol (the paper fixes no
+ *              rule; this is the per-sample increment).
+ *   kmax:      iteration cap (>= 1).
+ *   precision: KLECGC_FP64 / KLECGC_MIXED / KLECGC_MIXED_DEFECT.
+ *   guess:     KLECGC_GUESS_*; U_guess ([S][N][nx]) is read only for USER.
+ *   U_out:     [S][N][nx] FP64: the last iterate of every sample.
+ *   iters_out: [S] int32: CGC updates performed until tol was met, -1 when
+ *              kmax was reached first, -2 for a non-finite iterate.  May be NULL.
+ *   status_out:[S] int32 klecgc_status per sample.  May be NULL.
+ * S == 0 is valid and does nothing.  Returns OK when every sample
+ * converged, NONFINITE if any sample produced NaN/Inf (or xi had one),
+ * else NOT_CONVERGED if any sample hit kmax; INVALID_ARG / UNSUPPORTED /
+ * OUT_OF_MEMORY / CUDA for argument and runtime errors (nothing written).
+ * Each sample's iterates are independent of the other samples.
+ */
+klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S,
+                           double dT, int32_t J, int32_t N, double alpha, double tol,
+                           int32_t kmax, int32_t precision, int32_t guess,
+                           const double* U_guess, double* U_out, int32_t* iters_out,
+                           int32_t* status_out, void* stream);
+
+/* Stage entry points (one step of the hot path each; used for stage-level
+ * checks).  Arguments have the meanings given for klecgc_solve. */
+
+/* Coefficient field a(x_{i+1/2}; xi) = exp(g) at the nx+1 faces of every
+ * sample: a_out [S][nx+1] FP64. */
+klecgc_status klecgc_field(klecgc_ctx* ctx, const double* xi, int64_t S,
+                           double* a_out, void* stream);
+
+/* Surrogate guess U^0(xi) = ubar + sum_k sqrt(lambda_k) zeta_k(xi) g_k
+ * (Algorithm 3 step 6) on the setup's grid: U0_out [S][N][nx].
+ * precision FP64 evaluates it in FP64; the mixed modes in FP32 with FP64
+ * output. */
+klecgc_status klecgc_guess(klecgc_ctx* ctx, const double* xi, int64_t S,
+                           int32_t precision, double* U0_out, void* stream);
+
+/* Step 1 of Algorithm 2 plus the right-hand side of the CGC system
+ * (eq. matrix_NT at the Newton point of eq. Newton2): for every sample and
+ * n = 1..N, Ftilde_n = F(start_n) with start_1 = u0 and start_n = U_{n-1},
+ * and r_n = (I + dT A) Ftilde_n - prev_n with prev_1 = alpha U_N and
+ * prev_n = U_{n-1}; this equals (I + dT A) b_n + dT f0 for the jump b of
+ * Section 3.2.  U_in, r_out: [S][N][nx] FP64.  precision selects the
+ * arithmetic of F (FP64, or FP32 increment form for the mixed modes). */
+klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t N,
+                                const double* U_in, double dT, int32_t J, double alpha,
+                                int32_t precision, double* r_out, void* stream);
+
+/* Diagonalized CGC solve (eq. three steps): u = (C_alpha (x) I + dT I (x) A)^{-1} r
+ * by (a) p = F_N^* Lambda_alpha r along n, (b) (lambda_n I + dT A) q_n = p_n,
+ * (c) u = Lambda_alpha^{-1} F_N q, with Lambda_alpha = diag(alpha^{(n-1)/N})
+ * and lambda_n = 1 - alpha^{1/N} exp(-2 pi i (n-1)/N).  (The printed
+ * eigenvector matrix Lambda_alpha F_N does not diagonalize C_alpha; its
+ * inverse scaling does.)  r_in, u_out: [S][N][nx] FP64; precision FP64 or
+ * KLECGC_MIXED_DEFECT (FP32 transform and solves). */
+klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t N,
+                               const double* r_in, double dT, double alpha,
+                               int32_t precision, double* u_out, void* stream);
+
+/* The paper's reference solution (Section 2, remark after eq. psys): the
+ * sequential fine solution U*_n, n = 1..N, in FP64: U_out [S][N][nx]. */
+klecgc_status klecgc_reference(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t N,
+                               int32_t J, double* U_out, void* stream);
+
+/* Sizes of the context (M_Q, P, ...). */
+klecgc_status klecgc_info(const klecgc_ctx* ctx, klecgc_info_t* out);
+
+/* Kernel classes of the profile (index into klecgc_profile_t arrays). */
+enum {
+    KLECGC_K_FIELD = 0,     /* coefficient field and face weights          */
+    KLECGC_K_FACTORS = 1,   /* fine and CGC factorizations                  */
+    KLECGC_K_GUESS = 2,     /* gPC basis and surrogate contraction          */
+    KLECGC_K_FINE = 3,      /* fine propagator + CGC right-hand side        */
+    KLECGC_K_CGC_FWD = 4,   /* step (a): DFT along the coarse times         */
+    KLECGC_K_CGC_SOLVE = 5, /* step (b): shifted tridiagonal solves         */
+    KLECGC_K_CGC_INV = 6,   /* step (c): inverse DFT, update, increment norm */
+    KLECGC_K_CONV = 7,      /* stopping rule                                */
+    KLECGC_K_LAYOUT = 8,    /* layout changes, checks                       */
+    KLECGC_K_COUNT = 9
+};
+
+typedef struct {
+    int64_t launches[16]; /* kernel launches per class since the last enable */
+    double ms[16];        /* summed CUDA-event time per class (0 when timing is off) */
+    int32_t n_classes;    /* KLECGC_K_COUNT */
+} klecgc_profile_t;
+
+/* Resets the per-class launch counters; with `timing` != 0, klecgc_solve also
+ * brackets every kernel launch with CUDA events on its stream and sums the
+ * elapsed times per class. */
+klecgc_status klecgc_profile_enable(klecgc_ctx* ctx, int32_t timing);
+
+/* Reads the counters and summed times accumulated since the last enable. */
+klecgc_status klecgc_profile_read(const klecgc_ctx* ctx, klecgc_profile_t* out);
+
+/* Releases the context and everything it allocated.  NULL is allowed. */
+void klecgc_free(klecgc_ctx* ctx);
+
+/* Static description of a status code. */
+const char* klecgc_status_string(klecgc_status s);
+
+/* Detail of the last error reported on the calling thread ("" if none). */
+const char* klecgc_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* KLECGC_H */

@@ -50,8 +50,15 @@ class Setup1D:
                               chunksize=max(1, len(xis) // (4 * processes))))
         return np.stack(out).reshape(len(xis), self.w.N, self.w.nx)
 
-    def operator(self, xi) -> heat1d.Heat1D:
+    def operator(self, xi, field_ulps: float = 0.0, seed: int = 0) -> heat1d.Heat1D:
+        """Operator of sample xi.  field_ulps > 0 multiplies every face value by
+        (1 +- field_ulps * 2^-53) with random signs: a model of the rounding of
+        an independently computed field, used to measure how strongly a result
+        depends on the last bits of a."""
         a = np.exp(kl_input.log_coefficient_1d(xi, self.basis))
+        if field_ulps:
+            sgn = np.random.default_rng(seed).choice([-1.0, 1.0], size=a.shape)
+            a = a * (1.0 + field_ulps * 2.0 ** -53 * sgn)
         return heat1d.Heat1D(a, self.w.reaction, self.w.forcing)
 
     def reference(self, xi) -> np.ndarray:
@@ -62,13 +69,13 @@ class Setup1D:
     def guess(self, xi) -> np.ndarray:
         return self.sur.guess(np.atleast_2d(xi)).reshape(-1, self.w.N, self.w.nx)
 
-    def solve_sample(self, xi, U0=None, kmax=None, history=False):
+    def solve_sample(self, xi, U0=None, kmax=None, history=False, cgc="diag", field_ulps=0.0):
         w = self.w
         if U0 is None:
             U0 = self.guess(xi)[0]
-        op = self.operator(xi)
+        op = self.operator(xi, field_ulps)
         return pcgc.pcgc_solve(op, self.u0, U0, self.dT, w.J, w.alpha, w.tol,
-                               kmax or w.kmax, history=history)
+                               kmax or w.kmax, history=history, cgc=cgc)
 
 
 def rel_l2(U, Uref) -> float:

@@ -67,20 +67,32 @@ def cgc_rhs(op, Uk: np.ndarray, b: np.ndarray, dT: float) -> np.ndarray:
     return dT * op.apply(Uk) + dT * Fu + b         # -dT (I (x) grad f) u_0 + dT F(u_0) + b
 
 
-def cgc_diagonalized(op, r: np.ndarray, dT: float, alpha: float) -> np.ndarray:
-    """Solve (C_alpha (x) I + dT I (x) A) u = r by steps (a)-(c), direct DFT."""
+def cgc_diagonalized(op, r: np.ndarray, dT: float, alpha: float,
+                     fft: bool = False) -> np.ndarray:
+    """Solve (C_alpha (x) I + dT I (x) A) u = r by steps (a)-(c), direct DFT.
+
+    fft=True applies F_N and F_N^* with numpy's FFT instead of the explicit
+    DFT matrix: the same method along another rounding path, used only to
+    measure the method's own rounding floor (the alpha^{-(n-1)/N} scaling of
+    step (c) multiplies roundoff by up to 1/alpha).
+    """
     N = r.shape[0]
     n = np.arange(N)
-    FN = dft_matrix(N)
     lam = 1.0 - alpha ** (1.0 / N) * np.exp(-2j * np.pi * n / N)
-    # (a) p = (V^{-1} (x) I) r = (F_N^* (x) I)(Lambda_alpha (x) I) r
-    p = FN.conj().T @ ((alpha ** (n / N))[:, None] * r)
+    sr = (alpha ** (n / N))[:, None] * r
+    if fft:
+        p = np.fft.fft(sr, axis=0) / np.sqrt(N)
+    else:
+        FN = dft_matrix(N)
+        # (a) p = (V^{-1} (x) I) r = (F_N^* (x) I)(Lambda_alpha (x) I) r
+        p = FN.conj().T @ sr
     # (b) (lambda_n I + dT A) q_n = p_n for every n (all N frequencies)
     q = np.empty_like(p)
     for k in range(N):
         q[k] = op.shifted_solve(lam[k], dT, p[k])
     # (c) u = (V (x) I) q = (Lambda_alpha^{-1} (x) I)(F_N (x) I) q
-    u = (alpha ** (-n / N))[:, None] * (FN @ q)
+    Fq = np.fft.ifft(q, axis=0) * np.sqrt(N) if fft else dft_matrix(N) @ q
+    u = (alpha ** (-n / N))[:, None] * Fq
     return u.real
 
 
@@ -107,15 +119,22 @@ def fine_sweep(op, u0: np.ndarray, Uk: np.ndarray, dT: float, J: int) -> np.ndar
     return F(op, starts, dT, J)
 
 
-def pcgc_iteration(op, u0, Uk, dT: float, J: int, alpha: float) -> np.ndarray:
+def pcgc_iteration(op, u0, Uk, dT: float, J: int, alpha: float, cgc: str = "diag") -> np.ndarray:
+    """One iteration of Algorithm 2.  cgc selects how eq. matrix_NT is solved:
+    "diag" (the three steps with a direct DFT, the paper's method), "fft"
+    (the same with numpy's FFT) or "dense" (Kronecker brute force, the exact
+    solution of the same system; used to measure the diagonalization's own
+    rounding error)."""
     Fend = fine_sweep(op, u0, Uk, dT, J)
     b = jump_b(op, Fend, Uk, dT, alpha)
     r = cgc_rhs(op, Uk, b, dT)
-    return cgc_diagonalized(op, r, dT, alpha)
+    if cgc == "dense":
+        return cgc_dense(op, r, dT, alpha)
+    return cgc_diagonalized(op, r, dT, alpha, fft=(cgc == "fft"))
 
 
 def pcgc_solve(op, u0, U0, dT: float, J: int, alpha: float, tol: float,
-               kmax: int, history: bool = False):
+               kmax: int, history: bool = False, cgc: str = "diag"):
     """Algorithm 2 from the initial guess U0 ([N, n]).
 
     Returns (U, iters, hist) where iters = number of CGC updates until the
@@ -124,7 +143,7 @@ def pcgc_solve(op, u0, U0, dT: float, J: int, alpha: float, tol: float,
     U = np.array(U0, dtype=np.float64)
     hist = [U.copy()] if history else None
     for k in range(kmax):
-        Un = pcgc_iteration(op, u0, U, dT, J, alpha)
+        Un = pcgc_iteration(op, u0, U, dT, J, alpha, cgc=cgc)
         delta = np.max(np.abs(Un - U))
         U = Un
         if history:

@@ -1,0 +1,862 @@
+// C ABI of libklecgc: context, setup (offline part of Algorithm 3) and the
+// solve loop (online part: Algorithm 2 from the surrogate guess).
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/klecgc.h"
+#include "common.cuh"
+#include "setup_host.h"
+
+namespace klecgc {
+
+static thread_local std::string g_last_error;
+void set_error(const std::string& msg) { g_last_error = msg; }
+
+struct DevBuf {
+    void* ptr = nullptr;
+    size_t bytes = 0;
+};
+
+static std::mutex g_tw_mutex;
+static std::map<int, bool> g_tw_done;
+
+static cudaError_t ensure_twiddles(int dev) {
+    std::lock_guard<std::mutex> lk(g_tw_mutex);
+    if (!g_tw_done[dev]) {
+        upload_twiddles();
+        cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+        g_tw_done[dev] = true;
+    }
+    return cudaSuccess;
+}
+
+}  // namespace klecgc
+
+using namespace klecgc;
+
+struct klecgc_ctx {
+    klecgc_problem prob{};
+    int device = 0;
+    int nx = 0, N = 0, J = 0, M = 0, P = 0, MQ = 0, p = 0;
+    double h = 0.0, dT = 0.0;
+    double lambda_sum = 0.0, lambda_kept = 0.0;
+    // device tables (owned)
+    double* basis = nullptr;   // [M][nx+1]  sqrt(lambda_m) phi_m(x_{i+1/2})
+    double* u0 = nullptr;      // [nx]
+    int* degrees = nullptr;    // [P][M]
+    double* ubar = nullptr;    // [nx*N]  internal order c = i*N + n
+    double* W = nullptr;       // [P][nx*N]
+    float* W32 = nullptr;      // FP32 copy of W
+    std::map<std::string, DevBuf> ws;  // grow-only scratch
+    std::vector<void*> owned;
+    // profile: launch counters and optional CUDA-event timing per kernel class
+    bool prof_timing = false;
+    int64_t prof_launches[KLECGC_K_COUNT] = {};
+    double prof_ms[KLECGC_K_COUNT] = {};
+    std::vector<cudaEvent_t> prof_free;
+    struct Pending {
+        int cls;
+        cudaEvent_t a, b;
+    };
+    std::vector<Pending> prof_pending;
+
+    cudaEvent_t prof_event() {
+        if (!prof_free.empty()) {
+            cudaEvent_t e = prof_free.back();
+            prof_free.pop_back();
+            return e;
+        }
+        cudaEvent_t e;
+        cudaEventCreate(&e);
+        return e;
+    }
+    // Runs `f` (one kernel launch) under class `cls`.
+    template <class F>
+    void launch(int cls, cudaStream_t st, F&& f) {
+        prof_launches[cls] += 1;
+        if (!prof_timing) {
+            f();
+            return;
+        }
+        cudaEvent_t a = prof_event(), b = prof_event();
+        cudaEventRecord(a, st);
+        f();
+        cudaEventRecord(b, st);
+        prof_pending.push_back({cls, a, b});
+    }
+    void prof_collect() {
+        for (auto& p : prof_pending) {
+            float ms = 0.f;
+            if (cudaEventSynchronize(p.b) == cudaSuccess && cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess)
+                prof_ms[p.cls] += ms;
+            prof_free.push_back(p.a);
+            prof_free.push_back(p.b);
+        }
+        prof_pending.clear();
+    }
+
+    template <typename T>
+    T* get(const std::string& name, size_t count, cudaError_t* err) {
+        DevBuf& b = ws[name];
+        size_t bytes = count * sizeof(T);
+        if (bytes == 0) bytes = 16;
+        if (b.bytes < bytes) {
+            if (b.ptr) cudaFree(b.ptr);
+            b.ptr = nullptr;
+            b.bytes = 0;
+            cudaError_t e = cudaMalloc(&b.ptr, bytes);
+            if (e != cudaSuccess) {
+                *err = e;
+                return nullptr;
+            }
+            b.bytes = bytes;
+        }
+        return (T*)b.ptr;
+    }
+    template <typename T>
+    cudaError_t alloc_owned(T** p, size_t count) {
+        cudaError_t e = cudaMalloc((void**)p, std::max<size_t>(count, 1) * sizeof(T));
+        if (e == cudaSuccess) owned.push_back(*p);
+        return e;
+    }
+    ~klecgc_ctx() {
+        prof_collect();
+        for (cudaEvent_t e : prof_free) cudaEventDestroy(e);
+        for (void* p : owned) cudaFree(p);
+        for (auto& kv : ws)
+            if (kv.second.ptr) cudaFree(kv.second.ptr);
+    }
+};
+
+namespace {
+
+bool is_device_ptr(const void* p) {
+    if (!p) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+klecgc_status fail(klecgc_status s, const std::string& msg) {
+    set_error(msg);
+    return s;
+}
+
+#define TRY(expr)                                                                       \
+    do {                                                                                \
+        cudaError_t e_ = (expr);                                                        \
+        if (e_ != cudaSuccess)                                                          \
+            return fail(e_ == cudaErrorMemoryAllocation ? KLECGC_E_OUT_OF_MEMORY          \
+                                                        : KLECGC_E_CUDA,                \
+                        std::string(#expr) + ": " + cudaGetErrorString(e_));            \
+    } while (0)
+
+#define WS(T, var, name, count)                                      \
+    cudaError_t var##_e = cudaSuccess;                               \
+    T* var = ctx->get<T>(name, (size_t)(count), &var##_e);           \
+    if (!var) TRY(var##_e)
+
+// Stage a caller array on the device: returns a device pointer holding the data.
+template <typename T>
+klecgc_status stage_in(klecgc_ctx* ctx, const T* user, size_t count, const char* name,
+                       cudaStream_t st, const T** out) {
+    if (is_device_ptr(user)) {
+        *out = user;
+        return KLECGC_OK;
+    }
+    WS(T, d, name, count);
+    TRY(cudaMemcpyAsync(d, user, count * sizeof(T), cudaMemcpyHostToDevice, st));
+    *out = d;
+    return KLECGC_OK;
+}
+
+bool pow2_in_range(int N) { return N >= 2 && N <= 64 && (N & (N - 1)) == 0; }
+
+klecgc_status check_dT(const klecgc_ctx* ctx, int N, double dT) {
+    double T = ctx->prob.T;
+    if (!(dT > 0) || std::fabs(N * dT - T) > 1e-12 * T)
+        return fail(KLECGC_E_INVALID_ARG, "N * dT must equal T");
+    return KLECGC_OK;
+}
+
+// Per-solve operators: coefficient field, face weights, fine and CGC factors.
+struct Operators {
+    double* a = nullptr;
+    double* wT = nullptr;
+    FineCoef64* f64 = nullptr;
+    FineCoef32* f32 = nullptr;
+    float4* tabA = nullptr;
+    float4* tabD = nullptr;
+    Cplx<double>* dinv64 = nullptr;
+    Cplx<double>* lu64 = nullptr;
+    Cplx<float>* dinv32 = nullptr;
+    Cplx<float>* lu32 = nullptr;
+};
+
+klecgc_status build_field(klecgc_ctx* ctx, const double* xi_d, int64_t S, cudaStream_t st,
+                          double** a_out) {
+    const int nf = ctx->nx + 1;
+    WS(double, a, "a", S * nf);
+    ctx->launch(KLECGC_K_FIELD, st, [&] { launch_field(xi_d, S, ctx->M, ctx->basis, nf, a, st); });
+    TRY(cudaGetLastError());
+    *a_out = a;
+    return KLECGC_OK;
+}
+
+// want_fine: 0 none, 1 FP64, 2 FP64+FP32; want_cgc: 0 none, 1 FP64, 2 FP32.
+klecgc_status build_operators(klecgc_ctx* ctx, const double* xi_d, int64_t S, int N, int J,
+                              double dT, double alpha, int want_fine, int want_cgc,
+                              cudaStream_t st, Operators* op) {
+    const int nx = ctx->nx, nf = nx + 1, K = N / 2 + 1;
+    klecgc_status s = build_field(ctx, xi_d, S, st, &op->a);
+    if (s != KLECGC_OK) return s;
+    {
+        WS(double, wT, "wT", S * nf);
+        ctx->launch(KLECGC_K_FIELD, st, [&] { launch_face_weights(op->a, S, nf, dT / (ctx->h * ctx->h), wT, st); });
+        op->wT = wT;
+    }
+    if (want_fine == 1) {
+        WS(FineCoef64, f64, "fine64", S * nf);
+        ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_factors(op->a, S, nx, ctx->h, dT / J, ctx->prob.reaction, f64, nullptr, st); });
+        op->f64 = f64;
+    } else if (want_fine == 2) {
+        const int R = fine32_rows_per_lane(nx);
+        if (R == 0) return fail(KLECGC_E_UNSUPPORTED, "mixed precision needs nx <= 2047");
+        WS(float4, tA, "tab32A", S * 32 * (int64_t)R);
+        WS(float4, tD, "tab32D", S * 32 * (int64_t)R);
+        ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_table32(op->a, S, nx, R, ctx->h, dT / J, ctx->prob.reaction, tA, tD, st); });
+        op->tabA = tA;
+        op->tabD = tD;
+    }
+    if (want_cgc) {
+        std::vector<double2> lam(K);
+        const double a1n = std::pow(alpha, 1.0 / N), pi = 3.14159265358979323846;
+        for (int k = 0; k < K; ++k) {
+            // lambda_k = 1 - alpha^{1/N} exp(-2 pi i k / N)
+            lam[k].x = 1.0 - a1n * std::cos(2.0 * pi * k / N);
+            lam[k].y = a1n * std::sin(2.0 * pi * k / N);
+        }
+        WS(double2, lam_d, "lam", K);
+        TRY(cudaMemcpyAsync(lam_d, lam.data(), K * sizeof(double2), cudaMemcpyHostToDevice, st));
+        if (want_cgc == 1) {
+            WS(Cplx<double>, di, "cgc_dinv64", S * nx * K);
+            WS(Cplx<double>, lu, "cgc_lu64", S * nx * K);
+            ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_cgc_factors<double>(op->a, S, nx, ctx->h, dT, ctx->prob.reaction, lam_d, K, di, lu, st); });
+            op->dinv64 = di;
+            op->lu64 = lu;
+        } else {
+            WS(Cplx<float>, di, "cgc_dinv32", S * nx * K);
+            WS(Cplx<float>, lu, "cgc_lu32", S * nx * K);
+            ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_cgc_factors<float>(op->a, S, nx, ctx->h, dT, ctx->prob.reaction, lam_d, K, di, lu, st); });
+            op->dinv32 = di;
+            op->lu32 = lu;
+        }
+    }
+    TRY(cudaGetLastError());
+    return KLECGC_OK;
+}
+
+// alpha^{j/N} and alpha^{-j/N} / (N/2) tables in precision T.
+template <typename T>
+klecgc_status scale_tables(klecgc_ctx* ctx, int N, double alpha, cudaStream_t st, T** sc,
+                           T** isc) {
+    std::vector<T> a(N), b(N);
+    for (int j = 0; j < N; ++j) {
+        a[j] = (T)std::pow(alpha, (double)j / N);
+        b[j] = (T)(std::pow(alpha, -(double)j / N) / (N / 2));
+    }
+    const char* n1 = sizeof(T) == 8 ? "scale64" : "scale32";
+    const char* n2 = sizeof(T) == 8 ? "iscale64" : "iscale32";
+    WS(T, d1, n1, N);
+    WS(T, d2, n2, N);
+    TRY(cudaMemcpyAsync(d1, a.data(), N * sizeof(T), cudaMemcpyHostToDevice, st));
+    TRY(cudaMemcpyAsync(d2, b.data(), N * sizeof(T), cudaMemcpyHostToDevice, st));
+    *sc = d1;
+    *isc = d2;
+    return KLECGC_OK;
+}
+
+// U^0 = ubar + psi(xi) W into U (internal layout [S][nx][N]).
+klecgc_status gpc_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S, bool fp64,
+                                 double* U, cudaStream_t st) {
+    const int64_t NC = (int64_t)ctx->nx * ctx->N;
+    if (fp64) {
+        WS(double, psi, "psi64", S * ctx->P);
+        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_psi<double>(xi_d, S, ctx->M, ctx->degrees, ctx->P, psi, st); });
+        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_gemm<double>(S, NC, ctx->P, psi, ctx->P, 1, ctx->W, NC, 1, U, NC, false, ctx->ubar, st); });
+    } else {
+        WS(float, psi, "psi32", S * ctx->P);
+        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_psi<float>(xi_d, S, ctx->M, ctx->degrees, ctx->P, psi, st); });
+        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_gemm<float>(S, NC, ctx->P, psi, ctx->P, 1, ctx->W32, NC, 1, U, NC, false, ctx->ubar, st); });
+    }
+    TRY(cudaGetLastError());
+    return KLECGC_OK;
+}
+
+klecgc_status check_xi_finite(klecgc_ctx* ctx, const double* xi_d, int64_t n, cudaStream_t st,
+                              bool* finite) {
+    WS(int, flag, "flag", 1);
+    TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_nonfinite_flag(xi_d, n, flag, st); });
+    int h = 0;
+    TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    *finite = (h == 0);
+    return KLECGC_OK;
+}
+
+// Copies an internal [S][nx][N] batch to the caller's [S][N][nx] array.
+klecgc_status export_batch(klecgc_ctx* ctx, const double* U_int, int64_t S, int N, double* out,
+                           cudaStream_t st) {
+    const int nx = ctx->nx;
+    if (is_device_ptr(out)) {
+        ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_transpose(U_int, out, S, nx, N, st); });
+        TRY(cudaGetLastError());
+    } else {
+        WS(double, tmp, "export", S * (int64_t)nx * N);
+        ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_transpose(U_int, tmp, S, nx, N, st); });
+        TRY(cudaGetLastError());
+        TRY(cudaMemcpyAsync(out, tmp, S * (size_t)nx * N * sizeof(double), cudaMemcpyDeviceToHost,
+                            st));
+    }
+    return KLECGC_OK;
+}
+
+// Reads a caller [S][N][nx] array into internal layout.
+klecgc_status import_batch(klecgc_ctx* ctx, const double* user, int64_t S, int N, double* U_int,
+                           cudaStream_t st) {
+    const double* src = nullptr;
+    klecgc_status s = stage_in(ctx, user, (size_t)S * ctx->nx * N, "import", st, &src);
+    if (s != KLECGC_OK) return s;
+    ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_transpose(src, U_int, S, N, ctx->nx, st); });
+    TRY(cudaGetLastError());
+    return KLECGC_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* klecgc_status_string(klecgc_status s) {
+    switch (s) {
+        case KLECGC_OK: return "ok";
+        case KLECGC_E_INVALID_ARG: return "invalid argument";
+        case KLECGC_E_OUT_OF_MEMORY: return "out of device memory";
+        case KLECGC_E_NOT_CONVERGED: return "not converged within kmax iterations";
+        case KLECGC_E_NONFINITE: return "non-finite value";
+        case KLECGC_E_CUDA: return "CUDA runtime error";
+        case KLECGC_E_UNSUPPORTED: return "unsupported configuration";
+    }
+    return "unknown status";
+}
+
+const char* klecgc_last_error(void) { return g_last_error.c_str(); }
+
+void klecgc_free(klecgc_ctx* ctx) {
+    if (!ctx) return;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(ctx->device);
+    delete ctx;
+    cudaSetDevice(cur);
+}
+
+klecgc_status klecgc_info(const klecgc_ctx* ctx, klecgc_info_t* out) {
+    if (!ctx || !out) return fail(KLECGC_E_INVALID_ARG, "NULL argument");
+    out->nx = ctx->nx;
+    out->N = ctx->N;
+    out->J = ctx->J;
+    out->M = ctx->M;
+    out->P = ctx->P;
+    out->MQ = ctx->MQ;
+    out->lambda_sum = ctx->lambda_sum;
+    out->lambda_kept = ctx->lambda_kept;
+    out->n_unknowns = ctx->nx;
+    out->device = ctx->device;
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_profile_enable(klecgc_ctx* ctx, int32_t timing) {
+    if (!ctx) return fail(KLECGC_E_INVALID_ARG, "NULL context");
+    ctx->prof_collect();
+    ctx->prof_timing = timing != 0;
+    for (int i = 0; i < KLECGC_K_COUNT; ++i) {
+        ctx->prof_launches[i] = 0;
+        ctx->prof_ms[i] = 0.0;
+    }
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_profile_read(const klecgc_ctx* ctx, klecgc_profile_t* out) {
+    if (!ctx || !out) return fail(KLECGC_E_INVALID_ARG, "NULL argument");
+    std::memset(out, 0, sizeof(*out));
+    out->n_classes = KLECGC_K_COUNT;
+    for (int i = 0; i < KLECGC_K_COUNT; ++i) {
+        out->launches[i] = ctx->prof_launches[i];
+        out->ms[i] = ctx->prof_ms[i];
+    }
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, klecgc_ctx** out,
+                           void* stream) {
+    set_error("");
+    if (!pr || !out || !xi_train) return fail(KLECGC_E_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    if (pr->dim != 1) return fail(KLECGC_E_UNSUPPORTED, "only dim = 1 is built");
+    if (pr->nx < 1 || pr->M < 1 || pr->gpc_degree < 0 || pr->n_train < 2 || !(pr->T > 0) ||
+        !(pr->sigma >= 0) || !(pr->corr_len > 0) || !(pr->eps_kl >= 0) || pr->J < 1 ||
+        !(pr->reaction >= 0) || !std::isfinite(pr->forcing) || pr->u0_kind < 0 ||
+        pr->u0_kind > 1)
+        return fail(KLECGC_E_INVALID_ARG, "problem field out of range");
+    if (!pow2_in_range(pr->N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
+    cudaStream_t st = (cudaStream_t)stream;
+    klecgc_ctx* ctx = new klecgc_ctx();
+    ctx->prob = *pr;
+    cudaGetDevice(&ctx->device);
+    ctx->nx = pr->nx;
+    ctx->N = pr->N;
+    ctx->J = pr->J;
+    ctx->M = pr->M;
+    ctx->p = pr->gpc_degree;
+    ctx->h = 1.0 / (pr->nx + 1);
+    ctx->dT = pr->T / pr->N;
+    auto bail = [&](klecgc_status s) {
+        delete ctx;
+        return s;
+    };
+#define STRY(expr)                                                                          \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return bail(fail(e_ == cudaErrorMemoryAllocation ? KLECGC_E_OUT_OF_MEMORY       \
+                                                             : KLECGC_E_CUDA,               \
+                             std::string(#expr) + ": " + cudaGetErrorString(e_)));          \
+    } while (0)
+#define SCHK(expr)                          \
+    do {                                    \
+        klecgc_status s_ = (expr);          \
+        if (s_ != KLECGC_OK) return bail(s_); \
+    } while (0)
+    STRY(ensure_twiddles(ctx->device));
+    const int nx = ctx->nx, nf = nx + 1, N = ctx->N, M = ctx->M, nt = pr->n_train;
+    const int64_t NC = (int64_t)nx * N;
+
+    // 1. input KL basis at the faces, initial value, gPC multi-indices
+    std::vector<double> lam, om;
+    std::vector<int> par;
+    kl_modes_1d(pr->corr_len, pr->sigma, M, lam, om, par);
+    std::vector<double> basis((size_t)M * nf), u0(nx);
+    for (int m = 0; m < M; ++m)
+        for (int f = 0; f < nf; ++f)
+            basis[(size_t)m * nf + f] = std::sqrt(lam[m]) * kl_phi_1d((f + 0.5) * ctx->h, om[m], par[m]);
+    for (int i = 0; i < nx; ++i)
+        u0[i] = pr->u0_kind == 0 ? std::sin(3.14159265358979323846 * (i + 1) * ctx->h) : 0.0;
+    std::vector<int> deg = gpc_multi_indices(M, ctx->p);
+    ctx->P = (int)(deg.size() / M);
+    const int P = ctx->P;
+    STRY(ctx->alloc_owned(&ctx->basis, basis.size()));
+    STRY(ctx->alloc_owned(&ctx->u0, nx));
+    STRY(ctx->alloc_owned(&ctx->degrees, deg.size()));
+    STRY(cudaMemcpyAsync(ctx->basis, basis.data(), basis.size() * 8, cudaMemcpyHostToDevice, st));
+    STRY(cudaMemcpyAsync(ctx->u0, u0.data(), nx * 8, cudaMemcpyHostToDevice, st));
+    STRY(cudaMemcpyAsync(ctx->degrees, deg.data(), deg.size() * 4, cudaMemcpyHostToDevice, st));
+
+    // 2. snapshots: sequential fine solution of every training sample
+    const double* xi_d = nullptr;
+    SCHK(stage_in(ctx, xi_train, (size_t)nt * M, "xi_train", st, &xi_d));
+    bool finite = true;
+    SCHK(check_xi_finite(ctx, xi_d, (int64_t)nt * M, st, &finite));
+    if (!finite) return bail(fail(KLECGC_E_NONFINITE, "xi_train has a non-finite entry"));
+    Operators op;
+    SCHK(build_operators(ctx, xi_d, nt, N, ctx->J, ctx->dT, 0.5, 1, 0, st, &op));
+    double* Y = nullptr;
+    STRY(cudaMalloc(&Y, (size_t)nt * NC * 8));
+    struct Guard {
+        double* p;
+        ~Guard() { cudaFree(p); }
+    } gY{Y};
+    {
+        WS(double, scr, "seq_scratch", (size_t)nt * nx);
+        if (!scr) return bail(KLECGC_E_OUT_OF_MEMORY);
+        launch_fine_sequential(nt, N, nx, ctx->J, ctx->dT / ctx->J * pr->forcing, ctx->u0, op.f64,
+                               scr, Y, st);
+    }
+    // 3. mean and covariance C = Ytilde Ytilde^T / n_t
+    STRY(ctx->alloc_owned(&ctx->ubar, NC));
+    launch_mean_center(Y, nt, NC, ctx->ubar, st);
+    double* Cd = nullptr;
+    STRY(cudaMalloc(&Cd, (size_t)nt * nt * 8));
+    Guard gC{Cd};
+    launch_gemm<double>(nt, nt, NC, Y, NC, 1, Y, 1, NC, Cd, nt, false, nullptr, st);
+    STRY(cudaGetLastError());
+    std::vector<double> C((size_t)nt * nt);
+    STRY(cudaMemcpyAsync(C.data(), Cd, C.size() * 8, cudaMemcpyDeviceToHost, st));
+    STRY(cudaStreamSynchronize(st));
+    for (double& c : C) c /= nt;
+    std::vector<double> ev, V;
+    if (!sym_eig(nt, C, ev, V)) return bail(fail(KLECGC_E_CUDA, "eigensolver did not converge"));
+    double total = 0.0;
+    for (double e : ev) total += e;
+    ctx->lambda_sum = total;
+    // M_Q: smallest count with captured fraction >= 1 - eps_kl, at most n_t - 1
+    int MQ = nt - 1;
+    double acc = 0.0;
+    for (int k = 0; k < nt; ++k) {
+        acc += ev[k];
+        if (acc >= (1.0 - pr->eps_kl) * total) {
+            MQ = k + 1;
+            break;
+        }
+    }
+    MQ = std::max(1, std::min(MQ, nt - 1));
+    while (MQ > 1 && !(ev[MQ - 1] > 0)) --MQ;
+    ctx->MQ = MQ;
+    ctx->lambda_kept = 0.0;
+    for (int k = 0; k < MQ; ++k) ctx->lambda_kept += ev[k];
+    // 4. modes g_k = (lambda_k n_t)^{-1/2} sum_j e_k^j ytilde_j, and
+    //    zeta_k(xi_j) = lambda_k^{-1/2} (ytilde_j, g_k) = sqrt(n_t) e_k^j
+    std::vector<double> Es((size_t)nt * MQ), Dz((size_t)nt * MQ);
+    for (int j = 0; j < nt; ++j)
+        for (int k = 0; k < MQ; ++k) {
+            double e = V[(size_t)j * nt + k];
+            Es[(size_t)j * MQ + k] = e / std::sqrt(ev[k] * nt);
+            Dz[(size_t)j * MQ + k] = std::sqrt((double)nt) * e;
+        }
+    double *Esd = nullptr, *Gd = nullptr;
+    STRY(cudaMalloc(&Esd, Es.size() * 8));
+    Guard gE{Esd};
+    STRY(cudaMalloc(&Gd, (size_t)MQ * NC * 8));
+    Guard gG{Gd};
+    STRY(cudaMemcpyAsync(Esd, Es.data(), Es.size() * 8, cudaMemcpyHostToDevice, st));
+    // G[k][c] = sum_j Es[j][k] Y[j][c]
+    launch_gemm<double>(MQ, NC, nt, Esd, 1, MQ, Y, NC, 1, Gd, NC, false, nullptr, st);
+    // 5. B = psi(Xi_t), least squares H = argmin ||B H - D||
+    double* Bd = nullptr;
+    STRY(cudaMalloc(&Bd, (size_t)nt * P * 8));
+    Guard gB{Bd};
+    launch_psi<double>(xi_d, nt, M, ctx->degrees, P, Bd, st);
+    STRY(cudaGetLastError());
+    std::vector<double> B((size_t)nt * P);
+    STRY(cudaMemcpyAsync(B.data(), Bd, B.size() * 8, cudaMemcpyDeviceToHost, st));
+    STRY(cudaStreamSynchronize(st));
+    if (nt < P) return bail(fail(KLECGC_E_INVALID_ARG, "n_train must be >= number of gPC terms"));
+    std::vector<double> H;
+    if (!lstsq(nt, P, MQ, B, Dz, H))
+        return bail(fail(KLECGC_E_INVALID_ARG, "gPC design matrix is rank deficient"));
+    // 6. W = (H diag(sqrt(lambda))) G
+    for (int j = 0; j < P; ++j)
+        for (int k = 0; k < MQ; ++k) H[(size_t)j * MQ + k] *= std::sqrt(ev[k]);
+    double* Hd = nullptr;
+    STRY(cudaMalloc(&Hd, H.size() * 8));
+    Guard gH{Hd};
+    STRY(cudaMemcpyAsync(Hd, H.data(), H.size() * 8, cudaMemcpyHostToDevice, st));
+    STRY(ctx->alloc_owned(&ctx->W, (size_t)P * NC));
+    STRY(ctx->alloc_owned(&ctx->W32, (size_t)P * NC));
+    launch_gemm<double>(P, NC, MQ, Hd, MQ, 1, Gd, NC, 1, ctx->W, NC, false, nullptr, st);
+    launch_to_float(ctx->W, ctx->W32, (int64_t)P * NC, st);
+    STRY(cudaGetLastError());
+    STRY(cudaStreamSynchronize(st));
+    // release the training-sized scratch
+    for (auto& kv : ctx->ws)
+        if (kv.second.ptr) cudaFree(kv.second.ptr);
+    ctx->ws.clear();
+    *out = ctx;
+    return KLECGC_OK;
+#undef STRY
+#undef SCHK
+}
+
+klecgc_status klecgc_field(klecgc_ctx* ctx, const double* xi, int64_t S, double* a_out,
+                           void* stream) {
+    set_error("");
+    if (!ctx || !xi || !a_out || S < 0) return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (S == 0) return KLECGC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* xi_d = nullptr;
+    klecgc_status s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d);
+    if (s != KLECGC_OK) return s;
+    double* a = nullptr;
+    if ((s = build_field(ctx, xi_d, S, st, &a)) != KLECGC_OK) return s;
+    TRY(cudaMemcpyAsync(a_out, a, (size_t)S * (ctx->nx + 1) * 8, cudaMemcpyDefault, st));
+    TRY(cudaStreamSynchronize(st));
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_guess(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t precision,
+                           double* U0_out, void* stream) {
+    set_error("");
+    if (!ctx || !xi || !U0_out || S < 0 || precision < 0 || precision > 2)
+        return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (S == 0) return KLECGC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* xi_d = nullptr;
+    klecgc_status s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d);
+    if (s != KLECGC_OK) return s;
+    WS(double, U, "U", S * (int64_t)ctx->nx * ctx->N);
+    if ((s = gpc_guess_internal(ctx, xi_d, S, precision == KLECGC_FP64, U, st)) != KLECGC_OK)
+        return s;
+    if ((s = export_batch(ctx, U, S, ctx->N, U0_out, st)) != KLECGC_OK) return s;
+    TRY(cudaStreamSynchronize(st));
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_reference(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t N, int32_t J,
+                               double* U_out, void* stream) {
+    set_error("");
+    if (!ctx || !xi || !U_out || S < 0 || N < 1 || J < 1)
+        return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (S == 0) return KLECGC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* xi_d = nullptr;
+    klecgc_status s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d);
+    if (s != KLECGC_OK) return s;
+    const double dT = ctx->prob.T / N;
+    Operators op;
+    if ((s = build_operators(ctx, xi_d, S, N, J, dT, 0.5, 1, 0, st, &op)) != KLECGC_OK) return s;
+    WS(double, scr, "seq_scratch", S * (int64_t)ctx->nx);
+    WS(double, U, "Uref", S * (int64_t)ctx->nx * N);
+    launch_fine_sequential(S, N, ctx->nx, J, dT / J * ctx->prob.forcing, ctx->u0, op.f64, scr, U,
+                           st);
+    TRY(cudaGetLastError());
+    if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) return s;
+    TRY(cudaStreamSynchronize(st));
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t N,
+                                const double* U_in, double dT, int32_t J, double alpha,
+                                int32_t precision, double* r_out, void* stream) {
+    set_error("");
+    if (!ctx || !xi || !U_in || !r_out || S < 0 || J < 1 || !(alpha > 0 && alpha < 1) ||
+        precision < 0 || precision > 2)
+        return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (!pow2_in_range(N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
+    klecgc_status s = check_dT(ctx, N, dT);
+    if (s != KLECGC_OK || S == 0) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nx = ctx->nx;
+    const double* xi_d = nullptr;
+    if ((s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d)) != KLECGC_OK) return s;
+    Operators op;
+    if ((s = build_operators(ctx, xi_d, S, N, J, dT, alpha, precision == KLECGC_FP64 ? 1 : 2, 0,
+                             st, &op)) != KLECGC_OK)
+        return s;
+    WS(double, U, "U", S * (int64_t)nx * N);
+    if ((s = import_batch(ctx, U_in, S, N, U, st)) != KLECGC_OK) return s;
+    WS(double, r, "r", S * (int64_t)nx * N);
+    WS(int, active, "active", S);
+    TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
+    if (precision == KLECGC_FP64) {
+        launch_fine_sweep_fp64(S, N, nx, J, dT, alpha, ctx->prob.reaction, ctx->prob.forcing, U,
+                               ctx->u0, op.f64, op.wT, r, active, st);
+    } else {
+        WS(double, Facc, "Facc", S * (int64_t)nx * N);
+        launch_fine32(S, N, nx, J, dT / J, dT, alpha, ctx->prob.reaction, ctx->prob.forcing, U,
+                      ctx->u0, nullptr, Facc, 0, op.tabA, op.tabD, op.wT, r, nullptr, 0, active,
+                      st);
+    }
+    TRY(cudaGetLastError());
+    if ((s = export_batch(ctx, r, S, N, r_out, st)) != KLECGC_OK) return s;
+    TRY(cudaStreamSynchronize(st));
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t N,
+                               const double* r_in, double dT, double alpha, int32_t precision,
+                               double* u_out, void* stream) {
+    set_error("");
+    if (!ctx || !xi || !r_in || !u_out || S < 0 || !(alpha > 0 && alpha < 1) ||
+        (precision != KLECGC_FP64 && precision != KLECGC_MIXED_DEFECT))
+        return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (!pow2_in_range(N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
+    klecgc_status s = check_dT(ctx, N, dT);
+    if (s != KLECGC_OK || S == 0) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nx = ctx->nx, K = N / 2 + 1;
+    const double* xi_d = nullptr;
+    if ((s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d)) != KLECGC_OK) return s;
+    const bool f64 = precision == KLECGC_FP64;
+    Operators op;
+    if ((s = build_operators(ctx, xi_d, S, N, 1, dT, alpha, 0, f64 ? 1 : 2, st, &op)) != KLECGC_OK)
+        return s;
+    WS(double, r, "r", S * (int64_t)nx * N);
+    if ((s = import_batch(ctx, r_in, S, N, r, st)) != KLECGC_OK) return s;
+    WS(double, U, "U", S * (int64_t)nx * N);
+    WS(int, active, "active", S);
+    TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
+    if (f64) {
+        double *sc, *isc;
+        if ((s = scale_tables<double>(ctx, N, alpha, st, &sc, &isc)) != KLECGC_OK) return s;
+        WS(Cplx<double>, p, "p64", S * (int64_t)nx * K);
+        launch_cgc_forward<double, double>(S, N, nx, r, sc, p, active, st);
+        launch_cgc_solve<double>(S, K, nx, op.dinv64, op.lu64, op.wT, p, active, st);
+        launch_cgc_inverse<double>(S, N, nx, p, isc, U, 2, nullptr, nullptr, active, st);
+    } else {
+        float *sc, *isc;
+        if ((s = scale_tables<float>(ctx, N, alpha, st, &sc, &isc)) != KLECGC_OK) return s;
+        WS(float, r32, "d32", S * (int64_t)nx * N);
+        launch_to_float(r, r32, S * (int64_t)nx * N, st);
+        WS(Cplx<float>, p, "p32", S * (int64_t)nx * K);
+        launch_cgc_forward<float, float>(S, N, nx, r32, sc, p, active, st);
+        launch_cgc_solve<float>(S, K, nx, op.dinv32, op.lu32, op.wT, p, active, st);
+        launch_cgc_inverse<float>(S, N, nx, p, isc, U, 2, nullptr, nullptr, active, st);
+    }
+    TRY(cudaGetLastError());
+    if ((s = export_batch(ctx, U, S, N, u_out, st)) != KLECGC_OK) return s;
+    TRY(cudaStreamSynchronize(st));
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double dT, int32_t J,
+                           int32_t N, double alpha, double tol, int32_t kmax, int32_t precision,
+                           int32_t guess, const double* U_guess, double* U_out, int32_t* iters_out,
+                           int32_t* status_out, void* stream) {
+    set_error("");
+    if (!ctx) return fail(KLECGC_E_INVALID_ARG, "NULL context");
+    if (S < 0 || (S > 0 && (!xi || !U_out))) return fail(KLECGC_E_INVALID_ARG, "bad array argument");
+    if (J < 1 || !(alpha > 0 && alpha < 1) || !(tol > 0) || kmax < 1 || precision < 0 ||
+        precision > 2 || guess < 0 || guess > 3 || (guess == KLECGC_GUESS_USER && !U_guess && S > 0))
+        return fail(KLECGC_E_INVALID_ARG, "argument out of range");
+    if (!pow2_in_range(N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
+    if (guess == KLECGC_GUESS_GPC && N != ctx->N)
+        return fail(KLECGC_E_INVALID_ARG, "the gPC guess needs the setup's N");
+    if (guess == KLECGC_GUESS_COARSE) return fail(KLECGC_E_UNSUPPORTED, "coarse guess not built");
+    klecgc_status s = check_dT(ctx, N, dT);
+    if (s != KLECGC_OK) return s;
+    if (S == 0) return KLECGC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nx = ctx->nx, K = N / 2 + 1;
+    const int64_t NS = S * (int64_t)nx * N;
+
+    const double* xi_d = nullptr;
+    if ((s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d)) != KLECGC_OK) return s;
+    bool finite = true;
+    if ((s = check_xi_finite(ctx, xi_d, S * ctx->M, st, &finite)) != KLECGC_OK) return s;
+    if (!finite) {
+        if (status_out) {
+            std::vector<int32_t> v(S, KLECGC_E_NONFINITE);
+            TRY(cudaMemcpyAsync(status_out, v.data(), S * 4, cudaMemcpyDefault, st));
+            TRY(cudaStreamSynchronize(st));
+        }
+        return fail(KLECGC_E_NONFINITE, "xi has a non-finite entry");
+    }
+    const bool f64 = precision == KLECGC_FP64;
+    const bool defect = precision == KLECGC_MIXED_DEFECT;
+    Operators op;
+    if ((s = build_operators(ctx, xi_d, S, N, J, dT, alpha, f64 ? 1 : 2, defect ? 2 : 1, st, &op)) !=
+        KLECGC_OK)
+        return s;
+
+    WS(double, U, "U", NS);
+    if (guess == KLECGC_GUESS_GPC) {
+        if ((s = gpc_guess_internal(ctx, xi_d, S, f64, U, st)) != KLECGC_OK) return s;
+    } else if (guess == KLECGC_GUESS_ZERO) {
+        TRY(cudaMemsetAsync(U, 0, NS * sizeof(double), st));
+    } else {
+        if ((s = import_batch(ctx, U_guess, S, N, U, st)) != KLECGC_OK) return s;
+    }
+    WS(int, active, "active", S);
+    WS(int32_t, iters, "iters", S);
+    WS(int32_t, status, "status", S);
+    WS(unsigned long long, delta, "delta", S);
+    WS(int, n_active, "n_active", 1);
+    TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
+    TRY(cudaMemsetAsync(iters, 0xff, S * sizeof(int32_t), st));
+    TRY(cudaMemsetAsync(status, 0, S * sizeof(int32_t), st));
+    TRY(cudaMemsetAsync(delta, 0, S * sizeof(unsigned long long), st));
+
+    double *sc64 = nullptr, *isc64 = nullptr;
+    float *sc32 = nullptr, *isc32 = nullptr;
+    if (defect) {
+        if ((s = scale_tables<float>(ctx, N, alpha, st, &sc32, &isc32)) != KLECGC_OK) return s;
+    } else {
+        if ((s = scale_tables<double>(ctx, N, alpha, st, &sc64, &isc64)) != KLECGC_OK) return s;
+    }
+    double* r = nullptr;
+    float* d32 = nullptr;
+    Cplx<double>* p64 = nullptr;
+    Cplx<float>* p32 = nullptr;
+    if (!defect) {
+        WS(double, rr, "r", NS);
+        WS(Cplx<double>, pp, "p64", S * (int64_t)nx * K);
+        r = rr;
+        p64 = pp;
+    } else {
+        WS(float, dd, "d32", NS);
+        WS(Cplx<float>, pp, "p32", S * (int64_t)nx * K);
+        d32 = dd;
+        p32 = pp;
+    }
+    double* Facc = nullptr;
+    float* c32 = nullptr;
+    if (!f64) {
+        WS(double, fa, "Facc", NS);
+        WS(float, cc, "c32", NS);
+        Facc = fa;
+        c32 = cc;
+    }
+    int* h_active = nullptr;
+    TRY(cudaMallocHost(&h_active, sizeof(int)));
+    struct HostGuard {
+        int* p;
+        ~HostGuard() { cudaFreeHost(p); }
+    } hg{h_active};
+
+    for (int k = 0; k < kmax; ++k) {
+        if (f64) {
+            ctx->launch(KLECGC_K_FINE, st, [&] {
+                launch_fine_sweep_fp64(S, N, nx, J, dT, alpha, ctx->prob.reaction,
+                                       ctx->prob.forcing, U, ctx->u0, op.f64, op.wT, r, active, st);
+            });
+        } else {
+            ctx->launch(KLECGC_K_FINE, st, [&] {
+                launch_fine32(S, N, nx, J, dT / J, dT, alpha, ctx->prob.reaction,
+                              ctx->prob.forcing, U, ctx->u0, c32, Facc, k == 0 ? 0 : 1, op.tabA,
+                              op.tabD, op.wT, r, d32, defect ? 1 : 0, active, st);
+            });
+        }
+        if (!defect) {
+            ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<double, double>(S, N, nx, r, sc64, p64, active, st); });
+            ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_cgc_solve<double>(S, K, nx, op.dinv64, op.lu64, op.wT, p64, active, st); });
+            ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc64, U, 0, delta, c32, active, st); });
+        } else {
+            ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<float, float>(S, N, nx, d32, sc32, p32, active, st); });
+            ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_cgc_solve<float>(S, K, nx, op.dinv32, op.lu32, op.wT, p32, active, st); });
+            ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<float>(S, N, nx, p32, isc32, U, 1, delta, c32, active, st); });
+        }
+        TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
+        ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
+        TRY(cudaGetLastError());
+        TRY(cudaMemcpyAsync(h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (*h_active == 0) break;
+    }
+    if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) return s;
+    std::vector<int32_t> hs(S), hi(S);
+    TRY(cudaMemcpyAsync(hs.data(), status, S * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(hi.data(), iters, S * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    ctx->prof_collect();
+    if (iters_out) TRY(cudaMemcpy(iters_out, hi.data(), S * 4, cudaMemcpyDefault));
+    if (status_out) TRY(cudaMemcpy(status_out, hs.data(), S * 4, cudaMemcpyDefault));
+    bool any_nf = false, any_nc = false;
+    for (int64_t i = 0; i < S; ++i) {
+        any_nf |= hs[i] == KLECGC_E_NONFINITE;
+        any_nc |= hs[i] == KLECGC_E_NOT_CONVERGED;
+    }
+    if (any_nf) return fail(KLECGC_E_NONFINITE, "a sample produced a non-finite iterate");
+    if (any_nc) return fail(KLECGC_E_NOT_CONVERGED, "a sample did not reach tol within kmax");
+    return KLECGC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,114 @@
+// Internal declarations shared by the translation units of libklecgc.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string>
+
+namespace klecgc {
+
+constexpr int kMaxN = 128;          // largest coarse-interval count (power of 2)
+constexpr int kTwiddleN = 128;      // cos/sin(2 pi t / 128) tables, t < 128
+
+template <typename T>
+struct Cplx {
+    T x, y;
+};
+
+// Fine-propagator coefficients of one row i of M = I + dt (A + c I), stored
+// per sample.  `l` is the LU multiplier of row i (0 for i = 0), `dinv` the
+// reciprocal pivot, `wd` = dt * a_{i-1/2} / h^2 (the weight of the face left
+// of row i; the off-diagonal M_{i-1,i} = M_{i,i-1} = -wd_i).
+struct alignas(32) FineCoef64 {
+    double l, dinv, wd, pad;
+};
+struct alignas(16) FineCoef32 {
+    float l, dinv, wd, pad;
+};
+
+// cos/sin(2 pi t / 128) in constant memory (set once per device).
+void upload_twiddles();
+
+// ---- k_field.cu ----
+void launch_field(const double* xi, int64_t S, int M, const double* basis, int nf, double* a,
+                  cudaStream_t st);
+void launch_fine_factors(const double* a, int64_t S, int nx, double h, double dt, double react,
+                         FineCoef64* f64, FineCoef32* f32, cudaStream_t st);
+template <typename T>
+void launch_cgc_factors(const double* a, int64_t S, int nx, double h, double dT, double react,
+                        const double2* lam, int K, Cplx<T>* dinv, Cplx<T>* lu, cudaStream_t st);
+void launch_face_weights(const double* a, int64_t S, int nf, double scale, double* w,
+                         cudaStream_t st);
+void launch_nonfinite_flag(const double* x, int64_t n, int* flag, cudaStream_t st);
+
+// ---- k_guess.cu ----
+template <typename T>
+void launch_psi(const double* xi, int64_t S, int M, const int* degrees, int P, T* psi,
+                cudaStream_t st);
+// C[m][n] (+)= sum_k A(m,k) B(k,n); A(m,k) = A[m*lda_m + k*lda_k], B likewise,
+// C row-major with leading dimension ldc; C is FP64, A/B of type T.
+template <typename T>
+void launch_gemm(int64_t Mr, int64_t Nc, int64_t K, const T* A, int64_t lda_m, int64_t lda_k,
+                 const T* B, int64_t ldb_k, int64_t ldb_n, double* C, int64_t ldc, bool accumulate,
+                 const double* row_bias, cudaStream_t st);
+void launch_mean_center(double* Y, int64_t rows, int64_t cols, double* mean, cudaStream_t st);
+void launch_to_float(const double* x, float* y, int64_t n, cudaStream_t st);
+
+// ---- k_fine.cu ----
+// Step 1 of Algorithm 2 plus the CGC right-hand side, internal layout
+// [S][nx][N] (time fastest).  out_mode 0: r = (I + dT A) F - prev;
+// out_mode 1 (defect): d = (I + dT A)(F - U_n), written as FP32.
+void launch_fine_sweep_fp64(int64_t S, int N, int nx, int J, double dT, double alpha, double react,
+                            double forcing, const double* U, const double* u0,
+                            const FineCoef64* fc, const double* wT, double* r, const int* active,
+                            cudaStream_t st);
+// ---- k_fine32.cu ----
+// FP32 increment-form fine sweep, register resident.  in_mode 0: Facc = F(start);
+// in_mode 1: Facc += F0(c32 of interval n-1).  out_mode 0: r (FP64); 1: defect d32.
+int fine32_rows_per_lane(int nx);
+void launch_fine_table32(const double* a, int64_t S, int nx, int R, double h, double dt,
+                         double react, float4* tabA, float4* tabD, cudaStream_t st);
+void launch_fine32(int64_t S, int N, int nx, int J, double dt, double dT, double alpha,
+                   double react, double forcing, const double* U, const double* u0,
+                   const float* c32, double* Facc, int in_mode, const float4* tabA,
+                   const float4* tabD, const double* wT, double* r, float* d32, int out_mode,
+                   const int* active, cudaStream_t st);
+void launch_fine_sequential(int64_t S, int N, int nx, int J, double dt_forcing, const double* u0,
+                            const FineCoef64* fc, double* scratch, double* U, cudaStream_t st);
+
+// ---- k_cgc.cu ----
+// Step (a): p[s][i][k] = sum_j alpha^{j/N} r[s][i][j] exp(-2 pi i j k / N), k <= N/2.
+template <typename T, typename TIN>
+void launch_cgc_forward(int64_t S, int N, int nx, const TIN* r, const T* scale, Cplx<T>* p,
+                        const int* active, cudaStream_t st);
+// Step (b): (lambda_k I + dT A) q_k = p_k in place.
+template <typename T>
+void launch_cgc_solve(int64_t S, int K, int nx, const Cplx<T>* dinv, const Cplx<T>* lu,
+                      const double* wT, Cplx<T>* p, const int* active, cudaStream_t st);
+// Step (c) + update: u_j = alpha^{-j/N} (1/N) sum_k q_k exp(+2 pi i j k / N).
+// mode 0: U <- u, delta = max|u - U_old|;  mode 1: U <- U + u, delta = max|u|;
+// mode 2: out <- u (no delta).  In modes 0 and 1 the increment U_new - U_old is
+// also stored as FP32 in c32 when c32 is not null.
+template <typename T>
+void launch_cgc_inverse(int64_t S, int N, int nx, const Cplx<T>* q, const T* iscale, double* U,
+                        int mode, unsigned long long* delta, float* c32, const int* active,
+                        cudaStream_t st);
+void launch_convergence(int64_t S, int iter, int kmax, double tol, unsigned long long* delta,
+                        int* active, int32_t* iters, int32_t* status, int* n_active,
+                        cudaStream_t st);
+// [S][A][B] -> [S][B][A] (FP64).
+void launch_transpose(const double* in, double* out, int64_t S, int A, int B, cudaStream_t st);
+
+// Thread-local last-error detail.
+void set_error(const std::string& msg);
+
+}  // namespace klecgc
+
+#define KLECGC_CUDA_TRY(expr)                                                                  \
+    do {                                                                                       \
+        cudaError_t e_ = (expr);                                                               \
+        if (e_ != cudaSuccess) {                                                               \
+            klecgc::set_error(std::string(#expr) + ": " + cudaGetErrorString(e_));              \
+            return e_ == cudaErrorMemoryAllocation ? KLECGC_E_OUT_OF_MEMORY : KLECGC_E_CUDA;   \
+        }                                                                                      \
+    } while (0)

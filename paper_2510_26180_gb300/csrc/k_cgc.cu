@@ -1,0 +1,417 @@
+// Diagonalized coarse grid correction (hot-path rows a5-a9), eq. three steps:
+//   (a) p = F_N^* (Lambda_alpha r)            real DFT along the N coarse times
+//   (b) (lambda_k I + dT(A + cI)) q_k = p_k   one complex tridiagonal solve per k
+//   (c) u = Lambda_alpha^{-1} F_N q           inverse DFT, fused with the update
+//                                             and the per-sample increment norm
+// with Lambda_alpha = diag(alpha^{j/N}) and lambda_k = 1 - alpha^{1/N} e^{-2 pi i k/N}.
+// (The eigenvector matrix is Lambda_alpha^{-1} F_N: the printed Lambda_alpha F_N
+// does not diagonalize C_alpha.)  Real r makes p Hermitian, p_{N-k} = conj(p_k),
+// and since A is real the same holds for q, so only k = 0..N/2 are solved.
+// The 1/sqrt(N) factors of F_N and F_N^* are combined into one 1/N in (c).
+//
+// Layouts: r, U: [S][nx][N]; p, q and the factors: [S][nx][K], K = N/2 + 1.
+#include <cmath>
+
+#include "common.cuh"
+
+namespace klecgc {
+
+__constant__ double c_cos64[kTwiddleN];
+__constant__ double c_sin64[kTwiddleN];
+__constant__ float c_cos32[kTwiddleN];
+__constant__ float c_sin32[kTwiddleN];
+
+void upload_twiddles() {
+    double c[kTwiddleN], s[kTwiddleN];
+    float cf[kTwiddleN], sf[kTwiddleN];
+    for (int t = 0; t < kTwiddleN; ++t) {
+        // exact values at the quarter points keep the trivial twiddles exact
+        double ang = 2.0 * 3.14159265358979323846 * t / kTwiddleN;
+        c[t] = (t == 32 || t == 96) ? 0.0 : std::cos(ang);
+        s[t] = (t == 0 || t == 64) ? 0.0 : std::sin(ang);
+        cf[t] = (float)c[t];
+        sf[t] = (float)s[t];
+    }
+    cudaMemcpyToSymbol(c_cos64, c, sizeof(c));
+    cudaMemcpyToSymbol(c_sin64, s, sizeof(s));
+    cudaMemcpyToSymbol(c_cos32, cf, sizeof(cf));
+    cudaMemcpyToSymbol(c_sin32, sf, sizeof(sf));
+}
+
+template <typename T>
+__device__ __forceinline__ T tw_cos(int t);
+template <typename T>
+__device__ __forceinline__ T tw_sin(int t);
+template <>
+__device__ __forceinline__ double tw_cos<double>(int t) { return c_cos64[t]; }
+template <>
+__device__ __forceinline__ double tw_sin<double>(int t) { return c_sin64[t]; }
+template <>
+__device__ __forceinline__ float tw_cos<float>(int t) { return c_cos32[t]; }
+template <>
+__device__ __forceinline__ float tw_sin<float>(int t) { return c_sin32[t]; }
+
+template <int L>
+__host__ __device__ constexpr int bitrev(int i) {
+    int r = 0;
+    for (int b = 1; b < L; b <<= 1) {
+        r = (r << 1) | (i & 1);
+        i >>= 1;
+    }
+    return r;
+}
+
+// In-register radix-2 complex FFT of length L (power of 2), unnormalized,
+// sign -1 (forward) or +1 (INV).  All indices are compile-time constants.
+template <typename T, int L, bool INV>
+__device__ __forceinline__ void cfft(T (&re)[L], T (&im)[L]) {
+#pragma unroll
+    for (int i = 0; i < L; ++i) {
+        const int j = bitrev<L>(i);
+        if (j > i) {
+            T a = re[i]; re[i] = re[j]; re[j] = a;
+            T b = im[i]; im[i] = im[j]; im[j] = b;
+        }
+    }
+#pragma unroll
+    for (int half = 1; half < L; half *= 2) {
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const int t = k * (kTwiddleN / (2 * half));
+            T wr = (T)1, wi = (T)0;
+            if (k != 0) {
+                wr = tw_cos<T>(t);
+                wi = INV ? tw_sin<T>(t) : -tw_sin<T>(t);
+            }
+#pragma unroll
+            for (int b = 0; b < L; b += 2 * half) {
+                const int i0 = b + k, i1 = i0 + half;
+                T xr, xi;
+                if (k == 0) {
+                    xr = re[i1];
+                    xi = im[i1];
+                } else {
+                    xr = re[i1] * wr - im[i1] * wi;
+                    xi = re[i1] * wi + im[i1] * wr;
+                }
+                re[i1] = re[i0] - xr;
+                im[i1] = im[i0] - xi;
+                re[i0] = re[i0] + xr;
+                im[i0] = im[i0] + xi;
+            }
+        }
+    }
+}
+
+constexpr int kTX = 32;  // x points per CTA in the transform kernels
+
+// (a): thread x of the tile transforms its own time series.
+template <typename T, typename TIN, int N>
+__global__ void __launch_bounds__(kTX) k_cgc_forward(int64_t S, int nx, const TIN* __restrict__ r,
+                                                     const T* __restrict__ scale,
+                                                     Cplx<T>* __restrict__ p,
+                                                     const int* __restrict__ active) {
+    constexpr int L = N / 2, K = N / 2 + 1;
+    __shared__ T sin_[kTX][N + 1];
+    __shared__ Cplx<T> sout[kTX * K];
+    const int64_t s = blockIdx.x;
+    if (!active[s]) return;
+    const int x0 = blockIdx.y * kTX;
+    const int rows = min(kTX, nx - x0);
+    const int tid = threadIdx.x;
+    const TIN* rin = r + (s * nx + x0) * (int64_t)N;
+    for (int e = tid; e < rows * N; e += kTX) {
+        int row = e / N, col = e - row * N;
+        sin_[row][col] = (T)rin[e] * scale[col];
+    }
+    __syncthreads();
+    if (tid < rows) {
+        T zr[L], zi[L];
+#pragma unroll
+        for (int m = 0; m < L; ++m) {
+            zr[m] = sin_[tid][2 * m];
+            zi[m] = sin_[tid][2 * m + 1];
+        }
+        cfft<T, L, false>(zr, zi);
+        Cplx<T>* o = sout + tid * K;
+#pragma unroll
+        for (int k = 0; k <= L; ++k) {
+            const int kk = k % L, km = (L - k) % L;
+            T Er = (T)0.5 * (zr[kk] + zr[km]), Ei = (T)0.5 * (zi[kk] - zi[km]);
+            T Or = (T)0.5 * (zi[kk] + zi[km]), Oi = (T)-0.5 * (zr[kk] - zr[km]);
+            T wr = (T)1, wi = (T)0;
+            if (k != 0) {
+                const int t = k * (kTwiddleN / N);
+                wr = tw_cos<T>(t);
+                wi = -tw_sin<T>(t);
+            }
+            o[k] = Cplx<T>{Er + wr * Or - wi * Oi, Ei + wr * Oi + wi * Or};
+        }
+    }
+    __syncthreads();
+    Cplx<T>* pout = p + (s * nx + x0) * (int64_t)K;
+    for (int e = tid; e < rows * K; e += kTX) pout[e] = sout[e];
+}
+
+template <typename T, typename TIN>
+void launch_cgc_forward(int64_t S, int N, int nx, const TIN* r, const T* scale, Cplx<T>* p,
+                        const int* active, cudaStream_t st) {
+    if (S == 0) return;
+    dim3 grid((unsigned)S, (unsigned)((nx + kTX - 1) / kTX));
+    switch (N) {
+#define KLECGC_FWD_CASE(NN) \
+    case NN: k_cgc_forward<T, TIN, NN><<<grid, kTX, 0, st>>>(S, nx, r, scale, p, active); break;
+        KLECGC_FWD_CASE(2)
+        KLECGC_FWD_CASE(4)
+        KLECGC_FWD_CASE(8)
+        KLECGC_FWD_CASE(16)
+        KLECGC_FWD_CASE(32)
+        KLECGC_FWD_CASE(64)
+#undef KLECGC_FWD_CASE
+        default: break;
+    }
+}
+template void launch_cgc_forward<double, double>(int64_t, int, int, const double*, const double*,
+                                                 Cplx<double>*, const int*, cudaStream_t);
+template void launch_cgc_forward<float, float>(int64_t, int, int, const float*, const float*,
+                                               Cplx<float>*, const int*, cudaStream_t);
+
+// (b): one thread per (sample, k); forward sweep w_i = dinv_i (p_i + wT_i w_{i-1}),
+// back substitution q_i = w_i - lu_i q_{i+1}, in place.
+template <typename T>
+__global__ void __launch_bounds__(128) k_cgc_solve(int64_t S, int K, int nx,
+                                                   const Cplx<T>* __restrict__ dinv,
+                                                   const Cplx<T>* __restrict__ lu,
+                                                   const double* __restrict__ wT,
+                                                   Cplx<T>* __restrict__ p,
+                                                   const int* __restrict__ active) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= S * K) return;
+    int64_t s = t / K;
+    int k = (int)(t - s * K);
+    if (!active[s]) return;
+    const int64_t base = s * (int64_t)nx * K + k;
+    const double* w = wT + s * (nx + 1);
+    T wr = 0, wi = 0;
+    for (int i = 0; i < nx; ++i) {
+        const int64_t o = base + (int64_t)i * K;
+        Cplx<T> pi = p[o], d = dinv[o];
+        T wl = (T)w[i];
+        T ar = pi.x + wl * wr, ai = pi.y + wl * wi;
+        wr = d.x * ar - d.y * ai;
+        wi = d.x * ai + d.y * ar;
+        p[o] = Cplx<T>{wr, wi};
+    }
+    T qr = 0, qi = 0;
+    for (int i = nx - 1; i >= 0; --i) {
+        const int64_t o = base + (int64_t)i * K;
+        Cplx<T> wv = p[o], u = lu[o];
+        T nr = wv.x - (u.x * qr - u.y * qi);
+        T ni = wv.y - (u.x * qi + u.y * qr);
+        qr = nr;
+        qi = ni;
+        p[o] = Cplx<T>{qr, qi};
+    }
+}
+
+template <typename T>
+void launch_cgc_solve(int64_t S, int K, int nx, const Cplx<T>* dinv, const Cplx<T>* lu,
+                      const double* wT, Cplx<T>* p, const int* active, cudaStream_t st) {
+    int64_t n = S * K;
+    if (n == 0) return;
+    k_cgc_solve<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(S, K, nx, dinv, lu, wT, p,
+                                                                 active);
+}
+template void launch_cgc_solve<double>(int64_t, int, int, const Cplx<double>*,
+                                       const Cplx<double>*, const double*, Cplx<double>*,
+                                       const int*, cudaStream_t);
+template void launch_cgc_solve<float>(int64_t, int, int, const Cplx<float>*, const Cplx<float>*,
+                                      const double*, Cplx<float>*, const int*, cudaStream_t);
+
+__device__ __forceinline__ unsigned long long abs_bits(double v) {
+    return (unsigned long long)__double_as_longlong(fabs(v));
+}
+
+// (c) + update + increment norm.
+template <typename T, int N>
+__global__ void __launch_bounds__(kTX) k_cgc_inverse(int64_t S, int nx,
+                                                     const Cplx<T>* __restrict__ q,
+                                                     const T* __restrict__ iscale,
+                                                     double* __restrict__ U, int mode,
+                                                     unsigned long long* __restrict__ delta,
+                                                     float* __restrict__ c32,
+                                                     const int* __restrict__ active) {
+    constexpr int L = N / 2, K = N / 2 + 1;
+    __shared__ Cplx<T> sq[kTX * K];
+    __shared__ double su[kTX][N + 1];
+    __shared__ float sc[kTX][N + 1];
+    const int64_t s = blockIdx.x;
+    if (!active[s]) return;
+    const int x0 = blockIdx.y * kTX;
+    const int rows = min(kTX, nx - x0);
+    const int tid = threadIdx.x;
+    const Cplx<T>* qin = q + (s * nx + x0) * (int64_t)K;
+    for (int e = tid; e < rows * K; e += kTX) sq[e] = qin[e];
+    double* Ut = U + (s * nx + x0) * (int64_t)N;
+    if (mode != 2)
+        for (int e = tid; e < rows * N; e += kTX) {
+            int row = e / N, col = e - row * N;
+            su[row][col] = Ut[e];
+        }
+    __syncthreads();
+    unsigned long long dmax = 0ull;
+    if (tid < rows) {
+        const Cplx<T>* X = sq + tid * K;
+        T zr[L], zi[L];
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            Cplx<T> A = X[k], B = X[L - k];
+            // E_k = (A + conj B)/2, O_k = (A - conj B) e^{+2 pi i k/N} / 2, Z_k = E_k + i O_k
+            T Er = (T)0.5 * (A.x + B.x), Ei = (T)0.5 * (A.y - B.y);
+            T Dr = (T)0.5 * (A.x - B.x), Di = (T)0.5 * (A.y + B.y);
+            T wr = (T)1, wi = (T)0;
+            if (k != 0) {
+                const int t = k * (kTwiddleN / N);
+                wr = tw_cos<T>(t);
+                wi = tw_sin<T>(t);
+            }
+            T Or = Dr * wr - Di * wi, Oi = Dr * wi + Di * wr;
+            zr[k] = Er - Oi;
+            zi[k] = Ei + Or;
+        }
+        cfft<T, L, true>(zr, zi);
+#pragma unroll
+        for (int m = 0; m < L; ++m) {
+            double u0 = (double)(zr[m] * iscale[2 * m]);
+            double u1 = (double)(zi[m] * iscale[2 * m + 1]);
+            if (mode == 0) {
+                double c0 = u0 - su[tid][2 * m], c1 = u1 - su[tid][2 * m + 1];
+                dmax = max(dmax, abs_bits(c0));
+                dmax = max(dmax, abs_bits(c1));
+                sc[tid][2 * m] = (float)c0;
+                sc[tid][2 * m + 1] = (float)c1;
+                su[tid][2 * m] = u0;
+                su[tid][2 * m + 1] = u1;
+            } else if (mode == 1) {
+                dmax = max(dmax, abs_bits(u0));
+                dmax = max(dmax, abs_bits(u1));
+                sc[tid][2 * m] = (float)u0;
+                sc[tid][2 * m + 1] = (float)u1;
+                su[tid][2 * m] += u0;
+                su[tid][2 * m + 1] += u1;
+            } else {
+                su[tid][2 * m] = u0;
+                su[tid][2 * m + 1] = u1;
+            }
+        }
+    }
+    __syncthreads();
+    for (int e = tid; e < rows * N; e += kTX) {
+        int row = e / N, col = e - row * N;
+        Ut[e] = su[row][col];
+    }
+    if (mode != 2 && c32) {
+        float* ct = c32 + (s * nx + x0) * (int64_t)N;
+        for (int e = tid; e < rows * N; e += kTX) {
+            int row = e / N, col = e - row * N;
+            ct[e] = sc[row][col];
+        }
+    }
+    if (mode != 2) {
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+        if (tid == 0 && dmax) atomicMax(delta + s, dmax);
+    }
+}
+
+template <typename T>
+void launch_cgc_inverse(int64_t S, int N, int nx, const Cplx<T>* q, const T* iscale, double* U,
+                        int mode, unsigned long long* delta, float* c32, const int* active,
+                        cudaStream_t st) {
+    if (S == 0) return;
+    dim3 grid((unsigned)S, (unsigned)((nx + kTX - 1) / kTX));
+    switch (N) {
+#define KLECGC_INV_CASE(NN)                                                                 \
+    case NN:                                                                                \
+        k_cgc_inverse<T, NN><<<grid, kTX, 0, st>>>(S, nx, q, iscale, U, mode, delta, c32, active); \
+        break;
+        KLECGC_INV_CASE(2)
+        KLECGC_INV_CASE(4)
+        KLECGC_INV_CASE(8)
+        KLECGC_INV_CASE(16)
+        KLECGC_INV_CASE(32)
+        KLECGC_INV_CASE(64)
+#undef KLECGC_INV_CASE
+        default: break;
+    }
+}
+template void launch_cgc_inverse<double>(int64_t, int, int, const Cplx<double>*, const double*,
+                                         double*, int, unsigned long long*, float*, const int*,
+                                         cudaStream_t);
+template void launch_cgc_inverse<float>(int64_t, int, int, const Cplx<float>*, const float*,
+                                        double*, int, unsigned long long*, float*, const int*,
+                                        cudaStream_t);
+
+// Stopping rule per sample (Algorithm 2, Step 3): stop after the first
+// iteration whose increment max-norm is <= tol.
+__global__ void k_convergence(int64_t S, int iter, int kmax, double tol,
+                              unsigned long long* __restrict__ delta, int* __restrict__ active,
+                              int32_t* __restrict__ iters, int32_t* __restrict__ status,
+                              int* __restrict__ n_active) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool still = false;
+    if (s < S && active[s]) {
+        double d = __longlong_as_double((long long)delta[s]);
+        delta[s] = 0ull;
+        if (!isfinite(d)) {
+            active[s] = 0;
+            iters[s] = -2;
+            status[s] = 4;  // KLECGC_E_NONFINITE
+        } else if (d <= tol) {
+            active[s] = 0;
+            iters[s] = iter + 1;
+            status[s] = 0;
+        } else if (iter + 1 >= kmax) {
+            active[s] = 0;
+            iters[s] = -1;
+            status[s] = 3;  // KLECGC_E_NOT_CONVERGED
+        } else {
+            still = true;
+        }
+    }
+    unsigned b = __ballot_sync(0xffffffffu, still);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_active, __popc(b));
+}
+
+void launch_convergence(int64_t S, int iter, int kmax, double tol, unsigned long long* delta,
+                        int* active, int32_t* iters, int32_t* status, int* n_active,
+                        cudaStream_t st) {
+    if (S == 0) return;
+    k_convergence<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(S, iter, kmax, tol, delta, active,
+                                                                iters, status, n_active);
+}
+
+__global__ void k_transpose(const double* __restrict__ in, double* __restrict__ out, int A, int B) {
+    __shared__ double tile[32][33];
+    const int64_t s = blockIdx.x;
+    const double* src = in + s * (int64_t)A * B;
+    double* dst = out + s * (int64_t)A * B;
+    int a0 = blockIdx.y * 32, b0 = blockIdx.z * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        int a = a0 + y, b = b0 + threadIdx.x;
+        if (a < A && b < B) tile[y][threadIdx.x] = src[(int64_t)a * B + b];
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        int b = b0 + y, a = a0 + threadIdx.x;
+        if (a < A && b < B) dst[(int64_t)b * A + a] = tile[threadIdx.x][y];
+    }
+}
+
+void launch_transpose(const double* in, double* out, int64_t S, int A, int B, cudaStream_t st) {
+    if (S == 0) return;
+    dim3 grid((unsigned)S, (unsigned)((A + 31) / 32), (unsigned)((B + 31) / 32));
+    k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, out, A, B);
+}
+
+}  // namespace klecgc

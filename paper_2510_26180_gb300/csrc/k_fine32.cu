@@ -1,0 +1,380 @@
+// FP32 fine propagator, register-resident (hot-path rows a3, a4; mixed modes).
+//
+// Each backward-Euler step of F solves (I + dt(A+cI)) delta = rhs in the
+// increment form (rhs = dt f0 - dt c v - dt A v, flux form), v += delta.
+// M = I + dt(A+cI) is the same for every step, interval and iteration of a
+// sample, so its LU factors are computed once per solve (FP64, rounded):
+//     forward   y_i = rhs_i - l_i y_{i-1}
+//     backward  x_i = dinv_i y_i - u_i x_{i+1}
+// One warp owns QS systems (intervals n of one sample); lane k holds rows
+// [kR, kR+R) of every system in registers for all J steps.  Both first-order
+// recurrences are split at the lane boundaries: each lane runs its rows
+// from a zero carry, the carries are propagated across the 32 lanes by a
+// 5-level shuffle scan, and a correction adds carry * (product of the
+// multipliers), y_i = yhat_i + F_i y_in, x_i = xhat_i + G_i x_in, where
+//     F_j = prod_{k<=j} (-l_k),  G_j = prod_{k>=j} (-u_k)   (within the lane's rows)
+// and the scan multipliers are products of whole-lane F/G: all of these are
+// data independent and precomputed.  The coupled system is solved exactly
+// (the same LU recurrences, regrouped); no reduced system is formed.
+//
+// Rows are padded to 32R >= nx + 1.  Padded rows have l = u = dinv = 0 so
+// they stay 0 and act as the Dirichlet value beyond the last row; the table
+// row nx still carries the weight of the boundary face nx.
+#include "common.cuh"
+
+namespace klecgc {
+
+// Per-sample factor table, [S][R][32]: A = {G_j, wd_j, l_j, 0}, D = {F_j, dinv_j, u_j, 0}
+// for row i = lane * R + j.  wd_j = dt a_{i-1/2} / h^2 (face left of row i).
+__global__ void k_fine_table32(const double* __restrict__ a, int64_t S, int nx, int R,
+                               double inv_h2, double dt, double react, float4* __restrict__ tabA,
+                               float4* __restrict__ tabD) {
+    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= S) return;
+    const int Rt = 32 * R;
+    const double* as = a + s * (nx + 1);
+    float4* A = tabA + s * (int64_t)Rt;
+    float4* D = tabD + s * (int64_t)Rt;
+    // pass 1: l, dinv, u, wd by row (layout [j][lane])
+    double piv = 1.0;
+    for (int i = 0; i < Rt; ++i) {
+        const int lane = i / R, j = i - lane * R;
+        const int o = j * 32 + lane;
+        double wl = i <= nx ? dt * as[i] * inv_h2 : 0.0;
+        double l = 0.0, dinv = 0.0, u = 0.0;
+        if (i < nx) {
+            double wr = dt * as[i + 1] * inv_h2;
+            double m = 1.0 + wl + wr + dt * react;
+            if (i > 0) {
+                l = -wl / piv;
+                m -= wl * wl / piv;
+            }
+            piv = m;
+            dinv = 1.0 / piv;
+            u = (i + 1 < nx) ? -wr * dinv : 0.0;
+        }
+        A[o] = make_float4(0.f, (float)wl, (float)l, 0.f);
+        D[o] = make_float4(0.f, (float)dinv, (float)u, 0.f);
+    }
+    // pass 2: within-lane products F (forward) and G (backward), in FP64
+    for (int lane = 0; lane < 32; ++lane) {
+        // products of the FP32-rounded multipliers: they must match the local sweeps
+        double F = 1.0;
+        for (int j = 0; j < R; ++j) {
+            F *= -(double)A[j * 32 + lane].z;
+            D[j * 32 + lane].x = (float)F;
+        }
+        double G = 1.0;
+        for (int j = R - 1; j >= 0; --j) {
+            G *= -(double)D[j * 32 + lane].z;
+            A[j * 32 + lane].x = (float)G;
+        }
+    }
+}
+
+template <int R, int QS>
+__global__ void __launch_bounds__(128) k_fine32(
+    int64_t S, int N, int nx, int J, int cps, float dt_react, float dt_f, float wT_scale,
+    float dTreact_f, double alpha, double dTreact, const double* __restrict__ U,
+    const double* __restrict__ u0, const float* __restrict__ c32, double* __restrict__ Facc,
+    int in_mode, const float4* __restrict__ tabA, const float4* __restrict__ tabD,
+    const double* __restrict__ wT, double* __restrict__ r, float* __restrict__ d32, int out_mode,
+    const int* __restrict__ active) {
+    extern __shared__ float4 smem[];
+    float4* sA = smem;
+    float4* sD = smem + R * 32;
+    const int64_t s = blockIdx.x / cps;
+    const int part = blockIdx.x - (int)(s * cps);
+    if (!active[s]) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = (part * (blockDim.x >> 5) + warp) * QS;
+    {
+        const float4* gA = tabA + s * (int64_t)(R * 32);
+        const float4* gD = tabD + s * (int64_t)(R * 32);
+        for (int e = threadIdx.x; e < R * 32; e += blockDim.x) {
+            sA[e] = gA[e];
+            sD[e] = gD[e];
+        }
+    }
+    __syncthreads();
+    if (n0 >= N) return;
+    constexpr unsigned FULL = 0xffffffffu;
+
+    // data-independent scan multipliers
+    float cf[5], cb[5];
+    {
+        float af = sD[(R - 1) * 32 + lane].x;  // F_{R-1}: product over the lane's rows
+        float ab = sA[lane].x;                 // G_0
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+            const int d = 1 << k;
+            float pf = __shfl_up_sync(FULL, af, d);
+            float pb = __shfl_down_sync(FULL, ab, d);
+            cf[k] = lane >= d ? af : 0.f;
+            cb[k] = lane + d <= 31 ? ab : 0.f;
+            if (lane >= d) af *= pf;
+            if (lane + d <= 31) ab *= pb;
+        }
+    }
+    float gprev = __shfl_up_sync(FULL, sA[(R - 1) * 32 + lane].x, 1);   // G_{R-1} of lane-1
+    float wd_right = __shfl_down_sync(FULL, sA[lane].y, 1);             // face right of row R-1
+    if (lane == 0) gprev = 0.f;
+    if (lane == 31) wd_right = 0.f;
+    const float src = in_mode == 0 ? dt_f : 0.f;
+
+    float v[QS][R], w[QS][R];
+    const int64_t sbase = s * (int64_t)nx * N;
+#pragma unroll
+    for (int q = 0; q < QS; ++q) {
+        const int n = n0 + q;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int i = lane * R + j;
+            float x0 = 0.f;
+            if (i < nx && n < N) {
+                if (in_mode == 0)
+                    x0 = (float)(n == 0 ? u0[i] : U[sbase + (int64_t)i * N + n - 1]);
+                else if (n > 0)
+                    x0 = c32[sbase + (int64_t)i * N + n - 1];
+            }
+            v[q][j] = x0;
+        }
+    }
+    // step-0 right-hand side and forward sweep (no pending update yet)
+#pragma unroll
+    for (int q = 0; q < QS; ++q) {
+        float vl = __shfl_up_sync(FULL, v[q][R - 1], 1);
+        float vr = __shfl_down_sync(FULL, v[q][0], 1);
+        if (lane == 0) vl = 0.f;
+        if (lane == 31) vr = 0.f;
+        float fprev = sA[lane].y * (v[q][0] - vl);
+        float yprev = 0.f;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const float4 ta = sA[j * 32 + lane];
+            const float wr = (j + 1 < R) ? sA[(j + 1) * 32 + lane].y : wd_right;
+            const float vn = (j + 1 < R) ? v[q][j + 1] : vr;
+            const float f = wr * (vn - v[q][j]);
+            const float rhs = (f - fprev) + (src - dt_react * v[q][j]);
+            yprev = fmaf(-ta.z, yprev, rhs);
+            w[q][j] = yprev;
+            fprev = f;
+        }
+    }
+
+    for (int step = 0; step < J; ++step) {
+        // forward carries
+        float yin[QS];
+#pragma unroll
+        for (int q = 0; q < QS; ++q) {
+            float b = w[q][R - 1];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) b = fmaf(cf[k], __shfl_up_sync(FULL, b, 1 << k), b);
+            float t = __shfl_up_sync(FULL, b, 1);
+            yin[q] = lane ? t : 0.f;
+        }
+        // descending: forward correction, diagonal, local backward sweep
+        float xn[QS];
+#pragma unroll
+        for (int q = 0; q < QS; ++q) xn[q] = 0.f;
+#pragma unroll
+        for (int j = R - 1; j >= 0; --j) {
+            const float4 td = sD[j * 32 + lane];
+#pragma unroll
+            for (int q = 0; q < QS; ++q) {
+                float y = fmaf(td.x, yin[q], w[q][j]);
+                float xh = fmaf(-td.z, xn[q], y * td.y);
+                w[q][j] = xh;
+                xn[q] = xh;
+            }
+        }
+        // backward carries: z = true x at this lane's first row
+        float z[QS], zin[QS];
+#pragma unroll
+        for (int q = 0; q < QS; ++q) {
+            float b = w[q][0];
+#pragma unroll
+            for (int k = 0; k < 5; ++k) b = fmaf(cb[k], __shfl_down_sync(FULL, b, 1 << k), b);
+            z[q] = b;
+            float t = __shfl_down_sync(FULL, b, 1);
+            zin[q] = lane < 31 ? t : 0.f;
+        }
+        const bool more = step + 1 < J;
+#pragma unroll
+        for (int q = 0; q < QS; ++q) {
+            // neighbour values after this step's update, for the next rhs
+            float pl = __shfl_up_sync(FULL, v[q][R - 1] + w[q][R - 1], 1);
+            float pr = __shfl_down_sync(FULL, v[q][0], 1);
+            const float vl = lane ? fmaf(gprev, z[q], pl) : 0.f;
+            const float vr = lane < 31 ? pr + zin[q] : 0.f;
+            float fprev = 0.f, yprev = 0.f, lprev = 0.f;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const float4 ta = sA[j * 32 + lane];
+                // The two rows next to a lane boundary must see bitwise-equal
+                // values there, or the flux through that face differs between
+                // them and the flux form stops being conservative.  The
+                // boundary rows are therefore updated by exactly the formulas
+                // the neighbouring lanes used for vl / vr above.
+                if (j == 0)
+                    v[q][0] = v[q][0] + z[q];
+                else if (j == R - 1)
+                    v[q][R - 1] = fmaf(ta.x, zin[q], v[q][R - 1] + w[q][R - 1]);
+                else
+                    v[q][j] += fmaf(ta.x, zin[q], w[q][j]);
+                if (more) {
+                    const float f = ta.y * (v[q][j] - (j ? v[q][j - 1] : vl));
+                    if (j) {
+                        const float rhs = (f - fprev) + (src - dt_react * v[q][j - 1]);
+                        yprev = fmaf(-lprev, yprev, rhs);
+                        w[q][j - 1] = yprev;
+                    }
+                    fprev = f;
+                    lprev = ta.z;
+                }
+            }
+            if (more) {
+                const float f = wd_right * (vr - v[q][R - 1]);
+                const float rhs = (f - fprev) + (src - dt_react * v[q][R - 1]);
+                w[q][R - 1] = fmaf(-lprev, yprev, rhs);
+            }
+        }
+    }
+
+    // epilogue: accumulate F, then the CGC right-hand side or the defect
+#pragma unroll
+    for (int q = 0; q < QS; ++q) {
+        const int n = n0 + q;
+        if (n >= N) continue;
+        const double* Us = U + sbase;
+        double* Fa = Facc + sbase;
+        // new F at this lane's first and last rows (for the neighbour exchange)
+        auto fnew = [&](int j) -> double {
+            const int i = lane * R + j;
+            if (i >= nx) return 0.0;
+            const double old = in_mode ? Fa[(int64_t)i * N + n] : 0.0;
+            return old + (double)v[q][j];
+        };
+        const double f_first = fnew(0), f_last = fnew(R - 1);
+        double fl = __shfl_up_sync(FULL, f_last, 1);
+        double fr = __shfl_down_sync(FULL, f_first, 1);
+        if (lane == 0) fl = 0.0;
+        if (lane == 31) fr = 0.0;
+        if (out_mode == 0) {
+            const double* wTs = wT + s * (nx + 1);
+            double Fm = fl, Fi = f_first;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const int i = lane * R + j;
+                const double Fp = (j + 1 < R) ? fnew(j + 1) : fr;
+                if (i < nx) {
+                    const int64_t o = (int64_t)i * N + n;
+                    Fa[o] = Fi;
+                    const double BF = Fi + wTs[i] * (Fi - Fm) - wTs[i + 1] * (Fp - Fi) + dTreact * Fi;
+                    const double prev = n == 0 ? alpha * Us[(int64_t)i * N + (N - 1)] : Us[o - 1];
+                    r[sbase + o] = BF - prev;
+                }
+                Fm = Fi;
+                Fi = Fp;
+            }
+        } else {
+            // D = F_n - U_n in FP64, then d = (I + dT(A + cI)) D in FP32 flux form
+            auto dval = [&](int j, double F) -> float {
+                const int i = lane * R + j;
+                return i < nx ? (float)(F - Us[(int64_t)i * N + n]) : 0.f;
+            };
+            const float d_first = dval(0, f_first), d_last = dval(R - 1, f_last);
+            float dl = __shfl_up_sync(FULL, d_last, 1);
+            float dr = __shfl_down_sync(FULL, d_first, 1);
+            if (lane == 0) dl = 0.f;
+            if (lane == 31) dr = 0.f;
+            float Dm = dl, Di = d_first;
+            double Fcur = f_first;
+            float* ds = d32 + sbase;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const int i = lane * R + j;
+                double Fnext = 0.0;
+                float Dp;
+                if (j + 1 < R) {
+                    Fnext = fnew(j + 1);
+                    Dp = dval(j + 1, Fnext);
+                } else {
+                    Dp = dr;
+                }
+                if (i < nx) {
+                    const int64_t o = (int64_t)i * N + n;
+                    Fa[o] = Fcur;
+                    const float wl = wT_scale * sA[j * 32 + lane].y;
+                    const float wr = wT_scale * ((j + 1 < R) ? sA[(j + 1) * 32 + lane].y : wd_right);
+                    ds[o] = Di + wl * (Di - Dm) - wr * (Dp - Di) + dTreact_f * Di;
+                }
+                Dm = Di;
+                Di = Dp;
+                Fcur = Fnext;
+            }
+        }
+    }
+}
+
+int fine32_rows_per_lane(int nx) {
+    const int need = (nx + 1 + 31) / 32;  // rows per lane so that 32R >= nx + 1
+    for (int R : {2, 4, 8, 16, 32, 64})
+        if (R >= need) return R;
+    return 0;
+}
+
+void launch_fine_table32(const double* a, int64_t S, int nx, int R, double h, double dt,
+                         double react, float4* tabA, float4* tabD, cudaStream_t st) {
+    if (S == 0) return;
+    k_fine_table32<<<(unsigned)((S + 63) / 64), 64, 0, st>>>(a, S, nx, R, 1.0 / (h * h), dt, react,
+                                                             tabA, tabD);
+}
+
+template <int R, int QS>
+static void launch_r(int64_t S, int N, int nx, int J, double dt, double dT, double alpha,
+                     double react, double forcing, const double* U, const double* u0,
+                     const float* c32, double* Facc, int in_mode, const float4* tabA,
+                     const float4* tabD, const double* wT, double* r, float* d32, int out_mode,
+                     const int* active, cudaStream_t st) {
+    constexpr int warps = 4;
+    const int per_cta = warps * QS;
+    const int cps = (N + per_cta - 1) / per_cta;
+    const size_t smem = 2 * (size_t)R * 32 * sizeof(float4);
+    static bool attr = false;
+    if (!attr && smem > 48 * 1024) {
+        cudaFuncSetAttribute(k_fine32<R, QS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = true;
+    }
+    const double wT_scale = (double)J;  // dT w = J * dt w
+    k_fine32<R, QS><<<(unsigned)(S * cps), warps * 32, smem, st>>>(
+        S, N, nx, J, cps, (float)(dt * react), (float)(dt * forcing), (float)wT_scale,
+        (float)(dT * react), alpha, dT * react, U, u0, c32, Facc, in_mode, tabA, tabD, wT, r, d32,
+        out_mode, active);
+}
+
+void launch_fine32(int64_t S, int N, int nx, int J, double dt, double dT, double alpha,
+                   double react, double forcing, const double* U, const double* u0,
+                   const float* c32, double* Facc, int in_mode, const float4* tabA,
+                   const float4* tabD, const double* wT, double* r, float* d32, int out_mode,
+                   const int* active, cudaStream_t st) {
+    if (S == 0) return;
+    switch (fine32_rows_per_lane(nx)) {
+#define KLECGC_F32(RR, QQ)                                                                     \
+    case RR:                                                                                   \
+        launch_r<RR, QQ>(S, N, nx, J, dt, dT, alpha, react, forcing, U, u0, c32, Facc, in_mode, \
+                         tabA, tabD, wT, r, d32, out_mode, active, st);                        \
+        break;
+        KLECGC_F32(2, 2)
+        KLECGC_F32(4, 2)
+        KLECGC_F32(8, 2)
+        KLECGC_F32(16, 2)
+        KLECGC_F32(32, 2)
+        KLECGC_F32(64, 1)
+#undef KLECGC_F32
+        default: break;
+    }
+}
+
+}  // namespace klecgc

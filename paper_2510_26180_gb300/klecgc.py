@@ -1,0 +1,207 @@
+"""ctypes binding of include/klecgc.h (same names, argument marshalling only).
+
+Arrays may be torch tensors (CUDA or CPU) or numpy arrays; they are passed
+to the library as raw pointers, and the library decides host/device from the
+pointer.  The CUDA stream defaults to torch's current stream.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+FP64, MIXED, MIXED_DEFECT = 0, 1, 2
+GUESS_GPC, GUESS_ZERO, GUESS_USER, GUESS_COARSE = 0, 1, 2, 3
+(OK, E_INVALID_ARG, E_OUT_OF_MEMORY, E_NOT_CONVERGED, E_NONFINITE, E_CUDA,
+ E_UNSUPPORTED) = range(7)
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_lib", "libklecgc.so")
+
+# Every symbol declared in include/klecgc.h.
+EXPORTS = ["klecgc_setup", "klecgc_solve", "klecgc_field", "klecgc_guess", "klecgc_fine_sweep",
+           "klecgc_cgc_apply", "klecgc_reference", "klecgc_info", "klecgc_free",
+           "klecgc_status_string", "klecgc_last_error", "klecgc_profile_enable",
+           "klecgc_profile_read"]
+PROFILE_CLASSES = ["field", "factors", "guess", "fine", "cgc_fwd", "cgc_solve", "cgc_inv",
+                   "conv", "layout"]
+
+
+class KlecgcError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"klecgc status {status}: {msg}")
+        self.status = status
+
+
+class Problem(ctypes.Structure):
+    _fields_ = [("dim", ctypes.c_int32), ("nx", ctypes.c_int32), ("T", ctypes.c_double),
+                ("sigma", ctypes.c_double), ("corr_len", ctypes.c_double),
+                ("M", ctypes.c_int32), ("gpc_degree", ctypes.c_int32),
+                ("n_train", ctypes.c_int32), ("eps_kl", ctypes.c_double),
+                ("N", ctypes.c_int32), ("J", ctypes.c_int32), ("reaction", ctypes.c_double),
+                ("forcing", ctypes.c_double), ("u0_kind", ctypes.c_int32)]
+
+    @classmethod
+    def from_workload(cls, w) -> "Problem":
+        return cls(dim=w.dim, nx=w.nx, T=w.T, sigma=w.sigma, corr_len=w.corr_len, M=w.M,
+                   gpc_degree=w.gpc_degree, n_train=w.n_train, eps_kl=w.eps_kl, N=w.N, J=w.J,
+                   reaction=w.reaction, forcing=w.forcing, u0_kind=w.u0_kind)
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64 * 16), ("ms", ctypes.c_double * 16),
+                ("n_classes", ctypes.c_int32)]
+
+
+class Info(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("N", ctypes.c_int32), ("J", ctypes.c_int32),
+                ("M", ctypes.c_int32), ("P", ctypes.c_int32), ("MQ", ctypes.c_int32),
+                ("lambda_sum", ctypes.c_double), ("lambda_kept", ctypes.c_double),
+                ("n_unknowns", ctypes.c_int32), ("device", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def load() -> ctypes.CDLL:
+    """Loads the compiled library; raises if it has not been built."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(LIB_PATH):
+        raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                           "`python -c 'import __graft_entry__ as g; g.build()'`")
+    lib = ctypes.CDLL(LIB_PATH)
+    P, D, I64, I32 = ctypes.c_void_p, ctypes.c_double, ctypes.c_int64, ctypes.c_int32
+    sig = {
+        "klecgc_setup": [ctypes.POINTER(Problem), P, ctypes.POINTER(P), P],
+        "klecgc_solve": [P, P, I64, D, I32, I32, D, D, I32, I32, I32, P, P, P, P, P],
+        "klecgc_field": [P, P, I64, P, P],
+        "klecgc_guess": [P, P, I64, I32, P, P],
+        "klecgc_fine_sweep": [P, P, I64, I32, P, D, I32, D, I32, P, P],
+        "klecgc_cgc_apply": [P, P, I64, I32, P, D, D, I32, P, P],
+        "klecgc_reference": [P, P, I64, I32, I32, P, P],
+        "klecgc_info": [P, ctypes.POINTER(Info)],
+        "klecgc_profile_enable": [P, I32],
+        "klecgc_profile_read": [P, ctypes.POINTER(Profile)],
+    }
+    for name, args in sig.items():
+        f = getattr(lib, name)
+        f.argtypes = args
+        f.restype = ctypes.c_int
+    lib.klecgc_free.argtypes = [P]
+    lib.klecgc_free.restype = None
+    lib.klecgc_status_string.argtypes = [ctypes.c_int]
+    lib.klecgc_status_string.restype = ctypes.c_char_p
+    lib.klecgc_last_error.argtypes = []
+    lib.klecgc_last_error.restype = ctypes.c_char_p
+    _lib = lib
+    return lib
+
+
+def exported_symbols():
+    """Names of EXPORTS that the loaded library actually exports."""
+    lib = load()
+    return [n for n in EXPORTS if hasattr(lib, n)]
+
+
+def _ptr(a, dtype):
+    """Raw pointer of a contiguous torch tensor / numpy array of `dtype`."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+            raise TypeError(f"expected a C-contiguous {dtype} array")
+        return a.ctypes.data
+    import torch
+    tdt = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+    if a.dtype != tdt or not a.is_contiguous():
+        raise TypeError(f"expected a contiguous {tdt} tensor")
+    return a.data_ptr()
+
+
+def _stream(stream):
+    if stream is not None:
+        return getattr(stream, "cuda_stream", stream)
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream().cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+def _check(status: int, allow=(OK,)) -> int:
+    if status not in allow:
+        lib = load()
+        raise KlecgcError(status, lib.klecgc_last_error().decode())
+    return status
+
+
+class Solver:
+    """Owns one klecgc context (klecgc_setup ... klecgc_free)."""
+
+    def __init__(self, problem: Problem, xi_train, stream=None):
+        self.lib = load()
+        self.problem = problem
+        h = ctypes.c_void_p()
+        _check(self.lib.klecgc_setup(ctypes.byref(problem), _ptr(xi_train, np.float64),
+                                     ctypes.byref(h), _stream(stream)))
+        self.h = h
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.klecgc_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def info(self) -> Info:
+        out = Info()
+        _check(self.lib.klecgc_info(self.h, ctypes.byref(out)))
+        return out
+
+    def profile_enable(self, timing: bool) -> None:
+        _check(self.lib.klecgc_profile_enable(self.h, 1 if timing else 0))
+
+    def profile_read(self) -> dict:
+        """{class: (launches, summed ms)} since the last profile_enable."""
+        p = Profile()
+        _check(self.lib.klecgc_profile_read(self.h, ctypes.byref(p)))
+        return {n: (int(p.launches[i]), float(p.ms[i])) for i, n in enumerate(PROFILE_CLASSES)}
+
+    def solve(self, xi, S, dT, J, N, alpha, tol, kmax, precision, guess, U_out,
+              iters_out=None, status_out=None, U_guess=None, stream=None,
+              allow=(OK, E_NOT_CONVERGED, E_NONFINITE)) -> int:
+        return _check(self.lib.klecgc_solve(
+            self.h, _ptr(xi, np.float64), S, dT, J, N, alpha, tol, kmax, precision, guess,
+            _ptr(U_guess, np.float64), _ptr(U_out, np.float64), _ptr(iters_out, np.int32),
+            _ptr(status_out, np.int32), _stream(stream)), allow)
+
+    def field(self, xi, S, a_out, stream=None) -> int:
+        return _check(self.lib.klecgc_field(self.h, _ptr(xi, np.float64), S,
+                                            _ptr(a_out, np.float64), _stream(stream)))
+
+    def guess(self, xi, S, precision, U0_out, stream=None) -> int:
+        return _check(self.lib.klecgc_guess(self.h, _ptr(xi, np.float64), S, precision,
+                                            _ptr(U0_out, np.float64), _stream(stream)))
+
+    def fine_sweep(self, xi, S, N, U_in, dT, J, alpha, precision, r_out, stream=None) -> int:
+        return _check(self.lib.klecgc_fine_sweep(
+            self.h, _ptr(xi, np.float64), S, N, _ptr(U_in, np.float64), dT, J, alpha, precision,
+            _ptr(r_out, np.float64), _stream(stream)))
+
+    def cgc_apply(self, xi, S, N, r_in, dT, alpha, precision, u_out, stream=None) -> int:
+        return _check(self.lib.klecgc_cgc_apply(
+            self.h, _ptr(xi, np.float64), S, N, _ptr(r_in, np.float64), dT, alpha, precision,
+            _ptr(u_out, np.float64), _stream(stream)))
+
+    def reference(self, xi, S, N, J, U_out, stream=None) -> int:
+        return _check(self.lib.klecgc_reference(self.h, _ptr(xi, np.float64), S, N, J,
+                                                 _ptr(U_out, np.float64), _stream(stream)))
