@@ -192,6 +192,29 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
 klecgc_status klecgc_reference(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t N,
                                int32_t J, double* U_out, void* stream);
 
+/*
+ * klecgc_reference_noalloc - klecgc_reference for callers that cannot
+ * allocate device memory (the paper has no counterpart: this is a library
+ * facility).  Such callers include code running under another framework's
+ * caching allocator that owns the free device memory, hosts that forbid
+ * allocation after start-up, and callbacks that must not let
+ * cudaMalloc/cudaFree synchronize the device.  The result equals
+ * klecgc_reference's; the working memory is one 32 MiB array compiled into
+ * the library, which every GPU that loads the library holds until exit.
+ *   xi:    [S][M] FP64 device array; U_out: [S][N][nx] FP64 device array.
+ *   Requires S * (6 nx + 5) <= 4194304 (32 MiB of doubles), else
+ *   INVALID_ARG with the sizes in klecgc_last_error(); host arrays and a
+ *   device other than the context's also give INVALID_ARG.
+ * Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).
+ * The first call on a device looks up the array's device address with
+ * cudaGetSymbolAddress; make that first call before any stream capture.
+ * Every call shares the array: calls whose GPU work overlaps (e.g. on two
+ * streams at once) race and must be serialized by the caller.  Nothing in
+ * the array needs to start at zero (each call writes what it reads).
+ */
+klecgc_status klecgc_reference_noalloc(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t N,
+                                       int32_t J, double* U_out, void* stream);
+
 /* Sizes of the context (M_Q, P, ...). */
 klecgc_status klecgc_info(const klecgc_ctx* ctx, klecgc_info_t* out);
 

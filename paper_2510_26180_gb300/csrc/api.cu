@@ -134,6 +134,15 @@ struct klecgc_ctx {
     }
 };
 
+namespace klecgc {
+bool ctx_view(const klecgc_ctx* ctx, CtxView* out) {
+    if (!ctx || !ctx->basis) return false;
+    *out = CtxView{ctx->basis, ctx->u0, ctx->nx, ctx->M, ctx->device,
+                   ctx->h, ctx->prob.T, ctx->prob.reaction, ctx->prob.forcing};
+    return true;
+}
+}  // namespace klecgc
+
 namespace {
 
 bool is_device_ptr(const void* p) {

@@ -102,6 +102,18 @@ void launch_transpose(const double* in, double* out, int64_t S, int A, int B, cu
 // Thread-local last-error detail.
 void set_error(const std::string& msg);
 
+// Read-only view of a context's problem data (defined in api.cu).
+struct CtxView {
+    const double* basis;  // [M][nx+1] field basis at the faces
+    const double* u0;     // [nx]
+    int nx, M, device;
+    double h, T, reaction, forcing;
+};
+}  // namespace klecgc
+struct klecgc_ctx;
+namespace klecgc {
+bool ctx_view(const klecgc_ctx* ctx, CtxView* out);
+
 }  // namespace klecgc
 
 #define KLECGC_CUDA_TRY(expr)                                                                  \

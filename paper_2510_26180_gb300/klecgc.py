@@ -23,7 +23,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libklecgc.so")
 EXPORTS = ["klecgc_setup", "klecgc_solve", "klecgc_field", "klecgc_guess", "klecgc_fine_sweep",
            "klecgc_cgc_apply", "klecgc_reference", "klecgc_info", "klecgc_free",
            "klecgc_status_string", "klecgc_last_error", "klecgc_profile_enable",
-           "klecgc_profile_read"]
+           "klecgc_profile_read", "klecgc_reference_noalloc"]
 PROFILE_CLASSES = ["field", "factors", "guess", "fine", "cgc_fwd", "cgc_solve", "cgc_inv",
                    "conv", "layout"]
 
@@ -82,6 +82,7 @@ def load() -> ctypes.CDLL:
         "klecgc_fine_sweep": [P, P, I64, I32, P, D, I32, D, I32, P, P],
         "klecgc_cgc_apply": [P, P, I64, I32, P, D, D, I32, P, P],
         "klecgc_reference": [P, P, I64, I32, I32, P, P],
+        "klecgc_reference_noalloc": [P, P, I64, I32, I32, P, P],
         "klecgc_info": [P, ctypes.POINTER(Info)],
         "klecgc_profile_enable": [P, I32],
         "klecgc_profile_read": [P, ctypes.POINTER(Profile)],
@@ -205,3 +206,9 @@ class Solver:
     def reference(self, xi, S, N, J, U_out, stream=None) -> int:
         return _check(self.lib.klecgc_reference(self.h, _ptr(xi, np.float64), S, N, J,
                                                  _ptr(U_out, np.float64), _stream(stream)))
+
+    def reference_noalloc(self, xi, S, N, J, U_out, stream=None) -> int:
+        """klecgc_reference without device allocation (device arrays only)."""
+        return _check(self.lib.klecgc_reference_noalloc(self.h, _ptr(xi, np.float64), S, N, J,
+                                                         _ptr(U_out, np.float64),
+                                                         _stream(stream)))
