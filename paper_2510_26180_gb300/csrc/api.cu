@@ -669,10 +669,10 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
         launch_fine_sweep_fp64(S, N, nx, J, dT, alpha, ctx->prob.reaction, ctx->prob.forcing, U,
                                ctx->u0, op.f64, op.wT, r, active, st);
     } else {
-        WS(double, Facc, "Facc", S * (int64_t)nx * N);
-        launch_fine32(S, N, nx, J, dT / J, dT, alpha, ctx->prob.reaction, ctx->prob.forcing, U,
-                      ctx->u0, nullptr, Facc, 0, op.tabA, op.tabD, op.wT, r, nullptr, 0, active,
-                      st);
+        WS(float, fo, "fout", S * (int64_t)nx * N);
+        launch_fine32(S, N, nx, J, dT / J, ctx->prob.reaction, ctx->prob.forcing, 0, U, nullptr,
+                      ctx->u0, nullptr, op.tabA, op.tabD, fo, active, st);
+        launch_jump_from_f32(S, N, nx, alpha, dT * ctx->prob.reaction, fo, U, op.wT, r, st);
     }
     TRY(cudaGetLastError());
     if ((s = export_batch(ctx, r, S, N, r_out, st)) != KLECGC_OK) return s;
@@ -791,28 +791,44 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
     } else {
         if ((s = scale_tables<double>(ctx, N, alpha, st, &sc64, &isc64)) != KLECGC_OK) return s;
     }
-    double* r = nullptr;
-    float* d32 = nullptr;
+    // buffers of the iteration
+    double* r = nullptr;                       // FP64 path: CGC right-hand side
     Cplx<double>* p64 = nullptr;
     Cplx<float>* p32 = nullptr;
-    if (!defect) {
+    float* fout = nullptr;                     // mixed paths: FP32 fine result
+    float* c32 = nullptr;                      // mixed paths: FP32 increment of U
+    double* Facc64[2] = {nullptr, nullptr};    // mixed: F(U_{n-1}) in FP64, two buffers
+    float2* Facc2[2] = {nullptr, nullptr};     // defect: F(U_{n-1}) as pairs, two buffers
+    float2* Udf = nullptr;                     // defect: the iterate as pairs (aliases U)
+    if (f64) {
         WS(double, rr, "r", NS);
-        WS(Cplx<double>, pp, "p64", S * (int64_t)nx * K);
         r = rr;
+    }
+    if (!defect) {
+        WS(Cplx<double>, pp, "p64", S * (int64_t)nx * K);
         p64 = pp;
     } else {
-        WS(float, dd, "d32", NS);
         WS(Cplx<float>, pp, "p32", S * (int64_t)nx * K);
-        d32 = dd;
         p32 = pp;
     }
-    double* Facc = nullptr;
-    float* c32 = nullptr;
     if (!f64) {
-        WS(double, fa, "Facc", NS);
+        WS(float, fo, "fout", NS);
         WS(float, cc, "c32", NS);
-        Facc = fa;
+        fout = fo;
         c32 = cc;
+        if (defect) {
+            WS(float2, fa, "FaccA2", NS);
+            WS(float2, fb, "FaccB2", NS);
+            Facc2[0] = fa;
+            Facc2[1] = fb;
+            ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_to_pairs(U, NS, st); });
+            Udf = reinterpret_cast<float2*>(U);
+        } else {
+            WS(double, fa, "FaccA", NS);
+            WS(double, fb, "FaccB", NS);
+            Facc64[0] = fa;
+            Facc64[1] = fb;
+        }
     }
     int* h_active = nullptr;
     TRY(cudaMallocHost(&h_active, sizeof(int)));
@@ -820,28 +836,41 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
         int* p;
         ~HostGuard() { cudaFreeHost(p); }
     } hg{h_active};
+    const double dTreact = dT * ctx->prob.reaction;
 
     for (int k = 0; k < kmax; ++k) {
+        const int cur = k & 1, prv = cur ^ 1;
         if (f64) {
             ctx->launch(KLECGC_K_FINE, st, [&] {
                 launch_fine_sweep_fp64(S, N, nx, J, dT, alpha, ctx->prob.reaction,
                                        ctx->prob.forcing, U, ctx->u0, op.f64, op.wT, r, active, st);
             });
+            ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<double, double>(S, N, nx, r, sc64, p64, active, st); });
         } else {
+            // F(start) on the first iteration, F0(increment) afterwards
             ctx->launch(KLECGC_K_FINE, st, [&] {
-                launch_fine32(S, N, nx, J, dT / J, dT, alpha, ctx->prob.reaction,
-                              ctx->prob.forcing, U, ctx->u0, c32, Facc, k == 0 ? 0 : 1, op.tabA,
-                              op.tabD, op.wT, r, d32, defect ? 1 : 0, active, st);
+                launch_fine32(S, N, nx, J, dT / J, ctx->prob.reaction, ctx->prob.forcing,
+                              k == 0 ? 0 : 1, defect ? nullptr : U, Udf, ctx->u0, c32, op.tabA,
+                              op.tabD, fout, active, st);
             });
+            if (defect)
+                ctx->launch(KLECGC_K_CGC_FWD, st, [&] {
+                    launch_cgc_forward_df(S, N, nx, fout, k == 0 ? nullptr : Facc2[prv], Facc2[cur],
+                                          Udf, op.wT, dTreact, sc32, p32, active, st);
+                });
+            else
+                ctx->launch(KLECGC_K_CGC_FWD, st, [&] {
+                    launch_cgc_forward_mixed(S, N, nx, fout, k == 0 ? nullptr : Facc64[prv],
+                                             Facc64[cur], U, op.wT, dTreact, alpha, sc64, p64,
+                                             active, st);
+                });
         }
         if (!defect) {
-            ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<double, double>(S, N, nx, r, sc64, p64, active, st); });
             ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_cgc_solve<double>(S, K, nx, op.dinv64, op.lu64, op.wT, p64, active, st); });
             ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc64, U, 0, delta, c32, active, st); });
         } else {
-            ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<float, float>(S, N, nx, d32, sc32, p32, active, st); });
             ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_cgc_solve<float>(S, K, nx, op.dinv32, op.lu32, op.wT, p32, active, st); });
-            ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<float>(S, N, nx, p32, isc32, U, 1, delta, c32, active, st); });
+            ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse_df(S, N, nx, p32, isc32, Udf, delta, c32, active, st); });
         }
         TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
         ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
@@ -850,6 +879,17 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
         TRY(cudaStreamSynchronize(st));
         if (*h_active == 0) break;
     }
+    if (defect) {
+        // pairs -> FP64 in the caller's layout
+        if (is_device_ptr(U_out)) {
+            ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_pairs_transpose_out(Udf, U_out, S, nx, N, st); });
+        } else {
+            WS(double, tmp, "export", NS);
+            ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_pairs_transpose_out(Udf, tmp, S, nx, N, st); });
+            TRY(cudaMemcpyAsync(U_out, tmp, NS * sizeof(double), cudaMemcpyDeviceToHost, st));
+        }
+        TRY(cudaGetLastError());
+    } else
     if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) return s;
     std::vector<int32_t> hs(S), hi(S);
     TRY(cudaMemcpyAsync(hs.data(), status, S * 4, cudaMemcpyDeviceToHost, st));

@@ -29,6 +29,31 @@ struct alignas(16) FineCoef32 {
 // cos/sin(2 pi t / 128) in constant memory (set once per device).
 void upload_twiddles();
 
+// Unevaluated sums of two floats (hi + lo, |lo| <= ulp(hi)/2): about 48-bit
+// values built from FP32 operations only (Knuth's TwoSum / Dekker's
+// FastTwoSum).  FP64 runs at 1/58 of the FP32 rate on this GPU, so iterates
+// and accumulators of the mixed path live in this form.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+    float s = a + b;
+    float bb = s - a;
+    float e = (a - (s - bb)) + (b - bb);
+    return make_float2(s, e);
+}
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {  // |a| >= |b|
+    float s = a + b;
+    return make_float2(s, b - (s - a));
+}
+// x + y for a pair x and a float y
+__device__ __forceinline__ float2 df_add(float2 x, float y) {
+    float2 s = two_sum(x.x, y);
+    return fast_two_sum(s.x, s.y + x.y);
+}
+// x - y for two pairs, rounded to one float
+__device__ __forceinline__ float df_sub(float2 x, float2 y) {
+    float2 s = two_sum(x.x, -y.x);
+    return s.x + (s.y + (x.y - y.y));
+}
+
 // ---- k_field.cu ----
 void launch_field(const double* xi, int64_t S, int M, const double* basis, int nf, double* a,
                   cudaStream_t st);
@@ -68,11 +93,15 @@ void launch_fine_sweep_fp64(int64_t S, int N, int nx, int J, double dT, double a
 int fine32_rows_per_lane(int nx);
 void launch_fine_table32(const double* a, int64_t S, int nx, int R, double h, double dt,
                          double react, float4* tabA, float4* tabD, cudaStream_t st);
-void launch_fine32(int64_t S, int N, int nx, int J, double dt, double dT, double alpha,
-                   double react, double forcing, const double* U, const double* u0,
-                   const float* c32, double* Facc, int in_mode, const float4* tabA,
-                   const float4* tabD, const double* wT, double* r, float* d32, int out_mode,
+// in_mode 0: fout = F(start), start_n = U_{n-1} (U64, or Udf.hi), u0 for n = 0;
+// in_mode 1: fout = F0(c_{n-1}), 0 for n = 0.  fout: [S][nx][N] FP32.
+void launch_fine32(int64_t S, int N, int nx, int J, double dt, double react, double forcing,
+                   int in_mode, const double* U64, const float2* Udf, const double* u0,
+                   const float* c32, const float4* tabA, const float4* tabD, float* fout,
                    const int* active, cudaStream_t st);
+// r = (I + dT(A + cI)) F - prev in FP64 from an FP32 F ([S][nx][N]).
+void launch_jump_from_f32(int64_t S, int N, int nx, double alpha, double dTreact, const float* F,
+                          const double* U, const double* wT, double* r, cudaStream_t st);
 void launch_fine_sequential(int64_t S, int N, int nx, int J, double dt_forcing, const double* u0,
                             const FineCoef64* fc, double* scratch, double* U, cudaStream_t st);
 
@@ -85,6 +114,27 @@ void launch_cgc_forward(int64_t S, int N, int nx, const TIN* r, const T* scale, 
 template <typename T>
 void launch_cgc_solve(int64_t S, int K, int nx, const Cplx<T>* dinv, const Cplx<T>* lu,
                       const double* wT, Cplx<T>* p, const int* active, cudaStream_t st);
+// Step (a) with the FP32 fine result folded in (mixed paths).  Facc_out =
+// Facc_in + fout (Facc_in null on the first iteration); then
+//  defect: d = (I + dT(A+cI)) (Facc_out - U) on pairs U, Facc (FP32 ops only);
+//  mixed:  r = (I + dT(A+cI)) Facc_out - prev in FP64.
+void launch_cgc_forward_df(int64_t S, int N, int nx, const float* fout, const float2* Facc_in,
+                           float2* Facc_out, const float2* Udf, const double* wT, double dTreact,
+                           const float* scale, Cplx<float>* p, const int* active,
+                           cudaStream_t st);
+void launch_cgc_forward_mixed(int64_t S, int N, int nx, const float* fout, const double* Facc_in,
+                              double* Facc_out, const double* U, const double* wT,
+                              double dTreact, double alpha, const double* scale,
+                              Cplx<double>* p, const int* active, cudaStream_t st);
+// Step (c) + pair update (defect path): Udf += u, c32 = u, delta = max|u|.
+void launch_cgc_inverse_df(int64_t S, int N, int nx, const Cplx<float>* q, const float* iscale,
+                           float2* Udf, unsigned long long* delta, float* c32, const int* active,
+                           cudaStream_t st);
+// FP64 [S][nx][N] <-> pairs, in place (same 8 bytes per value).
+void launch_to_pairs(double* U, int64_t n, cudaStream_t st);
+// pairs [S][nx][N] -> FP64 [S][N][nx]
+void launch_pairs_transpose_out(const float2* in, double* out, int64_t S, int nx, int N,
+                                cudaStream_t st);
 // Step (c) + update: u_j = alpha^{-j/N} (1/N) sum_k q_k exp(+2 pi i j k / N).
 // mode 0: U <- u, delta = max|u - U_old|;  mode 1: U <- U + u, delta = max|u|;
 // mode 2: out <- u (no delta).  In modes 0 and 1 the increment U_new - U_old is

@@ -105,13 +105,178 @@ __device__ __forceinline__ void cfft(T (&re)[L], T (&im)[L]) {
 
 constexpr int kTX = 32;  // x points per CTA in the transform kernels
 
+// Real DFT of one time series x[0..N-1] (unnormalized, sign -1) into
+// o[0..N/2]: complex FFT of the N/2 packed pairs, then the even/odd split.
+template <typename T, int N>
+__device__ __forceinline__ void rfft_row(const T (&x)[N], Cplx<T>* o) {
+    constexpr int L = N / 2;
+    T zr[L], zi[L];
+#pragma unroll
+    for (int m = 0; m < L; ++m) {
+        zr[m] = x[2 * m];
+        zi[m] = x[2 * m + 1];
+    }
+    cfft<T, L, false>(zr, zi);
+#pragma unroll
+    for (int k = 0; k <= L; ++k) {
+        const int kk = k % L, km = (L - k) % L;
+        T Er = (T)0.5 * (zr[kk] + zr[km]), Ei = (T)0.5 * (zi[kk] - zi[km]);
+        T Or = (T)0.5 * (zi[kk] + zi[km]), Oi = (T)-0.5 * (zr[kk] - zr[km]);
+        T wr = (T)1, wi = (T)0;
+        if (k != 0) {
+            const int t = k * (kTwiddleN / N);
+            wr = tw_cos<T>(t);
+            wi = -tw_sin<T>(t);
+        }
+        o[k] = Cplx<T>{Er + wr * Or - wi * Oi, Ei + wr * Oi + wi * Or};
+    }
+}
+
+// (a) for the defect path, fused with the accumulation of F and the defect:
+//   F_new = F_old + fout (pairs), D = F_new - U (pairs -> float),
+//   d = (I + dT(A + cI)) D (flux form, FP32), then p = DFT_n(alpha^{n/N} d).
+// The tile carries one halo row on each side for the x-neighbours of D.
+// F_new is written to a second buffer: the halo rows are recomputed here and
+// written by the neighbouring tile, so an in-place update would race.
+template <int N>
+__global__ void __launch_bounds__(kTX) k_cgc_forward_df(
+    int64_t S, int nx, const float* __restrict__ fout, const float2* __restrict__ Facc_in,
+    float2* __restrict__ Facc_out, const float2* __restrict__ Udf, const double* __restrict__ wT,
+    float dTreact, const float* __restrict__ scale, Cplx<float>* __restrict__ p,
+    const int* __restrict__ active) {
+    constexpr int K = N / 2 + 1;
+    __shared__ float sD[kTX + 2][N + 1];
+    __shared__ float sw[kTX + 1];
+    __shared__ Cplx<float> sout[kTX * K];
+    const int64_t s = blockIdx.x;
+    if (!active[s]) return;
+    const int x0 = blockIdx.y * kTX;
+    const int rows = min(kTX, nx - x0);
+    const int tid = threadIdx.x;
+    const int64_t base = s * (int64_t)nx * N;
+    for (int e = tid; e < (rows + 2) * N; e += kTX) {
+        const int row = e / N, col = e - row * N, x = x0 - 1 + row;
+        float D = 0.f;
+        if (x >= 0 && x < nx) {
+            const int64_t o = base + (int64_t)x * N + col;
+            const float f = fout[o];
+            const float2 F = Facc_in ? df_add(Facc_in[o], f) : make_float2(f, 0.f);
+            if (row >= 1 && row <= rows) Facc_out[o] = F;
+            D = df_sub(F, Udf[o]);
+        }
+        sD[row][col] = D;
+    }
+    for (int e = tid; e <= rows; e += kTX) sw[e] = (float)wT[s * (nx + 1) + x0 + e];
+    __syncthreads();
+    if (tid < rows) {
+        const float wl = sw[tid], wr = sw[tid + 1];
+        float xs[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            const float D = sD[tid + 1][n];
+            const float d = D + wl * (D - sD[tid][n]) - wr * (sD[tid + 2][n] - D) + dTreact * D;
+            xs[n] = d * scale[n];
+        }
+        rfft_row<float, N>(xs, sout + tid * K);
+    }
+    __syncthreads();
+    Cplx<float>* pout = p + (s * nx + x0) * (int64_t)K;
+    for (int e = tid; e < rows * K; e += kTX) pout[e] = sout[e];
+}
+
+// (a) for the mixed path (FP64 CGC): F_new = F_old + fout (FP64),
+// r = (I + dT(A + cI)) F_new - prev, prev_0 = alpha U_{N-1}, prev_n = U_{n-1}.
+template <int N>
+__global__ void __launch_bounds__(kTX) k_cgc_forward_mixed(
+    int64_t S, int nx, const float* __restrict__ fout, const double* __restrict__ Facc_in,
+    double* __restrict__ Facc_out, const double* __restrict__ U, const double* __restrict__ wT,
+    double dTreact, double alpha, const double* __restrict__ scale, Cplx<double>* __restrict__ p,
+    const int* __restrict__ active) {
+    constexpr int K = N / 2 + 1;
+    __shared__ double sF[kTX + 2][N + 1];
+    __shared__ double sw[kTX + 1];
+    __shared__ Cplx<double> sout[kTX * K];
+    const int64_t s = blockIdx.x;
+    if (!active[s]) return;
+    const int x0 = blockIdx.y * kTX;
+    const int rows = min(kTX, nx - x0);
+    const int tid = threadIdx.x;
+    const int64_t base = s * (int64_t)nx * N;
+    for (int e = tid; e < (rows + 2) * N; e += kTX) {
+        const int row = e / N, col = e - row * N, x = x0 - 1 + row;
+        double F = 0.0;
+        if (x >= 0 && x < nx) {
+            const int64_t o = base + (int64_t)x * N + col;
+            F = (double)fout[o];
+            if (Facc_in) F += Facc_in[o];
+            if (row >= 1 && row <= rows) Facc_out[o] = F;
+        }
+        sF[row][col] = F;
+    }
+    for (int e = tid; e <= rows; e += kTX) sw[e] = wT[s * (nx + 1) + x0 + e];
+    __syncthreads();
+    if (tid < rows) {
+        const double wl = sw[tid], wr = sw[tid + 1];
+        const double* Ux = U + base + (int64_t)(x0 + tid) * N;
+        double xs[N];
+#pragma unroll
+        for (int n = 0; n < N; ++n) {
+            const double F = sF[tid + 1][n];
+            const double prev = n == 0 ? alpha * Ux[N - 1] : Ux[n - 1];
+            const double r = F + wl * (F - sF[tid][n]) - wr * (sF[tid + 2][n] - F) + dTreact * F;
+            xs[n] = (r - prev) * scale[n];
+        }
+        rfft_row<double, N>(xs, sout + tid * K);
+    }
+    __syncthreads();
+    Cplx<double>* pout = p + (s * nx + x0) * (int64_t)K;
+    for (int e = tid; e < rows * K; e += kTX) pout[e] = sout[e];
+}
+
+#define KLECGC_N_SWITCH(N, CALL)      \
+    switch (N) {                      \
+        case 2: CALL(2); break;       \
+        case 4: CALL(4); break;       \
+        case 8: CALL(8); break;       \
+        case 16: CALL(16); break;     \
+        case 32: CALL(32); break;     \
+        case 64: CALL(64); break;     \
+        default: break;               \
+    }
+
+void launch_cgc_forward_df(int64_t S, int N, int nx, const float* fout, const float2* Facc_in,
+                           float2* Facc_out, const float2* Udf, const double* wT, double dTreact,
+                           const float* scale, Cplx<float>* p, const int* active,
+                           cudaStream_t st) {
+    if (S == 0) return;
+    dim3 grid((unsigned)S, (unsigned)((nx + kTX - 1) / kTX));
+#define KLECGC_FDF(NN)                                                                     \
+    k_cgc_forward_df<NN><<<grid, kTX, 0, st>>>(S, nx, fout, Facc_in, Facc_out, Udf, wT,   \
+                                               (float)dTreact, scale, p, active)
+    KLECGC_N_SWITCH(N, KLECGC_FDF)
+#undef KLECGC_FDF
+}
+
+void launch_cgc_forward_mixed(int64_t S, int N, int nx, const float* fout, const double* Facc_in,
+                              double* Facc_out, const double* U, const double* wT,
+                              double dTreact, double alpha, const double* scale,
+                              Cplx<double>* p, const int* active, cudaStream_t st) {
+    if (S == 0) return;
+    dim3 grid((unsigned)S, (unsigned)((nx + kTX - 1) / kTX));
+#define KLECGC_FMX(NN)                                                                        \
+    k_cgc_forward_mixed<NN><<<grid, kTX, 0, st>>>(S, nx, fout, Facc_in, Facc_out, U, wT,     \
+                                                  dTreact, alpha, scale, p, active)
+    KLECGC_N_SWITCH(N, KLECGC_FMX)
+#undef KLECGC_FMX
+}
+
 // (a): thread x of the tile transforms its own time series.
 template <typename T, typename TIN, int N>
 __global__ void __launch_bounds__(kTX) k_cgc_forward(int64_t S, int nx, const TIN* __restrict__ r,
                                                      const T* __restrict__ scale,
                                                      Cplx<T>* __restrict__ p,
                                                      const int* __restrict__ active) {
-    constexpr int L = N / 2, K = N / 2 + 1;
+    constexpr int K = N / 2 + 1;
     __shared__ T sin_[kTX][N + 1];
     __shared__ Cplx<T> sout[kTX * K];
     const int64_t s = blockIdx.x;
@@ -126,27 +291,10 @@ __global__ void __launch_bounds__(kTX) k_cgc_forward(int64_t S, int nx, const TI
     }
     __syncthreads();
     if (tid < rows) {
-        T zr[L], zi[L];
+        T xs[N];
 #pragma unroll
-        for (int m = 0; m < L; ++m) {
-            zr[m] = sin_[tid][2 * m];
-            zi[m] = sin_[tid][2 * m + 1];
-        }
-        cfft<T, L, false>(zr, zi);
-        Cplx<T>* o = sout + tid * K;
-#pragma unroll
-        for (int k = 0; k <= L; ++k) {
-            const int kk = k % L, km = (L - k) % L;
-            T Er = (T)0.5 * (zr[kk] + zr[km]), Ei = (T)0.5 * (zi[kk] - zi[km]);
-            T Or = (T)0.5 * (zi[kk] + zi[km]), Oi = (T)-0.5 * (zr[kk] - zr[km]);
-            T wr = (T)1, wi = (T)0;
-            if (k != 0) {
-                const int t = k * (kTwiddleN / N);
-                wr = tw_cos<T>(t);
-                wi = -tw_sin<T>(t);
-            }
-            o[k] = Cplx<T>{Er + wr * Or - wi * Oi, Ei + wr * Oi + wi * Or};
-        }
+        for (int n = 0; n < N; ++n) xs[n] = sin_[tid][n];
+        rfft_row<T, N>(xs, sout + tid * K);
     }
     __syncthreads();
     Cplx<T>* pout = p + (s * nx + x0) * (int64_t)K;
@@ -351,6 +499,131 @@ template void launch_cgc_inverse<double>(int64_t, int, int, const Cplx<double>*,
 template void launch_cgc_inverse<float>(int64_t, int, int, const Cplx<float>*, const float*,
                                         double*, int, unsigned long long*, float*, const int*,
                                         cudaStream_t);
+
+// (c) + update for the defect path: U (pairs) += u, c32 = u, delta = max|u|.
+template <int N>
+__global__ void __launch_bounds__(kTX) k_cgc_inverse_df(int64_t S, int nx,
+                                                        const Cplx<float>* __restrict__ q,
+                                                        const float* __restrict__ iscale,
+                                                        float2* __restrict__ Udf,
+                                                        unsigned long long* __restrict__ delta,
+                                                        float* __restrict__ c32,
+                                                        const int* __restrict__ active) {
+    constexpr int L = N / 2, K = N / 2 + 1;
+    __shared__ Cplx<float> sq[kTX * K];
+    __shared__ float2 su[kTX][N + 1];
+    __shared__ float sc[kTX][N + 1];
+    const int64_t s = blockIdx.x;
+    if (!active[s]) return;
+    const int x0 = blockIdx.y * kTX;
+    const int rows = min(kTX, nx - x0);
+    const int tid = threadIdx.x;
+    const Cplx<float>* qin = q + (s * nx + x0) * (int64_t)K;
+    for (int e = tid; e < rows * K; e += kTX) sq[e] = qin[e];
+    float2* Ut = Udf + (s * nx + x0) * (int64_t)N;
+    for (int e = tid; e < rows * N; e += kTX) {
+        const int row = e / N, col = e - row * N;
+        su[row][col] = Ut[e];
+    }
+    __syncthreads();
+    float umax = 0.f;
+    bool bad = false;
+    if (tid < rows) {
+        const Cplx<float>* X = sq + tid * K;
+        float zr[L], zi[L];
+#pragma unroll
+        for (int k = 0; k < L; ++k) {
+            Cplx<float> A = X[k], B = X[L - k];
+            float Er = 0.5f * (A.x + B.x), Ei = 0.5f * (A.y - B.y);
+            float Dr = 0.5f * (A.x - B.x), Di = 0.5f * (A.y + B.y);
+            float wr = 1.f, wi = 0.f;
+            if (k != 0) {
+                const int t = k * (kTwiddleN / N);
+                wr = tw_cos<float>(t);
+                wi = tw_sin<float>(t);
+            }
+            float Or = Dr * wr - Di * wi, Oi = Dr * wi + Di * wr;
+            zr[k] = Er - Oi;
+            zi[k] = Ei + Or;
+        }
+        cfft<float, L, true>(zr, zi);
+#pragma unroll
+        for (int m = 0; m < L; ++m) {
+            const float u0 = zr[m] * iscale[2 * m], u1 = zi[m] * iscale[2 * m + 1];
+            umax = fmaxf(umax, fmaxf(fabsf(u0), fabsf(u1)));
+            bad |= (u0 != u0) || (u1 != u1);
+            su[tid][2 * m] = df_add(su[tid][2 * m], u0);
+            su[tid][2 * m + 1] = df_add(su[tid][2 * m + 1], u1);
+            sc[tid][2 * m] = u0;
+            sc[tid][2 * m + 1] = u1;
+        }
+    }
+    __syncthreads();
+    float* ct = c32 + (s * nx + x0) * (int64_t)N;
+    for (int e = tid; e < rows * N; e += kTX) {
+        const int row = e / N, col = e - row * N;
+        Ut[e] = su[row][col];
+        ct[e] = sc[row][col];
+    }
+    // a NaN increment must reach the stopping rule (fmaxf drops NaNs)
+    unsigned long long dmax = bad ? 0x7ff8000000000000ull : abs_bits((double)umax);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
+    if (tid == 0 && dmax) atomicMax(delta + s, dmax);
+}
+
+void launch_cgc_inverse_df(int64_t S, int N, int nx, const Cplx<float>* q, const float* iscale,
+                           float2* Udf, unsigned long long* delta, float* c32, const int* active,
+                           cudaStream_t st) {
+    if (S == 0) return;
+    dim3 grid((unsigned)S, (unsigned)((nx + kTX - 1) / kTX));
+#define KLECGC_IDF(NN) \
+    k_cgc_inverse_df<NN><<<grid, kTX, 0, st>>>(S, nx, q, iscale, Udf, delta, c32, active)
+    KLECGC_N_SWITCH(N, KLECGC_IDF)
+#undef KLECGC_IDF
+}
+
+__global__ void k_to_pairs(double* __restrict__ U, int64_t n) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const double v = U[t];
+    const float hi = (float)v;
+    const float lo = (float)(v - (double)hi);
+    reinterpret_cast<float2*>(U)[t] = make_float2(hi, lo);
+}
+
+void launch_to_pairs(double* U, int64_t n, cudaStream_t st) {
+    if (n == 0) return;
+    k_to_pairs<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(U, n);
+}
+
+__global__ void k_pairs_transpose_out(const float2* __restrict__ in, double* __restrict__ out,
+                                      int A, int B) {
+    __shared__ double tile[32][33];
+    const int64_t s = blockIdx.x;
+    const float2* src = in + s * (int64_t)A * B;
+    double* dst = out + s * (int64_t)A * B;
+    int a0 = blockIdx.y * 32, b0 = blockIdx.z * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        int a = a0 + y, b = b0 + threadIdx.x;
+        if (a < A && b < B) {
+            const float2 v = src[(int64_t)a * B + b];
+            tile[y][threadIdx.x] = (double)v.x + (double)v.y;
+        }
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        int b = b0 + y, a = a0 + threadIdx.x;
+        if (a < A && b < B) dst[(int64_t)b * A + a] = tile[threadIdx.x][y];
+    }
+}
+
+void launch_pairs_transpose_out(const float2* in, double* out, int64_t S, int nx, int N,
+                                cudaStream_t st) {
+    if (S == 0) return;
+    dim3 grid((unsigned)S, (unsigned)((nx + 31) / 32), (unsigned)((N + 31) / 32));
+    k_pairs_transpose_out<<<grid, dim3(32, 8), 0, st>>>(in, out, nx, N);
+}
 
 // Stopping rule per sample (Algorithm 2, Step 3): stop after the first
 // iteration whose increment max-norm is <= tol.

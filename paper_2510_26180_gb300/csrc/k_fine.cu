@@ -71,6 +71,35 @@ void launch_fine_sweep_fp64(int64_t S, int N, int nx, int J, double dT, double a
         S, N, nx, J, dT, alpha, dT * react, dt * forcing, U, u0, fc, wT, r, active);
 }
 
+// r = (I + dT(A + cI)) F - prev in FP64 for an FP32 F (stage entry of the
+// mixed fine sweep): one thread per (sample, interval), rows in sequence.
+__global__ void k_jump_from_f32(int64_t S, int N, int nx, double alpha, double dTreact,
+                                const float* __restrict__ F, const double* __restrict__ U,
+                                const double* __restrict__ wT, double* __restrict__ r) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    int64_t s = t / N;
+    int n = (int)(t - s * N);
+    if (s >= S) return;
+    const int64_t base = s * (int64_t)nx * N;
+    const double* wTs = wT + s * (nx + 1);
+    double Fm = 0.0, Fi = F[base + n];
+    for (int i = 0; i < nx; ++i) {
+        const double Fp = (i + 1 < nx) ? (double)F[base + (int64_t)(i + 1) * N + n] : 0.0;
+        const double BF = Fi + wTs[i] * (Fi - Fm) - wTs[i + 1] * (Fp - Fi) + dTreact * Fi;
+        r[base + (int64_t)i * N + n] = BF - prev_value(U + base, i, n, N, alpha);
+        Fm = Fi;
+        Fi = Fp;
+    }
+}
+
+void launch_jump_from_f32(int64_t S, int N, int nx, double alpha, double dTreact, const float* F,
+                          const double* U, const double* wT, double* r, cudaStream_t st) {
+    int64_t n = S * N;
+    if (n == 0) return;
+    k_jump_from_f32<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(S, N, nx, alpha, dTreact, F, U,
+                                                                 wT, r);
+}
+
 // Reference solution U*: N*J sequential backward-Euler steps per sample, one
 // thread per sample, state in scratch[nx][S] (samples interleaved so that a
 // warp's accesses coalesce).  Output U[s][i][n] (internal layout).

@@ -20,6 +20,15 @@
 // Rows are padded to 32R >= nx + 1.  Padded rows have l = u = dinv = 0 so
 // they stay 0 and act as the Dirichlet value beyond the last row; the table
 // row nx still carries the weight of the boundary face nx.
+//
+// Output: the FP32 end values of every interval, fout[s][i][n].  F is affine,
+// F(v + e) = F(v) + F0(e) with F0 the source-free propagator, so the caller
+// runs F on the start values once (in_mode 0) and afterwards F0 on the FP32
+// increments c = U^k - U^{k-1} (in_mode 1); the accumulation of F(U^k) in
+// higher precision, the CGC right-hand side and the defect are formed by the
+// CGC transform kernel that consumes fout.  The rounding of each F0 term is
+// proportional to that term, so the iteration converges to its tolerance
+// instead of stalling at FP32 resolution.
 #include "common.cuh"
 
 namespace klecgc {
@@ -72,14 +81,12 @@ __global__ void k_fine_table32(const double* __restrict__ a, int64_t S, int nx, 
     }
 }
 
-template <int R, int QS>
+template <int R, int QS, bool REACT>
 __global__ void __launch_bounds__(128) k_fine32(
-    int64_t S, int N, int nx, int J, int cps, float dt_react, float dt_f, float wT_scale,
-    float dTreact_f, double alpha, double dTreact, const double* __restrict__ U,
-    const double* __restrict__ u0, const float* __restrict__ c32, double* __restrict__ Facc,
-    int in_mode, const float4* __restrict__ tabA, const float4* __restrict__ tabD,
-    const double* __restrict__ wT, double* __restrict__ r, float* __restrict__ d32, int out_mode,
-    const int* __restrict__ active) {
+    int64_t S, int N, int nx, int J, int cps, float dt_react, float dt_f, int in_mode,
+    const double* __restrict__ U64, const float2* __restrict__ Udf, const double* __restrict__ u0,
+    const float* __restrict__ c32, const float4* __restrict__ tabA, const float4* __restrict__ tabD,
+    float* __restrict__ fout, const int* __restrict__ active) {
     extern __shared__ float4 smem[];
     float4* sA = smem;
     float4* sD = smem + R * 32;
@@ -132,10 +139,13 @@ __global__ void __launch_bounds__(128) k_fine32(
             const int i = lane * R + j;
             float x0 = 0.f;
             if (i < nx && n < N) {
-                if (in_mode == 0)
-                    x0 = (float)(n == 0 ? u0[i] : U[sbase + (int64_t)i * N + n - 1]);
-                else if (n > 0)
-                    x0 = c32[sbase + (int64_t)i * N + n - 1];
+                const int64_t o = sbase + (int64_t)i * N + n - 1;
+                if (in_mode == 1)
+                    x0 = n > 0 ? c32[o] : 0.f;
+                else if (n == 0)
+                    x0 = (float)u0[i];
+                else
+                    x0 = Udf ? Udf[o].x : (float)U64[o];
             }
             v[q][j] = x0;
         }
@@ -155,7 +165,8 @@ __global__ void __launch_bounds__(128) k_fine32(
             const float wr = (j + 1 < R) ? sA[(j + 1) * 32 + lane].y : wd_right;
             const float vn = (j + 1 < R) ? v[q][j + 1] : vr;
             const float f = wr * (vn - v[q][j]);
-            const float rhs = (f - fprev) + (src - dt_react * v[q][j]);
+            float rhs = f - fprev;
+            if (REACT) rhs += src - dt_react * v[q][j];
             yprev = fmaf(-ta.z, yprev, rhs);
             w[q][j] = yprev;
             fprev = f;
@@ -225,7 +236,8 @@ __global__ void __launch_bounds__(128) k_fine32(
                 if (more) {
                     const float f = ta.y * (v[q][j] - (j ? v[q][j - 1] : vl));
                     if (j) {
-                        const float rhs = (f - fprev) + (src - dt_react * v[q][j - 1]);
+                        float rhs = f - fprev;
+                        if (REACT) rhs += src - dt_react * v[q][j - 1];
                         yprev = fmaf(-lprev, yprev, rhs);
                         w[q][j - 1] = yprev;
                     }
@@ -235,84 +247,25 @@ __global__ void __launch_bounds__(128) k_fine32(
             }
             if (more) {
                 const float f = wd_right * (vr - v[q][R - 1]);
-                const float rhs = (f - fprev) + (src - dt_react * v[q][R - 1]);
+                float rhs = f - fprev;
+                if (REACT) rhs += src - dt_react * v[q][R - 1];
                 w[q][R - 1] = fmaf(-lprev, yprev, rhs);
             }
         }
     }
 
-    // epilogue: accumulate F, then the CGC right-hand side or the defect
+    // epilogue: F (in_mode 0) or F0(c) (in_mode 1) for this lane's rows, FP32
 #pragma unroll
-    for (int q = 0; q < QS; ++q) {
-        const int n = n0 + q;
-        if (n >= N) continue;
-        const double* Us = U + sbase;
-        double* Fa = Facc + sbase;
-        // new F at this lane's first and last rows (for the neighbour exchange)
-        auto fnew = [&](int j) -> double {
-            const int i = lane * R + j;
-            if (i >= nx) return 0.0;
-            const double old = in_mode ? Fa[(int64_t)i * N + n] : 0.0;
-            return old + (double)v[q][j];
-        };
-        const double f_first = fnew(0), f_last = fnew(R - 1);
-        double fl = __shfl_up_sync(FULL, f_last, 1);
-        double fr = __shfl_down_sync(FULL, f_first, 1);
-        if (lane == 0) fl = 0.0;
-        if (lane == 31) fr = 0.0;
-        if (out_mode == 0) {
-            const double* wTs = wT + s * (nx + 1);
-            double Fm = fl, Fi = f_first;
-#pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const int i = lane * R + j;
-                const double Fp = (j + 1 < R) ? fnew(j + 1) : fr;
-                if (i < nx) {
-                    const int64_t o = (int64_t)i * N + n;
-                    Fa[o] = Fi;
-                    const double BF = Fi + wTs[i] * (Fi - Fm) - wTs[i + 1] * (Fp - Fi) + dTreact * Fi;
-                    const double prev = n == 0 ? alpha * Us[(int64_t)i * N + (N - 1)] : Us[o - 1];
-                    r[sbase + o] = BF - prev;
-                }
-                Fm = Fi;
-                Fi = Fp;
-            }
+    for (int j = 0; j < R; ++j) {
+        const int i = lane * R + j;
+        if (i >= nx) break;
+        float* o = fout + sbase + (int64_t)i * N + n0;
+        if (QS == 2 && n0 + 1 < N) {
+            *reinterpret_cast<float2*>(o) = make_float2(v[0][j], v[QS - 1][j]);
         } else {
-            // D = F_n - U_n in FP64, then d = (I + dT(A + cI)) D in FP32 flux form
-            auto dval = [&](int j, double F) -> float {
-                const int i = lane * R + j;
-                return i < nx ? (float)(F - Us[(int64_t)i * N + n]) : 0.f;
-            };
-            const float d_first = dval(0, f_first), d_last = dval(R - 1, f_last);
-            float dl = __shfl_up_sync(FULL, d_last, 1);
-            float dr = __shfl_down_sync(FULL, d_first, 1);
-            if (lane == 0) dl = 0.f;
-            if (lane == 31) dr = 0.f;
-            float Dm = dl, Di = d_first;
-            double Fcur = f_first;
-            float* ds = d32 + sbase;
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const int i = lane * R + j;
-                double Fnext = 0.0;
-                float Dp;
-                if (j + 1 < R) {
-                    Fnext = fnew(j + 1);
-                    Dp = dval(j + 1, Fnext);
-                } else {
-                    Dp = dr;
-                }
-                if (i < nx) {
-                    const int64_t o = (int64_t)i * N + n;
-                    Fa[o] = Fcur;
-                    const float wl = wT_scale * sA[j * 32 + lane].y;
-                    const float wr = wT_scale * ((j + 1 < R) ? sA[(j + 1) * 32 + lane].y : wd_right);
-                    ds[o] = Di + wl * (Di - Dm) - wr * (Dp - Di) + dTreact_f * Di;
-                }
-                Dm = Di;
-                Di = Dp;
-                Fcur = Fnext;
-            }
+            for (int q = 0; q < QS; ++q)
+                if (n0 + q < N) o[q] = v[q][j];
         }
     }
 }
@@ -331,11 +284,10 @@ void launch_fine_table32(const double* a, int64_t S, int nx, int R, double h, do
                                                              tabA, tabD);
 }
 
-template <int R, int QS>
-static void launch_r(int64_t S, int N, int nx, int J, double dt, double dT, double alpha,
-                     double react, double forcing, const double* U, const double* u0,
-                     const float* c32, double* Facc, int in_mode, const float4* tabA,
-                     const float4* tabD, const double* wT, double* r, float* d32, int out_mode,
+template <int R, int QS, bool REACT>
+static void launch_r(int64_t S, int N, int nx, int J, double dt, double react, double forcing,
+                     int in_mode, const double* U64, const float2* Udf, const double* u0,
+                     const float* c32, const float4* tabA, const float4* tabD, float* fout,
                      const int* active, cudaStream_t st) {
     constexpr int warps = 4;
     const int per_cta = warps * QS;
@@ -343,28 +295,39 @@ static void launch_r(int64_t S, int N, int nx, int J, double dt, double dT, doub
     const size_t smem = 2 * (size_t)R * 32 * sizeof(float4);
     static bool attr = false;
     if (!attr && smem > 48 * 1024) {
-        cudaFuncSetAttribute(k_fine32<R, QS>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_fine32<R, QS, REACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              (int)smem);
         attr = true;
     }
-    const double wT_scale = (double)J;  // dT w = J * dt w
-    k_fine32<R, QS><<<(unsigned)(S * cps), warps * 32, smem, st>>>(
-        S, N, nx, J, cps, (float)(dt * react), (float)(dt * forcing), (float)wT_scale,
-        (float)(dT * react), alpha, dT * react, U, u0, c32, Facc, in_mode, tabA, tabD, wT, r, d32,
-        out_mode, active);
+    k_fine32<R, QS, REACT><<<(unsigned)(S * cps), warps * 32, smem, st>>>(
+        S, N, nx, J, cps, (float)(dt * react), (float)(dt * forcing), in_mode, U64, Udf, u0, c32,
+        tabA, tabD, fout, active);
 }
 
-void launch_fine32(int64_t S, int N, int nx, int J, double dt, double dT, double alpha,
-                   double react, double forcing, const double* U, const double* u0,
-                   const float* c32, double* Facc, int in_mode, const float4* tabA,
-                   const float4* tabD, const double* wT, double* r, float* d32, int out_mode,
+template <int R, int QS>
+static void launch_rr(int64_t S, int N, int nx, int J, double dt, double react, double forcing,
+                      int in_mode, const double* U64, const float2* Udf, const double* u0,
+                      const float* c32, const float4* tabA, const float4* tabD, float* fout,
+                      const int* active, cudaStream_t st) {
+    const bool react_terms = react != 0.0 || (forcing != 0.0 && in_mode == 0);
+    if (react_terms)
+        launch_r<R, QS, true>(S, N, nx, J, dt, react, forcing, in_mode, U64, Udf, u0, c32, tabA,
+                              tabD, fout, active, st);
+    else
+        launch_r<R, QS, false>(S, N, nx, J, dt, react, forcing, in_mode, U64, Udf, u0, c32, tabA,
+                               tabD, fout, active, st);
+}
+
+void launch_fine32(int64_t S, int N, int nx, int J, double dt, double react, double forcing,
+                   int in_mode, const double* U64, const float2* Udf, const double* u0,
+                   const float* c32, const float4* tabA, const float4* tabD, float* fout,
                    const int* active, cudaStream_t st) {
     if (S == 0) return;
     switch (fine32_rows_per_lane(nx)) {
-#define KLECGC_F32(RR, QQ)                                                                     \
-    case RR:                                                                                   \
-        launch_r<RR, QQ>(S, N, nx, J, dt, dT, alpha, react, forcing, U, u0, c32, Facc, in_mode, \
-                         tabA, tabD, wT, r, d32, out_mode, active, st);                        \
+#define KLECGC_F32(RR, QQ)                                                                   \
+    case RR:                                                                                 \
+        launch_rr<RR, QQ>(S, N, nx, J, dt, react, forcing, in_mode, U64, Udf, u0, c32, tabA, \
+                          tabD, fout, active, st);                                           \
         break;
         KLECGC_F32(2, 2)
         KLECGC_F32(4, 2)
