@@ -203,12 +203,12 @@ struct Operators {
     double* wT = nullptr;
     FineCoef64* f64 = nullptr;
     FineCoef32* f32 = nullptr;
-    float4* tabA = nullptr;
-    float4* tabD = nullptr;
+    void* tab32 = nullptr;
     Cplx<double>* dinv64 = nullptr;
     Cplx<double>* lu64 = nullptr;
     Cplx<float>* dinv32 = nullptr;
     Cplx<float>* lu32 = nullptr;
+    float* wT32 = nullptr;
 };
 
 klecgc_status build_field(klecgc_ctx* ctx, const double* xi_d, int64_t S, cudaStream_t st,
@@ -240,11 +240,9 @@ klecgc_status build_operators(klecgc_ctx* ctx, const double* xi_d, int64_t S, in
     } else if (want_fine == 2) {
         const int R = fine32_rows_per_lane(nx);
         if (R == 0) return fail(KLECGC_E_UNSUPPORTED, "mixed precision needs nx <= 2047");
-        WS(float4, tA, "tab32A", S * 32 * (int64_t)R);
-        WS(float4, tD, "tab32D", S * 32 * (int64_t)R);
-        ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_table32(op->a, S, nx, R, ctx->h, dT / J, ctx->prob.reaction, tA, tD, st); });
-        op->tabA = tA;
-        op->tabD = tD;
+        WS(char, tb, "tab32", fine_table32_bytes(S, R));
+        ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_table32(op->a, S, nx, R, ctx->h, dT / J, ctx->prob.reaction, tb, st); });
+        op->tab32 = tb;
     }
     if (want_cgc) {
         std::vector<double2> lam(K);
@@ -263,11 +261,18 @@ klecgc_status build_operators(klecgc_ctx* ctx, const double* xi_d, int64_t S, in
             op->dinv64 = di;
             op->lu64 = lu;
         } else {
+            std::vector<float2> lam32(K);
+            for (int k = 0; k < K; ++k) lam32[k] = make_float2((float)lam[k].x, (float)lam[k].y);
+            WS(float2, lam32_d, "lam32", K);
+            TRY(cudaMemcpyAsync(lam32_d, lam32.data(), K * sizeof(float2), cudaMemcpyHostToDevice, st));
+            WS(float, wT32, "wT32", S * nf);
             WS(Cplx<float>, di, "cgc_dinv32", S * nx * K);
             WS(Cplx<float>, lu, "cgc_lu32", S * nx * K);
-            ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_cgc_factors<float>(op->a, S, nx, ctx->h, dT, ctx->prob.reaction, lam_d, K, di, lu, st); });
+            ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_to_float(op->wT, wT32, S * nf, st); });
+            ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_cgc_factors32(wT32, S, nx, dT * ctx->prob.reaction, lam32_d, K, di, lu, st); });
             op->dinv32 = di;
             op->lu32 = lu;
+            op->wT32 = wT32;
         }
     }
     TRY(cudaGetLastError());
@@ -671,7 +676,7 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
     } else {
         WS(float, fo, "fout", S * (int64_t)nx * N);
         launch_fine32(S, N, nx, J, dT / J, ctx->prob.reaction, ctx->prob.forcing, 0, U, nullptr,
-                      ctx->u0, nullptr, op.tabA, op.tabD, fo, active, st);
+                      ctx->u0, nullptr, op.tab32, fo, active, st);
         launch_jump_from_f32(S, N, nx, alpha, dT * ctx->prob.reaction, fo, U, op.wT, r, st);
     }
     TRY(cudaGetLastError());
@@ -708,7 +713,7 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
         if ((s = scale_tables<double>(ctx, N, alpha, st, &sc, &isc)) != KLECGC_OK) return s;
         WS(Cplx<double>, p, "p64", S * (int64_t)nx * K);
         launch_cgc_forward<double, double>(S, N, nx, r, sc, p, active, st);
-        launch_cgc_solve<double>(S, K, nx, op.dinv64, op.lu64, op.wT, p, active, st);
+        launch_cgc_solve<double, double>(S, K, nx, op.dinv64, op.lu64, op.wT, p, active, st);
         launch_cgc_inverse<double>(S, N, nx, p, isc, U, 2, nullptr, nullptr, active, st);
     } else {
         float *sc, *isc;
@@ -717,7 +722,7 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
         launch_to_float(r, r32, S * (int64_t)nx * N, st);
         WS(Cplx<float>, p, "p32", S * (int64_t)nx * K);
         launch_cgc_forward<float, float>(S, N, nx, r32, sc, p, active, st);
-        launch_cgc_solve<float>(S, K, nx, op.dinv32, op.lu32, op.wT, p, active, st);
+        launch_cgc_solve<float, float>(S, K, nx, op.dinv32, op.lu32, op.wT32, p, active, st);
         launch_cgc_inverse<float>(S, N, nx, p, isc, U, 2, nullptr, nullptr, active, st);
     }
     TRY(cudaGetLastError());
@@ -850,8 +855,8 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
             // F(start) on the first iteration, F0(increment) afterwards
             ctx->launch(KLECGC_K_FINE, st, [&] {
                 launch_fine32(S, N, nx, J, dT / J, ctx->prob.reaction, ctx->prob.forcing,
-                              k == 0 ? 0 : 1, defect ? nullptr : U, Udf, ctx->u0, c32, op.tabA,
-                              op.tabD, fout, active, st);
+                              k == 0 ? 0 : 1, defect ? nullptr : U, Udf, ctx->u0, c32, op.tab32,
+                              fout, active, st);
             });
             if (defect)
                 ctx->launch(KLECGC_K_CGC_FWD, st, [&] {
@@ -866,10 +871,10 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
                 });
         }
         if (!defect) {
-            ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_cgc_solve<double>(S, K, nx, op.dinv64, op.lu64, op.wT, p64, active, st); });
+            ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_cgc_solve<double, double>(S, K, nx, op.dinv64, op.lu64, op.wT, p64, active, st); });
             ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc64, U, 0, delta, c32, active, st); });
         } else {
-            ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_cgc_solve<float>(S, K, nx, op.dinv32, op.lu32, op.wT, p32, active, st); });
+            ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_cgc_solve<float, float>(S, K, nx, op.dinv32, op.lu32, op.wT32, p32, active, st); });
             ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse_df(S, N, nx, p32, isc32, Udf, delta, c32, active, st); });
         }
         TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));

@@ -62,6 +62,9 @@ void launch_fine_factors(const double* a, int64_t S, int nx, double h, double dt
 template <typename T>
 void launch_cgc_factors(const double* a, int64_t S, int nx, double h, double dT, double react,
                         const double2* lam, int K, Cplx<T>* dinv, Cplx<T>* lu, cudaStream_t st);
+void launch_cgc_factors32(const float* wT32, int64_t S, int nx, double dTreact,
+                          const float2* lam, int K, Cplx<float>* dinv, Cplx<float>* lu,
+                          cudaStream_t st);
 void launch_face_weights(const double* a, int64_t S, int nf, double scale, double* w,
                          cudaStream_t st);
 void launch_nonfinite_flag(const double* x, int64_t n, int* flag, cudaStream_t st);
@@ -91,14 +94,15 @@ void launch_fine_sweep_fp64(int64_t S, int N, int nx, int J, double dT, double a
 // FP32 increment-form fine sweep, register resident.  in_mode 0: Facc = F(start);
 // in_mode 1: Facc += F0(c32 of interval n-1).  out_mode 0: r (FP64); 1: defect d32.
 int fine32_rows_per_lane(int nx);
+size_t fine_table32_bytes(int64_t S, int R);
 void launch_fine_table32(const double* a, int64_t S, int nx, int R, double h, double dt,
-                         double react, float4* tabA, float4* tabD, cudaStream_t st);
+                         double react, void* table, cudaStream_t st);
 // in_mode 0: fout = F(start), start_n = U_{n-1} (U64, or Udf.hi), u0 for n = 0;
 // in_mode 1: fout = F0(c_{n-1}), 0 for n = 0.  fout: [S][nx][N] FP32.
 void launch_fine32(int64_t S, int N, int nx, int J, double dt, double react, double forcing,
                    int in_mode, const double* U64, const float2* Udf, const double* u0,
-                   const float* c32, const float4* tabA, const float4* tabD, float* fout,
-                   const int* active, cudaStream_t st);
+                   const float* c32, const void* table, float* fout, const int* active,
+                   cudaStream_t st);
 // r = (I + dT(A + cI)) F - prev in FP64 from an FP32 F ([S][nx][N]).
 void launch_jump_from_f32(int64_t S, int N, int nx, double alpha, double dTreact, const float* F,
                           const double* U, const double* wT, double* r, cudaStream_t st);
@@ -111,9 +115,9 @@ template <typename T, typename TIN>
 void launch_cgc_forward(int64_t S, int N, int nx, const TIN* r, const T* scale, Cplx<T>* p,
                         const int* active, cudaStream_t st);
 // Step (b): (lambda_k I + dT A) q_k = p_k in place.
-template <typename T>
+template <typename T, typename TW>
 void launch_cgc_solve(int64_t S, int K, int nx, const Cplx<T>* dinv, const Cplx<T>* lu,
-                      const double* wT, Cplx<T>* p, const int* active, cudaStream_t st);
+                      const TW* wT, Cplx<T>* p, const int* active, cudaStream_t st);
 // Step (a) with the FP32 fine result folded in (mixed paths).  Facc_out =
 // Facc_in + fout (Facc_in null on the first iteration); then
 //  defect: d = (I + dT(A+cI)) (Facc_out - U) on pairs U, Facc (FP32 ops only);

@@ -138,35 +138,73 @@ __device__ __forceinline__ void rfft_row(const T (&x)[N], Cplx<T>* o) {
 // The tile carries one halo row on each side for the x-neighbours of D.
 // F_new is written to a second buffer: the halo rows are recomputed here and
 // written by the neighbouring tile, so an in-place update would race.
+constexpr int kTXF = 64;  // x points (= threads) per CTA in the FP32 transform kernels
+
 template <int N>
-__global__ void __launch_bounds__(kTX) k_cgc_forward_df(
+__global__ void __launch_bounds__(kTXF) k_cgc_forward_df(
     int64_t S, int nx, const float* __restrict__ fout, const float2* __restrict__ Facc_in,
     float2* __restrict__ Facc_out, const float2* __restrict__ Udf, const double* __restrict__ wT,
     float dTreact, const float* __restrict__ scale, Cplx<float>* __restrict__ p,
     const int* __restrict__ active) {
     constexpr int K = N / 2 + 1;
-    __shared__ float sD[kTX + 2][N + 1];
-    __shared__ float sw[kTX + 1];
-    __shared__ Cplx<float> sout[kTX * K];
+    __shared__ float sD[kTXF + 2][N + 1];
+    __shared__ float sw[kTXF + 1];
+    __shared__ Cplx<float> sout[kTXF * K];
     const int64_t s = blockIdx.x;
     if (!active[s]) return;
-    const int x0 = blockIdx.y * kTX;
-    const int rows = min(kTX, nx - x0);
+    const int x0 = blockIdx.y * kTXF;
+    const int rows = min(kTXF, nx - x0);
     const int tid = threadIdx.x;
     const int64_t base = s * (int64_t)nx * N;
-    for (int e = tid; e < (rows + 2) * N; e += kTX) {
-        const int row = e / N, col = e - row * N, x = x0 - 1 + row;
-        float D = 0.f;
-        if (x >= 0 && x < nx) {
-            const int64_t o = base + (int64_t)x * N + col;
-            const float f = fout[o];
-            const float2 F = Facc_in ? df_add(Facc_in[o], f) : make_float2(f, 0.f);
-            if (row >= 1 && row <= rows) Facc_out[o] = F;
-            D = df_sub(F, Udf[o]);
+    if constexpr (N % 4 == 0) {
+        // 4 consecutive coarse times per access: 16-byte fout, 2 x 16-byte pair loads
+        constexpr int G = N / 4;
+#pragma unroll 4
+        for (int e = tid; e < (rows + 2) * G; e += kTXF) {
+            const int row = e / G, c = (e - row * G) * 4, x = x0 - 1 + row;
+            float D[4] = {0.f, 0.f, 0.f, 0.f};
+            if (x >= 0 && x < nx) {
+                const int64_t o = base + (int64_t)x * N + c;
+                const float4 f = *reinterpret_cast<const float4*>(fout + o);
+                const float4 u01 = *reinterpret_cast<const float4*>(Udf + o);
+                const float4 u23 = *reinterpret_cast<const float4*>(Udf + o + 2);
+                float2 F0 = make_float2(f.x, 0.f), F1 = make_float2(f.y, 0.f);
+                float2 F2 = make_float2(f.z, 0.f), F3 = make_float2(f.w, 0.f);
+                if (Facc_in) {
+                    const float4 a01 = *reinterpret_cast<const float4*>(Facc_in + o);
+                    const float4 a23 = *reinterpret_cast<const float4*>(Facc_in + o + 2);
+                    F0 = df_add(make_float2(a01.x, a01.y), f.x);
+                    F1 = df_add(make_float2(a01.z, a01.w), f.y);
+                    F2 = df_add(make_float2(a23.x, a23.y), f.z);
+                    F3 = df_add(make_float2(a23.z, a23.w), f.w);
+                }
+                if (row >= 1 && row <= rows) {
+                    *reinterpret_cast<float4*>(Facc_out + o) = make_float4(F0.x, F0.y, F1.x, F1.y);
+                    *reinterpret_cast<float4*>(Facc_out + o + 2) = make_float4(F2.x, F2.y, F3.x, F3.y);
+                }
+                D[0] = df_sub(F0, make_float2(u01.x, u01.y));
+                D[1] = df_sub(F1, make_float2(u01.z, u01.w));
+                D[2] = df_sub(F2, make_float2(u23.x, u23.y));
+                D[3] = df_sub(F3, make_float2(u23.z, u23.w));
+            }
+#pragma unroll
+            for (int q = 0; q < 4; ++q) sD[row][c + q] = D[q];
         }
-        sD[row][col] = D;
+    } else {
+        for (int e = tid; e < (rows + 2) * N; e += kTXF) {
+            const int row = e / N, col = e - row * N, x = x0 - 1 + row;
+            float D = 0.f;
+            if (x >= 0 && x < nx) {
+                const int64_t o = base + (int64_t)x * N + col;
+                const float f = fout[o];
+                const float2 F = Facc_in ? df_add(Facc_in[o], f) : make_float2(f, 0.f);
+                if (row >= 1 && row <= rows) Facc_out[o] = F;
+                D = df_sub(F, Udf[o]);
+            }
+            sD[row][col] = D;
+        }
     }
-    for (int e = tid; e <= rows; e += kTX) sw[e] = (float)wT[s * (nx + 1) + x0 + e];
+    for (int e = tid; e <= rows; e += kTXF) sw[e] = (float)wT[s * (nx + 1) + x0 + e];
     __syncthreads();
     if (tid < rows) {
         const float wl = sw[tid], wr = sw[tid + 1];
@@ -181,7 +219,7 @@ __global__ void __launch_bounds__(kTX) k_cgc_forward_df(
     }
     __syncthreads();
     Cplx<float>* pout = p + (s * nx + x0) * (int64_t)K;
-    for (int e = tid; e < rows * K; e += kTX) pout[e] = sout[e];
+    for (int e = tid; e < rows * K; e += kTXF) pout[e] = sout[e];
 }
 
 // (a) for the mixed path (FP64 CGC): F_new = F_old + fout (FP64),
@@ -249,9 +287,9 @@ void launch_cgc_forward_df(int64_t S, int N, int nx, const float* fout, const fl
                            const float* scale, Cplx<float>* p, const int* active,
                            cudaStream_t st) {
     if (S == 0) return;
-    dim3 grid((unsigned)S, (unsigned)((nx + kTX - 1) / kTX));
+    dim3 grid((unsigned)S, (unsigned)((nx + kTXF - 1) / kTXF));
 #define KLECGC_FDF(NN)                                                                     \
-    k_cgc_forward_df<NN><<<grid, kTX, 0, st>>>(S, nx, fout, Facc_in, Facc_out, Udf, wT,   \
+    k_cgc_forward_df<NN><<<grid, kTXF, 0, st>>>(S, nx, fout, Facc_in, Facc_out, Udf, wT,   \
                                                (float)dTreact, scale, p, active)
     KLECGC_N_SWITCH(N, KLECGC_FDF)
 #undef KLECGC_FDF
@@ -325,56 +363,91 @@ template void launch_cgc_forward<float, float>(int64_t, int, int, const float*, 
                                                Cplx<float>*, const int*, cudaStream_t);
 
 // (b): one thread per (sample, k); forward sweep w_i = dinv_i (p_i + wT_i w_{i-1}),
-// back substitution q_i = w_i - lu_i q_{i+1}, in place.
-template <typename T>
+// back substitution q_i = w_i - lu_i q_{i+1}, in place.  Rows are loaded in
+// chunks of CH before the dependent recurrence runs over them, so that CH
+// loads per thread are in flight instead of one.  TW is the type of the face
+// weights (FP32 for the FP32 solve: no FP64 conversion in the loop).
+template <typename T, typename TW>
 __global__ void __launch_bounds__(128) k_cgc_solve(int64_t S, int K, int nx,
                                                    const Cplx<T>* __restrict__ dinv,
                                                    const Cplx<T>* __restrict__ lu,
-                                                   const double* __restrict__ wT,
+                                                   const TW* __restrict__ wT,
                                                    Cplx<T>* __restrict__ p,
                                                    const int* __restrict__ active) {
+    constexpr int CH = 8;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= S * K) return;
     int64_t s = t / K;
     int k = (int)(t - s * K);
     if (!active[s]) return;
     const int64_t base = s * (int64_t)nx * K + k;
-    const double* w = wT + s * (nx + 1);
+    const TW* w = wT + s * (nx + 1);
     T wr = 0, wi = 0;
-    for (int i = 0; i < nx; ++i) {
-        const int64_t o = base + (int64_t)i * K;
-        Cplx<T> pi = p[o], d = dinv[o];
-        T wl = (T)w[i];
-        T ar = pi.x + wl * wr, ai = pi.y + wl * wi;
-        wr = d.x * ar - d.y * ai;
-        wi = d.x * ai + d.y * ar;
-        p[o] = Cplx<T>{wr, wi};
+    for (int i0 = 0; i0 < nx; i0 += CH) {
+        Cplx<T> pc[CH], dc[CH];
+        T wc[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = i0 + c;
+            if (i < nx) {
+                const int64_t o = base + (int64_t)i * K;
+                pc[c] = p[o];
+                dc[c] = dinv[o];
+                wc[c] = (T)w[i];
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = i0 + c;
+            if (i < nx) {
+                const T ar = pc[c].x + wc[c] * wr, ai = pc[c].y + wc[c] * wi;
+                wr = dc[c].x * ar - dc[c].y * ai;
+                wi = dc[c].x * ai + dc[c].y * ar;
+                p[base + (int64_t)i * K] = Cplx<T>{wr, wi};
+            }
+        }
     }
     T qr = 0, qi = 0;
-    for (int i = nx - 1; i >= 0; --i) {
-        const int64_t o = base + (int64_t)i * K;
-        Cplx<T> wv = p[o], u = lu[o];
-        T nr = wv.x - (u.x * qr - u.y * qi);
-        T ni = wv.y - (u.x * qi + u.y * qr);
-        qr = nr;
-        qi = ni;
-        p[o] = Cplx<T>{qr, qi};
+    const int last0 = ((nx - 1) / CH) * CH;
+    for (int i0 = last0; i0 >= 0; i0 -= CH) {
+        Cplx<T> wc[CH], uc[CH];
+#pragma unroll
+        for (int c = 0; c < CH; ++c) {
+            const int i = i0 + c;
+            if (i < nx) {
+                const int64_t o = base + (int64_t)i * K;
+                wc[c] = p[o];
+                uc[c] = lu[o];
+            }
+        }
+#pragma unroll
+        for (int c = CH - 1; c >= 0; --c) {
+            const int i = i0 + c;
+            if (i < nx) {
+                const T nr = wc[c].x - (uc[c].x * qr - uc[c].y * qi);
+                const T ni = wc[c].y - (uc[c].x * qi + uc[c].y * qr);
+                qr = nr;
+                qi = ni;
+                p[base + (int64_t)i * K] = Cplx<T>{qr, qi};
+            }
+        }
     }
 }
 
-template <typename T>
+template <typename T, typename TW>
 void launch_cgc_solve(int64_t S, int K, int nx, const Cplx<T>* dinv, const Cplx<T>* lu,
-                      const double* wT, Cplx<T>* p, const int* active, cudaStream_t st) {
+                      const TW* wT, Cplx<T>* p, const int* active, cudaStream_t st) {
     int64_t n = S * K;
     if (n == 0) return;
-    k_cgc_solve<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(S, K, nx, dinv, lu, wT, p,
-                                                                 active);
+    k_cgc_solve<T, TW><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(S, K, nx, dinv, lu, wT, p,
+                                                                     active);
 }
-template void launch_cgc_solve<double>(int64_t, int, int, const Cplx<double>*,
-                                       const Cplx<double>*, const double*, Cplx<double>*,
-                                       const int*, cudaStream_t);
-template void launch_cgc_solve<float>(int64_t, int, int, const Cplx<float>*, const Cplx<float>*,
-                                      const double*, Cplx<float>*, const int*, cudaStream_t);
+template void launch_cgc_solve<double, double>(int64_t, int, int, const Cplx<double>*,
+                                               const Cplx<double>*, const double*, Cplx<double>*,
+                                               const int*, cudaStream_t);
+template void launch_cgc_solve<float, float>(int64_t, int, int, const Cplx<float>*,
+                                             const Cplx<float>*, const float*, Cplx<float>*,
+                                             const int*, cudaStream_t);
 
 __device__ __forceinline__ unsigned long long abs_bits(double v) {
     return (unsigned long long)__double_as_longlong(fabs(v));
@@ -503,12 +576,12 @@ template void launch_cgc_inverse<float>(int64_t, int, int, const Cplx<float>*, c
 // (c) + update for the defect path: U (pairs) += u, c32 = u, delta = max|u|.
 template <int N>
 __global__ void __launch_bounds__(kTX) k_cgc_inverse_df(int64_t S, int nx,
-                                                        const Cplx<float>* __restrict__ q,
-                                                        const float* __restrict__ iscale,
-                                                        float2* __restrict__ Udf,
-                                                        unsigned long long* __restrict__ delta,
-                                                        float* __restrict__ c32,
-                                                        const int* __restrict__ active) {
+                                                         const Cplx<float>* __restrict__ q,
+                                                         const float* __restrict__ iscale,
+                                                         float2* __restrict__ Udf,
+                                                         unsigned long long* __restrict__ delta,
+                                                         float* __restrict__ c32,
+                                                         const int* __restrict__ active) {
     constexpr int L = N / 2, K = N / 2 + 1;
     __shared__ Cplx<float> sq[kTX * K];
     __shared__ float2 su[kTX][N + 1];
@@ -521,9 +594,14 @@ __global__ void __launch_bounds__(kTX) k_cgc_inverse_df(int64_t S, int nx,
     const Cplx<float>* qin = q + (s * nx + x0) * (int64_t)K;
     for (int e = tid; e < rows * K; e += kTX) sq[e] = qin[e];
     float2* Ut = Udf + (s * nx + x0) * (int64_t)N;
-    for (int e = tid; e < rows * N; e += kTX) {
-        const int row = e / N, col = e - row * N;
-        su[row][col] = Ut[e];
+    if constexpr (N % 2 == 0 && N >= 2) {
+        constexpr int G = N / 2;
+        for (int e = tid; e < rows * G; e += kTX) {
+            const int row = e / G, c = (e - row * G) * 2;
+            const float4 v = *reinterpret_cast<const float4*>(Ut + (int64_t)row * N + c);
+            su[row][c] = make_float2(v.x, v.y);
+            su[row][c + 1] = make_float2(v.z, v.w);
+        }
     }
     __syncthreads();
     float umax = 0.f;
@@ -560,16 +638,20 @@ __global__ void __launch_bounds__(kTX) k_cgc_inverse_df(int64_t S, int nx,
     }
     __syncthreads();
     float* ct = c32 + (s * nx + x0) * (int64_t)N;
-    for (int e = tid; e < rows * N; e += kTX) {
-        const int row = e / N, col = e - row * N;
-        Ut[e] = su[row][col];
-        ct[e] = sc[row][col];
+    {
+        constexpr int G = N / 2;
+        for (int e = tid; e < rows * G; e += kTX) {
+            const int row = e / G, c = (e - row * G) * 2;
+            const float2 a = su[row][c], b = su[row][c + 1];
+            *reinterpret_cast<float4*>(Ut + (int64_t)row * N + c) = make_float4(a.x, a.y, b.x, b.y);
+            *reinterpret_cast<float2*>(ct + (int64_t)row * N + c) = make_float2(sc[row][c], sc[row][c + 1]);
+        }
     }
     // a NaN increment must reach the stopping rule (fmaxf drops NaNs)
     unsigned long long dmax = bad ? 0x7ff8000000000000ull : abs_bits((double)umax);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
-    if (tid == 0 && dmax) atomicMax(delta + s, dmax);
+    if ((tid & 31) == 0 && dmax) atomicMax(delta + s, dmax);
 }
 
 void launch_cgc_inverse_df(int64_t S, int N, int nx, const Cplx<float>* q, const float* iscale,

@@ -131,6 +131,53 @@ template void launch_cgc_factors<float>(const double*, int64_t, int, double, dou
                                         const double2*, int, Cplx<float>*, Cplx<float>*,
                                         cudaStream_t);
 
+// FP32 variant for the defect path, whose CGC is an FP32 approximate inverse.
+// With lambda' = lambda_k + dT c and w_i = dT a_{i-1/2}/h^2, the pivots are
+// written piv_i = w_{i+1} + sigma_i with
+//     sigma_0 = lambda' + w_0,  sigma_i = lambda' + w_i sigma_{i-1} / (w_i + sigma_{i-1}),
+// which is the same recurrence as piv_i = delta_i - w_i^2/piv_{i-1} but free of
+// cancellation: the small part sigma, which carries the smooth modes, never
+// emerges from differences of O(w) numbers, so FP32 keeps it accurate.
+__global__ void k_cgc_factors32(const float* __restrict__ wT32, int64_t S, int nx, float dTreact,
+                                const float2* __restrict__ lam, int K,
+                                Cplx<float>* __restrict__ dinv, Cplx<float>* __restrict__ lu) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= S * K) return;
+    int64_t s = t / K;
+    int k = (int)(t - s * K);
+    const float* ws = wT32 + s * (nx + 1);
+    const float2 lk = lam[k];
+    const float lr = lk.x + dTreact, li = lk.y;
+    float sr = lr + ws[0], si = li;  // sigma_0
+    for (int i = 0; i < nx; ++i) {
+        const float wr = ws[i + 1];
+        if (i > 0) {
+            // sigma_i = lambda' + w_i sigma / (w_i + sigma)
+            const float wl = ws[i];
+            const float br = wl + sr, bi = si;
+            const float inv = 1.f / (br * br + bi * bi);
+            const float qr = (sr * br + si * bi) * inv, qi = (si * br - sr * bi) * inv;
+            sr = lr + wl * qr;
+            si = li + wl * qi;
+        }
+        const float pr = wr + sr, pi = si;  // piv_i = w_{i+1} + sigma_i
+        const float den = pr * pr + pi * pi;
+        const float ir = pr / den, ii = -pi / den;
+        const int64_t o = (s * nx + i) * K + k;
+        dinv[o] = Cplx<float>{ir, ii};
+        lu[o] = (i + 1 < nx) ? Cplx<float>{-wr * ir, -wr * ii} : Cplx<float>{0.f, 0.f};
+    }
+}
+
+void launch_cgc_factors32(const float* wT32, int64_t S, int nx, double dTreact,
+                          const float2* lam, int K, Cplx<float>* dinv, Cplx<float>* lu,
+                          cudaStream_t st) {
+    int64_t n = S * K;
+    if (n == 0) return;
+    k_cgc_factors32<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(wT32, S, nx, (float)dTreact, lam,
+                                                                  K, dinv, lu);
+}
+
 __global__ void k_nonfinite(const double* __restrict__ x, int64_t n, int* flag) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool bad = false;

@@ -33,18 +33,27 @@
 
 namespace klecgc {
 
-// Per-sample factor table, [S][R][32]: A = {G_j, wd_j, l_j, 0}, D = {F_j, dinv_j, u_j, 0}
-// for row i = lane * R + j.  wd_j = dt a_{i-1/2} / h^2 (face left of row i).
+// Per-sample factor table, four arrays of [S][R][32] entries (row i = lane*R + j
+// at index j*32 + lane):  GW = {G_j, wd_j} and L = l_j for the ascending pass,
+// FD = {F_j, dinv_j} and U = u_j for the descending pass.  wd_j = dt a_{i-1/2}/h^2.
+struct Table32 {
+    float2* GW;
+    float* L;
+    float2* FD;
+    float* U;
+};
+
 __global__ void k_fine_table32(const double* __restrict__ a, int64_t S, int nx, int R,
-                               double inv_h2, double dt, double react, float4* __restrict__ tabA,
-                               float4* __restrict__ tabD) {
+                               double inv_h2, double dt, double react, Table32 tb) {
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (s >= S) return;
     const int Rt = 32 * R;
     const double* as = a + s * (nx + 1);
-    float4* A = tabA + s * (int64_t)Rt;
-    float4* D = tabD + s * (int64_t)Rt;
-    // pass 1: l, dinv, u, wd by row (layout [j][lane])
+    float2* GW = tb.GW + s * (int64_t)Rt;
+    float* L = tb.L + s * (int64_t)Rt;
+    float2* FD = tb.FD + s * (int64_t)Rt;
+    float* Uu = tb.U + s * (int64_t)Rt;
+    // pass 1: l, dinv, u, wd by row
     double piv = 1.0;
     for (int i = 0; i < Rt; ++i) {
         const int lane = i / R, j = i - lane * R;
@@ -62,21 +71,23 @@ __global__ void k_fine_table32(const double* __restrict__ a, int64_t S, int nx, 
             dinv = 1.0 / piv;
             u = (i + 1 < nx) ? -wr * dinv : 0.0;
         }
-        A[o] = make_float4(0.f, (float)wl, (float)l, 0.f);
-        D[o] = make_float4(0.f, (float)dinv, (float)u, 0.f);
+        GW[o] = make_float2(0.f, (float)wl);
+        L[o] = (float)l;
+        FD[o] = make_float2(0.f, (float)dinv);
+        Uu[o] = (float)u;
     }
-    // pass 2: within-lane products F (forward) and G (backward), in FP64
+    // pass 2: within-lane products of the FP32-rounded multipliers (they must
+    // match the local sweeps): F forward, G backward, formed in FP64
     for (int lane = 0; lane < 32; ++lane) {
-        // products of the FP32-rounded multipliers: they must match the local sweeps
         double F = 1.0;
         for (int j = 0; j < R; ++j) {
-            F *= -(double)A[j * 32 + lane].z;
-            D[j * 32 + lane].x = (float)F;
+            F *= -(double)L[j * 32 + lane];
+            FD[j * 32 + lane].x = (float)F;
         }
         double G = 1.0;
         for (int j = R - 1; j >= 0; --j) {
-            G *= -(double)D[j * 32 + lane].z;
-            A[j * 32 + lane].x = (float)G;
+            G *= -(double)Uu[j * 32 + lane];
+            GW[j * 32 + lane].x = (float)G;
         }
     }
 }
@@ -85,22 +96,25 @@ template <int R, int QS, bool REACT>
 __global__ void __launch_bounds__(128) k_fine32(
     int64_t S, int N, int nx, int J, int cps, float dt_react, float dt_f, int in_mode,
     const double* __restrict__ U64, const float2* __restrict__ Udf, const double* __restrict__ u0,
-    const float* __restrict__ c32, const float4* __restrict__ tabA, const float4* __restrict__ tabD,
-    float* __restrict__ fout, const int* __restrict__ active) {
-    extern __shared__ float4 smem[];
-    float4* sA = smem;
-    float4* sD = smem + R * 32;
+    const float* __restrict__ c32, Table32 tb, float* __restrict__ fout,
+    const int* __restrict__ active) {
+    extern __shared__ float2 smem2[];
+    float2* sGW = smem2;                 // [R][32] {G, wd}
+    float2* sFD = smem2 + R * 32;        // [R][32] {F, dinv}
+    float* sL = reinterpret_cast<float*>(smem2 + 2 * R * 32);
+    float* sU = sL + R * 32;
     const int64_t s = blockIdx.x / cps;
     const int part = blockIdx.x - (int)(s * cps);
     if (!active[s]) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = (part * (blockDim.x >> 5) + warp) * QS;
     {
-        const float4* gA = tabA + s * (int64_t)(R * 32);
-        const float4* gD = tabD + s * (int64_t)(R * 32);
+        const int64_t off = s * (int64_t)(R * 32);
         for (int e = threadIdx.x; e < R * 32; e += blockDim.x) {
-            sA[e] = gA[e];
-            sD[e] = gD[e];
+            sGW[e] = tb.GW[off + e];
+            sFD[e] = tb.FD[off + e];
+            sL[e] = tb.L[off + e];
+            sU[e] = tb.U[off + e];
         }
     }
     __syncthreads();
@@ -110,8 +124,8 @@ __global__ void __launch_bounds__(128) k_fine32(
     // data-independent scan multipliers
     float cf[5], cb[5];
     {
-        float af = sD[(R - 1) * 32 + lane].x;  // F_{R-1}: product over the lane's rows
-        float ab = sA[lane].x;                 // G_0
+        float af = sFD[(R - 1) * 32 + lane].x;  // F_{R-1}: product over the lane's rows
+        float ab = sGW[lane].x;                 // G_0
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             const int d = 1 << k;
@@ -123,8 +137,8 @@ __global__ void __launch_bounds__(128) k_fine32(
             if (lane + d <= 31) ab *= pb;
         }
     }
-    float gprev = __shfl_up_sync(FULL, sA[(R - 1) * 32 + lane].x, 1);   // G_{R-1} of lane-1
-    float wd_right = __shfl_down_sync(FULL, sA[lane].y, 1);             // face right of row R-1
+    float gprev = __shfl_up_sync(FULL, sGW[(R - 1) * 32 + lane].x, 1);   // G_{R-1} of lane-1
+    float wd_right = __shfl_down_sync(FULL, sGW[lane].y, 1);             // face right of row R-1
     if (lane == 0) gprev = 0.f;
     if (lane == 31) wd_right = 0.f;
     const float src = in_mode == 0 ? dt_f : 0.f;
@@ -157,17 +171,17 @@ __global__ void __launch_bounds__(128) k_fine32(
         float vr = __shfl_down_sync(FULL, v[q][0], 1);
         if (lane == 0) vl = 0.f;
         if (lane == 31) vr = 0.f;
-        float fprev = sA[lane].y * (v[q][0] - vl);
+        float fprev = sGW[lane].y * (v[q][0] - vl);
         float yprev = 0.f;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-            const float4 ta = sA[j * 32 + lane];
-            const float wr = (j + 1 < R) ? sA[(j + 1) * 32 + lane].y : wd_right;
+            const float lj = sL[j * 32 + lane];
+            const float wr = (j + 1 < R) ? sGW[(j + 1) * 32 + lane].y : wd_right;
             const float vn = (j + 1 < R) ? v[q][j + 1] : vr;
             const float f = wr * (vn - v[q][j]);
             float rhs = f - fprev;
             if (REACT) rhs += src - dt_react * v[q][j];
-            yprev = fmaf(-ta.z, yprev, rhs);
+            yprev = fmaf(-lj, yprev, rhs);
             w[q][j] = yprev;
             fprev = f;
         }
@@ -190,11 +204,12 @@ __global__ void __launch_bounds__(128) k_fine32(
         for (int q = 0; q < QS; ++q) xn[q] = 0.f;
 #pragma unroll
         for (int j = R - 1; j >= 0; --j) {
-            const float4 td = sD[j * 32 + lane];
+            const float2 fd = sFD[j * 32 + lane];
+            const float uj = sU[j * 32 + lane];
 #pragma unroll
             for (int q = 0; q < QS; ++q) {
-                float y = fmaf(td.x, yin[q], w[q][j]);
-                float xh = fmaf(-td.z, xn[q], y * td.y);
+                float y = fmaf(fd.x, yin[q], w[q][j]);
+                float xh = fmaf(-uj, xn[q], y * fd.y);
                 w[q][j] = xh;
                 xn[q] = xh;
             }
@@ -221,7 +236,7 @@ __global__ void __launch_bounds__(128) k_fine32(
             float fprev = 0.f, yprev = 0.f, lprev = 0.f;
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                const float4 ta = sA[j * 32 + lane];
+                const float2 gw = sGW[j * 32 + lane];
                 // The two rows next to a lane boundary must see bitwise-equal
                 // values there, or the flux through that face differs between
                 // them and the flux form stops being conservative.  The
@@ -230,11 +245,11 @@ __global__ void __launch_bounds__(128) k_fine32(
                 if (j == 0)
                     v[q][0] = v[q][0] + z[q];
                 else if (j == R - 1)
-                    v[q][R - 1] = fmaf(ta.x, zin[q], v[q][R - 1] + w[q][R - 1]);
+                    v[q][R - 1] = fmaf(gw.x, zin[q], v[q][R - 1] + w[q][R - 1]);
                 else
-                    v[q][j] += fmaf(ta.x, zin[q], w[q][j]);
+                    v[q][j] += fmaf(gw.x, zin[q], w[q][j]);
                 if (more) {
-                    const float f = ta.y * (v[q][j] - (j ? v[q][j - 1] : vl));
+                    const float f = gw.y * (v[q][j] - (j ? v[q][j - 1] : vl));
                     if (j) {
                         float rhs = f - fprev;
                         if (REACT) rhs += src - dt_react * v[q][j - 1];
@@ -242,7 +257,7 @@ __global__ void __launch_bounds__(128) k_fine32(
                         w[q][j - 1] = yprev;
                     }
                     fprev = f;
-                    lprev = ta.z;
+                    lprev = sL[j * 32 + lane];
                 }
             }
             if (more) {
@@ -277,22 +292,32 @@ int fine32_rows_per_lane(int nx) {
     return 0;
 }
 
+size_t fine_table32_bytes(int64_t S, int R) { return (size_t)S * R * 32 * 24; }
+
 void launch_fine_table32(const double* a, int64_t S, int nx, int R, double h, double dt,
-                         double react, float4* tabA, float4* tabD, cudaStream_t st) {
+                         double react, void* table, cudaStream_t st) {
     if (S == 0) return;
+    const int64_t n = S * (int64_t)R * 32;
+    char* p = static_cast<char*>(table);
+    Table32 tb{reinterpret_cast<float2*>(p), reinterpret_cast<float*>(p + 16 * n),
+               reinterpret_cast<float2*>(p + 8 * n), reinterpret_cast<float*>(p + 20 * n)};
     k_fine_table32<<<(unsigned)((S + 63) / 64), 64, 0, st>>>(a, S, nx, R, 1.0 / (h * h), dt, react,
-                                                             tabA, tabD);
+                                                             tb);
 }
 
 template <int R, int QS, bool REACT>
 static void launch_r(int64_t S, int N, int nx, int J, double dt, double react, double forcing,
                      int in_mode, const double* U64, const float2* Udf, const double* u0,
-                     const float* c32, const float4* tabA, const float4* tabD, float* fout,
-                     const int* active, cudaStream_t st) {
+                     const float* c32, const void* table, float* fout, const int* active,
+                     cudaStream_t st) {
     constexpr int warps = 4;
     const int per_cta = warps * QS;
     const int cps = (N + per_cta - 1) / per_cta;
-    const size_t smem = 2 * (size_t)R * 32 * sizeof(float4);
+    const size_t smem = (size_t)R * 32 * 24;
+    const int64_t n = S * (int64_t)R * 32;
+    char* p = const_cast<char*>(static_cast<const char*>(table));
+    Table32 tb{reinterpret_cast<float2*>(p), reinterpret_cast<float*>(p + 16 * n),
+               reinterpret_cast<float2*>(p + 8 * n), reinterpret_cast<float*>(p + 20 * n)};
     static bool attr = false;
     if (!attr && smem > 48 * 1024) {
         cudaFuncSetAttribute(k_fine32<R, QS, REACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -301,33 +326,33 @@ static void launch_r(int64_t S, int N, int nx, int J, double dt, double react, d
     }
     k_fine32<R, QS, REACT><<<(unsigned)(S * cps), warps * 32, smem, st>>>(
         S, N, nx, J, cps, (float)(dt * react), (float)(dt * forcing), in_mode, U64, Udf, u0, c32,
-        tabA, tabD, fout, active);
+        tb, fout, active);
 }
 
 template <int R, int QS>
 static void launch_rr(int64_t S, int N, int nx, int J, double dt, double react, double forcing,
                       int in_mode, const double* U64, const float2* Udf, const double* u0,
-                      const float* c32, const float4* tabA, const float4* tabD, float* fout,
-                      const int* active, cudaStream_t st) {
+                      const float* c32, const void* table, float* fout, const int* active,
+                      cudaStream_t st) {
     const bool react_terms = react != 0.0 || (forcing != 0.0 && in_mode == 0);
     if (react_terms)
-        launch_r<R, QS, true>(S, N, nx, J, dt, react, forcing, in_mode, U64, Udf, u0, c32, tabA,
-                              tabD, fout, active, st);
+        launch_r<R, QS, true>(S, N, nx, J, dt, react, forcing, in_mode, U64, Udf, u0, c32, table,
+                              fout, active, st);
     else
-        launch_r<R, QS, false>(S, N, nx, J, dt, react, forcing, in_mode, U64, Udf, u0, c32, tabA,
-                               tabD, fout, active, st);
+        launch_r<R, QS, false>(S, N, nx, J, dt, react, forcing, in_mode, U64, Udf, u0, c32, table,
+                               fout, active, st);
 }
 
 void launch_fine32(int64_t S, int N, int nx, int J, double dt, double react, double forcing,
                    int in_mode, const double* U64, const float2* Udf, const double* u0,
-                   const float* c32, const float4* tabA, const float4* tabD, float* fout,
-                   const int* active, cudaStream_t st) {
+                   const float* c32, const void* table, float* fout, const int* active,
+                   cudaStream_t st) {
     if (S == 0) return;
     switch (fine32_rows_per_lane(nx)) {
 #define KLECGC_F32(RR, QQ)                                                                   \
     case RR:                                                                                 \
-        launch_rr<RR, QQ>(S, N, nx, J, dt, react, forcing, in_mode, U64, Udf, u0, c32, tabA, \
-                          tabD, fout, active, st);                                           \
+        launch_rr<RR, QQ>(S, N, nx, J, dt, react, forcing, in_mode, U64, Udf, u0, c32, table, \
+                          fout, active, st);                                                  \
         break;
         KLECGC_F32(2, 2)
         KLECGC_F32(4, 2)
