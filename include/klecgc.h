@@ -70,7 +70,9 @@ enum {
     KLECGC_GUESS_GPC = 0,   /* KL + gPC surrogate (Algorithm 3, step 6) */
     KLECGC_GUESS_ZERO = 1,  /* U^0 = 0 */
     KLECGC_GUESS_USER = 2,  /* U^0 given by the caller in U_guess */
-    KLECGC_GUESS_COARSE = 3 /* U^0_n = G(U^0_{n-1}), U^0_0 = u0 (Section 3.1) */
+    KLECGC_GUESS_COARSE = 3, /* U^0_n = G(U^0_{n-1}), U^0_0 = u0 (Section 3.1) */
+    KLECGC_GUESS_MLP = 4     /* learned network (klecgc_mlp_*); the gPC surrogate is its
+                                fallback when an output is not finite */
 };
 
 typedef struct {
@@ -214,6 +216,58 @@ klecgc_status klecgc_reference(klecgc_ctx* ctx, const double* xi, int64_t S, int
  */
 klecgc_status klecgc_reference_noalloc(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t N,
                                        int32_t J, double* U_out, void* stream);
+
+/*
+ * Learned initial guess.  The paper's guess is the KL/gPC surrogate
+ * (Algorithm 3, step 6); these entry points add a learned one with the same
+ * role: an MLP M -> 256 -> 256 -> 256 -> 64 N (ReLU hidden layers) maps xi to
+ * the state at the N coarse times sampled at x_m = (m+1)/65, m = 0..63,
+ * normalized per output column ((y - mean) / std); the guess is its output
+ * de-normalized and linearly interpolated (zero boundary values) to the grid.
+ * Parameters: one flat FP32 vector [W1, b1, W2, b2, W3, b3, W4, b4], W_l
+ * stored [out][in].  GEMMs use BF16 operands with FP32 accumulation; master
+ * weights, Adam moments, activations before the BF16 rounding and the loss
+ * are FP32.
+ */
+
+/* Sets the parameters (n_params floats, host or device) and the output
+ * normalization (out_mean/out_std: 64 N floats each; NULL = 0 and 1).
+ * INVALID_ARG if n_params does not match the architecture or std <= 0. */
+klecgc_status klecgc_mlp_set(klecgc_ctx* ctx, const float* params, int64_t n_params,
+                             const float* out_mean, const float* out_std);
+
+/* Copies the parameters and normalization out (each may be NULL); *n_params
+ * receives the parameter count (also when no network is set). */
+klecgc_status klecgc_mlp_get(const klecgc_ctx* ctx, float* params, float* out_mean,
+                             float* out_std, int64_t* n_params);
+
+/* Mean squared error over B samples of the normalized targets
+ * (targets: [B][N][64] raw FP32, normalized with the context's mean/std)
+ * and its gradient w.r.t. the parameters (grad_out: n_params FP32, host or
+ * device; may be NULL). */
+klecgc_status klecgc_mlp_loss_grad(klecgc_ctx* ctx, const double* xi, const float* targets,
+                                   int64_t B, double* loss_out, float* grad_out, void* stream);
+
+/* Trains from the current parameters with Adam (beta 0.9/0.999, eps 1e-8),
+ * mini-batches of `batch` rows of a permutation drawn per epoch from `seed`
+ * (xorshift64*), learning rate cosine-annealed from lr to lr_final over all
+ * steps.  fit_norm != 0 first sets the output normalization to the
+ * per-column mean and std of the targets.  xi: [n][M] FP64, targets:
+ * [n][N][64] FP32 (host or device).  epoch_loss (host, may be NULL)
+ * receives the mean loss of each epoch.  NONFINITE if the loss diverges. */
+klecgc_status klecgc_mlp_train(klecgc_ctx* ctx, const double* xi, const float* targets, int64_t n,
+                               int32_t epochs, int32_t batch, double lr, double lr_final,
+                               uint64_t seed, int32_t fit_norm, float* epoch_loss, void* stream);
+
+/* Learned guess U0_out [S][N][nx] FP64 for S samples (NONFINITE if an output
+ * is not finite; the solve then uses the gPC surrogate instead). */
+klecgc_status klecgc_mlp_guess(klecgc_ctx* ctx, const double* xi, int64_t S, double* U0_out,
+                               void* stream);
+
+/* Samples a batch U [S][N][nx] (FP64) at the 64 network points:
+ * T_out [S][N][64] FP32, linear interpolation with zero boundary values. */
+klecgc_status klecgc_downsample(klecgc_ctx* ctx, const double* U, int64_t S, int32_t N,
+                                float* T_out, void* stream);
 
 /* Sizes of the context (M_Q, P, ...). */
 klecgc_status klecgc_info(const klecgc_ctx* ctx, klecgc_info_t* out);

@@ -6,11 +6,11 @@ by the binding on first use) fails loudly when the compiled library is
 missing.
 """
 from .klecgc import (FP64, MIXED, MIXED_DEFECT, GUESS_GPC, GUESS_ZERO, GUESS_USER,
-                     GUESS_COARSE, OK, E_INVALID_ARG, E_OUT_OF_MEMORY, E_NOT_CONVERGED,
+                     GUESS_COARSE, GUESS_MLP, OK, E_INVALID_ARG, E_OUT_OF_MEMORY, E_NOT_CONVERGED,
                      E_NONFINITE, E_CUDA, E_UNSUPPORTED, KlecgcError, Problem, Solver, load,
                      exported_symbols)
 
 __all__ = ["FP64", "MIXED", "MIXED_DEFECT", "GUESS_GPC", "GUESS_ZERO", "GUESS_USER",
-           "GUESS_COARSE", "OK", "E_INVALID_ARG", "E_OUT_OF_MEMORY", "E_NOT_CONVERGED",
+           "GUESS_COARSE", "GUESS_MLP", "OK", "E_INVALID_ARG", "E_OUT_OF_MEMORY", "E_NOT_CONVERGED",
            "E_NONFINITE", "E_CUDA", "E_UNSUPPORTED", "KlecgcError", "Problem", "Solver", "load",
            "exported_symbols"]

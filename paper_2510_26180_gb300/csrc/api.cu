@@ -36,6 +36,25 @@ static cudaError_t ensure_twiddles(int dev) {
     return cudaSuccess;
 }
 
+// Learned-guess network M -> W -> W -> W -> D (D = 64 N), flat FP32 parameters
+// [W1, b1, W2, b2, W3, b3, W4, b4] with W_l stored [out][in].
+struct MlpState {
+    int sizes[5] = {0, 0, 0, 0, 0};
+    int64_t woff[4] = {0, 0, 0, 0}, boff[4] = {0, 0, 0, 0};
+    int64_t P = 0;
+    int D = 0;
+    float* theta = nullptr;      // FP32 master parameters
+    __nv_bfloat16* thb = nullptr;  // BF16 copy (GEMM operands)
+    float* m = nullptr;
+    float* v = nullptr;
+    float* grad = nullptr;
+    float* mean = nullptr;       // [D] output normalization
+    float* stdv = nullptr;
+    float* inv_std = nullptr;
+    int adam_t = 0;
+    bool ready = false;
+};
+
 }  // namespace klecgc
 
 using namespace klecgc;
@@ -55,6 +74,7 @@ struct klecgc_ctx {
     float* W32 = nullptr;      // FP32 copy of W
     std::map<std::string, DevBuf> ws;  // grow-only scratch
     std::vector<void*> owned;
+    MlpState mlp;
     // profile: launch counters and optional CUDA-event timing per kernel class
     bool prof_timing = false;
     int64_t prof_launches[KLECGC_K_COUNT] = {};
@@ -314,6 +334,154 @@ klecgc_status gpc_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S,
     }
     TRY(cudaGetLastError());
     return KLECGC_OK;
+}
+
+// ---------------------------------------------------------------- learned guess
+klecgc_status mlp_alloc(klecgc_ctx* ctx) {
+    MlpState& q = ctx->mlp;
+    if (q.theta) return KLECGC_OK;
+    const int W = 256;
+    q.sizes[0] = ctx->M;
+    q.sizes[1] = q.sizes[2] = q.sizes[3] = W;
+    q.sizes[4] = 64 * ctx->N;
+    q.D = q.sizes[4];
+    int64_t k = 0;
+    for (int l = 0; l < 4; ++l) {
+        q.woff[l] = k;
+        k += (int64_t)q.sizes[l + 1] * q.sizes[l];
+        q.boff[l] = k;
+        k += q.sizes[l + 1];
+    }
+    q.P = k;
+    TRY(ctx->alloc_owned(&q.theta, q.P));
+    TRY(ctx->alloc_owned(&q.thb, q.P));
+    TRY(ctx->alloc_owned(&q.m, q.P));
+    TRY(ctx->alloc_owned(&q.v, q.P));
+    TRY(ctx->alloc_owned(&q.grad, q.P));
+    TRY(ctx->alloc_owned(&q.mean, q.D));
+    TRY(ctx->alloc_owned(&q.stdv, q.D));
+    TRY(ctx->alloc_owned(&q.inv_std, q.D));
+    std::vector<float> zero(q.D, 0.f), one(q.D, 1.f);
+    TRY(cudaMemcpy(q.mean, zero.data(), q.D * 4, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(q.stdv, one.data(), q.D * 4, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(q.inv_std, one.data(), q.D * 4, cudaMemcpyHostToDevice));
+    TRY(cudaMemset(q.theta, 0, q.P * 4));
+    TRY(cudaMemset(q.thb, 0, q.P * 2));
+    return KLECGC_OK;
+}
+
+struct MlpBuffers {
+    float* Z[3];
+    __nv_bfloat16* A[3];
+    float* dZ[2];
+    __nv_bfloat16* dZb[2];
+};
+
+klecgc_status mlp_buffers(klecgc_ctx* ctx, int B, MlpBuffers* b) {
+    const int W = ctx->mlp.sizes[1];
+    const char* zn[3] = {"mlp_Z0", "mlp_Z1", "mlp_Z2"};
+    const char* an[3] = {"mlp_A0", "mlp_A1", "mlp_A2"};
+    for (int l = 0; l < 3; ++l) {
+        WS(float, z, zn[l], (size_t)B * W);
+        WS(__nv_bfloat16, a, an[l], (size_t)B * W);
+        b->Z[l] = z;
+        b->A[l] = a;
+    }
+    WS(float, d0, "mlp_dZ0", (size_t)B * W);
+    WS(float, d1, "mlp_dZ1", (size_t)B * W);
+    WS(__nv_bfloat16, e0, "mlp_dZb0", (size_t)B * W);
+    WS(__nv_bfloat16, e1, "mlp_dZb1", (size_t)B * W);
+    b->dZ[0] = d0;
+    b->dZ[1] = d1;
+    b->dZb[0] = e0;
+    b->dZb[1] = e1;
+    return KLECGC_OK;
+}
+
+// Y = net(X), X BF16 [B][M]; hidden pre-activations and activations kept in b.
+void mlp_forward(klecgc_ctx* ctx, int B, const __nv_bfloat16* X, const MlpBuffers& b, float* Y,
+                 cudaStream_t st) {
+    MlpState& q = ctx->mlp;
+    const __nv_bfloat16* in = X;
+    int kin = q.sizes[0];
+    for (int l = 0; l < 4; ++l) {
+        const int out = q.sizes[l + 1];
+        const __nv_bfloat16* W = q.thb + q.woff[l];
+        const float* bias = q.theta + q.boff[l];
+        if (l < 3) {
+            ctx->launch(KLECGC_K_GUESS, st, [&] {
+                launch_gemm_bf16(false, true, B, out, kin, in, kin, W, kin, bias, nullptr, 0,
+                                 b.Z[l], out, b.A[l], out, true, st);
+            });
+            in = b.A[l];
+            kin = out;
+        } else {
+            ctx->launch(KLECGC_K_GUESS, st, [&] {
+                launch_gemm_bf16(false, true, B, out, kin, in, kin, W, kin, bias, nullptr, 0, Y,
+                                 out, nullptr, 0, false, st);
+            });
+        }
+    }
+}
+
+// Gradient of the loss w.r.t. all parameters into q.grad, from dY (FP32 and BF16).
+void mlp_backward(klecgc_ctx* ctx, int B, const __nv_bfloat16* X, const MlpBuffers& b,
+                  const float* dY, const __nv_bfloat16* dYb, cudaStream_t st) {
+    MlpState& q = ctx->mlp;
+    const float* dZf = dY;
+    const __nv_bfloat16* dZb = dYb;
+    for (int l = 3; l >= 0; --l) {
+        const int out = q.sizes[l + 1], kin = q.sizes[l];
+        const __nv_bfloat16* Ain = l == 0 ? X : b.A[l - 1];
+        ctx->launch(KLECGC_K_GUESS, st, [&] {
+            launch_gemm_bf16(true, false, out, kin, B, dZb, out, Ain, kin, nullptr, nullptr, 0,
+                             q.grad + q.woff[l], kin, nullptr, 0, false, st);
+        });
+        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_colsum(B, out, dZf, q.grad + q.boff[l], st); });
+        if (l > 0) {
+            const int nb = l & 1;
+            ctx->launch(KLECGC_K_GUESS, st, [&] {
+                launch_gemm_bf16(false, false, B, kin, out, dZb, out, q.thb + q.woff[l], kin,
+                                 nullptr, b.Z[l - 1], kin, b.dZ[nb], kin, b.dZb[nb], kin, false,
+                                 st);
+            });
+            dZf = b.dZ[nb];
+            dZb = b.dZb[nb];
+        }
+    }
+}
+
+// Learned guess of S samples into U (internal layout [S][nx][N]); *finite
+// reports whether every network output was finite.
+klecgc_status mlp_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S, double* U,
+                                 cudaStream_t st, bool* finite) {
+    MlpState& q = ctx->mlp;
+    const int B = (int)S;
+    MlpBuffers b;
+    klecgc_status s = mlp_buffers(ctx, B, &b);
+    if (s != KLECGC_OK) return s;
+    WS(__nv_bfloat16, X, "mlp_X", (size_t)B * q.sizes[0]);
+    WS(float, Y, "mlp_Y", (size_t)B * q.D);
+    ctx->launch(KLECGC_K_GUESS, st, [&] {
+        launch_mlp_gather(B, q.sizes[0], q.D, nullptr, 0, xi_d, nullptr, nullptr, nullptr, X,
+                          nullptr, st);
+    });
+    mlp_forward(ctx, B, X, b, Y, st);
+    ctx->launch(KLECGC_K_GUESS, st, [&] { launch_upsample(S, ctx->N, ctx->nx, Y, q.mean, q.stdv, U, st); });
+    WS(int, flag, "mlp_flag", 1);
+    TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
+    launch_nonfinite_f32((int64_t)B * q.D, Y, flag, st);
+    int h = 0;
+    TRY(cudaMemcpyAsync(&h, flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    *finite = h == 0;
+    return KLECGC_OK;
+}
+
+template <typename T>
+klecgc_status stage_any(klecgc_ctx* ctx, const T* user, size_t count, const char* name,
+                        cudaStream_t st, const T** out) {
+    return stage_in(ctx, user, count, name, st, out);
 }
 
 klecgc_status check_xi_finite(klecgc_ctx* ctx, const double* xi_d, int64_t n, cudaStream_t st,
@@ -647,6 +815,188 @@ klecgc_status klecgc_reference(klecgc_ctx* ctx, const double* xi, int64_t S, int
     return KLECGC_OK;
 }
 
+klecgc_status klecgc_mlp_set(klecgc_ctx* ctx, const float* params, int64_t n_params,
+                            const float* out_mean, const float* out_std) {
+    set_error("");
+    if (!ctx || !params) return fail(KLECGC_E_INVALID_ARG, "NULL argument");
+    klecgc_status s = mlp_alloc(ctx);
+    if (s != KLECGC_OK) return s;
+    MlpState& q = ctx->mlp;
+    if (n_params != q.P)
+        return fail(KLECGC_E_INVALID_ARG, "expected " + std::to_string(q.P) + " parameters");
+    TRY(cudaMemcpy(q.theta, params, q.P * 4, cudaMemcpyDefault));
+    launch_f32_to_bf16(q.P, q.theta, q.thb, 0);
+    std::vector<float> mu(q.D, 0.f), sd(q.D, 1.f);
+    if (out_mean) TRY(cudaMemcpy(mu.data(), out_mean, q.D * 4, cudaMemcpyDefault));
+    if (out_std) TRY(cudaMemcpy(sd.data(), out_std, q.D * 4, cudaMemcpyDefault));
+    std::vector<float> inv(q.D);
+    for (int c = 0; c < q.D; ++c) {
+        if (!(sd[c] > 0) || !std::isfinite(sd[c]) || !std::isfinite(mu[c]))
+            return fail(KLECGC_E_INVALID_ARG, "output normalization must be finite, std > 0");
+        inv[c] = 1.f / sd[c];
+    }
+    TRY(cudaMemcpy(q.mean, mu.data(), q.D * 4, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(q.stdv, sd.data(), q.D * 4, cudaMemcpyHostToDevice));
+    TRY(cudaMemcpy(q.inv_std, inv.data(), q.D * 4, cudaMemcpyHostToDevice));
+    TRY(cudaDeviceSynchronize());
+    q.ready = true;
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_mlp_get(const klecgc_ctx* ctx, float* params, float* out_mean,
+                            float* out_std, int64_t* n_params) {
+    set_error("");
+    if (!ctx) return fail(KLECGC_E_INVALID_ARG, "NULL context");
+    const MlpState& q = ctx->mlp;
+    if (n_params) *n_params = q.theta ? q.P : (int64_t)(ctx->M * 256 + 256 + 2 * (256 * 256 + 256) +
+                                                        256 * 64 * ctx->N + 64 * ctx->N);
+    if (!q.theta) return params || out_mean || out_std ? fail(KLECGC_E_INVALID_ARG, "no network") : KLECGC_OK;
+    if (params) TRY(cudaMemcpy(params, q.theta, q.P * 4, cudaMemcpyDefault));
+    if (out_mean) TRY(cudaMemcpy(out_mean, q.mean, q.D * 4, cudaMemcpyDefault));
+    if (out_std) TRY(cudaMemcpy(out_std, q.stdv, q.D * 4, cudaMemcpyDefault));
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_mlp_loss_grad(klecgc_ctx* ctx, const double* xi, const float* targets,
+                                   int64_t B, double* loss_out, float* grad_out, void* stream) {
+    set_error("");
+    if (!ctx || !xi || !targets || B < 1 || B > (1 << 20)) return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (!ctx->mlp.ready) return fail(KLECGC_E_INVALID_ARG, "set the network first (klecgc_mlp_set)");
+    cudaStream_t st = (cudaStream_t)stream;
+    MlpState& q = ctx->mlp;
+    const double* xi_d = nullptr;
+    const float* tg = nullptr;
+    klecgc_status s = stage_in(ctx, xi, (size_t)B * ctx->M, "mlp_xi", st, &xi_d);
+    if (s != KLECGC_OK) return s;
+    if ((s = stage_in(ctx, targets, (size_t)B * q.D, "mlp_targets", st, &tg)) != KLECGC_OK) return s;
+    MlpBuffers b;
+    if ((s = mlp_buffers(ctx, (int)B, &b)) != KLECGC_OK) return s;
+    WS(__nv_bfloat16, X, "mlp_X", (size_t)B * q.sizes[0]);
+    WS(float, T, "mlp_T", (size_t)B * q.D);
+    WS(float, Y, "mlp_Y", (size_t)B * q.D);
+    WS(float, dY, "mlp_dY", (size_t)B * q.D);
+    WS(__nv_bfloat16, dYb, "mlp_dYb", (size_t)B * q.D);
+    WS(float, lsum, "mlp_loss", 1);
+    TRY(cudaMemsetAsync(lsum, 0, sizeof(float), st));
+    launch_mlp_gather((int)B, q.sizes[0], q.D, nullptr, 0, xi_d, tg, q.mean, q.inv_std, X, T, st);
+    mlp_forward(ctx, (int)B, X, b, Y, st);
+    launch_mse(B * q.D, 1.f / (float)(B * q.D), 1.f / (float)(B * q.D), Y, T, dY, dYb, lsum, st);
+    mlp_backward(ctx, (int)B, X, b, dY, dYb, st);
+    TRY(cudaGetLastError());
+    float lh = 0.f;
+    TRY(cudaMemcpyAsync(&lh, lsum, sizeof(float), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    if (loss_out) *loss_out = lh;
+    if (grad_out) TRY(cudaMemcpy(grad_out, q.grad, q.P * 4, cudaMemcpyDefault));
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_mlp_train(klecgc_ctx* ctx, const double* xi, const float* targets, int64_t n,
+                               int32_t epochs, int32_t batch, double lr, double lr_final,
+                               uint64_t seed, int32_t fit_norm, float* epoch_loss, void* stream) {
+    set_error("");
+    if (!ctx || !xi || !targets || n < 1 || epochs < 1 || batch < 1 || batch > n || !(lr > 0) ||
+        !(lr_final >= 0))
+        return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (!ctx->mlp.ready) return fail(KLECGC_E_INVALID_ARG, "set the initial network first (klecgc_mlp_set)");
+    cudaStream_t st = (cudaStream_t)stream;
+    MlpState& q = ctx->mlp;
+    const double* xi_d = nullptr;
+    const float* tg = nullptr;
+    klecgc_status s = stage_in(ctx, xi, (size_t)n * ctx->M, "mlp_train_xi", st, &xi_d);
+    if (s != KLECGC_OK) return s;
+    if ((s = stage_in(ctx, targets, (size_t)n * q.D, "mlp_train_t", st, &tg)) != KLECGC_OK) return s;
+    if (fit_norm) launch_colstats(n, q.D, tg, q.mean, q.stdv, q.inv_std, st);
+    const int B = batch;
+    MlpBuffers b;
+    if ((s = mlp_buffers(ctx, B, &b)) != KLECGC_OK) return s;
+    WS(__nv_bfloat16, X, "mlp_X", (size_t)B * q.sizes[0]);
+    WS(float, T, "mlp_T", (size_t)B * q.D);
+    WS(float, Y, "mlp_Y", (size_t)B * q.D);
+    WS(float, dY, "mlp_dY", (size_t)B * q.D);
+    WS(__nv_bfloat16, dYb, "mlp_dYb", (size_t)B * q.D);
+    WS(float, lsum, "mlp_loss", 1);
+    WS(int, perm_d, "mlp_perm", (size_t)n);
+    TRY(cudaMemsetAsync(q.m, 0, q.P * 4, st));
+    TRY(cudaMemsetAsync(q.v, 0, q.P * 4, st));
+    q.adam_t = 0;
+    const int64_t nb = n / B;
+    const double total = (double)epochs * nb;
+    std::vector<int> perm(n);
+    uint64_t state = seed * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
+    auto next = [&]() {  // xorshift64*
+        state ^= state >> 12;
+        state ^= state << 25;
+        state ^= state >> 27;
+        return state * 0x2545F4914F6CDD1Dull;
+    };
+    for (int ep = 0; ep < epochs; ++ep) {
+        for (int64_t i = 0; i < n; ++i) perm[i] = (int)i;
+        for (int64_t i = n - 1; i > 0; --i) std::swap(perm[i], perm[next() % (uint64_t)(i + 1)]);
+        TRY(cudaMemcpyAsync(perm_d, perm.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+        TRY(cudaMemsetAsync(lsum, 0, sizeof(float), st));
+        for (int64_t bi = 0; bi < nb; ++bi) {
+            q.adam_t += 1;
+            const double frac = (q.adam_t - 1) / total;
+            const float lr_t = (float)(lr_final + 0.5 * (lr - lr_final) * (1.0 + std::cos(3.14159265358979 * frac)));
+            launch_mlp_gather(B, q.sizes[0], q.D, perm_d, (int)(bi * B), xi_d, tg, q.mean,
+                              q.inv_std, X, T, st);
+            mlp_forward(ctx, B, X, b, Y, st);
+            const float sc = 1.f / (float)((int64_t)B * q.D);
+            launch_mse((int64_t)B * q.D, sc, sc / (float)nb, Y, T, dY, dYb, lsum, st);
+            mlp_backward(ctx, B, X, b, dY, dYb, st);
+            launch_adam(q.P, lr_t, q.adam_t, q.theta, q.grad, q.m, q.v, q.thb, st);
+        }
+        TRY(cudaGetLastError());
+        float lh = 0.f;
+        TRY(cudaMemcpyAsync(&lh, lsum, sizeof(float), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (epoch_loss) epoch_loss[ep] = lh;
+        if (!std::isfinite(lh)) return fail(KLECGC_E_NONFINITE, "training loss is not finite");
+    }
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_mlp_guess(klecgc_ctx* ctx, const double* xi, int64_t S, double* U0_out,
+                               void* stream) {
+    set_error("");
+    if (!ctx || !xi || !U0_out || S < 0 || S > (1 << 20)) return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (!ctx->mlp.ready) return fail(KLECGC_E_INVALID_ARG, "no network (klecgc_mlp_set / klecgc_mlp_train)");
+    if (S == 0) return KLECGC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* xi_d = nullptr;
+    klecgc_status s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d);
+    if (s != KLECGC_OK) return s;
+    WS(double, U, "U", S * (int64_t)ctx->nx * ctx->N);
+    bool finite = true;
+    if ((s = mlp_guess_internal(ctx, xi_d, S, U, st, &finite)) != KLECGC_OK) return s;
+    if ((s = export_batch(ctx, U, S, ctx->N, U0_out, st)) != KLECGC_OK) return s;
+    TRY(cudaStreamSynchronize(st));
+    return finite ? KLECGC_OK : fail(KLECGC_E_NONFINITE, "network output is not finite");
+}
+
+klecgc_status klecgc_downsample(klecgc_ctx* ctx, const double* U, int64_t S, int32_t N,
+                                float* T_out, void* stream) {
+    set_error("");
+    if (!ctx || !U || !T_out || S < 0 || N < 1) return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (S == 0) return KLECGC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const double* Ud = nullptr;
+    klecgc_status s = stage_in(ctx, U, (size_t)S * N * ctx->nx, "ds_in", st, &Ud);
+    if (s != KLECGC_OK) return s;
+    float* T = T_out;
+    const bool dev = is_device_ptr(T_out);
+    if (!dev) {
+        WS(float, t, "ds_out", (size_t)S * N * 64);
+        T = t;
+    }
+    launch_downsample(S * (int64_t)N, ctx->nx, Ud, T, st);
+    TRY(cudaGetLastError());
+    if (!dev) TRY(cudaMemcpyAsync(T_out, T, (size_t)S * N * 64 * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    return KLECGC_OK;
+}
+
 klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t N,
                                 const double* U_in, double dT, int32_t J, double alpha,
                                 int32_t precision, double* r_out, void* stream) {
@@ -739,11 +1089,13 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
     if (!ctx) return fail(KLECGC_E_INVALID_ARG, "NULL context");
     if (S < 0 || (S > 0 && (!xi || !U_out))) return fail(KLECGC_E_INVALID_ARG, "bad array argument");
     if (J < 1 || !(alpha > 0 && alpha < 1) || !(tol > 0) || kmax < 1 || precision < 0 ||
-        precision > 2 || guess < 0 || guess > 3 || (guess == KLECGC_GUESS_USER && !U_guess && S > 0))
+        precision > 2 || guess < 0 || guess > 4 || (guess == KLECGC_GUESS_USER && !U_guess && S > 0))
         return fail(KLECGC_E_INVALID_ARG, "argument out of range");
     if (!pow2_in_range(N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
-    if (guess == KLECGC_GUESS_GPC && N != ctx->N)
-        return fail(KLECGC_E_INVALID_ARG, "the gPC guess needs the setup's N");
+    if ((guess == KLECGC_GUESS_GPC || guess == KLECGC_GUESS_MLP) && N != ctx->N)
+        return fail(KLECGC_E_INVALID_ARG, "the gPC and learned guesses need the setup's N");
+    if (guess == KLECGC_GUESS_MLP && !ctx->mlp.ready)
+        return fail(KLECGC_E_INVALID_ARG, "no network (klecgc_mlp_set / klecgc_mlp_train)");
     if (guess == KLECGC_GUESS_COARSE) return fail(KLECGC_E_UNSUPPORTED, "coarse guess not built");
     klecgc_status s = check_dT(ctx, N, dT);
     if (s != KLECGC_OK) return s;
@@ -772,8 +1124,14 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
         return s;
 
     WS(double, U, "U", NS);
-    if (guess == KLECGC_GUESS_GPC) {
+    bool mlp_ok = false;
+    if (guess == KLECGC_GUESS_MLP) {
+        if ((s = mlp_guess_internal(ctx, xi_d, S, U, st, &mlp_ok)) != KLECGC_OK) return s;
+    }
+    if (guess == KLECGC_GUESS_GPC || (guess == KLECGC_GUESS_MLP && !mlp_ok)) {
+        // the surrogate is also the fallback of the learned guess (non-finite output)
         if ((s = gpc_guess_internal(ctx, xi_d, S, f64, U, st)) != KLECGC_OK) return s;
+    } else if (guess == KLECGC_GUESS_MLP) {
     } else if (guess == KLECGC_GUESS_ZERO) {
         TRY(cudaMemsetAsync(U, 0, NS * sizeof(double), st));
     } else {

@@ -153,6 +153,30 @@ void launch_convergence(int64_t S, int iter, int kmax, double tol, unsigned long
 // [S][A][B] -> [S][B][A] (FP64).
 void launch_transpose(const double* in, double* out, int64_t S, int A, int B, cudaStream_t st);
 
+// ---- k_mlp.cu ----
+}  // namespace klecgc
+#include <cuda_bf16.h>
+namespace klecgc {
+void launch_gemm_bf16(bool ta, bool tb, int M, int N, int K, const __nv_bfloat16* A, int lda,
+                      const __nv_bfloat16* B, int ldb, const float* bias, const float* zmask,
+                      int ldz, float* C, int ldc, __nv_bfloat16* Cb, int ldcb, bool relu,
+                      cudaStream_t st);
+void launch_mlp_gather(int B, int M, int D, const int* perm, int b0, const double* xi,
+                       const float* targ, const float* mean, const float* inv_std,
+                       __nv_bfloat16* X, float* T, cudaStream_t st);
+void launch_mse(int64_t n, float gscale, float lscale, const float* Y, const float* T, float* dY,
+                __nv_bfloat16* dYb, float* loss, cudaStream_t st);
+void launch_colsum(int B, int D, const float* dZ, float* db, cudaStream_t st);
+void launch_adam(int64_t n, float lr, int t, float* th, const float* g, float* m, float* v,
+                 __nv_bfloat16* thb, cudaStream_t st);
+void launch_f32_to_bf16(int64_t n, const float* x, __nv_bfloat16* y, cudaStream_t st);
+void launch_downsample(int64_t rows, int nx, const double* U, float* T, cudaStream_t st);
+void launch_upsample(int64_t S, int N, int nx, const float* Y, const float* mean,
+                     const float* stdv, double* U, cudaStream_t st);
+void launch_colstats(int64_t n, int D, const float* T, float* mean, float* stdv, float* inv_std,
+                     cudaStream_t st);
+void launch_nonfinite_f32(int64_t n, const float* x, int* flag, cudaStream_t st);
+
 // Thread-local last-error detail.
 void set_error(const std::string& msg);
 

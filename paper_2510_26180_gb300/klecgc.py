@@ -12,7 +12,7 @@ import os
 import numpy as np
 
 FP64, MIXED, MIXED_DEFECT = 0, 1, 2
-GUESS_GPC, GUESS_ZERO, GUESS_USER, GUESS_COARSE = 0, 1, 2, 3
+GUESS_GPC, GUESS_ZERO, GUESS_USER, GUESS_COARSE, GUESS_MLP = 0, 1, 2, 3, 4
 (OK, E_INVALID_ARG, E_OUT_OF_MEMORY, E_NOT_CONVERGED, E_NONFINITE, E_CUDA,
  E_UNSUPPORTED) = range(7)
 
@@ -23,7 +23,8 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libklecgc.so")
 EXPORTS = ["klecgc_setup", "klecgc_solve", "klecgc_field", "klecgc_guess", "klecgc_fine_sweep",
            "klecgc_cgc_apply", "klecgc_reference", "klecgc_info", "klecgc_free",
            "klecgc_status_string", "klecgc_last_error", "klecgc_profile_enable",
-           "klecgc_profile_read", "klecgc_reference_noalloc"]
+           "klecgc_profile_read", "klecgc_reference_noalloc", "klecgc_mlp_set", "klecgc_mlp_get",
+           "klecgc_mlp_loss_grad", "klecgc_mlp_train", "klecgc_mlp_guess", "klecgc_downsample"]
 PROFILE_CLASSES = ["field", "factors", "guess", "fine", "cgc_fwd", "cgc_solve", "cgc_inv",
                    "conv", "layout"]
 
@@ -85,6 +86,12 @@ def load() -> ctypes.CDLL:
         "klecgc_reference_noalloc": [P, P, I64, I32, I32, P, P],
         "klecgc_info": [P, ctypes.POINTER(Info)],
         "klecgc_profile_enable": [P, I32],
+        "klecgc_mlp_set": [P, P, I64, P, P],
+        "klecgc_mlp_get": [P, P, P, P, ctypes.POINTER(ctypes.c_int64)],
+        "klecgc_mlp_loss_grad": [P, P, P, I64, ctypes.POINTER(ctypes.c_double), P, P],
+        "klecgc_mlp_train": [P, P, P, I64, I32, I32, D, D, ctypes.c_uint64, I32, P, P],
+        "klecgc_mlp_guess": [P, P, I64, P, P],
+        "klecgc_downsample": [P, P, I64, I32, P, P],
         "klecgc_profile_read": [P, ctypes.POINTER(Profile)],
     }
     for name, args in sig.items():
@@ -116,7 +123,7 @@ def _ptr(a, dtype):
             raise TypeError(f"expected a C-contiguous {dtype} array")
         return a.ctypes.data
     import torch
-    tdt = {np.float64: torch.float64, np.int32: torch.int32}[dtype]
+    tdt = {np.float64: torch.float64, np.int32: torch.int32, np.float32: torch.float32}[dtype]
     if a.dtype != tdt or not a.is_contiguous():
         raise TypeError(f"expected a contiguous {tdt} tensor")
     return a.data_ptr()
@@ -206,6 +213,48 @@ class Solver:
     def reference(self, xi, S, N, J, U_out, stream=None) -> int:
         return _check(self.lib.klecgc_reference(self.h, _ptr(xi, np.float64), S, N, J,
                                                  _ptr(U_out, np.float64), _stream(stream)))
+
+    # ---- learned guess
+    def mlp_n_params(self) -> int:
+        n = ctypes.c_int64()
+        _check(self.lib.klecgc_mlp_get(self.h, None, None, None, ctypes.byref(n)))
+        return n.value
+
+    def mlp_set(self, params, out_mean=None, out_std=None) -> int:
+        n = params.numel() if hasattr(params, "numel") else params.size
+        return _check(self.lib.klecgc_mlp_set(self.h, _ptr(params, np.float32), n,
+                                              _ptr(out_mean, np.float32),
+                                              _ptr(out_std, np.float32)))
+
+    def mlp_get(self, params=None, out_mean=None, out_std=None) -> int:
+        return _check(self.lib.klecgc_mlp_get(self.h, _ptr(params, np.float32),
+                                              _ptr(out_mean, np.float32),
+                                              _ptr(out_std, np.float32), None))
+
+    def mlp_loss_grad(self, xi, targets, B, grad_out=None, stream=None) -> float:
+        loss = ctypes.c_double()
+        _check(self.lib.klecgc_mlp_loss_grad(self.h, _ptr(xi, np.float64),
+                                             _ptr(targets, np.float32), B, ctypes.byref(loss),
+                                             _ptr(grad_out, np.float32), _stream(stream)))
+        return loss.value
+
+    def mlp_train(self, xi, targets, n, epochs, batch, lr, lr_final, seed, fit_norm=True,
+                  stream=None) -> np.ndarray:
+        losses = np.zeros(epochs, dtype=np.float32)
+        _check(self.lib.klecgc_mlp_train(self.h, _ptr(xi, np.float64), _ptr(targets, np.float32),
+                                         n, epochs, batch, lr, lr_final, seed,
+                                         1 if fit_norm else 0, losses.ctypes.data,
+                                         _stream(stream)))
+        return losses
+
+    def mlp_guess(self, xi, S, U0_out, stream=None) -> int:
+        return _check(self.lib.klecgc_mlp_guess(self.h, _ptr(xi, np.float64), S,
+                                                _ptr(U0_out, np.float64), _stream(stream)),
+                      (OK, E_NONFINITE))
+
+    def downsample(self, U, S, N, T_out, stream=None) -> int:
+        return _check(self.lib.klecgc_downsample(self.h, _ptr(U, np.float64), S, N,
+                                                 _ptr(T_out, np.float32), _stream(stream)))
 
     def reference_noalloc(self, xi, S, N, J, U_out, stream=None) -> int:
         """klecgc_reference without device allocation (device arrays only)."""
