@@ -90,7 +90,7 @@ def modes_2d(sigma: float, corr_len: float, M: int):
     pairs = []
     for i in range(n1):
         for j in range(n1):
-            pairs.append((sigma ** 2 * lam1[i] * lam1[j], i, j))
+            pairs.append((sigma ** 2 * (lam1[i] * lam1[j]), i, j))   # (i,j), (j,i) tie exactly
     pairs.sort(key=lambda t: (-t[0], t[1] + t[2], t[1]))
     return pairs[:M], (lam1, om1, par1)
 

@@ -78,6 +78,61 @@ class Setup1D:
                                kmax or w.kmax, history=history, cgc=cgc)
 
 
+def _reference_worker_2d(args):
+    w, xi = args
+    st = Setup2D(w, build=False)
+    return st.reference(xi).reshape(-1)
+
+
+class Setup2D(Setup1D):
+    """Same stages as Setup1D on the 2D reaction-diffusion problem (rd2d)."""
+
+    def __init__(self, w, xi_train=None, build=True, processes=1):
+        from synth import draw_train
+        from . import rd2d
+        self.w = w
+        nx = w.nx
+        self.xpts, self.ypts = rd2d.face_points(nx)
+        self.bx = rd2d.field_basis_2d(w.sigma, w.corr_len, w.M, self.xpts)
+        self.by = rd2d.field_basis_2d(w.sigma, w.corr_len, w.M, self.ypts)
+        if w.u0_kind == 0:
+            x = (np.arange(nx) + 1) / (nx + 1)
+            self.u0 = np.outer(np.sin(np.pi * x), np.sin(np.pi * x)).reshape(-1)
+        else:
+            self.u0 = np.zeros(nx * nx)
+        self.dT = w.T / w.N
+        if xi_train is None:
+            xi_train = draw_train(w)
+        self.xi_train = xi_train
+        self.sur = None
+        if build:
+            snaps = self.references(xi_train, processes)
+            self.sur = build_surrogate(snaps.reshape(len(xi_train), -1), xi_train,
+                                       w.gpc_degree, w.eps_kl)
+
+    def operator(self, xi, field_ulps: float = 0.0, seed: int = 0):
+        from . import rd2d
+        ax = np.exp(np.tensordot(np.asarray(xi, dtype=np.float64), self.bx, axes=1))
+        ay = np.exp(np.tensordot(np.asarray(xi, dtype=np.float64), self.by, axes=1))
+        if field_ulps:
+            rng = np.random.default_rng(seed)
+            ax = ax * (1.0 + field_ulps * 2.0 ** -53 * rng.choice([-1.0, 1.0], size=ax.shape))
+            ay = ay * (1.0 + field_ulps * 2.0 ** -53 * rng.choice([-1.0, 1.0], size=ay.shape))
+        return rd2d.RD2D(ax, ay, self.w.reaction, self.w.forcing)
+
+    def references(self, xis, processes=1) -> np.ndarray:
+        if processes <= 1 or len(xis) < 2:
+            return np.stack([self.reference(x) for x in xis])
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn")) as ex:
+            out = list(ex.map(_reference_worker_2d, [(self.w, x) for x in xis]))
+        return np.stack(out).reshape(len(xis), self.w.N, -1)
+
+    def guess(self, xi) -> np.ndarray:
+        return self.sur.guess(np.atleast_2d(xi)).reshape(-1, self.w.N, self.w.nx * self.w.nx)
+
+
 def rel_l2(U, Uref) -> float:
     return float(np.linalg.norm(np.ravel(U) - np.ravel(Uref)) /
                  np.linalg.norm(np.ravel(Uref)))

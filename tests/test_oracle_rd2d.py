@@ -1,0 +1,77 @@
+"""Pins of the 2D reaction-diffusion oracle against closed forms and brute force."""
+import math
+
+import numpy as np
+
+from oracle import pcgc, rd2d
+
+
+def _op(nx, const=False, reaction=0.0, forcing=0.0, seed=0):
+    rng = np.random.default_rng(seed)
+    ax = np.ones((nx, nx + 1)) if const else np.exp(0.4 * rng.standard_normal((nx, nx + 1)))
+    ay = np.ones((nx + 1, nx)) if const else np.exp(0.4 * rng.standard_normal((nx + 1, nx)))
+    return rd2d.RD2D(ax, ay, reaction, forcing)
+
+
+def test_five_point_spectrum_and_eigenvector():
+    # a == 1: mu_jk = (4/h^2)(sin^2(j pi h/2) + sin^2(k pi h/2)) + c, eigvec sin(j pi x) sin(k pi y)
+    nx, c = 9, 0.6
+    op = _op(nx, const=True, reaction=c)
+    h = op.h
+    s = 4 / h ** 2 * np.sin(np.arange(1, nx + 1) * np.pi * h / 2) ** 2
+    mu = np.sort((s[:, None] + s[None, :]).ravel() + c)
+    assert np.allclose(np.sort(np.linalg.eigvalsh(op.dense())), mu, rtol=1e-12)
+    x = (np.arange(nx) + 1) * h
+    v = np.outer(np.sin(2 * np.pi * x), np.sin(np.pi * x)).ravel()   # [iy][ix]: y-mode 2, x-mode 1
+    lam = s[0] + s[1] + c
+    assert np.allclose(op.apply(v), lam * v, rtol=1e-11, atol=1e-9)
+    # one backward-Euler step scales it by 1/(1 + dt lam)
+    assert np.allclose(op.be_step(v, 0.01), v / (1 + 0.01 * lam), rtol=1e-12)
+
+
+def test_operator_symmetric_and_matches_stencil_definition():
+    op = _op(6, seed=3, reaction=1.0)
+    A = op.dense()
+    assert np.allclose(A, A.T)
+    # row sums: reaction c plus the boundary-face weights (interior faces cancel)
+    nx, h2 = op.nx, op.h ** 2
+    rng = np.random.default_rng(3)
+    ax = np.exp(0.4 * rng.standard_normal((nx, nx + 1)))
+    ay = np.exp(0.4 * rng.standard_normal((nx + 1, nx)))
+    bnd = np.zeros((nx, nx))
+    bnd[:, 0] += ax[:, 0]
+    bnd[:, -1] += ax[:, -1]
+    bnd[0, :] += ay[0, :]
+    bnd[-1, :] += ay[-1, :]
+    assert np.allclose(A.sum(1), 1.0 + bnd.ravel() / h2)
+
+
+def test_three_step_solve_equals_dense_kron_solve_2d():
+    op = _op(3, seed=4, reaction=1.0)
+    N, alpha, dT = 4, 1e-2, 0.25
+    r = np.random.default_rng(1).standard_normal((N, op.n))
+    assert np.allclose(pcgc.cgc_diagonalized(op, r, dT, alpha), pcgc.cgc_dense(op, r, dT, alpha),
+                       rtol=1e-11, atol=1e-12)
+
+
+def test_pcgc_reaches_fine_solution_2d():
+    op = _op(5, seed=5, reaction=1.0, forcing=1.0)
+    N, J = 6, 3
+    u0 = np.zeros(op.n)
+    from oracle import heat1d
+    Ustar = heat1d.fine_sequential(op, u0, N, J, 1.0)
+    U, its, _ = pcgc.pcgc_solve(op, u0, np.zeros((N, op.n)), 1.0 / N, J, 1e-3, 1e-13, 60)
+    assert its > 0 and np.max(np.abs(U - Ustar)) < 1e-12
+
+
+def test_face_points_and_2d_basis_products():
+    (X1x, X2x), (X1y, X2y) = rd2d.face_points(4)
+    h = 0.2
+    assert np.allclose(X1x[0], (np.arange(5) + 0.5) * h) and np.allclose(X2x[:, 0], (np.arange(4) + 1) * h)
+    assert np.allclose(X1y[0], (np.arange(4) + 1) * h) and np.allclose(X2y[:, 0], (np.arange(5) + 0.5) * h)
+    B = rd2d.field_basis_2d(0.4, 0.3, 3, (X1x, X2x))
+    from oracle import kl_input
+    pairs, (lam1, om1, par1) = kl_input.modes_2d(0.4, 0.3, 3)
+    lam, i, j = pairs[1]
+    ref = math.sqrt(lam) * kl_input.exp_cov_phi_1d(X1x, om1[i], par1[i]) * kl_input.exp_cov_phi_1d(X2x, om1[j], par1[j])
+    assert np.allclose(B[1], ref)
