@@ -26,7 +26,14 @@
  *    completed, so the returned status is final.
  *  - Layouts are row-major.  A solution batch U has shape [S][N][nx^dim]:
  *    U[s][n][i] approximates u(x_i, T_{n+1}) for n = 0..N-1 (U_1..U_N of the
- *    paper), x_i the interior grid points in lexicographic order.
+ *    paper), x_i the interior grid points in lexicographic order (2D:
+ *    i = iy*nx + ix for the point ((ix+1)h, (iy+1)h)).
+ *  - dim = 2 uses the five-point flux-form operator with the coefficient at
+ *    the edge midpoints; its linear systems (the backward-Euler steps of F
+ *    and the shifted CGC systems of eq. three steps (b)) are solved by
+ *    Jacobi-preconditioned CG / COCG to a relative residual (see
+ *    klecgc_set_krylov) instead of the 1D direct factorizations.  2D runs in
+ *    FP64 only (precision KLECGC_FP64) and has no learned guess.
  *  - No exception crosses the ABI and no device trap is used: every error
  *    is a status code; klecgc_last_error() returns a one-line detail for
  *    the calling thread.
@@ -76,7 +83,7 @@ enum {
 };
 
 typedef struct {
-    int32_t dim;          /* space dimension: 1 (2 is reserved) */
+    int32_t dim;          /* space dimension: 1 or 2 ((0,1)^2, nx <= 2047) */
     int32_t nx;           /* interior points per direction, h = 1/(nx+1) */
     double T;             /* final time */
     double sigma;         /* std-dev of the Gaussian log-coefficient g */
@@ -118,7 +125,12 @@ typedef struct {
  * xi_train: [n_train][M] FP64, host or device.  Runs on the current CUDA
  * device.  On success *out owns the context (free with klecgc_free).
  * Errors: INVALID_ARG (bad problem fields, NULL pointers),
- * OUT_OF_MEMORY, NONFINITE (xi_train), CUDA, UNSUPPORTED (dim != 1).
+ * OUT_OF_MEMORY, NONFINITE (xi_train), CUDA, UNSUPPORTED (dim not 1 or 2),
+ * NOT_CONVERGED (2D: a snapshot's Krylov solve reached the iteration cap).
+ * 2D input KL: the covariance sigma^2 exp(-|x1-y1|/l) exp(-|x2-y2|/l) is
+ * separable; its eigenpairs are (sigma^2 mu_i mu_j, phi_i(x1) phi_j(x2)) of the
+ * unit-variance 1D pairs, ordered by decreasing eigenvalue, ties (i, j) /
+ * (j, i) by smaller i + j, then smaller i; the first M are used.
  */
 klecgc_status klecgc_setup(const klecgc_problem* problem, const double* xi_train,
                            klecgc_ctx** out, void* stream);
@@ -134,7 +146,8 @@ klecgc_status klecgc_setup(const klecgc_problem* problem, const double* xi_train
  *              max_n ||U^{k}_n - U^{k-1}_n||_inf <= tol (the paper fixes no
  *              rule; this is the per-sample increment).
  *   kmax:      iteration cap (>= 1).
- *   precision: KLECGC_FP64 / KLECGC_MIXED / KLECGC_MIXED_DEFECT.
+ *   precision: KLECGC_FP64 / KLECGC_MIXED / KLECGC_MIXED_DEFECT (2D: FP64
+ *              only, else UNSUPPORTED).
  *   guess:     KLECGC_GUESS_*; U_guess ([S][N][nx]) is read only for USER.
  *   U_out:     [S][N][nx] FP64: the last iterate of every sample.
  *   iters_out: [S] int32: CGC updates performed until tol was met, -1 when
@@ -156,7 +169,9 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S,
  * checks).  Arguments have the meanings given for klecgc_solve. */
 
 /* Coefficient field a(x_{i+1/2}; xi) = exp(g) at the nx+1 faces of every
- * sample: a_out [S][nx+1] FP64. */
+ * sample: a_out [S][nx+1] FP64.  2D: a_out [S][2 nx (nx+1)], the x-faces
+ * [nx][nx+1] at ((fx+1/2)h, (iy+1)h) first, then the y-faces [nx+1][nx] at
+ * ((ix+1)h, (fy+1/2)h). */
 klecgc_status klecgc_field(klecgc_ctx* ctx, const double* xi, int64_t S,
                            double* a_out, void* stream);
 
@@ -208,6 +223,7 @@ klecgc_status klecgc_reference(klecgc_ctx* ctx, const double* xi, int64_t S, int
  *   INVALID_ARG with the sizes in klecgc_last_error(); host arrays and a
  *   device other than the context's also give INVALID_ARG.
  * Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).
+ * 1D contexts only (UNSUPPORTED for dim = 2).
  * The first call on a device looks up the array's device address with
  * cudaGetSymbolAddress; make that first call before any stream capture.
  * Every call shares the array: calls whose GPU work overlaps (e.g. on two
@@ -227,7 +243,7 @@ klecgc_status klecgc_reference_noalloc(klecgc_ctx* ctx, const double* xi, int64_
  * Parameters: one flat FP32 vector [W1, b1, W2, b2, W3, b3, W4, b4], W_l
  * stored [out][in].  GEMMs use BF16 operands with FP32 accumulation; master
  * weights, Adam moments, activations before the BF16 rounding and the loss
- * are FP32.
+ * are FP32.  1D contexts only (UNSUPPORTED for dim = 2).
  */
 
 /* Sets the parameters (n_params floats, host or device) and the output
@@ -268,6 +284,25 @@ klecgc_status klecgc_mlp_guess(klecgc_ctx* ctx, const double* xi, int64_t S, dou
  * T_out [S][N][64] FP32, linear interpolation with zero boundary values. */
 klecgc_status klecgc_downsample(klecgc_ctx* ctx, const double* U, int64_t S, int32_t N,
                                 float* T_out, void* stream);
+
+/*
+ * 2D Krylov solves (dim = 2 only; 1D uses direct factorizations).
+ * Each backward-Euler step (I + dt(A + cI)) v' = v + dt f0 of F is solved by
+ * Jacobi-preconditioned CG warm-started from v, stopped when
+ * ||b - M v'||_2 <= rtol_fine ||b||_2; each shifted CGC system
+ * (lambda_k I + dT(A + cI)) q_k = p_k (eq. three steps (b)) by
+ * Jacobi-preconditioned COCG from zero, stopped when ||r||_2 <= rtol_cgc
+ * ||p_k||_2.  Either stops after maxit iterations at most; a sample with
+ * such a solve gets status NOT_CONVERGED.  Defaults 1e-10, 1e-10, 10000.
+ * INVALID_ARG unless 0 < rtol < 1 and maxit >= 1.
+ */
+klecgc_status klecgc_set_krylov(klecgc_ctx* ctx, double rtol_fine, double rtol_cgc,
+                                int32_t maxit);
+
+/* Krylov iterations of the last 2D call (klecgc_solve, klecgc_fine_sweep,
+ * klecgc_cgc_apply, klecgc_reference), summed over all linear systems, for
+ * F and for the CGC solves.  Either pointer may be NULL. */
+klecgc_status klecgc_krylov_stats(const klecgc_ctx* ctx, int64_t* its_fine, int64_t* its_cgc);
 
 /* Sizes of the context (M_Q, P, ...). */
 klecgc_status klecgc_info(const klecgc_ctx* ctx, klecgc_info_t* out);

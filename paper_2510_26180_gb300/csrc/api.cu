@@ -63,14 +63,21 @@ struct klecgc_ctx {
     klecgc_problem prob{};
     int device = 0;
     int nx = 0, N = 0, J = 0, M = 0, P = 0, MQ = 0, p = 0;
+    int dim = 1;
+    int ns = 0;   // unknowns nx^dim
+    int nf = 0;   // coefficient faces per sample: nx+1 (1D), 2 nx (nx+1) (2D)
+    // 2D Krylov solves: relative residual tolerances, iteration cap, counters
+    double kry_rtol_fine = 1e-10, kry_rtol_cgc = 1e-10;
+    int kry_maxit = 10000;
+    unsigned long long kry_it_fine = 0, kry_it_cgc = 0;
     double h = 0.0, dT = 0.0;
     double lambda_sum = 0.0, lambda_kept = 0.0;
     // device tables (owned)
-    double* basis = nullptr;   // [M][nx+1]  sqrt(lambda_m) phi_m(x_{i+1/2})
-    double* u0 = nullptr;      // [nx]
+    double* basis = nullptr;   // [M][nf]  sqrt(lambda_m) phi_m at the faces
+    double* u0 = nullptr;      // [ns]
     int* degrees = nullptr;    // [P][M]
-    double* ubar = nullptr;    // [nx*N]  internal order c = i*N + n
-    double* W = nullptr;       // [P][nx*N]
+    double* ubar = nullptr;    // [ns*N]  internal order c = i*N + n
+    double* W = nullptr;       // [P][ns*N]
     float* W32 = nullptr;      // FP32 copy of W
     std::map<std::string, DevBuf> ws;  // grow-only scratch
     std::vector<void*> owned;
@@ -158,7 +165,7 @@ namespace klecgc {
 bool ctx_view(const klecgc_ctx* ctx, CtxView* out) {
     if (!ctx || !ctx->basis) return false;
     *out = CtxView{ctx->basis, ctx->u0, ctx->nx, ctx->M, ctx->device,
-                   ctx->h, ctx->prob.T, ctx->prob.reaction, ctx->prob.forcing};
+                   ctx->h, ctx->prob.T, ctx->prob.reaction, ctx->prob.forcing, ctx->dim};
     return true;
 }
 }  // namespace klecgc
@@ -233,11 +240,28 @@ struct Operators {
 
 klecgc_status build_field(klecgc_ctx* ctx, const double* xi_d, int64_t S, cudaStream_t st,
                           double** a_out) {
-    const int nf = ctx->nx + 1;
+    const int nf = ctx->nf;
     WS(double, a, "a", S * nf);
     ctx->launch(KLECGC_K_FIELD, st, [&] { launch_field(xi_d, S, ctx->M, ctx->basis, nf, a, st); });
     TRY(cudaGetLastError());
     *a_out = a;
+    return KLECGC_OK;
+}
+
+// Eigenvalues lambda_k = 1 - alpha^{1/N} exp(-2 pi i k / N), k = 0..N/2, of
+// C_alpha (host copy in lam, device copy in *lam_d).
+klecgc_status upload_lambda(klecgc_ctx* ctx, int N, double alpha, cudaStream_t st,
+                            std::vector<double2>& lam, double2** lam_d) {
+    const int K = N / 2 + 1;
+    lam.resize(K);
+    const double a1n = std::pow(alpha, 1.0 / N), pi = 3.14159265358979323846;
+    for (int k = 0; k < K; ++k) {
+        lam[k].x = 1.0 - a1n * std::cos(2.0 * pi * k / N);
+        lam[k].y = a1n * std::sin(2.0 * pi * k / N);
+    }
+    WS(double2, d, "lam", K);
+    TRY(cudaMemcpyAsync(d, lam.data(), K * sizeof(double2), cudaMemcpyHostToDevice, st));
+    *lam_d = d;
     return KLECGC_OK;
 }
 
@@ -265,15 +289,10 @@ klecgc_status build_operators(klecgc_ctx* ctx, const double* xi_d, int64_t S, in
         op->tab32 = tb;
     }
     if (want_cgc) {
-        std::vector<double2> lam(K);
-        const double a1n = std::pow(alpha, 1.0 / N), pi = 3.14159265358979323846;
-        for (int k = 0; k < K; ++k) {
-            // lambda_k = 1 - alpha^{1/N} exp(-2 pi i k / N)
-            lam[k].x = 1.0 - a1n * std::cos(2.0 * pi * k / N);
-            lam[k].y = a1n * std::sin(2.0 * pi * k / N);
-        }
-        WS(double2, lam_d, "lam", K);
-        TRY(cudaMemcpyAsync(lam_d, lam.data(), K * sizeof(double2), cudaMemcpyHostToDevice, st));
+        std::vector<double2> lam;
+        double2* lam_d = nullptr;
+        klecgc_status ls = upload_lambda(ctx, N, alpha, st, lam, &lam_d);
+        if (ls != KLECGC_OK) return ls;
         if (want_cgc == 1) {
             WS(Cplx<double>, di, "cgc_dinv64", S * nx * K);
             WS(Cplx<double>, lu, "cgc_lu64", S * nx * K);
@@ -299,6 +318,83 @@ klecgc_status build_operators(klecgc_ctx* ctx, const double* xi_d, int64_t S, in
     return KLECGC_OK;
 }
 
+// 2D: coefficient field and the face weights dt a / h^2 (fine, if wdt) and
+// dT a / h^2 (CGC, if wdT), layout [S][nf].
+klecgc_status build_weights_2d(klecgc_ctx* ctx, const double* xi_d, int64_t S, double dt,
+                               double dT, cudaStream_t st, double** wdt, double** wdT) {
+    const int nf = ctx->nf;
+    double* a = nullptr;
+    klecgc_status s = build_field(ctx, xi_d, S, st, &a);
+    if (s != KLECGC_OK) return s;
+    const double ih2 = 1.0 / (ctx->h * ctx->h);
+    if (wdt) {
+        WS(double, w, "w2d_fine", S * nf);
+        ctx->launch(KLECGC_K_FIELD, st, [&] { launch_face_weights(a, S, nf, dt * ih2, w, st); });
+        *wdt = w;
+    }
+    if (wdT) {
+        WS(double, w, "w2d_cgc", S * nf);
+        ctx->launch(KLECGC_K_FIELD, st, [&] { launch_face_weights(a, S, nf, dT * ih2, w, st); });
+        *wdT = w;
+    }
+    TRY(cudaGetLastError());
+    return KLECGC_OK;
+}
+
+// Per-sample flags of Krylov solves that reached the iteration cap, and the
+// iteration counter, zeroed.
+klecgc_status krylov_flags(klecgc_ctx* ctx, int64_t S, cudaStream_t st, int** ifail,
+                           unsigned long long** its) {
+    WS(int, f, "kry_fail", S);
+    WS(unsigned long long, c, "kry_its", 2);
+    TRY(cudaMemsetAsync(f, 0, S * sizeof(int), st));
+    TRY(cudaMemsetAsync(c, 0, 2 * sizeof(unsigned long long), st));
+    *ifail = f;
+    *its = c;
+    return KLECGC_OK;
+}
+
+// Reads the counters of krylov_flags after the stream work; true if some
+// sample's solve reached the cap (its samples are listed in ifail).
+klecgc_status krylov_read(klecgc_ctx* ctx, int64_t S, const int* ifail,
+                          const unsigned long long* its, cudaStream_t st, std::vector<int>* hf,
+                          bool* any) {
+    unsigned long long h[2] = {0, 0};
+    hf->assign(S, 0);
+    TRY(cudaMemcpyAsync(h, its, sizeof(h), cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(hf->data(), ifail, S * sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    ctx->kry_it_fine = h[0];
+    ctx->kry_it_cgc = h[1];
+    *any = false;
+    for (int v : *hf) *any |= v != 0;
+    return KLECGC_OK;
+}
+
+// Sequential fine solution of the 2D problem: out [S][ns][N] (internal layout).
+klecgc_status sequential_2d(klecgc_ctx* ctx, const double* xi_d, int64_t S, int N, int J,
+                            double* out, cudaStream_t st, bool* capped) {
+    const double dT = ctx->prob.T / N, dt = dT / J;
+    double* wdt = nullptr;
+    klecgc_status s = build_weights_2d(ctx, xi_d, S, dt, dT, st, &wdt, nullptr);
+    if (s != KLECGC_OK) return s;
+    int* ifail = nullptr;
+    unsigned long long* its = nullptr;
+    if ((s = krylov_flags(ctx, S, st, &ifail, &its)) != KLECGC_OK) return s;
+    WS(int, act, "act_all", S);
+    TRY(cudaMemsetAsync(act, 0xff, S * sizeof(int), st));
+    const Plan2D pl = plan_2d(0, ctx->nx, S);
+    WS(double, scr, "k2d_scratch", pl.scratch_doubles);
+    ctx->launch(KLECGC_K_FINE, st, [&] {
+        launch_fine2d(pl, S, N, ctx->nx, J, dt * ctx->prob.reaction, dt * ctx->prob.forcing, 0.0,
+                      1, nullptr, ctx->u0, wdt, ctx->kry_rtol_fine, ctx->kry_maxit, out, act,
+                      ifail, its, scr, st);
+    });
+    TRY(cudaGetLastError());
+    std::vector<int> hf;
+    return krylov_read(ctx, S, ifail, its, st, &hf, capped);
+}
+
 // alpha^{j/N} and alpha^{-j/N} / (N/2) tables in precision T.
 template <typename T>
 klecgc_status scale_tables(klecgc_ctx* ctx, int N, double alpha, cudaStream_t st, T** sc,
@@ -322,7 +418,7 @@ klecgc_status scale_tables(klecgc_ctx* ctx, int N, double alpha, cudaStream_t st
 // U^0 = ubar + psi(xi) W into U (internal layout [S][nx][N]).
 klecgc_status gpc_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S, bool fp64,
                                  double* U, cudaStream_t st) {
-    const int64_t NC = (int64_t)ctx->nx * ctx->N;
+    const int64_t NC = (int64_t)ctx->ns * ctx->N;
     if (fp64) {
         WS(double, psi, "psi64", S * ctx->P);
         ctx->launch(KLECGC_K_GUESS, st, [&] { launch_psi<double>(xi_d, S, ctx->M, ctx->degrees, ctx->P, psi, st); });
@@ -339,6 +435,7 @@ klecgc_status gpc_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S,
 // ---------------------------------------------------------------- learned guess
 klecgc_status mlp_alloc(klecgc_ctx* ctx) {
     MlpState& q = ctx->mlp;
+    if (ctx->dim != 1) return fail(KLECGC_E_UNSUPPORTED, "the learned guess is 1D only");
     if (q.theta) return KLECGC_OK;
     const int W = 256;
     q.sizes[0] = ctx->M;
@@ -499,7 +596,7 @@ klecgc_status check_xi_finite(klecgc_ctx* ctx, const double* xi_d, int64_t n, cu
 // Copies an internal [S][nx][N] batch to the caller's [S][N][nx] array.
 klecgc_status export_batch(klecgc_ctx* ctx, const double* U_int, int64_t S, int N, double* out,
                            cudaStream_t st) {
-    const int nx = ctx->nx;
+    const int nx = ctx->ns;
     if (is_device_ptr(out)) {
         ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_transpose(U_int, out, S, nx, N, st); });
         TRY(cudaGetLastError());
@@ -517,9 +614,9 @@ klecgc_status export_batch(klecgc_ctx* ctx, const double* U_int, int64_t S, int 
 klecgc_status import_batch(klecgc_ctx* ctx, const double* user, int64_t S, int N, double* U_int,
                            cudaStream_t st) {
     const double* src = nullptr;
-    klecgc_status s = stage_in(ctx, user, (size_t)S * ctx->nx * N, "import", st, &src);
+    klecgc_status s = stage_in(ctx, user, (size_t)S * ctx->ns * N, "import", st, &src);
     if (s != KLECGC_OK) return s;
-    ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_transpose(src, U_int, S, N, ctx->nx, st); });
+    ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_transpose(src, U_int, S, N, ctx->ns, st); });
     TRY(cudaGetLastError());
     return KLECGC_OK;
 }
@@ -562,8 +659,27 @@ klecgc_status klecgc_info(const klecgc_ctx* ctx, klecgc_info_t* out) {
     out->MQ = ctx->MQ;
     out->lambda_sum = ctx->lambda_sum;
     out->lambda_kept = ctx->lambda_kept;
-    out->n_unknowns = ctx->nx;
+    out->n_unknowns = ctx->ns;
     out->device = ctx->device;
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_set_krylov(klecgc_ctx* ctx, double rtol_fine, double rtol_cgc,
+                                int32_t maxit) {
+    set_error("");
+    if (!ctx || !(rtol_fine > 0 && rtol_fine < 1) || !(rtol_cgc > 0 && rtol_cgc < 1) || maxit < 1)
+        return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    ctx->kry_rtol_fine = rtol_fine;
+    ctx->kry_rtol_cgc = rtol_cgc;
+    ctx->kry_maxit = maxit;
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_krylov_stats(const klecgc_ctx* ctx, int64_t* its_fine, int64_t* its_cgc) {
+    set_error("");
+    if (!ctx) return fail(KLECGC_E_INVALID_ARG, "NULL context");
+    if (its_fine) *its_fine = (int64_t)ctx->kry_it_fine;
+    if (its_cgc) *its_cgc = (int64_t)ctx->kry_it_cgc;
     return KLECGC_OK;
 }
 
@@ -594,7 +710,8 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     set_error("");
     if (!pr || !out || !xi_train) return fail(KLECGC_E_INVALID_ARG, "NULL argument");
     *out = nullptr;
-    if (pr->dim != 1) return fail(KLECGC_E_UNSUPPORTED, "only dim = 1 is built");
+    if (pr->dim != 1 && pr->dim != 2) return fail(KLECGC_E_UNSUPPORTED, "dim must be 1 or 2");
+    if (pr->dim == 2 && pr->nx > 2047) return fail(KLECGC_E_UNSUPPORTED, "2D needs nx <= 2047");
     if (pr->nx < 1 || pr->M < 1 || pr->gpc_degree < 0 || pr->n_train < 2 || !(pr->T > 0) ||
         !(pr->sigma >= 0) || !(pr->corr_len > 0) || !(pr->eps_kl >= 0) || pr->J < 1 ||
         !(pr->reaction >= 0) || !std::isfinite(pr->forcing) || pr->u0_kind < 0 ||
@@ -606,6 +723,9 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     ctx->prob = *pr;
     cudaGetDevice(&ctx->device);
     ctx->nx = pr->nx;
+    ctx->dim = pr->dim;
+    ctx->ns = pr->dim == 1 ? pr->nx : pr->nx * pr->nx;
+    ctx->nf = pr->dim == 1 ? pr->nx + 1 : 2 * pr->nx * (pr->nx + 1);
     ctx->N = pr->N;
     ctx->J = pr->J;
     ctx->M = pr->M;
@@ -630,27 +750,56 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
         if (s_ != KLECGC_OK) return bail(s_); \
     } while (0)
     STRY(ensure_twiddles(ctx->device));
-    const int nx = ctx->nx, nf = nx + 1, N = ctx->N, M = ctx->M, nt = pr->n_train;
-    const int64_t NC = (int64_t)nx * N;
+    const int nx = ctx->nx, nf = ctx->nf, ns = ctx->ns, N = ctx->N, M = ctx->M, nt = pr->n_train;
+    const int64_t NC = (int64_t)ns * N;
+    const double pi = 3.14159265358979323846, h = ctx->h;
 
     // 1. input KL basis at the faces, initial value, gPC multi-indices
-    std::vector<double> lam, om;
-    std::vector<int> par;
-    kl_modes_1d(pr->corr_len, pr->sigma, M, lam, om, par);
-    std::vector<double> basis((size_t)M * nf), u0(nx);
-    for (int m = 0; m < M; ++m)
-        for (int f = 0; f < nf; ++f)
-            basis[(size_t)m * nf + f] = std::sqrt(lam[m]) * kl_phi_1d((f + 0.5) * ctx->h, om[m], par[m]);
-    for (int i = 0; i < nx; ++i)
-        u0[i] = pr->u0_kind == 0 ? std::sin(3.14159265358979323846 * (i + 1) * ctx->h) : 0.0;
+    std::vector<double> basis((size_t)M * nf), u0(ns);
+    if (ctx->dim == 1) {
+        std::vector<double> lam, om;
+        std::vector<int> par;
+        kl_modes_1d(pr->corr_len, pr->sigma, M, lam, om, par);
+        for (int m = 0; m < M; ++m)
+            for (int f = 0; f < nf; ++f)
+                basis[(size_t)m * nf + f] = std::sqrt(lam[m]) * kl_phi_1d((f + 0.5) * h, om[m], par[m]);
+        for (int i = 0; i < nx; ++i) u0[i] = pr->u0_kind == 0 ? std::sin(pi * (i + 1) * h) : 0.0;
+    } else {
+        // separable modes sigma^2 mu_i mu_j, phi_i(x1) phi_j(x2); x-faces
+        // [nx][nx+1] at ((fx+1/2)h, (iy+1)h), then y-faces [nx+1][nx] at
+        // ((ix+1)h, (fy+1/2)h)
+        std::vector<double> lam;
+        std::vector<int> mi, mj;
+        std::vector<double> mu, om;
+        std::vector<int> par;
+        kl_modes_2d(pr->corr_len, pr->sigma, M, lam, mi, mj, mu, om, par);
+        const int nxf = nx * (nx + 1);
+        for (int m = 0; m < M; ++m) {
+            const double sl = std::sqrt(lam[m]);
+            double* bm = basis.data() + (size_t)m * nf;
+            for (int iy = 0; iy < nx; ++iy)
+                for (int fx = 0; fx <= nx; ++fx)
+                    bm[iy * (nx + 1) + fx] = sl * kl_phi_1d((fx + 0.5) * h, om[mi[m]], par[mi[m]]) *
+                                             kl_phi_1d((iy + 1) * h, om[mj[m]], par[mj[m]]);
+            for (int fy = 0; fy <= nx; ++fy)
+                for (int ix = 0; ix < nx; ++ix)
+                    bm[nxf + fy * nx + ix] = sl * kl_phi_1d((ix + 1) * h, om[mi[m]], par[mi[m]]) *
+                                             kl_phi_1d((fy + 0.5) * h, om[mj[m]], par[mj[m]]);
+        }
+        for (int iy = 0; iy < nx; ++iy)
+            for (int ix = 0; ix < nx; ++ix)
+                u0[iy * nx + ix] = pr->u0_kind == 0
+                                       ? std::sin(pi * (ix + 1) * h) * std::sin(pi * (iy + 1) * h)
+                                       : 0.0;
+    }
     std::vector<int> deg = gpc_multi_indices(M, ctx->p);
     ctx->P = (int)(deg.size() / M);
     const int P = ctx->P;
     STRY(ctx->alloc_owned(&ctx->basis, basis.size()));
-    STRY(ctx->alloc_owned(&ctx->u0, nx));
+    STRY(ctx->alloc_owned(&ctx->u0, ns));
     STRY(ctx->alloc_owned(&ctx->degrees, deg.size()));
     STRY(cudaMemcpyAsync(ctx->basis, basis.data(), basis.size() * 8, cudaMemcpyHostToDevice, st));
-    STRY(cudaMemcpyAsync(ctx->u0, u0.data(), nx * 8, cudaMemcpyHostToDevice, st));
+    STRY(cudaMemcpyAsync(ctx->u0, u0.data(), ns * 8, cudaMemcpyHostToDevice, st));
     STRY(cudaMemcpyAsync(ctx->degrees, deg.data(), deg.size() * 4, cudaMemcpyHostToDevice, st));
 
     // 2. snapshots: sequential fine solution of every training sample
@@ -659,19 +808,25 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     bool finite = true;
     SCHK(check_xi_finite(ctx, xi_d, (int64_t)nt * M, st, &finite));
     if (!finite) return bail(fail(KLECGC_E_NONFINITE, "xi_train has a non-finite entry"));
-    Operators op;
-    SCHK(build_operators(ctx, xi_d, nt, N, ctx->J, ctx->dT, 0.5, 1, 0, st, &op));
     double* Y = nullptr;
     STRY(cudaMalloc(&Y, (size_t)nt * NC * 8));
     struct Guard {
         double* p;
         ~Guard() { cudaFree(p); }
     } gY{Y};
-    {
+    if (ctx->dim == 1) {
+        Operators op;
+        SCHK(build_operators(ctx, xi_d, nt, N, ctx->J, ctx->dT, 0.5, 1, 0, st, &op));
         WS(double, scr, "seq_scratch", (size_t)nt * nx);
         if (!scr) return bail(KLECGC_E_OUT_OF_MEMORY);
         launch_fine_sequential(nt, N, nx, ctx->J, ctx->dT / ctx->J * pr->forcing, ctx->u0, op.f64,
                                scr, Y, st);
+    } else {
+        bool capped = false;
+        SCHK(sequential_2d(ctx, xi_d, nt, N, ctx->J, Y, st, &capped));
+        if (capped)
+            return bail(fail(KLECGC_E_NOT_CONVERGED,
+                             "a snapshot's fine step reached the Krylov iteration cap"));
     }
     // 3. mean and covariance C = Ytilde Ytilde^T / n_t
     STRY(ctx->alloc_owned(&ctx->ubar, NC));
@@ -769,7 +924,7 @@ klecgc_status klecgc_field(klecgc_ctx* ctx, const double* xi, int64_t S, double*
     if (s != KLECGC_OK) return s;
     double* a = nullptr;
     if ((s = build_field(ctx, xi_d, S, st, &a)) != KLECGC_OK) return s;
-    TRY(cudaMemcpyAsync(a_out, a, (size_t)S * (ctx->nx + 1) * 8, cudaMemcpyDefault, st));
+    TRY(cudaMemcpyAsync(a_out, a, (size_t)S * ctx->nf * 8, cudaMemcpyDefault, st));
     TRY(cudaStreamSynchronize(st));
     return KLECGC_OK;
 }
@@ -784,7 +939,7 @@ klecgc_status klecgc_guess(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t
     const double* xi_d = nullptr;
     klecgc_status s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d);
     if (s != KLECGC_OK) return s;
-    WS(double, U, "U", S * (int64_t)ctx->nx * ctx->N);
+    WS(double, U, "U", S * (int64_t)ctx->ns * ctx->N);
     if ((s = gpc_guess_internal(ctx, xi_d, S, precision == KLECGC_FP64, U, st)) != KLECGC_OK)
         return s;
     if ((s = export_batch(ctx, U, S, ctx->N, U0_out, st)) != KLECGC_OK) return s;
@@ -803,15 +958,21 @@ klecgc_status klecgc_reference(klecgc_ctx* ctx, const double* xi, int64_t S, int
     klecgc_status s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d);
     if (s != KLECGC_OK) return s;
     const double dT = ctx->prob.T / N;
-    Operators op;
-    if ((s = build_operators(ctx, xi_d, S, N, J, dT, 0.5, 1, 0, st, &op)) != KLECGC_OK) return s;
-    WS(double, scr, "seq_scratch", S * (int64_t)ctx->nx);
-    WS(double, U, "Uref", S * (int64_t)ctx->nx * N);
-    launch_fine_sequential(S, N, ctx->nx, J, dT / J * ctx->prob.forcing, ctx->u0, op.f64, scr, U,
-                           st);
-    TRY(cudaGetLastError());
+    WS(double, U, "Uref", S * (int64_t)ctx->ns * N);
+    bool capped = false;
+    if (ctx->dim == 2) {
+        if ((s = sequential_2d(ctx, xi_d, S, N, J, U, st, &capped)) != KLECGC_OK) return s;
+    } else {
+        Operators op;
+        if ((s = build_operators(ctx, xi_d, S, N, J, dT, 0.5, 1, 0, st, &op)) != KLECGC_OK) return s;
+        WS(double, scr, "seq_scratch", S * (int64_t)ctx->nx);
+        launch_fine_sequential(S, N, ctx->nx, J, dT / J * ctx->prob.forcing, ctx->u0, op.f64, scr,
+                               U, st);
+        TRY(cudaGetLastError());
+    }
     if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) return s;
     TRY(cudaStreamSynchronize(st));
+    if (capped) return fail(KLECGC_E_NOT_CONVERGED, "a fine step reached the Krylov iteration cap");
     return KLECGC_OK;
 }
 
@@ -979,6 +1140,7 @@ klecgc_status klecgc_downsample(klecgc_ctx* ctx, const double* U, int64_t S, int
                                 float* T_out, void* stream) {
     set_error("");
     if (!ctx || !U || !T_out || S < 0 || N < 1) return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (ctx->dim != 1) return fail(KLECGC_E_UNSUPPORTED, "the network grid is 1D only");
     if (S == 0) return KLECGC_OK;
     cudaStream_t st = (cudaStream_t)stream;
     const double* Ud = nullptr;
@@ -1008,9 +1170,37 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
     klecgc_status s = check_dT(ctx, N, dT);
     if (s != KLECGC_OK || S == 0) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    const int nx = ctx->nx;
+    const int nx = ctx->ns;
     const double* xi_d = nullptr;
     if ((s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d)) != KLECGC_OK) return s;
+    if (ctx->dim == 2) {
+        if (precision != KLECGC_FP64) return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 only");
+        double* wdt = nullptr;
+        if ((s = build_weights_2d(ctx, xi_d, S, dT / J, dT, st, &wdt, nullptr)) != KLECGC_OK) return s;
+        WS(double, U, "U", S * (int64_t)nx * N);
+        if ((s = import_batch(ctx, U_in, S, N, U, st)) != KLECGC_OK) return s;
+        WS(double, r, "r", S * (int64_t)nx * N);
+        WS(int, active, "active", S);
+        TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
+        int* ifail = nullptr;
+        unsigned long long* its = nullptr;
+        if ((s = krylov_flags(ctx, S, st, &ifail, &its)) != KLECGC_OK) return s;
+        const Plan2D pl = plan_2d(0, ctx->nx, S * N);
+        WS(double, scr, "k2d_scratch", pl.scratch_doubles);
+        const double dt = dT / J;
+        ctx->launch(KLECGC_K_FINE, st, [&] {
+            launch_fine2d(pl, S, N, ctx->nx, J, dt * ctx->prob.reaction, dt * ctx->prob.forcing,
+                          alpha, 0, U, ctx->u0, wdt, ctx->kry_rtol_fine, ctx->kry_maxit, r, active,
+                          ifail, its, scr, st);
+        });
+        TRY(cudaGetLastError());
+        if ((s = export_batch(ctx, r, S, N, r_out, st)) != KLECGC_OK) return s;
+        std::vector<int> hf;
+        bool capped = false;
+        if ((s = krylov_read(ctx, S, ifail, its, st, &hf, &capped)) != KLECGC_OK) return s;
+        if (capped) return fail(KLECGC_E_NOT_CONVERGED, "a fine step reached the Krylov iteration cap");
+        return KLECGC_OK;
+    }
     Operators op;
     if ((s = build_operators(ctx, xi_d, S, N, J, dT, alpha, precision == KLECGC_FP64 ? 1 : 2, 0,
                              st, &op)) != KLECGC_OK)
@@ -1046,10 +1236,42 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
     klecgc_status s = check_dT(ctx, N, dT);
     if (s != KLECGC_OK || S == 0) return s;
     cudaStream_t st = (cudaStream_t)stream;
-    const int nx = ctx->nx, K = N / 2 + 1;
+    const int nx = ctx->ns, K = N / 2 + 1;
     const double* xi_d = nullptr;
     if ((s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d)) != KLECGC_OK) return s;
     const bool f64 = precision == KLECGC_FP64;
+    if (ctx->dim == 2) {
+        if (!f64) return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 only");
+        double* wdT = nullptr;
+        if ((s = build_weights_2d(ctx, xi_d, S, dT, dT, st, nullptr, &wdT)) != KLECGC_OK) return s;
+        std::vector<double2> lam;
+        double2* lam_d = nullptr;
+        if ((s = upload_lambda(ctx, N, alpha, st, lam, &lam_d)) != KLECGC_OK) return s;
+        WS(double, r, "r", S * (int64_t)nx * N);
+        if ((s = import_batch(ctx, r_in, S, N, r, st)) != KLECGC_OK) return s;
+        WS(double, U, "U", S * (int64_t)nx * N);
+        WS(int, active, "active", S);
+        TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
+        int* ifail = nullptr;
+        unsigned long long* its = nullptr;
+        if ((s = krylov_flags(ctx, S, st, &ifail, &its)) != KLECGC_OK) return s;
+        double *sc, *isc;
+        if ((s = scale_tables<double>(ctx, N, alpha, st, &sc, &isc)) != KLECGC_OK) return s;
+        WS(Cplx<double>, p, "p64", S * (int64_t)nx * K);
+        const Plan2D pl = plan_2d(1, ctx->nx, S * K);
+        WS(double, scr, "k2d_scratch_c", pl.scratch_doubles);
+        launch_cgc_forward<double, double>(S, N, nx, r, sc, p, active, st);
+        launch_cgc_solve2d(pl, S, K, ctx->nx, dT * ctx->prob.reaction, lam_d, wdT,
+                           ctx->kry_rtol_cgc, ctx->kry_maxit, p, active, ifail, its + 1, scr, st);
+        launch_cgc_inverse<double>(S, N, nx, p, isc, U, 2, nullptr, nullptr, active, st);
+        TRY(cudaGetLastError());
+        if ((s = export_batch(ctx, U, S, N, u_out, st)) != KLECGC_OK) return s;
+        std::vector<int> hf;
+        bool capped = false;
+        if ((s = krylov_read(ctx, S, ifail, its, st, &hf, &capped)) != KLECGC_OK) return s;
+        if (capped) return fail(KLECGC_E_NOT_CONVERGED, "a shifted solve reached the Krylov iteration cap");
+        return KLECGC_OK;
+    }
     Operators op;
     if ((s = build_operators(ctx, xi_d, S, N, 1, dT, alpha, 0, f64 ? 1 : 2, st, &op)) != KLECGC_OK)
         return s;
@@ -1097,11 +1319,12 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
     if (guess == KLECGC_GUESS_MLP && !ctx->mlp.ready)
         return fail(KLECGC_E_INVALID_ARG, "no network (klecgc_mlp_set / klecgc_mlp_train)");
     if (guess == KLECGC_GUESS_COARSE) return fail(KLECGC_E_UNSUPPORTED, "coarse guess not built");
+    if (ctx->dim == 2 && precision != KLECGC_FP64) return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 only");
     klecgc_status s = check_dT(ctx, N, dT);
     if (s != KLECGC_OK) return s;
     if (S == 0) return KLECGC_OK;
     cudaStream_t st = (cudaStream_t)stream;
-    const int nx = ctx->nx, K = N / 2 + 1;
+    const int nx = ctx->ns, K = N / 2 + 1;  // nx: unknowns per time level
     const int64_t NS = S * (int64_t)nx * N;
 
     const double* xi_d = nullptr;
@@ -1119,9 +1342,13 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
     const bool f64 = precision == KLECGC_FP64;
     const bool defect = precision == KLECGC_MIXED_DEFECT;
     Operators op;
-    if ((s = build_operators(ctx, xi_d, S, N, J, dT, alpha, f64 ? 1 : 2, defect ? 2 : 1, st, &op)) !=
-        KLECGC_OK)
+    double *wdt2 = nullptr, *wdT2 = nullptr;  // 2D face weights (fine, CGC)
+    if (ctx->dim == 2) {
+        if ((s = build_weights_2d(ctx, xi_d, S, dT / J, dT, st, &wdt2, &wdT2)) != KLECGC_OK) return s;
+    } else if ((s = build_operators(ctx, xi_d, S, N, J, dT, alpha, f64 ? 1 : 2, defect ? 2 : 1, st,
+                                    &op)) != KLECGC_OK) {
         return s;
+    }
 
     WS(double, U, "U", NS);
     bool mlp_ok = false;
@@ -1200,8 +1427,46 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
         ~HostGuard() { cudaFreeHost(p); }
     } hg{h_active};
     const double dTreact = dT * ctx->prob.reaction;
+    // 2D: Krylov solves instead of factorizations
+    int* ifail = nullptr;
+    unsigned long long* kits = nullptr;
+    double2* lam_d = nullptr;
+    Plan2D plF, plC;
+    double *scrF = nullptr, *scrC = nullptr;
+    if (ctx->dim == 2) {
+        if ((s = krylov_flags(ctx, S, st, &ifail, &kits)) != KLECGC_OK) return s;
+        std::vector<double2> lam;
+        if ((s = upload_lambda(ctx, N, alpha, st, lam, &lam_d)) != KLECGC_OK) return s;
+        plF = plan_2d(0, ctx->nx, S * N);
+        plC = plan_2d(1, ctx->nx, S * K);
+        WS(double, a1, "k2d_scratch", plF.scratch_doubles);
+        WS(double, a2, "k2d_scratch_c", plC.scratch_doubles);
+        scrF = a1;
+        scrC = a2;
+    }
 
     for (int k = 0; k < kmax; ++k) {
+        if (ctx->dim == 2) {
+            const double dt = dT / J;
+            ctx->launch(KLECGC_K_FINE, st, [&] {
+                launch_fine2d(plF, S, N, ctx->nx, J, dt * ctx->prob.reaction,
+                              dt * ctx->prob.forcing, alpha, 0, U, ctx->u0, wdt2,
+                              ctx->kry_rtol_fine, ctx->kry_maxit, r, active, ifail, kits, scrF, st);
+            });
+            ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<double, double>(S, N, nx, r, sc64, p64, active, st); });
+            ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] {
+                launch_cgc_solve2d(plC, S, K, ctx->nx, dTreact, lam_d, wdT2, ctx->kry_rtol_cgc,
+                                   ctx->kry_maxit, p64, active, ifail, kits + 1, scrC, st);
+            });
+            ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc64, U, 0, delta, nullptr, active, st); });
+            TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
+            ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
+            TRY(cudaGetLastError());
+            TRY(cudaMemcpyAsync(h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+            TRY(cudaStreamSynchronize(st));
+            if (*h_active == 0) break;
+            continue;
+        }
         const int cur = k & 1, prv = cur ^ 1;
         if (f64) {
             ctx->launch(KLECGC_K_FINE, st, [&] {
@@ -1259,6 +1524,14 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
     TRY(cudaMemcpyAsync(hi.data(), iters, S * 4, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
     ctx->prof_collect();
+    bool capped = false;
+    if (ctx->dim == 2) {
+        // a sample whose Krylov solve reached the cap has an inexact iterate
+        std::vector<int> hf;
+        if ((s = krylov_read(ctx, S, ifail, kits, st, &hf, &capped)) != KLECGC_OK) return s;
+        for (int64_t i = 0; i < S; ++i)
+            if (hf[i] && hs[i] == KLECGC_OK) hs[i] = KLECGC_E_NOT_CONVERGED;
+    }
     if (iters_out) TRY(cudaMemcpy(iters_out, hi.data(), S * 4, cudaMemcpyDefault));
     if (status_out) TRY(cudaMemcpy(status_out, hs.data(), S * 4, cudaMemcpyDefault));
     bool any_nf = false, any_nc = false;
@@ -1267,7 +1540,9 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
         any_nc |= hs[i] == KLECGC_E_NOT_CONVERGED;
     }
     if (any_nf) return fail(KLECGC_E_NONFINITE, "a sample produced a non-finite iterate");
-    if (any_nc) return fail(KLECGC_E_NOT_CONVERGED, "a sample did not reach tol within kmax");
+    if (any_nc)
+        return fail(KLECGC_E_NOT_CONVERGED, capped ? "a Krylov solve reached its iteration cap"
+                                                   : "a sample did not reach tol within kmax");
     return KLECGC_OK;
 }
 

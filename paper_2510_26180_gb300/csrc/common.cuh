@@ -109,6 +109,27 @@ void launch_jump_from_f32(int64_t S, int N, int nx, double alpha, double dTreact
 void launch_fine_sequential(int64_t S, int N, int nx, int J, double dt_forcing, const double* u0,
                             const FineCoef64* fc, double* scratch, double* U, cudaStream_t st);
 
+// ---- k_2d.cu ---- (2D five-point problem; U/out layout [S][nx*nx][N])
+struct Plan2D {
+    int64_t grid = 1;            // CTAs of the persistent launch
+    int smem = 0;                // dynamic shared memory per CTA (0: global slices)
+    int64_t per_cta = 0;         // doubles of global working storage per CTA
+    int64_t scratch_doubles = 0; // total global working storage
+};
+// kind 0: fine propagator, kind 1: shifted CGC solves; items = work items.
+Plan2D plan_2d(int kind, int nx, int64_t items);
+// mode 0: r = (I + L_dT) F(start) - prev per (s, n); mode 1: sequential fine
+// solution out[s][.][n] per s.  wdt: [S][2 nx (nx+1)] weights dt a / h^2.
+void launch_fine2d(const Plan2D& pl, int64_t S, int N, int nx, int J, double dtc, double dtf,
+                   double alpha, int mode, const double* U, const double* u0, const double* wdt,
+                   double rtol, int maxit, double* out, const int* active, int* ifail,
+                   unsigned long long* itcount, double* scratch, cudaStream_t st);
+// (lambda_k I + L_dT) q = p in place, p: [S][nx*nx][K]; wdT = dT a / h^2.
+void launch_cgc_solve2d(const Plan2D& pl, int64_t S, int K, int nx, double dTc,
+                        const double2* lam, const double* wdT, double rtol, int maxit,
+                        Cplx<double>* p, const int* active, int* ifail,
+                        unsigned long long* itcount, double* scratch, cudaStream_t st);
+
 // ---- k_cgc.cu ----
 // Step (a): p[s][i][k] = sum_j alpha^{j/N} r[s][i][j] exp(-2 pi i j k / N), k <= N/2.
 template <typename T, typename TIN>
@@ -186,6 +207,7 @@ struct CtxView {
     const double* u0;     // [nx]
     int nx, M, device;
     double h, T, reaction, forcing;
+    int dim;
 };
 }  // namespace klecgc
 struct klecgc_ctx;

@@ -1,0 +1,440 @@
+// 2D problem (five-point operator on an nx x nx interior grid): the fine
+// propagator F (hot-path row a3 with the jump epilogue a4) and the shifted
+// CGC solves of eq. three steps (b) (row a6), both by preconditioned Krylov
+// iterations, one CTA per linear system.
+//
+// Operator (flux form, zero Dirichlet values, unknown (ix, iy) at index
+// i = iy*nx + ix):  (L v)_i = c' v_i + sum_f w_f (v_i - v_nb(f))
+// over the four faces f of cell i; a neighbour outside the grid is 0.
+// Per sample the face weights are stored x-faces first, then y-faces:
+//   wx[iy][fx], fx = 0..nx (face between ix = fx-1 and ix = fx),
+//   wy[fy][ix], fy = 0..nx (face between iy = fy-1 and iy = fy),
+// scaled by the step: w = dt a / h^2 for F, w = dT a / h^2 for the CGC,
+// with c' = dt c or dT c accordingly.
+//
+//  F:   (I + L_dt) v^{m+1} = v^m + dt f0, J steps, Jacobi-preconditioned CG
+//       warm-started from v^m, stopped at ||r||_2 <= rtol ||b||_2.
+//  CGC: (lambda_k I + L_dT) q_k = p_k, Jacobi-preconditioned COCG (CG with the
+//       unconjugated bilinear form; lambda_k I + L is complex symmetric),
+//       stopped at ||r||_2 <= rtol ||p_k||_2.
+//
+// Each CTA keeps its system's weights, diagonal and Krylov vectors in shared
+// memory when they fit (else in a global slice of its own) and loops over
+// work items.  The two dot products of an iteration are fused into two block
+// reductions; every thread sums the per-warp partials in the same order, so
+// all threads take the same (uniform) convergence decision.  Iteration
+// counts are capped (maxit); a solve that reaches the cap sets ifail[s].
+#include "common.cuh"
+
+namespace klecgc {
+
+namespace {
+
+constexpr int kThreads2d = 256;
+constexpr int kWarps2d = kThreads2d / 32;
+
+// Sum of NV values over the block; red: [2][NV][32] doubles, ph alternates.
+template <int NV>
+__device__ __forceinline__ void block_sum(double (&v)[NV], double* red, int& ph) {
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+    double* b = red + ph * NV * 32;
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) b[j * 32 + w] = v[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        double s = 0.0;
+        for (int q = 0; q < kWarps2d; ++q) s += b[j * 32 + q];
+        v[j] = s;
+    }
+    ph ^= 1;
+}
+
+// sum over the four faces of w_f (v_i - v_nb), plus c' v_i.
+struct Stencil {
+    const double* wx;
+    const double* wy;
+    int nx;
+    __device__ __forceinline__ double apply(const double* v, int i, int ix, int iy, double c) const {
+        const double vi = v[i];
+        const double* wr = wx + iy * (nx + 1) + ix;
+        const double vw = ix > 0 ? v[i - 1] : 0.0;
+        const double ve = ix < nx - 1 ? v[i + 1] : 0.0;
+        const double vs = iy > 0 ? v[i - nx] : 0.0;
+        const double vn = iy < nx - 1 ? v[i + nx] : 0.0;
+        double acc = c * vi;
+        acc = fma(wr[0], vi - vw, acc);
+        acc = fma(wr[1], vi - ve, acc);
+        acc = fma(wy[iy * nx + ix], vi - vs, acc);
+        acc = fma(wy[(iy + 1) * nx + ix], vi - vn, acc);
+        return acc;
+    }
+    __device__ __forceinline__ double2 apply2(const double2* v, int i, int ix, int iy, double c) const {
+        const double2 vi = v[i];
+        const double2 z = make_double2(0.0, 0.0);
+        const double* wr = wx + iy * (nx + 1) + ix;
+        const double2 vw = ix > 0 ? v[i - 1] : z;
+        const double2 ve = ix < nx - 1 ? v[i + 1] : z;
+        const double2 vs = iy > 0 ? v[i - nx] : z;
+        const double2 vn = iy < nx - 1 ? v[i + nx] : z;
+        const double a0 = wr[0], a1 = wr[1], a2 = wy[iy * nx + ix], a3 = wy[(iy + 1) * nx + ix];
+        double re = c * vi.x, im = c * vi.y;
+        re = fma(a0, vi.x - vw.x, re);
+        im = fma(a0, vi.y - vw.y, im);
+        re = fma(a1, vi.x - ve.x, re);
+        im = fma(a1, vi.y - ve.y, im);
+        re = fma(a2, vi.x - vs.x, re);
+        im = fma(a2, vi.y - vs.y, im);
+        re = fma(a3, vi.x - vn.x, re);
+        im = fma(a3, vi.y - vn.y, im);
+        return make_double2(re, im);
+    }
+    // sum of the four face weights of cell i
+    __device__ __forceinline__ double wsum(int ix, int iy) const {
+        const double* wr = wx + iy * (nx + 1) + ix;
+        return wr[0] + wr[1] + wy[iy * nx + ix] + wy[(iy + 1) * nx + ix];
+    }
+};
+
+__device__ __forceinline__ void cpy_weights(double* dst, const double* src, int nf) {
+    for (int e = threadIdx.x; e < nf; e += blockDim.x) dst[e] = src[e];
+}
+
+// ------------------------------------------------------------------- F
+// mode 0 (parareal sweep): item (s, n); start = u0 (n = 0) or U[s][.][n-1];
+//   after J steps writes r[s][i][n] = (I + L_dT) F_i - prev_i with
+//   prev = alpha U[s][.][N-1] (n = 0) or U[s][.][n-1]; L_dT = J L_dt.
+// mode 1 (sequential fine solution): item s; start u0; after every J steps
+//   writes out[s][i][n] = v_i.
+// U, out: internal layout [S][n_unknowns][N].
+__global__ void __launch_bounds__(kThreads2d) k_fine2d(
+    int64_t S, int N, int nx, int J, double dtc, double dtf, double alpha, int mode,
+    const double* __restrict__ U, const double* __restrict__ u0, const double* __restrict__ wdt,
+    double rtol2, int maxit, double* __restrict__ out, const int* __restrict__ active,
+    int* __restrict__ ifail, unsigned long long* __restrict__ itcount, double* __restrict__ gscr,
+    int64_t per_cta) {
+    extern __shared__ __align__(16) double dsm[];
+    __shared__ double red[2 * 3 * 32];
+    const int n = nx * nx, nf = 2 * nx * (nx + 1);
+    double* W = gscr ? gscr + blockIdx.x * per_cta : dsm;
+    double* dinv = W + nf;
+    double* x = dinv + n;
+    double* r = x + n;
+    double* z = r + n;
+    double* p = z + n;
+    double* q = p + n;
+    const Stencil L{W, W + nx * (nx + 1), nx};
+    const int64_t items = mode == 0 ? S * N : S;
+    int ph = 0;
+    unsigned long long its_total = 0;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t s = mode == 0 ? item / N : item;
+        const int n0 = mode == 0 ? (int)(item - s * N) : 0;
+        if (!active[s]) continue;
+        __syncthreads();  // the previous item's epilogue has read its vectors
+        cpy_weights(W, wdt + s * nf, nf);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int iy = i / nx, ix = i - iy * nx;
+            dinv[i] = 1.0 / (1.0 + dtc + L.wsum(ix, iy));
+            x[i] = (mode == 1 || n0 == 0) ? u0[i] : U[(s * n + i) * N + n0 - 1];
+        }
+        bool failed = false;
+        const int nint = mode == 0 ? 1 : N;
+        for (int ni = 0; ni < nint; ++ni) {
+            for (int j = 0; j < J; ++j) {
+                __syncthreads();  // x complete
+                // r = b - M x = dtf - L x, z = D^{-1} r, p = z
+                double v3[3] = {0.0, 0.0, 0.0};  // ||b||^2, r.z, ||r||^2
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const int iy = i / nx, ix = i - iy * nx;
+                    const double xi = x[i];
+                    const double ri = dtf - L.apply(x, i, ix, iy, dtc);
+                    const double zi = dinv[i] * ri;
+                    r[i] = ri;
+                    z[i] = zi;
+                    p[i] = zi;
+                    const double bi = xi + dtf;
+                    v3[0] = fma(bi, bi, v3[0]);
+                    v3[1] = fma(ri, zi, v3[1]);
+                    v3[2] = fma(ri, ri, v3[2]);
+                }
+                block_sum<3>(v3, red, ph);
+                const double lim = rtol2 * v3[0];
+                double rz = v3[1];
+                if (!(v3[2] > lim)) continue;  // x already solves the step
+                // q = M p, p.q
+                double v1[1] = {0.0};
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const int iy = i / nx, ix = i - iy * nx;
+                    const double qi = p[i] + L.apply(p, i, ix, iy, dtc);
+                    q[i] = qi;
+                    v1[0] = fma(p[i], qi, v1[0]);
+                }
+                block_sum<1>(v1, red, ph);
+                double pq = v1[0];
+                int it = 0;
+                for (;;) {
+                    const double a = rz / pq;
+                    double v2[2] = {0.0, 0.0};  // ||r||^2, r.z
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        x[i] = fma(a, p[i], x[i]);
+                        const double ri = fma(-a, q[i], r[i]);
+                        const double zi = dinv[i] * ri;
+                        r[i] = ri;
+                        z[i] = zi;
+                        v2[0] = fma(ri, ri, v2[0]);
+                        v2[1] = fma(ri, zi, v2[1]);
+                    }
+                    block_sum<2>(v2, red, ph);
+                    ++it;
+                    if (!(v2[0] > lim)) break;
+                    if (it >= maxit) {
+                        failed = true;
+                        break;
+                    }
+                    const double beta = v2[1] / rz;
+                    rz = v2[1];
+                    // p = z + beta p, q = M z + beta q (= M p)
+                    double w1[1] = {0.0};
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        const int iy = i / nx, ix = i - iy * nx;
+                        const double zi = z[i];
+                        const double pi = fma(beta, p[i], zi);
+                        const double qi = fma(beta, q[i], zi + L.apply(z, i, ix, iy, dtc));
+                        p[i] = pi;
+                        q[i] = qi;
+                        w1[0] = fma(pi, qi, w1[0]);
+                    }
+                    block_sum<1>(w1, red, ph);
+                    pq = w1[0];
+                }
+                its_total += it;
+            }
+            if (mode == 1) {
+                __syncthreads();
+                for (int i = threadIdx.x; i < n; i += blockDim.x) out[(s * n + i) * N + ni] = x[i];
+            }
+        }
+        if (mode == 0) {
+            __syncthreads();  // x complete
+            const double dTc = J * dtc;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int iy = i / nx, ix = i - iy * nx;
+                const double Fi = x[i];
+                const double LF = J * (L.apply(x, i, ix, iy, dtc) - dtc * Fi) + dTc * Fi;
+                const double prev = n0 == 0 ? alpha * U[(s * n + i) * N + N - 1]
+                                            : U[(s * n + i) * N + n0 - 1];
+                out[(s * n + i) * N + n0] = (Fi + LF) - prev;
+            }
+        }
+        if (failed && threadIdx.x == 0) ifail[s] = 1;
+    }
+    if (threadIdx.x == 0 && itcount && its_total) atomicAdd(itcount, its_total);
+}
+
+// ------------------------------------------------------------------- CGC (b)
+// item (s, k), k = 0..K-1: solves (lambda_k I + L_dT) q = p in place in
+// p[s][i][k] (layout [S][n_unknowns][K]).
+__global__ void __launch_bounds__(kThreads2d) k_cgc_solve2d(
+    int64_t S, int K, int nx, double dTc, const double2* __restrict__ lam,
+    const double* __restrict__ wdT, double rtol2, int maxit, double2* __restrict__ pio,
+    const int* __restrict__ active, int* __restrict__ ifail,
+    unsigned long long* __restrict__ itcount, double* __restrict__ gscr, int64_t per_cta) {
+    extern __shared__ __align__(16) double dsm[];
+    __shared__ double red[2 * 3 * 32];
+    const int n = nx * nx, nf = 2 * nx * (nx + 1);
+    double* W = gscr ? gscr + blockIdx.x * per_cta : dsm;
+    double2* dinv = reinterpret_cast<double2*>(W + nf + (nf & 1));
+    double2* x = dinv + n;
+    double2* r = x + n;
+    double2* z = r + n;
+    double2* p = z + n;
+    double2* q = p + n;
+    const Stencil L{W, W + nx * (nx + 1), nx};
+    int ph = 0;
+    unsigned long long its_total = 0;
+    for (int64_t item = blockIdx.x; item < S * K; item += gridDim.x) {
+        const int64_t s = item / K;
+        const int k = (int)(item - s * K);
+        if (!active[s]) continue;
+        __syncthreads();
+        cpy_weights(W, wdT + s * nf, nf);
+        __syncthreads();
+        const double2 lk = lam[k];
+        double v3[3] = {0.0, 0.0, 0.0};  // ||b||^2, r.z (complex)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int iy = i / nx, ix = i - iy * nx;
+            const double dr = lk.x + dTc + L.wsum(ix, iy), di = lk.y;
+            const double den = dr * dr + di * di;
+            const double2 dv = make_double2(dr / den, -di / den);
+            dinv[i] = dv;
+            const double2 b = pio[(s * n + i) * K + k];
+            const double2 zi = make_double2(dv.x * b.x - dv.y * b.y, dv.x * b.y + dv.y * b.x);
+            x[i] = make_double2(0.0, 0.0);
+            r[i] = b;
+            z[i] = zi;
+            p[i] = zi;
+            v3[0] = fma(b.x, b.x, fma(b.y, b.y, v3[0]));
+            v3[1] = fma(b.x, zi.x, fma(-b.y, zi.y, v3[1]));
+            v3[2] = fma(b.x, zi.y, fma(b.y, zi.x, v3[2]));
+        }
+        block_sum<3>(v3, red, ph);
+        const double lim = rtol2 * v3[0];
+        bool failed = false;
+        int it = 0;
+        if (v3[0] > 0.0) {
+            double rzr = v3[1], rzi = v3[2];
+            // q = M p, p.q
+            double v2[2] = {0.0, 0.0};
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int iy = i / nx, ix = i - iy * nx;
+                const double2 pi = p[i];
+                const double2 lp = L.apply2(p, i, ix, iy, dTc);
+                const double2 qi = make_double2(lk.x * pi.x - lk.y * pi.y + lp.x,
+                                                lk.x * pi.y + lk.y * pi.x + lp.y);
+                q[i] = qi;
+                v2[0] = fma(pi.x, qi.x, fma(-pi.y, qi.y, v2[0]));
+                v2[1] = fma(pi.x, qi.y, fma(pi.y, qi.x, v2[1]));
+            }
+            block_sum<2>(v2, red, ph);
+            double pqr = v2[0], pqi = v2[1];
+            for (;;) {
+                // a = rz / pq
+                const double den = pqr * pqr + pqi * pqi;
+                const double ar = (rzr * pqr + rzi * pqi) / den, ai = (rzi * pqr - rzr * pqi) / den;
+                double u3[3] = {0.0, 0.0, 0.0};  // ||r||^2, r.z
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const double2 pi = p[i], qi = q[i], dv = dinv[i];
+                    double2 xi = x[i], ri = r[i];
+                    xi.x = fma(ar, pi.x, fma(-ai, pi.y, xi.x));
+                    xi.y = fma(ar, pi.y, fma(ai, pi.x, xi.y));
+                    ri.x = fma(-ar, qi.x, fma(ai, qi.y, ri.x));
+                    ri.y = fma(-ar, qi.y, fma(-ai, qi.x, ri.y));
+                    const double2 zi = make_double2(dv.x * ri.x - dv.y * ri.y, dv.x * ri.y + dv.y * ri.x);
+                    x[i] = xi;
+                    r[i] = ri;
+                    z[i] = zi;
+                    u3[0] = fma(ri.x, ri.x, fma(ri.y, ri.y, u3[0]));
+                    u3[1] = fma(ri.x, zi.x, fma(-ri.y, zi.y, u3[1]));
+                    u3[2] = fma(ri.x, zi.y, fma(ri.y, zi.x, u3[2]));
+                }
+                block_sum<3>(u3, red, ph);
+                ++it;
+                if (!(u3[0] > lim)) break;
+                if (it >= maxit) {
+                    failed = true;
+                    break;
+                }
+                // beta = rz_new / rz
+                const double dd = rzr * rzr + rzi * rzi;
+                const double br = (u3[1] * rzr + u3[2] * rzi) / dd, bi = (u3[2] * rzr - u3[1] * rzi) / dd;
+                rzr = u3[1];
+                rzi = u3[2];
+                double w2[2] = {0.0, 0.0};
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const int iy = i / nx, ix = i - iy * nx;
+                    const double2 zi = z[i], po = p[i], qo = q[i];
+                    const double2 lz = L.apply2(z, i, ix, iy, dTc);
+                    const double2 mz = make_double2(lk.x * zi.x - lk.y * zi.y + lz.x,
+                                                    lk.x * zi.y + lk.y * zi.x + lz.y);
+                    const double2 pn = make_double2(fma(br, po.x, fma(-bi, po.y, zi.x)),
+                                                    fma(br, po.y, fma(bi, po.x, zi.y)));
+                    const double2 qn = make_double2(fma(br, qo.x, fma(-bi, qo.y, mz.x)),
+                                                    fma(br, qo.y, fma(bi, qo.x, mz.y)));
+                    p[i] = pn;
+                    q[i] = qn;
+                    w2[0] = fma(pn.x, qn.x, fma(-pn.y, qn.y, w2[0]));
+                    w2[1] = fma(pn.x, qn.y, fma(pn.y, qn.x, w2[1]));
+                }
+                block_sum<2>(w2, red, ph);
+                pqr = w2[0];
+                pqi = w2[1];
+            }
+        }
+        its_total += it;
+        for (int i = threadIdx.x; i < n; i += blockDim.x) pio[(s * n + i) * K + k] = x[i];
+        if (failed && threadIdx.x == 0) ifail[s] = 1;
+    }
+    if (threadIdx.x == 0 && itcount && its_total) atomicAdd(itcount, its_total);
+}
+
+int num_sms() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev);
+    return v > 0 ? v : 1;
+}
+
+int max_dyn_smem() {
+    int dev = 0, v = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&v, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    return v;
+}
+
+// Doubles of working storage per system.
+int64_t per_system(int kind, int nx) {
+    const int64_t n = (int64_t)nx * nx, nf = 2 * (int64_t)nx * (nx + 1);
+    return kind == 0 ? nf + 6 * n : nf + (nf & 1) + 12 * n;
+}
+
+}  // namespace
+
+Plan2D plan_2d(int kind, int nx, int64_t items) {
+    Plan2D pl;
+    const int64_t per = per_system(kind, nx);
+    const int64_t bytes = per * 8;
+    const int sm = num_sms();
+    const int static_bytes = 2 * 3 * 32 * 8;
+    if (bytes + static_bytes <= max_dyn_smem()) {
+        pl.smem = (int)bytes;
+        int occ = 0;
+        if (kind == 0) {
+            cudaFuncSetAttribute(k_fine2d, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fine2d, kThreads2d, pl.smem);
+        } else {
+            cudaFuncSetAttribute(k_cgc_solve2d, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgc_solve2d, kThreads2d, pl.smem);
+        }
+        pl.grid = (int64_t)sm * (occ > 0 ? occ : 1);
+        pl.per_cta = 0;
+    } else {
+        // working storage in global memory: two CTAs per SM, one slice each
+        pl.smem = 0;
+        pl.grid = 2 * (int64_t)sm;
+        pl.per_cta = per + (per & 1);
+    }
+    if (pl.grid > items) pl.grid = items;
+    if (pl.grid < 1) pl.grid = 1;
+    pl.scratch_doubles = pl.per_cta * pl.grid;
+    return pl;
+}
+
+void launch_fine2d(const Plan2D& pl, int64_t S, int N, int nx, int J, double dtc, double dtf,
+                   double alpha, int mode, const double* U, const double* u0, const double* wdt,
+                   double rtol, int maxit, double* out, const int* active, int* ifail,
+                   unsigned long long* itcount, double* scratch, cudaStream_t st) {
+    if (S == 0) return;
+    k_fine2d<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
+        S, N, nx, J, dtc, dtf, alpha, mode, U, u0, wdt, rtol * rtol, maxit, out, active, ifail,
+        itcount, pl.per_cta ? scratch : nullptr, pl.per_cta);
+}
+
+void launch_cgc_solve2d(const Plan2D& pl, int64_t S, int K, int nx, double dTc,
+                        const double2* lam, const double* wdT, double rtol, int maxit,
+                        Cplx<double>* p, const int* active, int* ifail,
+                        unsigned long long* itcount, double* scratch, cudaStream_t st) {
+    if (S == 0) return;
+    k_cgc_solve2d<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
+        S, K, nx, dTc, lam, wdT, rtol * rtol, maxit, reinterpret_cast<double2*>(p), active, ifail,
+        itcount, pl.per_cta ? scratch : nullptr, pl.per_cta);
+}
+
+}  // namespace klecgc

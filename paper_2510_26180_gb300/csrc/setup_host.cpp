@@ -60,6 +60,37 @@ void kl_modes_1d(double corr_len, double sigma, int count, std::vector<double>& 
     for (double w : omega) lam.push_back(2.0 * c * sigma * sigma / (w * w + c * c));
 }
 
+void kl_modes_2d(double corr_len, double sigma, int count, std::vector<double>& lam,
+                 std::vector<int>& mi, std::vector<int>& mj, std::vector<double>& mu,
+                 std::vector<double>& omega, std::vector<int>& parity) {
+    // The separable kernel sigma^2 exp(-|x1-y1|/l) exp(-|x2-y2|/l) has the
+    // eigenpairs (sigma^2 mu_i mu_j, phi_i(x1) phi_j(x2)) of the unit-variance
+    // 1D pairs.  A pair among the top `count` has both indices below count.
+    const int n1 = count + 2;
+    kl_modes_1d(corr_len, 1.0, n1, mu, omega, parity);
+    struct Pair {
+        double lam;
+        int i, j;
+    };
+    std::vector<Pair> all;
+    for (int i = 0; i < n1; ++i)
+        for (int j = 0; j < n1; ++j) all.push_back({sigma * sigma * (mu[i] * mu[j]), i, j});
+    // descending eigenvalue; (i, j) and (j, i) tie exactly: smaller i + j, then smaller i
+    std::stable_sort(all.begin(), all.end(), [](const Pair& a, const Pair& b) {
+        if (a.lam != b.lam) return a.lam > b.lam;
+        if (a.i + a.j != b.i + b.j) return a.i + a.j < b.i + b.j;
+        return a.i < b.i;
+    });
+    lam.clear();
+    mi.clear();
+    mj.clear();
+    for (int m = 0; m < count; ++m) {
+        lam.push_back(all[m].lam);
+        mi.push_back(all[m].i);
+        mj.push_back(all[m].j);
+    }
+}
+
 double kl_phi_1d(double x, double w, int parity) {
     double t = x - 0.5;
     if (parity == 0) return std::cos(w * t) / std::sqrt(0.5 + std::sin(w) / (2.0 * w));

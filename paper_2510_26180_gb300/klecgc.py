@@ -24,7 +24,8 @@ EXPORTS = ["klecgc_setup", "klecgc_solve", "klecgc_field", "klecgc_guess", "klec
            "klecgc_cgc_apply", "klecgc_reference", "klecgc_info", "klecgc_free",
            "klecgc_status_string", "klecgc_last_error", "klecgc_profile_enable",
            "klecgc_profile_read", "klecgc_reference_noalloc", "klecgc_mlp_set", "klecgc_mlp_get",
-           "klecgc_mlp_loss_grad", "klecgc_mlp_train", "klecgc_mlp_guess", "klecgc_downsample"]
+           "klecgc_mlp_loss_grad", "klecgc_mlp_train", "klecgc_mlp_guess", "klecgc_downsample",
+           "klecgc_set_krylov", "klecgc_krylov_stats"]
 PROFILE_CLASSES = ["field", "factors", "guess", "fine", "cgc_fwd", "cgc_solve", "cgc_inv",
                    "conv", "layout"]
 
@@ -93,6 +94,8 @@ def load() -> ctypes.CDLL:
         "klecgc_mlp_guess": [P, P, I64, P, P],
         "klecgc_downsample": [P, P, I64, I32, P, P],
         "klecgc_profile_read": [P, ctypes.POINTER(Profile)],
+        "klecgc_set_krylov": [P, D, D, I32],
+        "klecgc_krylov_stats": [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -213,6 +216,16 @@ class Solver:
     def reference(self, xi, S, N, J, U_out, stream=None) -> int:
         return _check(self.lib.klecgc_reference(self.h, _ptr(xi, np.float64), S, N, J,
                                                  _ptr(U_out, np.float64), _stream(stream)))
+
+    # ---- 2D Krylov solves
+    def set_krylov(self, rtol_fine, rtol_cgc, maxit) -> int:
+        return _check(self.lib.klecgc_set_krylov(self.h, rtol_fine, rtol_cgc, maxit))
+
+    def krylov_stats(self) -> tuple:
+        """(fine, CGC) Krylov iterations summed over the systems of the last call."""
+        a, b = ctypes.c_int64(), ctypes.c_int64()
+        _check(self.lib.klecgc_krylov_stats(self.h, ctypes.byref(a), ctypes.byref(b)))
+        return a.value, b.value
 
     # ---- learned guess
     def mlp_n_params(self) -> int:

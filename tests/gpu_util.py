@@ -26,3 +26,10 @@ def rel(a, b):
     a = np.asarray(a)
     b = np.asarray(b)
     return float(np.linalg.norm((a - b).ravel()) / np.linalg.norm(b.ravel()))
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_setup2d(name, **over):
+    from oracle.klecgc import Setup2D
+    w = workload(name, **over)
+    return Setup2D(w)
