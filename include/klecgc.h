@@ -304,6 +304,19 @@ klecgc_status klecgc_set_krylov(klecgc_ctx* ctx, double rtol_fine, double rtol_c
  * F and for the CGC solves.  Either pointer may be NULL. */
 klecgc_status klecgc_krylov_stats(const klecgc_ctx* ctx, int64_t* its_fine, int64_t* its_cgc);
 
+/*
+ * Context persistence (a library facility; the paper's offline stage is
+ * re-run otherwise).  klecgc_save writes the problem, the surrogate tables
+ * (input-KL basis, u0, gPC multi-indices, ubar, W), the Krylov settings and,
+ * when set, the learned network to `path` (a binary file of this library's
+ * own format, native byte order).  klecgc_load creates a context on the
+ * current CUDA device from such a file: its guesses and solves equal those
+ * of the saved context.  Errors: INVALID_ARG (cannot open, not a context
+ * file, inconsistent or truncated), OUT_OF_MEMORY, CUDA.
+ */
+klecgc_status klecgc_save(const klecgc_ctx* ctx, const char* path);
+klecgc_status klecgc_load(const char* path, klecgc_ctx** out, void* stream);
+
 /* Sizes of the context (M_Q, P, ...). */
 klecgc_status klecgc_info(const klecgc_ctx* ctx, klecgc_info_t* out);
 

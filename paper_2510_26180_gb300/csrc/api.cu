@@ -415,6 +415,34 @@ klecgc_status scale_tables(klecgc_ctx* ctx, int N, double alpha, cudaStream_t st
     return KLECGC_OK;
 }
 
+// Coarse sweep U^0_n = G(U^0_{n-1}), U^0_0 = u0 (the initial guess by G alone,
+// Section 3.1): N backward-Euler steps of dT per sample into U (internal
+// layout).  field: the coefficient a [S][nx+1] (1D) or the weights dT a / h^2
+// [S][nf] (2D).
+klecgc_status coarse_guess_internal(klecgc_ctx* ctx, int64_t S, int N, double dT,
+                                    const double* field, double* U, cudaStream_t st) {
+    const double react = ctx->prob.reaction, forcing = ctx->prob.forcing;
+    if (ctx->dim == 1) {
+        WS(FineCoef64, fc, "coarse64", S * (int64_t)(ctx->nx + 1));
+        WS(double, scr, "seq_scratch", S * (int64_t)ctx->nx);
+        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_fine_factors(field, S, ctx->nx, ctx->h, dT, react, fc, nullptr, st); });
+        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_fine_sequential(S, N, ctx->nx, 1, dT * forcing, ctx->u0, fc, scr, U, st); });
+    } else {
+        WS(int, act, "act_all", S);
+        WS(int, gfail, "coarse_fail", S);
+        TRY(cudaMemsetAsync(act, 0xff, S * sizeof(int), st));
+        const Plan2D pl = plan_2d(0, ctx->nx, S);
+        WS(double, scr, "k2d_scratch_g", pl.scratch_doubles);
+        // a guess needs no tight solve: its error only costs iterations
+        ctx->launch(KLECGC_K_GUESS, st, [&] {
+            launch_fine2d(pl, S, N, ctx->nx, 1, dT * react, dT * forcing, 0.0, 1, nullptr, ctx->u0,
+                          field, ctx->kry_rtol_fine, ctx->kry_maxit, U, act, gfail, nullptr, scr, st);
+        });
+    }
+    TRY(cudaGetLastError());
+    return KLECGC_OK;
+}
+
 // U^0 = ubar + psi(xi) W into U (internal layout [S][nx][N]).
 klecgc_status gpc_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S, bool fp64,
                                  double* U, cudaStream_t st) {
@@ -647,6 +675,175 @@ void klecgc_free(klecgc_ctx* ctx) {
     cudaSetDevice(ctx->device);
     delete ctx;
     cudaSetDevice(cur);
+}
+
+// ------------------------------------------------------------ save / load
+// File: magic, version, klecgc_problem, sizes, then the device tables as
+// raw arrays in native byte order (basis, u0, degrees, ubar, W) and, when a network
+// is set, its parameters and output normalization.
+}  // extern "C"
+namespace {
+constexpr char kMagic[8] = {'K', 'L', 'E', 'C', 'G', 'C', 'v', '1'};
+constexpr int32_t kVersion = 1;
+
+struct FileHead {
+    char magic[8];
+    int32_t version;
+    int32_t dim, nx, N, J, M, P, MQ, p, ns, nf;
+    int32_t mlp_ready, kry_maxit;
+    double h, dT, lambda_sum, lambda_kept, kry_rtol_fine, kry_rtol_cgc;
+    int64_t mlp_P;
+    int32_t mlp_D, pad;
+};
+
+template <typename T>
+bool put_dev(FILE* f, const T* d, size_t n) {
+    std::vector<T> h(n);
+    if (n && cudaMemcpy(h.data(), d, n * sizeof(T), cudaMemcpyDeviceToHost) != cudaSuccess) return false;
+    return std::fwrite(h.data(), sizeof(T), n, f) == n;
+}
+
+template <typename T>
+klecgc_status get_dev(FILE* f, klecgc_ctx* ctx, T** d, size_t n) {
+    std::vector<T> h(n);
+    if (std::fread(h.data(), sizeof(T), n, f) != n) return fail(KLECGC_E_INVALID_ARG, "truncated file");
+    TRY(ctx->alloc_owned(d, n));
+    TRY(cudaMemcpy(*d, h.data(), n * sizeof(T), cudaMemcpyHostToDevice));
+    return KLECGC_OK;
+}
+}  // namespace
+extern "C" {
+
+klecgc_status klecgc_save(const klecgc_ctx* ctx, const char* path) {
+    set_error("");
+    if (!ctx || !path || !ctx->W) return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return fail(KLECGC_E_INVALID_ARG, std::string("cannot open ") + path);
+    FileHead hd{};
+    std::memcpy(hd.magic, kMagic, 8);
+    hd.version = kVersion;
+    hd.dim = ctx->dim;
+    hd.nx = ctx->nx;
+    hd.N = ctx->N;
+    hd.J = ctx->J;
+    hd.M = ctx->M;
+    hd.P = ctx->P;
+    hd.MQ = ctx->MQ;
+    hd.p = ctx->p;
+    hd.ns = ctx->ns;
+    hd.nf = ctx->nf;
+    hd.mlp_ready = ctx->mlp.ready ? 1 : 0;
+    hd.kry_maxit = ctx->kry_maxit;
+    hd.h = ctx->h;
+    hd.dT = ctx->dT;
+    hd.lambda_sum = ctx->lambda_sum;
+    hd.lambda_kept = ctx->lambda_kept;
+    hd.kry_rtol_fine = ctx->kry_rtol_fine;
+    hd.kry_rtol_cgc = ctx->kry_rtol_cgc;
+    hd.mlp_P = ctx->mlp.ready ? ctx->mlp.P : 0;
+    hd.mlp_D = ctx->mlp.ready ? ctx->mlp.D : 0;
+    int cur = 0;
+    cudaGetDevice(&cur);
+    cudaSetDevice(ctx->device);
+    const size_t NC = (size_t)ctx->ns * ctx->N;
+    bool ok = std::fwrite(&hd, sizeof(hd), 1, f) == 1 &&
+              std::fwrite(&ctx->prob, sizeof(ctx->prob), 1, f) == 1 &&
+              put_dev(f, ctx->basis, (size_t)ctx->M * ctx->nf) && put_dev(f, ctx->u0, ctx->ns) &&
+              put_dev(f, ctx->degrees, (size_t)ctx->P * ctx->M) && put_dev(f, ctx->ubar, NC) &&
+              put_dev(f, ctx->W, (size_t)ctx->P * NC);
+    if (ok && ctx->mlp.ready)
+        ok = put_dev(f, ctx->mlp.theta, ctx->mlp.P) && put_dev(f, ctx->mlp.mean, ctx->mlp.D) &&
+             put_dev(f, ctx->mlp.stdv, ctx->mlp.D);
+    cudaSetDevice(cur);
+    ok = (std::fclose(f) == 0) && ok;
+    return ok ? KLECGC_OK : fail(KLECGC_E_CUDA, std::string("writing ") + path + " failed");
+}
+
+klecgc_status klecgc_load(const char* path, klecgc_ctx** out, void* stream) {
+    set_error("");
+    if (!path || !out) return fail(KLECGC_E_INVALID_ARG, "NULL argument");
+    *out = nullptr;
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return fail(KLECGC_E_INVALID_ARG, std::string("cannot open ") + path);
+    struct Closer {
+        FILE* f;
+        ~Closer() { std::fclose(f); }
+    } closer{f};
+    FileHead hd{};
+    klecgc_problem pr{};
+    if (std::fread(&hd, sizeof(hd), 1, f) != 1 || std::memcmp(hd.magic, kMagic, 8) != 0 ||
+        hd.version != kVersion || std::fread(&pr, sizeof(pr), 1, f) != 1)
+        return fail(KLECGC_E_INVALID_ARG, std::string(path) + " is not a klecgc context file");
+    const bool sane = (hd.dim == 1 || hd.dim == 2) && hd.nx >= 1 && hd.nx <= 1 << 20 &&
+                      pow2_in_range(hd.N) && hd.M >= 1 && hd.M <= 4096 && hd.P >= 1 &&
+                      hd.MQ >= 1 && hd.ns == (hd.dim == 1 ? hd.nx : hd.nx * hd.nx) &&
+                      hd.nf == (hd.dim == 1 ? hd.nx + 1 : 2 * hd.nx * (hd.nx + 1)) &&
+                      pr.dim == hd.dim && pr.nx == hd.nx && pr.N == hd.N && pr.M == hd.M &&
+                      (int64_t)hd.P * hd.ns * hd.N < ((int64_t)1 << 36) &&
+                      (hd.mlp_ready == 0 || (hd.mlp_P > 0 && hd.mlp_D == 64 * hd.N && hd.dim == 1));
+    if (!sane) return fail(KLECGC_E_INVALID_ARG, std::string(path) + ": inconsistent header");
+    cudaStream_t st = (cudaStream_t)stream;
+    klecgc_ctx* ctx = new klecgc_ctx();
+    auto bail = [&](klecgc_status s) {
+        delete ctx;
+        return s;
+    };
+    ctx->prob = pr;
+    cudaGetDevice(&ctx->device);
+    ctx->dim = hd.dim;
+    ctx->nx = hd.nx;
+    ctx->N = hd.N;
+    ctx->J = hd.J;
+    ctx->M = hd.M;
+    ctx->P = hd.P;
+    ctx->MQ = hd.MQ;
+    ctx->p = hd.p;
+    ctx->ns = hd.ns;
+    ctx->nf = hd.nf;
+    ctx->h = hd.h;
+    ctx->dT = hd.dT;
+    ctx->lambda_sum = hd.lambda_sum;
+    ctx->lambda_kept = hd.lambda_kept;
+    ctx->kry_rtol_fine = hd.kry_rtol_fine;
+    ctx->kry_rtol_cgc = hd.kry_rtol_cgc;
+    ctx->kry_maxit = hd.kry_maxit;
+    if (ensure_twiddles(ctx->device) != cudaSuccess) return bail(fail(KLECGC_E_CUDA, "twiddles"));
+    const size_t NC = (size_t)ctx->ns * ctx->N;
+    klecgc_status s;
+    if ((s = get_dev(f, ctx, &ctx->basis, (size_t)ctx->M * ctx->nf)) != KLECGC_OK ||
+        (s = get_dev(f, ctx, &ctx->u0, ctx->ns)) != KLECGC_OK ||
+        (s = get_dev(f, ctx, &ctx->degrees, (size_t)ctx->P * ctx->M)) != KLECGC_OK ||
+        (s = get_dev(f, ctx, &ctx->ubar, NC)) != KLECGC_OK ||
+        (s = get_dev(f, ctx, &ctx->W, (size_t)ctx->P * NC)) != KLECGC_OK)
+        return bail(s);
+    if (ctx->alloc_owned(&ctx->W32, (size_t)ctx->P * NC) != cudaSuccess)
+        return bail(fail(KLECGC_E_OUT_OF_MEMORY, "W32"));
+    launch_to_float(ctx->W, ctx->W32, (int64_t)ctx->P * NC, st);
+    if (hd.mlp_ready) {
+        if ((s = mlp_alloc(ctx)) != KLECGC_OK) return bail(s);
+        MlpState& q = ctx->mlp;
+        if (q.P != hd.mlp_P || q.D != hd.mlp_D)
+            return bail(fail(KLECGC_E_INVALID_ARG, "network size does not match the problem"));
+        std::vector<float> th(q.P), mu(q.D), sd(q.D), inv(q.D);
+        if (std::fread(th.data(), 4, q.P, f) != (size_t)q.P || std::fread(mu.data(), 4, q.D, f) != (size_t)q.D ||
+            std::fread(sd.data(), 4, q.D, f) != (size_t)q.D)
+            return bail(fail(KLECGC_E_INVALID_ARG, "truncated file"));
+        for (int c = 0; c < q.D; ++c) {
+            if (!(sd[c] > 0)) return bail(fail(KLECGC_E_INVALID_ARG, "bad output normalization"));
+            inv[c] = 1.f / sd[c];
+        }
+        if (cudaMemcpy(q.theta, th.data(), q.P * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(q.mean, mu.data(), q.D * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(q.stdv, sd.data(), q.D * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(q.inv_std, inv.data(), q.D * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return bail(fail(KLECGC_E_CUDA, "network upload"));
+        launch_f32_to_bf16(q.P, q.theta, q.thb, st);
+        q.ready = true;
+    }
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
+        return bail(fail(KLECGC_E_CUDA, "upload"));
+    *out = ctx;
+    return KLECGC_OK;
 }
 
 klecgc_status klecgc_info(const klecgc_ctx* ctx, klecgc_info_t* out) {
@@ -1318,7 +1515,6 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
         return fail(KLECGC_E_INVALID_ARG, "the gPC and learned guesses need the setup's N");
     if (guess == KLECGC_GUESS_MLP && !ctx->mlp.ready)
         return fail(KLECGC_E_INVALID_ARG, "no network (klecgc_mlp_set / klecgc_mlp_train)");
-    if (guess == KLECGC_GUESS_COARSE) return fail(KLECGC_E_UNSUPPORTED, "coarse guess not built");
     if (ctx->dim == 2 && precision != KLECGC_FP64) return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 only");
     klecgc_status s = check_dT(ctx, N, dT);
     if (s != KLECGC_OK) return s;
@@ -1361,6 +1557,9 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
     } else if (guess == KLECGC_GUESS_MLP) {
     } else if (guess == KLECGC_GUESS_ZERO) {
         TRY(cudaMemsetAsync(U, 0, NS * sizeof(double), st));
+    } else if (guess == KLECGC_GUESS_COARSE) {
+        if ((s = coarse_guess_internal(ctx, S, N, dT, ctx->dim == 2 ? wdT2 : op.a, U, st)) != KLECGC_OK)
+            return s;
     } else {
         if ((s = import_batch(ctx, U_guess, S, N, U, st)) != KLECGC_OK) return s;
     }

@@ -25,7 +25,7 @@ EXPORTS = ["klecgc_setup", "klecgc_solve", "klecgc_field", "klecgc_guess", "klec
            "klecgc_status_string", "klecgc_last_error", "klecgc_profile_enable",
            "klecgc_profile_read", "klecgc_reference_noalloc", "klecgc_mlp_set", "klecgc_mlp_get",
            "klecgc_mlp_loss_grad", "klecgc_mlp_train", "klecgc_mlp_guess", "klecgc_downsample",
-           "klecgc_set_krylov", "klecgc_krylov_stats"]
+           "klecgc_set_krylov", "klecgc_krylov_stats", "klecgc_save", "klecgc_load"]
 PROFILE_CLASSES = ["field", "factors", "guess", "fine", "cgc_fwd", "cgc_solve", "cgc_inv",
                    "conv", "layout"]
 
@@ -95,6 +95,8 @@ def load() -> ctypes.CDLL:
         "klecgc_downsample": [P, P, I64, I32, P, P],
         "klecgc_profile_read": [P, ctypes.POINTER(Profile)],
         "klecgc_set_krylov": [P, D, D, I32],
+        "klecgc_save": [P, ctypes.c_char_p],
+        "klecgc_load": [ctypes.c_char_p, ctypes.POINTER(P), P],
         "klecgc_krylov_stats": [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     }
     for name, args in sig.items():
@@ -161,6 +163,20 @@ class Solver:
         _check(self.lib.klecgc_setup(ctypes.byref(problem), _ptr(xi_train, np.float64),
                                      ctypes.byref(h), _stream(stream)))
         self.h = h
+
+    @classmethod
+    def load(cls, path: str, stream=None) -> "Solver":
+        """A solver from a context file written by save()."""
+        self = cls.__new__(cls)
+        self.lib = load()
+        self.problem = None
+        h = ctypes.c_void_p()
+        _check(self.lib.klecgc_load(os.fsencode(path), ctypes.byref(h), _stream(stream)))
+        self.h = h
+        return self
+
+    def save(self, path: str) -> int:
+        return _check(self.lib.klecgc_save(self.h, os.fsencode(path)))
 
     def close(self):
         if getattr(self, "h", None):

@@ -43,3 +43,21 @@ def test_package_does_not_import_oracle():
                     assert not any(a.name.split(".")[0] == "oracle" for a in node.names), fn
                 if isinstance(node, ast.ImportFrom):
                     assert (node.module or "").split(".")[0] != "oracle", fn
+
+
+def test_load_rejects_files_that_are_not_contexts(tmp_path):
+    # klecgc_load validates the file header before any CUDA call
+    import ctypes
+    import paper_2510_26180_gb300 as pkg
+    lib = pkg.load()
+    h = ctypes.c_void_p()
+    missing = os.fsencode(str(tmp_path / "missing.ctx"))
+    assert lib.klecgc_load(missing, ctypes.byref(h), None) == pkg.E_INVALID_ARG
+    assert b"cannot open" in lib.klecgc_last_error()
+    junk = tmp_path / "junk.ctx"
+    junk.write_bytes(b"not a context file" * 20)
+    assert lib.klecgc_load(os.fsencode(str(junk)), ctypes.byref(h), None) == pkg.E_INVALID_ARG
+    assert h.value is None
+    bad = tmp_path / "short.ctx"
+    bad.write_bytes(b"KLECGCv1")
+    assert lib.klecgc_load(os.fsencode(str(bad)), ctypes.byref(h), None) == pkg.E_INVALID_ARG
