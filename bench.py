@@ -34,6 +34,12 @@ PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_defect": 2}
 DTYPES = {"fp64": "f64", "mixed": "f32+f64", "mixed_defect": "f32+f64"}
 FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA x max clock
 FP64_ALU_PEAK = 1.25                              # TFLOP/s, GB300 nominal FP64
+# DRAM bytes per point (read + write) of the mixed-defect kernels, from one ncu
+# capture each on 512 samples of heat1d_nx1023 (profiles/k_fine32_*.md,
+# profiles/k_cgc_*.md); the roofline's traffic scales them to a launch by its
+# points.  Valid while those kernels are unchanged.
+MEASURED_TRAFFIC_B_PER_POINT = {"fine": 236.2e6 / 33.52e6, "cgc_fwd": 1047.6e6 / 33.52e6,
+                                "cgc_solve": 725.9e6 / 33.52e6, "cgc_inv": 751.0e6 / 33.52e6}
 
 
 def peaks():
@@ -44,14 +50,26 @@ def peaks():
     return 6800.0, "fallback"
 
 
-def workload_desc(w, S, precision):
-    return {"workload": f"{w.name}: 1D u_t=(a u_x)_x, a=exp(KL, M={w.M}), Nx={w.nx}, N={w.N}, "
-                        f"J={w.J}, gPC p={w.gpc_degree}, alpha={w.alpha}, tol={w.tol}",
+def workload_desc(w, S, precision, overrides=None):
+    if w.dim == 2:
+        name = (f"{w.name}: 2D u_t=div(a grad u)-{w.reaction:g}u+{w.forcing:g} on (0,1)^2, "
+                f"a=exp(separable KL, M={w.M}), {w.nx}^2 interior points, N={w.N}, J={w.J}, "
+                f"gPC p={w.gpc_degree}, alpha={w.alpha}, tol={w.tol}, Krylov rtol 1e-10")
+    else:
+        name = (f"{w.name}: 1D u_t=(a u_x)_x, a=exp(KL, M={w.M}), Nx={w.nx}, N={w.N}, "
+                f"J={w.J}, gPC p={w.gpc_degree}, alpha={w.alpha}, tol={w.tol}")
+    d = {"workload": name,
             "samples_per_gpu": S, "nx": w.nx, "N": w.N, "J": w.J, "M": w.M,
             "gpc_degree": w.gpc_degree, "n_train": w.n_train, "alpha": w.alpha, "tol": w.tol,
             "precision": precision,
-            "l2": "inputs larger than L2: per-step working set ~12 GB (U, r, p, factors)",
+            "l2": "inputs larger than L2: per-step working set ~12 GB (U, r, p, factors)"
+                  if w.dim == 1 else
+                  f"per-step state {S * w.N * w.nx ** 2 * 8 * 4 / 1e9:.2f} GB (U, r, p); "
+                  "L2 not flushed",
             "parallelism": "sample shards per GPU, no collective"}
+    if overrides:
+        d["overrides"] = overrides
+    return d
 
 
 class ClockSampler:
@@ -119,13 +137,13 @@ def oracle_pool(w, cores):
     Worker processes run single-threaded BLAS so that `cores` processes use
     `cores` hardware threads."""
     import multiprocessing as mp
-    from oracle.klecgc import Setup1D
+    from oracle.klecgc import Setup1D, Setup2D
     saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
                                             "MKL_NUM_THREADS")}
     for k in saved:
         os.environ[k] = "1"
     try:
-        setup = Setup1D(w, processes=cores)
+        setup = (Setup2D if w.dim == 2 else Setup1D)(w, processes=cores)
         pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_init, initargs=(setup,))
     finally:
         for k, v in saved.items():
@@ -168,7 +186,8 @@ def run_reference(args, w):
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_desc(w, n_sub, "fp64"), "mean_iters": float(np.mean(iters)),
+            "config": workload_desc(w, n_sub, "fp64", args.overrides),
+            "mean_iters": float(np.mean(iters)),
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores,
                              "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
@@ -178,10 +197,39 @@ def run_reference(args, w):
 
 
 # ---------------------------------------------------------------- GPU arm
+def traffic_per_launch(cls, prec, points, launches):
+    """Measured DRAM bytes per launch (mixed-defect kernels only), else None."""
+    if prec != "mixed_defect" or cls not in MEASURED_TRAFFIC_B_PER_POINT:
+        return None
+    return MEASURED_TRAFFIC_B_PER_POINT[cls] * points / max(launches, 1)
+
+
+def roofline_2d(cls, ms, launches, units):
+    """2D FP64 Krylov kernels: FP64 operations (an FMA counts 2) per unknown.
+
+    CG iteration of F: 9 (x, r, z updates, two dot products) + 20 (stencil
+    apply of z, p and q recurrences, p.q); per step 38 more (initial residual
+    and the first q = M p).  COCG iteration: 34 + 58, complex."""
+    ns = units["ns"]
+    if cls == "fine":
+        flops = (29.0 * units["kry_fine"] + 38.0 * units["fine_steps"]) * ns
+    elif cls == "cgc_solve":
+        flops = 92.0 * units["kry_cgc"] * ns
+    else:
+        return None
+    ach = flops / (ms / 1e3) / 1e12
+    return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK,
+            "unit": "TFLOP/s", "frac": ach / FP64_ALU_PEAK, "traffic": None,
+            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s",
+            "work": f"{flops / max(launches, 1):.3e} FP64 flop per launch"}
+
+
 def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
     """Algorithmic work of kernel class `cls` over the timed region."""
     if ms <= 0:
         return None
+    if w.dim == 2:
+        return roofline_2d(cls, ms, launches, units)
     row_steps = units["row_steps"]
     pts = units["points"]
     if cls == "fine":
@@ -193,7 +241,7 @@ def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
             peak, unit = FP32_ALU_PEAK, "TFLOP/s"
         ach = flops / (ms / 1e3) / 1e12
         return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": peak, "unit": unit,
-                "frac": ach / peak, "traffic": None,
+                "frac": ach / peak, "traffic": traffic_per_launch(cls, prec, pts, launches),
                 "peak_source": "derived: 152 SMs x lanes x 2 x 2070 MHz" if prec != "fp64"
                 else "nominal GB300 FP64 1.25 TFLOP/s",
                 "work": f"{flops / max(launches, 1):.3e} flop per launch"}
@@ -208,7 +256,8 @@ def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
     byts = per_pt * pts
     ach = byts / (ms / 1e3) / 1e9
     return {"kernel": cls, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
-            "frac": ach / hbm_peak, "traffic": None, "peak_source": peak_kind,
+            "frac": ach / hbm_peak, "traffic": traffic_per_launch(cls, prec, pts, launches),
+            "peak_source": peak_kind,
             "work": f"{byts / max(launches, 1):.3e} bytes per launch"}
 
 
@@ -241,7 +290,8 @@ def run_gpu(args, w):
     info = solver.info()
     xi_h = draw_xi(S, w.M, w.seed + 1000 * rank)
     xi = torch.from_numpy(xi_h).to(dev)
-    U = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev)
+    ns = w.nx ** w.dim
+    U = torch.empty((S, w.N, ns), dtype=torch.float64, device=dev)
     it = torch.empty(S, dtype=torch.int32, device=dev)
     stt = torch.empty(S, dtype=torch.int32, device=dev)
     dT = w.T / w.N
@@ -261,9 +311,15 @@ def run_gpu(args, w):
     if world > 1:
         dist.barrier()
     torch.cuda.synchronize()
+    # inputs smaller than L2 (129 MB): overwrite a 256 MB buffer between steps
+    flush = None
+    if S * w.N * ns * 8 * 4 < 2 * 129e6:
+        flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(args.steps):
+    for i in range(args.steps):
+        if flush is not None and i:
+            flush.fill_(i & 0xff)
         step()
     e1.record(stream)
     torch.cuda.synchronize()
@@ -272,6 +328,7 @@ def run_gpu(args, w):
     clocks = sampler.stop()
     prof = solver.profile_read()
     solver.profile_enable(False)
+    kry = solver.krylov_stats() if w.dim == 2 else (0, 0)   # of the last timed solve
     ms = e0.elapsed_time(e1) / args.steps
 
     # accuracy of the last timed step against U* (FP64 reference kernel)
@@ -282,8 +339,8 @@ def run_gpu(args, w):
     status = stt.cpu().numpy()
     ok = (status == 0) & (err <= 1e-6)
     n_ok = int(ok.sum())
-    row_steps = float(np.clip(iters, 0, None).sum()) * w.N * w.nx * w.J * args.steps
-    points = float(np.clip(iters, 0, None).sum()) * w.N * w.nx * args.steps
+    row_steps = float(np.clip(iters, 0, None).sum()) * w.N * ns * w.J * args.steps
+    points = float(np.clip(iters, 0, None).sum()) * w.N * ns * args.steps
 
     ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
     nok_t = torch.tensor([float(n_ok)], dtype=torch.float64, device=dev)
@@ -295,7 +352,7 @@ def run_gpu(args, w):
 
     # end-to-end through the C ABI with pinned host buffers (copies timed)
     xi_pin = torch.from_numpy(xi_h).pin_memory()
-    U_pin = torch.empty((S, w.N, w.nx), dtype=torch.float64).pin_memory()
+    U_pin = torch.empty((S, w.N, ns), dtype=torch.float64).pin_memory()
     it_pin = torch.empty(S, dtype=torch.int32).pin_memory()
     st_pin = torch.empty(S, dtype=torch.int32).pin_memory()
     step(xin=xi_pin, Uo=U_pin, ito=it_pin, sto=st_pin)
@@ -336,7 +393,9 @@ def run_gpu(args, w):
                 "speedup_of_headline": value / (ok64 * world / (ms64 / 1e3)) if ok64 else None}
 
     hbm_peak, peak_kind = peaks()
-    units = {"row_steps": row_steps, "points": points}
+    units = {"row_steps": row_steps, "points": points, "ns": ns,
+             "kry_fine": kry[0] * args.steps, "kry_cgc": kry[1] * args.steps,
+             "fine_steps": float(np.clip(iters, 0, None).sum()) * w.N * w.J * args.steps}
     kernels = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}
     tot_ms = sum(v["ms"] for v in kernels.values()) or 1.0
     for v in kernels.values():
@@ -364,7 +423,8 @@ def run_gpu(args, w):
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPES[prec], "data": "synthetic", "config": workload_desc(w, S, prec),
+            "dtype": DTYPES[prec], "data": "synthetic",
+            "config": workload_desc(w, S, prec, args.overrides),
             "mean_iters": float(iters.mean()), "converged": n_ok, "samples": S,
             "max_rel_err": float(err.max()), "MQ": info.MQ, "P": info.P,
             "fp64_path": fp64, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,
@@ -388,9 +448,19 @@ def main():
     ap.add_argument("--samples", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--set", action="append", default=[], metavar="FIELD=VALUE",
+                    help="override a workload field, e.g. --set nx=63 (repeatable)")
     args = ap.parse_args()
     from synth import workload
-    w = workload(args.workload)
+    over = {}
+    for kv in args.set:
+        k, v = kv.split("=", 1)
+        over[k] = float(v) if any(c in v for c in ".e") else int(v)
+    w = workload(args.workload, **over)
+    args.overrides = over
+    if w.dim == 2:
+        args.precision = "fp64"      # the 2D path is FP64 only
+        args.skip_fp64 = True
     if args.impl == "reference":
         return run_reference(args, w)
     return run_gpu(args, w)
