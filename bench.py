@@ -29,6 +29,8 @@ sys.path.insert(0, ROOT)
 
 import numpy as np  # noqa: E402
 
+from synth import draw_uneven_shapes, draw_xi  # noqa: E402
+
 METRIC = "converged samples/sec at rel err ≤1e-6 vs FP64 oracle; mean parareal iters"
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_defect": 2}
 DTYPES = {"fp64": "f64", "mixed": "f32+f64", "mixed_defect": "f32+f64"}
@@ -437,6 +439,230 @@ def run_gpu(args, w):
     return 0
 
 
+# ---------------------------------------------------------------- uneven batch
+def batch_groups(w):
+    """Per-instance (Nx, N, J), the (Nx, N) groups (one context each, surrogate
+    built at J = 32) and the instances' context indices."""
+    shapes = draw_uneven_shapes(w)
+    keys = sorted({(int(a), int(b)) for a, b, _ in shapes})
+    index = {k: i for i, k in enumerate(keys)}
+    ci = np.array([index[(int(a), int(b))] for a, b, _ in shapes], dtype=np.int32)
+    return shapes, keys, ci
+
+
+def _oracle_solve_inst(task):
+    from oracle import pcgc
+    from oracle.heat1d import Heat1D, u0_sine
+    a, U0, N, J, alpha, tol, kmax, reaction, forcing, u0_kind, T = task
+    op = Heat1D(a, reaction, forcing)
+    nx = len(a) - 1
+    u0 = u0_sine(nx) if u0_kind == 0 else np.zeros(nx)
+    U, k, _ = pcgc.pcgc_solve(op, u0, U0, T / N, J, alpha, tol, kmax)
+    return U, k
+
+
+def oracle_batch(w, shapes, keys, ci, xi, ids, cores):
+    """Oracle on instances `ids`: set-ups of their groups (untimed, all cores),
+    then timed: surrogate guesses and per-instance Algorithm 2 in a pool."""
+    import multiprocessing as mp
+    from oracle import kl_input
+    from oracle.klecgc import Setup1D
+    setups = {}
+    for g in sorted({int(ci[i]) for i in ids}):
+        nx, N = keys[g]
+        setups[g] = Setup1D(w.with_(nx=nx, N=N, J=32), processes=cores)
+    pool = mp.get_context("spawn").Pool(cores)
+    with pool:
+        t = time.perf_counter()
+        tasks = []
+        for i in ids:
+            st = setups[int(ci[i])]
+            a = np.exp(kl_input.log_coefficient_1d(xi[i], st.basis))
+            tasks.append((a, st.guess(xi[i])[0], st.w.N, int(shapes[i][2]), w.alpha, w.tol,
+                          w.kmax, w.reaction, w.forcing, w.u0_kind, w.T))
+        out = pool.map(_oracle_solve_inst, tasks, chunksize=1)
+        dt = time.perf_counter() - t
+    return dt, out
+
+
+def run_batch_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    cores = os.cpu_count() or 1
+    shapes, keys, ci = batch_groups(w)
+    xi = draw_xi(w.S, w.M, w.seed + 1)
+    n_sub = max(16, cores)
+    ids = list(range(n_sub))
+    times, outs = [], None
+    for _ in range(args.steps):
+        dt, outs = oracle_batch(w, shapes, keys, ci, xi, ids, cores)
+        times.append(dt)
+    t = float(np.mean(times))
+    value = n_sub / t
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "samples/s",
+            "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": t * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": batch_desc(w, n_sub, "fp64", keys), "mean_iters": float(np.mean([k for _, k in outs])),
+            "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores, "kind": "oracle",
+                             "sample": f"first {n_sub} of the {w.S} instances per step (their "
+                                       "groups' surrogates set up untimed)"},
+            "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+def batch_desc(w, S, precision, keys):
+    e = w.extra
+    return {"workload": f"{w.name}: {S} 1D instances u_t=(a u_x)_x, Nx in {list(e['nx_choices'])}, "
+                        f"N in {list(e['N_choices'])}, J in {list(e['J_choices'])} (uniform per "
+                        f"instance), M={w.M}, gPC p={w.gpc_degree} per (Nx, N) group at J=32, "
+                        f"alpha={w.alpha}, tol={w.tol}",
+            "instances": S, "groups": len(keys), "precision": precision,
+            "l2": "inputs larger than L2 (per-step working set ~15 GB)",
+            "parallelism": "one GPU; classes of equal (Nx, N, J) on 8 streams"}
+
+
+def run_gpu_batch(args, w):
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2510_26180_gb300 as pkg
+    from synth import draw_train
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    prec = args.precision
+    cores = os.cpu_count() or 1
+    shapes, keys, ci = batch_groups(w)
+    n = w.S
+    xi_h = draw_xi(n, w.M, w.seed + 1 + 1000 * rank)
+    do_cpu = (not args.no_cpu_baseline) and world == 1 and rank == 0
+    cpu = None
+    if do_cpu:
+        n_sub = max(16, cores)
+        dt, outs = oracle_batch(w, shapes, keys, ci, xi_h, list(range(n_sub)), cores)
+    solvers = []
+    for nx, N in keys:
+        wg = w.with_(nx=nx, N=N, J=32)
+        solvers.append(pkg.Solver(pkg.Problem.from_workload(wg), draw_train(wg)))
+    J = shapes[:, 2]
+    sizes = np.array([keys[c][0] * keys[c][1] for c in ci], dtype=np.int64)
+    off = np.concatenate([[0], np.cumsum(sizes)])
+    xi = torch.from_numpy(xi_h).to(dev)
+    U = torch.empty(int(off[-1]), dtype=torch.float64, device=dev)
+    it = torch.empty(n, dtype=torch.int32, device=dev)
+    stt = torch.empty(n, dtype=torch.int32, device=dev)
+
+    def step(xin=xi, Uo=U, ito=it, sto=stt):
+        return pkg.solve_batch(solvers, ci, J, xin, w.alpha, w.tol, w.kmax, PRECISIONS[prec],
+                               pkg.GUESS_GPC, Uo, ito, sto)
+
+    for _ in range(args.warmup):
+        step()
+    stream = torch.cuda.current_stream()
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(f"GPU-{uuid}" if uuid is not None else str(local))
+    for s in solvers:
+        s.profile_enable(True)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    prof = {}
+    for s in solvers:
+        for k, (c, t) in s.profile_read().items():
+            a = prof.setdefault(k, [0, 0.0])
+            a[0] += c
+            a[1] += t
+        s.profile_enable(False)
+    ms = e0.elapsed_time(e1) / args.steps
+    # accuracy against U* per class (FP64 reference kernel)
+    Uh = U.cpu().numpy()
+    iters = it.cpu().numpy()
+    status = stt.cpu().numpy()
+    err = np.zeros(n)
+    for c in range(len(keys)):
+        nx, N = keys[c]
+        for j in sorted(set(J[ci == c])):
+            ids = np.nonzero((ci == c) & (J == j))[0]
+            R = torch.empty((len(ids), N, nx), dtype=torch.float64, device=dev)
+            solvers[c].reference(torch.from_numpy(xi_h[ids]).to(dev), len(ids), N, int(j), R)
+            R = R.cpu().numpy()
+            for q, i in enumerate(ids):
+                blk = Uh[off[i]:off[i + 1]]
+                err[i] = np.linalg.norm(blk - R[q].ravel()) / np.linalg.norm(R[q])
+    ok = (status == 0) & (err <= 1e-6)
+    n_ok = int(ok.sum())
+    value = n_ok / (ms / 1e3)
+    # end to end with pinned host buffers
+    xi_pin = torch.from_numpy(xi_h).pin_memory()
+    U_pin = torch.empty(int(off[-1]), dtype=torch.float64).pin_memory()
+    it_pin = torch.empty(n, dtype=torch.int32).pin_memory()
+    st_pin = torch.empty(n, dtype=torch.int32).pin_memory()
+    step(xi_pin, U_pin, it_pin, st_pin)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    e_steps = max(1, min(args.steps, 2))
+    for _ in range(e_steps):
+        step(xi_pin, U_pin, it_pin, st_pin)
+    torch.cuda.synchronize()
+    e2e_s = (time.perf_counter() - t0) / e_steps
+    e2e_ok = int(((st_pin.numpy() == 0) & ok).sum())
+    e2e = {"value": e2e_ok / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(xi_h.nbytes),
+           "d2h_bytes_per_step": int(U_pin.numel() * 8 + 8 * n)}
+    # roofline of the dominant class (fine: FP32 ALU on the mixed path)
+    kernels = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}
+    tot = sum(v["ms"] for v in kernels.values()) or 1.0
+    for v in kernels.values():
+        v["share"] = v["ms"] / tot
+    dom = max(kernels, key=lambda k: kernels[k]["ms"])
+    itc = np.clip(iters, 0, None).astype(np.float64)
+    Ns = np.array([keys[c][1] for c in ci], dtype=np.float64)
+    nxs = np.array([keys[c][0] for c in ci], dtype=np.float64)
+    row_steps = float((itc * Ns * nxs * J).sum()) * args.steps
+    points = float((itc * Ns * nxs).sum()) * args.steps
+    hbm_peak, peak_kind = peaks()
+    roof = roofline_entry(dom, kernels[dom]["ms"], kernels[dom]["launches"],
+                          {"row_steps": row_steps, "points": points}, prec, w, hbm_peak,
+                          peak_kind)
+    if roof is not None:
+        roof["traffic"] = None      # the per-point bytes were measured on the uniform workload
+    if do_cpu:
+        d = []
+        same = 0
+        for q in range(n_sub):
+            blk = Uh[off[q]:off[q + 1]].reshape(outs[q][0].shape)
+            d.append(float(np.linalg.norm(blk - outs[q][0]) / np.linalg.norm(outs[q][0])))
+            same += int(iters[q]) == outs[q][1]
+        cpu = {"value": n_sub / dt, "unit": "samples/s", "cores": cores, "kind": "oracle",
+               "sample": f"first {n_sub} of the {n} instances (their groups' oracle surrogates "
+                         "set up untimed)", "gpu_vs_oracle_max_rel": max(d),
+               "equal_iters": f"{same}/{n_sub}"}
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[prec], "data": "synthetic", "config": batch_desc(w, n, prec, keys),
+            "mean_iters": float(iters.mean()), "converged": n_ok, "samples": n,
+            "max_rel_err": float(err.max()), "roofline": roof, "kernels": kernels,
+            "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": int(sum(v["launches"] for v in kernels.values())), "clocks": clocks}
+    if rank == 0:
+        print(json.dumps(line))
+    for s in solvers:
+        s.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -461,6 +687,10 @@ def main():
     if w.dim == 2:
         args.precision = "fp64"      # the 2D path is FP64 only
         args.skip_fp64 = True
+    if w.name == "heat1d_uneven":
+        if args.impl == "reference":
+            return run_batch_reference(args, w)
+        return run_gpu_batch(args, w)
     if args.impl == "reference":
         return run_reference(args, w)
     return run_gpu(args, w)

@@ -165,6 +165,35 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S,
                            const double* U_guess, double* U_out, int32_t* iters_out,
                            int32_t* status_out, void* stream);
 
+/*
+ * klecgc_solve_batch - klecgc_solve for an uneven batch of n instances whose
+ * grids, time partitions and fine steps differ (a library facility for
+ * many small problems at once; the paper solves one configuration at a
+ * time).  Instance i uses context ctxs[inst[i].ctx] (its problem, nx, N =
+ * the setup's N, dT = T / N, and surrogate) and inst[i].J fine steps per
+ * interval.  Instances of equal (context, J) form a class solved as one
+ * batch; the classes run concurrently on a pool of streams, iteration by
+ * iteration, until each class's samples have met tol or kmax.
+ *   xi:        [n][M] FP64 (host or device), every context has the same M.
+ *   guess:     KLECGC_GUESS_GPC, _ZERO or _COARSE.
+ *   U_out:     packed FP64 output (host or device): instance i's [N_i][n_i]
+ *              block starts at sum_{j<i} N_j n_j (n_i = nx^dim of its context).
+ *   iters_out, status_out: [n] int32 as for klecgc_solve (may be NULL).
+ * Return and per-instance status as klecgc_solve.  Every context must live
+ * on the current device; 2D contexts need precision KLECGC_FP64.  The
+ * per-class scratch stays in the contexts for reuse until klecgc_free.
+ */
+typedef struct {
+    int32_t ctx;  /* index into ctxs */
+    int32_t J;    /* fine steps per coarse interval (>= 1) */
+} klecgc_instance;
+
+klecgc_status klecgc_solve_batch(klecgc_ctx* const* ctxs, int32_t n_ctx,
+                                 const klecgc_instance* inst, int64_t n, const double* xi,
+                                 double alpha, double tol, int32_t kmax, int32_t precision,
+                                 int32_t guess, double* U_out, int32_t* iters_out,
+                                 int32_t* status_out, void* stream);
+
 /* Stage entry points (one step of the hot path each; used for stage-level
  * checks).  Arguments have the meanings given for klecgc_solve. */
 

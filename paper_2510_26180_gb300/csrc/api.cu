@@ -1,5 +1,6 @@
 // C ABI of libklecgc: context, setup (offline part of Algorithm 3) and the
 // solve loop (online part: Algorithm 2 from the surrogate guess).
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
 #include <cstring>
@@ -80,6 +81,7 @@ struct klecgc_ctx {
     double* W = nullptr;       // [P][ns*N]
     float* W32 = nullptr;      // FP32 copy of W
     std::map<std::string, DevBuf> ws;  // grow-only scratch
+    std::string ws_tag;                // appended to scratch names (one batch class each)
     std::vector<void*> owned;
     MlpState mlp;
     // profile: launch counters and optional CUDA-event timing per kernel class
@@ -130,7 +132,7 @@ struct klecgc_ctx {
 
     template <typename T>
     T* get(const std::string& name, size_t count, cudaError_t* err) {
-        DevBuf& b = ws[name];
+        DevBuf& b = ws[ws_tag.empty() ? name : name + ws_tag];
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;
         if (b.bytes < bytes) {
@@ -1500,53 +1502,82 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
     return KLECGC_OK;
 }
 
-klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double dT, int32_t J,
-                           int32_t N, double alpha, double tol, int32_t kmax, int32_t precision,
-                           int32_t guess, const double* U_guess, double* U_out, int32_t* iters_out,
-                           int32_t* status_out, void* stream) {
-    set_error("");
-    if (!ctx) return fail(KLECGC_E_INVALID_ARG, "NULL context");
-    if (S < 0 || (S > 0 && (!xi || !U_out))) return fail(KLECGC_E_INVALID_ARG, "bad array argument");
-    if (J < 1 || !(alpha > 0 && alpha < 1) || !(tol > 0) || kmax < 1 || precision < 0 ||
-        precision > 2 || guess < 0 || guess > 4 || (guess == KLECGC_GUESS_USER && !U_guess && S > 0))
-        return fail(KLECGC_E_INVALID_ARG, "argument out of range");
-    if (!pow2_in_range(N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
-    if ((guess == KLECGC_GUESS_GPC || guess == KLECGC_GUESS_MLP) && N != ctx->N)
-        return fail(KLECGC_E_INVALID_ARG, "the gPC and learned guesses need the setup's N");
-    if (guess == KLECGC_GUESS_MLP && !ctx->mlp.ready)
-        return fail(KLECGC_E_INVALID_ARG, "no network (klecgc_mlp_set / klecgc_mlp_train)");
-    if (ctx->dim == 2 && precision != KLECGC_FP64) return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 only");
-    klecgc_status s = check_dT(ctx, N, dT);
-    if (s != KLECGC_OK) return s;
-    if (S == 0) return KLECGC_OK;
-    cudaStream_t st = (cudaStream_t)stream;
-    const int nx = ctx->ns, K = N / 2 + 1;  // nx: unknowns per time level
-    const int64_t NS = S * (int64_t)nx * N;
+}  // extern "C"
 
-    const double* xi_d = nullptr;
-    if ((s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d)) != KLECGC_OK) return s;
-    bool finite = true;
-    if ((s = check_xi_finite(ctx, xi_d, S * ctx->M, st, &finite)) != KLECGC_OK) return s;
-    if (!finite) {
-        if (status_out) {
-            std::vector<int32_t> v(S, KLECGC_E_NONFINITE);
-            TRY(cudaMemcpyAsync(status_out, v.data(), S * 4, cudaMemcpyDefault, st));
-            TRY(cudaStreamSynchronize(st));
-        }
-        return fail(KLECGC_E_NONFINITE, "xi has a non-finite entry");
-    }
-    const bool f64 = precision == KLECGC_FP64;
-    const bool defect = precision == KLECGC_MIXED_DEFECT;
+namespace {
+
+// Scratch names carry `tag` while a run's code executes.
+struct TagScope {
+    klecgc_ctx* ctx;
+    std::string saved;
+    TagScope(klecgc_ctx* c, const std::string& t) : ctx(c), saved(c->ws_tag) { c->ws_tag = t; }
+    ~TagScope() { ctx->ws_tag = saved; }
+};
+
+// One solve of S samples with one context and one (N, J, dT): the online
+// part of Algorithm 3 split into begin (operators, guess), step (one
+// parareal iteration: F, the CGC steps (a)-(c), the stopping rule, and an
+// asynchronous copy of the active count) and finish (export).  klecgc_solve
+// runs one; klecgc_solve_batch interleaves several, one per class of equal
+// (context, J), on a pool of streams.
+struct SolveRun {
+    klecgc_ctx* ctx = nullptr;
+    std::string tag;
+    cudaStream_t st = nullptr;
+    int64_t S = 0;
+    int N = 0, J = 0, K = 0, nx = 0, kmax = 0, precision = 0, guess = 0;
+    double dT = 0, alpha = 0, tol = 0;
+    bool f64 = false, defect = false;
     Operators op;
     double *wdt2 = nullptr, *wdT2 = nullptr;  // 2D face weights (fine, CGC)
+    double* U = nullptr;
+    int* active = nullptr;
+    int32_t *iters = nullptr, *status = nullptr;
+    unsigned long long* delta = nullptr;
+    int* n_active = nullptr;
+    double *sc64 = nullptr, *isc64 = nullptr;
+    float *sc32 = nullptr, *isc32 = nullptr;
+    double* r = nullptr;                       // FP64 path: CGC right-hand side
+    Cplx<double>* p64 = nullptr;
+    Cplx<float>* p32 = nullptr;
+    float* fout = nullptr;                     // mixed paths: FP32 fine result
+    float* c32 = nullptr;                      // mixed paths: FP32 increment of U
+    double* Facc64[2] = {nullptr, nullptr};    // mixed: F(U_{n-1}) in FP64, two buffers
+    float2* Facc2[2] = {nullptr, nullptr};     // defect: F(U_{n-1}) as pairs, two buffers
+    float2* Udf = nullptr;                     // defect: the iterate as pairs (aliases U)
+    int* ifail = nullptr;                      // 2D: Krylov cap flags and counters
+    unsigned long long* kits = nullptr;
+    double2* lam_d = nullptr;
+    Plan2D plF, plC;
+    double *scrF = nullptr, *scrC = nullptr;
+    int* h_active = nullptr;                   // pinned, one int (owned by the caller)
+    int k_next = 0;
+
+    klecgc_status begin(const double* xi_d, const double* U_guess);
+    klecgc_status step();
+    bool finished() const { return *h_active == 0 || k_next >= kmax; }
+    klecgc_status finish(double* U_out, std::vector<int32_t>& hs, std::vector<int32_t>& hi,
+                         bool* capped);
+};
+
+klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
+    TagScope ts(ctx, tag);
+    klecgc_status s;
+    nx = ctx->ns;  // unknowns per time level
+    K = N / 2 + 1;
+    f64 = precision == KLECGC_FP64;
+    defect = precision == KLECGC_MIXED_DEFECT;
+    const int64_t NS = S * (int64_t)nx * N;
     if (ctx->dim == 2) {
         if ((s = build_weights_2d(ctx, xi_d, S, dT / J, dT, st, &wdt2, &wdT2)) != KLECGC_OK) return s;
     } else if ((s = build_operators(ctx, xi_d, S, N, J, dT, alpha, f64 ? 1 : 2, defect ? 2 : 1, st,
                                     &op)) != KLECGC_OK) {
         return s;
     }
-
-    WS(double, U, "U", NS);
+    {
+        WS(double, u, "U", NS);
+        U = u;
+    }
     bool mlp_ok = false;
     if (guess == KLECGC_GUESS_MLP) {
         if ((s = mlp_guess_internal(ctx, xi_d, S, U, st, &mlp_ok)) != KLECGC_OK) return s;
@@ -1563,32 +1594,27 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
     } else {
         if ((s = import_batch(ctx, U_guess, S, N, U, st)) != KLECGC_OK) return s;
     }
-    WS(int, active, "active", S);
-    WS(int32_t, iters, "iters", S);
-    WS(int32_t, status, "status", S);
-    WS(unsigned long long, delta, "delta", S);
-    WS(int, n_active, "n_active", 1);
+    {
+        WS(int, a, "active", S);
+        WS(int32_t, it, "iters", S);
+        WS(int32_t, sta, "status", S);
+        WS(unsigned long long, de, "delta", S);
+        WS(int, na, "n_active", 1);
+        active = a;
+        iters = it;
+        status = sta;
+        delta = de;
+        n_active = na;
+    }
     TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
     TRY(cudaMemsetAsync(iters, 0xff, S * sizeof(int32_t), st));
     TRY(cudaMemsetAsync(status, 0, S * sizeof(int32_t), st));
     TRY(cudaMemsetAsync(delta, 0, S * sizeof(unsigned long long), st));
-
-    double *sc64 = nullptr, *isc64 = nullptr;
-    float *sc32 = nullptr, *isc32 = nullptr;
     if (defect) {
         if ((s = scale_tables<float>(ctx, N, alpha, st, &sc32, &isc32)) != KLECGC_OK) return s;
     } else {
         if ((s = scale_tables<double>(ctx, N, alpha, st, &sc64, &isc64)) != KLECGC_OK) return s;
     }
-    // buffers of the iteration
-    double* r = nullptr;                       // FP64 path: CGC right-hand side
-    Cplx<double>* p64 = nullptr;
-    Cplx<float>* p32 = nullptr;
-    float* fout = nullptr;                     // mixed paths: FP32 fine result
-    float* c32 = nullptr;                      // mixed paths: FP32 increment of U
-    double* Facc64[2] = {nullptr, nullptr};    // mixed: F(U_{n-1}) in FP64, two buffers
-    float2* Facc2[2] = {nullptr, nullptr};     // defect: F(U_{n-1}) as pairs, two buffers
-    float2* Udf = nullptr;                     // defect: the iterate as pairs (aliases U)
     if (f64) {
         WS(double, rr, "r", NS);
         r = rr;
@@ -1619,20 +1645,8 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
             Facc64[1] = fb;
         }
     }
-    int* h_active = nullptr;
-    TRY(cudaMallocHost(&h_active, sizeof(int)));
-    struct HostGuard {
-        int* p;
-        ~HostGuard() { cudaFreeHost(p); }
-    } hg{h_active};
-    const double dTreact = dT * ctx->prob.reaction;
-    // 2D: Krylov solves instead of factorizations
-    int* ifail = nullptr;
-    unsigned long long* kits = nullptr;
-    double2* lam_d = nullptr;
-    Plan2D plF, plC;
-    double *scrF = nullptr, *scrC = nullptr;
     if (ctx->dim == 2) {
+        // Krylov solves instead of factorizations
         if ((s = krylov_flags(ctx, S, st, &ifail, &kits)) != KLECGC_OK) return s;
         std::vector<double2> lam;
         if ((s = upload_lambda(ctx, N, alpha, st, lam, &lam_d)) != KLECGC_OK) return s;
@@ -1643,29 +1657,30 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
         scrF = a1;
         scrC = a2;
     }
+    TRY(cudaGetLastError());
+    k_next = 0;
+    *h_active = 1;
+    return KLECGC_OK;
+}
 
-    for (int k = 0; k < kmax; ++k) {
-        if (ctx->dim == 2) {
-            const double dt = dT / J;
-            ctx->launch(KLECGC_K_FINE, st, [&] {
-                launch_fine2d(plF, S, N, ctx->nx, J, dt * ctx->prob.reaction,
-                              dt * ctx->prob.forcing, alpha, 0, U, ctx->u0, wdt2,
-                              ctx->kry_rtol_fine, ctx->kry_maxit, r, active, ifail, kits, scrF, st);
-            });
-            ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<double, double>(S, N, nx, r, sc64, p64, active, st); });
-            ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] {
-                launch_cgc_solve2d(plC, S, K, ctx->nx, dTreact, lam_d, wdT2, ctx->kry_rtol_cgc,
-                                   ctx->kry_maxit, p64, active, ifail, kits + 1, scrC, st);
-            });
-            ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc64, U, 0, delta, nullptr, active, st); });
-            TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
-            ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
-            TRY(cudaGetLastError());
-            TRY(cudaMemcpyAsync(h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-            TRY(cudaStreamSynchronize(st));
-            if (*h_active == 0) break;
-            continue;
-        }
+klecgc_status SolveRun::step() {
+    TagScope ts(ctx, tag);
+    const int k = k_next++;
+    const double dTreact = dT * ctx->prob.reaction;
+    if (ctx->dim == 2) {
+        const double dt = dT / J;
+        ctx->launch(KLECGC_K_FINE, st, [&] {
+            launch_fine2d(plF, S, N, ctx->nx, J, dt * ctx->prob.reaction, dt * ctx->prob.forcing,
+                          alpha, 0, U, ctx->u0, wdt2, ctx->kry_rtol_fine, ctx->kry_maxit, r,
+                          active, ifail, kits, scrF, st);
+        });
+        ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<double, double>(S, N, nx, r, sc64, p64, active, st); });
+        ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] {
+            launch_cgc_solve2d(plC, S, K, ctx->nx, dTreact, lam_d, wdT2, ctx->kry_rtol_cgc,
+                               ctx->kry_maxit, p64, active, ifail, kits + 1, scrC, st);
+        });
+        ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc64, U, 0, delta, nullptr, active, st); });
+    } else {
         const int cur = k & 1, prv = cur ^ 1;
         if (f64) {
             ctx->launch(KLECGC_K_FINE, st, [&] {
@@ -1699,13 +1714,21 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
             ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_cgc_solve<float, float>(S, K, nx, op.dinv32, op.lu32, op.wT32, p32, active, st); });
             ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse_df(S, N, nx, p32, isc32, Udf, delta, c32, active, st); });
         }
-        TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
-        ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
-        TRY(cudaGetLastError());
-        TRY(cudaMemcpyAsync(h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-        TRY(cudaStreamSynchronize(st));
-        if (*h_active == 0) break;
     }
+    TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
+    ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
+    TRY(cudaGetLastError());
+    TRY(cudaMemcpyAsync(h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return KLECGC_OK;
+}
+
+// U_out: [S][N][n] (host or device).  hs / hi receive the per-sample status
+// and iteration counts (the stream is synchronized).
+klecgc_status SolveRun::finish(double* U_out, std::vector<int32_t>& hs, std::vector<int32_t>& hi,
+                               bool* capped) {
+    TagScope ts(ctx, tag);
+    klecgc_status s;
+    const int64_t NS = S * (int64_t)nx * N;
     if (defect) {
         // pairs -> FP64 in the caller's layout
         if (is_device_ptr(U_out)) {
@@ -1716,33 +1739,284 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
             TRY(cudaMemcpyAsync(U_out, tmp, NS * sizeof(double), cudaMemcpyDeviceToHost, st));
         }
         TRY(cudaGetLastError());
-    } else
-    if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) return s;
-    std::vector<int32_t> hs(S), hi(S);
+    } else if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) {
+        return s;
+    }
+    hs.assign(S, 0);
+    hi.assign(S, 0);
     TRY(cudaMemcpyAsync(hs.data(), status, S * 4, cudaMemcpyDeviceToHost, st));
     TRY(cudaMemcpyAsync(hi.data(), iters, S * 4, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
-    ctx->prof_collect();
-    bool capped = false;
+    *capped = false;
     if (ctx->dim == 2) {
         // a sample whose Krylov solve reached the cap has an inexact iterate
         std::vector<int> hf;
-        if ((s = krylov_read(ctx, S, ifail, kits, st, &hf, &capped)) != KLECGC_OK) return s;
+        if ((s = krylov_read(ctx, S, ifail, kits, st, &hf, capped)) != KLECGC_OK) return s;
         for (int64_t i = 0; i < S; ++i)
             if (hf[i] && hs[i] == KLECGC_OK) hs[i] = KLECGC_E_NOT_CONVERGED;
     }
-    if (iters_out) TRY(cudaMemcpy(iters_out, hi.data(), S * 4, cudaMemcpyDefault));
-    if (status_out) TRY(cudaMemcpy(status_out, hs.data(), S * 4, cudaMemcpyDefault));
+    return KLECGC_OK;
+}
+
+klecgc_status status_summary(const std::vector<int32_t>& hs, bool capped) {
     bool any_nf = false, any_nc = false;
-    for (int64_t i = 0; i < S; ++i) {
-        any_nf |= hs[i] == KLECGC_E_NONFINITE;
-        any_nc |= hs[i] == KLECGC_E_NOT_CONVERGED;
+    for (int32_t v : hs) {
+        any_nf |= v == KLECGC_E_NONFINITE;
+        any_nc |= v == KLECGC_E_NOT_CONVERGED;
     }
     if (any_nf) return fail(KLECGC_E_NONFINITE, "a sample produced a non-finite iterate");
     if (any_nc)
         return fail(KLECGC_E_NOT_CONVERGED, capped ? "a Krylov solve reached its iteration cap"
                                                    : "a sample did not reach tol within kmax");
     return KLECGC_OK;
+}
+
+struct PinnedInts {
+    int* p = nullptr;
+    ~PinnedInts() {
+        if (p) cudaFreeHost(p);
+    }
+};
+
+}  // namespace
+
+extern "C" {
+
+klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double dT, int32_t J,
+                           int32_t N, double alpha, double tol, int32_t kmax, int32_t precision,
+                           int32_t guess, const double* U_guess, double* U_out, int32_t* iters_out,
+                           int32_t* status_out, void* stream) {
+    set_error("");
+    if (!ctx) return fail(KLECGC_E_INVALID_ARG, "NULL context");
+    if (S < 0 || (S > 0 && (!xi || !U_out))) return fail(KLECGC_E_INVALID_ARG, "bad array argument");
+    if (J < 1 || !(alpha > 0 && alpha < 1) || !(tol > 0) || kmax < 1 || precision < 0 ||
+        precision > 2 || guess < 0 || guess > 4 || (guess == KLECGC_GUESS_USER && !U_guess && S > 0))
+        return fail(KLECGC_E_INVALID_ARG, "argument out of range");
+    if (!pow2_in_range(N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
+    if ((guess == KLECGC_GUESS_GPC || guess == KLECGC_GUESS_MLP) && N != ctx->N)
+        return fail(KLECGC_E_INVALID_ARG, "the gPC and learned guesses need the setup's N");
+    if (guess == KLECGC_GUESS_MLP && !ctx->mlp.ready)
+        return fail(KLECGC_E_INVALID_ARG, "no network (klecgc_mlp_set / klecgc_mlp_train)");
+    if (ctx->dim == 2 && precision != KLECGC_FP64) return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 only");
+    klecgc_status s = check_dT(ctx, N, dT);
+    if (s != KLECGC_OK) return s;
+    if (S == 0) return KLECGC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+
+    const double* xi_d = nullptr;
+    if ((s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d)) != KLECGC_OK) return s;
+    bool finite = true;
+    if ((s = check_xi_finite(ctx, xi_d, S * ctx->M, st, &finite)) != KLECGC_OK) return s;
+    if (!finite) {
+        if (status_out) {
+            std::vector<int32_t> v(S, KLECGC_E_NONFINITE);
+            TRY(cudaMemcpyAsync(status_out, v.data(), S * 4, cudaMemcpyDefault, st));
+            TRY(cudaStreamSynchronize(st));
+        }
+        return fail(KLECGC_E_NONFINITE, "xi has a non-finite entry");
+    }
+    PinnedInts pin;
+    TRY(cudaMallocHost(&pin.p, sizeof(int)));
+    SolveRun run;
+    run.ctx = ctx;
+    run.st = st;
+    run.S = S;
+    run.N = N;
+    run.J = J;
+    run.kmax = kmax;
+    run.precision = precision;
+    run.guess = guess;
+    run.dT = dT;
+    run.alpha = alpha;
+    run.tol = tol;
+    run.h_active = pin.p;
+    if ((s = run.begin(xi_d, U_guess)) != KLECGC_OK) return s;
+    while (true) {
+        if ((s = run.step()) != KLECGC_OK) return s;
+        TRY(cudaStreamSynchronize(st));
+        if (run.finished()) break;
+    }
+    std::vector<int32_t> hs, hi;
+    bool capped = false;
+    if ((s = run.finish(U_out, hs, hi, &capped)) != KLECGC_OK) return s;
+    ctx->prof_collect();
+    if (iters_out) TRY(cudaMemcpy(iters_out, hi.data(), S * 4, cudaMemcpyDefault));
+    if (status_out) TRY(cudaMemcpy(status_out, hs.data(), S * 4, cudaMemcpyDefault));
+    return status_summary(hs, capped);
+}
+
+klecgc_status klecgc_solve_batch(klecgc_ctx* const* ctxs, int32_t n_ctx,
+                                 const klecgc_instance* inst, int64_t n, const double* xi,
+                                 double alpha, double tol, int32_t kmax, int32_t precision,
+                                 int32_t guess, double* U_out, int32_t* iters_out,
+                                 int32_t* status_out, void* stream) {
+    set_error("");
+    if (!ctxs || n_ctx < 1 || n < 0 || (n > 0 && (!inst || !xi || !U_out)))
+        return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (!(alpha > 0 && alpha < 1) || !(tol > 0) || kmax < 1 || precision < 0 || precision > 2 ||
+        !(guess == KLECGC_GUESS_GPC || guess == KLECGC_GUESS_ZERO || guess == KLECGC_GUESS_COARSE))
+        return fail(KLECGC_E_INVALID_ARG, "argument out of range (batch guesses: GPC, ZERO, COARSE)");
+    int dev = 0;
+    TRY(cudaGetDevice(&dev));
+    const int M = ctxs[0] ? ctxs[0]->M : 0;
+    for (int c = 0; c < n_ctx; ++c) {
+        const klecgc_ctx* x = ctxs[c];
+        if (!x || !x->basis) return fail(KLECGC_E_INVALID_ARG, "NULL context");
+        if (x->device != dev) return fail(KLECGC_E_INVALID_ARG, "every context must be on the current device");
+        if (x->M != M) return fail(KLECGC_E_INVALID_ARG, "every context must have the same M");
+        if (x->dim == 2 && precision != KLECGC_FP64) return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 only");
+    }
+    for (int64_t i = 0; i < n; ++i)
+        if (inst[i].ctx < 0 || inst[i].ctx >= n_ctx || inst[i].J < 1)
+            return fail(KLECGC_E_INVALID_ARG, "instance " + std::to_string(i) + ": bad ctx index or J");
+    if (n == 0) return KLECGC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    klecgc_ctx* c0 = ctxs[0];
+    klecgc_status s;
+
+    // packed output offsets, classes of equal (context, J), largest work first
+    std::vector<int64_t> off(n);
+    int64_t total = 0;
+    for (int64_t i = 0; i < n; ++i) {
+        off[i] = total;
+        total += (int64_t)ctxs[inst[i].ctx]->N * ctxs[inst[i].ctx]->ns;
+    }
+    std::map<std::pair<int, int>, std::vector<int64_t>> groups;
+    for (int64_t i = 0; i < n; ++i) groups[{inst[i].ctx, inst[i].J}].push_back(i);
+    struct Cls {
+        int ci, J;
+        std::vector<int64_t> ids;
+        double work;
+    };
+    std::vector<Cls> cls;
+    for (auto& g : groups) {
+        const klecgc_ctx* x = ctxs[g.first.first];
+        cls.push_back({g.first.first, g.first.second, g.second,
+                       (double)g.second.size() * x->N * x->ns * g.first.second});
+    }
+    std::stable_sort(cls.begin(), cls.end(), [](const Cls& a, const Cls& b) { return a.work > b.work; });
+    const int nc = (int)cls.size();
+
+    const double* xi_d = nullptr;
+    if ((s = stage_in(c0, xi, (size_t)n * M, "batch_xi", st, &xi_d)) != KLECGC_OK) return s;
+    bool finite = true;
+    if ((s = check_xi_finite(c0, xi_d, n * M, st, &finite)) != KLECGC_OK) return s;
+    if (!finite) {
+        if (status_out) {
+            std::vector<int32_t> v(n, KLECGC_E_NONFINITE);
+            TRY(cudaMemcpyAsync(status_out, v.data(), n * 4, cudaMemcpyDefault, st));
+            TRY(cudaStreamSynchronize(st));
+        }
+        return fail(KLECGC_E_NONFINITE, "xi has a non-finite entry");
+    }
+
+    // a pool of streams ordered after the caller's stream
+    struct Pool {
+        std::vector<cudaStream_t> s;
+        cudaEvent_t ev = nullptr;
+        ~Pool() {
+            for (cudaStream_t x : s) cudaStreamDestroy(x);
+            if (ev) cudaEventDestroy(ev);
+        }
+    } pool;
+    const int P = std::min(nc, 8);
+    TRY(cudaEventCreateWithFlags(&pool.ev, cudaEventDisableTiming));
+    TRY(cudaEventRecord(pool.ev, st));
+    for (int i = 0; i < P; ++i) {
+        cudaStream_t x;
+        TRY(cudaStreamCreateWithFlags(&x, cudaStreamNonBlocking));
+        pool.s.push_back(x);
+        TRY(cudaStreamWaitEvent(x, pool.ev, 0));
+    }
+    PinnedInts pin;
+    TRY(cudaMallocHost(&pin.p, nc * sizeof(int)));
+    std::vector<SolveRun> runs(nc);
+    for (int c = 0; c < nc; ++c) {
+        SolveRun& R = runs[c];
+        R.ctx = ctxs[cls[c].ci];
+        R.tag = "#b" + std::to_string(c);
+        R.st = pool.s[c % P];
+        R.S = (int64_t)cls[c].ids.size();
+        R.N = R.ctx->N;
+        R.J = cls[c].J;
+        R.kmax = kmax;
+        R.precision = precision;
+        R.guess = guess;
+        R.dT = R.ctx->prob.T / R.N;
+        R.alpha = alpha;
+        R.tol = tol;
+        R.h_active = pin.p + c;
+        klecgc_ctx* ctx = R.ctx;
+        double* xic = nullptr;
+        {
+            TagScope ts(ctx, R.tag);
+            WS(double, xg, "bxi", R.S * M);
+            WS(int64_t, idx, "bidx", R.S);
+            TRY(cudaMemcpyAsync(idx, cls[c].ids.data(), R.S * sizeof(int64_t), cudaMemcpyHostToDevice, R.st));
+            launch_gather_rows(xi_d, idx, R.S, M, xg, R.st);
+            xic = xg;
+        }
+        if ((s = R.begin(xic, nullptr)) != KLECGC_OK) return s;
+    }
+    // iterations in lockstep: every class still active enqueues one step,
+    // then the host reads each class's active count
+    std::vector<char> done(nc, 0);
+    for (int left = nc; left > 0;) {
+        for (int c = 0; c < nc; ++c)
+            if (!done[c] && (s = runs[c].step()) != KLECGC_OK) return s;
+        for (int c = 0; c < nc; ++c) {
+            if (done[c]) continue;
+            TRY(cudaStreamSynchronize(runs[c].st));
+            if (runs[c].finished()) {
+                done[c] = 1;
+                --left;
+            }
+        }
+    }
+    // results: class blocks scattered to the packed per-instance layout
+    const bool dev_out = is_device_ptr(U_out);
+    double* dst = U_out;
+    if (!dev_out) {
+        klecgc_ctx* ctx = c0;
+        WS(double, big, "batch_out", total);
+        dst = big;
+    }
+    std::vector<int32_t> hs_all(n), hi_all(n);
+    bool capped_any = false;
+    for (int c = 0; c < nc; ++c) {
+        SolveRun& R = runs[c];
+        klecgc_ctx* ctx = R.ctx;
+        const int64_t block = (int64_t)R.N * ctx->ns;
+        double* tmp = nullptr;
+        int64_t* offd = nullptr;
+        {
+            TagScope ts(ctx, R.tag);
+            WS(double, t, "bU", R.S * block);
+            WS(int64_t, o, "boff", R.S);
+            tmp = t;
+            offd = o;
+        }
+        std::vector<int32_t> hs, hi;
+        bool capped = false;
+        if ((s = R.finish(tmp, hs, hi, &capped)) != KLECGC_OK) return s;
+        capped_any |= capped;
+        std::vector<int64_t> oh(R.S);
+        for (int64_t j = 0; j < R.S; ++j) {
+            const int64_t i = cls[c].ids[j];
+            oh[j] = off[i];
+            hs_all[i] = hs[j];
+            hi_all[i] = hi[j];
+        }
+        TRY(cudaMemcpyAsync(offd, oh.data(), R.S * sizeof(int64_t), cudaMemcpyHostToDevice, R.st));
+        ctx->launch(KLECGC_K_LAYOUT, R.st, [&] { launch_scatter_blocks(tmp, offd, R.S, block, dst, R.st); });
+        TRY(cudaGetLastError());
+    }
+    for (cudaStream_t x : pool.s) TRY(cudaStreamSynchronize(x));
+    if (!dev_out) TRY(cudaMemcpy(U_out, dst, total * sizeof(double), cudaMemcpyDeviceToHost));
+    for (int c = 0; c < n_ctx; ++c) ctxs[c]->prof_collect();
+    if (iters_out) TRY(cudaMemcpy(iters_out, hi_all.data(), n * 4, cudaMemcpyDefault));
+    if (status_out) TRY(cudaMemcpy(status_out, hs_all.data(), n * 4, cudaMemcpyDefault));
+    return status_summary(hs_all, capped_any);
 }
 
 }  // extern "C"

@@ -130,6 +130,12 @@ void launch_cgc_solve2d(const Plan2D& pl, int64_t S, int K, int nx, double dTc,
                         Cplx<double>* p, const int* active, int* ifail,
                         unsigned long long* itcount, double* scratch, cudaStream_t st);
 
+// ---- k_batch.cu ---- (uneven batch)
+void launch_gather_rows(const double* in, const int64_t* idx, int64_t S, int M, double* out,
+                        cudaStream_t st);
+void launch_scatter_blocks(const double* src, const int64_t* off, int64_t S, int64_t block,
+                           double* dst, cudaStream_t st);
+
 // ---- k_cgc.cu ----
 // Step (a): p[s][i][k] = sum_j alpha^{j/N} r[s][i][j] exp(-2 pi i j k / N), k <= N/2.
 template <typename T, typename TIN>

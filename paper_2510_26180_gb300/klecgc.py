@@ -25,7 +25,8 @@ EXPORTS = ["klecgc_setup", "klecgc_solve", "klecgc_field", "klecgc_guess", "klec
            "klecgc_status_string", "klecgc_last_error", "klecgc_profile_enable",
            "klecgc_profile_read", "klecgc_reference_noalloc", "klecgc_mlp_set", "klecgc_mlp_get",
            "klecgc_mlp_loss_grad", "klecgc_mlp_train", "klecgc_mlp_guess", "klecgc_downsample",
-           "klecgc_set_krylov", "klecgc_krylov_stats", "klecgc_save", "klecgc_load"]
+           "klecgc_set_krylov", "klecgc_krylov_stats", "klecgc_save", "klecgc_load",
+           "klecgc_solve_batch"]
 PROFILE_CLASSES = ["field", "factors", "guess", "fine", "cgc_fwd", "cgc_solve", "cgc_inv",
                    "conv", "layout"]
 
@@ -49,6 +50,10 @@ class Problem(ctypes.Structure):
         return cls(dim=w.dim, nx=w.nx, T=w.T, sigma=w.sigma, corr_len=w.corr_len, M=w.M,
                    gpc_degree=w.gpc_degree, n_train=w.n_train, eps_kl=w.eps_kl, N=w.N, J=w.J,
                    reaction=w.reaction, forcing=w.forcing, u0_kind=w.u0_kind)
+
+
+class Instance(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_int32), ("J", ctypes.c_int32)]
 
 
 class Profile(ctypes.Structure):
@@ -97,6 +102,8 @@ def load() -> ctypes.CDLL:
         "klecgc_set_krylov": [P, D, D, I32],
         "klecgc_save": [P, ctypes.c_char_p],
         "klecgc_load": [ctypes.c_char_p, ctypes.POINTER(P), P],
+        "klecgc_solve_batch": [ctypes.POINTER(P), I32, ctypes.POINTER(Instance), I64, P, D, D,
+                               I32, I32, I32, P, P, P, P],
         "klecgc_krylov_stats": [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
     }
     for name, args in sig.items():
@@ -151,6 +158,24 @@ def _check(status: int, allow=(OK,)) -> int:
         lib = load()
         raise KlecgcError(status, lib.klecgc_last_error().decode())
     return status
+
+
+def solve_batch(solvers, ctx_index, J, xi, alpha, tol, kmax, precision, guess, U_out,
+                iters_out=None, status_out=None, stream=None,
+                allow=(OK, E_NOT_CONVERGED, E_NONFINITE)) -> int:
+    """klecgc_solve_batch: instance i uses solvers[ctx_index[i]] and J[i] fine
+    steps; U_out is the packed per-instance output (see the header)."""
+    lib = load()
+    n = len(ctx_index)
+    inst = (Instance * max(n, 1))()
+    for i in range(n):
+        inst[i].ctx = int(ctx_index[i])
+        inst[i].J = int(J[i])
+    handles = (ctypes.c_void_p * len(solvers))(*[s.h.value for s in solvers])
+    return _check(lib.klecgc_solve_batch(handles, len(solvers), inst, n, _ptr(xi, np.float64),
+                                         alpha, tol, kmax, precision, guess,
+                                         _ptr(U_out, np.float64), _ptr(iters_out, np.int32),
+                                         _ptr(status_out, np.int32), _stream(stream)), allow)
 
 
 class Solver:

@@ -61,3 +61,15 @@ def test_load_rejects_files_that_are_not_contexts(tmp_path):
     bad = tmp_path / "short.ctx"
     bad.write_bytes(b"KLECGCv1")
     assert lib.klecgc_load(os.fsencode(str(bad)), ctypes.byref(h), None) == pkg.E_INVALID_ARG
+
+
+def test_batch_rejects_bad_arguments_before_any_cuda_call():
+    import ctypes
+    import paper_2510_26180_gb300 as pkg
+    lib = pkg.load()
+    inst = (pkg.klecgc.Instance * 1)()
+    assert lib.klecgc_solve_batch(None, 1, inst, 1, None, 0.1, 1e-8, 5, 0, 0, None, None, None,
+                                  None) == pkg.E_INVALID_ARG
+    ctxs = (ctypes.c_void_p * 1)(None)
+    assert lib.klecgc_solve_batch(ctxs, 0, inst, 1, None, 0.1, 1e-8, 5, 0, 0, None, None, None,
+                                  None) == pkg.E_INVALID_ARG
