@@ -80,6 +80,9 @@ struct klecgc_ctx {
     double* ubar = nullptr;    // [ns*N]  internal order c = i*N + n
     double* W = nullptr;       // [P][ns*N]
     float* W32 = nullptr;      // FP32 copy of W
+    float* W32t = nullptr;     // [ns*N][Kp] FP32 W^T, zero-padded (tensor-core guess)
+    int Kp = 0;
+    int* tc_err = nullptr;     // set by the tensor-core guess when a wait timed out
     std::map<std::string, DevBuf> ws;  // grow-only scratch
     std::string ws_tag;                // appended to scratch names (one batch class each)
     std::vector<void*> owned;
@@ -445,18 +448,31 @@ klecgc_status coarse_guess_internal(klecgc_ctx* ctx, int64_t S, int N, double dT
     return KLECGC_OK;
 }
 
+// Reads and clears the tensor-core guess's timeout flag (stream synchronized).
+klecgc_status check_tc(klecgc_ctx* ctx, cudaStream_t st) {
+    int h = 0;
+    TRY(cudaMemcpyAsync(&h, ctx->tc_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    if (h) {
+        TRY(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), st));
+        return fail(KLECGC_E_CUDA, "the tensor-core guess pipeline timed out");
+    }
+    return KLECGC_OK;
+}
+
 // U^0 = ubar + psi(xi) W into U (internal layout [S][nx][N]).
 klecgc_status gpc_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S, bool fp64,
                                  double* U, cudaStream_t st) {
     const int64_t NC = (int64_t)ctx->ns * ctx->N;
     if (fp64) {
         WS(double, psi, "psi64", S * ctx->P);
-        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_psi<double>(xi_d, S, ctx->M, ctx->degrees, ctx->P, psi, st); });
+        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_psi<double>(xi_d, S, ctx->M, ctx->degrees, ctx->P, psi, ctx->P, st); });
         ctx->launch(KLECGC_K_GUESS, st, [&] { launch_gemm<double>(S, NC, ctx->P, psi, ctx->P, 1, ctx->W, NC, 1, U, NC, false, ctx->ubar, st); });
     } else {
-        WS(float, psi, "psi32", S * ctx->P);
-        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_psi<float>(xi_d, S, ctx->M, ctx->degrees, ctx->P, psi, st); });
-        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_gemm<float>(S, NC, ctx->P, psi, ctx->P, 1, ctx->W32, NC, 1, U, NC, false, ctx->ubar, st); });
+        // tcgen05 tensor cores, 3xTF32 split (FP32-level accuracy)
+        WS(float, psi, "psi32", S * ctx->Kp);
+        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_psi<float>(xi_d, S, ctx->M, ctx->degrees, ctx->P, psi, ctx->Kp, st); });
+        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_guess_tc(S, NC, ctx->Kp, psi, ctx->W32t, ctx->ubar, U, ctx->tc_err, st); });
     }
     TRY(cudaGetLastError());
     return KLECGC_OK;
@@ -818,9 +834,15 @@ klecgc_status klecgc_load(const char* path, klecgc_ctx** out, void* stream) {
         (s = get_dev(f, ctx, &ctx->ubar, NC)) != KLECGC_OK ||
         (s = get_dev(f, ctx, &ctx->W, (size_t)ctx->P * NC)) != KLECGC_OK)
         return bail(s);
-    if (ctx->alloc_owned(&ctx->W32, (size_t)ctx->P * NC) != cudaSuccess)
+    ctx->Kp = guess_tc_k_padded(ctx->P);
+    if (ctx->alloc_owned(&ctx->W32, (size_t)ctx->P * NC) != cudaSuccess ||
+        ctx->alloc_owned(&ctx->W32t, (size_t)ctx->Kp * NC) != cudaSuccess ||
+        ctx->alloc_owned(&ctx->tc_err, 1) != cudaSuccess)
         return bail(fail(KLECGC_E_OUT_OF_MEMORY, "W32"));
+    if (cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), st) != cudaSuccess)
+        return bail(fail(KLECGC_E_CUDA, "memset"));
     launch_to_float(ctx->W, ctx->W32, (int64_t)ctx->P * NC, st);
+    launch_pad_transpose(ctx->W32, ctx->P, NC, ctx->Kp, ctx->W32t, st);
     if (hd.mlp_ready) {
         if ((s = mlp_alloc(ctx)) != KLECGC_OK) return bail(s);
         MlpState& q = ctx->mlp;
@@ -1080,7 +1102,7 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     double* Bd = nullptr;
     STRY(cudaMalloc(&Bd, (size_t)nt * P * 8));
     Guard gB{Bd};
-    launch_psi<double>(xi_d, nt, M, ctx->degrees, P, Bd, st);
+    launch_psi<double>(xi_d, nt, M, ctx->degrees, P, Bd, P, st);
     STRY(cudaGetLastError());
     std::vector<double> B((size_t)nt * P);
     STRY(cudaMemcpyAsync(B.data(), Bd, B.size() * 8, cudaMemcpyDeviceToHost, st));
@@ -1098,8 +1120,13 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     STRY(cudaMemcpyAsync(Hd, H.data(), H.size() * 8, cudaMemcpyHostToDevice, st));
     STRY(ctx->alloc_owned(&ctx->W, (size_t)P * NC));
     STRY(ctx->alloc_owned(&ctx->W32, (size_t)P * NC));
+    ctx->Kp = guess_tc_k_padded(P);
+    STRY(ctx->alloc_owned(&ctx->W32t, (size_t)ctx->Kp * NC));
+    STRY(ctx->alloc_owned(&ctx->tc_err, 1));
+    STRY(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), st));
     launch_gemm<double>(P, NC, MQ, Hd, MQ, 1, Gd, NC, 1, ctx->W, NC, false, nullptr, st);
     launch_to_float(ctx->W, ctx->W32, (int64_t)P * NC, st);
+    launch_pad_transpose(ctx->W32, P, NC, ctx->Kp, ctx->W32t, st);
     STRY(cudaGetLastError());
     STRY(cudaStreamSynchronize(st));
     // release the training-sized scratch
@@ -1143,7 +1170,7 @@ klecgc_status klecgc_guess(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t
         return s;
     if ((s = export_batch(ctx, U, S, ctx->N, U0_out, st)) != KLECGC_OK) return s;
     TRY(cudaStreamSynchronize(st));
-    return KLECGC_OK;
+    return check_tc(ctx, st);
 }
 
 klecgc_status klecgc_reference(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t N, int32_t J,
@@ -1747,6 +1774,7 @@ klecgc_status SolveRun::finish(double* U_out, std::vector<int32_t>& hs, std::vec
     TRY(cudaMemcpyAsync(hs.data(), status, S * 4, cudaMemcpyDeviceToHost, st));
     TRY(cudaMemcpyAsync(hi.data(), iters, S * 4, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
+    if ((s = check_tc(ctx, st)) != KLECGC_OK) return s;
     *capped = false;
     if (ctx->dim == 2) {
         // a sample whose Krylov solve reached the cap has an inexact iterate

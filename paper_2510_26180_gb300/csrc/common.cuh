@@ -72,6 +72,7 @@ void launch_nonfinite_flag(const double* x, int64_t n, int* flag, cudaStream_t s
 // ---- k_guess.cu ----
 template <typename T>
 void launch_psi(const double* xi, int64_t S, int M, const int* degrees, int P, T* psi,
+                int ld,
                 cudaStream_t st);
 // C[m][n] (+)= sum_k A(m,k) B(k,n); A(m,k) = A[m*lda_m + k*lda_k], B likewise,
 // C row-major with leading dimension ldc; C is FP64, A/B of type T.
@@ -135,6 +136,16 @@ void launch_gather_rows(const double* in, const int64_t* idx, int64_t S, int M, 
                         cudaStream_t st);
 void launch_scatter_blocks(const double* src, const int64_t* off, int64_t S, int64_t block,
                            double* dst, cudaStream_t st);
+
+// ---- k_tc.cu ---- (tcgen05 surrogate guess)
+// K extent of the padded psi / W^T rows (multiple of the MMA chunk).
+int guess_tc_k_padded(int P);
+// Wt[c][j] = W[j][c] (j < P), zero up to Kp.
+void launch_pad_transpose(const float* W, int P, int64_t NC, int Kp, float* Wt, cudaStream_t st);
+// U[s][c] = ubar[c] + sum_j psi[s][j] Wt[c][j] (psi [S][Kp], zero-padded; NC even);
+// *err = 1 if a pipeline wait ran out of its budget.
+void launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi, const float* Wt,
+                     const double* ubar, double* U, int* err, cudaStream_t st);
 
 // ---- k_cgc.cu ----
 // Step (a): p[s][i][k] = sum_j alpha^{j/N} r[s][i][j] exp(-2 pi i j k / N), k <= N/2.

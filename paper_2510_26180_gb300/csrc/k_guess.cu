@@ -19,13 +19,18 @@ __device__ __forceinline__ double hermite_on(int k, double x) {
     return pc;
 }
 
+// psi[s][j] for j < P; row stride ld >= P, columns P..ld-1 set to 0.
 template <typename T>
 __global__ void k_psi(const double* __restrict__ xi, int64_t S, int M,
-                      const int* __restrict__ degrees, int P, T* __restrict__ psi) {
+                      const int* __restrict__ degrees, int P, int ld, T* __restrict__ psi) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= S * P) return;
-    int64_t s = t / P;
-    int j = (int)(t - s * P);
+    if (t >= S * ld) return;
+    int64_t s = t / ld;
+    int j = (int)(t - s * ld);
+    if (j >= P) {
+        psi[t] = (T)0;
+        return;
+    }
     double v = 1.0;
     for (int l = 0; l < M; ++l) {
         int k = degrees[j * M + l];
@@ -35,15 +40,15 @@ __global__ void k_psi(const double* __restrict__ xi, int64_t S, int M,
 }
 
 template <typename T>
-void launch_psi(const double* xi, int64_t S, int M, const int* degrees, int P, T* psi,
+void launch_psi(const double* xi, int64_t S, int M, const int* degrees, int P, T* psi, int ld,
                 cudaStream_t st) {
-    int64_t n = S * P;
+    int64_t n = S * ld;
     if (n == 0) return;
-    k_psi<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xi, S, M, degrees, P, psi);
+    k_psi<T><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(xi, S, M, degrees, P, ld, psi);
 }
-template void launch_psi<double>(const double*, int64_t, int, const int*, int, double*,
+template void launch_psi<double>(const double*, int64_t, int, const int*, int, double*, int,
                                  cudaStream_t);
-template void launch_psi<float>(const double*, int64_t, int, const int*, int, float*,
+template void launch_psi<float>(const double*, int64_t, int, const int*, int, float*, int,
                                 cudaStream_t);
 
 // Tiled SIMT product, 64x64 output tile, 16-deep k slices, 4x4 outputs per thread.

@@ -273,3 +273,21 @@ def test_zero_and_user_guess():
                  it2, U_guess=ug)
     assert np.all(it2.cpu().numpy() <= it.cpu().numpy())
     assert it2.cpu().numpy().sum() < it.cpu().numpy().sum()
+
+
+@pytest.mark.parametrize("S,over", [(1, {}), (130, {}), (300, dict(gpc_degree=4, n_train=140)),
+                                    (129, dict(nx=100, N=8, J=5))],
+                         ids=["S1", "S130", "S300_P70", "S129_nx100"])
+def test_guess_tensor_core_matches_fp64(S, over):
+    """The mixed guess runs on the tcgen05 tensor cores (3xTF32 split); it must
+    equal the FP64 guess (pinned to the oracle above) to FP32 accuracy on ragged
+    tiles (S, N*Nx not multiples of the 128 x 256 tile; P padded to 32)."""
+    solver, w = gpu_solver("heat1d_nx63", **over) if over else gpu_solver("heat1d_nx63")
+    xi = draw_xi(S, w.M, 18)
+    G64 = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
+    G32 = torch.empty_like(G64)
+    solver.guess(T(xi), S, 0, G64)
+    solver.guess(T(xi), S, 2, G32)
+    assert rel(G32.cpu().numpy(), G64.cpu().numpy()) < 2e-6
+    if over.get("gpc_degree"):
+        assert solver.info().P == 70
