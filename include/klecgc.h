@@ -32,8 +32,11 @@
  *    the edge midpoints; its linear systems (the backward-Euler steps of F
  *    and the shifted CGC systems of eq. three steps (b)) are solved by
  *    Jacobi-preconditioned CG / COCG to a relative residual (see
- *    klecgc_set_krylov) instead of the 1D direct factorizations.  2D runs in
- *    FP64 only (precision KLECGC_FP64) and has no learned guess.
+ *    klecgc_set_krylov) instead of the 1D direct factorizations.  2D takes
+ *    precision KLECGC_FP64 (FP64 Krylov solves) or KLECGC_MIXED (each step of
+ *    F by FP64 iterative refinement around an FP32 Jacobi-PCG: the residual
+ *    is kept in FP64, so the result meets the same FP64 residual test; the
+ *    CGC stays FP64); it has no learned guess.
  *  - No exception crosses the ABI and no device trap is used: every error
  *    is a status code; klecgc_last_error() returns a one-line detail for
  *    the calling thread.
@@ -147,7 +150,7 @@ klecgc_status klecgc_setup(const klecgc_problem* problem, const double* xi_train
  *              rule; this is the per-sample increment).
  *   kmax:      iteration cap (>= 1).
  *   precision: KLECGC_FP64 / KLECGC_MIXED / KLECGC_MIXED_DEFECT (2D: FP64
- *              only, else UNSUPPORTED).
+ *              or MIXED, else UNSUPPORTED).
  *   guess:     KLECGC_GUESS_*; U_guess ([S][N][nx]) is read only for USER.
  *   U_out:     [S][N][nx] FP64: the last iterate of every sample.
  *   iters_out: [S] int32: CGC updates performed until tol was met, -1 when
@@ -180,7 +183,8 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S,
  *              block starts at sum_{j<i} N_j n_j (n_i = nx^dim of its context).
  *   iters_out, status_out: [n] int32 as for klecgc_solve (may be NULL).
  * Return and per-instance status as klecgc_solve.  Every context must live
- * on the current device; 2D contexts need precision KLECGC_FP64.  The
+ * on the current device; 2D contexts need precision KLECGC_FP64 or
+ * KLECGC_MIXED.  The
  * per-class scratch stays in the contexts for reuse until klecgc_free.
  */
 typedef struct {

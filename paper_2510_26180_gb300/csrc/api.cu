@@ -222,6 +222,10 @@ klecgc_status stage_in(klecgc_ctx* ctx, const T* user, size_t count, const char*
 
 bool pow2_in_range(int N) { return N >= 2 && N <= 64 && (N & (N - 1)) == 0; }
 
+// Relative tolerance of the FP32 inner solves of the mixed 2D propagator (each
+// FP64 refinement gains about this factor).
+constexpr double kInnerRtol = 1e-4;
+
 klecgc_status check_dT(const klecgc_ctx* ctx, int N, double dT) {
     double T = ctx->prob.T;
     if (!(dT > 0) || std::fabs(N * dT - T) > 1e-12 * T)
@@ -1400,7 +1404,8 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
     const double* xi_d = nullptr;
     if ((s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d)) != KLECGC_OK) return s;
     if (ctx->dim == 2) {
-        if (precision != KLECGC_FP64) return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 only");
+        if (precision == KLECGC_MIXED_DEFECT)
+            return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 or MIXED only");
         double* wdt = nullptr;
         if ((s = build_weights_2d(ctx, xi_d, S, dT / J, dT, st, &wdt, nullptr)) != KLECGC_OK) return s;
         WS(double, U, "U", S * (int64_t)nx * N);
@@ -1411,13 +1416,20 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
         int* ifail = nullptr;
         unsigned long long* its = nullptr;
         if ((s = krylov_flags(ctx, S, st, &ifail, &its)) != KLECGC_OK) return s;
-        const Plan2D pl = plan_2d(0, ctx->nx, S * N);
+        const bool mixed = precision == KLECGC_MIXED;
+        const Plan2D pl = plan_2d(mixed ? 2 : 0, ctx->nx, S * N);
         WS(double, scr, "k2d_scratch", pl.scratch_doubles);
         const double dt = dT / J;
         ctx->launch(KLECGC_K_FINE, st, [&] {
-            launch_fine2d(pl, S, N, ctx->nx, J, dt * ctx->prob.reaction, dt * ctx->prob.forcing,
-                          alpha, 0, U, ctx->u0, wdt, ctx->kry_rtol_fine, ctx->kry_maxit, r, active,
-                          ifail, its, scr, st);
+            if (mixed)
+                launch_fine2d_mixed(pl, S, N, ctx->nx, J, dt * ctx->prob.reaction,
+                                    dt * ctx->prob.forcing, alpha, 0, U, ctx->u0, wdt,
+                                    ctx->kry_rtol_fine, kInnerRtol, ctx->kry_maxit, r, active,
+                                    ifail, its, scr, st);
+            else
+                launch_fine2d(pl, S, N, ctx->nx, J, dt * ctx->prob.reaction,
+                              dt * ctx->prob.forcing, alpha, 0, U, ctx->u0, wdt,
+                              ctx->kry_rtol_fine, ctx->kry_maxit, r, active, ifail, its, scr, st);
         });
         TRY(cudaGetLastError());
         if ((s = export_batch(ctx, r, S, N, r_out, st)) != KLECGC_OK) return s;
@@ -1642,7 +1654,7 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
     } else {
         if ((s = scale_tables<double>(ctx, N, alpha, st, &sc64, &isc64)) != KLECGC_OK) return s;
     }
-    if (f64) {
+    if (f64 || ctx->dim == 2) {
         WS(double, rr, "r", NS);
         r = rr;
     }
@@ -1653,7 +1665,7 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
         WS(Cplx<float>, pp, "p32", S * (int64_t)nx * K);
         p32 = pp;
     }
-    if (!f64) {
+    if (!f64 && ctx->dim == 1) {
         WS(float, fo, "fout", NS);
         WS(float, cc, "c32", NS);
         fout = fo;
@@ -1677,7 +1689,7 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
         if ((s = krylov_flags(ctx, S, st, &ifail, &kits)) != KLECGC_OK) return s;
         std::vector<double2> lam;
         if ((s = upload_lambda(ctx, N, alpha, st, lam, &lam_d)) != KLECGC_OK) return s;
-        plF = plan_2d(0, ctx->nx, S * N);
+        plF = plan_2d(precision == KLECGC_MIXED ? 2 : 0, ctx->nx, S * N);
         plC = plan_2d(1, ctx->nx, S * K);
         WS(double, a1, "k2d_scratch", plF.scratch_doubles);
         WS(double, a2, "k2d_scratch_c", plC.scratch_doubles);
@@ -1696,11 +1708,20 @@ klecgc_status SolveRun::step() {
     const double dTreact = dT * ctx->prob.reaction;
     if (ctx->dim == 2) {
         const double dt = dT / J;
-        ctx->launch(KLECGC_K_FINE, st, [&] {
-            launch_fine2d(plF, S, N, ctx->nx, J, dt * ctx->prob.reaction, dt * ctx->prob.forcing,
-                          alpha, 0, U, ctx->u0, wdt2, ctx->kry_rtol_fine, ctx->kry_maxit, r,
-                          active, ifail, kits, scrF, st);
-        });
+        if (precision == KLECGC_MIXED)
+            ctx->launch(KLECGC_K_FINE, st, [&] {
+                launch_fine2d_mixed(plF, S, N, ctx->nx, J, dt * ctx->prob.reaction,
+                                    dt * ctx->prob.forcing, alpha, 0, U, ctx->u0, wdt2,
+                                    ctx->kry_rtol_fine, kInnerRtol, ctx->kry_maxit, r, active,
+                                    ifail, kits, scrF, st);
+            });
+        else
+            ctx->launch(KLECGC_K_FINE, st, [&] {
+                launch_fine2d(plF, S, N, ctx->nx, J, dt * ctx->prob.reaction,
+                              dt * ctx->prob.forcing, alpha, 0, U, ctx->u0, wdt2,
+                              ctx->kry_rtol_fine, ctx->kry_maxit, r, active, ifail, kits, scrF,
+                              st);
+            });
         ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<double, double>(S, N, nx, r, sc64, p64, active, st); });
         ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] {
             launch_cgc_solve2d(plC, S, K, ctx->nx, dTreact, lam_d, wdT2, ctx->kry_rtol_cgc,
@@ -1825,7 +1846,8 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
         return fail(KLECGC_E_INVALID_ARG, "the gPC and learned guesses need the setup's N");
     if (guess == KLECGC_GUESS_MLP && !ctx->mlp.ready)
         return fail(KLECGC_E_INVALID_ARG, "no network (klecgc_mlp_set / klecgc_mlp_train)");
-    if (ctx->dim == 2 && precision != KLECGC_FP64) return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 only");
+    if (ctx->dim == 2 && precision == KLECGC_MIXED_DEFECT)
+        return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 or MIXED only");
     klecgc_status s = check_dT(ctx, N, dT);
     if (s != KLECGC_OK) return s;
     if (S == 0) return KLECGC_OK;
@@ -1892,7 +1914,8 @@ klecgc_status klecgc_solve_batch(klecgc_ctx* const* ctxs, int32_t n_ctx,
         if (!x || !x->basis) return fail(KLECGC_E_INVALID_ARG, "NULL context");
         if (x->device != dev) return fail(KLECGC_E_INVALID_ARG, "every context must be on the current device");
         if (x->M != M) return fail(KLECGC_E_INVALID_ARG, "every context must have the same M");
-        if (x->dim == 2 && precision != KLECGC_FP64) return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 only");
+        if (x->dim == 2 && precision == KLECGC_MIXED_DEFECT)
+            return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 or MIXED only");
     }
     for (int64_t i = 0; i < n; ++i)
         if (inst[i].ctx < 0 || inst[i].ctx >= n_ctx || inst[i].J < 1)

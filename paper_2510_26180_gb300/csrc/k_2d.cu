@@ -33,15 +33,19 @@ namespace {
 constexpr int kThreads2d = 256;
 constexpr int kWarps2d = kThreads2d / 32;
 
-// Sum of NV values over the block; red: [2][NV][32] doubles, ph alternates.
+// Sum of NV <= 3 values over the block; red: [2][3][32] doubles, ph alternates.
+// The two halves are fixed (stride 3 x 32 whatever NV is), so consecutive
+// reductions never share a slot: a warp that races ahead into the next
+// reduction writes the other half while slower warps still read this one.
 template <int NV>
 __device__ __forceinline__ void block_sum(double (&v)[NV], double* red, int& ph) {
+    static_assert(NV >= 1 && NV <= 3, "reduction width");
     const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
 #pragma unroll
     for (int j = 0; j < NV; ++j)
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
-    double* b = red + ph * NV * 32;
+    double* b = red + ph * 3 * 32;
     if (lane == 0) {
 #pragma unroll
         for (int j = 0; j < NV; ++j) b[j * 32 + w] = v[j];
@@ -239,6 +243,217 @@ __global__ void __launch_bounds__(kThreads2d) k_fine2d(
     if (threadIdx.x == 0 && itcount && its_total) atomicAdd(itcount, its_total);
 }
 
+// ------------------------------------------------------------------- F, mixed
+// The same propagator with every backward-Euler step solved by FP64
+// iterative refinement around an FP32 Jacobi-PCG: the residual r = b - M x is
+// formed once in FP64 and then updated in FP64 (r -= M d for each FP32
+// correction d, x += d), so the solution is FP64-accurate (the stopping test
+// is the same ||r||_2 <= rtol ||b||_2 on the FP64 residual) while the Krylov
+// iterations run on the FP32 pipes.  Each inner solve stops at
+// ||r32|| <= tin ||r32_0|| (or maxit); at most kMaxRef refinements per step.
+// Working storage: x, r in FP64; FP32 weights, diagonal and the inner
+// vectors d, r, z, p, q.  The FP64 weights are read from wdt (global).
+constexpr int kMaxRef = 12;
+
+struct Stencil32 {
+    const float* wx;
+    const float* wy;
+    int nx;
+    __device__ __forceinline__ float apply(const float* v, int i, int ix, int iy, float c) const {
+        const float vi = v[i];
+        const float* wr = wx + iy * (nx + 1) + ix;
+        const float vw = ix > 0 ? v[i - 1] : 0.f;
+        const float ve = ix < nx - 1 ? v[i + 1] : 0.f;
+        const float vs = iy > 0 ? v[i - nx] : 0.f;
+        const float vn = iy < nx - 1 ? v[i + nx] : 0.f;
+        float acc = c * vi;
+        acc = fmaf(wr[0], vi - vw, acc);
+        acc = fmaf(wr[1], vi - ve, acc);
+        acc = fmaf(wy[iy * nx + ix], vi - vs, acc);
+        acc = fmaf(wy[(iy + 1) * nx + ix], vi - vn, acc);
+        return acc;
+    }
+    __device__ __forceinline__ float wsum(int ix, int iy) const {
+        const float* wr = wx + iy * (nx + 1) + ix;
+        return wr[0] + wr[1] + wy[iy * nx + ix] + wy[(iy + 1) * nx + ix];
+    }
+};
+
+// (I + L64) applied to the FP32 vector d, in FP64.
+__device__ __forceinline__ double apply_m64(const Stencil& L, const float* d, int i, int ix,
+                                            int iy, int nx, double c) {
+    const double di = d[i];
+    const double* wr = L.wx + iy * (nx + 1) + ix;
+    const double dw = ix > 0 ? (double)d[i - 1] : 0.0;
+    const double de = ix < nx - 1 ? (double)d[i + 1] : 0.0;
+    const double ds = iy > 0 ? (double)d[i - nx] : 0.0;
+    const double dn = iy < nx - 1 ? (double)d[i + nx] : 0.0;
+    double acc = fma(c, di, di);
+    acc = fma(wr[0], di - dw, acc);
+    acc = fma(wr[1], di - de, acc);
+    acc = fma(L.wy[iy * nx + ix], di - ds, acc);
+    acc = fma(L.wy[(iy + 1) * nx + ix], di - dn, acc);
+    return acc;
+}
+
+__global__ void __launch_bounds__(kThreads2d) k_fine2d_mixed(
+    int64_t S, int N, int nx, int J, double dtc, double dtf, double alpha, int mode,
+    const double* __restrict__ U, const double* __restrict__ u0, const double* __restrict__ wdt,
+    double rtol2, float tin2, int maxit, double* __restrict__ out, const int* __restrict__ active,
+    int* __restrict__ ifail, unsigned long long* __restrict__ itcount, double* __restrict__ gscr,
+    int64_t per_cta) {
+    extern __shared__ __align__(16) double dsm[];
+    __shared__ double red[2 * 3 * 32];
+    const int n = nx * nx, nf = 2 * nx * (nx + 1);
+    double* x = gscr ? gscr + blockIdx.x * per_cta : dsm;
+    double* r = x + n;
+    float* W32 = reinterpret_cast<float*>(r + n);
+    float* dinv = W32 + nf;
+    float* dv = dinv + n;
+    float* rv = dv + n;
+    float* zv = rv + n;
+    float* pv = zv + n;
+    float* qv = pv + n;
+    const Stencil32 L32{W32, W32 + nx * (nx + 1), nx};
+    const float c32 = (float)dtc;
+    const int64_t items = mode == 0 ? S * N : S;
+    int ph = 0;
+    unsigned long long its_total = 0;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t s = mode == 0 ? item / N : item;
+        const int n0 = mode == 0 ? (int)(item - s * N) : 0;
+        if (!active[s]) continue;
+        const double* wg = wdt + s * nf;
+        const Stencil L{wg, wg + nx * (nx + 1), nx};
+        __syncthreads();  // the previous item's epilogue has read its vectors
+        for (int e = threadIdx.x; e < nf; e += blockDim.x) W32[e] = (float)wg[e];
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int iy = i / nx, ix = i - iy * nx;
+            dinv[i] = 1.f / (1.f + c32 + L32.wsum(ix, iy));
+            x[i] = (mode == 1 || n0 == 0) ? u0[i] : U[(s * n + i) * N + n0 - 1];
+        }
+        bool failed = false;
+        const int nint = mode == 0 ? 1 : N;
+        for (int ni = 0; ni < nint; ++ni) {
+            for (int j = 0; j < J; ++j) {
+                __syncthreads();  // x complete
+                // FP64 residual of the step at x = x_old: r = dtf - L x
+                double v2[2] = {0.0, 0.0};  // ||b||^2, ||r||^2
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const int iy = i / nx, ix = i - iy * nx;
+                    const double ri = dtf - L.apply(x, i, ix, iy, dtc);
+                    const double bi = x[i] + dtf;
+                    r[i] = ri;
+                    v2[0] = fma(bi, bi, v2[0]);
+                    v2[1] = fma(ri, ri, v2[1]);
+                }
+                block_sum<2>(v2, red, ph);
+                const double lim = rtol2 * v2[0];
+                double rr64 = v2[1];
+                int ref = 0;
+                while (rr64 > lim) {
+                    if (ref++ >= kMaxRef) {
+                        failed = true;
+                        break;
+                    }
+                    // inner FP32 PCG: (I + L32) d = r / sigma, d0 = 0, sigma the RMS of
+                    // r (keeps the FP32 values and their squares far from underflow)
+                    const double sigma = sqrt(rr64 / n), isig = 1.0 / sigma;
+                    float v3[3] = {0.f, 0.f, 0.f};  // r.z, ||r||^2
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        const float ri = (float)(r[i] * isig);
+                        const float zi = dinv[i] * ri;
+                        dv[i] = 0.f;
+                        rv[i] = ri;
+                        zv[i] = zi;
+                        pv[i] = zi;
+                        v3[0] = fmaf(ri, zi, v3[0]);
+                        v3[1] = fmaf(ri, ri, v3[1]);
+                    }
+                    double w2[2] = {v3[0], v3[1]};
+                    block_sum<2>(w2, red, ph);
+                    float rz = (float)w2[0];
+                    const float ilim = tin2 * (float)w2[1];
+                    double w1[1] = {0.0};
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        const int iy = i / nx, ix = i - iy * nx;
+                        const float qi = pv[i] + L32.apply(pv, i, ix, iy, c32);
+                        qv[i] = qi;
+                        w1[0] += (double)(pv[i] * qi);
+                    }
+                    block_sum<1>(w1, red, ph);
+                    float pq = (float)w1[0];
+                    int it = 0;
+                    for (;;) {
+                        const float a = rz / pq;
+                        float u2[2] = {0.f, 0.f};
+                        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                            dv[i] = fmaf(a, pv[i], dv[i]);
+                            const float ri = fmaf(-a, qv[i], rv[i]);
+                            const float zi = dinv[i] * ri;
+                            rv[i] = ri;
+                            zv[i] = zi;
+                            u2[0] = fmaf(ri, ri, u2[0]);
+                            u2[1] = fmaf(ri, zi, u2[1]);
+                        }
+                        double y2[2] = {u2[0], u2[1]};
+                        block_sum<2>(y2, red, ph);
+                        ++it;
+                        if (!((float)y2[0] > ilim) || it >= maxit) break;
+                        const float rzn = (float)y2[1];
+                        const float beta = rzn / rz;
+                        rz = rzn;
+                        double y1[1] = {0.0};
+                        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                            const int iy = i / nx, ix = i - iy * nx;
+                            const float zi = zv[i];
+                            const float pi = fmaf(beta, pv[i], zi);
+                            const float qi = fmaf(beta, qv[i], zi + L32.apply(zv, i, ix, iy, c32));
+                            pv[i] = pi;
+                            qv[i] = qi;
+                            y1[0] += (double)(pi * qi);
+                        }
+                        block_sum<1>(y1, red, ph);
+                        pq = (float)y1[0];
+                    }
+                    its_total += it;
+                    // FP64 update: x += sigma d, r -= sigma (I + L) d   (d complete
+                    // after the last reduction)
+                    double z1[1] = {0.0};
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        const int iy = i / nx, ix = i - iy * nx;
+                        x[i] = fma(sigma, (double)dv[i], x[i]);
+                        const double ri = fma(-sigma, apply_m64(L, dv, i, ix, iy, nx, dtc), r[i]);
+                        r[i] = ri;
+                        z1[0] = fma(ri, ri, z1[0]);
+                    }
+                    block_sum<1>(z1, red, ph);
+                    rr64 = z1[0];
+                }
+            }
+            if (mode == 1) {
+                __syncthreads();
+                for (int i = threadIdx.x; i < n; i += blockDim.x) out[(s * n + i) * N + ni] = x[i];
+            }
+        }
+        if (mode == 0) {
+            __syncthreads();  // x complete
+            const double dTc = J * dtc;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int iy = i / nx, ix = i - iy * nx;
+                const double Fi = x[i];
+                const double LF = J * (L.apply(x, i, ix, iy, dtc) - dtc * Fi) + dTc * Fi;
+                const double prev = n0 == 0 ? alpha * U[(s * n + i) * N + N - 1]
+                                            : U[(s * n + i) * N + n0 - 1];
+                out[(s * n + i) * N + n0] = (Fi + LF) - prev;
+            }
+        }
+        if (failed && threadIdx.x == 0) ifail[s] = 1;
+    }
+    if (threadIdx.x == 0 && itcount && its_total) atomicAdd(itcount, its_total);
+}
+
 // ------------------------------------------------------------------- CGC (b)
 // item (s, k), k = 0..K-1: solves (lambda_k I + L_dT) q = p in place in
 // p[s][i][k] (layout [S][n_unknowns][K]).
@@ -382,6 +597,7 @@ int max_dyn_smem() {
 // Doubles of working storage per system.
 int64_t per_system(int kind, int nx) {
     const int64_t n = (int64_t)nx * nx, nf = 2 * (int64_t)nx * (nx + 1);
+    if (kind == 2) return 2 * n + (nf + 6 * n + 1) / 2;   // FP64 x, r; FP32 rest
     return kind == 0 ? nf + 6 * n : nf + (nf & 1) + 12 * n;
 }
 
@@ -399,6 +615,11 @@ Plan2D plan_2d(int kind, int nx, int64_t items) {
         if (kind == 0) {
             cudaFuncSetAttribute(k_fine2d, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fine2d, kThreads2d, pl.smem);
+        } else if (kind == 2) {
+            cudaFuncSetAttribute(k_fine2d_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 pl.smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fine2d_mixed, kThreads2d,
+                                                          pl.smem);
         } else {
             cudaFuncSetAttribute(k_cgc_solve2d, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgc_solve2d, kThreads2d, pl.smem);
@@ -425,6 +646,17 @@ void launch_fine2d(const Plan2D& pl, int64_t S, int N, int nx, int J, double dtc
     k_fine2d<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
         S, N, nx, J, dtc, dtf, alpha, mode, U, u0, wdt, rtol * rtol, maxit, out, active, ifail,
         itcount, pl.per_cta ? scratch : nullptr, pl.per_cta);
+}
+
+void launch_fine2d_mixed(const Plan2D& pl, int64_t S, int N, int nx, int J, double dtc,
+                         double dtf, double alpha, int mode, const double* U, const double* u0,
+                         const double* wdt, double rtol, double tin, int maxit, double* out,
+                         const int* active, int* ifail, unsigned long long* itcount,
+                         double* scratch, cudaStream_t st) {
+    if (S == 0) return;
+    k_fine2d_mixed<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
+        S, N, nx, J, dtc, dtf, alpha, mode, U, u0, wdt, rtol * rtol, (float)(tin * tin), maxit,
+        out, active, ifail, itcount, pl.per_cta ? scratch : nullptr, pl.per_cta);
 }
 
 void launch_cgc_solve2d(const Plan2D& pl, int64_t S, int K, int nx, double dTc,

@@ -197,13 +197,63 @@ def test_2d_unsupported_modes():
     S = 2
     xi = T(draw_xi(S, w.M, 37))
     U = torch.empty((S, w.N, w.nx * w.nx), dtype=torch.float64, device=dev())
-    for prec in (pkg.MIXED, pkg.MIXED_DEFECT):
-        with pytest.raises(pkg.KlecgcError) as e:
-            solver.solve(xi, S, w.T / w.N, w.J, w.N, w.alpha, w.tol, 5, prec, pkg.GUESS_GPC, U)
-        assert e.value.status == pkg.E_UNSUPPORTED
+    with pytest.raises(pkg.KlecgcError) as e:
+        solver.solve(xi, S, w.T / w.N, w.J, w.N, w.alpha, w.tol, 5, pkg.MIXED_DEFECT,
+                     pkg.GUESS_GPC, U)
+    assert e.value.status == pkg.E_UNSUPPORTED
     with pytest.raises(pkg.KlecgcError) as e:
         solver.mlp_set(torch.zeros(solver.mlp_n_params(), dtype=torch.float32, device=dev()))
     assert e.value.status == pkg.E_UNSUPPORTED
     with pytest.raises(pkg.KlecgcError) as e:
         solver.reference_noalloc(xi, S, w.N, w.J, U)
     assert e.value.status == pkg.E_UNSUPPORTED
+
+
+@pytest.mark.parametrize("over", [SMALL, BIG], ids=["nx15", "nx63"])
+def test_2d_fine_sweep_mixed_refinement_matches_oracle(over):
+    """The mixed propagator (FP64 refinement around FP32 PCG) meets the same
+    FP64 residual test, so it has the FP64 bar."""
+    import paper_2510_26180_gb300 as pkg
+    from oracle import pcgc
+    solver, w = solver2d(over)
+    st = oracle_setup2d("rd2d_255", **over)
+    S, dT = 3, w.T / w.N
+    xi = draw_xi(S, w.M, 38)
+    Uin = np.stack([st.reference(x) for x in xi]) * 0.97 + 2e-3
+    r = torch.empty_like(T(Uin))
+    solver.fine_sweep(T(xi), S, w.N, T(Uin), dT, w.J, w.alpha, pkg.MIXED, r)
+    assert solver.krylov_stats()[0] > 0
+    for s in range(S):
+        op = st.operator(xi[s])
+        Fend = pcgc.fine_sweep(op, st.u0, Uin[s], dT, w.J)
+        ref = pcgc.cgc_rhs(op, Uin[s], pcgc.jump_b(op, Fend, Uin[s], dT, w.alpha), dT)
+        opp = st.operator(xi[s], 4.0)
+        Fp = pcgc.fine_sweep(opp, st.u0, Uin[s], dT, w.J)
+        refp = pcgc.cgc_rhs(opp, Uin[s], pcgc.jump_b(opp, Fp, Uin[s], dT, w.alpha), dT)
+        amp = 1.0 + dT * abs(op.A).sum(1).max()
+        bar = max(1e-12, 4 * rel(refp, ref), 10 * 2.3e-16 * amp)
+        assert rel(r[s].cpu().numpy(), ref) < bar
+
+
+@pytest.mark.parametrize("over", [SMALL, MID], ids=["nx15", "nx31"])
+def test_2d_solve_mixed_matches_oracle(over):
+    import paper_2510_26180_gb300 as pkg
+    solver, w = solver2d(over)
+    st = oracle_setup2d("rd2d_255", **over)
+    S = 6
+    xi = draw_xi(S, w.M, 39)
+    n = w.nx * w.nx
+    U = torch.empty((S, w.N, n), dtype=torch.float64, device=dev())
+    it = torch.empty(S, dtype=torch.int32, device=dev())
+    stt = torch.empty(S, dtype=torch.int32, device=dev())
+    code = solver.solve(T(xi), S, w.T / w.N, w.J, w.N, w.alpha, w.tol, w.kmax, pkg.MIXED,
+                        pkg.GUESS_GPC, U, it, stt)
+    assert code == 0
+    U, it = U.cpu().numpy(), it.cpu().numpy()
+    for s in range(S):
+        Uo, ko, _ = st.solve_sample(xi[s])
+        Up, _, _ = st.solve_sample(xi[s], field_ulps=4.0)
+        Uf, _, _ = st.solve_sample(xi[s], cgc="fft")
+        floor = rel(Up, Uo) + rel(Uf, Uo)
+        assert it[s] == ko
+        assert rel(U[s], Uo) < max(1e-12, 4 * floor)
