@@ -206,24 +206,29 @@ def traffic_per_launch(cls, prec, points, launches):
     return MEASURED_TRAFFIC_B_PER_POINT[cls] * points / max(launches, 1)
 
 
-def roofline_2d(cls, ms, launches, units):
-    """2D FP64 Krylov kernels: FP64 operations (an FMA counts 2) per unknown.
+def roofline_2d(cls, ms, launches, units, prec):
+    """2D Krylov kernels: floating-point operations (an FMA counts 2) per unknown.
 
     CG iteration of F: 9 (x, r, z updates, two dot products) + 20 (stencil
     apply of z, p and q recurrences, p.q); per step 38 more (initial residual
-    and the first q = M p).  COCG iteration: 34 + 58, complex."""
+    and the first q = M p).  COCG iteration: 34 + 58, complex.  On the mixed
+    path the CG iterations are FP32 (the FP64 refinement work, ~40 flop per
+    unknown per step, is left out), so the roof is the FP32 one."""
     ns = units["ns"]
+    fp32 = prec == "mixed" and cls == "fine"
     if cls == "fine":
         flops = (29.0 * units["kry_fine"] + 38.0 * units["fine_steps"]) * ns
     elif cls == "cgc_solve":
         flops = 92.0 * units["kry_cgc"] * ns
     else:
         return None
+    peak = FP32_ALU_PEAK if fp32 else FP64_ALU_PEAK
     ach = flops / (ms / 1e3) / 1e12
-    return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK,
-            "unit": "TFLOP/s", "frac": ach / FP64_ALU_PEAK, "traffic": None,
-            "peak_source": "nominal GB300 FP64 1.25 TFLOP/s",
-            "work": f"{flops / max(launches, 1):.3e} FP64 flop per launch"}
+    return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": peak,
+            "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+            "peak_source": ("derived: 152 SMs x lanes x 2 x 2070 MHz" if fp32
+                            else "nominal GB300 FP64 1.25 TFLOP/s"),
+            "work": f"{flops / max(launches, 1):.3e} {'FP32' if fp32 else 'FP64'} flop per launch"}
 
 
 def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
@@ -231,7 +236,7 @@ def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
     if ms <= 0:
         return None
     if w.dim == 2:
-        return roofline_2d(cls, ms, launches, units)
+        return roofline_2d(cls, ms, launches, units, prec)
     row_steps = units["row_steps"]
     pts = units["points"]
     if cls == "fine":
@@ -685,7 +690,10 @@ def main():
     w = workload(args.workload, **over)
     args.overrides = over
     if w.dim == 2:
-        args.precision = "fp64"      # the 2D path is FP64 only
+        # 2D: FP64 Krylov solves, or MIXED (FP64 refinement around FP32 PCG for
+        # F); the defect variant is 1D only, so it maps to MIXED
+        if args.precision == "mixed_defect":
+            args.precision = "mixed"
         args.skip_fp64 = True
     if w.name == "heat1d_uneven":
         if args.impl == "reference":

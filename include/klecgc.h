@@ -36,7 +36,8 @@
  *    precision KLECGC_FP64 (FP64 Krylov solves) or KLECGC_MIXED (each step of
  *    F by FP64 iterative refinement around an FP32 Jacobi-PCG: the residual
  *    is kept in FP64, so the result meets the same FP64 residual test; the
- *    CGC stays FP64); it has no learned guess.
+ *    shifted CGC systems likewise around an FP32 COCG); it has no learned
+ *    guess.
  *  - No exception crosses the ABI and no device trap is used: every error
  *    is a status code; klecgc_last_error() returns a one-line detail for
  *    the calling thread.
@@ -232,7 +233,8 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
  * and lambda_n = 1 - alpha^{1/N} exp(-2 pi i (n-1)/N).  (The printed
  * eigenvector matrix Lambda_alpha F_N does not diagonalize C_alpha; its
  * inverse scaling does.)  r_in, u_out: [S][N][nx] FP64; precision FP64 or
- * KLECGC_MIXED_DEFECT (FP32 transform and solves). */
+ * KLECGC_MIXED_DEFECT (FP32 transform and solves); 2D: FP64 or KLECGC_MIXED
+ * (FP64 refinement around FP32 COCG, same FP64 residual test). */
 klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int32_t N,
                                const double* r_in, double dT, double alpha,
                                int32_t precision, double* u_out, void* stream);

@@ -1467,9 +1467,11 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
                                const double* r_in, double dT, double alpha, int32_t precision,
                                double* u_out, void* stream) {
     set_error("");
-    if (!ctx || !xi || !r_in || !u_out || S < 0 || !(alpha > 0 && alpha < 1) ||
-        (precision != KLECGC_FP64 && precision != KLECGC_MIXED_DEFECT))
+    if (!ctx || !xi || !r_in || !u_out || S < 0 || !(alpha > 0 && alpha < 1) || precision < 0 ||
+        precision > 2)
         return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (ctx->dim == 1 && precision == KLECGC_MIXED)
+        return fail(KLECGC_E_INVALID_ARG, "1D: precision FP64 or MIXED_DEFECT");
     if (!pow2_in_range(N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
     klecgc_status s = check_dT(ctx, N, dT);
     if (s != KLECGC_OK || S == 0) return s;
@@ -1479,7 +1481,9 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
     if ((s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d)) != KLECGC_OK) return s;
     const bool f64 = precision == KLECGC_FP64;
     if (ctx->dim == 2) {
-        if (!f64) return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 only");
+        if (precision == KLECGC_MIXED_DEFECT)
+            return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 or MIXED only");
+        const bool mixed = precision == KLECGC_MIXED;
         double* wdT = nullptr;
         if ((s = build_weights_2d(ctx, xi_d, S, dT, dT, st, nullptr, &wdT)) != KLECGC_OK) return s;
         std::vector<double2> lam;
@@ -1496,11 +1500,17 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
         double *sc, *isc;
         if ((s = scale_tables<double>(ctx, N, alpha, st, &sc, &isc)) != KLECGC_OK) return s;
         WS(Cplx<double>, p, "p64", S * (int64_t)nx * K);
-        const Plan2D pl = plan_2d(1, ctx->nx, S * K);
+        const Plan2D pl = plan_2d(mixed ? 3 : 1, ctx->nx, S * K);
         WS(double, scr, "k2d_scratch_c", pl.scratch_doubles);
         launch_cgc_forward<double, double>(S, N, nx, r, sc, p, active, st);
-        launch_cgc_solve2d(pl, S, K, ctx->nx, dT * ctx->prob.reaction, lam_d, wdT,
-                           ctx->kry_rtol_cgc, ctx->kry_maxit, p, active, ifail, its + 1, scr, st);
+        if (mixed)
+            launch_cgc_solve2d_mixed(pl, S, K, ctx->nx, dT * ctx->prob.reaction, lam_d, wdT,
+                                     ctx->kry_rtol_cgc, kInnerRtol, ctx->kry_maxit, p, active,
+                                     ifail, its + 1, scr, st);
+        else
+            launch_cgc_solve2d(pl, S, K, ctx->nx, dT * ctx->prob.reaction, lam_d, wdT,
+                               ctx->kry_rtol_cgc, ctx->kry_maxit, p, active, ifail, its + 1, scr,
+                               st);
         launch_cgc_inverse<double>(S, N, nx, p, isc, U, 2, nullptr, nullptr, active, st);
         TRY(cudaGetLastError());
         if ((s = export_batch(ctx, U, S, N, u_out, st)) != KLECGC_OK) return s;
@@ -1690,7 +1700,7 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
         std::vector<double2> lam;
         if ((s = upload_lambda(ctx, N, alpha, st, lam, &lam_d)) != KLECGC_OK) return s;
         plF = plan_2d(precision == KLECGC_MIXED ? 2 : 0, ctx->nx, S * N);
-        plC = plan_2d(1, ctx->nx, S * K);
+        plC = plan_2d(precision == KLECGC_MIXED ? 3 : 1, ctx->nx, S * K);
         WS(double, a1, "k2d_scratch", plF.scratch_doubles);
         WS(double, a2, "k2d_scratch_c", plC.scratch_doubles);
         scrF = a1;
@@ -1724,8 +1734,13 @@ klecgc_status SolveRun::step() {
             });
         ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<double, double>(S, N, nx, r, sc64, p64, active, st); });
         ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] {
-            launch_cgc_solve2d(plC, S, K, ctx->nx, dTreact, lam_d, wdT2, ctx->kry_rtol_cgc,
-                               ctx->kry_maxit, p64, active, ifail, kits + 1, scrC, st);
+            if (precision == KLECGC_MIXED)
+                launch_cgc_solve2d_mixed(plC, S, K, ctx->nx, dTreact, lam_d, wdT2,
+                                         ctx->kry_rtol_cgc, kInnerRtol, ctx->kry_maxit, p64,
+                                         active, ifail, kits + 1, scrC, st);
+            else
+                launch_cgc_solve2d(plC, S, K, ctx->nx, dTreact, lam_d, wdT2, ctx->kry_rtol_cgc,
+                                   ctx->kry_maxit, p64, active, ifail, kits + 1, scrC, st);
         });
         ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc64, U, 0, delta, nullptr, active, st); });
     } else {

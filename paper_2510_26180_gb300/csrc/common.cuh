@@ -117,7 +117,8 @@ struct Plan2D {
     int64_t per_cta = 0;         // doubles of global working storage per CTA
     int64_t scratch_doubles = 0; // total global working storage
 };
-// kind 0: fine propagator, 1: shifted CGC solves, 2: mixed fine; items = work items.
+// kind 0: fine propagator, 1: shifted CGC solves, 2: mixed fine, 3: mixed CGC;
+// items = work items.
 Plan2D plan_2d(int kind, int nx, int64_t items);
 // mode 0: r = (I + L_dT) F(start) - prev per (s, n); mode 1: sequential fine
 // solution out[s][.][n] per s.  wdt: [S][2 nx (nx+1)] weights dt a / h^2.
@@ -132,6 +133,11 @@ void launch_fine2d_mixed(const Plan2D& pl, int64_t S, int N, int nx, int J, doub
                          const double* wdt, double rtol, double tin, int maxit, double* out,
                          const int* active, int* ifail, unsigned long long* itcount,
                          double* scratch, cudaStream_t st);
+// (lambda_k I + L_dT) q = p in place by FP64 refinement around FP32 COCG (plan kind 3).
+void launch_cgc_solve2d_mixed(const Plan2D& pl, int64_t S, int K, int nx, double dTc,
+                              const double2* lam, const double* wdT, double rtol, double tin,
+                              int maxit, Cplx<double>* p, const int* active, int* ifail,
+                              unsigned long long* itcount, double* scratch, cudaStream_t st);
 // (lambda_k I + L_dT) q = p in place, p: [S][nx*nx][K]; wdT = dT a / h^2.
 void launch_cgc_solve2d(const Plan2D& pl, int64_t S, int K, int nx, double dTc,
                         const double2* lam, const double* wdT, double rtol, int maxit,

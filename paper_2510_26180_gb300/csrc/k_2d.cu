@@ -60,6 +60,31 @@ __device__ __forceinline__ void block_sum(double (&v)[NV], double* red, int& ph)
     ph ^= 1;
 }
 
+// The same reduction in FP32 (the inner solves of the mixed propagator; FP64
+// adds run at 1/64 of the FP32 rate).  red32: [2][3][32] floats.
+template <int NV>
+__device__ __forceinline__ void block_sum32(float (&v)[NV], float* red32, int& ph) {
+    static_assert(NV >= 1 && NV <= 3, "reduction width");
+    const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) v[j] += __shfl_xor_sync(0xffffffffu, v[j], off);
+    float* b = red32 + ph * 3 * 32;
+    if (lane == 0) {
+#pragma unroll
+        for (int j = 0; j < NV; ++j) b[j * 32 + w] = v[j];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < NV; ++j) {
+        float s = 0.f;
+        for (int q = 0; q < kWarps2d; ++q) s += b[j * 32 + q];
+        v[j] = s;
+    }
+    ph ^= 1;
+}
+
 // sum over the four faces of w_f (v_i - v_nb), plus c' v_i.
 struct Stencil {
     const double* wx;
@@ -304,6 +329,7 @@ __global__ void __launch_bounds__(kThreads2d) k_fine2d_mixed(
     int64_t per_cta) {
     extern __shared__ __align__(16) double dsm[];
     __shared__ double red[2 * 3 * 32];
+    __shared__ float red32[2 * 3 * 32];
     const int n = nx * nx, nf = 2 * nx * (nx + 1);
     double* x = gscr ? gscr + blockIdx.x * per_cta : dsm;
     double* r = x + n;
@@ -317,7 +343,7 @@ __global__ void __launch_bounds__(kThreads2d) k_fine2d_mixed(
     const Stencil32 L32{W32, W32 + nx * (nx + 1), nx};
     const float c32 = (float)dtc;
     const int64_t items = mode == 0 ? S * N : S;
-    int ph = 0;
+    int ph = 0, ph32 = 0;
     unsigned long long its_total = 0;
     for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
         const int64_t s = mode == 0 ? item / N : item;
@@ -371,19 +397,19 @@ __global__ void __launch_bounds__(kThreads2d) k_fine2d_mixed(
                         v3[0] = fmaf(ri, zi, v3[0]);
                         v3[1] = fmaf(ri, ri, v3[1]);
                     }
-                    double w2[2] = {v3[0], v3[1]};
-                    block_sum<2>(w2, red, ph);
-                    float rz = (float)w2[0];
-                    const float ilim = tin2 * (float)w2[1];
-                    double w1[1] = {0.0};
+                    float w2[2] = {v3[0], v3[1]};
+                    block_sum32<2>(w2, red32, ph32);
+                    float rz = w2[0];
+                    const float ilim = tin2 * w2[1];
+                    float w1[1] = {0.f};
                     for (int i = threadIdx.x; i < n; i += blockDim.x) {
                         const int iy = i / nx, ix = i - iy * nx;
                         const float qi = pv[i] + L32.apply(pv, i, ix, iy, c32);
                         qv[i] = qi;
-                        w1[0] += (double)(pv[i] * qi);
+                        w1[0] = fmaf(pv[i], qi, w1[0]);
                     }
-                    block_sum<1>(w1, red, ph);
-                    float pq = (float)w1[0];
+                    block_sum32<1>(w1, red32, ph32);
+                    float pq = w1[0];
                     int it = 0;
                     for (;;) {
                         const float a = rz / pq;
@@ -397,14 +423,13 @@ __global__ void __launch_bounds__(kThreads2d) k_fine2d_mixed(
                             u2[0] = fmaf(ri, ri, u2[0]);
                             u2[1] = fmaf(ri, zi, u2[1]);
                         }
-                        double y2[2] = {u2[0], u2[1]};
-                        block_sum<2>(y2, red, ph);
+                        block_sum32<2>(u2, red32, ph32);
                         ++it;
-                        if (!((float)y2[0] > ilim) || it >= maxit) break;
-                        const float rzn = (float)y2[1];
+                        if (!(u2[0] > ilim) || it >= maxit) break;
+                        const float rzn = u2[1];
                         const float beta = rzn / rz;
                         rz = rzn;
-                        double y1[1] = {0.0};
+                        float y1[1] = {0.f};
                         for (int i = threadIdx.x; i < n; i += blockDim.x) {
                             const int iy = i / nx, ix = i - iy * nx;
                             const float zi = zv[i];
@@ -412,10 +437,10 @@ __global__ void __launch_bounds__(kThreads2d) k_fine2d_mixed(
                             const float qi = fmaf(beta, qv[i], zi + L32.apply(zv, i, ix, iy, c32));
                             pv[i] = pi;
                             qv[i] = qi;
-                            y1[0] += (double)(pi * qi);
+                            y1[0] = fmaf(pi, qi, y1[0]);
                         }
-                        block_sum<1>(y1, red, ph);
-                        pq = (float)y1[0];
+                        block_sum32<1>(y1, red32, ph32);
+                        pq = y1[0];
                     }
                     its_total += it;
                     // FP64 update: x += sigma d, r -= sigma (I + L) d   (d complete
@@ -580,6 +605,225 @@ __global__ void __launch_bounds__(kThreads2d) k_cgc_solve2d(
     if (threadIdx.x == 0 && itcount && its_total) atomicAdd(itcount, its_total);
 }
 
+// ------------------------------------------------------------------- CGC (b), mixed
+// The shifted solves by FP64 iterative refinement around an FP32 Jacobi-COCG,
+// as for F: x accumulates in FP64 in the output p itself, the residual is
+// kept and updated in FP64 (complex), each correction equation is scaled by
+// the residual's RMS and solved in FP32 to tin; the stopping test is
+// ||r||_2 <= rtol ||p_k||_2 on the FP64 residual.  Working storage: r in FP64
+// (complex); FP32 weights, complex diagonal and the inner vectors d, r, z, p, q.
+__device__ __forceinline__ float2 cmulf(float2 a, float2 b) {
+    return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
+}
+
+// L32 applied to a complex FP32 vector (real weights).
+__device__ __forceinline__ float2 apply2f(const Stencil32& L, const float2* v, int i, int ix,
+                                         int iy, float c) {
+    const int nx = L.nx;
+    const float2 vi = v[i];
+    const float2 z = make_float2(0.f, 0.f);
+    const float* wr = L.wx + iy * (nx + 1) + ix;
+    const float2 vw = ix > 0 ? v[i - 1] : z;
+    const float2 ve = ix < nx - 1 ? v[i + 1] : z;
+    const float2 vs = iy > 0 ? v[i - nx] : z;
+    const float2 vn = iy < nx - 1 ? v[i + nx] : z;
+    const float a0 = wr[0], a1 = wr[1], a2 = L.wy[iy * nx + ix], a3 = L.wy[(iy + 1) * nx + ix];
+    float re = c * vi.x, im = c * vi.y;
+    re = fmaf(a0, vi.x - vw.x, re);
+    im = fmaf(a0, vi.y - vw.y, im);
+    re = fmaf(a1, vi.x - ve.x, re);
+    im = fmaf(a1, vi.y - ve.y, im);
+    re = fmaf(a2, vi.x - vs.x, re);
+    im = fmaf(a2, vi.y - vs.y, im);
+    re = fmaf(a3, vi.x - vn.x, re);
+    im = fmaf(a3, vi.y - vn.y, im);
+    return make_float2(re, im);
+}
+
+// (lambda I + L64) applied to the complex FP32 vector d, in FP64.
+__device__ __forceinline__ double2 apply_shift64(const Stencil& L, const float2* d, int i, int ix,
+                                                 int iy, int nx, double c, double2 lk) {
+    const float2 df = d[i];
+    const double dr = df.x, di = df.y;
+    const double* wr = L.wx + iy * (nx + 1) + ix;
+    const float2 z = make_float2(0.f, 0.f);
+    const float2 fw = ix > 0 ? d[i - 1] : z;
+    const float2 fe = ix < nx - 1 ? d[i + 1] : z;
+    const float2 fs = iy > 0 ? d[i - nx] : z;
+    const float2 fn = iy < nx - 1 ? d[i + nx] : z;
+    const double a0 = wr[0], a1 = wr[1], a2 = L.wy[iy * nx + ix], a3 = L.wy[(iy + 1) * nx + ix];
+    double re = fma(lk.x, dr, fma(-lk.y, di, c * dr));
+    double im = fma(lk.x, di, fma(lk.y, dr, c * di));
+    re = fma(a0, dr - fw.x, re);
+    im = fma(a0, di - fw.y, im);
+    re = fma(a1, dr - fe.x, re);
+    im = fma(a1, di - fe.y, im);
+    re = fma(a2, dr - fs.x, re);
+    im = fma(a2, di - fs.y, im);
+    re = fma(a3, dr - fn.x, re);
+    im = fma(a3, di - fn.y, im);
+    return make_double2(re, im);
+}
+
+__global__ void __launch_bounds__(kThreads2d) k_cgc_solve2d_mixed(
+    int64_t S, int K, int nx, double dTc, const double2* __restrict__ lam,
+    const double* __restrict__ wdT, double rtol2, float tin2, int maxit,
+    double2* __restrict__ pio, const int* __restrict__ active, int* __restrict__ ifail,
+    unsigned long long* __restrict__ itcount, double* __restrict__ gscr, int64_t per_cta) {
+    extern __shared__ __align__(16) double dsm[];
+    __shared__ double red[2 * 3 * 32];
+    __shared__ float red32[2 * 3 * 32];
+    const int n = nx * nx, nf = 2 * nx * (nx + 1);
+    double2* r = reinterpret_cast<double2*>(gscr ? gscr + blockIdx.x * per_cta : dsm);
+    float* W32 = reinterpret_cast<float*>(r + n);
+    float2* dinv = reinterpret_cast<float2*>(W32 + nf + (nf & 1));
+    float2* dv = dinv + n;
+    float2* rv = dv + n;
+    float2* zv = rv + n;
+    float2* pv = zv + n;
+    float2* qv = pv + n;
+    const Stencil32 L32{W32, W32 + nx * (nx + 1), nx};
+    const float c32 = (float)dTc;
+    int ph = 0, ph32 = 0;
+    unsigned long long its_total = 0;
+    for (int64_t item = blockIdx.x; item < S * K; item += gridDim.x) {
+        const int64_t s = item / K;
+        const int k = (int)(item - s * K);
+        if (!active[s]) continue;
+        const double* wg = wdT + s * nf;
+        const Stencil L{wg, wg + nx * (nx + 1), nx};
+        const double2 lk = lam[k];
+        const float2 lk32 = make_float2((float)lk.x, (float)lk.y);
+        __syncthreads();  // the previous item is done with the shared vectors
+        for (int e = threadIdx.x; e < nf; e += blockDim.x) W32[e] = (float)wg[e];
+        __syncthreads();
+        double v1[1] = {0.0};  // ||b||^2
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int iy = i / nx, ix = i - iy * nx;
+            const float dr = lk32.x + c32 + L32.wsum(ix, iy), di = lk32.y;
+            const float den = dr * dr + di * di;
+            dinv[i] = make_float2(dr / den, -di / den);
+            double2* o = pio + (s * n + i) * K + k;
+            const double2 b = *o;
+            r[i] = b;
+            *o = make_double2(0.0, 0.0);   // x accumulates here
+            v1[0] = fma(b.x, b.x, fma(b.y, b.y, v1[0]));
+        }
+        block_sum<1>(v1, red, ph);
+        const double lim = rtol2 * v1[0];
+        double rr64 = v1[0];
+        bool failed = false;
+        int ref = 0;
+        while (rr64 > lim) {
+            if (ref++ >= kMaxRef) {
+                failed = true;
+                break;
+            }
+            const double sigma = sqrt(rr64 / n), isig = 1.0 / sigma;
+            // inner FP32 COCG: (lambda I + L32) d = r / sigma, d0 = 0
+            float v3[3] = {0.f, 0.f, 0.f};  // ||r||^2, r.z (complex, unconjugated)
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const double2 rd = r[i];
+                const float2 ri = make_float2((float)(rd.x * isig), (float)(rd.y * isig));
+                const float2 zi = cmulf(dinv[i], ri);
+                dv[i] = make_float2(0.f, 0.f);
+                rv[i] = ri;
+                zv[i] = zi;
+                pv[i] = zi;
+                v3[0] = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, v3[0]));
+                v3[1] = fmaf(ri.x, zi.x, fmaf(-ri.y, zi.y, v3[1]));
+                v3[2] = fmaf(ri.x, zi.y, fmaf(ri.y, zi.x, v3[2]));
+            }
+            block_sum32<3>(v3, red32, ph32);
+            const float ilim = tin2 * v3[0];
+            float rzr = v3[1], rzi = v3[2];
+            // q = M p, p.q
+            float w2[2] = {0.f, 0.f};
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int iy = i / nx, ix = i - iy * nx;
+                const float2 pi = pv[i];
+                const float2 lp = apply2f(L32, pv, i, ix, iy, c32);
+                const float2 qi = make_float2(lk32.x * pi.x - lk32.y * pi.y + lp.x,
+                                              lk32.x * pi.y + lk32.y * pi.x + lp.y);
+                qv[i] = qi;
+                w2[0] = fmaf(pi.x, qi.x, fmaf(-pi.y, qi.y, w2[0]));
+                w2[1] = fmaf(pi.x, qi.y, fmaf(pi.y, qi.x, w2[1]));
+            }
+            block_sum32<2>(w2, red32, ph32);
+            float pqr = w2[0], pqi = w2[1];
+            int it = 0;
+            for (;;) {
+                const float den = pqr * pqr + pqi * pqi;
+                const float ar = (rzr * pqr + rzi * pqi) / den, ai = (rzi * pqr - rzr * pqi) / den;
+                float u3[3] = {0.f, 0.f, 0.f};
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const float2 pi = pv[i], qi = qv[i], dvi = dinv[i];
+                    float2 di = dv[i], ri = rv[i];
+                    di.x = fmaf(ar, pi.x, fmaf(-ai, pi.y, di.x));
+                    di.y = fmaf(ar, pi.y, fmaf(ai, pi.x, di.y));
+                    ri.x = fmaf(-ar, qi.x, fmaf(ai, qi.y, ri.x));
+                    ri.y = fmaf(-ar, qi.y, fmaf(-ai, qi.x, ri.y));
+                    const float2 zi = cmulf(dvi, ri);
+                    dv[i] = di;
+                    rv[i] = ri;
+                    zv[i] = zi;
+                    u3[0] = fmaf(ri.x, ri.x, fmaf(ri.y, ri.y, u3[0]));
+                    u3[1] = fmaf(ri.x, zi.x, fmaf(-ri.y, zi.y, u3[1]));
+                    u3[2] = fmaf(ri.x, zi.y, fmaf(ri.y, zi.x, u3[2]));
+                }
+                block_sum32<3>(u3, red32, ph32);
+                ++it;
+                if (!(u3[0] > ilim) || it >= maxit) break;
+                const float dd = rzr * rzr + rzi * rzi;
+                const float br = (u3[1] * rzr + u3[2] * rzi) / dd, bi = (u3[2] * rzr - u3[1] * rzi) / dd;
+                rzr = u3[1];
+                rzi = u3[2];
+                float y2[2] = {0.f, 0.f};
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const int iy = i / nx, ix = i - iy * nx;
+                    const float2 zi = zv[i], po = pv[i], qo = qv[i];
+                    const float2 lz = apply2f(L32, zv, i, ix, iy, c32);
+                    const float2 mz = make_float2(lk32.x * zi.x - lk32.y * zi.y + lz.x,
+                                                  lk32.x * zi.y + lk32.y * zi.x + lz.y);
+                    const float2 pn = make_float2(fmaf(br, po.x, fmaf(-bi, po.y, zi.x)),
+                                                  fmaf(br, po.y, fmaf(bi, po.x, zi.y)));
+                    const float2 qn = make_float2(fmaf(br, qo.x, fmaf(-bi, qo.y, mz.x)),
+                                                  fmaf(br, qo.y, fmaf(bi, qo.x, mz.y)));
+                    pv[i] = pn;
+                    qv[i] = qn;
+                    y2[0] = fmaf(pn.x, qn.x, fmaf(-pn.y, qn.y, y2[0]));
+                    y2[1] = fmaf(pn.x, qn.y, fmaf(pn.y, qn.x, y2[1]));
+                }
+                block_sum32<2>(y2, red32, ph32);
+                pqr = y2[0];
+                pqi = y2[1];
+            }
+            its_total += it;
+            // FP64 update: x += sigma d (in the output), r -= sigma (lambda I + L) d
+            double z1[1] = {0.0};
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int iy = i / nx, ix = i - iy * nx;
+                double2* o = pio + (s * n + i) * K + k;
+                const float2 di = dv[i];
+                double2 xo = *o;
+                xo.x = fma(sigma, (double)di.x, xo.x);
+                xo.y = fma(sigma, (double)di.y, xo.y);
+                *o = xo;
+                const double2 md = apply_shift64(L, dv, i, ix, iy, nx, dTc, lk);
+                double2 ri = r[i];
+                ri.x = fma(-sigma, md.x, ri.x);
+                ri.y = fma(-sigma, md.y, ri.y);
+                r[i] = ri;
+                z1[0] = fma(ri.x, ri.x, fma(ri.y, ri.y, z1[0]));
+            }
+            block_sum<1>(z1, red, ph);
+            rr64 = z1[0];
+        }
+        if (failed && threadIdx.x == 0) ifail[s] = 1;
+    }
+    if (threadIdx.x == 0 && itcount && its_total) atomicAdd(itcount, its_total);
+}
+
 int num_sms() {
     int dev = 0, v = 0;
     cudaGetDevice(&dev);
@@ -598,6 +842,7 @@ int max_dyn_smem() {
 int64_t per_system(int kind, int nx) {
     const int64_t n = (int64_t)nx * nx, nf = 2 * (int64_t)nx * (nx + 1);
     if (kind == 2) return 2 * n + (nf + 6 * n + 1) / 2;   // FP64 x, r; FP32 rest
+    if (kind == 3) return 2 * n + (nf + (nf & 1) + 12 * n + 1) / 2;  // FP64 r; FP32 rest
     return kind == 0 ? nf + 6 * n : nf + (nf & 1) + 12 * n;
 }
 
@@ -619,6 +864,11 @@ Plan2D plan_2d(int kind, int nx, int64_t items) {
             cudaFuncSetAttribute(k_fine2d_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  pl.smem);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fine2d_mixed, kThreads2d,
+                                                          pl.smem);
+        } else if (kind == 3) {
+            cudaFuncSetAttribute(k_cgc_solve2d_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 pl.smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgc_solve2d_mixed, kThreads2d,
                                                           pl.smem);
         } else {
             cudaFuncSetAttribute(k_cgc_solve2d, cudaFuncAttributeMaxDynamicSharedMemorySize, pl.smem);
@@ -657,6 +907,17 @@ void launch_fine2d_mixed(const Plan2D& pl, int64_t S, int N, int nx, int J, doub
     k_fine2d_mixed<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
         S, N, nx, J, dtc, dtf, alpha, mode, U, u0, wdt, rtol * rtol, (float)(tin * tin), maxit,
         out, active, ifail, itcount, pl.per_cta ? scratch : nullptr, pl.per_cta);
+}
+
+void launch_cgc_solve2d_mixed(const Plan2D& pl, int64_t S, int K, int nx, double dTc,
+                              const double2* lam, const double* wdT, double rtol, double tin,
+                              int maxit, Cplx<double>* p, const int* active, int* ifail,
+                              unsigned long long* itcount, double* scratch, cudaStream_t st) {
+    if (S == 0) return;
+    k_cgc_solve2d_mixed<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
+        S, K, nx, dTc, lam, wdT, rtol * rtol, (float)(tin * tin), maxit,
+        reinterpret_cast<double2*>(p), active, ifail, itcount, pl.per_cta ? scratch : nullptr,
+        pl.per_cta);
 }
 
 void launch_cgc_solve2d(const Plan2D& pl, int64_t S, int K, int nx, double dTc,

@@ -257,3 +257,27 @@ def test_2d_solve_mixed_matches_oracle(over):
         floor = rel(Up, Uo) + rel(Uf, Uo)
         assert it[s] == ko
         assert rel(U[s], Uo) < max(1e-12, 4 * floor)
+
+
+@pytest.mark.parametrize("over,alpha", [(SMALL, 1e-3), (MID, 1e-2), (BIG, 1e-3)],
+                         ids=["nx15", "nx31", "nx63"])
+def test_2d_cgc_apply_mixed_refinement_matches_oracle(over, alpha):
+    import paper_2510_26180_gb300 as pkg
+    from oracle import pcgc
+    solver, w = solver2d(over)
+    st = oracle_setup2d("rd2d_255", **over)
+    S, N, dT = 3, w.N, w.T / w.N
+    n = w.nx * w.nx
+    xi = draw_xi(S, w.M, 40)
+    r = np.random.default_rng(7).standard_normal((S, N, n))
+    u = torch.empty_like(T(r))
+    solver.cgc_apply(T(xi), S, N, T(r), dT, alpha, pkg.MIXED, u)
+    assert solver.krylov_stats()[1] > 0
+    for s in range(S):
+        op = st.operator(xi[s])
+        ref = pcgc.cgc_diagonalized(op, r[s], dT, alpha)
+        floor = rel(pcgc.cgc_diagonalized(op, r[s], dT, alpha, fft=True), ref)
+        floor += rel(pcgc.cgc_diagonalized(st.operator(xi[s], 4.0), r[s], dT, alpha), ref)
+        kry = 4 * 2.2e-16 * shifted_cond(op, dT, alpha, N) * alpha ** (-(N - 1) / N)
+        d = rel(u[s].cpu().numpy(), ref)
+        assert d < max(1e-12, 4 * floor, kry), (s, d, floor, kry)
