@@ -170,6 +170,22 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S,
                            int32_t* status_out, void* stream);
 
 /*
+ * klecgc_solve_parareal - classical parareal (Algorithm 1, eq. pred_correc),
+ * the paper's comparison method: every iteration runs F on all intervals in
+ * parallel and then the sequential coarse correction
+ *     U^{k+1}_n = G(U^{k+1}_{n-1}) + F(U^k_{n-1}) - G(U^k_{n-1}),  U_0 = u0,
+ * with G one backward-Euler step of dT, per sample in order of n (no alpha
+ * twist, no diagonalization).  FP64, 1D contexts (UNSUPPORTED for dim = 2).
+ * Arguments, stopping rule, outputs and return as klecgc_solve, except: any
+ * N >= 1 (no FFT); guess KLECGC_GUESS_GPC (N must be the setup's N), _ZERO,
+ * _USER or _COARSE (the usual parareal start, U^0_n = G(U^0_{n-1})).
+ */
+klecgc_status klecgc_solve_parareal(klecgc_ctx* ctx, const double* xi, int64_t S, double dT,
+                                    int32_t J, int32_t N, double tol, int32_t kmax,
+                                    int32_t guess, const double* U_guess, double* U_out,
+                                    int32_t* iters_out, int32_t* status_out, void* stream);
+
+/*
  * klecgc_solve_batch - klecgc_solve for an uneven batch of n instances whose
  * grids, time partitions and fine steps differ (a library facility for
  * many small problems at once; the paper solves one configuration at a

@@ -1910,6 +1910,81 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
     return status_summary(hs, capped);
 }
 
+klecgc_status klecgc_solve_parareal(klecgc_ctx* ctx, const double* xi, int64_t S, double dT,
+                                    int32_t J, int32_t N, double tol, int32_t kmax,
+                                    int32_t guess, const double* U_guess, double* U_out,
+                                    int32_t* iters_out, int32_t* status_out, void* stream) {
+    set_error("");
+    if (!ctx) return fail(KLECGC_E_INVALID_ARG, "NULL context");
+    if (S < 0 || (S > 0 && (!xi || !U_out))) return fail(KLECGC_E_INVALID_ARG, "bad array argument");
+    if (J < 1 || N < 1 || N > 4096 || !(tol > 0) || kmax < 1 || guess < 0 || guess > 3 ||
+        (guess == KLECGC_GUESS_USER && !U_guess && S > 0))
+        return fail(KLECGC_E_INVALID_ARG, "argument out of range");
+    if (ctx->dim != 1) return fail(KLECGC_E_UNSUPPORTED, "classical parareal: 1D only");
+    if (guess == KLECGC_GUESS_GPC && N != ctx->N)
+        return fail(KLECGC_E_INVALID_ARG, "the gPC guess needs the setup's N");
+    klecgc_status s = check_dT(ctx, N, dT);
+    if (s != KLECGC_OK) return s;
+    if (S == 0) return KLECGC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int nx = ctx->nx;
+    const int64_t NS = S * (int64_t)nx * N;
+    const double* xi_d = nullptr;
+    if ((s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d)) != KLECGC_OK) return s;
+    bool finite = true;
+    if ((s = check_xi_finite(ctx, xi_d, S * ctx->M, st, &finite)) != KLECGC_OK) return s;
+    if (!finite) return fail(KLECGC_E_NONFINITE, "xi has a non-finite entry");
+    Operators op;
+    if ((s = build_operators(ctx, xi_d, S, N, J, dT, 0.5, 1, 0, st, &op)) != KLECGC_OK) return s;
+    WS(FineCoef64, gc, "coarse64", S * (int64_t)(nx + 1));
+    ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_factors(op.a, S, nx, ctx->h, dT, ctx->prob.reaction, gc, nullptr, st); });
+    WS(double, U, "U", NS);
+    if (guess == KLECGC_GUESS_GPC) {
+        if ((s = gpc_guess_internal(ctx, xi_d, S, true, U, st)) != KLECGC_OK) return s;
+    } else if (guess == KLECGC_GUESS_ZERO) {
+        TRY(cudaMemsetAsync(U, 0, NS * sizeof(double), st));
+    } else if (guess == KLECGC_GUESS_COARSE) {
+        if ((s = coarse_guess_internal(ctx, S, N, dT, op.a, U, st)) != KLECGC_OK) return s;
+    } else if ((s = import_batch(ctx, U_guess, S, N, U, st)) != KLECGC_OK) {
+        return s;
+    }
+    WS(double, F, "r", NS);
+    WS(double, scr, "par_scratch", 2 * S * (int64_t)nx);
+    WS(int, active, "active", S);
+    WS(int32_t, iters, "iters", S);
+    WS(int32_t, status, "status", S);
+    WS(unsigned long long, delta, "delta", S);
+    WS(int, n_active, "n_active", 1);
+    TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
+    TRY(cudaMemsetAsync(iters, 0xff, S * sizeof(int32_t), st));
+    TRY(cudaMemsetAsync(status, 0, S * sizeof(int32_t), st));
+    PinnedInts pin;
+    TRY(cudaMallocHost(&pin.p, sizeof(int)));
+    const double dTf = dT * ctx->prob.forcing;
+    for (int k = 0; k < kmax; ++k) {
+        ctx->launch(KLECGC_K_FINE, st, [&] {
+            launch_fine_sweep_fp64(S, N, nx, J, dT, 0.5, ctx->prob.reaction, ctx->prob.forcing, U,
+                                   ctx->u0, op.f64, op.wT, F, active, st, 0);
+        });
+        ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_parareal_correct(S, N, nx, dTf, ctx->u0, gc, F, U, scr, delta, active, st); });
+        TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
+        ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
+        TRY(cudaGetLastError());
+        TRY(cudaMemcpyAsync(pin.p, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (*pin.p == 0) break;
+    }
+    if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) return s;
+    std::vector<int32_t> hs(S), hi(S);
+    TRY(cudaMemcpyAsync(hs.data(), status, S * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(hi.data(), iters, S * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    ctx->prof_collect();
+    if (iters_out) TRY(cudaMemcpy(iters_out, hi.data(), S * 4, cudaMemcpyDefault));
+    if (status_out) TRY(cudaMemcpy(status_out, hs.data(), S * 4, cudaMemcpyDefault));
+    return status_summary(hs, false);
+}
+
 klecgc_status klecgc_solve_batch(klecgc_ctx* const* ctxs, int32_t n_ctx,
                                  const klecgc_instance* inst, int64_t n, const double* xi,
                                  double alpha, double tol, int32_t kmax, int32_t precision,

@@ -90,7 +90,12 @@ void launch_to_float(const double* x, float* y, int64_t n, cudaStream_t st);
 void launch_fine_sweep_fp64(int64_t S, int N, int nx, int J, double dT, double alpha, double react,
                             double forcing, const double* U, const double* u0,
                             const FineCoef64* fc, const double* wT, double* r, const int* active,
-                            cudaStream_t st);
+                            cudaStream_t st, int jump = 1);
+// Classical parareal correction (Algorithm 1), one thread per sample; gc: LU
+// factors of I + dT(A + cI); F: fine end values; U updated in place.
+void launch_parareal_correct(int64_t S, int N, int nx, double dTf, const double* u0,
+                             const FineCoef64* gc, const double* F, double* U, double* scratch,
+                             unsigned long long* delta, const int* active, cudaStream_t st);
 // ---- k_fine32.cu ----
 // FP32 increment-form fine sweep, register resident.  in_mode 0: Facc = F(start);
 // in_mode 1: Facc += F0(c32 of interval n-1).  out_mode 0: r (FP64); 1: defect d32.

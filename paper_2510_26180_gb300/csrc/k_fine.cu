@@ -20,10 +20,12 @@ __device__ __forceinline__ double prev_value(const double* Us, int i, int n, int
 }
 
 // FP64: direct Thomas on the LU factors of M_F, state in place in r.
+// jump = 0 leaves the fine end values F_n themselves in r (classical parareal).
 __global__ void __launch_bounds__(128) k_fine_sweep_fp64(
     int64_t S, int N, int nx, int J, double dT, double alpha, double dTreact, double dtf,
     const double* __restrict__ U, const double* __restrict__ u0, const FineCoef64* __restrict__ fc,
-    const double* __restrict__ wT, double* __restrict__ r, const int* __restrict__ active) {
+    const double* __restrict__ wT, double* __restrict__ r, const int* __restrict__ active,
+    int jump) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     int64_t s = t / N;
     int n = (int)(t - s * N);
@@ -47,6 +49,7 @@ __global__ void __launch_bounds__(128) k_fine_sweep_fp64(
             *p = x;
         }
     }
+    if (!jump) return;
     // the jump reads F at rows i-1..i+1 of its own column: write r into the
     // same column only after F_{i+1} has been read (sliding window below).
     double Fm = 0.0, Fi = rs[n];
@@ -63,12 +66,79 @@ __global__ void __launch_bounds__(128) k_fine_sweep_fp64(
 void launch_fine_sweep_fp64(int64_t S, int N, int nx, int J, double dT, double alpha, double react,
                             double forcing, const double* U, const double* u0,
                             const FineCoef64* fc, const double* wT, double* r, const int* active,
-                            cudaStream_t st) {
+                            cudaStream_t st, int jump) {
     int64_t n = S * N;
     if (n == 0) return;
     double dt = dT / J;
     k_fine_sweep_fp64<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
-        S, N, nx, J, dT, alpha, dT * react, dt * forcing, U, u0, fc, wT, r, active);
+        S, N, nx, J, dT, alpha, dT * react, dt * forcing, U, u0, fc, wT, r, active, jump);
+}
+
+// Sequential correction of classical parareal (Algorithm 1, eq. pred_correc):
+//     U^{k+1}_n = G(U^{k+1}_{n-1}) + F(U^k_{n-1}) - G(U^k_{n-1}),  U_0 = u0,
+// G one backward-Euler step of dT (LU factors gc of I + dT(A + cI)).  One
+// thread per sample; F: the fine end values [S][nx][N]; U is updated in place
+// (G(U^k_{n-1}) is taken before U_{n-1} is overwritten); scratch [2][nx][S]
+// holds G(U^k_{n-1}) and the new start value.  delta[s] receives the bit
+// pattern of max_n ||U^{k+1}_n - U^k_n||_inf (NaN kept).
+__device__ __forceinline__ void be_solve_col(const FineCoef64* c, int nx, double dtf, double* v,
+                                             int64_t stride) {
+    double y = 0.0;
+    for (int i = 0; i < nx; ++i) {
+        y = fma(-c[i].l, y, v[i * stride] + dtf);
+        v[i * stride] = y;
+    }
+    double x = 0.0;
+    for (int i = nx - 1; i >= 0; --i) {
+        x = fma(c[i + 1].wd, x, v[i * stride]) * c[i].dinv;
+        v[i * stride] = x;
+    }
+}
+
+__global__ void __launch_bounds__(64) k_parareal_correct(
+    int64_t S, int N, int nx, double dTf, const double* __restrict__ u0,
+    const FineCoef64* __restrict__ gc, const double* __restrict__ F, double* __restrict__ U,
+    double* __restrict__ scratch, unsigned long long* __restrict__ delta,
+    const int* __restrict__ active) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= S || !active[s]) return;
+    const FineCoef64* c = gc + s * (nx + 1);
+    double* gold = scratch + s;                  // [nx][S]
+    double* vnew = scratch + (int64_t)nx * S + s;
+    const double* Fs = F + s * (int64_t)nx * N;
+    double* Us = U + s * (int64_t)nx * N;
+    // G(U^k_0 := u0) and the new start value u0
+    for (int i = 0; i < nx; ++i) {
+        gold[(int64_t)i * S] = u0[i];
+        vnew[(int64_t)i * S] = u0[i];
+    }
+    be_solve_col(c, nx, dTf, gold, S);
+    double dmax = 0.0;
+    bool bad = false;
+    for (int n = 0; n < N; ++n) {
+        be_solve_col(c, nx, dTf, vnew, S);   // G(U^{k+1}_{n-1})
+        for (int i = 0; i < nx; ++i) {
+            const int64_t o = (int64_t)i * N + n;
+            const double uold = Us[o];
+            const double unew = vnew[(int64_t)i * S] + Fs[o] - gold[(int64_t)i * S];
+            gold[(int64_t)i * S] = uold;     // start of G(U^k_n) for the next n
+            vnew[(int64_t)i * S] = unew;
+            Us[o] = unew;
+            const double d = fabs(unew - uold);
+            dmax = fmax(dmax, d);
+            bad |= d != d;
+        }
+        if (n + 1 < N) be_solve_col(c, nx, dTf, gold, S);  // G(U^k_n)
+    }
+    delta[s] = bad ? 0x7ff8000000000000ull : (unsigned long long)__double_as_longlong(dmax);
+}
+
+void launch_parareal_correct(int64_t S, int N, int nx, double dTf, const double* u0,
+                             const FineCoef64* gc, const double* F, double* U, double* scratch,
+                             unsigned long long* delta, const int* active, cudaStream_t st) {
+    if (S == 0) return;
+    k_parareal_correct<<<(unsigned)((S + 63) / 64), 64, 0, st>>>(S, N, nx, dTf, u0, gc, F, U,
+                                                                scratch, delta, active);
 }
 
 // r = (I + dT(A + cI)) F - prev in FP64 for an FP32 F (stage entry of the

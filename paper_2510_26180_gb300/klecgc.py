@@ -26,7 +26,7 @@ EXPORTS = ["klecgc_setup", "klecgc_solve", "klecgc_field", "klecgc_guess", "klec
            "klecgc_profile_read", "klecgc_reference_noalloc", "klecgc_mlp_set", "klecgc_mlp_get",
            "klecgc_mlp_loss_grad", "klecgc_mlp_train", "klecgc_mlp_guess", "klecgc_downsample",
            "klecgc_set_krylov", "klecgc_krylov_stats", "klecgc_save", "klecgc_load",
-           "klecgc_solve_batch"]
+           "klecgc_solve_batch", "klecgc_solve_parareal"]
 PROFILE_CLASSES = ["field", "factors", "guess", "fine", "cgc_fwd", "cgc_solve", "cgc_inv",
                    "conv", "layout"]
 
@@ -100,6 +100,7 @@ def load() -> ctypes.CDLL:
         "klecgc_downsample": [P, P, I64, I32, P, P],
         "klecgc_profile_read": [P, ctypes.POINTER(Profile)],
         "klecgc_set_krylov": [P, D, D, I32],
+        "klecgc_solve_parareal": [P, P, I64, D, I32, I32, D, I32, I32, P, P, P, P, P],
         "klecgc_save": [P, ctypes.c_char_p],
         "klecgc_load": [ctypes.c_char_p, ctypes.POINTER(P), P],
         "klecgc_solve_batch": [ctypes.POINTER(P), I32, ctypes.POINTER(Instance), I64, P, D, D,
@@ -233,6 +234,15 @@ class Solver:
               allow=(OK, E_NOT_CONVERGED, E_NONFINITE)) -> int:
         return _check(self.lib.klecgc_solve(
             self.h, _ptr(xi, np.float64), S, dT, J, N, alpha, tol, kmax, precision, guess,
+            _ptr(U_guess, np.float64), _ptr(U_out, np.float64), _ptr(iters_out, np.int32),
+            _ptr(status_out, np.int32), _stream(stream)), allow)
+
+    def solve_parareal(self, xi, S, dT, J, N, tol, kmax, guess, U_out, iters_out=None,
+                       status_out=None, U_guess=None, stream=None,
+                       allow=(OK, E_NOT_CONVERGED, E_NONFINITE)) -> int:
+        """Classical parareal (Algorithm 1): the paper's comparison method."""
+        return _check(self.lib.klecgc_solve_parareal(
+            self.h, _ptr(xi, np.float64), S, dT, J, N, tol, kmax, guess,
             _ptr(U_guess, np.float64), _ptr(U_out, np.float64), _ptr(iters_out, np.int32),
             _ptr(status_out, np.int32), _stream(stream)), allow)
 
