@@ -133,6 +133,50 @@ class Setup2D(Setup1D):
         return self.sur.guess(np.atleast_2d(xi)).reshape(-1, self.w.N, self.w.nx * self.w.nx)
 
 
+def _reference_worker_ac(args):
+    w, xi = args
+    st = SetupAC1D(w, build=False)
+    return st.reference(xi).reshape(-1)
+
+
+class SetupAC1D(Setup1D):
+    """Same stages as Setup1D on the Allen-Cahn-type problem (oracle.nonlinear):
+    Newton backward-Euler propagators and the simplified-Newton CGC with
+    w.cgc_newton steps."""
+
+    def operator(self, xi, field_ulps: float = 0.0, seed: int = 0):
+        from . import nonlinear
+        a = np.exp(kl_input.log_coefficient_1d(xi, self.basis))
+        if field_ulps:
+            sgn = np.random.default_rng(seed).choice([-1.0, 1.0], size=a.shape)
+            a = a * (1.0 + field_ulps * 2.0 ** -53 * sgn)
+        return nonlinear.CubicRD1D(a, self.w.reaction, self.w.forcing)
+
+    def reference(self, xi) -> np.ndarray:
+        from . import nonlinear
+        return nonlinear.fine_sequential(self.operator(xi), self.u0, self.w.N, self.w.J,
+                                         self.w.T)
+
+    def references(self, xis, processes=1) -> np.ndarray:
+        if processes <= 1 or len(xis) < 2:
+            return np.stack([self.reference(x) for x in xis])
+        import multiprocessing as mp
+        from concurrent.futures import ProcessPoolExecutor
+        with ProcessPoolExecutor(processes, mp_context=mp.get_context("spawn")) as ex:
+            out = list(ex.map(_reference_worker_ac, [(self.w, x) for x in xis]))
+        return np.stack(out).reshape(len(xis), self.w.N, self.w.nx)
+
+    def solve_sample(self, xi, U0=None, kmax=None, history=False, cgc="diag", field_ulps=0.0):
+        from . import nonlinear
+        w = self.w
+        if U0 is None:
+            U0 = self.guess(xi)[0]
+        op = self.operator(xi, field_ulps)
+        U, k = nonlinear.pcgc_solve(op, self.u0, U0, self.dT, w.J, w.alpha, w.tol,
+                                    kmax or w.kmax, w.cgc_newton)
+        return U, k, None
+
+
 def rel_l2(U, Uref) -> float:
     return float(np.linalg.norm(np.ravel(U) - np.ravel(Uref)) /
                  np.linalg.norm(np.ravel(Uref)))

@@ -15,6 +15,8 @@ Workload names describe what they are:
 * ``rd2d_255``      2D reaction-diffusion on a 255x255 grid, N=32, J=32,
                     M=20 separable KL, degree 2, 1024 samples.
 * ``heat1d_uneven`` 8192 1D instances with Nx, N, J drawn per instance.
+* ``ac1d_nx127``    1D Allen-Cahn-type problem (cubic reaction, random
+                    diffusion), Nx=127, N=32, J=16, 256 samples.
 * ``mlp_guess``     learned-guess workload on the heat1d_nx1023 problem.
 
 Values the paper leaves open are fixed here (training-set size n_t = 2P,
@@ -50,6 +52,8 @@ class Workload:
     u0_kind: int = 0        # 0: sin(pi x) (1D) / product of sines (2D); 1: zero
     kmax: int = 60
     extra: dict = field(default_factory=dict)
+    reaction_kind: int = 0  # 0: linear c u; 1: cubic c (u^3 - u) (Allen-Cahn type)
+    cgc_newton: int = 1     # simplified Newton steps per CGC (nonlinear problems)
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
@@ -75,6 +79,11 @@ WORKLOADS = {
         alpha=1e-4, tol=1e-8, S=8192, seed=4, train_seed=104,
         extra=dict(nx_choices=(127, 255, 511, 1023, 2047),
                    N_choices=(16, 32, 64), J_choices=(8, 16, 32, 64, 128))),
+    "ac1d_nx127": Workload(
+        name="ac1d_nx127", dim=1, nx=127, T=8.0, N=32, J=16, sigma=0.3,
+        corr_len=0.3, M=6, gpc_degree=2, n_train=56, eps_kl=1e-10,
+        alpha=1e-3, tol=1e-8, S=256, seed=7, train_seed=107,
+        reaction=5.0, forcing=0.0, u0_kind=0, reaction_kind=1, cgc_newton=3),
     "mlp_guess": Workload(
         name="mlp_guess", dim=1, nx=1023, T=1.0, N=64, J=64, sigma=0.5,
         corr_len=0.5, M=10, gpc_degree=3, n_train=572, eps_kl=1e-10,
