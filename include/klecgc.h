@@ -101,6 +101,10 @@ typedef struct {
     double reaction;      /* c >= 0 in div(a grad u) - c u + f0 */
     double forcing;       /* f0 (constant source) */
     int32_t u0_kind;      /* 0: u0 = sin(pi x) (product of sines in 2D); 1: u0 = 0 */
+    int32_t reaction_kind; /* 0: linear reaction -c u; 1: cubic -c (u^3 - u)
+                              (Allen-Cahn type; 1D, FP64; see klecgc_solve) */
+    int32_t cgc_newton;    /* simplified Newton steps per CGC for reaction_kind 1
+                              (eq. Newton2); 0 means 1 */
 } klecgc_problem;
 
 typedef struct {
@@ -162,6 +166,13 @@ klecgc_status klecgc_setup(const klecgc_problem* problem, const double* xi_train
  * else NOT_CONVERGED if any sample hit kmax; INVALID_ARG / UNSUPPORTED /
  * OUT_OF_MEMORY / CUDA for argument and runtime errors (nothing written).
  * Each sample's iterates are independent of the other samples.
+ * Cubic reaction (problem reaction_kind 1, f(u) = div(a grad u) - c (u^3 - u)
+ * + f0, 1D): F and G take Newton iterations for every backward-Euler step
+ * (tridiagonal Jacobian, to 1e-14 relative); the CGC solves eq. matrix_NT by
+ * problem.cgc_newton simplified Newton steps of eq. Newton2 with the
+ * time-averaged Jacobian of eq. Jac, each diagonalized like the linear CGC.
+ * FP64 only; guesses GPC, ZERO, USER, COARSE; the stage entry points, the
+ * batch, classical parareal and the learned guess take linear problems only.
  */
 klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S,
                            double dT, int32_t J, int32_t N, double alpha, double tol,

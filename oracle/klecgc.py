@@ -173,7 +173,7 @@ class SetupAC1D(Setup1D):
             U0 = self.guess(xi)[0]
         op = self.operator(xi, field_ulps)
         U, k = nonlinear.pcgc_solve(op, self.u0, U0, self.dT, w.J, w.alpha, w.tol,
-                                    kmax or w.kmax, w.cgc_newton)
+                                    kmax or w.kmax, w.cgc_newton, dense=(cgc == "dense"))
         return U, k, None
 
 

@@ -148,24 +148,27 @@ def cgc_newton_dense(op, u, b, dT, alpha):
     return np.linalg.solve(Jbar, rhs.reshape(-1)).reshape(N, n)
 
 
-def pcgc_iteration(op, u0, Uk, dT, J, alpha, L):
+def pcgc_iteration(op, u0, Uk, dT, J, alpha, L, dense=False):
     """One iteration of Algorithm 2 with the nonlinear CGC: F on all intervals,
-    the jump b, then L simplified Newton steps from u_0 = U^k."""
+    the jump b, then L simplified Newton steps from u_0 = U^k.  dense=True
+    solves each step's Jbar system densely (the same method along another
+    rounding path, used to measure the diagonalization's rounding floor)."""
     starts = np.empty_like(Uk)
     starts[0] = u0
     starts[1:] = Uk[:-1]
     Fend = F(op, starts, dT, J)
     b = jump_b(op, Fend, Uk, dT, alpha)
     u = Uk.copy()
+    step = cgc_newton_dense if dense else cgc_newton_step
     for _ in range(L):
-        u = cgc_newton_step(op, u, b, dT, alpha)
+        u = step(op, u, b, dT, alpha)
     return u
 
 
-def pcgc_solve(op, u0, U0, dT, J, alpha, tol, kmax, L):
+def pcgc_solve(op, u0, U0, dT, J, alpha, tol, kmax, L, dense=False):
     U = np.array(U0, dtype=np.float64)
     for k in range(kmax):
-        Un = pcgc_iteration(op, u0, U, dT, J, alpha, L)
+        Un = pcgc_iteration(op, u0, U, dT, J, alpha, L, dense)
         delta = np.max(np.abs(Un - U))
         U = Un
         if not np.isfinite(delta):

@@ -170,7 +170,8 @@ namespace klecgc {
 bool ctx_view(const klecgc_ctx* ctx, CtxView* out) {
     if (!ctx || !ctx->basis) return false;
     *out = CtxView{ctx->basis, ctx->u0, ctx->nx, ctx->M, ctx->device,
-                   ctx->h, ctx->prob.T, ctx->prob.reaction, ctx->prob.forcing, ctx->dim};
+                   ctx->h, ctx->prob.T, ctx->prob.reaction, ctx->prob.forcing, ctx->dim,
+                   ctx->prob.reaction_kind};
     return true;
 }
 }  // namespace klecgc
@@ -404,6 +405,42 @@ klecgc_status sequential_2d(klecgc_ctx* ctx, const double* xi_d, int64_t S, int 
     return krylov_read(ctx, S, ifail, its, st, &hf, capped);
 }
 
+bool nonlinear(const klecgc_ctx* ctx) { return ctx->prob.reaction_kind == 1; }
+
+// Nonlinear problem: coefficient field and the face weights a / h^2.
+klecgc_status nl_weights(klecgc_ctx* ctx, const double* xi_d, int64_t S, cudaStream_t st,
+                         double** a_out, double** wf_out) {
+    double* a = nullptr;
+    klecgc_status s = build_field(ctx, xi_d, S, st, &a);
+    if (s != KLECGC_OK) return s;
+    WS(double, wf, "wf_nl", S * (int64_t)ctx->nf);
+    ctx->launch(KLECGC_K_FIELD, st, [&] { launch_face_weights(a, S, ctx->nf, 1.0 / (ctx->h * ctx->h), wf, st); });
+    TRY(cudaGetLastError());
+    *a_out = a;
+    *wf_out = wf;
+    return KLECGC_OK;
+}
+
+// Sequential Newton fine solution (N intervals of J steps of T/(N J)) into U
+// (internal layout); *capped if a Newton step reached its iteration cap.
+klecgc_status nl_sequential(klecgc_ctx* ctx, const double* wf, int64_t S, int N, int J,
+                            double dt, double* U, cudaStream_t st, bool* capped) {
+    WS(double, scr, "nl_seq_scratch", 4 * S * (int64_t)ctx->nx);
+    WS(int, flag, "nl_seq_fail", S);
+    TRY(cudaMemsetAsync(flag, 0, S * sizeof(int), st));
+    ctx->launch(KLECGC_K_FINE, st, [&] {
+        launch_sequential_newton(S, N, ctx->nx, J, dt, ctx->prob.reaction, ctx->prob.forcing,
+                                 ctx->u0, wf, scr, U, flag, st);
+    });
+    TRY(cudaGetLastError());
+    std::vector<int> h(S);
+    TRY(cudaMemcpyAsync(h.data(), flag, S * sizeof(int), cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    *capped = false;
+    for (int v : h) *capped |= v != 0;
+    return KLECGC_OK;
+}
+
 // alpha^{j/N} and alpha^{-j/N} / (N/2) tables in precision T.
 template <typename T>
 klecgc_status scale_tables(klecgc_ctx* ctx, int N, double alpha, cudaStream_t st, T** sc,
@@ -485,7 +522,8 @@ klecgc_status gpc_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S,
 // ---------------------------------------------------------------- learned guess
 klecgc_status mlp_alloc(klecgc_ctx* ctx) {
     MlpState& q = ctx->mlp;
-    if (ctx->dim != 1) return fail(KLECGC_E_UNSUPPORTED, "the learned guess is 1D only");
+    if (ctx->dim != 1 || nonlinear(ctx))
+        return fail(KLECGC_E_UNSUPPORTED, "the learned guess is for the linear 1D problem only");
     if (q.theta) return KLECGC_OK;
     const int W = 256;
     q.sizes[0] = ctx->M;
@@ -706,7 +744,7 @@ void klecgc_free(klecgc_ctx* ctx) {
 }  // extern "C"
 namespace {
 constexpr char kMagic[8] = {'K', 'L', 'E', 'C', 'G', 'C', 'v', '1'};
-constexpr int32_t kVersion = 1;
+constexpr int32_t kVersion = 2;   // 2: problem with reaction_kind, cgc_newton
 
 struct FileHead {
     char magic[8];
@@ -940,8 +978,10 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     if (pr->nx < 1 || pr->M < 1 || pr->gpc_degree < 0 || pr->n_train < 2 || !(pr->T > 0) ||
         !(pr->sigma >= 0) || !(pr->corr_len > 0) || !(pr->eps_kl >= 0) || pr->J < 1 ||
         !(pr->reaction >= 0) || !std::isfinite(pr->forcing) || pr->u0_kind < 0 ||
-        pr->u0_kind > 1)
+        pr->u0_kind > 1 || pr->reaction_kind < 0 || pr->reaction_kind > 1 || pr->cgc_newton < 0)
         return fail(KLECGC_E_INVALID_ARG, "problem field out of range");
+    if (pr->reaction_kind == 1 && pr->dim != 1)
+        return fail(KLECGC_E_UNSUPPORTED, "the cubic reaction is 1D only");
     if (!pow2_in_range(pr->N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
     cudaStream_t st = (cudaStream_t)stream;
     klecgc_ctx* ctx = new klecgc_ctx();
@@ -1039,7 +1079,14 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
         double* p;
         ~Guard() { cudaFree(p); }
     } gY{Y};
-    if (ctx->dim == 1) {
+    if (nonlinear(ctx)) {
+        double *a = nullptr, *wf = nullptr;
+        SCHK(nl_weights(ctx, xi_d, nt, st, &a, &wf));
+        bool capped = false;
+        SCHK(nl_sequential(ctx, wf, nt, N, ctx->J, ctx->dT / ctx->J, Y, st, &capped));
+        if (capped)
+            return bail(fail(KLECGC_E_NOT_CONVERGED, "a snapshot's Newton step reached its cap"));
+    } else if (ctx->dim == 1) {
         Operators op;
         SCHK(build_operators(ctx, xi_d, nt, N, ctx->J, ctx->dT, 0.5, 1, 0, st, &op));
         WS(double, scr, "seq_scratch", (size_t)nt * nx);
@@ -1190,7 +1237,11 @@ klecgc_status klecgc_reference(klecgc_ctx* ctx, const double* xi, int64_t S, int
     const double dT = ctx->prob.T / N;
     WS(double, U, "Uref", S * (int64_t)ctx->ns * N);
     bool capped = false;
-    if (ctx->dim == 2) {
+    if (nonlinear(ctx)) {
+        double *a = nullptr, *wf = nullptr;
+        if ((s = nl_weights(ctx, xi_d, S, st, &a, &wf)) != KLECGC_OK) return s;
+        if ((s = nl_sequential(ctx, wf, S, N, J, dT / J, U, st, &capped)) != KLECGC_OK) return s;
+    } else if (ctx->dim == 2) {
         if ((s = sequential_2d(ctx, xi_d, S, N, J, U, st, &capped)) != KLECGC_OK) return s;
     } else {
         Operators op;
@@ -1202,7 +1253,7 @@ klecgc_status klecgc_reference(klecgc_ctx* ctx, const double* xi, int64_t S, int
     }
     if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) return s;
     TRY(cudaStreamSynchronize(st));
-    if (capped) return fail(KLECGC_E_NOT_CONVERGED, "a fine step reached the Krylov iteration cap");
+    if (capped) return fail(KLECGC_E_NOT_CONVERGED, "a fine step reached its iteration cap");
     return KLECGC_OK;
 }
 
@@ -1397,6 +1448,8 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
         precision < 0 || precision > 2)
         return fail(KLECGC_E_INVALID_ARG, "bad argument");
     if (!pow2_in_range(N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
+    if (nonlinear(ctx))
+        return fail(KLECGC_E_UNSUPPORTED, "stage entry points: linear problems only");
     klecgc_status s = check_dT(ctx, N, dT);
     if (s != KLECGC_OK || S == 0) return s;
     cudaStream_t st = (cudaStream_t)stream;
@@ -1472,6 +1525,8 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
         return fail(KLECGC_E_INVALID_ARG, "bad argument");
     if (ctx->dim == 1 && precision == KLECGC_MIXED)
         return fail(KLECGC_E_INVALID_ARG, "1D: precision FP64 or MIXED_DEFECT");
+    if (nonlinear(ctx))
+        return fail(KLECGC_E_UNSUPPORTED, "stage entry points: linear problems only");
     if (!pow2_in_range(N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
     klecgc_status s = check_dT(ctx, N, dT);
     if (s != KLECGC_OK || S == 0) return s;
@@ -1842,6 +1897,102 @@ struct PinnedInts {
     }
 };
 
+// Algorithm 2 with the nonlinear CGC (reaction_kind 1, FP64): per iteration,
+// F by Newton steps and the jump b (k_fine_newton), then cgc_newton
+// simplified Newton steps of eq. Newton2 from u_0 = U^k, each the three
+// diagonalized steps with the averaged Jacobian (k_nl_prep, shifted factors
+// with the diagonal extra, forward transform, solves, inverse transform); the
+// last one writes U^{k+1} and the increment norm.
+klecgc_status solve_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S, double dT, int J,
+                              int N, double alpha, double tol, int kmax, int guess,
+                              const double* U_guess, double* U_out, std::vector<int32_t>& hs,
+                              std::vector<int32_t>& hi, bool* capped, cudaStream_t st) {
+    klecgc_status s;
+    const int nx = ctx->nx, K = N / 2 + 1;
+    const int64_t NS = S * (int64_t)nx * N;
+    const int L = ctx->prob.cgc_newton > 0 ? ctx->prob.cgc_newton : 1;
+    const double c = ctx->prob.reaction, f0 = ctx->prob.forcing;
+    double *a = nullptr, *wf = nullptr;
+    if ((s = nl_weights(ctx, xi_d, S, st, &a, &wf)) != KLECGC_OK) return s;
+    WS(double, wT, "wT", S * (int64_t)ctx->nf);
+    ctx->launch(KLECGC_K_FIELD, st, [&] { launch_face_weights(a, S, ctx->nf, dT / (ctx->h * ctx->h), wT, st); });
+    WS(double, U, "U", NS);
+    if (guess == KLECGC_GUESS_GPC) {
+        if ((s = gpc_guess_internal(ctx, xi_d, S, true, U, st)) != KLECGC_OK) return s;
+    } else if (guess == KLECGC_GUESS_ZERO) {
+        TRY(cudaMemsetAsync(U, 0, NS * sizeof(double), st));
+    } else if (guess == KLECGC_GUESS_COARSE) {
+        bool cap = false;
+        if ((s = nl_sequential(ctx, wf, S, N, 1, dT, U, st, &cap)) != KLECGC_OK) return s;
+    } else if ((s = import_batch(ctx, U_guess, S, N, U, st)) != KLECGC_OK) {
+        return s;
+    }
+    std::vector<double2> lam;
+    double2* lam_d = nullptr;
+    if ((s = upload_lambda(ctx, N, alpha, st, lam, &lam_d)) != KLECGC_OK) return s;
+    double *sc, *isc;
+    if ((s = scale_tables<double>(ctx, N, alpha, st, &sc, &isc)) != KLECGC_OK) return s;
+    WS(double, b, "nl_b", NS);
+    WS(double, rhs, "r", NS);
+    WS(double, ul, "nl_ul", NS);
+    WS(double, e, "nl_e", S * (int64_t)nx);
+    WS(double, scr, "nl_scratch", 4 * NS);
+    WS(Cplx<double>, p64, "p64", S * (int64_t)nx * K);
+    WS(Cplx<double>, di, "cgc_dinv64", S * (int64_t)nx * K);
+    WS(Cplx<double>, lu, "cgc_lu64", S * (int64_t)nx * K);
+    WS(int, active, "active", S);
+    WS(int32_t, iters, "iters", S);
+    WS(int32_t, status, "status", S);
+    WS(unsigned long long, delta, "delta", S);
+    WS(int, n_active, "n_active", 1);
+    WS(int, ifail, "nl_fail", S);
+    TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
+    TRY(cudaMemsetAsync(iters, 0xff, S * sizeof(int32_t), st));
+    TRY(cudaMemsetAsync(status, 0, S * sizeof(int32_t), st));
+    TRY(cudaMemsetAsync(delta, 0, S * sizeof(unsigned long long), st));
+    TRY(cudaMemsetAsync(ifail, 0, S * sizeof(int), st));
+    PinnedInts pin;
+    TRY(cudaMallocHost(&pin.p, sizeof(int)));
+    for (int k = 0; k < kmax; ++k) {
+        ctx->launch(KLECGC_K_FINE, st, [&] {
+            launch_fine_newton(S, N, nx, J, dT, alpha, c, f0, U, ctx->u0, wf, b, scr, active,
+                               ifail, st);
+        });
+        for (int l = 0; l < L; ++l) {
+            const double* cur = l == 0 ? U : ul;
+            ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_nl_prep(S, N, nx, dT, c, f0, cur, b, wf, rhs, e, active, st); });
+            ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_cgc_factors<double>(a, S, nx, ctx->h, dT, 0.0, lam_d, K, di, lu, st, e); });
+            ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<double, double>(S, N, nx, rhs, sc, p64, active, st); });
+            ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_cgc_solve<double, double>(S, K, nx, di, lu, wT, p64, active, st); });
+            if (l + 1 == L)
+                ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc, U, 0, delta, nullptr, active, st); });
+            else
+                ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc, ul, 2, nullptr, nullptr, active, st); });
+        }
+        TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
+        ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
+        TRY(cudaGetLastError());
+        TRY(cudaMemcpyAsync(pin.p, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (*pin.p == 0) break;
+    }
+    if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) return s;
+    hs.assign(S, 0);
+    hi.assign(S, 0);
+    std::vector<int> hf(S);
+    TRY(cudaMemcpyAsync(hs.data(), status, S * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(hi.data(), iters, S * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(hf.data(), ifail, S * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    *capped = false;
+    for (int64_t i = 0; i < S; ++i)
+        if (hf[i] && hs[i] == KLECGC_OK) {
+            hs[i] = KLECGC_E_NOT_CONVERGED;
+            *capped = true;
+        }
+    return KLECGC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1863,6 +2014,8 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
         return fail(KLECGC_E_INVALID_ARG, "no network (klecgc_mlp_set / klecgc_mlp_train)");
     if (ctx->dim == 2 && precision == KLECGC_MIXED_DEFECT)
         return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 or MIXED only");
+    if (nonlinear(ctx) && (precision != KLECGC_FP64 || guess == KLECGC_GUESS_MLP))
+        return fail(KLECGC_E_UNSUPPORTED, "cubic reaction: FP64, guesses GPC/ZERO/USER/COARSE");
     klecgc_status s = check_dT(ctx, N, dT);
     if (s != KLECGC_OK) return s;
     if (S == 0) return KLECGC_OK;
@@ -1879,6 +2032,17 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
             TRY(cudaStreamSynchronize(st));
         }
         return fail(KLECGC_E_NONFINITE, "xi has a non-finite entry");
+    }
+    if (nonlinear(ctx)) {
+        std::vector<int32_t> hs, hi;
+        bool capped = false;
+        if ((s = solve_nonlinear(ctx, xi_d, S, dT, J, N, alpha, tol, kmax, guess, U_guess, U_out,
+                                 hs, hi, &capped, st)) != KLECGC_OK)
+            return s;
+        ctx->prof_collect();
+        if (iters_out) TRY(cudaMemcpy(iters_out, hi.data(), S * 4, cudaMemcpyDefault));
+        if (status_out) TRY(cudaMemcpy(status_out, hs.data(), S * 4, cudaMemcpyDefault));
+        return status_summary(hs, capped);
     }
     PinnedInts pin;
     TRY(cudaMallocHost(&pin.p, sizeof(int)));
@@ -1920,7 +2084,8 @@ klecgc_status klecgc_solve_parareal(klecgc_ctx* ctx, const double* xi, int64_t S
     if (J < 1 || N < 1 || N > 4096 || !(tol > 0) || kmax < 1 || guess < 0 || guess > 3 ||
         (guess == KLECGC_GUESS_USER && !U_guess && S > 0))
         return fail(KLECGC_E_INVALID_ARG, "argument out of range");
-    if (ctx->dim != 1) return fail(KLECGC_E_UNSUPPORTED, "classical parareal: 1D only");
+    if (ctx->dim != 1 || nonlinear(ctx))
+        return fail(KLECGC_E_UNSUPPORTED, "classical parareal: linear 1D problems only");
     if (guess == KLECGC_GUESS_GPC && N != ctx->N)
         return fail(KLECGC_E_INVALID_ARG, "the gPC guess needs the setup's N");
     klecgc_status s = check_dT(ctx, N, dT);
@@ -2006,6 +2171,7 @@ klecgc_status klecgc_solve_batch(klecgc_ctx* const* ctxs, int32_t n_ctx,
         if (x->M != M) return fail(KLECGC_E_INVALID_ARG, "every context must have the same M");
         if (x->dim == 2 && precision == KLECGC_MIXED_DEFECT)
             return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 or MIXED only");
+        if (nonlinear(x)) return fail(KLECGC_E_UNSUPPORTED, "the batch takes linear problems");
     }
     for (int64_t i = 0; i < n; ++i)
         if (inst[i].ctx < 0 || inst[i].ctx >= n_ctx || inst[i].J < 1)

@@ -61,7 +61,8 @@ void launch_fine_factors(const double* a, int64_t S, int nx, double h, double dt
                          FineCoef64* f64, FineCoef32* f32, cudaStream_t st);
 template <typename T>
 void launch_cgc_factors(const double* a, int64_t S, int nx, double h, double dT, double react,
-                        const double2* lam, int K, Cplx<T>* dinv, Cplx<T>* lu, cudaStream_t st);
+                        const double2* lam, int K, Cplx<T>* dinv, Cplx<T>* lu, cudaStream_t st,
+                        const double* ext = nullptr);
 void launch_cgc_factors32(const float* wT32, int64_t S, int nx, double dTreact,
                           const float2* lam, int K, Cplx<float>* dinv, Cplx<float>* lu,
                           cudaStream_t st);
@@ -165,6 +166,21 @@ void launch_pad_transpose(const float* W, int P, int64_t NC, int Kp, float* Wt, 
 void launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi, const float* Wt,
                      const double* ubar, double* U, int* err, cudaStream_t st);
 
+// ---- k_nonlinear.cu ---- (cubic reaction, simplified-Newton CGC; wf = a / h^2)
+// F by Newton backward-Euler steps and the jump b = F - G(prev) per (s, n);
+// scratch: 4 S nx N doubles.
+void launch_fine_newton(int64_t S, int N, int nx, int J, double dT, double alpha, double c,
+                        double f0, const double* U, const double* u0, const double* wf, double* b,
+                        double* scratch, const int* active, int* ifail, cudaStream_t st);
+// N J sequential Newton steps of dt per sample (one thread each); scratch 4 nx S.
+void launch_sequential_newton(int64_t S, int N, int nx, int J, double dt, double c, double f0,
+                              const double* u0, const double* wf, double* scratch, double* U,
+                              int* ifail, cudaStream_t st);
+// e = c (3 mean_n (u - b)^2 - 1) per row and the right-hand side of eq. Newton2.
+void launch_nl_prep(int64_t S, int N, int nx, double dT, double c, double f0, const double* u,
+                    const double* b, const double* wf, double* rhs, double* e, const int* active,
+                    cudaStream_t st);
+
 // ---- k_cgc.cu ----
 // Step (a): p[s][i][k] = sum_j alpha^{j/N} r[s][i][j] exp(-2 pi i j k / N), k <= N/2.
 template <typename T, typename TIN>
@@ -243,6 +259,7 @@ struct CtxView {
     int nx, M, device;
     double h, T, reaction, forcing;
     int dim;
+    int reaction_kind;
 };
 }  // namespace klecgc
 struct klecgc_ctx;

@@ -82,10 +82,13 @@ void launch_fine_factors(const double* a, int64_t S, int nx, double h, double dt
 // lambda_k + dT(w_i + w_{i+1} + c) and real off-diagonal -dT w_i.  Stored
 // per (s, i, k): dinv_i = 1/piv_i and lu_i = M_{i,i+1} dinv_i, layout
 // [S][nx][K] so that the K systems of one sample are contiguous per row.
+// ext (optional, [S][nx]): a per-row addition dT ext_i to the diagonal (the
+// averaged Jacobian of the nonlinear CGC).
 template <typename T>
 __global__ void k_cgc_factors(const double* __restrict__ a, int64_t S, int nx, double wscale,
                               double dTreact, const double2* __restrict__ lam, int K,
-                              Cplx<T>* __restrict__ dinv, Cplx<T>* __restrict__ lu) {
+                              Cplx<T>* __restrict__ dinv, Cplx<T>* __restrict__ lu,
+                              const double* __restrict__ ext, double dT) {
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= S * K) return;
     int64_t s = t / K;
@@ -97,6 +100,7 @@ __global__ void k_cgc_factors(const double* __restrict__ a, int64_t S, int nx, d
     for (int i = 0; i < nx; ++i) {
         double wr = wscale * as[i + 1];
         double dr = lk.x + wl + wr + dTreact, di = lk.y;
+        if (ext) dr += dT * ext[s * nx + i];
         if (i > 0) {
             // piv_i = delta_i - wl^2 / piv_{i-1}
             double den = pr * pr + pi * pi;
@@ -118,18 +122,19 @@ __global__ void k_cgc_factors(const double* __restrict__ a, int64_t S, int nx, d
 
 template <typename T>
 void launch_cgc_factors(const double* a, int64_t S, int nx, double h, double dT, double react,
-                        const double2* lam, int K, Cplx<T>* dinv, Cplx<T>* lu, cudaStream_t st) {
+                        const double2* lam, int K, Cplx<T>* dinv, Cplx<T>* lu, cudaStream_t st,
+                        const double* ext) {
     int64_t n = S * K;
     if (n == 0) return;
-    k_cgc_factors<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(a, S, nx, dT / (h * h),
-                                                                   dT * react, lam, K, dinv, lu);
+    k_cgc_factors<T><<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+        a, S, nx, dT / (h * h), dT * react, lam, K, dinv, lu, ext, dT);
 }
 template void launch_cgc_factors<double>(const double*, int64_t, int, double, double, double,
                                          const double2*, int, Cplx<double>*, Cplx<double>*,
-                                         cudaStream_t);
+                                         cudaStream_t, const double*);
 template void launch_cgc_factors<float>(const double*, int64_t, int, double, double, double,
                                         const double2*, int, Cplx<float>*, Cplx<float>*,
-                                        cudaStream_t);
+                                        cudaStream_t, const double*);
 
 // FP32 variant for the defect path, whose CGC is an FP32 approximate inverse.
 // With lambda' = lambda_k + dT c and w_i = dT a_{i-1/2}/h^2, the pivots are

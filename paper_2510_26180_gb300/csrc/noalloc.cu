@@ -99,7 +99,9 @@ extern "C" klecgc_status klecgc_reference_noalloc(klecgc_ctx* ctx, const double*
     CtxView cv;
     if (!ctx || !ctx_view(ctx, &cv) || S < 0 || N < 1 || J < 1)
         return fail_na(KLECGC_E_INVALID_ARG, "bad argument");
-    if (cv.dim != 1) return fail_na(KLECGC_E_UNSUPPORTED, "the allocation-free entry point is 1D only");
+    if (cv.dim != 1 || cv.reaction_kind != 0)
+        return fail_na(KLECGC_E_UNSUPPORTED,
+                       "the allocation-free entry point takes the linear 1D problem only");
     if (S == 0) return KLECGC_OK;
     if (!on_device(xi) || !on_device(U_out))
         return fail_na(KLECGC_E_INVALID_ARG, "xi and U_out must be device arrays");

@@ -43,13 +43,16 @@ class Problem(ctypes.Structure):
                 ("M", ctypes.c_int32), ("gpc_degree", ctypes.c_int32),
                 ("n_train", ctypes.c_int32), ("eps_kl", ctypes.c_double),
                 ("N", ctypes.c_int32), ("J", ctypes.c_int32), ("reaction", ctypes.c_double),
-                ("forcing", ctypes.c_double), ("u0_kind", ctypes.c_int32)]
+                ("forcing", ctypes.c_double), ("u0_kind", ctypes.c_int32),
+                ("reaction_kind", ctypes.c_int32), ("cgc_newton", ctypes.c_int32)]
 
     @classmethod
     def from_workload(cls, w) -> "Problem":
         return cls(dim=w.dim, nx=w.nx, T=w.T, sigma=w.sigma, corr_len=w.corr_len, M=w.M,
                    gpc_degree=w.gpc_degree, n_train=w.n_train, eps_kl=w.eps_kl, N=w.N, J=w.J,
-                   reaction=w.reaction, forcing=w.forcing, u0_kind=w.u0_kind)
+                   reaction=w.reaction, forcing=w.forcing, u0_kind=w.u0_kind,
+                   reaction_kind=getattr(w, "reaction_kind", 0),
+                   cgc_newton=getattr(w, "cgc_newton", 1))
 
 
 class Instance(ctypes.Structure):

@@ -33,3 +33,10 @@ def oracle_setup2d(name, **over):
     from oracle.klecgc import Setup2D
     w = workload(name, **over)
     return Setup2D(w)
+
+
+@functools.lru_cache(maxsize=None)
+def oracle_setup_ac(name, **over):
+    from oracle.klecgc import SetupAC1D
+    w = workload(name, **over)
+    return SetupAC1D(w)

@@ -1,0 +1,108 @@
+"""Nonlinear problem on the GPU (cubic reaction, simplified-Newton CGC)
+against the oracle: the Newton reference, whole solves with iteration
+counts, the coarse start, the reduction to the linear problem at c = 0, and
+the modes it rejects.  Bars as for the linear FP64 path: 1e-12 relative L2,
+or 4x the oracle's own floor (dense instead of diagonalized Jbar solves, and
+the field perturbed by 4 ulps) where that is larger."""
+import numpy as np
+import pytest
+
+from synth import draw_xi
+from tests.gpu_util import gpu_solver, oracle_setup_ac, rel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SMALL = dict(N=16, J=8)
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def T(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dev())
+
+
+def test_nonlinear_reference_matches_oracle():
+    from oracle import nonlinear as nl
+    solver, w = gpu_solver("ac1d_nx127", **SMALL)
+    st = oracle_setup_ac("ac1d_nx127", **SMALL)
+    S = 4
+    xi = draw_xi(S, w.M, 71)
+    U = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
+    solver.reference(T(xi), S, w.N, w.J, U)
+    for s in range(S):
+        ref = st.reference(xi[s])
+        refp = nl.fine_sequential(st.operator(xi[s], 4.0), st.u0, w.N, w.J, w.T)
+        d = rel(U[s].cpu().numpy(), ref)
+        assert d < max(1e-12, 4 * rel(refp, ref)), d
+
+
+@pytest.mark.parametrize("guess", ["gpc", "coarse"])
+def test_nonlinear_solve_matches_oracle(guess):
+    import paper_2510_26180_gb300 as pkg
+    from oracle import nonlinear as nl
+    solver, w = gpu_solver("ac1d_nx127", **SMALL)
+    st = oracle_setup_ac("ac1d_nx127", **SMALL)
+    S = 4
+    xi = draw_xi(S, w.M, 72)
+    U = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
+    it = torch.empty(S, dtype=torch.int32, device=dev())
+    g = pkg.GUESS_GPC if guess == "gpc" else pkg.GUESS_COARSE
+    code = solver.solve(T(xi), S, w.T / w.N, w.J, w.N, w.alpha, w.tol, w.kmax, pkg.FP64, g, U, it)
+    assert code == 0
+    U, it = U.cpu().numpy(), it.cpu().numpy()
+    for s in range(S):
+        op = st.operator(xi[s])
+        U0 = st.guess(xi[s])[0] if guess == "gpc" else \
+            np.stack(list(_coarse(nl, op, st.u0, w.N, w.T / w.N)))
+        Uo, ko, _ = st.solve_sample(xi[s], U0=U0)
+        Ud, _, _ = st.solve_sample(xi[s], U0=U0, cgc="dense")
+        Up, _, _ = st.solve_sample(xi[s], U0=U0, field_ulps=4.0)
+        floor = rel(Ud, Uo) + rel(Up, Uo)
+        assert it[s] == ko, (s, it[s], ko)
+        assert rel(U[s], Uo) < max(1e-12, 4 * floor), (s, rel(U[s], Uo), floor)
+        assert rel(U[s], st.reference(xi[s])) < 1e-6
+
+
+def _coarse(nl, op, u0, N, dT):
+    v = np.asarray(u0, dtype=np.float64)
+    for _ in range(N):
+        v = nl.G(op, v, dT)
+        yield v
+
+
+def test_zero_reaction_matches_the_linear_solver():
+    import paper_2510_26180_gb300 as pkg
+    lin, w = gpu_solver("heat1d_nx63")
+    nlin, _ = gpu_solver("heat1d_nx63", reaction_kind=1, cgc_newton=2)
+    S = 6
+    xi = T(draw_xi(S, w.M, 73))
+    U1 = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
+    U2 = torch.empty_like(U1)
+    i1 = torch.empty(S, dtype=torch.int32, device=dev())
+    i2 = torch.empty_like(i1)
+    assert lin.solve(xi, S, w.T / w.N, w.J, w.N, w.alpha, w.tol, w.kmax, 0, pkg.GUESS_GPC, U1, i1) == 0
+    assert nlin.solve(xi, S, w.T / w.N, w.J, w.N, w.alpha, w.tol, w.kmax, 0, pkg.GUESS_GPC, U2, i2) == 0
+    assert torch.equal(i1, i2)
+    assert rel(U2.cpu().numpy(), U1.cpu().numpy()) < 1e-10
+
+
+def test_nonlinear_rejects_unsupported_modes():
+    import paper_2510_26180_gb300 as pkg
+    solver, w = gpu_solver("ac1d_nx127", **SMALL)
+    S = 2
+    xi = T(draw_xi(S, w.M, 74))
+    U = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
+    for call in (
+        lambda: solver.solve(xi, S, w.T / w.N, w.J, w.N, w.alpha, w.tol, 5, pkg.MIXED_DEFECT,
+                             pkg.GUESS_GPC, U),
+        lambda: solver.fine_sweep(xi, S, w.N, U, w.T / w.N, w.J, w.alpha, 0, U),
+        lambda: solver.solve_parareal(xi, S, w.T / w.N, w.J, w.N, w.tol, 5, pkg.GUESS_ZERO, U),
+        lambda: solver.reference_noalloc(xi, S, w.N, w.J, U),
+    ):
+        with pytest.raises(pkg.KlecgcError) as e:
+            call()
+        assert e.value.status == pkg.E_UNSUPPORTED
