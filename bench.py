@@ -53,7 +53,12 @@ def peaks():
 
 
 def workload_desc(w, S, precision, overrides=None):
-    if w.dim == 2:
+    if w.reaction_kind == 1:
+        name = (f"{w.name}: 1D u_t=(a u_x)_x-{w.reaction:g}(u^3-u)+{w.forcing:g}, a=exp(KL, "
+                f"M={w.M}), Nx={w.nx}, N={w.N}, J={w.J}, Newton backward Euler, "
+                f"{w.cgc_newton} simplified Newton steps per CGC, gPC p={w.gpc_degree}, "
+                f"alpha={w.alpha}, tol={w.tol}")
+    elif w.dim == 2:
         name = (f"{w.name}: 2D u_t=div(a grad u)-{w.reaction:g}u+{w.forcing:g} on (0,1)^2, "
                 f"a=exp(separable KL, M={w.M}), {w.nx}^2 interior points, N={w.N}, J={w.J}, "
                 f"gPC p={w.gpc_degree}, alpha={w.alpha}, tol={w.tol}, Krylov rtol 1e-10")
@@ -139,13 +144,14 @@ def oracle_pool(w, cores):
     Worker processes run single-threaded BLAS so that `cores` processes use
     `cores` hardware threads."""
     import multiprocessing as mp
-    from oracle.klecgc import Setup1D, Setup2D
+    from oracle.klecgc import Setup1D, Setup2D, SetupAC1D
     saved = {k: os.environ.get(k) for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS",
                                             "MKL_NUM_THREADS")}
     for k in saved:
         os.environ[k] = "1"
     try:
-        setup = (Setup2D if w.dim == 2 else Setup1D)(w, processes=cores)
+        kind = Setup2D if w.dim == 2 else (SetupAC1D if w.reaction_kind == 1 else Setup1D)
+        setup = kind(w, processes=cores)
         pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_init, initargs=(setup,))
     finally:
         for k, v in saved.items():
@@ -237,6 +243,17 @@ def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
         return None
     if w.dim == 2:
         return roofline_2d(cls, ms, launches, units, prec)
+    if w.reaction_kind == 1:
+        if cls != "fine":
+            return None
+        # Newton iteration of a backward-Euler step: ~33 FP64 flop per row
+        # (residual 13, Thomas forward 15 incl. two divisions, back 5)
+        flops = 33.0 * units["kry_fine"] * w.nx
+        ach = flops / (ms / 1e3) / 1e12
+        return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK,
+                "unit": "TFLOP/s", "frac": ach / FP64_ALU_PEAK, "traffic": None,
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s",
+                "work": f"{flops / max(launches, 1):.3e} FP64 flop per launch"}
     row_steps = units["row_steps"]
     pts = units["points"]
     if cls == "fine":
@@ -335,7 +352,7 @@ def run_gpu(args, w):
     clocks = sampler.stop()
     prof = solver.profile_read()
     solver.profile_enable(False)
-    kry = solver.krylov_stats() if w.dim == 2 else (0, 0)   # of the last timed solve
+    kry = solver.krylov_stats() if (w.dim == 2 or w.reaction_kind == 1) else (0, 0)
     ms = e0.elapsed_time(e1) / args.steps
 
     # accuracy of the last timed step against U* (FP64 reference kernel)
@@ -689,6 +706,9 @@ def main():
         over[k] = float(v) if any(c in v for c in ".e") else int(v)
     w = workload(args.workload, **over)
     args.overrides = over
+    if w.reaction_kind == 1:
+        args.precision = "fp64"      # the cubic-reaction path is FP64
+        args.skip_fp64 = True
     if w.dim == 2:
         # 2D: FP64 Krylov solves, or MIXED (FP64 refinement around FP32 PCG for
         # F); the defect variant is 1D only, so it maps to MIXED

@@ -363,7 +363,9 @@ klecgc_status klecgc_set_krylov(klecgc_ctx* ctx, double rtol_fine, double rtol_c
 
 /* Krylov iterations of the last 2D call (klecgc_solve, klecgc_fine_sweep,
  * klecgc_cgc_apply, klecgc_reference), summed over all linear systems, for
- * F and for the CGC solves.  Either pointer may be NULL. */
+ * F and for the CGC solves; for the cubic reaction (reaction_kind 1) the
+ * Newton iterations of F and G of the last klecgc_solve (its_cgc = 0).
+ * Either pointer may be NULL. */
 klecgc_status klecgc_krylov_stats(const klecgc_ctx* ctx, int64_t* its_fine, int64_t* its_cgc);
 
 /*

@@ -1946,6 +1946,8 @@ klecgc_status solve_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S, do
     WS(unsigned long long, delta, "delta", S);
     WS(int, n_active, "n_active", 1);
     WS(int, ifail, "nl_fail", S);
+    WS(unsigned long long, nits, "kry_its", 2);
+    TRY(cudaMemsetAsync(nits, 0, 2 * sizeof(unsigned long long), st));
     TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
     TRY(cudaMemsetAsync(iters, 0xff, S * sizeof(int32_t), st));
     TRY(cudaMemsetAsync(status, 0, S * sizeof(int32_t), st));
@@ -1956,7 +1958,7 @@ klecgc_status solve_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S, do
     for (int k = 0; k < kmax; ++k) {
         ctx->launch(KLECGC_K_FINE, st, [&] {
             launch_fine_newton(S, N, nx, J, dT, alpha, c, f0, U, ctx->u0, wf, b, scr, active,
-                               ifail, st);
+                               ifail, nits, st);
         });
         for (int l = 0; l < L; ++l) {
             const double* cur = l == 0 ? U : ul;
@@ -1980,10 +1982,14 @@ klecgc_status solve_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S, do
     hs.assign(S, 0);
     hi.assign(S, 0);
     std::vector<int> hf(S);
+    unsigned long long hn[2] = {0, 0};
     TRY(cudaMemcpyAsync(hs.data(), status, S * 4, cudaMemcpyDeviceToHost, st));
     TRY(cudaMemcpyAsync(hi.data(), iters, S * 4, cudaMemcpyDeviceToHost, st));
     TRY(cudaMemcpyAsync(hf.data(), ifail, S * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(hn, nits, sizeof(hn), cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
+    ctx->kry_it_fine = hn[0];   // Newton iterations of F and G
+    ctx->kry_it_cgc = 0;
     *capped = false;
     for (int64_t i = 0; i < S; ++i)
         if (hf[i] && hs[i] == KLECGC_OK) {

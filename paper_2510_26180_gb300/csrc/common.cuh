@@ -171,7 +171,8 @@ void launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi, const floa
 // scratch: 4 S nx N doubles.
 void launch_fine_newton(int64_t S, int N, int nx, int J, double dT, double alpha, double c,
                         double f0, const double* U, const double* u0, const double* wf, double* b,
-                        double* scratch, const int* active, int* ifail, cudaStream_t st);
+                        double* scratch, const int* active, int* ifail,
+                        unsigned long long* itcount, cudaStream_t st);
 // N J sequential Newton steps of dt per sample (one thread each); scratch 4 nx S.
 void launch_sequential_newton(int64_t S, int N, int nx, int J, double dt, double c, double f0,
                               const double* u0, const double* wf, double* scratch, double* U,

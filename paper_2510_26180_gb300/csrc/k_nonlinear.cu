@@ -32,11 +32,12 @@ constexpr int kNewtonMax = 50;
 // One Newton backward-Euler step on the column w (stride st): v is the start
 // value (overwritten by nothing), w the iterate (in/out), cp / dp Thomas
 // scratch.  wf: face weights a/h^2 (nx + 1), dt, c, f0.  Returns false if the
-// iteration cap was reached.
+// iteration cap was reached; adds the Newton iterations taken to *its.
 __device__ bool newton_be(int nx, const double* __restrict__ wf, double dt, double c,
                           double f0, const double* v, double* w, double* cp, double* dp,
-                          int64_t st) {
+                          int64_t st, unsigned long long* its) {
     for (int it = 0; it < kNewtonMax; ++it) {
+        ++*its;
         // residual R = w + dt A w + dt c (w^3 - w) - v - dt f0 and the Thomas
         // forward elimination of (I + dt A + dt c diag(3 w^2 - 1)) d = R
         double wl = 0.0, wi = w[0], prevc = 0.0, prevd = 0.0;
@@ -83,7 +84,7 @@ __global__ void __launch_bounds__(128) k_fine_newton(
     const double* __restrict__ U, const double* __restrict__ u0, const double* __restrict__ wf,
     double* __restrict__ bout, double* __restrict__ vs, double* __restrict__ cps,
     double* __restrict__ dps, double* __restrict__ gs, const int* __restrict__ active,
-    int* __restrict__ ifail) {
+    int* __restrict__ ifail, unsigned long long* __restrict__ itcount) {
     const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t s = t / N;
     const int n = (int)(t - s * N);
@@ -96,11 +97,12 @@ __global__ void __launch_bounds__(128) k_fine_newton(
     double* cp = cps + base;
     double* dp = dps + base;
     bool ok = true;
+    unsigned long long its = 0;
     for (int i = 0; i < nx; ++i) w[(int64_t)i * N] = n == 0 ? u0[i] : Us[(int64_t)i * N + n - 1];
     const double dt = dT / J;
     for (int j = 0; j < J && ok; ++j) {
         for (int i = 0; i < nx; ++i) v[(int64_t)i * N] = w[(int64_t)i * N];
-        ok = newton_be(nx, wfs, dt, c, f0, v, w, cp, dp, N);
+        ok = newton_be(nx, wfs, dt, c, f0, v, w, cp, dp, N, &its);
     }
     // G(prev): one step of dT from prev (start v, iterate g); F stays in w
     double* g = gs + base;
@@ -109,20 +111,22 @@ __global__ void __launch_bounds__(128) k_fine_newton(
         v[(int64_t)i * N] = pv;
         g[(int64_t)i * N] = pv;
     }
-    if (ok) ok = newton_be(nx, wfs, dT, c, f0, v, g, cp, dp, N);
+    if (ok) ok = newton_be(nx, wfs, dT, c, f0, v, g, cp, dp, N, &its);
     for (int i = 0; i < nx; ++i) w[(int64_t)i * N] -= g[(int64_t)i * N];
     if (!ok) ifail[s] = 1;
+    if (itcount) atomicAdd(itcount, its);
 }
 
 void launch_fine_newton(int64_t S, int N, int nx, int J, double dT, double alpha, double c,
                         double f0, const double* U, const double* u0, const double* wf, double* b,
-                        double* scratch, const int* active, int* ifail, cudaStream_t st) {
+                        double* scratch, const int* active, int* ifail,
+                        unsigned long long* itcount, cudaStream_t st) {
     const int64_t n = S * N;
     if (n == 0) return;
     const int64_t NS = n * nx;
     k_fine_newton<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
         S, N, nx, J, dT, alpha, c, f0, U, u0, wf, b, scratch, scratch + NS, scratch + 2 * NS,
-        scratch + 3 * NS, active, ifail);
+        scratch + 3 * NS, active, ifail, itcount);
 }
 
 // Sequential fine solution with Newton steps (reference, snapshots, the
@@ -140,12 +144,13 @@ __global__ void __launch_bounds__(64) k_sequential_newton(
     double* dp = cp + plane;
     const double* wfs = wf + s * (nx + 1);
     bool ok = true;
+    unsigned long long its = 0;
     for (int i = 0; i < nx; ++i) w[(int64_t)i * S] = u0[i];
     double* Us = U + s * (int64_t)nx * N;
     for (int n = 0; n < N; ++n) {
         for (int j = 0; j < J && ok; ++j) {
             for (int i = 0; i < nx; ++i) v[(int64_t)i * S] = w[(int64_t)i * S];
-            ok = newton_be(nx, wfs, dt, c, f0, v, w, cp, dp, S);
+            ok = newton_be(nx, wfs, dt, c, f0, v, w, cp, dp, S, &its);
         }
         for (int i = 0; i < nx; ++i) Us[(int64_t)i * N + n] = w[(int64_t)i * S];
     }
