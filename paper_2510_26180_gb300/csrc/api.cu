@@ -80,7 +80,8 @@ struct klecgc_ctx {
     double* ubar = nullptr;    // [ns*N]  internal order c = i*N + n
     double* W = nullptr;       // [P][ns*N]
     float* W32 = nullptr;      // FP32 copy of W
-    float* W32t = nullptr;     // [ns*N][Kp] FP32 W^T, zero-padded (tensor-core guess)
+    float* W32t = nullptr;     // [ns*N][Kp] TF32 head of W^T, zero-padded (tensor-core guess)
+    float* W32t_lo = nullptr;  // [ns*N][Kp] its tail W^T - head
     int Kp = 0;
     int* tc_err = nullptr;     // set by the tensor-core guess when a wait timed out
     std::map<std::string, DevBuf> ws;  // grow-only scratch
@@ -512,8 +513,15 @@ klecgc_status gpc_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S,
     } else {
         // tcgen05 tensor cores, 3xTF32 split (FP32-level accuracy)
         WS(float, psi, "psi32", S * ctx->Kp);
+        WS(float, psi_lo, "psi32lo", S * ctx->Kp);
         ctx->launch(KLECGC_K_GUESS, st, [&] { launch_psi<float>(xi_d, S, ctx->M, ctx->degrees, ctx->P, psi, ctx->Kp, st); });
-        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_guess_tc(S, NC, ctx->Kp, psi, ctx->W32t, ctx->ubar, U, ctx->tc_err, st); });
+        ctx->launch(KLECGC_K_GUESS, st, [&] { launch_split_tf32(psi, S * ctx->Kp, psi, psi_lo, st); });
+        cudaError_t e = cudaSuccess;
+        ctx->launch(KLECGC_K_GUESS, st, [&] {
+            e = launch_guess_tc(S, NC, ctx->Kp, psi, psi_lo, ctx->W32t, ctx->W32t_lo, ctx->ubar, U,
+                                ctx->tc_err, st);
+        });
+        TRY(e);
     }
     TRY(cudaGetLastError());
     return KLECGC_OK;
@@ -879,12 +887,14 @@ klecgc_status klecgc_load(const char* path, klecgc_ctx** out, void* stream) {
     ctx->Kp = guess_tc_k_padded(ctx->P);
     if (ctx->alloc_owned(&ctx->W32, (size_t)ctx->P * NC) != cudaSuccess ||
         ctx->alloc_owned(&ctx->W32t, (size_t)ctx->Kp * NC) != cudaSuccess ||
+        ctx->alloc_owned(&ctx->W32t_lo, (size_t)ctx->Kp * NC) != cudaSuccess ||
         ctx->alloc_owned(&ctx->tc_err, 1) != cudaSuccess)
         return bail(fail(KLECGC_E_OUT_OF_MEMORY, "W32"));
     if (cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), st) != cudaSuccess)
         return bail(fail(KLECGC_E_CUDA, "memset"));
     launch_to_float(ctx->W, ctx->W32, (int64_t)ctx->P * NC, st);
     launch_pad_transpose(ctx->W32, ctx->P, NC, ctx->Kp, ctx->W32t, st);
+    launch_split_tf32(ctx->W32t, (int64_t)ctx->Kp * NC, ctx->W32t, ctx->W32t_lo, st);
     if (hd.mlp_ready) {
         if ((s = mlp_alloc(ctx)) != KLECGC_OK) return bail(s);
         MlpState& q = ctx->mlp;
@@ -1173,11 +1183,13 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     STRY(ctx->alloc_owned(&ctx->W32, (size_t)P * NC));
     ctx->Kp = guess_tc_k_padded(P);
     STRY(ctx->alloc_owned(&ctx->W32t, (size_t)ctx->Kp * NC));
+    STRY(ctx->alloc_owned(&ctx->W32t_lo, (size_t)ctx->Kp * NC));
     STRY(ctx->alloc_owned(&ctx->tc_err, 1));
     STRY(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), st));
     launch_gemm<double>(P, NC, MQ, Hd, MQ, 1, Gd, NC, 1, ctx->W, NC, false, nullptr, st);
     launch_to_float(ctx->W, ctx->W32, (int64_t)P * NC, st);
     launch_pad_transpose(ctx->W32, P, NC, ctx->Kp, ctx->W32t, st);
+    launch_split_tf32(ctx->W32t, (int64_t)ctx->Kp * NC, ctx->W32t, ctx->W32t_lo, st);
     STRY(cudaGetLastError());
     STRY(cudaStreamSynchronize(st));
     // release the training-sized scratch

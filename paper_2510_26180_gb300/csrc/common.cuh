@@ -161,10 +161,15 @@ void launch_scatter_blocks(const double* src, const int64_t* off, int64_t S, int
 int guess_tc_k_padded(int P);
 // Wt[c][j] = W[j][c] (j < P), zero up to Kp.
 void launch_pad_transpose(const float* W, int P, int64_t NC, int Kp, float* Wt, cudaStream_t st);
-// U[s][c] = ubar[c] + sum_j psi[s][j] Wt[c][j] (psi [S][Kp], zero-padded; NC even);
-// *err = 1 if a pipeline wait ran out of its budget.
-void launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi, const float* Wt,
-                     const double* ubar, double* U, int* err, cudaStream_t st);
+// hi = TF32 rounding of x, lo = x - hi.
+void launch_split_tf32(const float* x, int64_t n, float* hi, float* lo, cudaStream_t st);
+// U[s][c] = ubar[c] + sum_j psi[s][j] Wt[c][j] with psi and Wt split into TF32
+// head and tail ([S][Kp], [NC][Kp], zero-padded, 16-byte aligned; NC even),
+// loaded by TMA; *err = 1 if a pipeline wait ran out of its budget.
+// Returns an error if the tensor maps cannot be encoded.
+cudaError_t launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi_hi,
+                            const float* psi_lo, const float* Wt_hi, const float* Wt_lo,
+                            const double* ubar, double* U, int* err, cudaStream_t st);
 
 // ---- k_nonlinear.cu ---- (cubic reaction, simplified-Newton CGC; wf = a / h^2)
 // F by Newton backward-Euler steps and the jump b = F - G(prev) per (s, n);

@@ -3,22 +3,24 @@
 //
 // One CTA computes a 128 x 256 output tile with tcgen05.mma (kind::tf32, FP32
 // accumulation in tensor memory).  To keep FP32 accuracy each operand is
-// split into a TF32 head and an FP32 tail, x = hi + lo, and the tile
-// accumulates hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32 rounding).
-// The 128 threads stage K-chunks of 32 of psi (A, 128 x 32) and W^T (B,
-// 256 x 32) into shared memory in the canonical no-swizzle K-major layout
-// (8-row x 16-byte core matrices), double-buffered: while the tensor core
-// multiplies one stage the threads fill the other.  One thread issues the
-// MMAs and commits them to the stage's mbarrier; every wait on an mbarrier is
-// bounded by a clock budget, after which the CTA sets the error flag, and
-// the CTA frees its tensor memory before it returns.
+// split into a TF32 head and an FP32 tail, x = hi + lo (k_split_tf32), and the
+// tile accumulates hi*hi + hi*lo + lo*hi (the lo*lo term is below FP32
+// rounding).  K-chunks of 32 of the four operands (psi head / tail 128 x 32,
+// W^T head / tail 256 x 32) arrive by TMA (cp.async.bulk.tensor, 128-byte
+// swizzle) into a two-stage shared-memory ring; one thread issues the loads,
+// one thread issues the MMAs and commits them to the stage's "empty"
+// mbarrier.  Every wait on an mbarrier is bounded by a clock budget, after
+// which the CTA sets the error flag, drains its copies and MMAs in flight
+// (again bounded) and frees its tensor memory before it returns.
 //
-// Shared-memory layout of one operand chunk (rows R, 32 K values): core
-// matrix (r / 8, k / 4) at byte (r/8 * 8 + k/4) * 128, row r % 8 at +16 (r % 8),
-// so the descriptor's leading byte offset (between core matrices along K) is
-// 128 and the stride byte offset (between 8-row groups) is 1024.  (Either
-// reading of the two offsets addresses only the operand's own chunk.)
+// Shared-memory layout of one operand chunk (R rows of 32 FP32 = 128 bytes):
+// row r at byte 128 r with its eight 16-byte pieces permuted by the 128-byte
+// swizzle (piece q of row r stored at piece q ^ (r % 8)); the 8-row groups are
+// 1024 bytes apart, the stride byte offset of the matrix descriptor.
+#include <cuda.h>  // CUtensorMap and the encode function's type (resolved at run time)
+
 #include <cstdint>
+#include <mutex>
 
 #include "common.cuh"
 
@@ -29,22 +31,11 @@ namespace {
 constexpr int TM = 128, TN = 256, TK = 32;
 constexpr int A_BYTES = TM * TK * 4, B_BYTES = TN * TK * 4;   // one split half
 constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;          // hi and lo of A and B
-constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 64;
+constexpr int SMEM_BYTES = 2 * STAGE_BYTES + 64 + 1024;   // + alignment of the stages
 constexpr long long kWaitCycles = 200000000LL;                   // ~0.1 s at 2 GHz
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
-}
-
-// Shared-memory matrix descriptor: start address, leading / stride byte
-// offsets (16-byte units), descriptor version 1, no swizzle.
-__device__ __forceinline__ uint64_t make_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-    uint64_t d = 0;
-    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
-    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;
-    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;
-    d |= (uint64_t)1 << 46;
-    return d;
 }
 
 // Instruction descriptor of kind::tf32: D FP32, A and B TF32, both K-major,
@@ -117,53 +108,64 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
     for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// Stages rows [r0, r0 + rows) of a K-major FP32 matrix (leading dimension ld,
-// row limit nrows, K columns k0 .. k0+31) as TF32 head and tail.  Thread t
-// handles rows t, t + 128, ...: a warp writes 32 consecutive 16-byte core
-// rows (conflict-free).
-template <int ROWS>
-__device__ __forceinline__ void stage_split(const float* __restrict__ g, int64_t ld,
-                                            int64_t r0, int64_t nrows, int k0, char* hi,
-                                            char* lo) {
-#pragma unroll
-    for (int rr = 0; rr < ROWS / 128; ++rr) {
-        const int r = threadIdx.x + rr * 128;
-        const int64_t gr = r0 + r;
-        float4 x[8];
-#pragma unroll
-        for (int kq = 0; kq < 8; ++kq)
-            x[kq] = gr < nrows ? *reinterpret_cast<const float4*>(g + gr * ld + k0 + 4 * kq)
-                               : make_float4(0.f, 0.f, 0.f, 0.f);
-#pragma unroll
-        for (int kq = 0; kq < 8; ++kq) {
-            const int off = ((r >> 3) * 8 + kq) * 128 + (r & 7) * 16;
-            float4 h, l;
-            h.x = tf32_hi(x[kq].x);
-            h.y = tf32_hi(x[kq].y);
-            h.z = tf32_hi(x[kq].z);
-            h.w = tf32_hi(x[kq].w);
-            l.x = x[kq].x - h.x;
-            l.y = x[kq].y - h.y;
-            l.z = x[kq].z - h.z;
-            l.w = x[kq].w - h.w;
-            *reinterpret_cast<float4*>(hi + off) = h;
-            *reinterpret_cast<float4*>(lo + off) = l;
-        }
-    }
+// Shared-memory descriptor of a K-major operand tile written by TMA with the
+// 128-byte swizzle: rows of 128 bytes (32 FP32), 8-row groups 1024 bytes apart
+// (stride byte offset), layout type 2 (SWIZZLE_128B), descriptor version 1;
+// the leading byte offset is unused for this layout (set to 16 bytes).  The
+// K step inside the 128-byte row advances the start address by 32 bytes.
+__device__ __forceinline__ uint64_t make_desc_sw128(uint32_t saddr) {
+    uint64_t d = 0;
+    d |= (uint64_t)((saddr & 0x3FFFF) >> 4);
+    d |= (uint64_t)1 << 16;
+    d |= (uint64_t)(1024 >> 4) << 32;
+    d |= (uint64_t)1 << 46;
+    d |= (uint64_t)2 << 61;
+    return d;
 }
 
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+// 2D tiled TMA load of box (x, y) into shared memory, completing on bar.
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, int x, int y,
+                                            uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, "
+        "{%2, %3}], [%4];" ::"r"(smem_u32(dst)),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+        : "memory");
+}
+
+// One CTA per 128 x 256 output tile.  Warp 0 (one thread) loads the four
+// operand tiles of each K-chunk (psi head / tail 128 x 32, W^T head / tail
+// 256 x 32) by TMA into a stage and arms its "full" barrier with the byte
+// count; warp 1 (one thread) waits on "full", issues the twelve MMAs of the
+// chunk and commits them to the stage's "empty" barrier, which the producer
+// waits on before it refills the stage.  All waits are bounded.
 __global__ void __launch_bounds__(128, 1) k_guess_tc(int64_t S, int64_t NC, int Kp,
-                                                    const float* __restrict__ psi,
-                                                    const float* __restrict__ Wt,
+                                                    const __grid_constant__ CUtensorMap mAh,
+                                                    const __grid_constant__ CUtensorMap mAl,
+                                                    const __grid_constant__ CUtensorMap mBh,
+                                                    const __grid_constant__ CUtensorMap mBl,
                                                     const double* __restrict__ ubar,
                                                     double* __restrict__ U, int* __restrict__ err) {
-    extern __shared__ __align__(1024) char smem[];
-    uint64_t* bar = reinterpret_cast<uint64_t*>(smem + 2 * STAGE_BYTES);  // [2]
-    uint32_t* tslot = reinterpret_cast<uint32_t*>(bar + 2);
+    extern __shared__ __align__(1024) char smem_raw[];
+    // 1024-byte alignment of the stages (the swizzle atoms)
+    char* smem = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + 2 * STAGE_BYTES);   // [2]
+    uint64_t* empty = full + 2;                                              // [2]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + 2);
+    int* flags = reinterpret_cast<int*>(tslot + 1);   // [0] skip, [1] loads issued, [2] chunks committed
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int64_t m0 = (int64_t)blockIdx.y * TM, n0 = (int64_t)blockIdx.x * TN;
     // once a CTA has timed out the launch's result is void: later CTAs skip
-    if (*reinterpret_cast<volatile int*>(err)) return;
+    // (read by one thread so that the whole CTA takes the same branch)
+    if (threadIdx.x == 0) flags[0] = *reinterpret_cast<volatile int*>(err);
+    __syncthreads();
+    if (flags[0]) return;
 
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
@@ -173,8 +175,10 @@ __global__ void __launch_bounds__(128, 1) k_guess_tc(int64_t S, int64_t NC, int 
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
     if (threadIdx.x == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int i = 0; i < 2; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -182,44 +186,63 @@ __global__ void __launch_bounds__(128, 1) k_guess_tc(int64_t S, int64_t NC, int 
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     const uint32_t tmem = *tslot;
     constexpr uint32_t idesc = make_idesc(TM, TN);
+    const int nch = Kp / TK;
     bool ok = true;
 
-    const int nch = Kp / TK;
-    for (int c = 0; c < nch; ++c) {
-        const int st = c & 1;
-        char* base = smem + st * STAGE_BYTES;
-        char* Ahi = base;
-        char* Alo = base + A_BYTES;
-        char* Bhi = base + 2 * A_BYTES;
-        char* Blo = Bhi + B_BYTES;
-        // the MMAs that last read this stage (chunk c - 2) must have finished
-        if (c >= 2 && ok) ok = mbar_wait(&bar[st], ((c - 2) >> 1) & 1);
-        stage_split<TM>(psi, Kp, m0, S, c * TK, Ahi, Alo);
-        stage_split<TN>(Wt, Kp, n0, NC, c * TK, Bhi, Blo);
-        // generic-proxy writes -> visible to the tensor core (async proxy)
-        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-        __syncthreads();
-        if (threadIdx.x == 0) {
+    int issued = 0, committed = 0;
+    if (warp == 0 && lane == 0) {
+        // producer
+        for (int c = 0; c < nch && ok; ++c) {
+            const int st = c & 1;
+            char* base = smem + st * STAGE_BYTES;
+            if (c >= 2) ok = mbar_wait(&empty[st], ((c - 2) >> 1) & 1);
+            if (!ok) break;
+            mbar_expect_tx(&full[st], STAGE_BYTES);
+            tma_load_2d(base, &mAh, c * TK, (int)m0, &full[st]);
+            tma_load_2d(base + A_BYTES, &mAl, c * TK, (int)m0, &full[st]);
+            tma_load_2d(base + 2 * A_BYTES, &mBh, c * TK, (int)n0, &full[st]);
+            tma_load_2d(base + 2 * A_BYTES + B_BYTES, &mBl, c * TK, (int)n0, &full[st]);
+            issued = c + 1;
+        }
+        flags[1] = issued;
+    } else if (warp == 1 && lane == 0) {
+        // MMA issuer
+        for (int c = 0; c < nch && ok; ++c) {
+            const int st = c & 1;
+            char* base = smem + st * STAGE_BYTES;
+            ok = mbar_wait(&full[st], (c >> 1) & 1);
+            if (!ok) break;
             asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t ah0 = smem_u32(base), al0 = smem_u32(base + A_BYTES);
+            const uint32_t bh0 = smem_u32(base + 2 * A_BYTES);
+            const uint32_t bl0 = smem_u32(base + 2 * A_BYTES + B_BYTES);
 #pragma unroll
             for (int kk = 0; kk < TK / 8; ++kk) {
-                // K step of 8 TF32 values = 2 core matrices along K
-                const uint32_t ko = kk * 2 * 128;
-                const uint64_t ah = make_desc(smem_u32(Ahi) + ko, 128, 1024);
-                const uint64_t al = make_desc(smem_u32(Alo) + ko, 128, 1024);
-                const uint64_t bh = make_desc(smem_u32(Bhi) + ko, 128, 1024);
-                const uint64_t bl = make_desc(smem_u32(Blo) + ko, 128, 1024);
+                const uint32_t ko = kk * 32;   // 8 TF32 values per K step
+                const uint64_t ah = make_desc_sw128(ah0 + ko), al = make_desc_sw128(al0 + ko);
+                const uint64_t bh = make_desc_sw128(bh0 + ko), bl = make_desc_sw128(bl0 + ko);
                 mma_tf32(tmem, ah, bh, idesc, (c | kk) ? 1u : 0u);
                 mma_tf32(tmem, ah, bl, idesc, 1u);
                 mma_tf32(tmem, al, bh, idesc, 1u);
             }
-            mma_commit(&bar[st]);
+            mma_commit(&empty[st]);
+            committed = c + 1;
         }
+        flags[2] = committed;
     }
-    // all MMAs done: the last commit of each stage
-    if (ok && nch >= 2) ok = mbar_wait(&bar[(nch - 2) & 1], ((nch - 2) >> 1) & 1);
-    if (ok && nch >= 1) ok = mbar_wait(&bar[(nch - 1) & 1], ((nch - 1) >> 1) & 1);
-    ok = __syncthreads_and(ok);   // uniform: the epilogue's TMEM loads are warp-collective
+    ok = __syncthreads_and(ok);
+    issued = flags[1];
+    committed = flags[2];
+    // every thread: the last commit of each stage has landed (all MMAs done);
+    // on failure also every TMA load still in flight, so that nothing writes
+    // shared memory or tensor memory after the CTA has left
+    bool done = true;
+    for (int c = committed - 2; c < committed; ++c)
+        if (c >= 0) done = mbar_wait(&empty[c & 1], (c >> 1) & 1) && done;
+    if (!ok)
+        for (int c = issued - 2; c < issued; ++c)
+            if (c >= committed && c >= 0) done = mbar_wait(&full[c & 1], (c >> 1) & 1) && done;
+    ok = __syncthreads_and(ok && done && committed == nch);   // uniform: TMEM loads are warp-collective
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
     if (ok) {
@@ -255,6 +278,16 @@ __global__ void __launch_bounds__(128, 1) k_guess_tc(int64_t S, int64_t NC, int 
                      : "memory");
 }
 
+// hi = TF32 rounding of x, lo = x - hi (exact), elementwise.
+// Elementwise, so x may alias hi (in-place split).
+__global__ void k_split_tf32(const float* x, int64_t n, float* hi, float* __restrict__ lo) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= n) return;
+    const float v = x[t], h = tf32_hi(v);
+    hi[t] = h;
+    lo[t] = v - h;
+}
+
 // out[c][j] = in[j][c] for j < P, 0 for P <= j < Kp (W^T, K-major for the MMA).
 __global__ void k_pad_transpose(const float* __restrict__ in, int P, int64_t NC, int Kp,
                                 float* __restrict__ out) {
@@ -284,16 +317,64 @@ void launch_pad_transpose(const float* W, int P, int64_t NC, int Kp, float* Wt, 
     k_pad_transpose<<<grid, dim3(32, 8), 0, st>>>(W, P, NC, Kp, Wt);
 }
 
-void launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi, const float* Wt,
-                     const double* ubar, double* U, int* err, cudaStream_t st) {
-    if (S == 0 || NC == 0) return;
+void launch_split_tf32(const float* x, int64_t n, float* hi, float* lo, cudaStream_t st) {
+    if (n == 0) return;
+    k_split_tf32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(x, n, hi, lo);
+}
+
+namespace {
+
+using EncodeTiled = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*,
+                                 const cuuint64_t*, const cuuint64_t*, const cuuint32_t*,
+                                 const cuuint32_t*, CUtensorMapInterleave, CUtensorMapSwizzle,
+                                 CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiled encode_fn() {
+    static EncodeTiled fn = nullptr;
+    static std::once_flag once;
+    std::call_once(once, [] {
+        void* p = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                             &q) == cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            fn = reinterpret_cast<EncodeTiled>(p);
+    });
+    return fn;
+}
+
+// [rows][Kp] FP32, box 32 x box_rows, 128-byte swizzle, zero fill outside.
+bool make_map(CUtensorMap* m, const float* base, int64_t rows, int Kp, int box_rows) {
+    EncodeTiled fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
+    const cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box,
+              es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+}  // namespace
+
+cudaError_t launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi_hi,
+                            const float* psi_lo, const float* Wt_hi, const float* Wt_lo,
+                            const double* ubar, double* U, int* err, cudaStream_t st) {
+    if (S == 0 || NC == 0) return cudaSuccess;
+    CUtensorMap mAh, mAl, mBh, mBl;
+    if (!make_map(&mAh, psi_hi, S, Kp, TM) || !make_map(&mAl, psi_lo, S, Kp, TM) ||
+        !make_map(&mBh, Wt_hi, NC, Kp, TN) || !make_map(&mBl, Wt_lo, NC, Kp, TN))
+        return cudaErrorInvalidValue;
     static bool attr = false;
     if (!attr) {
         cudaFuncSetAttribute(k_guess_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         attr = true;
     }
     dim3 grid((unsigned)((NC + TN - 1) / TN), (unsigned)((S + TM - 1) / TM));
-    k_guess_tc<<<grid, 128, SMEM_BYTES, st>>>(S, NC, Kp, psi, Wt, ubar, U, err);
+    k_guess_tc<<<grid, 128, SMEM_BYTES, st>>>(S, NC, Kp, mAh, mAl, mBh, mBl, ubar, U, err);
+    return cudaGetLastError();
 }
 
 }  // namespace klecgc
