@@ -140,9 +140,10 @@ def _reference_worker_ac(args):
 
 
 class SetupAC1D(Setup1D):
-    """Same stages as Setup1D on the Allen-Cahn-type problem (oracle.nonlinear):
-    Newton backward-Euler propagators and the simplified-Newton CGC with
-    w.cgc_newton steps."""
+    """Same stages as Setup1D on the nonlinear problems of oracle.nonlinear
+    (w.reaction_kind 1: Allen-Cahn-type reaction, 2: Burgers-type
+    convection): Newton backward-Euler propagators and the simplified-Newton
+    CGC with w.cgc_newton steps."""
 
     def operator(self, xi, field_ulps: float = 0.0, seed: int = 0):
         from . import nonlinear
@@ -150,7 +151,8 @@ class SetupAC1D(Setup1D):
         if field_ulps:
             sgn = np.random.default_rng(seed).choice([-1.0, 1.0], size=a.shape)
             a = a * (1.0 + field_ulps * 2.0 ** -53 * sgn)
-        return nonlinear.CubicRD1D(a, self.w.reaction, self.w.forcing)
+        cls = nonlinear.BurgersEO1D if self.w.reaction_kind == 2 else nonlinear.CubicRD1D
+        return cls(a, self.w.reaction, self.w.forcing)
 
     def reference(self, xi) -> np.ndarray:
         from . import nonlinear

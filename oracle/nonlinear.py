@@ -1,12 +1,22 @@
-"""Nonlinear problem and the nonlinear coarse grid correction (oracle).
+"""Nonlinear problems and the nonlinear coarse grid correction (oracle).
 
 Test infrastructure only (imported by tests/, smoke() and bench.py's CPU
 legs); shares no code with the library.
 
-Problem (eq. psys with a nonlinear f, Allen-Cahn-type reaction):
-    f(u) = -A u - c (u^3 - u) + f0,
-A the 1D flux-form operator of oracle.heat1d (a at the faces, zero Dirichlet
-values).  grad f(u) = -A - c diag(3 u^2 - 1).
+Problems (eq. psys with a nonlinear f), A the 1D flux-form operator of
+oracle.heat1d (a at the faces, zero Dirichlet values):
+
+* Allen-Cahn-type reaction (CubicRD1D):
+      f(u) = -A u - c (u^3 - u) + f0,   grad f(u) = -A - c diag(3 u^2 - 1).
+* Burgers-type convection (BurgersEO1D, Section 5, Burgers equation): the
+  convective term (u^2/2)_x in conservative upwind form with the
+  Engquist-Osher flux splitting,
+      f(u) = -A u - c conv(u) + f0,
+      conv(u)_i = (Phi(u_i, u_{i+1}) - Phi(u_{i-1}, u_i)) / h,
+      Phi(l, r) = max(l, 0)^2 / 2 + min(r, 0)^2 / 2,   u_0 = u_{nx+1} = 0;
+  for u >= 0 this is the backward (upwind) difference (u_i^2 - u_{i-1}^2)/(2h).
+  grad conv(u) is tridiagonal: |u_i|/h on the diagonal, min(u_{i+1}, 0)/h
+  right of it and -max(u_{i-1}, 0)/h left of it.
 
 Propagators (backward Euler, Section 5): one step of size dt solves
     w - v = dt f(w)   <=>   w + dt A w + dt c (w^3 - w) = v + dt f0
@@ -53,6 +63,10 @@ class CubicRD1D(Heat1D):
         ab[2, :-1] = dt * self.off
         return ab
 
+    def avg_K_dense(self, u, b):
+        """-gradf_bar = A + diag(averaged_extra(u, b)) (eq. Jac), dense."""
+        return self.dense() + np.diag(averaged_extra(self, u, b))
+
     def be_step_newton(self, v, dt, tol=1e-14, maxit=50):
         """w with w + dt A w + dt c (w^3 - w) = v + dt f0 (Newton from w = v)."""
         v = np.asarray(v, dtype=np.float64)
@@ -66,6 +80,83 @@ class CubicRD1D(Heat1D):
             if np.max(np.abs(d)) <= tol * max(1.0, np.max(np.abs(w))):
                 break
         return w
+
+
+class BurgersEO1D(Heat1D):
+    """Heat1D's operator A (reaction 0) plus the convection c (u^2/2)_x in
+    Engquist-Osher upwind form (module docstring)."""
+
+    def __init__(self, a_faces, c: float, forcing: float = 0.0):
+        super().__init__(a_faces, 0.0, forcing)
+        self.c = float(c)
+
+    def conv(self, U):
+        U = np.asarray(U, dtype=np.float64)
+        z = np.zeros(U.shape[:-1] + (1,))
+        P = np.concatenate([z, U, z], axis=-1)             # boundary zeros
+        flux = np.maximum(P[..., :-1], 0.0) ** 2 / 2 + np.minimum(P[..., 1:], 0.0) ** 2 / 2
+        return (flux[..., 1:] - flux[..., :-1]) / self.h   # faces i+1/2 minus i-1/2
+
+    def f(self, U):
+        return -self.apply(U) - self.c * self.conv(U) + self.forcing
+
+    def K_bands(self, w):
+        """Bands of K(w) = -grad f(w) = A + c grad conv(w) along the last axis:
+        (sub, diag, sup), sub[i] = K[i, i-1] (sub[0] unused), sup[i] = K[i, i+1]
+        (sup[-1] unused)."""
+        w = np.asarray(w, dtype=np.float64)
+        ch = self.c / self.h
+        diag = self.diag + ch * np.abs(w)
+        sub = np.zeros_like(w)
+        sup = np.zeros_like(w)
+        sub[..., 1:] = self.off - ch * np.maximum(w[..., :-1], 0.0)
+        sup[..., :-1] = self.off + ch * np.minimum(w[..., 1:], 0.0)
+        return sub, diag, sup
+
+    @staticmethod
+    def _dense(sub, diag, sup):
+        return np.diag(diag) + np.diag(sub[1:], -1) + np.diag(sup[:-1], 1)
+
+    def jacobian(self, w):
+        """grad f(w), dense."""
+        return -self._dense(*self.K_bands(w))
+
+    def avg_K_dense(self, u, b):
+        """-gradf_bar = -(1/N) sum_n grad f(U_n - b_n) (eq. Jac), dense: the
+        band entries averaged over the N intervals."""
+        sub, diag, sup = self.K_bands(np.asarray(u) - np.asarray(b))
+        return self._dense(sub.mean(axis=0), diag.mean(axis=0), sup.mean(axis=0))
+
+    def be_step_newton(self, v, dt, tol=1e-14, maxit=50):
+        """w with w + dt A w + dt c conv(w) = v + dt f0 (Newton from w = v)."""
+        v = np.asarray(v, dtype=np.float64)
+        w = v.copy()
+        rhs = v + dt * self.forcing
+        for _ in range(maxit):
+            R = w + dt * self.apply(w) + dt * self.c * self.conv(w) - rhs
+            sub, diag, sup = self.K_bands(w)
+            ab = np.zeros((3, self.n))
+            ab[0, 1:] = dt * sup[:-1]
+            ab[1] = 1.0 + dt * diag
+            ab[2, :-1] = dt * sub[1:]
+            d = solve_banded((1, 1), ab, R)
+            w = w - d
+            if np.max(np.abs(d)) <= tol * max(1.0, np.max(np.abs(w))):
+                break
+        return w
+
+
+def _be_step_rows(op, V, dt):
+    V = np.asarray(V, dtype=np.float64)
+    if V.ndim == 1:
+        return op.be_step_newton(V, dt)
+    return np.stack([op.be_step_newton(v, dt) for v in V])
+
+
+# the linear oracle's propagators (oracle.pcgc F, G, parareal_classical,
+# coarse_guess) call op.be_step: on these problems it is the Newton step
+CubicRD1D.be_step = _be_step_rows
+BurgersEO1D.be_step = _be_step_rows
 
 
 def F(op: CubicRD1D, starts, dT: float, J: int):
@@ -120,11 +211,9 @@ def averaged_extra(op, u, b):
 
 def cgc_newton_step(op, u, b, dT, alpha):
     """One simplified Newton step (eq. Newton2) by the diagonalization (eq.
-    three steps) with A replaced by -gradf_bar = A + diag(extra)."""
+    three steps) with A replaced by -gradf_bar."""
     N, n = u.shape
-    extra = averaged_extra(op, u, b)
-    Ad = op.dense()
-    K = Ad + np.diag(extra)                         # -gradf_bar
+    K = op.avg_K_dense(u, b)                        # -gradf_bar
     rhs = dT * (u @ K.T) + dT * op.f(u - b) + b      # -dT(I(x)gradf_bar)u + dT F(u) + b
     j = np.arange(N)
     lam = 1.0 - alpha ** (1.0 / N) * np.exp(-2j * np.pi * j / N)
@@ -139,8 +228,7 @@ def cgc_newton_step(op, u, b, dT, alpha):
 def cgc_newton_dense(op, u, b, dT, alpha):
     """The same step by a dense solve of Jbar (brute force)."""
     N, n = u.shape
-    extra = averaged_extra(op, u, b)
-    K = op.dense() + np.diag(extra)
+    K = op.avg_K_dense(u, b)
     Ca = np.eye(N) - np.eye(N, k=-1)
     Ca[0, -1] = -alpha
     Jbar = np.kron(Ca, np.eye(n)) + dT * np.kron(np.eye(N), K)

@@ -17,6 +17,10 @@ Workload names describe what they are:
 * ``heat1d_uneven`` 8192 1D instances with Nx, N, J drawn per instance.
 * ``ac1d_nx127``    1D Allen-Cahn-type problem (cubic reaction, random
                     diffusion), Nx=127, N=32, J=16, 256 samples.
+* ``burgers1d_nx99`` 1D Burgers-type problem u_t + 25 (u^2/2)_x = (a u_x)_x
+                    (upwind convection, random diffusion), Nx=99, T=0.08,
+                    N=32, J=40, 256 samples, |Xi_t| = 36 (the paper's Burgers
+                    set-up, Section 5, rescaled in time by its mean viscosity).
 * ``mlp_guess``     learned-guess workload on the heat1d_nx1023 problem.
 
 Values the paper leaves open are fixed here (training-set size n_t = 2P,
@@ -84,6 +88,11 @@ WORKLOADS = {
         corr_len=0.3, M=6, gpc_degree=2, n_train=56, eps_kl=1e-10,
         alpha=1e-3, tol=1e-8, S=256, seed=7, train_seed=107,
         reaction=5.0, forcing=0.0, u0_kind=0, reaction_kind=1, cgc_newton=3),
+    "burgers1d_nx99": Workload(
+        name="burgers1d_nx99", dim=1, nx=99, T=0.08, N=32, J=40, sigma=0.3,
+        corr_len=0.3, M=4, gpc_degree=2, n_train=36, eps_kl=1e-10,
+        alpha=1e-3, tol=1e-8, S=256, seed=8, train_seed=108,
+        reaction=25.0, forcing=0.0, u0_kind=0, reaction_kind=2, cgc_newton=3),
     "mlp_guess": Workload(
         name="mlp_guess", dim=1, nx=1023, T=1.0, N=64, J=64, sigma=0.5,
         corr_len=0.5, M=10, gpc_degree=3, n_train=572, eps_kl=1e-10,
