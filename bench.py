@@ -53,7 +53,12 @@ def peaks():
 
 
 def workload_desc(w, S, precision, overrides=None):
-    if w.reaction_kind == 1:
+    if w.reaction_kind == 2:
+        name = (f"{w.name}: 1D u_t+{w.reaction:g}(u^2/2)_x=(a u_x)_x+{w.forcing:g} (Engquist-Osher "
+                f"upwind convection), a=exp(KL, M={w.M}), Nx={w.nx}, T={w.T:g}, N={w.N}, J={w.J}, "
+                f"Newton backward Euler, {w.cgc_newton} simplified Newton steps per CGC, "
+                f"gPC p={w.gpc_degree}, n_t={w.n_train}, alpha={w.alpha}, tol={w.tol}")
+    elif w.reaction_kind == 1:
         name = (f"{w.name}: 1D u_t=(a u_x)_x-{w.reaction:g}(u^3-u)+{w.forcing:g}, a=exp(KL, "
                 f"M={w.M}), Nx={w.nx}, N={w.N}, J={w.J}, Newton backward Euler, "
                 f"{w.cgc_newton} simplified Newton steps per CGC, gPC p={w.gpc_degree}, "
@@ -150,7 +155,7 @@ def oracle_pool(w, cores):
     for k in saved:
         os.environ[k] = "1"
     try:
-        kind = Setup2D if w.dim == 2 else (SetupAC1D if w.reaction_kind == 1 else Setup1D)
+        kind = Setup2D if w.dim == 2 else (SetupAC1D if w.reaction_kind else Setup1D)
         setup = kind(w, processes=cores)
         pool = mp.get_context("spawn").Pool(cores, initializer=_oracle_init, initargs=(setup,))
     finally:
@@ -243,12 +248,14 @@ def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
         return None
     if w.dim == 2:
         return roofline_2d(cls, ms, launches, units, prec)
-    if w.reaction_kind == 1:
+    if w.reaction_kind:
         if cls != "fine":
             return None
-        # Newton iteration of a backward-Euler step: ~33 FP64 flop per row
-        # (residual 13, Thomas forward 15 incl. two divisions, back 5)
-        flops = 33.0 * units["kry_fine"] * w.nx
+        # Newton iteration of a backward-Euler step, FP64 flop per row: cubic
+        # ~33 (residual 13, Thomas forward 15 incl. two divisions, back 5);
+        # Burgers-type ~45 (residual with the two face fluxes 20, Jacobian
+        # bands 7, Thomas forward 13, back 5)
+        flops = (45.0 if w.reaction_kind == 2 else 33.0) * units["kry_fine"] * w.nx
         ach = flops / (ms / 1e3) / 1e12
         return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK,
                 "unit": "TFLOP/s", "frac": ach / FP64_ALU_PEAK, "traffic": None,
@@ -352,7 +359,7 @@ def run_gpu(args, w):
     clocks = sampler.stop()
     prof = solver.profile_read()
     solver.profile_enable(False)
-    kry = solver.krylov_stats() if (w.dim == 2 or w.reaction_kind == 1) else (0, 0)
+    kry = solver.krylov_stats() if (w.dim == 2 or w.reaction_kind) else (0, 0)
     ms = e0.elapsed_time(e1) / args.steps
 
     # accuracy of the last timed step against U* (FP64 reference kernel)
@@ -706,8 +713,8 @@ def main():
         over[k] = float(v) if any(c in v for c in ".e") else int(v)
     w = workload(args.workload, **over)
     args.overrides = over
-    if w.reaction_kind == 1:
-        args.precision = "fp64"      # the cubic-reaction path is FP64
+    if w.reaction_kind:
+        args.precision = "fp64"      # the nonlinear paths are FP64
         args.skip_fp64 = True
     if w.dim == 2:
         # 2D: FP64 Krylov solves, or MIXED (FP64 refinement around FP32 PCG for

@@ -102,9 +102,11 @@ typedef struct {
     double forcing;       /* f0 (constant source) */
     int32_t u0_kind;      /* 0: u0 = sin(pi x) (product of sines in 2D); 1: u0 = 0 */
     int32_t reaction_kind; /* 0: linear reaction -c u; 1: cubic -c (u^3 - u)
-                              (Allen-Cahn type; 1D, FP64; see klecgc_solve) */
-    int32_t cgc_newton;    /* simplified Newton steps per CGC for reaction_kind 1
-                              (eq. Newton2); 0 means 1 */
+                              (Allen-Cahn type); 2: convection -c (u^2/2)_x,
+                              Engquist-Osher upwind (Burgers type); 1 and 2
+                              are 1D and FP64 (see klecgc_solve) */
+    int32_t cgc_newton;    /* simplified Newton steps per CGC for reaction_kind
+                              1 and 2 (eq. Newton2); 0 means 1 */
 } klecgc_problem;
 
 typedef struct {
@@ -166,13 +168,18 @@ klecgc_status klecgc_setup(const klecgc_problem* problem, const double* xi_train
  * else NOT_CONVERGED if any sample hit kmax; INVALID_ARG / UNSUPPORTED /
  * OUT_OF_MEMORY / CUDA for argument and runtime errors (nothing written).
  * Each sample's iterates are independent of the other samples.
- * Cubic reaction (problem reaction_kind 1, f(u) = div(a grad u) - c (u^3 - u)
- * + f0, 1D): F and G take Newton iterations for every backward-Euler step
- * (tridiagonal Jacobian, to 1e-14 relative); the CGC solves eq. matrix_NT by
+ * Nonlinear problems (1D): problem reaction_kind 1, f(u) = div(a grad u) -
+ * c (u^3 - u) + f0 (Allen-Cahn type), and reaction_kind 2, f(u) =
+ * div(a grad u) - c (u^2/2)_x + f0 (Burgers type; Section 5 discretizes the
+ * convection by upwinding, here the conservative Engquist-Osher flux
+ * (max(u_l, 0)^2 + min(u_r, 0)^2) / 2 at each face, zero boundary values):
+ * F and G take Newton iterations for every backward-Euler step (tridiagonal
+ * Jacobian, to 1e-14 relative); the CGC solves eq. matrix_NT by
  * problem.cgc_newton simplified Newton steps of eq. Newton2 with the
- * time-averaged Jacobian of eq. Jac, each diagonalized like the linear CGC.
- * FP64 only; guesses GPC, ZERO, USER, COARSE; the stage entry points, the
- * batch, classical parareal and the learned guess take linear problems only.
+ * time-averaged Jacobian of eq. Jac (non-symmetric tridiagonal for kind 2),
+ * each diagonalized like the linear CGC.  FP64 only; guesses GPC, ZERO,
+ * USER, COARSE; the stage entry points, the batch and the learned guess
+ * take linear problems only.
  */
 klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S,
                            double dT, int32_t J, int32_t N, double alpha, double tol,
@@ -186,7 +193,10 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S,
  * parallel and then the sequential coarse correction
  *     U^{k+1}_n = G(U^{k+1}_{n-1}) + F(U^k_{n-1}) - G(U^k_{n-1}),  U_0 = u0,
  * with G one backward-Euler step of dT, per sample in order of n (no alpha
- * twist, no diagonalization).  FP64, 1D contexts (UNSUPPORTED for dim = 2).
+ * twist, no diagonalization).  FP64, 1D contexts (UNSUPPORTED for dim = 2);
+ * for the nonlinear problems (reaction_kind 1, 2) F and G are the Newton
+ * backward-Euler propagators of klecgc_solve (KLE-CGC of Section 5 with the
+ * gPC guess).
  * Arguments, stopping rule, outputs and return as klecgc_solve, except: any
  * N >= 1 (no FFT); guess KLECGC_GUESS_GPC (N must be the setup's N), _ZERO,
  * _USER or _COARSE (the usual parareal start, U^0_n = G(U^0_{n-1})).

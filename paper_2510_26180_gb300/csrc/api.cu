@@ -406,7 +406,9 @@ klecgc_status sequential_2d(klecgc_ctx* ctx, const double* xi_d, int64_t S, int 
     return krylov_read(ctx, S, ifail, its, st, &hf, capped);
 }
 
-bool nonlinear(const klecgc_ctx* ctx) { return ctx->prob.reaction_kind == 1; }
+bool nonlinear(const klecgc_ctx* ctx) {
+    return ctx->prob.reaction_kind == 1 || ctx->prob.reaction_kind == 2;
+}
 
 // Nonlinear problem: coefficient field and the face weights a / h^2.
 klecgc_status nl_weights(klecgc_ctx* ctx, const double* xi_d, int64_t S, cudaStream_t st,
@@ -430,8 +432,8 @@ klecgc_status nl_sequential(klecgc_ctx* ctx, const double* wf, int64_t S, int N,
     WS(int, flag, "nl_seq_fail", S);
     TRY(cudaMemsetAsync(flag, 0, S * sizeof(int), st));
     ctx->launch(KLECGC_K_FINE, st, [&] {
-        launch_sequential_newton(S, N, ctx->nx, J, dt, ctx->prob.reaction, ctx->prob.forcing,
-                                 ctx->u0, wf, scr, U, flag, st);
+        launch_sequential_newton(ctx->prob.reaction_kind, S, N, ctx->nx, J, dt, ctx->prob.reaction,
+                                 ctx->prob.forcing, ctx->u0, wf, scr, U, flag, st);
     });
     TRY(cudaGetLastError());
     std::vector<int> h(S);
@@ -988,10 +990,10 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     if (pr->nx < 1 || pr->M < 1 || pr->gpc_degree < 0 || pr->n_train < 2 || !(pr->T > 0) ||
         !(pr->sigma >= 0) || !(pr->corr_len > 0) || !(pr->eps_kl >= 0) || pr->J < 1 ||
         !(pr->reaction >= 0) || !std::isfinite(pr->forcing) || pr->u0_kind < 0 ||
-        pr->u0_kind > 1 || pr->reaction_kind < 0 || pr->reaction_kind > 1 || pr->cgc_newton < 0)
+        pr->u0_kind > 1 || pr->reaction_kind < 0 || pr->reaction_kind > 2 || pr->cgc_newton < 0)
         return fail(KLECGC_E_INVALID_ARG, "problem field out of range");
-    if (pr->reaction_kind == 1 && pr->dim != 1)
-        return fail(KLECGC_E_UNSUPPORTED, "the cubic reaction is 1D only");
+    if (pr->reaction_kind != 0 && pr->dim != 1)
+        return fail(KLECGC_E_UNSUPPORTED, "the nonlinear problems are 1D only");
     if (!pow2_in_range(pr->N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
     cudaStream_t st = (cudaStream_t)stream;
     klecgc_ctx* ctx = new klecgc_ctx();
@@ -1909,11 +1911,12 @@ struct PinnedInts {
     }
 };
 
-// Algorithm 2 with the nonlinear CGC (reaction_kind 1, FP64): per iteration,
-// F by Newton steps and the jump b (k_fine_newton), then cgc_newton
-// simplified Newton steps of eq. Newton2 from u_0 = U^k, each the three
-// diagonalized steps with the averaged Jacobian (k_nl_prep, shifted factors
-// with the diagonal extra, forward transform, solves, inverse transform); the
+// Algorithm 2 with the nonlinear CGC (reaction_kind 1 or 2, FP64): per
+// iteration, F by Newton steps and the jump b (k_fine_newton), then
+// cgc_newton simplified Newton steps of eq. Newton2 from u_0 = U^k, each the
+// three diagonalized steps with the averaged Jacobian (k_nl_prep and shifted
+// factors with the diagonal extra, or k_nl_prep_burgers and the factors of
+// the face couplings; forward transform, solves, inverse transform); the
 // last one writes U^{k+1} and the increment norm.
 klecgc_status solve_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S, double dT, int J,
                               int N, double alpha, double tol, int kmax, int guess,
@@ -1924,9 +1927,11 @@ klecgc_status solve_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S, do
     const int64_t NS = S * (int64_t)nx * N;
     const int L = ctx->prob.cgc_newton > 0 ? ctx->prob.cgc_newton : 1;
     const double c = ctx->prob.reaction, f0 = ctx->prob.forcing;
+    const int kind = ctx->prob.reaction_kind;
     double *a = nullptr, *wf = nullptr;
     if ((s = nl_weights(ctx, xi_d, S, st, &a, &wf)) != KLECGC_OK) return s;
     WS(double, wT, "wT", S * (int64_t)ctx->nf);
+    WS(double, up, "nl_up", S * (int64_t)ctx->nf);
     ctx->launch(KLECGC_K_FIELD, st, [&] { launch_face_weights(a, S, ctx->nf, dT / (ctx->h * ctx->h), wT, st); });
     WS(double, U, "U", NS);
     if (guess == KLECGC_GUESS_GPC) {
@@ -1969,13 +1974,19 @@ klecgc_status solve_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S, do
     TRY(cudaMallocHost(&pin.p, sizeof(int)));
     for (int k = 0; k < kmax; ++k) {
         ctx->launch(KLECGC_K_FINE, st, [&] {
-            launch_fine_newton(S, N, nx, J, dT, alpha, c, f0, U, ctx->u0, wf, b, scr, active,
-                               ifail, nits, st);
+            launch_fine_newton(kind, S, N, nx, J, dT, alpha, c, f0, 1, U, ctx->u0, wf, b, scr,
+                               active, ifail, nits, st);
         });
         for (int l = 0; l < L; ++l) {
             const double* cur = l == 0 ? U : ul;
-            ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_nl_prep(S, N, nx, dT, c, f0, cur, b, wf, rhs, e, active, st); });
-            ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_cgc_factors<double>(a, S, nx, ctx->h, dT, 0.0, lam_d, K, di, lu, st, e); });
+            if (kind == 2) {
+                // wT receives the lower face couplings lo (k_cgc_solve's wT)
+                ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_nl_prep_burgers(S, N, nx, dT, c, f0, cur, b, wf, rhs, wT, up, active, st); });
+                ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_cgc_factors_faces(S, nx, wT, up, lam_d, K, di, lu, active, st); });
+            } else {
+                ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_nl_prep(S, N, nx, dT, c, f0, cur, b, wf, rhs, e, active, st); });
+                ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_cgc_factors<double>(a, S, nx, ctx->h, dT, 0.0, lam_d, K, di, lu, st, e); });
+            }
             ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<double, double>(S, N, nx, rhs, sc, p64, active, st); });
             ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_cgc_solve<double, double>(S, K, nx, di, lu, wT, p64, active, st); });
             if (l + 1 == L)
@@ -2011,6 +2022,76 @@ klecgc_status solve_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S, do
     return KLECGC_OK;
 }
 
+// Algorithm 1 with Newton propagators (nonlinear problems, FP64): per
+// iteration F on every interval (k_fine_newton without the jump), then the
+// sequential correction with Newton G (k_parareal_correct_newton).
+klecgc_status parareal_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S, double dT,
+                                 int J, int N, double tol, int kmax, int guess,
+                                 const double* U_guess, double* U_out, std::vector<int32_t>& hs,
+                                 std::vector<int32_t>& hi, cudaStream_t st) {
+    klecgc_status s;
+    const int nx = ctx->nx, kind = ctx->prob.reaction_kind;
+    const int64_t NS = S * (int64_t)nx * N;
+    const double c = ctx->prob.reaction, f0 = ctx->prob.forcing;
+    double *a = nullptr, *wf = nullptr;
+    if ((s = nl_weights(ctx, xi_d, S, st, &a, &wf)) != KLECGC_OK) return s;
+    WS(double, U, "U", NS);
+    if (guess == KLECGC_GUESS_GPC) {
+        if ((s = gpc_guess_internal(ctx, xi_d, S, true, U, st)) != KLECGC_OK) return s;
+    } else if (guess == KLECGC_GUESS_ZERO) {
+        TRY(cudaMemsetAsync(U, 0, NS * sizeof(double), st));
+    } else if (guess == KLECGC_GUESS_COARSE) {
+        bool cap = false;
+        if ((s = nl_sequential(ctx, wf, S, N, 1, dT, U, st, &cap)) != KLECGC_OK) return s;
+    } else if ((s = import_batch(ctx, U_guess, S, N, U, st)) != KLECGC_OK) {
+        return s;
+    }
+    WS(double, Fend, "r", NS);
+    WS(double, scr, "nl_scratch", 4 * NS);
+    WS(double, pscr, "par_scratch_nl", 5 * S * (int64_t)nx);
+    WS(int, active, "active", S);
+    WS(int32_t, iters, "iters", S);
+    WS(int32_t, status, "status", S);
+    WS(unsigned long long, delta, "delta", S);
+    WS(int, n_active, "n_active", 1);
+    WS(int, ifail, "nl_fail", S);
+    WS(unsigned long long, nits, "kry_its", 2);
+    TRY(cudaMemsetAsync(nits, 0, 2 * sizeof(unsigned long long), st));
+    TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
+    TRY(cudaMemsetAsync(iters, 0xff, S * sizeof(int32_t), st));
+    TRY(cudaMemsetAsync(status, 0, S * sizeof(int32_t), st));
+    TRY(cudaMemsetAsync(ifail, 0, S * sizeof(int), st));
+    PinnedInts pin;
+    TRY(cudaMallocHost(&pin.p, sizeof(int)));
+    for (int k = 0; k < kmax; ++k) {
+        ctx->launch(KLECGC_K_FINE, st, [&] {
+            launch_fine_newton(kind, S, N, nx, J, dT, 0.0, c, f0, 0, U, ctx->u0, wf, Fend, scr,
+                               active, ifail, nits, st);
+        });
+        ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] {
+            launch_parareal_correct_newton(kind, S, N, nx, dT, c, f0, ctx->u0, wf, Fend, U, pscr,
+                                           delta, active, ifail, st);
+        });
+        TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
+        ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
+        TRY(cudaGetLastError());
+        TRY(cudaMemcpyAsync(pin.p, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (*pin.p == 0) break;
+    }
+    if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) return s;
+    hs.assign(S, 0);
+    hi.assign(S, 0);
+    std::vector<int> hf(S);
+    TRY(cudaMemcpyAsync(hs.data(), status, S * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(hi.data(), iters, S * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaMemcpyAsync(hf.data(), ifail, S * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    for (int64_t i = 0; i < S; ++i)
+        if (hf[i] && hs[i] == KLECGC_OK) hs[i] = KLECGC_E_NOT_CONVERGED;
+    return KLECGC_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -2033,7 +2114,7 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
     if (ctx->dim == 2 && precision == KLECGC_MIXED_DEFECT)
         return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 or MIXED only");
     if (nonlinear(ctx) && (precision != KLECGC_FP64 || guess == KLECGC_GUESS_MLP))
-        return fail(KLECGC_E_UNSUPPORTED, "cubic reaction: FP64, guesses GPC/ZERO/USER/COARSE");
+        return fail(KLECGC_E_UNSUPPORTED, "nonlinear problems: FP64, guesses GPC/ZERO/USER/COARSE");
     klecgc_status s = check_dT(ctx, N, dT);
     if (s != KLECGC_OK) return s;
     if (S == 0) return KLECGC_OK;
@@ -2102,8 +2183,7 @@ klecgc_status klecgc_solve_parareal(klecgc_ctx* ctx, const double* xi, int64_t S
     if (J < 1 || N < 1 || N > 4096 || !(tol > 0) || kmax < 1 || guess < 0 || guess > 3 ||
         (guess == KLECGC_GUESS_USER && !U_guess && S > 0))
         return fail(KLECGC_E_INVALID_ARG, "argument out of range");
-    if (ctx->dim != 1 || nonlinear(ctx))
-        return fail(KLECGC_E_UNSUPPORTED, "classical parareal: linear 1D problems only");
+    if (ctx->dim != 1) return fail(KLECGC_E_UNSUPPORTED, "classical parareal: 1D problems only");
     if (guess == KLECGC_GUESS_GPC && N != ctx->N)
         return fail(KLECGC_E_INVALID_ARG, "the gPC guess needs the setup's N");
     klecgc_status s = check_dT(ctx, N, dT);
@@ -2117,6 +2197,16 @@ klecgc_status klecgc_solve_parareal(klecgc_ctx* ctx, const double* xi, int64_t S
     bool finite = true;
     if ((s = check_xi_finite(ctx, xi_d, S * ctx->M, st, &finite)) != KLECGC_OK) return s;
     if (!finite) return fail(KLECGC_E_NONFINITE, "xi has a non-finite entry");
+    if (nonlinear(ctx)) {
+        std::vector<int32_t> hs, hi;
+        if ((s = parareal_nonlinear(ctx, xi_d, S, dT, J, N, tol, kmax, guess, U_guess, U_out, hs,
+                                    hi, st)) != KLECGC_OK)
+            return s;
+        ctx->prof_collect();
+        if (iters_out) TRY(cudaMemcpy(iters_out, hi.data(), S * 4, cudaMemcpyDefault));
+        if (status_out) TRY(cudaMemcpy(status_out, hs.data(), S * 4, cudaMemcpyDefault));
+        return status_summary(hs, false);
+    }
     Operators op;
     if ((s = build_operators(ctx, xi_d, S, N, J, dT, 0.5, 1, 0, st, &op)) != KLECGC_OK) return s;
     WS(FineCoef64, gc, "coarse64", S * (int64_t)(nx + 1));

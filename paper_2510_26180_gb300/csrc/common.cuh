@@ -171,17 +171,33 @@ cudaError_t launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi_hi,
                             const float* psi_lo, const float* Wt_hi, const float* Wt_lo,
                             const double* ubar, double* U, int* err, cudaStream_t st);
 
-// ---- k_nonlinear.cu ---- (cubic reaction, simplified-Newton CGC; wf = a / h^2)
-// F by Newton backward-Euler steps and the jump b = F - G(prev) per (s, n);
-// scratch: 4 S nx N doubles.
-void launch_fine_newton(int64_t S, int N, int nx, int J, double dT, double alpha, double c,
-                        double f0, const double* U, const double* u0, const double* wf, double* b,
-                        double* scratch, const int* active, int* ifail,
-                        unsigned long long* itcount, cudaStream_t st);
+// ---- k_nonlinear.cu ---- (kind 1 cubic reaction, kind 2 Burgers-type
+// convection; simplified-Newton CGC; wf = a / h^2; c the problem's coefficient)
+// F by Newton backward-Euler steps and, with jump, b = F - G(prev) per (s, n)
+// (else F); scratch: 4 S nx N doubles.
+void launch_fine_newton(int kind, int64_t S, int N, int nx, int J, double dT, double alpha,
+                        double c, double f0, int jump, const double* U, const double* u0,
+                        const double* wf, double* b, double* scratch, const int* active,
+                        int* ifail, unsigned long long* itcount, cudaStream_t st);
 // N J sequential Newton steps of dt per sample (one thread each); scratch 4 nx S.
-void launch_sequential_newton(int64_t S, int N, int nx, int J, double dt, double c, double f0,
-                              const double* u0, const double* wf, double* scratch, double* U,
-                              int* ifail, cudaStream_t st);
+void launch_sequential_newton(int kind, int64_t S, int N, int nx, int J, double dt, double c,
+                              double f0, const double* u0, const double* wf, double* scratch,
+                              double* U, int* ifail, cudaStream_t st);
+// Kind 2: face couplings lo, up ([S][nx+1], dT-scaled) of the averaged
+// Jacobian and the right-hand side of eq. Newton2.
+void launch_nl_prep_burgers(int64_t S, int N, int nx, double dT, double c, double f0,
+                            const double* u, const double* b, const double* wf, double* rhs,
+                            double* lo, double* up, const int* active, cudaStream_t st);
+// Factors of lambda_k I + dT K from the face couplings (k_cgc_solve layout).
+void launch_cgc_factors_faces(int64_t S, int nx, const double* lo, const double* up,
+                              const double2* lam, int K, Cplx<double>* dinv, Cplx<double>* lu,
+                              const int* active, cudaStream_t st);
+// Classical parareal correction with Newton G; scratch 5 nx S doubles.
+void launch_parareal_correct_newton(int kind, int64_t S, int N, int nx, double dT, double c,
+                                    double f0, const double* u0, const double* wf,
+                                    const double* F, double* U, double* scratch,
+                                    unsigned long long* delta, const int* active, int* ifail,
+                                    cudaStream_t st);
 // e = c (3 mean_n (u - b)^2 - 1) per row and the right-hand side of eq. Newton2.
 void launch_nl_prep(int64_t S, int N, int nx, double dT, double c, double f0, const double* u,
                     const double* b, const double* wf, double* rhs, double* e, const int* active,

@@ -1,23 +1,34 @@
-// Nonlinear 1D problem (Allen-Cahn-type reaction) and the nonlinear coarse
-// grid correction by simplified Newton (Section 3.2, eqs. Newton, Jac, Newton2).
+// Nonlinear 1D problems and the nonlinear coarse grid correction by
+// simplified Newton (Section 3.2, eqs. Newton, Jac, Newton2).  A is the
+// flux-form operator with face weights wf_i = a_{i-1/2} / h^2.
 //
-//   f(u) = -A u - c (u^3 - u) + f0,   grad f(u) = -A - c diag(3 u^2 - 1),
-// A the flux-form operator with face weights wf_i = a_{i-1/2} / h^2.
+//   kind 1 (Allen-Cahn-type):  f(u) = -A u - c (u^3 - u) + f0,
+//                              grad f(u) = -A - c diag(3 u^2 - 1);
+//   kind 2 (Burgers-type):     f(u) = -A u - c conv(u) + f0, the convection
+//       (u^2/2)_x in conservative upwind form with the Engquist-Osher flux
+//       splitting (Section 5, Burgers equation: upwind convection, central
+//       diffusion):  conv(u)_i = (Phi(u_i, u_{i+1}) - Phi(u_{i-1}, u_i)) / h,
+//       Phi(l, r) = max(l, 0)^2 / 2 + min(r, 0)^2 / 2, zero boundary values;
+//       -grad f(u) = A + (c/h) tridiag(-max(u_{i-1}, 0), |u_i|, min(u_{i+1}, 0)).
 //
 // Backward Euler (both propagators): one step of size dt solves
-//     w + dt A w + dt c (w^3 - w) = v + dt f0
-// by Newton's method from w = v: the Jacobian I + dt A + dt c diag(3 w^2 - 1) is
-// tridiagonal and factored anew in every Newton iteration (Thomas), stopping
-// when max |dw| <= 1e-14 max(1, max |w|) (at most kNewtonMax iterations; a step
-// that reaches the cap sets the sample's flag).
+//     w - dt f(w) = v   (w + dt A w + dt (nonlinear term) = v + dt f0)
+// by Newton's method from w = v: the Jacobian I - dt grad f(w) is tridiagonal
+// and factored anew in every Newton iteration (Thomas), stopping when
+// max |dw| <= 1e-14 max(1, max |w|) (at most kNewtonMax iterations; a step that
+// reaches the cap sets the sample's flag).
 //
 // CGC: eq. matrix_NT, (C_alpha (x) I) u = dT F(u) + b, F(u)_n = f(U_n - b_n), by
 // simplified Newton steps from u_0 = U^k:
-//     Jbar u_{l+1} = dT (I (x) K) u_l + dT F(u_l) + b,  K = -gradf_bar = A + diag(e),
-//     e_i = c (3 m_i - 1),  m_i = (1/N) sum_n (U_{n,i} - b_{n,i})^2   (eq. Jac),
-// Jbar = C_alpha (x) I + dT I (x) K: the linear three steps with the shifted
-// factors built from the diagonal extra dT e (k_nl_prep writes e and the
-// right-hand side; the transforms and solves are the linear kernels).
+//     Jbar u_{l+1} = dT (I (x) K) u_l + dT F(u_l) + b,  K = -gradf_bar,
+// gradf_bar = (1/N) sum_n grad f(U_{n,l} - b_n) (eq. Jac), Jbar = C_alpha (x) I +
+// dT I (x) K: the linear three steps with shifted factors of K.  Kind 1:
+// K = A + diag(e), e_i = c (3 m_i - 1), m_i = mean_n (U_{n,i} - b_{n,i})^2
+// (k_nl_prep).  Kind 2: K is a non-symmetric tridiagonal written with face
+// couplings (dT-scaled), row i: -lo_i u_{i-1} + (up_i + lo_{i+1}) u_i -
+// up_{i+1} u_{i+1}, lo_i = dT (wf_i + (c/h) mean_n max(z_{i-1}, 0)),
+// up_i = dT (wf_i - (c/h) mean_n min(z_i, 0)), z = U - b (k_nl_prep_burgers;
+// k_cgc_factors_faces factors lambda_k I + dT K from them).
 //
 // Layout: U, b, rhs [S][nx][N]; columns (s, n) are strided by N (a warp of
 // consecutive n coalesces).
@@ -29,28 +40,46 @@ namespace {
 
 constexpr int kNewtonMax = 50;
 
+__device__ __forceinline__ double eo_flux(double l, double r) {
+    const double p = fmax(l, 0.0), m = fmin(r, 0.0);
+    return 0.5 * (p * p + m * m);
+}
+
 // One Newton backward-Euler step on the column w (stride st): v is the start
 // value (overwritten by nothing), w the iterate (in/out), cp / dp Thomas
-// scratch.  wf: face weights a/h^2 (nx + 1), dt, c, f0.  Returns false if the
-// iteration cap was reached; adds the Newton iterations taken to *its.
+// scratch.  wf: face weights a/h^2 (nx + 1), dt, c (KIND 1: the cubic
+// coefficient; KIND 2: c/h), f0.  Returns false if the iteration cap was
+// reached; adds the Newton iterations taken to *its.
+template <int KIND>
 __device__ bool newton_be(int nx, const double* __restrict__ wf, double dt, double c,
                           double f0, const double* v, double* w, double* cp, double* dp,
                           int64_t st, unsigned long long* its) {
     for (int it = 0; it < kNewtonMax; ++it) {
         ++*its;
-        // residual R = w + dt A w + dt c (w^3 - w) - v - dt f0 and the Thomas
-        // forward elimination of (I + dt A + dt c diag(3 w^2 - 1)) d = R
+        // residual R = w - dt f(w) - v and the Thomas forward elimination of
+        // (I - dt grad f(w)) d = R, row i: lower d_{i-1} + diag d_i + upper d_{i+1}
         double wl = 0.0, wi = w[0], prevc = 0.0, prevd = 0.0;
         for (int i = 0; i < nx; ++i) {
             const double wr = i + 1 < nx ? w[(int64_t)(i + 1) * st] : 0.0;
             const double fl = dt * wf[i], fr = dt * wf[i + 1];
             const double Aw = fl * (wi - wl) - fr * (wr - wi);          // dt A w
-            const double R = wi + Aw + dt * c * (wi * wi * wi - wi) - v[(int64_t)i * st] - dt * f0;
-            const double diag = 1.0 + fl + fr + dt * c * (3.0 * wi * wi - 1.0);
-            // row i: -fl d_{i-1} + diag d_i - fr d_{i+1} = R
-            const double den = diag + fl * prevc;                    // diag - (-fl) c'_{i-1}
-            const double ci = -fr / den;                             // c'_i (upper / pivot)
-            const double di = (R + fl * prevd) / den;
+            double R, diag, lower, upper;
+            if (KIND == 1) {
+                R = wi + Aw + dt * c * (wi * wi * wi - wi) - v[(int64_t)i * st] - dt * f0;
+                diag = 1.0 + fl + fr + dt * c * (3.0 * wi * wi - 1.0);
+                lower = -fl;
+                upper = -fr;
+            } else {
+                const double dc = dt * c;
+                R = wi + Aw + dc * (eo_flux(wi, wr) - eo_flux(wl, wi)) - v[(int64_t)i * st] -
+                    dt * f0;
+                diag = 1.0 + fl + fr + dc * fabs(wi);
+                lower = -fl - dc * fmax(wl, 0.0);
+                upper = -fr + dc * fmin(wr, 0.0);
+            }
+            const double den = diag - lower * prevc;                 // pivot
+            const double ci = upper / den;                           // c'_i
+            const double di = (R - lower * prevd) / den;
             cp[(int64_t)i * st] = ci;
             dp[(int64_t)i * st] = di;
             prevc = ci;
@@ -76,11 +105,12 @@ __device__ bool newton_be(int nx, const double* __restrict__ wf, double dt, doub
 
 }  // namespace
 
-// F (J steps of dt = dT/J from start_n = u0 or U_{n-1}) and the jump
-// b_n = F_n - G(prev_n), prev_1 = alpha U_N, prev_n = U_{n-1}, per column (s, n).
-// Scratch: v, cp, dp, g [S][nx][N]; bout receives b (and holds F meanwhile).
+// F (J steps of dt = dT/J from start_n = u0 or U_{n-1}) and, with jump set,
+// the jump b_n = F_n - G(prev_n), prev_1 = alpha U_N, prev_n = U_{n-1}, per
+// column (s, n); without it bout receives F.  Scratch: v, cp, dp, g [S][nx][N].
+template <int KIND>
 __global__ void __launch_bounds__(128) k_fine_newton(
-    int64_t S, int N, int nx, int J, double dT, double alpha, double c, double f0,
+    int64_t S, int N, int nx, int J, double dT, double alpha, double c, double f0, int jump,
     const double* __restrict__ U, const double* __restrict__ u0, const double* __restrict__ wf,
     double* __restrict__ bout, double* __restrict__ vs, double* __restrict__ cps,
     double* __restrict__ dps, double* __restrict__ gs, const int* __restrict__ active,
@@ -102,35 +132,49 @@ __global__ void __launch_bounds__(128) k_fine_newton(
     const double dt = dT / J;
     for (int j = 0; j < J && ok; ++j) {
         for (int i = 0; i < nx; ++i) v[(int64_t)i * N] = w[(int64_t)i * N];
-        ok = newton_be(nx, wfs, dt, c, f0, v, w, cp, dp, N, &its);
+        ok = newton_be<KIND>(nx, wfs, dt, c, f0, v, w, cp, dp, N, &its);
     }
-    // G(prev): one step of dT from prev (start v, iterate g); F stays in w
-    double* g = gs + base;
-    for (int i = 0; i < nx; ++i) {
-        const double pv = n == 0 ? alpha * Us[(int64_t)i * N + N - 1] : Us[(int64_t)i * N + n - 1];
-        v[(int64_t)i * N] = pv;
-        g[(int64_t)i * N] = pv;
+    if (jump) {
+        // G(prev): one step of dT from prev (start v, iterate g); F stays in w
+        double* g = gs + base;
+        for (int i = 0; i < nx; ++i) {
+            const double pv =
+                n == 0 ? alpha * Us[(int64_t)i * N + N - 1] : Us[(int64_t)i * N + n - 1];
+            v[(int64_t)i * N] = pv;
+            g[(int64_t)i * N] = pv;
+        }
+        if (ok) ok = newton_be<KIND>(nx, wfs, dT, c, f0, v, g, cp, dp, N, &its);
+        for (int i = 0; i < nx; ++i) w[(int64_t)i * N] -= g[(int64_t)i * N];
     }
-    if (ok) ok = newton_be(nx, wfs, dT, c, f0, v, g, cp, dp, N, &its);
-    for (int i = 0; i < nx; ++i) w[(int64_t)i * N] -= g[(int64_t)i * N];
     if (!ok) ifail[s] = 1;
     if (itcount) atomicAdd(itcount, its);
 }
 
-void launch_fine_newton(int64_t S, int N, int nx, int J, double dT, double alpha, double c,
-                        double f0, const double* U, const double* u0, const double* wf, double* b,
-                        double* scratch, const int* active, int* ifail,
-                        unsigned long long* itcount, cudaStream_t st) {
+// Host value of the kernels' c: the cubic coefficient (kind 1) or c/h (kind 2).
+static double kind_coef(int kind, int nx, double c) { return kind == 2 ? c * (nx + 1) : c; }
+
+void launch_fine_newton(int kind, int64_t S, int N, int nx, int J, double dT, double alpha,
+                        double c, double f0, int jump, const double* U, const double* u0,
+                        const double* wf, double* b, double* scratch, const int* active,
+                        int* ifail, unsigned long long* itcount, cudaStream_t st) {
     const int64_t n = S * N;
     if (n == 0) return;
     const int64_t NS = n * nx;
-    k_fine_newton<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
-        S, N, nx, J, dT, alpha, c, f0, U, u0, wf, b, scratch, scratch + NS, scratch + 2 * NS,
-        scratch + 3 * NS, active, ifail, itcount);
+    const double ck = kind_coef(kind, nx, c);
+    const unsigned grid = (unsigned)((n + 127) / 128);
+    if (kind == 2)
+        k_fine_newton<2><<<grid, 128, 0, st>>>(S, N, nx, J, dT, alpha, ck, f0, jump, U, u0, wf, b,
+                                               scratch, scratch + NS, scratch + 2 * NS,
+                                               scratch + 3 * NS, active, ifail, itcount);
+    else
+        k_fine_newton<1><<<grid, 128, 0, st>>>(S, N, nx, J, dT, alpha, ck, f0, jump, U, u0, wf, b,
+                                               scratch, scratch + NS, scratch + 2 * NS,
+                                               scratch + 3 * NS, active, ifail, itcount);
 }
 
 // Sequential fine solution with Newton steps (reference, snapshots, the
 // coarse guess with J = 1): one thread per sample, scratch [4][nx][S].
+template <int KIND>
 __global__ void __launch_bounds__(64) k_sequential_newton(
     int64_t S, int N, int nx, int J, double dt, double c, double f0, const double* __restrict__ u0,
     const double* __restrict__ wf, double* __restrict__ scr, double* __restrict__ U,
@@ -150,19 +194,25 @@ __global__ void __launch_bounds__(64) k_sequential_newton(
     for (int n = 0; n < N; ++n) {
         for (int j = 0; j < J && ok; ++j) {
             for (int i = 0; i < nx; ++i) v[(int64_t)i * S] = w[(int64_t)i * S];
-            ok = newton_be(nx, wfs, dt, c, f0, v, w, cp, dp, S, &its);
+            ok = newton_be<KIND>(nx, wfs, dt, c, f0, v, w, cp, dp, S, &its);
         }
         for (int i = 0; i < nx; ++i) Us[(int64_t)i * N + n] = w[(int64_t)i * S];
     }
     if (!ok && ifail) ifail[s] = 1;
 }
 
-void launch_sequential_newton(int64_t S, int N, int nx, int J, double dt, double c, double f0,
-                              const double* u0, const double* wf, double* scratch, double* U,
-                              int* ifail, cudaStream_t st) {
+void launch_sequential_newton(int kind, int64_t S, int N, int nx, int J, double dt, double c,
+                              double f0, const double* u0, const double* wf, double* scratch,
+                              double* U, int* ifail, cudaStream_t st) {
     if (S == 0) return;
-    k_sequential_newton<<<(unsigned)((S + 63) / 64), 64, 0, st>>>(S, N, nx, J, dt, c, f0, u0, wf,
-                                                                  scratch, U, ifail);
+    const double ck = kind_coef(kind, nx, c);
+    const unsigned grid = (unsigned)((S + 63) / 64);
+    if (kind == 2)
+        k_sequential_newton<2><<<grid, 64, 0, st>>>(S, N, nx, J, dt, ck, f0, u0, wf, scratch, U,
+                                                    ifail);
+    else
+        k_sequential_newton<1><<<grid, 64, 0, st>>>(S, N, nx, J, dt, ck, f0, u0, wf, scratch, U,
+                                                    ifail);
 }
 
 // Simplified Newton step, part 1: per row (s, i), e_i = c (3 m_i - 1) with
@@ -206,6 +256,188 @@ void launch_nl_prep(int64_t S, int N, int nx, double dT, double c, double f0, co
     if (n == 0) return;
     k_nl_prep<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(S, N, nx, dT, c, f0, u, b, wf, rhs, e,
                                                            active);
+}
+
+// Simplified Newton step, part 1 for kind 2: per row (s, i) the face
+// couplings lo_i, up_i (and lo_nx, up_nx from the last row) of dT K, and
+//   rhs_n,i = (dT K u_n)_i + dT f(u_n - b_n)_i + b_n,i.
+// ch = c/h.  mean_n max(z, 0) and mean_n min(z, 0) of the rows i-1, i, i+1
+// are recomputed by each row's thread (N values each).
+__global__ void k_nl_prep_burgers(int64_t S, int N, int nx, double dT, double ch, double f0,
+                                  const double* __restrict__ u, const double* __restrict__ b,
+                                  const double* __restrict__ wf, double* __restrict__ rhs,
+                                  double* __restrict__ lo, double* __restrict__ up,
+                                  const int* __restrict__ active) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t s = t / nx;
+    const int i = (int)(t - s * nx);
+    if (s >= S || !active[s]) return;
+    const int64_t row = (s * nx + i) * (int64_t)N;
+    double pos[3] = {0.0, 0.0, 0.0}, neg[3] = {0.0, 0.0, 0.0};
+    for (int d = 0; d < 3; ++d) {
+        const int j = i + d - 1;
+        if (j < 0 || j >= nx) continue;
+        const double* uj = u + row + (int64_t)(d - 1) * N;
+        const double* bj = b + row + (int64_t)(d - 1) * N;
+        double p = 0.0, m = 0.0;
+        for (int n = 0; n < N; ++n) {
+            const double z = uj[n] - bj[n];
+            p += fmax(z, 0.0);
+            m += fmin(z, 0.0);
+        }
+        pos[d] = p / N;
+        neg[d] = m / N;
+    }
+    const double* wfs = wf + s * (nx + 1);
+    const double wl = wfs[i], wr = wfs[i + 1];
+    const double lo_i = dT * (wl + ch * pos[0]), up_i = dT * (wl - ch * neg[1]);
+    const double lo_r = dT * (wr + ch * pos[1]);
+    const double up_r = i + 1 < nx ? dT * (wr - ch * neg[2]) : dT * wr;
+    lo[s * (nx + 1) + i] = lo_i;
+    up[s * (nx + 1) + i] = up_i;
+    if (i + 1 == nx) {
+        lo[s * (nx + 1) + nx] = lo_r;
+        up[s * (nx + 1) + nx] = up_r;
+    }
+    const bool hasl = i > 0, hasr = i + 1 < nx;
+    const double* ur = u + row;
+    const double* br = b + row;
+    for (int n = 0; n < N; ++n) {
+        const double ui = ur[n], zi = ui - br[n];
+        const double ul = hasl ? ur[n - N] : 0.0, uR = hasr ? ur[n + N] : 0.0;
+        const double zl = hasl ? ul - br[n - N] : 0.0, zr = hasr ? uR - br[n + N] : 0.0;
+        const double Ku = -lo_i * ul + (up_i + lo_r) * ui - up_r * uR;      // (dT K u)_i
+        const double Az = wl * (zi - zl) - wr * (zr - zi);
+        const double fz = -Az - ch * (eo_flux(zi, zr) - eo_flux(zl, zi)) + f0;
+        rhs[row + n] = Ku + dT * fz + br[n];
+    }
+}
+
+void launch_nl_prep_burgers(int64_t S, int N, int nx, double dT, double c, double f0,
+                            const double* u, const double* b, const double* wf, double* rhs,
+                            double* lo, double* up, const int* active, cudaStream_t st) {
+    const int64_t n = S * nx;
+    if (n == 0) return;
+    k_nl_prep_burgers<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(
+        S, N, nx, dT, c * (nx + 1), f0, u, b, wf, rhs, lo, up, active);
+}
+
+// Factors of lambda_k I + dT K for a tridiagonal dT K given by its face
+// couplings (row i: -lo_i, up_i + lo_{i+1}, -up_{i+1}), one thread per
+// (s, k): pivots piv_i = lambda_k + up_i + lo_{i+1} - lo_i up_i / piv_{i-1};
+// dinv_i = 1 / piv_i and lu_i = -up_{i+1} / piv_i, the layout k_cgc_solve
+// reads (with lo as its lower couplings).
+__global__ void k_cgc_factors_faces(int64_t S, int nx, const double* __restrict__ lo,
+                                    const double* __restrict__ up,
+                                    const double2* __restrict__ lam, int K,
+                                    Cplx<double>* __restrict__ dinv, Cplx<double>* __restrict__ lu,
+                                    const int* __restrict__ active) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= S * K) return;
+    const int64_t s = t / K;
+    const int k = (int)(t - s * K);
+    if (!active[s]) return;
+    const double* los = lo + s * (nx + 1);
+    const double* ups = up + s * (nx + 1);
+    const double2 lk = lam[k];
+    double pr = 1.0, pi = 0.0;
+    for (int i = 0; i < nx; ++i) {
+        double dr = lk.x + ups[i] + los[i + 1], di = lk.y;
+        if (i > 0) {
+            const double q = los[i] * ups[i] / (pr * pr + pi * pi);
+            dr -= q * pr;
+            di += q * pi;
+        }
+        pr = dr;
+        pi = di;
+        const double den = pr * pr + pi * pi;
+        const double ir = pr / den, ii = -pi / den;
+        const int64_t o = (s * nx + i) * K + k;
+        dinv[o] = Cplx<double>{ir, ii};
+        const double w = i + 1 < nx ? ups[i + 1] : 0.0;
+        lu[o] = Cplx<double>{-w * ir, -w * ii};
+    }
+}
+
+void launch_cgc_factors_faces(int64_t S, int nx, const double* lo, const double* up,
+                              const double2* lam, int K, Cplx<double>* dinv, Cplx<double>* lu,
+                              const int* active, cudaStream_t st) {
+    const int64_t n = S * K;
+    if (n == 0) return;
+    k_cgc_factors_faces<<<(unsigned)((n + 127) / 128), 128, 0, st>>>(S, nx, lo, up, lam, K, dinv,
+                                                                     lu, active);
+}
+
+// Classical parareal correction (Algorithm 1, eq. pred_correc) with Newton
+// propagators, one thread per sample, in sequence over n:
+//     U^{k+1}_n = G(U^{k+1}_{n-1}) + F_n - G(U^k_{n-1}),  U_0 = u0,
+// F = F(U^k_{n-1}) the fine end values.  delta[s] = max |U^{k+1} - U^k| (as
+// bits).  Scratch [5][nx][S]: G(U^k) iterate, G(U^{k+1}) iterate, start
+// value, Thomas c', d'.
+template <int KIND>
+__global__ void __launch_bounds__(64) k_parareal_correct_newton(
+    int64_t S, int N, int nx, double dT, double c, double f0, const double* __restrict__ u0,
+    const double* __restrict__ wf, const double* __restrict__ F, double* __restrict__ U,
+    double* __restrict__ scr, unsigned long long* __restrict__ delta,
+    const int* __restrict__ active, int* __restrict__ ifail) {
+    const int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (s >= S || !active[s]) return;
+    const int64_t plane = (int64_t)nx * S;
+    double* gold = scr + s;
+    double* vnew = gold + plane;
+    double* v = vnew + plane;
+    double* cp = v + plane;
+    double* dp = cp + plane;
+    const double* wfs = wf + s * (nx + 1);
+    const double* Fs = F + s * (int64_t)nx * N;
+    double* Us = U + s * (int64_t)nx * N;
+    unsigned long long its = 0;
+    bool ok = true;
+    for (int i = 0; i < nx; ++i) {
+        gold[(int64_t)i * S] = u0[i];
+        vnew[(int64_t)i * S] = u0[i];
+        v[(int64_t)i * S] = u0[i];
+    }
+    ok = newton_be<KIND>(nx, wfs, dT, c, f0, v, gold, cp, dp, S, &its);   // G(U^k_0)
+    double dmax = 0.0;
+    bool bad = false;
+    for (int n = 0; n < N; ++n) {
+        for (int i = 0; i < nx; ++i) v[(int64_t)i * S] = vnew[(int64_t)i * S];
+        if (ok) ok = newton_be<KIND>(nx, wfs, dT, c, f0, v, vnew, cp, dp, S, &its);
+        for (int i = 0; i < nx; ++i) {
+            const int64_t o = (int64_t)i * N + n;
+            const double uold = Us[o];
+            const double unew = vnew[(int64_t)i * S] + Fs[o] - gold[(int64_t)i * S];
+            gold[(int64_t)i * S] = uold;   // start of G(U^k_n) for the next n
+            vnew[(int64_t)i * S] = unew;
+            Us[o] = unew;
+            const double d = fabs(unew - uold);
+            dmax = fmax(dmax, d);
+            bad |= d != d;
+        }
+        if (n + 1 < N) {
+            for (int i = 0; i < nx; ++i) v[(int64_t)i * S] = gold[(int64_t)i * S];
+            if (ok) ok = newton_be<KIND>(nx, wfs, dT, c, f0, v, gold, cp, dp, S, &its);
+        }
+    }
+    if (!ok) ifail[s] = 1;
+    delta[s] = bad ? 0x7ff8000000000000ull : (unsigned long long)__double_as_longlong(dmax);
+}
+
+void launch_parareal_correct_newton(int kind, int64_t S, int N, int nx, double dT, double c,
+                                    double f0, const double* u0, const double* wf,
+                                    const double* F, double* U, double* scratch,
+                                    unsigned long long* delta, const int* active, int* ifail,
+                                    cudaStream_t st) {
+    if (S == 0) return;
+    const double ck = kind_coef(kind, nx, c);
+    const unsigned grid = (unsigned)((S + 63) / 64);
+    if (kind == 2)
+        k_parareal_correct_newton<2><<<grid, 64, 0, st>>>(S, N, nx, dT, ck, f0, u0, wf, F, U,
+                                                          scratch, delta, active, ifail);
+    else
+        k_parareal_correct_newton<1><<<grid, 64, 0, st>>>(S, N, nx, dT, ck, f0, u0, wf, F, U,
+                                                          scratch, delta, active, ifail);
 }
 
 }  // namespace klecgc

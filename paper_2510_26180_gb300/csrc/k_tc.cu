@@ -160,7 +160,9 @@ __global__ void __launch_bounds__(128, 1) k_guess_tc(int64_t S, int64_t NC, int 
     uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + 2);
     int* flags = reinterpret_cast<int*>(tslot + 1);   // [0] skip, [1] loads issued, [2] chunks committed
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int64_t m0 = (int64_t)blockIdx.y * TM, n0 = (int64_t)blockIdx.x * TN;
+    // row tiles vary fastest: the CTAs that share a W^T tile run together and
+    // read it from L2 (W^T is larger than L2 at the bench sizes)
+    const int64_t m0 = (int64_t)blockIdx.x * TM, n0 = (int64_t)blockIdx.y * TN;
     // once a CTA has timed out the launch's result is void: later CTAs skip
     // (read by one thread so that the whole CTA takes the same branch)
     if (threadIdx.x == 0) flags[0] = *reinterpret_cast<volatile int*>(err);
@@ -372,7 +374,9 @@ cudaError_t launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi_hi,
         cudaFuncSetAttribute(k_guess_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES);
         attr = true;
     }
-    dim3 grid((unsigned)((NC + TN - 1) / TN), (unsigned)((S + TM - 1) / TM));
+    const int64_t tiles_n = (NC + TN - 1) / TN;
+    if (tiles_n > 65535) return cudaErrorInvalidValue;
+    dim3 grid((unsigned)((S + TM - 1) / TM), (unsigned)tiles_n);
     k_guess_tc<<<grid, 128, SMEM_BYTES, st>>>(S, NC, Kp, mAh, mAl, mBh, mBl, ubar, U, err);
     return cudaGetLastError();
 }

@@ -1,9 +1,10 @@
-"""Nonlinear problem on the GPU (cubic reaction, simplified-Newton CGC)
-against the oracle: the Newton reference, whole solves with iteration
-counts, the coarse start, the reduction to the linear problem at c = 0, and
-the modes it rejects.  Bars as for the linear FP64 path: 1e-12 relative L2,
-or 4x the oracle's own floor (dense instead of diagonalized Jbar solves, and
-the field perturbed by 4 ulps) where that is larger."""
+"""Nonlinear problems on the GPU (cubic reaction and Burgers-type convection,
+simplified-Newton CGC) against the oracle: the Newton reference, whole
+solves with iteration counts, the coarse start, classical parareal with
+Newton propagators, the reduction to the linear problem at c = 0, and the
+modes they reject.  Bars as for the linear FP64 path: 1e-12 relative L2, or
+4x the oracle's own floor (dense instead of diagonalized Jbar solves, and the
+field perturbed by 4 ulps) where that is larger."""
 import numpy as np
 import pytest
 
@@ -15,6 +16,7 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 
 SMALL = dict(N=16, J=8)
+PROBLEMS = ["ac1d_nx127", "burgers1d_nx99"]
 
 
 def dev():
@@ -25,10 +27,11 @@ def T(x):
     return torch.from_numpy(np.ascontiguousarray(x)).to(dev())
 
 
-def test_nonlinear_reference_matches_oracle():
+@pytest.mark.parametrize("name", PROBLEMS)
+def test_nonlinear_reference_matches_oracle(name):
     from oracle import nonlinear as nl
-    solver, w = gpu_solver("ac1d_nx127", **SMALL)
-    st = oracle_setup_ac("ac1d_nx127", **SMALL)
+    solver, w = gpu_solver(name, **SMALL)
+    st = oracle_setup_ac(name, **SMALL)
     S = 4
     xi = draw_xi(S, w.M, 71)
     U = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
@@ -40,12 +43,13 @@ def test_nonlinear_reference_matches_oracle():
         assert d < max(1e-12, 4 * rel(refp, ref)), d
 
 
+@pytest.mark.parametrize("name", PROBLEMS)
 @pytest.mark.parametrize("guess", ["gpc", "coarse"])
-def test_nonlinear_solve_matches_oracle(guess):
+def test_nonlinear_solve_matches_oracle(name, guess):
     import paper_2510_26180_gb300 as pkg
     from oracle import nonlinear as nl
-    solver, w = gpu_solver("ac1d_nx127", **SMALL)
-    st = oracle_setup_ac("ac1d_nx127", **SMALL)
+    solver, w = gpu_solver(name, **SMALL)
+    st = oracle_setup_ac(name, **SMALL)
     S = 4
     xi = draw_xi(S, w.M, 72)
     U = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
@@ -64,6 +68,34 @@ def test_nonlinear_solve_matches_oracle(guess):
         floor = rel(Ud, Uo) + rel(Up, Uo)
         assert it[s] == ko, (s, it[s], ko)
         assert rel(U[s], Uo) < max(1e-12, 4 * floor), (s, rel(U[s], Uo), floor)
+        assert rel(U[s], st.reference(xi[s])) < 1e-6
+
+
+@pytest.mark.parametrize("name", PROBLEMS)
+def test_nonlinear_parareal_matches_oracle(name):
+    """Algorithm 1 with Newton F and G from the gPC guess (KLE-CGC of the
+    paper's nonlinear experiments): iteration counts equal, iterates at the
+    oracle's floor, the end point at the sequential fine solution."""
+    import paper_2510_26180_gb300 as pkg
+    from oracle import pcgc
+    solver, w = gpu_solver(name, **SMALL)
+    st = oracle_setup_ac(name, **SMALL)
+    S = 4
+    xi = draw_xi(S, w.M, 75)
+    U = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
+    it = torch.empty(S, dtype=torch.int32, device=dev())
+    code = solver.solve_parareal(T(xi), S, w.T / w.N, w.J, w.N, w.tol, w.N + 1, pkg.GUESS_GPC,
+                                 U, it)
+    assert code == 0
+    U, it = U.cpu().numpy(), it.cpu().numpy()
+    for s in range(S):
+        U0 = st.guess(xi[s])[0]
+        its = pcgc.parareal_classical(st.operator(xi[s]), st.u0, U0, w.T / w.N, w.J, w.N + 1)
+        ko = next(k for k in range(1, len(its)) if np.max(np.abs(its[k] - its[k - 1])) <= w.tol)
+        assert it[s] == ko, (s, it[s], ko)
+        itp = pcgc.parareal_classical(st.operator(xi[s], 4.0), st.u0, U0, w.T / w.N, w.J, ko)
+        floor = rel(itp[ko], its[ko])
+        assert rel(U[s], its[ko]) < max(1e-12, 4 * floor), (s, rel(U[s], its[ko]), floor)
         assert rel(U[s], st.reference(xi[s])) < 1e-6
 
 
@@ -100,7 +132,6 @@ def test_nonlinear_rejects_unsupported_modes():
         lambda: solver.solve(xi, S, w.T / w.N, w.J, w.N, w.alpha, w.tol, 5, pkg.MIXED_DEFECT,
                              pkg.GUESS_GPC, U),
         lambda: solver.fine_sweep(xi, S, w.N, U, w.T / w.N, w.J, w.alpha, 0, U),
-        lambda: solver.solve_parareal(xi, S, w.T / w.N, w.J, w.N, w.tol, 5, pkg.GUESS_ZERO, U),
         lambda: solver.reference_noalloc(xi, S, w.N, w.J, U),
     ):
         with pytest.raises(pkg.KlecgcError) as e:
