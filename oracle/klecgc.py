@@ -85,7 +85,8 @@ def _reference_worker_2d(args):
 
 
 class Setup2D(Setup1D):
-    """Same stages as Setup1D on the 2D reaction-diffusion problem (rd2d)."""
+    """Same stages as Setup1D on the 2D reaction-(advection-)diffusion problem
+    (rd2d)."""
 
     def __init__(self, w, xi_train=None, build=True, processes=1):
         from synth import draw_train
@@ -95,9 +96,12 @@ class Setup2D(Setup1D):
         self.xpts, self.ypts = rd2d.face_points(nx)
         self.bx = rd2d.field_basis_2d(w.sigma, w.corr_len, w.M, self.xpts)
         self.by = rd2d.field_basis_2d(w.sigma, w.corr_len, w.M, self.ypts)
+        x = (np.arange(nx) + 1) / (nx + 1)
         if w.u0_kind == 0:
-            x = (np.arange(nx) + 1) / (nx + 1)
             self.u0 = np.outer(np.sin(np.pi * x), np.sin(np.pi * x)).reshape(-1)
+        elif w.u0_kind == 2:
+            # sin(pi x1) sin(2 pi x2), index iy*nx + ix (rows are x2)
+            self.u0 = np.outer(np.sin(2 * np.pi * x), np.sin(np.pi * x)).reshape(-1)
         else:
             self.u0 = np.zeros(nx * nx)
         self.dT = w.T / w.N
@@ -118,7 +122,8 @@ class Setup2D(Setup1D):
             rng = np.random.default_rng(seed)
             ax = ax * (1.0 + field_ulps * 2.0 ** -53 * rng.choice([-1.0, 1.0], size=ax.shape))
             ay = ay * (1.0 + field_ulps * 2.0 ** -53 * rng.choice([-1.0, 1.0], size=ay.shape))
-        return rd2d.RD2D(ax, ay, self.w.reaction, self.w.forcing)
+        return rd2d.RD2D(ax, ay, self.w.reaction, self.w.forcing,
+                         getattr(self.w, "advection", 0.0))
 
     def references(self, xis, processes=1) -> np.ndarray:
         if processes <= 1 or len(xis) < 2:

@@ -10,6 +10,12 @@ The coefficient is sampled at the edge midpoints:
 a = exp(g), g the KL expansion of the separable exponential covariance
 sigma^2 exp(-|x1-y1|/ell) exp(-|x2-y2|/ell) (products of the 1D modes).
 
+Advection-diffusion (Section 5, advection-diffusion equation): the velocity
+b(x) = b0 (x2, x1) (the paper's b0 = 0.1), which is >= 0 on the domain, adds
+b . grad u by first-order upwind (here backward) differences,
+  + b0 x2 (u - u_W)/h + b0 x1 (u - u_S)/h   at the cell (x1, x2),
+so A is no longer symmetric.
+
 Every linear solve is a sparse direct solve (SuperLU, scipy.sparse.linalg):
 the exact backward-Euler step and the exact shifted CGC solve, which the
 GPU approximates by preconditioned Krylov iterations to a tolerance.
@@ -29,7 +35,7 @@ from . import kl_input
 
 class RD2D:
     def __init__(self, ax: np.ndarray, ay: np.ndarray, reaction: float = 0.0,
-                 forcing: float = 0.0):
+                 forcing: float = 0.0, advection: float = 0.0):
         ax = np.asarray(ax, dtype=np.float64)
         ay = np.asarray(ay, dtype=np.float64)
         self.nx = ax.shape[0]
@@ -46,6 +52,15 @@ class RD2D:
                 wW, wE = ax[iy, ix] / h2, ax[iy, ix + 1] / h2
                 wS, wN = ay[iy, ix] / h2, ay[iy + 1, ix] / h2
                 diag[k] += wW + wE + wS + wN
+                # upwind convection: b1 = b0 x2 >= 0 takes u_W, b2 = b0 x1 >= 0
+                # takes u_S; b1/h = b0 (iy + 1), b2/h = b0 (ix + 1)
+                c1 = advection * (iy + 1)
+                c2 = advection * (ix + 1)
+                diag[k] += c1 + c2
+                if ix > 0:
+                    rows.append(k); cols.append(k - 1); vals.append(-c1)
+                if iy > 0:
+                    rows.append(k); cols.append(k - nx); vals.append(-c2)
                 if ix > 0:
                     rows.append(k); cols.append(k - 1); vals.append(-wW)
                 if ix < nx - 1:
@@ -58,6 +73,7 @@ class RD2D:
         self.A = sp.csr_matrix((vals, (rows, cols)), shape=(n, n))
         self.forcing = float(forcing)
         self.reaction = float(reaction)
+        self.advection = float(advection)
         self._lu = {}
 
     @property

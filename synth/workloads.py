@@ -14,6 +14,11 @@ Workload names describe what they are:
                     alpha=1e-4, 4096 samples (FP64 and mixed precision).
 * ``rd2d_255``      2D reaction-diffusion on a 255x255 grid, N=32, J=32,
                     M=20 separable KL, degree 2, 1024 samples.
+* ``ade2d_nx19``    2D advection-diffusion u_t = div(a grad u) - b . grad u + 1,
+                    b = 0.1 (x2, x1) (upwind), u0 = sin(pi x1) sin(2 pi x2),
+                    h = 1/20, T=1, N=32, J=50, M=4 separable KL, degree 2,
+                    1024 samples (the paper's advection-diffusion set-up,
+                    Section 5, with a KL-random diffusion).
 * ``heat1d_uneven`` 8192 1D instances with Nx, N, J drawn per instance.
 * ``ac1d_nx127``    1D Allen-Cahn-type problem (cubic reaction, random
                     diffusion), Nx=127, N=32, J=16, 256 samples.
@@ -53,11 +58,14 @@ class Workload:
     train_seed: int     # seed of the training set Xi_t
     reaction: float = 0.0   # c in u_t = div(a grad u) - c u + f
     forcing: float = 0.0    # f (constant)
-    u0_kind: int = 0        # 0: sin(pi x) (1D) / product of sines (2D); 1: zero
+    u0_kind: int = 0        # 0: sin(pi x) (1D) / product of sines (2D); 1: zero;
+                            # 2 (2D): sin(pi x1) sin(2 pi x2)
     kmax: int = 60
     extra: dict = field(default_factory=dict)
-    reaction_kind: int = 0  # 0: linear c u; 1: cubic c (u^3 - u) (Allen-Cahn type)
+    reaction_kind: int = 0  # 0: linear c u; 1: cubic c (u^3 - u) (Allen-Cahn type);
+                            # 2: convection c (u^2/2)_x (Burgers type)
     cgc_newton: int = 1     # simplified Newton steps per CGC (nonlinear problems)
+    advection: float = 0.0  # b0 of the 2D velocity b = b0 (x2, x1) (upwind)
 
     def with_(self, **kw) -> "Workload":
         return replace(self, **kw)
@@ -77,6 +85,11 @@ WORKLOADS = {
         corr_len=0.3, M=20, gpc_degree=2, n_train=462, eps_kl=1e-10,
         alpha=1e-3, tol=1e-8, S=1024, seed=3, train_seed=103,
         reaction=1.0, forcing=1.0, u0_kind=1),
+    "ade2d_nx19": Workload(
+        name="ade2d_nx19", dim=2, nx=19, T=1.0, N=32, J=50, sigma=0.3,
+        corr_len=0.3, M=4, gpc_degree=2, n_train=30, eps_kl=1e-10,
+        alpha=1e-3, tol=1e-8, S=1024, seed=9, train_seed=109,
+        reaction=0.0, forcing=1.0, u0_kind=2, advection=0.1),
     "heat1d_uneven": Workload(
         name="heat1d_uneven", dim=1, nx=1023, T=1.0, N=64, J=64, sigma=0.5,
         corr_len=0.5, M=10, gpc_degree=3, n_train=572, eps_kl=1e-10,

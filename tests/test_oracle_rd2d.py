@@ -2,15 +2,16 @@
 import math
 
 import numpy as np
+import pytest
 
 from oracle import pcgc, rd2d
 
 
-def _op(nx, const=False, reaction=0.0, forcing=0.0, seed=0):
+def _op(nx, const=False, reaction=0.0, forcing=0.0, seed=0, advection=0.0):
     rng = np.random.default_rng(seed)
     ax = np.ones((nx, nx + 1)) if const else np.exp(0.4 * rng.standard_normal((nx, nx + 1)))
     ay = np.ones((nx + 1, nx)) if const else np.exp(0.4 * rng.standard_normal((nx + 1, nx)))
-    return rd2d.RD2D(ax, ay, reaction, forcing)
+    return rd2d.RD2D(ax, ay, reaction, forcing, advection)
 
 
 def test_five_point_spectrum_and_eigenvector():
@@ -46,16 +47,18 @@ def test_operator_symmetric_and_matches_stencil_definition():
     assert np.allclose(A.sum(1), 1.0 + bnd.ravel() / h2)
 
 
-def test_three_step_solve_equals_dense_kron_solve_2d():
-    op = _op(3, seed=4, reaction=1.0)
+@pytest.mark.parametrize("advection", [0.0, 3.0])
+def test_three_step_solve_equals_dense_kron_solve_2d(advection):
+    op = _op(3, seed=4, reaction=1.0, advection=advection)
     N, alpha, dT = 4, 1e-2, 0.25
     r = np.random.default_rng(1).standard_normal((N, op.n))
     assert np.allclose(pcgc.cgc_diagonalized(op, r, dT, alpha), pcgc.cgc_dense(op, r, dT, alpha),
                        rtol=1e-11, atol=1e-12)
 
 
-def test_pcgc_reaches_fine_solution_2d():
-    op = _op(5, seed=5, reaction=1.0, forcing=1.0)
+@pytest.mark.parametrize("advection", [0.0, 3.0])
+def test_pcgc_reaches_fine_solution_2d(advection):
+    op = _op(5, seed=5, reaction=1.0, forcing=1.0, advection=advection)
     N, J = 6, 3
     u0 = np.zeros(op.n)
     from oracle import heat1d
@@ -75,3 +78,40 @@ def test_face_points_and_2d_basis_products():
     lam, i, j = pairs[1]
     ref = math.sqrt(lam) * kl_input.exp_cov_phi_1d(X1x, om1[i], par1[i]) * kl_input.exp_cov_phi_1d(X2x, om1[j], par1[j])
     assert np.allclose(B[1], ref)
+
+
+def test_upwind_advection_is_exact_on_linear_functions():
+    # a = 1, b = b0 (x2, x1): the five-point Laplacian of x1 (x2) vanishes and
+    # the backward differences of a linear function are exact, so away from
+    # the boundary rows where the zero Dirichlet value differs from it,
+    # A x1 = b0 x2 and A x2 = b0 x1.
+    nx, b0 = 9, 2.5
+    op = _op(nx, const=True, advection=b0)
+    x = (np.arange(nx) + 1) * op.h
+    X1, X2 = np.meshgrid(x, x)          # [iy][ix]
+    A1 = op.apply(X1.ravel()).reshape(nx, nx)
+    assert np.allclose(A1[1:-1, :-1], (b0 * X2)[1:-1, :-1], rtol=1e-12, atol=1e-10)
+    A2 = op.apply(X2.ravel()).reshape(nx, nx)
+    assert np.allclose(A2[:-1, 1:-1], (b0 * X1)[:-1, 1:-1], rtol=1e-12, atol=1e-10)
+    # the skew part comes from the convection alone
+    A0 = _op(nx, const=True).dense()
+    assert np.allclose(A0, A0.T)
+    assert not np.allclose(op.dense(), op.dense().T)
+
+
+def test_advection_diffusion_converges_to_the_manufactured_solution():
+    # a = 1: -lap u + b . grad u = f for u = sin(pi x1) sin(2 pi x2); upwind
+    # convection is first order, so the error halves with h
+    b0, errs = 5.0, []
+    from scipy.sparse.linalg import spsolve
+    for nx in (15, 31, 63):
+        op = _op(nx, const=True, advection=b0)
+        x = (np.arange(nx) + 1) * op.h
+        X1, X2 = np.meshgrid(x, x)
+        u = np.sin(np.pi * X1) * np.sin(2 * np.pi * X2)
+        f = (5 * np.pi ** 2 * u + b0 * X2 * np.pi * np.cos(np.pi * X1) * np.sin(2 * np.pi * X2)
+             + b0 * X1 * 2 * np.pi * np.sin(np.pi * X1) * np.cos(2 * np.pi * X2))
+        errs.append(np.max(np.abs(spsolve(op.A.tocsc(), f.ravel()) - u.ravel())))
+    assert errs[0] < 0.1
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 1.7 < e1 / e2 < 2.3, errs
