@@ -63,6 +63,11 @@ def workload_desc(w, S, precision, overrides=None):
                 f"M={w.M}), Nx={w.nx}, N={w.N}, J={w.J}, Newton backward Euler, "
                 f"{w.cgc_newton} simplified Newton steps per CGC, gPC p={w.gpc_degree}, "
                 f"alpha={w.alpha}, tol={w.tol}")
+    elif w.dim == 2 and w.advection > 0:
+        name = (f"{w.name}: 2D u_t=div(a grad u)-{w.advection:g}(x2,x1).grad u-{w.reaction:g}u"
+                f"+{w.forcing:g} on (0,1)^2 (upwind convection, BiCGStab), a=exp(separable KL, "
+                f"M={w.M}), {w.nx}^2 interior points, N={w.N}, J={w.J}, gPC p={w.gpc_degree}, "
+                f"n_t={w.n_train}, alpha={w.alpha}, tol={w.tol}, Krylov rtol 1e-10")
     elif w.dim == 2:
         name = (f"{w.name}: 2D u_t=div(a grad u)-{w.reaction:g}u+{w.forcing:g} on (0,1)^2, "
                 f"a=exp(separable KL, M={w.M}), {w.nx}^2 interior points, N={w.N}, J={w.J}, "
@@ -217,20 +222,24 @@ def traffic_per_launch(cls, prec, points, launches):
     return MEASURED_TRAFFIC_B_PER_POINT[cls] * points / max(launches, 1)
 
 
-def roofline_2d(cls, ms, launches, units, prec):
+def roofline_2d(cls, ms, launches, units, prec, adv=False):
     """2D Krylov kernels: floating-point operations (an FMA counts 2) per unknown.
 
     CG iteration of F: 9 (x, r, z updates, two dot products) + 20 (stencil
     apply of z, p and q recurrences, p.q); per step 38 more (initial residual
     and the first q = M p).  COCG iteration: 34 + 58, complex.  On the mixed
     path the CG iterations are FP32 (the FP64 refinement work, ~40 flop per
-    unknown per step, is left out), so the roof is the FP32 one."""
+    unknown per step, is left out), so the roof is the FP32 one.
+    Advection-diffusion (BiCGStab, two stencil applications of 22 flop with
+    the upwind terms per iteration): 70 per iteration + 28 per step (real);
+    ~196 per iteration of the complex shifted solves."""
     ns = units["ns"]
     fp32 = prec == "mixed" and cls == "fine"
     if cls == "fine":
-        flops = (29.0 * units["kry_fine"] + 38.0 * units["fine_steps"]) * ns
+        per_it, per_step = (70.0, 28.0) if adv else (29.0, 38.0)
+        flops = (per_it * units["kry_fine"] + per_step * units["fine_steps"]) * ns
     elif cls == "cgc_solve":
-        flops = 92.0 * units["kry_cgc"] * ns
+        flops = (196.0 if adv else 92.0) * units["kry_cgc"] * ns
     else:
         return None
     peak = FP32_ALU_PEAK if fp32 else FP64_ALU_PEAK
@@ -247,7 +256,7 @@ def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
     if ms <= 0:
         return None
     if w.dim == 2:
-        return roofline_2d(cls, ms, launches, units, prec)
+        return roofline_2d(cls, ms, launches, units, prec, w.advection > 0)
     if w.reaction_kind:
         if cls != "fine":
             return None
@@ -718,9 +727,12 @@ def main():
         args.skip_fp64 = True
     if w.dim == 2:
         # 2D: FP64 Krylov solves, or MIXED (FP64 refinement around FP32 PCG for
-        # F); the defect variant is 1D only, so it maps to MIXED
+        # F); the defect variant is 1D only, so it maps to MIXED; the
+        # advection-diffusion path (BiCGStab) is FP64
         if args.precision == "mixed_defect":
             args.precision = "mixed"
+        if w.advection > 0:
+            args.precision = "fp64"
         args.skip_fp64 = True
     if w.name == "heat1d_uneven":
         if args.impl == "reference":

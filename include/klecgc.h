@@ -100,13 +100,17 @@ typedef struct {
     int32_t J;            /* fine steps per interval used for the snapshots */
     double reaction;      /* c >= 0 in div(a grad u) - c u + f0 */
     double forcing;       /* f0 (constant source) */
-    int32_t u0_kind;      /* 0: u0 = sin(pi x) (product of sines in 2D); 1: u0 = 0 */
+    int32_t u0_kind;      /* 0: u0 = sin(pi x) (product of sines in 2D); 1: u0 = 0;
+                             2 (2D): u0 = sin(pi x1) sin(2 pi x2) */
     int32_t reaction_kind; /* 0: linear reaction -c u; 1: cubic -c (u^3 - u)
                               (Allen-Cahn type); 2: convection -c (u^2/2)_x,
                               Engquist-Osher upwind (Burgers type); 1 and 2
                               are 1D and FP64 (see klecgc_solve) */
     int32_t cgc_newton;    /* simplified Newton steps per CGC for reaction_kind
                               1 and 2 (eq. Newton2); 0 means 1 */
+    double advection;      /* b0 >= 0 of the convection b . grad u, b = b0 (x2, x1)
+                              (advection-diffusion, Section 5), first-order
+                              upwind; 2D, reaction_kind 0, FP64 only; 0: none */
 } klecgc_problem;
 
 typedef struct {

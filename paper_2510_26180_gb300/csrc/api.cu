@@ -382,6 +382,14 @@ klecgc_status krylov_read(klecgc_ctx* ctx, int64_t S, const int* ifail,
     return KLECGC_OK;
 }
 
+// 2D plan kinds: BiCGStab with advection, else CG / COCG (or their mixed forms).
+int fine_kind(const klecgc_ctx* ctx, bool mixed) {
+    return ctx->prob.advection > 0 ? 4 : (mixed ? 2 : 0);
+}
+int cgc_kind(const klecgc_ctx* ctx, bool mixed) {
+    return ctx->prob.advection > 0 ? 5 : (mixed ? 3 : 1);
+}
+
 // Sequential fine solution of the 2D problem: out [S][ns][N] (internal layout).
 klecgc_status sequential_2d(klecgc_ctx* ctx, const double* xi_d, int64_t S, int N, int J,
                             double* out, cudaStream_t st, bool* capped) {
@@ -394,10 +402,11 @@ klecgc_status sequential_2d(klecgc_ctx* ctx, const double* xi_d, int64_t S, int 
     if ((s = krylov_flags(ctx, S, st, &ifail, &its)) != KLECGC_OK) return s;
     WS(int, act, "act_all", S);
     TRY(cudaMemsetAsync(act, 0xff, S * sizeof(int), st));
-    const Plan2D pl = plan_2d(0, ctx->nx, S);
+    const Plan2D pl = plan_2d(fine_kind(ctx, false), ctx->nx, S);
     WS(double, scr, "k2d_scratch", pl.scratch_doubles);
     ctx->launch(KLECGC_K_FINE, st, [&] {
-        launch_fine2d(pl, S, N, ctx->nx, J, dt * ctx->prob.reaction, dt * ctx->prob.forcing, 0.0,
+        launch_fine2d(pl, S, N, ctx->nx, J, dt * ctx->prob.reaction, dt * ctx->prob.forcing,
+                      dt * ctx->prob.advection, 0.0,
                       1, nullptr, ctx->u0, wdt, ctx->kry_rtol_fine, ctx->kry_maxit, out, act,
                       ifail, its, scr, st);
     });
@@ -480,11 +489,12 @@ klecgc_status coarse_guess_internal(klecgc_ctx* ctx, int64_t S, int N, double dT
         WS(int, act, "act_all", S);
         WS(int, gfail, "coarse_fail", S);
         TRY(cudaMemsetAsync(act, 0xff, S * sizeof(int), st));
-        const Plan2D pl = plan_2d(0, ctx->nx, S);
+        const Plan2D pl = plan_2d(fine_kind(ctx, false), ctx->nx, S);
         WS(double, scr, "k2d_scratch_g", pl.scratch_doubles);
         // a guess needs no tight solve: its error only costs iterations
         ctx->launch(KLECGC_K_GUESS, st, [&] {
-            launch_fine2d(pl, S, N, ctx->nx, 1, dT * react, dT * forcing, 0.0, 1, nullptr, ctx->u0,
+            launch_fine2d(pl, S, N, ctx->nx, 1, dT * react, dT * forcing,
+                          dT * ctx->prob.advection, 0.0, 1, nullptr, ctx->u0,
                           field, ctx->kry_rtol_fine, ctx->kry_maxit, U, act, gfail, nullptr, scr, st);
         });
     }
@@ -754,7 +764,7 @@ void klecgc_free(klecgc_ctx* ctx) {
 }  // extern "C"
 namespace {
 constexpr char kMagic[8] = {'K', 'L', 'E', 'C', 'G', 'C', 'v', '1'};
-constexpr int32_t kVersion = 2;   // 2: problem with reaction_kind, cgc_newton
+constexpr int32_t kVersion = 3;   // 3: problem with advection
 
 struct FileHead {
     char magic[8];
@@ -990,8 +1000,13 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     if (pr->nx < 1 || pr->M < 1 || pr->gpc_degree < 0 || pr->n_train < 2 || !(pr->T > 0) ||
         !(pr->sigma >= 0) || !(pr->corr_len > 0) || !(pr->eps_kl >= 0) || pr->J < 1 ||
         !(pr->reaction >= 0) || !std::isfinite(pr->forcing) || pr->u0_kind < 0 ||
-        pr->u0_kind > 1 || pr->reaction_kind < 0 || pr->reaction_kind > 2 || pr->cgc_newton < 0)
+        pr->u0_kind > 2 || pr->reaction_kind < 0 || pr->reaction_kind > 2 || pr->cgc_newton < 0 ||
+        !(pr->advection >= 0) || !std::isfinite(pr->advection))
         return fail(KLECGC_E_INVALID_ARG, "problem field out of range");
+    if ((pr->u0_kind == 2 || pr->advection > 0) && pr->dim != 2)
+        return fail(KLECGC_E_UNSUPPORTED, "u0_kind 2 and advection are 2D only");
+    if (pr->advection > 0 && pr->reaction_kind != 0)
+        return fail(KLECGC_E_UNSUPPORTED, "advection with a linear reaction only");
     if (pr->reaction_kind != 0 && pr->dim != 1)
         return fail(KLECGC_E_UNSUPPORTED, "the nonlinear problems are 1D only");
     if (!pow2_in_range(pr->N)) return fail(KLECGC_E_UNSUPPORTED, "N must be a power of 2 in [2, 64]");
@@ -1065,8 +1080,9 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
         }
         for (int iy = 0; iy < nx; ++iy)
             for (int ix = 0; ix < nx; ++ix)
-                u0[iy * nx + ix] = pr->u0_kind == 0
-                                       ? std::sin(pi * (ix + 1) * h) * std::sin(pi * (iy + 1) * h)
+                u0[iy * nx + ix] =
+                    pr->u0_kind == 0   ? std::sin(pi * (ix + 1) * h) * std::sin(pi * (iy + 1) * h)
+                    : pr->u0_kind == 2 ? std::sin(pi * (ix + 1) * h) * std::sin(2 * pi * (iy + 1) * h)
                                        : 0.0;
     }
     std::vector<int> deg = gpc_multi_indices(M, ctx->p);
@@ -1473,6 +1489,8 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
     if (ctx->dim == 2) {
         if (precision == KLECGC_MIXED_DEFECT)
             return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 or MIXED only");
+        if (ctx->prob.advection > 0 && precision != KLECGC_FP64)
+            return fail(KLECGC_E_UNSUPPORTED, "advection-diffusion: FP64 only");
         double* wdt = nullptr;
         if ((s = build_weights_2d(ctx, xi_d, S, dT / J, dT, st, &wdt, nullptr)) != KLECGC_OK) return s;
         WS(double, U, "U", S * (int64_t)nx * N);
@@ -1484,7 +1502,7 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
         unsigned long long* its = nullptr;
         if ((s = krylov_flags(ctx, S, st, &ifail, &its)) != KLECGC_OK) return s;
         const bool mixed = precision == KLECGC_MIXED;
-        const Plan2D pl = plan_2d(mixed ? 2 : 0, ctx->nx, S * N);
+        const Plan2D pl = plan_2d(fine_kind(ctx, mixed), ctx->nx, S * N);
         WS(double, scr, "k2d_scratch", pl.scratch_doubles);
         const double dt = dT / J;
         ctx->launch(KLECGC_K_FINE, st, [&] {
@@ -1495,8 +1513,9 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
                                     ifail, its, scr, st);
             else
                 launch_fine2d(pl, S, N, ctx->nx, J, dt * ctx->prob.reaction,
-                              dt * ctx->prob.forcing, alpha, 0, U, ctx->u0, wdt,
-                              ctx->kry_rtol_fine, ctx->kry_maxit, r, active, ifail, its, scr, st);
+                              dt * ctx->prob.forcing, dt * ctx->prob.advection, alpha, 0, U,
+                              ctx->u0, wdt, ctx->kry_rtol_fine, ctx->kry_maxit, r, active, ifail,
+                              its, scr, st);
         });
         TRY(cudaGetLastError());
         if ((s = export_batch(ctx, r, S, N, r_out, st)) != KLECGC_OK) return s;
@@ -1552,6 +1571,8 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
     if (ctx->dim == 2) {
         if (precision == KLECGC_MIXED_DEFECT)
             return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 or MIXED only");
+        if (ctx->prob.advection > 0 && precision != KLECGC_FP64)
+            return fail(KLECGC_E_UNSUPPORTED, "advection-diffusion: FP64 only");
         const bool mixed = precision == KLECGC_MIXED;
         double* wdT = nullptr;
         if ((s = build_weights_2d(ctx, xi_d, S, dT, dT, st, nullptr, &wdT)) != KLECGC_OK) return s;
@@ -1569,7 +1590,7 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
         double *sc, *isc;
         if ((s = scale_tables<double>(ctx, N, alpha, st, &sc, &isc)) != KLECGC_OK) return s;
         WS(Cplx<double>, p, "p64", S * (int64_t)nx * K);
-        const Plan2D pl = plan_2d(mixed ? 3 : 1, ctx->nx, S * K);
+        const Plan2D pl = plan_2d(cgc_kind(ctx, mixed), ctx->nx, S * K);
         WS(double, scr, "k2d_scratch_c", pl.scratch_doubles);
         launch_cgc_forward<double, double>(S, N, nx, r, sc, p, active, st);
         if (mixed)
@@ -1577,9 +1598,9 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
                                      ctx->kry_rtol_cgc, kInnerRtol, ctx->kry_maxit, p, active,
                                      ifail, its + 1, scr, st);
         else
-            launch_cgc_solve2d(pl, S, K, ctx->nx, dT * ctx->prob.reaction, lam_d, wdT,
-                               ctx->kry_rtol_cgc, ctx->kry_maxit, p, active, ifail, its + 1, scr,
-                               st);
+            launch_cgc_solve2d(pl, S, K, ctx->nx, dT * ctx->prob.reaction,
+                               dT * ctx->prob.advection, lam_d, wdT, ctx->kry_rtol_cgc,
+                               ctx->kry_maxit, p, active, ifail, its + 1, scr, st);
         launch_cgc_inverse<double>(S, N, nx, p, isc, U, 2, nullptr, nullptr, active, st);
         TRY(cudaGetLastError());
         if ((s = export_batch(ctx, U, S, N, u_out, st)) != KLECGC_OK) return s;
@@ -1768,8 +1789,8 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
         if ((s = krylov_flags(ctx, S, st, &ifail, &kits)) != KLECGC_OK) return s;
         std::vector<double2> lam;
         if ((s = upload_lambda(ctx, N, alpha, st, lam, &lam_d)) != KLECGC_OK) return s;
-        plF = plan_2d(precision == KLECGC_MIXED ? 2 : 0, ctx->nx, S * N);
-        plC = plan_2d(precision == KLECGC_MIXED ? 3 : 1, ctx->nx, S * K);
+        plF = plan_2d(fine_kind(ctx, precision == KLECGC_MIXED), ctx->nx, S * N);
+        plC = plan_2d(cgc_kind(ctx, precision == KLECGC_MIXED), ctx->nx, S * K);
         WS(double, a1, "k2d_scratch", plF.scratch_doubles);
         WS(double, a2, "k2d_scratch_c", plC.scratch_doubles);
         scrF = a1;
@@ -1797,9 +1818,9 @@ klecgc_status SolveRun::step() {
         else
             ctx->launch(KLECGC_K_FINE, st, [&] {
                 launch_fine2d(plF, S, N, ctx->nx, J, dt * ctx->prob.reaction,
-                              dt * ctx->prob.forcing, alpha, 0, U, ctx->u0, wdt2,
-                              ctx->kry_rtol_fine, ctx->kry_maxit, r, active, ifail, kits, scrF,
-                              st);
+                              dt * ctx->prob.forcing, dt * ctx->prob.advection, alpha, 0, U,
+                              ctx->u0, wdt2, ctx->kry_rtol_fine, ctx->kry_maxit, r, active,
+                              ifail, kits, scrF, st);
             });
         ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<double, double>(S, N, nx, r, sc64, p64, active, st); });
         ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] {
@@ -1808,8 +1829,9 @@ klecgc_status SolveRun::step() {
                                          ctx->kry_rtol_cgc, kInnerRtol, ctx->kry_maxit, p64,
                                          active, ifail, kits + 1, scrC, st);
             else
-                launch_cgc_solve2d(plC, S, K, ctx->nx, dTreact, lam_d, wdT2, ctx->kry_rtol_cgc,
-                                   ctx->kry_maxit, p64, active, ifail, kits + 1, scrC, st);
+                launch_cgc_solve2d(plC, S, K, ctx->nx, dTreact, dT * ctx->prob.advection, lam_d,
+                                   wdT2, ctx->kry_rtol_cgc, ctx->kry_maxit, p64, active, ifail,
+                                   kits + 1, scrC, st);
         });
         ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc64, U, 0, delta, nullptr, active, st); });
     } else {
@@ -2113,6 +2135,8 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
         return fail(KLECGC_E_INVALID_ARG, "no network (klecgc_mlp_set / klecgc_mlp_train)");
     if (ctx->dim == 2 && precision == KLECGC_MIXED_DEFECT)
         return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 or MIXED only");
+    if (ctx->prob.advection > 0 && precision != KLECGC_FP64)
+        return fail(KLECGC_E_UNSUPPORTED, "advection-diffusion: FP64 only");
     if (nonlinear(ctx) && (precision != KLECGC_FP64 || guess == KLECGC_GUESS_MLP))
         return fail(KLECGC_E_UNSUPPORTED, "nonlinear problems: FP64, guesses GPC/ZERO/USER/COARSE");
     klecgc_status s = check_dT(ctx, N, dT);
@@ -2279,6 +2303,8 @@ klecgc_status klecgc_solve_batch(klecgc_ctx* const* ctxs, int32_t n_ctx,
         if (x->M != M) return fail(KLECGC_E_INVALID_ARG, "every context must have the same M");
         if (x->dim == 2 && precision == KLECGC_MIXED_DEFECT)
             return fail(KLECGC_E_UNSUPPORTED, "2D: FP64 or MIXED only");
+        if (x->prob.advection > 0 && precision != KLECGC_FP64)
+            return fail(KLECGC_E_UNSUPPORTED, "advection-diffusion: FP64 only");
         if (nonlinear(x)) return fail(KLECGC_E_UNSUPPORTED, "the batch takes linear problems");
     }
     for (int64_t i = 0; i < n; ++i)

@@ -123,15 +123,17 @@ struct Plan2D {
     int64_t per_cta = 0;         // doubles of global working storage per CTA
     int64_t scratch_doubles = 0; // total global working storage
 };
-// kind 0: fine propagator, 1: shifted CGC solves, 2: mixed fine, 3: mixed CGC;
-// items = work items.
+// kind 0: fine propagator, 1: shifted CGC solves, 2: mixed fine, 3: mixed CGC,
+// 4 / 5: fine / CGC with advection (BiCGStab); items = work items.
 Plan2D plan_2d(int kind, int nx, int64_t items);
 // mode 0: r = (I + L_dT) F(start) - prev per (s, n); mode 1: sequential fine
 // solution out[s][.][n] per s.  wdt: [S][2 nx (nx+1)] weights dt a / h^2.
+// adv = dt b0 of the upwind convection (advection-diffusion, BiCGStab, plan
+// kind 4), 0 for the symmetric problem (CG, plan kind 0).
 void launch_fine2d(const Plan2D& pl, int64_t S, int N, int nx, int J, double dtc, double dtf,
-                   double alpha, int mode, const double* U, const double* u0, const double* wdt,
-                   double rtol, int maxit, double* out, const int* active, int* ifail,
-                   unsigned long long* itcount, double* scratch, cudaStream_t st);
+                   double adv, double alpha, int mode, const double* U, const double* u0,
+                   const double* wdt, double rtol, int maxit, double* out, const int* active,
+                   int* ifail, unsigned long long* itcount, double* scratch, cudaStream_t st);
 // The same with each backward-Euler step solved by FP64 iterative refinement
 // around an FP32 Jacobi-PCG (inner relative tolerance tin, plan kind 2).
 void launch_fine2d_mixed(const Plan2D& pl, int64_t S, int N, int nx, int J, double dtc,
@@ -144,8 +146,9 @@ void launch_cgc_solve2d_mixed(const Plan2D& pl, int64_t S, int K, int nx, double
                               const double2* lam, const double* wdT, double rtol, double tin,
                               int maxit, Cplx<double>* p, const int* active, int* ifail,
                               unsigned long long* itcount, double* scratch, cudaStream_t st);
-// (lambda_k I + L_dT) q = p in place, p: [S][nx*nx][K]; wdT = dT a / h^2.
-void launch_cgc_solve2d(const Plan2D& pl, int64_t S, int K, int nx, double dTc,
+// (lambda_k I + L_dT) q = p in place, p: [S][nx*nx][K]; wdT = dT a / h^2;
+// adv = dT b0 (BiCGStab, plan kind 5) or 0 (COCG, plan kind 1).
+void launch_cgc_solve2d(const Plan2D& pl, int64_t S, int K, int nx, double dTc, double adv,
                         const double2* lam, const double* wdT, double rtol, int maxit,
                         Cplx<double>* p, const int* active, int* ifail,
                         unsigned long long* itcount, double* scratch, cudaStream_t st);

@@ -18,6 +18,12 @@
 //       unconjugated bilinear form; lambda_k I + L is complex symmetric),
 //       stopped at ||r||_2 <= rtol ||p_k||_2.
 //
+// Advection-diffusion (b = b0 (x2, x1) >= 0, upwind): L gains
+//   adv (iy+1) (v_i - v_W) + adv (ix+1) (v_i - v_S),  adv = dt b0 or dT b0,
+// the operator is no longer symmetric, and both solves use Jacobi-
+// preconditioned BiCGStab (right preconditioning; Hermitian inner products
+// in the complex case) instead of CG / COCG, with the same stopping rules.
+//
 // Each CTA keeps its system's weights, diagonal and Krylov vectors in shared
 // memory when they fit (else in a global slice of its own) and loops over
 // work items.  The two dot products of an iteration are fused into two block
@@ -263,6 +269,348 @@ __global__ void __launch_bounds__(kThreads2d) k_fine2d(
                 out[(s * n + i) * N + n0] = (Fi + LF) - prev;
             }
         }
+        if (failed && threadIdx.x == 0) ifail[s] = 1;
+    }
+    if (threadIdx.x == 0 && itcount && its_total) atomicAdd(itcount, its_total);
+}
+
+// The five-point operator plus the upwind convection (advection-diffusion).
+struct StencilAdv {
+    Stencil L;
+    double adv;   // step * b0
+    __device__ __forceinline__ double apply(const double* v, int i, int ix, int iy, double c) const {
+        const double vi = v[i];
+        const double vw = ix > 0 ? v[i - 1] : 0.0;
+        const double vs = iy > 0 ? v[i - L.nx] : 0.0;
+        double acc = L.apply(v, i, ix, iy, c);
+        acc = fma(adv * (iy + 1), vi - vw, acc);
+        acc = fma(adv * (ix + 1), vi - vs, acc);
+        return acc;
+    }
+    __device__ __forceinline__ double2 apply2(const double2* v, int i, int ix, int iy,
+                                              double c) const {
+        const double2 vi = v[i];
+        const double2 z = make_double2(0.0, 0.0);
+        const double2 vw = ix > 0 ? v[i - 1] : z;
+        const double2 vs = iy > 0 ? v[i - L.nx] : z;
+        double2 acc = L.apply2(v, i, ix, iy, c);
+        const double a1 = adv * (iy + 1), a2 = adv * (ix + 1);
+        acc.x = fma(a1, vi.x - vw.x, acc.x);
+        acc.y = fma(a1, vi.y - vw.y, acc.y);
+        acc.x = fma(a2, vi.x - vs.x, acc.x);
+        acc.y = fma(a2, vi.y - vs.y, acc.y);
+        return acc;
+    }
+    __device__ __forceinline__ double diag(int ix, int iy) const {
+        return L.wsum(ix, iy) + adv * (iy + 1) + adv * (ix + 1);
+    }
+};
+
+// ------------------------------------------------------------------- F, advection
+// k_fine2d with BiCGStab for the non-symmetric backward-Euler systems
+// (I + L_dt) v' = v + dt f0, warm-started from v; modes and outputs as
+// k_fine2d.  adv = dt b0.  Working storage: weights, dinv, x, r (also s),
+// rh, p, v, y (also z), t.
+__global__ void __launch_bounds__(kThreads2d) k_fine2d_bicgs(
+    int64_t S, int N, int nx, int J, double dtc, double dtf, double adv, double alpha, int mode,
+    const double* __restrict__ U, const double* __restrict__ u0, const double* __restrict__ wdt,
+    double rtol2, int maxit, double* __restrict__ out, const int* __restrict__ active,
+    int* __restrict__ ifail, unsigned long long* __restrict__ itcount, double* __restrict__ gscr,
+    int64_t per_cta) {
+    extern __shared__ __align__(16) double dsm[];
+    __shared__ double red[2 * 3 * 32];
+    const int n = nx * nx, nf = 2 * nx * (nx + 1);
+    double* W = gscr ? gscr + blockIdx.x * per_cta : dsm;
+    double* dinv = W + nf;
+    double* x = dinv + n;
+    double* r = x + n;
+    double* rh = r + n;
+    double* p = rh + n;
+    double* v = p + n;
+    double* y = v + n;
+    double* t = y + n;
+    const StencilAdv L{{W, W + nx * (nx + 1), nx}, adv};
+    const int64_t items = mode == 0 ? S * N : S;
+    int ph = 0;
+    unsigned long long its_total = 0;
+    for (int64_t item = blockIdx.x; item < items; item += gridDim.x) {
+        const int64_t s = mode == 0 ? item / N : item;
+        const int n0 = mode == 0 ? (int)(item - s * N) : 0;
+        if (!active[s]) continue;
+        __syncthreads();  // the previous item's epilogue has read its vectors
+        cpy_weights(W, wdt + s * nf, nf);
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int iy = i / nx, ix = i - iy * nx;
+            dinv[i] = 1.0 / (1.0 + dtc + L.diag(ix, iy));
+            x[i] = (mode == 1 || n0 == 0) ? u0[i] : U[(s * n + i) * N + n0 - 1];
+        }
+        bool failed = false;
+        const int nint = mode == 0 ? 1 : N;
+        for (int ni = 0; ni < nint; ++ni) {
+            for (int j = 0; j < J; ++j) {
+                __syncthreads();  // x complete
+                // r = b - M x = dtf - L x, rh = r
+                double v2[2] = {0.0, 0.0};  // ||b||^2, ||r||^2
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const int iy = i / nx, ix = i - iy * nx;
+                    const double ri = dtf - L.apply(x, i, ix, iy, dtc);
+                    const double bi = x[i] + dtf;
+                    r[i] = ri;
+                    rh[i] = ri;
+                    p[i] = 0.0;
+                    v[i] = 0.0;
+                    v2[0] = fma(bi, bi, v2[0]);
+                    v2[1] = fma(ri, ri, v2[1]);
+                }
+                block_sum<2>(v2, red, ph);
+                const double lim = rtol2 * v2[0];
+                if (!(v2[1] > lim)) continue;  // x already solves the step
+                double rho = 1.0, al = 1.0, om = 1.0, rho_new = v2[1];
+                int it = 0;
+                for (;;) {
+                    const double beta = (rho_new / rho) * (al / om);
+                    // p = r + beta (p - om v), y = D^{-1} p
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        const double pi = fma(beta, fma(-om, v[i], p[i]), r[i]);
+                        p[i] = pi;
+                        y[i] = dinv[i] * pi;
+                    }
+                    __syncthreads();
+                    // v = M y, (rh, v)
+                    double w1[1] = {0.0};
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        const int iy = i / nx, ix = i - iy * nx;
+                        const double vi = y[i] + L.apply(y, i, ix, iy, dtc);
+                        v[i] = vi;
+                        w1[0] = fma(rh[i], vi, w1[0]);
+                    }
+                    block_sum<1>(w1, red, ph);
+                    if (!(w1[0] != 0.0)) {
+                        failed = true;
+                        break;
+                    }
+                    al = rho_new / w1[0];
+                    // x += al y, s = r - al v (in r), z = D^{-1} s (in y), ||s||^2
+                    double s1[1] = {0.0};
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        x[i] = fma(al, y[i], x[i]);
+                        const double si = fma(-al, v[i], r[i]);
+                        r[i] = si;
+                        y[i] = dinv[i] * si;
+                        s1[0] = fma(si, si, s1[0]);
+                    }
+                    block_sum<1>(s1, red, ph);
+                    ++it;
+                    if (!(s1[0] > lim)) break;
+                    // t = M z, (t, s), (t, t)
+                    double w2[2] = {0.0, 0.0};
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        const int iy = i / nx, ix = i - iy * nx;
+                        const double ti = y[i] + L.apply(y, i, ix, iy, dtc);
+                        t[i] = ti;
+                        w2[0] = fma(ti, r[i], w2[0]);
+                        w2[1] = fma(ti, ti, w2[1]);
+                    }
+                    block_sum<2>(w2, red, ph);
+                    if (!(w2[1] > 0.0)) {
+                        failed = true;
+                        break;
+                    }
+                    om = w2[0] / w2[1];
+                    // x += om z, r = s - om t, ||r||^2, (rh, r)
+                    double u2[2] = {0.0, 0.0};
+                    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                        x[i] = fma(om, y[i], x[i]);
+                        const double ri = fma(-om, t[i], r[i]);
+                        r[i] = ri;
+                        u2[0] = fma(ri, ri, u2[0]);
+                        u2[1] = fma(rh[i], ri, u2[1]);
+                    }
+                    block_sum<2>(u2, red, ph);
+                    if (!(u2[0] > lim)) break;
+                    if (it >= maxit || !(om != 0.0) || !(u2[1] != 0.0)) {
+                        failed = true;
+                        break;
+                    }
+                    rho = rho_new;
+                    rho_new = u2[1];
+                }
+                its_total += it;
+            }
+            if (mode == 1) {
+                __syncthreads();
+                for (int i = threadIdx.x; i < n; i += blockDim.x) out[(s * n + i) * N + ni] = x[i];
+            }
+        }
+        if (mode == 0) {
+            __syncthreads();  // x complete
+            const double dTc = J * dtc;
+            for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                const int iy = i / nx, ix = i - iy * nx;
+                const double Fi = x[i];
+                const double LF = J * (L.apply(x, i, ix, iy, dtc) - dtc * Fi) + dTc * Fi;
+                const double prev = n0 == 0 ? alpha * U[(s * n + i) * N + N - 1]
+                                            : U[(s * n + i) * N + n0 - 1];
+                out[(s * n + i) * N + n0] = (Fi + LF) - prev;
+            }
+        }
+        if (failed && threadIdx.x == 0) ifail[s] = 1;
+    }
+    if (threadIdx.x == 0 && itcount && its_total) atomicAdd(itcount, its_total);
+}
+
+__device__ __forceinline__ double2 cmul(double2 a, double2 b) {
+    return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+// conj(a) b
+__device__ __forceinline__ double2 cdotc(double2 a, double2 b) {
+    return make_double2(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x);
+}
+__device__ __forceinline__ double2 cdiv(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+// c + a b
+__device__ __forceinline__ double2 cfma(double2 a, double2 b, double2 c) {
+    return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+
+// ------------------------------------------------------------------- CGC (b), advection
+// (lambda_k I + L_dT) q_k = p_k by Jacobi-preconditioned complex BiCGStab
+// from zero (Hermitian inner products), in place in pio; adv = dT b0.
+// Working storage: weights, dinv, x, r (also s), rh, p, v, y (also z), t.
+__global__ void __launch_bounds__(kThreads2d) k_cgc_solve2d_bicgs(
+    int64_t S, int K, int nx, double dTc, double adv, const double2* __restrict__ lam,
+    const double* __restrict__ wdT, double rtol2, int maxit, double2* __restrict__ pio,
+    const int* __restrict__ active, int* __restrict__ ifail,
+    unsigned long long* __restrict__ itcount, double* __restrict__ gscr, int64_t per_cta) {
+    extern __shared__ __align__(16) double dsm[];
+    __shared__ double red[2 * 3 * 32];
+    const int n = nx * nx, nf = 2 * nx * (nx + 1);
+    double* W = gscr ? gscr + blockIdx.x * per_cta : dsm;
+    double2* dinv = reinterpret_cast<double2*>(W + nf + (nf & 1));
+    double2* x = dinv + n;
+    double2* r = x + n;
+    double2* rh = r + n;
+    double2* p = rh + n;
+    double2* v = p + n;
+    double2* y = v + n;
+    double2* t = y + n;
+    const StencilAdv L{{W, W + nx * (nx + 1), nx}, adv};
+    const double2 zero = make_double2(0.0, 0.0);
+    int ph = 0;
+    unsigned long long its_total = 0;
+    for (int64_t item = blockIdx.x; item < S * K; item += gridDim.x) {
+        const int64_t s = item / K;
+        const int k = (int)(item - s * K);
+        if (!active[s]) continue;
+        __syncthreads();
+        cpy_weights(W, wdT + s * nf, nf);
+        __syncthreads();
+        const double2 lk = lam[k];
+        double b2[1] = {0.0};  // ||b||^2 (= ||r||^2 = (rh, r) at x = 0)
+        for (int i = threadIdx.x; i < n; i += blockDim.x) {
+            const int iy = i / nx, ix = i - iy * nx;
+            dinv[i] = cdiv(make_double2(1.0, 0.0),
+                           make_double2(lk.x + dTc + L.diag(ix, iy), lk.y));
+            const double2 b = pio[(s * n + i) * K + k];
+            x[i] = zero;
+            r[i] = b;
+            rh[i] = b;
+            p[i] = zero;
+            v[i] = zero;
+            b2[0] = fma(b.x, b.x, fma(b.y, b.y, b2[0]));
+        }
+        block_sum<1>(b2, red, ph);
+        const double lim = rtol2 * b2[0];
+        bool failed = false;
+        int it = 0;
+        if (b2[0] > 0.0) {
+            double2 rho = make_double2(1.0, 0.0), al = rho, om = rho;
+            double2 rho_new = make_double2(b2[0], 0.0);
+            for (;;) {
+                const double2 beta = cmul(cdiv(rho_new, rho), cdiv(al, om));
+                const double2 mom = make_double2(-om.x, -om.y);
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const double2 pi = cfma(beta, cfma(mom, v[i], p[i]), r[i]);
+                    p[i] = pi;
+                    y[i] = cmul(dinv[i], pi);
+                }
+                __syncthreads();
+                double w1[2] = {0.0, 0.0};   // (rh, v)
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const int iy = i / nx, ix = i - iy * nx;
+                    const double2 yi = y[i];
+                    const double2 ly = L.apply2(y, i, ix, iy, dTc);
+                    const double2 vi = make_double2(lk.x * yi.x - lk.y * yi.y + ly.x,
+                                                    lk.x * yi.y + lk.y * yi.x + ly.y);
+                    v[i] = vi;
+                    const double2 d = cdotc(rh[i], vi);
+                    w1[0] += d.x;
+                    w1[1] += d.y;
+                }
+                block_sum<2>(w1, red, ph);
+                if (!(w1[0] != 0.0 || w1[1] != 0.0)) {
+                    failed = true;
+                    break;
+                }
+                al = cdiv(rho_new, make_double2(w1[0], w1[1]));
+                const double2 mal = make_double2(-al.x, -al.y);
+                double s1[1] = {0.0};
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    x[i] = cfma(al, y[i], x[i]);
+                    const double2 si = cfma(mal, v[i], r[i]);
+                    r[i] = si;
+                    y[i] = cmul(dinv[i], si);
+                    s1[0] = fma(si.x, si.x, fma(si.y, si.y, s1[0]));
+                }
+                block_sum<1>(s1, red, ph);
+                ++it;
+                if (!(s1[0] > lim)) break;
+                double w3[3] = {0.0, 0.0, 0.0};   // (t, s), (t, t)
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    const int iy = i / nx, ix = i - iy * nx;
+                    const double2 zi = y[i];
+                    const double2 lz = L.apply2(y, i, ix, iy, dTc);
+                    const double2 ti = make_double2(lk.x * zi.x - lk.y * zi.y + lz.x,
+                                                    lk.x * zi.y + lk.y * zi.x + lz.y);
+                    t[i] = ti;
+                    const double2 d = cdotc(ti, r[i]);
+                    w3[0] += d.x;
+                    w3[1] += d.y;
+                    w3[2] = fma(ti.x, ti.x, fma(ti.y, ti.y, w3[2]));
+                }
+                block_sum<3>(w3, red, ph);
+                if (!(w3[2] > 0.0)) {
+                    failed = true;
+                    break;
+                }
+                om = make_double2(w3[0] / w3[2], w3[1] / w3[2]);
+                const double2 mom2 = make_double2(-om.x, -om.y);
+                double u3[3] = {0.0, 0.0, 0.0};   // ||r||^2, (rh, r)
+                for (int i = threadIdx.x; i < n; i += blockDim.x) {
+                    x[i] = cfma(om, y[i], x[i]);
+                    const double2 ri = cfma(mom2, t[i], r[i]);
+                    r[i] = ri;
+                    u3[0] = fma(ri.x, ri.x, fma(ri.y, ri.y, u3[0]));
+                    const double2 d = cdotc(rh[i], ri);
+                    u3[1] += d.x;
+                    u3[2] += d.y;
+                }
+                block_sum<3>(u3, red, ph);
+                if (!(u3[0] > lim)) break;
+                if (it >= maxit || !(om.x != 0.0 || om.y != 0.0) || !(u3[1] != 0.0 || u3[2] != 0.0)) {
+                    failed = true;
+                    break;
+                }
+                rho = rho_new;
+                rho_new = make_double2(u3[1], u3[2]);
+            }
+        }
+        its_total += it;
+        __syncthreads();
+        for (int i = threadIdx.x; i < n; i += blockDim.x) pio[(s * n + i) * K + k] = x[i];
         if (failed && threadIdx.x == 0) ifail[s] = 1;
     }
     if (threadIdx.x == 0 && itcount && its_total) atomicAdd(itcount, its_total);
@@ -843,6 +1191,8 @@ int64_t per_system(int kind, int nx) {
     const int64_t n = (int64_t)nx * nx, nf = 2 * (int64_t)nx * (nx + 1);
     if (kind == 2) return 2 * n + (nf + 6 * n + 1) / 2;   // FP64 x, r; FP32 rest
     if (kind == 3) return 2 * n + (nf + (nf & 1) + 12 * n + 1) / 2;  // FP64 r; FP32 rest
+    if (kind == 4) return nf + 8 * n;                       // BiCGStab, real
+    if (kind == 5) return nf + (nf & 1) + 16 * n;           // BiCGStab, complex
     return kind == 0 ? nf + 6 * n : nf + (nf & 1) + 12 * n;
 }
 
@@ -864,6 +1214,16 @@ Plan2D plan_2d(int kind, int nx, int64_t items) {
             cudaFuncSetAttribute(k_fine2d_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  pl.smem);
             cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fine2d_mixed, kThreads2d,
+                                                          pl.smem);
+        } else if (kind == 4) {
+            cudaFuncSetAttribute(k_fine2d_bicgs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 pl.smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_fine2d_bicgs, kThreads2d,
+                                                          pl.smem);
+        } else if (kind == 5) {
+            cudaFuncSetAttribute(k_cgc_solve2d_bicgs, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 pl.smem);
+            cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cgc_solve2d_bicgs, kThreads2d,
                                                           pl.smem);
         } else if (kind == 3) {
             cudaFuncSetAttribute(k_cgc_solve2d_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -889,13 +1249,18 @@ Plan2D plan_2d(int kind, int nx, int64_t items) {
 }
 
 void launch_fine2d(const Plan2D& pl, int64_t S, int N, int nx, int J, double dtc, double dtf,
-                   double alpha, int mode, const double* U, const double* u0, const double* wdt,
-                   double rtol, int maxit, double* out, const int* active, int* ifail,
-                   unsigned long long* itcount, double* scratch, cudaStream_t st) {
+                   double adv, double alpha, int mode, const double* U, const double* u0,
+                   const double* wdt, double rtol, int maxit, double* out, const int* active,
+                   int* ifail, unsigned long long* itcount, double* scratch, cudaStream_t st) {
     if (S == 0) return;
-    k_fine2d<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
-        S, N, nx, J, dtc, dtf, alpha, mode, U, u0, wdt, rtol * rtol, maxit, out, active, ifail,
-        itcount, pl.per_cta ? scratch : nullptr, pl.per_cta);
+    if (adv != 0.0)
+        k_fine2d_bicgs<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
+            S, N, nx, J, dtc, dtf, adv, alpha, mode, U, u0, wdt, rtol * rtol, maxit, out, active,
+            ifail, itcount, pl.per_cta ? scratch : nullptr, pl.per_cta);
+    else
+        k_fine2d<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
+            S, N, nx, J, dtc, dtf, alpha, mode, U, u0, wdt, rtol * rtol, maxit, out, active,
+            ifail, itcount, pl.per_cta ? scratch : nullptr, pl.per_cta);
 }
 
 void launch_fine2d_mixed(const Plan2D& pl, int64_t S, int N, int nx, int J, double dtc,
@@ -920,14 +1285,19 @@ void launch_cgc_solve2d_mixed(const Plan2D& pl, int64_t S, int K, int nx, double
         pl.per_cta);
 }
 
-void launch_cgc_solve2d(const Plan2D& pl, int64_t S, int K, int nx, double dTc,
+void launch_cgc_solve2d(const Plan2D& pl, int64_t S, int K, int nx, double dTc, double adv,
                         const double2* lam, const double* wdT, double rtol, int maxit,
                         Cplx<double>* p, const int* active, int* ifail,
                         unsigned long long* itcount, double* scratch, cudaStream_t st) {
     if (S == 0) return;
-    k_cgc_solve2d<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
-        S, K, nx, dTc, lam, wdT, rtol * rtol, maxit, reinterpret_cast<double2*>(p), active, ifail,
-        itcount, pl.per_cta ? scratch : nullptr, pl.per_cta);
+    if (adv != 0.0)
+        k_cgc_solve2d_bicgs<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
+            S, K, nx, dTc, adv, lam, wdT, rtol * rtol, maxit, reinterpret_cast<double2*>(p),
+            active, ifail, itcount, pl.per_cta ? scratch : nullptr, pl.per_cta);
+    else
+        k_cgc_solve2d<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
+            S, K, nx, dTc, lam, wdT, rtol * rtol, maxit, reinterpret_cast<double2*>(p), active,
+            ifail, itcount, pl.per_cta ? scratch : nullptr, pl.per_cta);
 }
 
 }  // namespace klecgc

@@ -44,7 +44,8 @@ class Problem(ctypes.Structure):
                 ("n_train", ctypes.c_int32), ("eps_kl", ctypes.c_double),
                 ("N", ctypes.c_int32), ("J", ctypes.c_int32), ("reaction", ctypes.c_double),
                 ("forcing", ctypes.c_double), ("u0_kind", ctypes.c_int32),
-                ("reaction_kind", ctypes.c_int32), ("cgc_newton", ctypes.c_int32)]
+                ("reaction_kind", ctypes.c_int32), ("cgc_newton", ctypes.c_int32),
+                ("advection", ctypes.c_double)]
 
     @classmethod
     def from_workload(cls, w) -> "Problem":
@@ -52,7 +53,8 @@ class Problem(ctypes.Structure):
                    gpc_degree=w.gpc_degree, n_train=w.n_train, eps_kl=w.eps_kl, N=w.N, J=w.J,
                    reaction=w.reaction, forcing=w.forcing, u0_kind=w.u0_kind,
                    reaction_kind=getattr(w, "reaction_kind", 0),
-                   cgc_newton=getattr(w, "cgc_newton", 1))
+                   cgc_newton=getattr(w, "cgc_newton", 1),
+                   advection=getattr(w, "advection", 0.0))
 
 
 class Instance(ctypes.Structure):

@@ -1,0 +1,165 @@
+"""2D advection-diffusion on the GPU (upwind convection b = b0 (x2, x1),
+BiCGStab for the non-symmetric backward-Euler and shifted CGC systems)
+against the sparse-direct CPU oracle.
+
+Bars as for the symmetric 2D problem (Krylov rtol 1e-14): 1e-12 relative
+L2, or 4x the oracle's own sensitivity (field perturbed by 4 ulps; for the
+CGC also the direct-DFT vs FFT distance) where that is larger; for the CGC
+also eps times the condition number of the shifted systems (computed
+densely: the matrices are not normal) scaled by alpha^{-(N-1)/N}.  The
+paper's b0 = 0.1 barely breaks the symmetry, so most cases use b0 = 5
+(cell Peclet number up to 5 h / (2 a)).  nx = 19 (the paper's h = 1/20) and
+31 keep the systems in shared memory, nx = 63 runs the global-memory
+variants.
+"""
+import numpy as np
+import pytest
+
+from synth import draw_xi
+from tests.gpu_util import gpu_solver, oracle_setup2d, rel
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+RTOL = 1e-14
+NAME = "ade2d_nx19"
+SMALL = dict(N=8, J=5, advection=5.0)
+PAPER = dict(N=8, J=5)
+MID = dict(nx=31, N=8, J=4, advection=5.0)
+BIG = dict(nx=63, N=4, J=2, M=4, gpc_degree=1, n_train=10, advection=5.0)
+
+
+def dev():
+    return torch.device("cuda:0")
+
+
+def T(x):
+    return torch.from_numpy(np.ascontiguousarray(x)).to(dev())
+
+
+def solver_ade(over):
+    solver, w = gpu_solver(NAME, **over)
+    solver.set_krylov(RTOL, RTOL, 20000)
+    return solver, w
+
+
+def shifted_cond_dense(op, dT, alpha, N):
+    A = op.dense()
+    k = np.arange(N // 2 + 1)
+    lam = 1.0 - alpha ** (1.0 / N) * np.exp(-2j * np.pi * k / N)
+    return max(np.linalg.cond(l * np.eye(A.shape[0]) + dT * A) for l in lam)
+
+
+@pytest.mark.parametrize("over", [SMALL, PAPER, BIG], ids=["nx19", "nx19_b0.1", "nx63_global"])
+def test_ade_reference_matches_sparse_direct(over):
+    from oracle import heat1d
+    solver, w = solver_ade(over)
+    st = oracle_setup2d(NAME, **over)
+    S = 3
+    xi = draw_xi(S, w.M, 91)
+    U = torch.empty((S, w.N, w.nx * w.nx), dtype=torch.float64, device=dev())
+    solver.reference(T(xi), S, w.N, w.J, U)
+    assert solver.krylov_stats()[0] > 0
+    for s in range(S):
+        ref = st.reference(xi[s])
+        floor = rel(heat1d.fine_sequential(st.operator(xi[s], 4.0), st.u0, w.N, w.J, w.T), ref)
+        d = rel(U[s].cpu().numpy(), ref)
+        assert d < max(1e-12, 4 * floor), (s, d, floor)
+
+
+@pytest.mark.parametrize("over", [SMALL, BIG], ids=["nx19", "nx63_global"])
+def test_ade_fine_sweep_matches_oracle(over):
+    from oracle import pcgc
+    solver, w = solver_ade(over)
+    st = oracle_setup2d(NAME, **over)
+    S, dT = 3, w.T / w.N
+    xi = draw_xi(S, w.M, 92)
+    Uin = np.stack([st.reference(x) for x in xi]) * 1.02 + 1e-3
+    r = torch.empty_like(T(Uin))
+    solver.fine_sweep(T(xi), S, w.N, T(Uin), dT, w.J, w.alpha, 0, r)
+    for s in range(S):
+        op = st.operator(xi[s])
+        Fend = pcgc.fine_sweep(op, st.u0, Uin[s], dT, w.J)
+        ref = pcgc.cgc_rhs(op, Uin[s], pcgc.jump_b(op, Fend, Uin[s], dT, w.alpha), dT)
+        opp = st.operator(xi[s], 4.0)
+        Fp = pcgc.fine_sweep(opp, st.u0, Uin[s], dT, w.J)
+        refp = pcgc.cgc_rhs(opp, Uin[s], pcgc.jump_b(opp, Fp, Uin[s], dT, w.alpha), dT)
+        amp = 1.0 + dT * abs(op.A).sum(1).max()
+        bar = max(1e-12, 4 * rel(refp, ref), 10 * 2.3e-16 * amp)
+        assert rel(r[s].cpu().numpy(), ref) < bar
+
+
+@pytest.mark.parametrize("over,alpha", [(SMALL, 1e-3), (SMALL, 0.2), (MID, 1e-2), (BIG, 1e-3)],
+                         ids=["nx19_a1e-3", "nx19_a0.2", "nx31", "nx63_global"])
+def test_ade_cgc_apply_matches_oracle(over, alpha):
+    from oracle import pcgc
+    solver, w = solver_ade(over)
+    st = oracle_setup2d(NAME, **over)
+    S, N, dT = 3, w.N, w.T / w.N
+    n = w.nx * w.nx
+    xi = draw_xi(S, w.M, 93)
+    r = np.random.default_rng(9).standard_normal((S, N, n))
+    u = torch.empty_like(T(r))
+    solver.cgc_apply(T(xi), S, N, T(r), dT, alpha, 0, u)
+    assert solver.krylov_stats()[1] > 0
+    for s in range(S):
+        op = st.operator(xi[s])
+        ref = pcgc.cgc_diagonalized(op, r[s], dT, alpha)
+        floor = rel(pcgc.cgc_diagonalized(op, r[s], dT, alpha, fft=True), ref)
+        floor += rel(pcgc.cgc_diagonalized(st.operator(xi[s], 4.0), r[s], dT, alpha), ref)
+        kry = 4 * 2.2e-16 * shifted_cond_dense(op, dT, alpha, N) * alpha ** (-(N - 1) / N)
+        d = rel(u[s].cpu().numpy(), ref)
+        assert d < max(1e-12, 4 * floor, kry), (s, d, floor, kry)
+
+
+@pytest.mark.parametrize("over,guess", [(SMALL, "gpc"), (PAPER, "gpc"), (SMALL, "coarse"),
+                                        (MID, "gpc")],
+                         ids=["nx19_gpc", "nx19_b0.1_gpc", "nx19_coarse", "nx31_gpc"])
+def test_ade_solve_matches_oracle(over, guess):
+    import paper_2510_26180_gb300 as pkg
+    from oracle import pcgc
+    solver, w = solver_ade(over)
+    st = oracle_setup2d(NAME, **over)
+    S = 4
+    xi = draw_xi(S, w.M, 94)
+    n = w.nx * w.nx
+    U = torch.empty((S, w.N, n), dtype=torch.float64, device=dev())
+    it = torch.empty(S, dtype=torch.int32, device=dev())
+    stt = torch.empty(S, dtype=torch.int32, device=dev())
+    g = pkg.GUESS_GPC if guess == "gpc" else pkg.GUESS_COARSE
+    code = solver.solve(T(xi), S, w.T / w.N, w.J, w.N, w.alpha, w.tol, w.kmax, pkg.FP64, g, U,
+                        it, stt)
+    assert code == 0
+    U, it, stt = U.cpu().numpy(), it.cpu().numpy(), stt.cpu().numpy()
+    assert np.all(stt == 0)
+    for s in range(S):
+        U0 = None if guess == "gpc" else \
+            pcgc.coarse_guess(st.operator(xi[s]), st.u0, w.N, w.T / w.N)
+        Uo, ko, _ = st.solve_sample(xi[s], U0=U0)
+        Up, _, _ = st.solve_sample(xi[s], U0=U0, field_ulps=4.0)
+        Uf, _, _ = st.solve_sample(xi[s], U0=U0, cgc="fft")
+        floor = rel(Up, Uo) + rel(Uf, Uo)
+        assert it[s] == ko, (s, it[s], ko)
+        d = rel(U[s], Uo)
+        assert d < max(1e-12, 4 * floor), (s, d, floor)
+        assert rel(U[s], st.reference(xi[s])) < 1e-6
+
+
+def test_ade_unsupported_modes():
+    import paper_2510_26180_gb300 as pkg
+    from synth import draw_train, workload
+    solver, w = solver_ade(SMALL)
+    S = 2
+    xi = T(draw_xi(S, w.M, 95))
+    U = torch.empty((S, w.N, w.nx * w.nx), dtype=torch.float64, device=dev())
+    with pytest.raises(pkg.KlecgcError) as e:
+        solver.solve(xi, S, w.T / w.N, w.J, w.N, w.alpha, w.tol, 5, pkg.MIXED, pkg.GUESS_GPC, U)
+    assert e.value.status == pkg.E_UNSUPPORTED
+    with pytest.raises(pkg.KlecgcError) as e:
+        solver.fine_sweep(xi, S, w.N, U, w.T / w.N, w.J, w.alpha, pkg.MIXED, U)
+    assert e.value.status == pkg.E_UNSUPPORTED
+    w1 = workload("heat1d_nx63", advection=1.0)
+    with pytest.raises(pkg.KlecgcError) as e:
+        pkg.Solver(pkg.Problem.from_workload(w1), draw_train(w1))
+    assert e.value.status == pkg.E_UNSUPPORTED
