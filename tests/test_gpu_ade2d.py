@@ -141,9 +141,18 @@ def test_ade_solve_matches_oracle(over, guess):
         Uf, _, _ = st.solve_sample(xi[s], U0=U0, cgc="fft")
         floor = rel(Up, Uo) + rel(Uf, Uo)
         assert it[s] == ko, (s, it[s], ko)
+        # the last CGC's Krylov solutions carry their attainable accuracy
+        # (eps times the condition number, amplified by step (c)), as in the
+        # CGC stage test; BiCGStab's recursive residual drifts from the true
+        # one by that much
+        kry = 4 * 2.2e-16 * kry_cond(st, xi[s], w) * w.alpha ** (-(w.N - 1) / w.N)
         d = rel(U[s], Uo)
-        assert d < max(1e-12, 4 * floor), (s, d, floor)
+        assert d < max(1e-12, 4 * floor, kry), (s, d, floor, kry)
         assert rel(U[s], st.reference(xi[s])) < 1e-6
+
+
+def kry_cond(st, xi, w):
+    return shifted_cond_dense(st.operator(xi), w.T / w.N, w.alpha, w.N)
 
 
 def test_ade_unsupported_modes():
