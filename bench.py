@@ -301,6 +301,57 @@ def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
             "work": f"{byts / max(launches, 1):.3e} bytes per launch"}
 
 
+def run_offline(args, w):
+    """Offline stage at scale (Algorithm 3 steps 1-5 on the device): set-up
+    wall time, retained modes M_Q, guess error against U* and mean parareal
+    iterations for training sets of the given multiples of P."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2510_26180_gb300 as pkg
+    from synth import draw_train, draw_xi
+    from math import comb
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    P = comb(w.gpc_degree + w.M, w.M)
+    S = args.samples or 256
+    xi_h = draw_xi(S, w.M, w.seed)
+    xi = torch.from_numpy(xi_h).to(dev)
+    ns = w.nx ** w.dim
+    rows = []
+    Uref = None
+    for mult in [float(x) for x in args.offline.split(",")]:
+        wt = w.with_(n_train=max(P, int(round(mult * P))), train_seed=w.train_seed)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        solver = pkg.Solver(pkg.Problem.from_workload(wt), draw_train(wt))
+        torch.cuda.synchronize()
+        setup_s = time.perf_counter() - t0
+        info = solver.info()
+        if Uref is None:
+            Uref = torch.empty((S, w.N, ns), dtype=torch.float64, device=dev)
+            solver.reference(xi, S, w.N, w.J, Uref)
+        U0 = torch.empty_like(Uref)
+        solver.guess(xi, S, 0, U0)
+        gerr = ((U0 - Uref).flatten(1).norm(dim=1) / Uref.flatten(1).norm(dim=1)).cpu().numpy()
+        U = torch.empty_like(Uref)
+        it = torch.empty(S, dtype=torch.int32, device=dev)
+        solver.solve(xi, S, w.T / w.N, w.J, w.N, w.alpha, w.tol, w.kmax,
+                     PRECISIONS[args.precision], pkg.GUESS_GPC, U, it)
+        its = it.cpu().numpy()
+        rows.append({"n_train": wt.n_train, "setup_s": round(setup_s, 3), "MQ": info.MQ,
+                     "captured": info.lambda_kept / info.lambda_sum,
+                     "guess_rel_err_mean": float(gerr.mean()),
+                     "guess_rel_err_max": float(gerr.max()),
+                     "mean_iters": float(its.mean()), "max_iters": int(its.max())})
+        solver.close()
+    print(json.dumps({"metric": "offline stage on the device: set-up time, M_Q, guess error, "
+                                "iterations vs training-set size",
+                      "config": workload_desc(w, S, args.precision), "P": P,
+                      "samples": S, "rows": rows}))
+    return 0
+
+
 def run_gpu(args, w):
     import torch
     import torch.distributed as dist
@@ -712,6 +763,8 @@ def main():
     ap.add_argument("--samples", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--offline", default="", metavar="MULTS",
+                    help="offline-stage scan: training sets of these multiples of P, e.g. 1,2,8")
     ap.add_argument("--set", action="append", default=[], metavar="FIELD=VALUE",
                     help="override a workload field, e.g. --set nx=63 (repeatable)")
     args = ap.parse_args()
@@ -734,6 +787,8 @@ def main():
         if w.advection > 0:
             args.precision = "fp64"
         args.skip_fp64 = True
+    if args.offline:
+        return run_offline(args, w)
     if w.name == "heat1d_uneven":
         if args.impl == "reference":
             return run_batch_reference(args, w)

@@ -1128,7 +1128,9 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
             return bail(fail(KLECGC_E_NOT_CONVERGED,
                              "a snapshot's fine step reached the Krylov iteration cap"));
     }
-    // 3. mean and covariance C = Ytilde Ytilde^T / n_t
+    // 3. mean and covariance C = Ytilde Ytilde^T / n_t: the Gram matrix
+    //    Ytilde Ytilde^T on the device, its eigenpairs by parallel Jacobi on
+    //    the device (eigenvalues of C = those of the Gram matrix / n_t)
     STRY(ctx->alloc_owned(&ctx->ubar, NC));
     launch_mean_center(Y, nt, NC, ctx->ubar, st);
     double* Cd = nullptr;
@@ -1136,12 +1138,28 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     Guard gC{Cd};
     launch_gemm<double>(nt, nt, NC, Y, NC, 1, Y, 1, NC, Cd, nt, false, nullptr, st);
     STRY(cudaGetLastError());
-    std::vector<double> C((size_t)nt * nt);
-    STRY(cudaMemcpyAsync(C.data(), Cd, C.size() * 8, cudaMemcpyDeviceToHost, st));
+    constexpr int kParts = 2048;
+    double* Vtd = nullptr;
+    const size_t vt_len = ((size_t)nt * nt + 1) & ~(size_t)1;   // keeps rot 16-byte aligned
+    STRY(cudaMalloc(&Vtd, (vt_len + (nt / 2 + 1) * 2 + 2 * kParts) * 8 + 64));
+    Guard gV{Vtd};
+    double2* rot = reinterpret_cast<double2*>(Vtd + vt_len);
+    double* part = reinterpret_cast<double*>(rot + nt / 2 + 1);
+    int* infod = reinterpret_cast<int*>(part + 2 * kParts);
+    STRY(launch_jacobi_eig(nt, Cd, Vtd, rot, part, kParts, 1e-15, 60, infod, st));
+    std::vector<double> diag(nt);
+    int info = 0;
+    STRY(cudaMemcpy2DAsync(diag.data(), 8, Cd, (size_t)(nt + 1) * 8, 8, nt,
+                           cudaMemcpyDeviceToHost, st));
+    STRY(cudaMemcpyAsync(&info, infod, sizeof(int), cudaMemcpyDeviceToHost, st));
     STRY(cudaStreamSynchronize(st));
-    for (double& c : C) c /= nt;
-    std::vector<double> ev, V;
-    if (!sym_eig(nt, C, ev, V)) return bail(fail(KLECGC_E_CUDA, "eigensolver did not converge"));
+    if (info < 0) return bail(fail(KLECGC_E_CUDA, "eigensolver did not converge"));
+    std::vector<int> order(nt);
+    for (int k = 0; k < nt; ++k) order[k] = k;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int a, int b) { return diag[a] > diag[b]; });
+    std::vector<double> ev(nt);
+    for (int k = 0; k < nt; ++k) ev[k] = diag[order[k]] / nt;
     double total = 0.0;
     for (double e : ev) total += e;
     ctx->lambda_sum = total;
@@ -1157,46 +1175,50 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     }
     MQ = std::max(1, std::min(MQ, nt - 1));
     while (MQ > 1 && !(ev[MQ - 1] > 0)) --MQ;
+    if (!(ev[0] > 0)) return bail(fail(KLECGC_E_INVALID_ARG, "the training snapshots do not vary"));
     ctx->MQ = MQ;
     ctx->lambda_kept = 0.0;
     for (int k = 0; k < MQ; ++k) ctx->lambda_kept += ev[k];
     // 4. modes g_k = (lambda_k n_t)^{-1/2} sum_j e_k^j ytilde_j, and
     //    zeta_k(xi_j) = lambda_k^{-1/2} (ytilde_j, g_k) = sqrt(n_t) e_k^j
-    std::vector<double> Es((size_t)nt * MQ), Dz((size_t)nt * MQ);
-    for (int j = 0; j < nt; ++j)
-        for (int k = 0; k < MQ; ++k) {
-            double e = V[(size_t)j * nt + k];
-            Es[(size_t)j * MQ + k] = e / std::sqrt(ev[k] * nt);
-            Dz[(size_t)j * MQ + k] = std::sqrt((double)nt) * e;
-        }
+    std::vector<double> kept(2 * (size_t)MQ);
+    for (int k = 0; k < MQ; ++k) {
+        kept[k] = ev[k];
+        kept[MQ + k] = std::sqrt(ev[k]);
+    }
+    double* small = nullptr;   // [MQ] ev, [MQ] sqrt(ev), [MQ] indices
+    STRY(cudaMalloc(&small, (2 * (size_t)MQ + MQ) * 8));
+    Guard gS{small};
+    int* idxd = reinterpret_cast<int*>(small + 2 * MQ);
+    STRY(cudaMemcpyAsync(small, kept.data(), kept.size() * 8, cudaMemcpyHostToDevice, st));
+    STRY(cudaMemcpyAsync(idxd, order.data(), (size_t)MQ * sizeof(int), cudaMemcpyHostToDevice, st));
     double *Esd = nullptr, *Gd = nullptr;
-    STRY(cudaMalloc(&Esd, Es.size() * 8));
+    STRY(cudaMalloc(&Esd, 2 * (size_t)MQ * nt * 8));
     Guard gE{Esd};
+    double* Dcd = Esd + (size_t)MQ * nt;
+    launch_gather_modes(Vtd, nt, idxd, small, MQ, Esd, Dcd, st);
     STRY(cudaMalloc(&Gd, (size_t)MQ * NC * 8));
     Guard gG{Gd};
-    STRY(cudaMemcpyAsync(Esd, Es.data(), Es.size() * 8, cudaMemcpyHostToDevice, st));
-    // G[k][c] = sum_j Es[j][k] Y[j][c]
-    launch_gemm<double>(MQ, NC, nt, Esd, 1, MQ, Y, NC, 1, Gd, NC, false, nullptr, st);
-    // 5. B = psi(Xi_t), least squares H = argmin ||B H - D||
-    double* Bd = nullptr;
-    STRY(cudaMalloc(&Bd, (size_t)nt * P * 8));
-    Guard gB{Bd};
-    launch_psi<double>(xi_d, nt, M, ctx->degrees, P, Bd, P, st);
-    STRY(cudaGetLastError());
-    std::vector<double> B((size_t)nt * P);
-    STRY(cudaMemcpyAsync(B.data(), Bd, B.size() * 8, cudaMemcpyDeviceToHost, st));
-    STRY(cudaStreamSynchronize(st));
+    // G[k][c] = sum_j Es[k][j] Y[j][c]
+    launch_gemm<double>(MQ, NC, nt, Esd, nt, 1, Y, NC, 1, Gd, NC, false, nullptr, st);
+    // 5. B = psi(Xi_t), least squares H = argmin ||B H - D|| on the device
+    //    (Householder QR), H scaled by sqrt(lambda_k) per column
     if (nt < P) return bail(fail(KLECGC_E_INVALID_ARG, "n_train must be >= number of gPC terms"));
-    std::vector<double> H;
-    if (!lstsq(nt, P, MQ, B, Dz, H))
-        return bail(fail(KLECGC_E_INVALID_ARG, "gPC design matrix is rank deficient"));
+    double* Bd = nullptr;
+    STRY(cudaMalloc(&Bd, (2 * (size_t)nt * P + nt + (size_t)P * MQ) * 8 + 64));
+    Guard gB{Bd};
+    double* Bcd = Bd + (size_t)nt * P;
+    double* vd = Bcd + (size_t)nt * P;
+    double* Hd = vd + nt;
+    int* linfo = reinterpret_cast<int*>(Hd + (size_t)P * MQ);
+    launch_psi<double>(xi_d, nt, M, ctx->degrees, P, Bd, P, st);
+    launch_transpose64(Bd, nt, P, Bcd, st);
+    launch_lstsq_qr(nt, P, MQ, Bcd, Dcd, vd, small + MQ, Hd, linfo, st);
+    STRY(cudaGetLastError());
+    STRY(cudaMemcpyAsync(&info, linfo, sizeof(int), cudaMemcpyDeviceToHost, st));
+    STRY(cudaStreamSynchronize(st));
+    if (info != 0) return bail(fail(KLECGC_E_INVALID_ARG, "gPC design matrix is rank deficient"));
     // 6. W = (H diag(sqrt(lambda))) G
-    for (int j = 0; j < P; ++j)
-        for (int k = 0; k < MQ; ++k) H[(size_t)j * MQ + k] *= std::sqrt(ev[k]);
-    double* Hd = nullptr;
-    STRY(cudaMalloc(&Hd, H.size() * 8));
-    Guard gH{Hd};
-    STRY(cudaMemcpyAsync(Hd, H.data(), H.size() * 8, cudaMemcpyHostToDevice, st));
     STRY(ctx->alloc_owned(&ctx->W, (size_t)P * NC));
     STRY(ctx->alloc_owned(&ctx->W32, (size_t)P * NC));
     ctx->Kp = guess_tc_k_padded(P);

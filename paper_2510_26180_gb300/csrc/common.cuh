@@ -206,6 +206,24 @@ void launch_nl_prep(int64_t S, int N, int nx, double dT, double c, double f0, co
                     const double* b, const double* wf, double* rhs, double* e, const int* active,
                     cudaStream_t st);
 
+// ---- k_offline.cu ---- (Algorithm 3 steps 2-5 on the device)
+// Eigenpairs of the symmetric n x n A (overwritten; its diagonal ends as the
+// eigenvalues) by parallel cyclic Jacobi, eigenvectors as the rows of Vt;
+// cooperative launch; rot: (n+1)/2 double2, part: 2 nparts doubles; *info =
+// sweeps taken, or -1 when max_sweeps did not reach the off-diagonal mass
+// tol^2 times the total.
+cudaError_t launch_jacobi_eig(int n, double* A, double* Vt, double2* rot, double* part, int nparts,
+                              double tol, int max_sweeps, int* info, cudaStream_t st);
+void launch_transpose64(const double* in, int rows, int cols, double* out, cudaStream_t st);
+// Es[k][j] = Vt[idx_k][j] / sqrt(ev_k nt), Dc[k][j] = sqrt(nt) Vt[idx_k][j].
+void launch_gather_modes(const double* Vt, int nt, const int* idx, const double* ev, int MQ,
+                         double* Es, double* Dc, cudaStream_t st);
+// X = argmin ||B X - D|| (Householder QR, one CTA), Bc [n][m] and Dc [r][m]
+// column-contiguous (overwritten), X [n][r] scaled by colscale per column;
+// v: m doubles; *info = 1 when rank deficient.
+void launch_lstsq_qr(int m, int n, int r, double* Bc, double* Dc, double* v,
+                     const double* colscale, double* X, int* info, cudaStream_t st);
+
 // ---- k_cgc.cu ----
 // Step (a): p[s][i][k] = sum_j alpha^{j/N} r[s][i][j] exp(-2 pi i j k / N), k <= N/2.
 template <typename T, typename TIN>

@@ -6,11 +6,8 @@
 //    (sine modes), one root per half period; found here by bisection.
 //  - Total-degree multi-indices of the Hermite gPC basis (eq. complete),
 //    ordered by degree, then decreasing lexicographically.
-//  - Symmetric eigensolver for the snapshot covariance C (Section 2.1):
-//    Householder reduction to tridiagonal form, then implicit QL iterations
-//    with a shift from the leading 2x2 block, eigenvectors accumulated.
-//  - Least squares h = argmin ||B h - D||_2 (eq. least square problem) by
-//    Householder QR.
+// The snapshot eigenproblem and the least-squares fit run on the device
+// (k_offline.cu).
 #include "setup_host.h"
 
 #include <algorithm>
@@ -115,154 +112,6 @@ std::vector<int> gpc_multi_indices(int M, int p) {
     std::vector<int> out, cur;
     for (int d = 0; d <= p; ++d) degree_level(M, d, cur, out);
     return out;
-}
-
-// A (n x n, row-major, symmetric) -> eigenvalues ev (descending) and
-// eigenvectors as the columns of V (row-major n x n).  Returns false if the
-// QL iteration did not converge.
-bool sym_eig(int n, std::vector<double> A, std::vector<double>& ev, std::vector<double>& V) {
-    auto a = [&](int i, int j) -> double& { return A[(size_t)i * n + j]; };
-    std::vector<double> Q((size_t)n * n, 0.0);
-    for (int i = 0; i < n; ++i) Q[(size_t)i * n + i] = 1.0;
-    std::vector<double> v(n), p(n), q(n);
-    // Householder: zero column k below the sub-diagonal, A <- H A H, Q <- Q H.
-    for (int k = 0; k + 2 < n; ++k) {
-        double nrm = 0.0;
-        for (int i = k + 1; i < n; ++i) nrm += a(i, k) * a(i, k);
-        nrm = std::sqrt(nrm);
-        if (nrm == 0.0) continue;
-        double alpha = a(k + 1, k) > 0 ? -nrm : nrm;
-        double vn = 0.0;
-        for (int i = k + 1; i < n; ++i) {
-            v[i] = a(i, k) - (i == k + 1 ? alpha : 0.0);
-            vn += v[i] * v[i];
-        }
-        vn = std::sqrt(vn);
-        if (vn == 0.0) continue;
-        for (int i = k + 1; i < n; ++i) v[i] /= vn;
-        // p = A v on the trailing block (rows/cols k..n-1 touched by H on k+1..)
-        for (int i = k; i < n; ++i) {
-            double s = 0.0;
-            for (int j = k + 1; j < n; ++j) s += a(i, j) * v[j];
-            p[i] = s;
-        }
-        double K = 0.0;
-        for (int i = k + 1; i < n; ++i) K += v[i] * p[i];
-        for (int i = k + 1; i < n; ++i) q[i] = p[i] - K * v[i];
-        for (int i = k + 1; i < n; ++i)
-            for (int j = k + 1; j < n; ++j) a(i, j) -= 2.0 * (v[i] * q[j] + q[i] * v[j]);
-        a(k + 1, k) = alpha;
-        a(k, k + 1) = alpha;
-        for (int i = k + 2; i < n; ++i) a(i, k) = a(k, i) = 0.0;
-        for (int r = 0; r < n; ++r) {
-            double s = 0.0;
-            for (int j = k + 1; j < n; ++j) s += Q[(size_t)r * n + j] * v[j];
-            for (int j = k + 1; j < n; ++j) Q[(size_t)r * n + j] -= 2.0 * s * v[j];
-        }
-    }
-    std::vector<double> d(n), e(n, 0.0);
-    for (int i = 0; i < n; ++i) d[i] = a(i, i);
-    for (int i = 0; i + 1 < n; ++i) e[i] = a(i + 1, i);
-    // Implicit QL: e[i] couples i and i+1.  Each sweep chases a rotation from
-    // the bottom of the unreduced block [l, m] up to l.
-    const double eps = 2.220446049250313e-16;
-    for (int l = 0; l < n; ++l) {
-        for (int iter = 0;; ++iter) {
-            int m = l;
-            for (; m + 1 < n; ++m)
-                if (std::fabs(e[m]) <= eps * (std::fabs(d[m]) + std::fabs(d[m + 1]))) break;
-            if (m == l) break;
-            if (iter > 200) return false;
-            double g = (d[l + 1] - d[l]) / (2.0 * e[l]);
-            double r = std::hypot(g, 1.0);
-            g = d[m] - d[l] + e[l] / (g + (g >= 0 ? r : -r));
-            double s = 1.0, c = 1.0, pp = 0.0;
-            bool early = false;
-            for (int i = m - 1; i >= l; --i) {
-                double f = s * e[i], b = c * e[i];
-                r = std::hypot(f, g);
-                e[i + 1] = r;
-                if (r == 0.0) {
-                    d[i + 1] -= pp;
-                    e[m] = 0.0;
-                    early = true;
-                    break;
-                }
-                s = f / r;
-                c = g / r;
-                g = d[i + 1] - pp;
-                r = (d[i] - g) * s + 2.0 * c * b;
-                pp = s * r;
-                d[i + 1] = g + pp;
-                g = c * r - b;
-                for (int row = 0; row < n; ++row) {
-                    double* qr = &Q[(size_t)row * n];
-                    double t1 = qr[i + 1];
-                    qr[i + 1] = s * qr[i] + c * t1;
-                    qr[i] = c * qr[i] - s * t1;
-                }
-            }
-            if (early) continue;
-            d[l] -= pp;
-            e[l] = g;
-            e[m] = 0.0;
-        }
-    }
-    std::vector<int> order(n);
-    std::iota(order.begin(), order.end(), 0);
-    std::sort(order.begin(), order.end(), [&](int x, int y) { return d[x] > d[y]; });
-    ev.resize(n);
-    V.assign((size_t)n * n, 0.0);
-    for (int c = 0; c < n; ++c) {
-        ev[c] = d[order[c]];
-        for (int r = 0; r < n; ++r) V[(size_t)r * n + c] = Q[(size_t)r * n + order[c]];
-    }
-    return true;
-}
-
-// Householder QR least squares: B (m x n, row-major, m >= n), D (m x r).
-// Returns X (n x r) minimizing ||B X - D||_F column by column.
-bool lstsq(int m, int n, int r, std::vector<double> B, std::vector<double> D,
-           std::vector<double>& X) {
-    if (m < n) return false;
-    auto b = [&](int i, int j) -> double& { return B[(size_t)i * n + j]; };
-    auto dd = [&](int i, int j) -> double& { return D[(size_t)i * r + j]; };
-    std::vector<double> v(m);
-    for (int k = 0; k < n; ++k) {
-        double nrm = 0.0;
-        for (int i = k; i < m; ++i) nrm += b(i, k) * b(i, k);
-        nrm = std::sqrt(nrm);
-        if (nrm == 0.0) return false;
-        double alpha = b(k, k) > 0 ? -nrm : nrm;
-        double vn = 0.0;
-        for (int i = k; i < m; ++i) {
-            v[i] = b(i, k) - (i == k ? alpha : 0.0);
-            vn += v[i] * v[i];
-        }
-        if (vn == 0.0) continue;
-        // apply H = I - 2 v v^T / (v^T v) to the remaining columns of B and to D
-        for (int j = k; j < n; ++j) {
-            double s = 0.0;
-            for (int i = k; i < m; ++i) s += v[i] * b(i, j);
-            s *= 2.0 / vn;
-            for (int i = k; i < m; ++i) b(i, j) -= s * v[i];
-        }
-        for (int j = 0; j < r; ++j) {
-            double s = 0.0;
-            for (int i = k; i < m; ++i) s += v[i] * dd(i, j);
-            s *= 2.0 / vn;
-            for (int i = k; i < m; ++i) dd(i, j) -= s * v[i];
-        }
-    }
-    X.assign((size_t)n * r, 0.0);
-    for (int j = 0; j < r; ++j)
-        for (int i = n - 1; i >= 0; --i) {
-            double s = dd(i, j);
-            for (int t = i + 1; t < n; ++t) s -= b(i, t) * X[(size_t)t * r + j];
-            if (b(i, i) == 0.0) return false;
-            X[(size_t)i * r + j] = s / b(i, i);
-        }
-    return true;
 }
 
 }  // namespace klecgc

@@ -14,8 +14,5 @@ void kl_modes_2d(double corr_len, double sigma, int count, std::vector<double>& 
                  std::vector<double>& omega, std::vector<int>& parity);
 double kl_phi_1d(double x, double w, int parity);
 std::vector<int> gpc_multi_indices(int M, int p);
-bool sym_eig(int n, std::vector<double> A, std::vector<double>& ev, std::vector<double>& V);
-bool lstsq(int m, int n, int r, std::vector<double> B, std::vector<double> D,
-           std::vector<double>& X);
 
 }  // namespace klecgc
