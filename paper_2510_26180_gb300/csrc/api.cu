@@ -1146,7 +1146,11 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     double2* rot = reinterpret_cast<double2*>(Vtd + vt_len);
     double* part = reinterpret_cast<double*>(rot + nt / 2 + 1);
     int* infod = reinterpret_cast<int*>(part + 2 * kParts);
-    STRY(launch_jacobi_eig(nt, Cd, Vtd, rot, part, kParts, 1e-15, 60, infod, st));
+    // stop at off-diagonal mass (max(n_t,16) eps)^2 times the total: each
+    // rotation leaves rounding of order eps |a_pp| in its entry, so the mass
+    // cannot fall below about n_t eps^2 times the total
+    const double jtol = std::max(nt, 16) * 2.220446049250313e-16;
+    STRY(launch_jacobi_eig(nt, Cd, Vtd, rot, part, kParts, jtol, 100, infod, st));
     std::vector<double> diag(nt);
     int info = 0;
     STRY(cudaMemcpy2DAsync(diag.data(), 8, Cd, (size_t)(nt + 1) * 8, 8, nt,

@@ -10,8 +10,11 @@
 // Algorithm 8.5.2), accumulated into V^T <- J^T V^T.  The phases of a step
 // (angles; rows; columns) are separated by grid-wide barriers of a
 // cooperative launch.  Sweeps stop when the off-diagonal mass falls below
-// tol^2 times the total; the diagonal then holds the eigenvalues and the rows
-// of V^T the eigenvectors.
+// tol^2 times the total, or when it stalls at the rounding floor (below
+// 1e-20 times the total and reduced less than 4x by a sweep, as happens with
+// the large cluster of near-zero eigenvalues of a rank-deficient Gram
+// matrix); the diagonal then holds the eigenvalues and the rows of V^T the
+// eigenvectors.
 //
 // Least squares: Householder QR of the design matrix (one CTA, columns
 // stored contiguously), applied to the right-hand sides, then back
@@ -61,6 +64,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_eig(
     for (int64_t e = tid; e < nn; e += nth) Vt[e] = (e / n == e % n) ? 1.0 : 0.0;
     int sweep = 0;
     bool converged = false;
+    double prev = 0.0;   // off-diagonal mass after the previous sweep
     for (;;) {
         // off-diagonal and total mass (every block sums the partials in the
         // same order, so the decision is uniform across the grid)
@@ -82,10 +86,13 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_eig(
             so += part[2 * b];
             st += part[2 * b + 1];
         }
-        if (so <= tol2 * st) {
+        // converged: below tol^2, or stalled at the rounding floor (less than a
+        // 4x reduction in a sweep once the off-diagonal fraction is under 1e-20)
+        if (so <= tol2 * st || (sweep > 0 && so <= 1e-20 * st && so > 0.25 * prev)) {
             converged = true;
             break;
         }
+        prev = so;
         if (sweep == max_sweeps) break;
         ++sweep;
         for (int t = 0; t < m - 1; ++t) {
