@@ -36,8 +36,13 @@ class Setup1D:
         self.sur = None
         if build:
             snaps = self.references(xi_train, processes)
-            self.sur = build_surrogate(snaps.reshape(len(xi_train), -1), xi_train,
-                                       w.gpc_degree, w.eps_kl)
+            self.snaps = snaps.reshape(len(xi_train), -1)
+            self.sur = build_surrogate(self.snaps, xi_train, w.gpc_degree, w.eps_kl)
+
+    def surrogate_svd(self):
+        """The same surrogate with the snapshot eigenpairs from an SVD."""
+        return build_surrogate(self.snaps, self.xi_train, self.w.gpc_degree, self.w.eps_kl,
+                               eig="svd")
 
     def references(self, xis, processes=1) -> np.ndarray:
         """U*(xi) for each row of xis, [S, N, nx]; optional spawn process pool."""

@@ -48,14 +48,22 @@ class Surrogate:
 
 
 def build_surrogate(snapshots: np.ndarray, xi_train: np.ndarray, p: int,
-                    eps_kl: float) -> Surrogate:
-    """snapshots: [n_t, N*n] flattened U*(xi_j)."""
+                    eps_kl: float, eig: str = "eigh") -> Surrogate:
+    """snapshots: [n_t, N*n] flattened U*(xi_j).  eig="svd" takes the
+    eigenpairs of C from the singular value decomposition of the
+    fluctuations instead (C = Ut Ut^T / n_t = U_s (Sigma^2 / n_t) U_s^T): the
+    same quantities along another rounding path, used to measure how much
+    the guess depends on the rounding of the small retained modes."""
     Y = np.asarray(snapshots, dtype=np.float64)
     nt = Y.shape[0]
     ubar = Y.mean(axis=0)
     Ut = Y - ubar[None, :]
-    C = (Ut @ Ut.T) / nt
-    lam, E = np.linalg.eigh(C)
+    if eig == "svd":
+        E, sv, _ = np.linalg.svd(Ut, full_matrices=False)
+        lam = sv ** 2 / nt
+    else:
+        C = (Ut @ Ut.T) / nt
+        lam, E = np.linalg.eigh(C)
     order = np.argsort(lam)[::-1]
     lam, E = lam[order], E[:, order]
     total = np.sum(lam)

@@ -39,7 +39,13 @@ def test_offline_stage_matches_oracle_surrogate(n_train):
     xi = draw_xi(S, w.M, 19)
     U0 = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
     solver.guess(torch.from_numpy(xi).to(dev()), S, 0, U0)
-    assert rel(U0.cpu().numpy(), st.guess(xi)) < 1e-10
+    ref = st.guess(xi)
+    # the retained modes with the smallest eigenvalues carry eigenvector
+    # rounding of order eps ||C|| / gap: the oracle's own floor is the
+    # distance between its eigh- and SVD-based surrogates
+    floor = rel(st.surrogate_svd().guess(xi).reshape(ref.shape), ref)
+    d = rel(U0.cpu().numpy(), ref)
+    assert d < max(1e-10, 4 * floor), (d, floor)
     solver.close()
 
 
@@ -55,5 +61,8 @@ def test_offline_stage_with_a_rank_deficient_gram_matrix():
     xi = draw_xi(S, w.M, 20)
     U0 = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
     solver.guess(torch.from_numpy(xi).to(dev()), S, 0, U0)
-    assert rel(U0.cpu().numpy(), st.guess(xi)) < 1e-9
+    ref = st.guess(xi)
+    floor = rel(st.surrogate_svd().guess(xi).reshape(ref.shape), ref)
+    d = rel(U0.cpu().numpy(), ref)
+    assert d < max(1e-10, 4 * floor), (d, floor)
     solver.close()
