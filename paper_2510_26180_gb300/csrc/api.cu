@@ -1146,10 +1146,9 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     double2* rot = reinterpret_cast<double2*>(Vtd + vt_len);
     double* part = reinterpret_cast<double*>(rot + nt / 2 + 1);
     int* infod = reinterpret_cast<int*>(part + 2 * kParts);
-    // stop at off-diagonal mass (max(n_t,16) eps)^2 times the total: each
-    // rotation leaves rounding of order eps |a_pp| in its entry, so the mass
-    // cannot fall below about n_t eps^2 times the total
-    const double jtol = std::max(nt, 16) * 2.220446049250313e-16;
+    // threshold 4 eps ||C||_F: a rotation leaves rounding of about eps |a_pp|
+    // in its entry, so entries below it carry no information
+    const double jtol = 4 * 2.220446049250313e-16;
     STRY(launch_jacobi_eig(nt, Cd, Vtd, rot, part, kParts, jtol, 100, infod, st));
     std::vector<double> diag(nt);
     int info = 0;

@@ -208,10 +208,10 @@ void launch_nl_prep(int64_t S, int N, int nx, double dT, double c, double f0, co
 
 // ---- k_offline.cu ---- (Algorithm 3 steps 2-5 on the device)
 // Eigenpairs of the symmetric n x n A (overwritten; its diagonal ends as the
-// eigenvalues) by parallel cyclic Jacobi, eigenvectors as the rows of Vt;
-// cooperative launch; rot: (n+1)/2 double2, part: 2 nparts doubles; *info =
-// sweeps taken, or -1 when max_sweeps did not reach the off-diagonal mass
-// tol^2 times the total.
+// eigenvalues) by parallel cyclic threshold Jacobi, eigenvectors as the rows
+// of Vt; cooperative launch; rot: (n+1)/2 double2, part: 2 nparts doubles;
+// *info = sweeps taken, or -1 when max_sweeps left an off-diagonal entry
+// above tol ||A||_F.
 cudaError_t launch_jacobi_eig(int n, double* A, double* Vt, double2* rot, double* part, int nparts,
                               double tol, int max_sweeps, int* info, cudaStream_t st);
 void launch_transpose64(const double* in, int rows, int cols, double* out, cudaStream_t st);

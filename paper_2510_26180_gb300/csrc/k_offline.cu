@@ -9,12 +9,15 @@
 // (each chosen to annihilate its pair's off-diagonal entry, Golub-Van Loan
 // Algorithm 8.5.2), accumulated into V^T <- J^T V^T.  The phases of a step
 // (angles; rows; columns) are separated by grid-wide barriers of a
-// cooperative launch.  Sweeps stop when the off-diagonal mass falls below
-// tol^2 times the total, or when it stalls at the rounding floor (below
-// 1e-20 times the total and reduced less than 4x by a sweep, as happens with
-// the large cluster of near-zero eigenvalues of a rank-deficient Gram
-// matrix); the diagonal then holds the eigenvalues and the rows of V^T the
-// eigenvectors.
+// cooperative launch.  Threshold variant: with tau = tol ||A||_F, a pair
+// whose entry is at most tau is not rotated, and the sweeps stop when no
+// off-diagonal entry exceeds tau (the eigenvalues are then within n tau of
+// those of A).  This leaves alone the rounding-level entries of the large
+// cluster of near-zero eigenvalues of a rank-deficient Gram matrix, which a
+// test on the total off-diagonal mass would keep rotating for many sweeps.
+// A sweep that reduces the mass above tau less than 4x once it is below
+// 1e-20 ||A||_F^2 also ends the iteration (rounding floor).  The diagonal then
+// holds the eigenvalues and the rows of V^T the eigenvectors.
 //
 // Least squares: Householder QR of the design matrix (one CTA, columns
 // stored contiguously), applied to the right-hand sides, then back
@@ -62,33 +65,32 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_eig(
     const int64_t tid = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     const int64_t nth = (int64_t)gridDim.x * blockDim.x;
     for (int64_t e = tid; e < nn; e += nth) Vt[e] = (e / n == e % n) ? 1.0 : 0.0;
+    // ||A||_F^2 (every block sums the partials in the same order, so all
+    // decisions below are uniform across the grid)
+    double tot = 0.0;
+    for (int64_t e = tid; e < nn; e += nth) tot = fma(A[e], A[e], tot);
+    tot = block_sum_1(tot, red);
+    if (threadIdx.x == 0) part[2 * blockIdx.x + 1] = tot;
+    grid.sync();
+    double st = 0.0;
+    for (unsigned b = 0; b < gridDim.x; ++b) st += part[2 * b + 1];
+    const double tau2 = tol2 * st;   // tau^2
+    const double tau = sqrt(tau2);
     int sweep = 0;
     bool converged = false;
-    double prev = 0.0;   // off-diagonal mass after the previous sweep
+    double prev = 0.0;   // off-diagonal mass above tau after the previous sweep
     for (;;) {
-        // off-diagonal and total mass (every block sums the partials in the
-        // same order, so the decision is uniform across the grid)
-        double off = 0.0, tot = 0.0;
+        double off = 0.0;
         for (int64_t e = tid; e < nn; e += nth) {
             const double a = A[e];
-            tot = fma(a, a, tot);
-            if (e / n != e % n) off = fma(a, a, off);
+            if (e / n != e % n && a * a > tau2) off = fma(a, a, off);
         }
         off = block_sum_1(off, red);
-        tot = block_sum_1(tot, red);
-        if (threadIdx.x == 0) {
-            part[2 * blockIdx.x] = off;
-            part[2 * blockIdx.x + 1] = tot;
-        }
+        if (threadIdx.x == 0) part[2 * blockIdx.x] = off;
         grid.sync();
-        double so = 0.0, st = 0.0;
-        for (unsigned b = 0; b < gridDim.x; ++b) {
-            so += part[2 * b];
-            st += part[2 * b + 1];
-        }
-        // converged: below tol^2, or stalled at the rounding floor (less than a
-        // 4x reduction in a sweep once the off-diagonal fraction is under 1e-20)
-        if (so <= tol2 * st || (sweep > 0 && so <= 1e-20 * st && so > 0.25 * prev)) {
+        double so = 0.0;
+        for (unsigned b = 0; b < gridDim.x; ++b) so += part[2 * b];
+        if (so == 0.0 || (sweep > 0 && so <= 1e-20 * st && so > 0.25 * prev)) {
             converged = true;
             break;
         }
@@ -103,7 +105,7 @@ __global__ void __launch_bounds__(kJacobiThreads) k_jacobi_eig(
                 double c = 1.0, s = 0.0;
                 if (q < n) {
                     const double apq = A[(int64_t)p * n + q];
-                    if (apq != 0.0) {
+                    if (fabs(apq) > tau) {
                         const double app = A[(int64_t)p * n + p], aqq = A[(int64_t)q * n + q];
                         const double tau = (aqq - app) / (2.0 * apq);
                         const double tt = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
