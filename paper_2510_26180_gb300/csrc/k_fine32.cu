@@ -1,9 +1,24 @@
 // FP32 fine propagator, register-resident (hot-path rows a3, a4; mixed modes).
 //
-// Each backward-Euler step of F solves (I + dt(A+cI)) delta = rhs in the
-// increment form (rhs = dt f0 - dt c v - dt A v, flux form), v += delta.
-// M = I + dt(A+cI) is the same for every step, interval and iteration of a
-// sample, so its LU factors are computed once per solve (FP64, rounded):
+// Each backward-Euler step of F is taken in increment form: with
+// M = I + dt(A+cI), step m solves M delta_m = rhs_m and sets v += delta_m.
+// The first right-hand side is rhs_1 = dt f0 - dt c v - dt A v (flux form);
+// afterwards rhs_{m+1} = delta_m exactly, because M delta_m = rhs_m gives
+// dt(A+cI) delta_m = rhs_m - delta_m, so dt f0 - dt(A+cI)(v + delta_m) =
+// rhs_m - (rhs_m - delta_m) (the increments of backward Euler evolve by the
+// source-free propagator, delta_{m+1} = M^{-1} delta_m), and such a step
+// needs no operator application: a row costs its two LU recurrences, the
+// carry correction and the accumulation of v.  Taken alone, though, this
+// recurrence counts the rounding of delta_m again in every later increment
+// (about J/2 times), where recomputing the right-hand side from v lets each
+// rounding error decay like any state perturbation.  So the right-hand side
+// is recomputed in flux form from v every kFluxEvery steps (and every step
+// on the start values, in_mode 0, whose magnitude is that of the solution),
+// which bounds the recount by kFluxEvery; on the increments of in_mode 1,
+// whose size shrinks with the iteration, that keeps F0's rounding well below
+// the solve's tolerance while 7 of 8 steps skip the operator.
+// M is the same for every step, interval and iteration of a sample, so its
+// LU factors are computed once per solve (FP64, rounded):
 //     forward   y_i = rhs_i - l_i y_{i-1}
 //     backward  x_i = dinv_i y_i - u_i x_{i+1}
 // One warp owns QS systems (intervals n of one sample); lane k holds rows
@@ -19,7 +34,8 @@
 //
 // Rows are padded to 32R >= nx + 1.  Padded rows have l = u = dinv = 0 so
 // they stay 0 and act as the Dirichlet value beyond the last row; the table
-// row nx still carries the weight of the boundary face nx.
+// row nx still carries the weight of the boundary face nx (used by the
+// flux-form first right-hand side).
 //
 // Output: the FP32 end values of every interval, fout[s][i][n].  F is affine,
 // F(v + e) = F(v) + F0(e) with F0 the source-free propagator, so the caller
@@ -33,14 +49,17 @@
 
 namespace klecgc {
 
+constexpr int kFluxEvery = 8;
+
 // Per-sample factor table, four arrays of [S][R][32] entries (row i = lane*R + j
-// at index j*32 + lane):  GW = {G_j, wd_j} and L = l_j for the ascending pass,
-// FD = {F_j, dinv_j} and U = u_j for the descending pass.  wd_j = dt a_{i-1/2}/h^2.
+// at index j*32 + lane):  GL = {G_j, l_j} for the ascending pass, FD =
+// {F_j, dinv_j} and U = u_j for the descending pass, WD = wd_j = dt a_{i-1/2}/h^2
+// for the first right-hand side.
 struct Table32 {
-    float2* GW;
-    float* L;
+    float2* GL;
     float2* FD;
     float* U;
+    float* WD;
 };
 
 __global__ void k_fine_table32(const double* __restrict__ a, int64_t S, int nx, int R,
@@ -49,10 +68,10 @@ __global__ void k_fine_table32(const double* __restrict__ a, int64_t S, int nx, 
     if (s >= S) return;
     const int Rt = 32 * R;
     const double* as = a + s * (nx + 1);
-    float2* GW = tb.GW + s * (int64_t)Rt;
-    float* L = tb.L + s * (int64_t)Rt;
+    float2* GL = tb.GL + s * (int64_t)Rt;
     float2* FD = tb.FD + s * (int64_t)Rt;
     float* Uu = tb.U + s * (int64_t)Rt;
+    float* WD = tb.WD + s * (int64_t)Rt;
     // pass 1: l, dinv, u, wd by row
     double piv = 1.0;
     for (int i = 0; i < Rt; ++i) {
@@ -71,8 +90,8 @@ __global__ void k_fine_table32(const double* __restrict__ a, int64_t S, int nx, 
             dinv = 1.0 / piv;
             u = (i + 1 < nx) ? -wr * dinv : 0.0;
         }
-        GW[o] = make_float2(0.f, (float)wl);
-        L[o] = (float)l;
+        GL[o] = make_float2(0.f, (float)l);
+        WD[o] = (float)wl;
         FD[o] = make_float2(0.f, (float)dinv);
         Uu[o] = (float)u;
     }
@@ -81,13 +100,13 @@ __global__ void k_fine_table32(const double* __restrict__ a, int64_t S, int nx, 
     for (int lane = 0; lane < 32; ++lane) {
         double F = 1.0;
         for (int j = 0; j < R; ++j) {
-            F *= -(double)L[j * 32 + lane];
+            F *= -(double)GL[j * 32 + lane].y;
             FD[j * 32 + lane].x = (float)F;
         }
         double G = 1.0;
         for (int j = R - 1; j >= 0; --j) {
             G *= -(double)Uu[j * 32 + lane];
-            GW[j * 32 + lane].x = (float)G;
+            GL[j * 32 + lane].x = (float)G;
         }
     }
 }
@@ -99,10 +118,10 @@ __global__ void __launch_bounds__(128) k_fine32(
     const float* __restrict__ c32, Table32 tb, float* __restrict__ fout,
     const int* __restrict__ active) {
     extern __shared__ float2 smem2[];
-    float2* sGW = smem2;                 // [R][32] {G, wd}
+    float2* sGL = smem2;                 // [R][32] {G, l}
     float2* sFD = smem2 + R * 32;        // [R][32] {F, dinv}
-    float* sL = reinterpret_cast<float*>(smem2 + 2 * R * 32);
-    float* sU = sL + R * 32;
+    float* sU = reinterpret_cast<float*>(smem2 + 2 * R * 32);
+    float* sWD = sU + R * 32;
     const int64_t s = blockIdx.x / cps;
     const int part = blockIdx.x - (int)(s * cps);
     if (!active[s]) return;
@@ -111,10 +130,10 @@ __global__ void __launch_bounds__(128) k_fine32(
     {
         const int64_t off = s * (int64_t)(R * 32);
         for (int e = threadIdx.x; e < R * 32; e += blockDim.x) {
-            sGW[e] = tb.GW[off + e];
+            sGL[e] = tb.GL[off + e];
             sFD[e] = tb.FD[off + e];
-            sL[e] = tb.L[off + e];
             sU[e] = tb.U[off + e];
+            sWD[e] = tb.WD[off + e];
         }
     }
     __syncthreads();
@@ -125,7 +144,7 @@ __global__ void __launch_bounds__(128) k_fine32(
     float cf[5], cb[5];
     {
         float af = sFD[(R - 1) * 32 + lane].x;  // F_{R-1}: product over the lane's rows
-        float ab = sGW[lane].x;                 // G_0
+        float ab = sGL[lane].x;                 // G_0
 #pragma unroll
         for (int k = 0; k < 5; ++k) {
             const int d = 1 << k;
@@ -137,10 +156,11 @@ __global__ void __launch_bounds__(128) k_fine32(
             if (lane + d <= 31) ab *= pb;
         }
     }
-    float gprev = __shfl_up_sync(FULL, sGW[(R - 1) * 32 + lane].x, 1);   // G_{R-1} of lane-1
-    float wd_right = __shfl_down_sync(FULL, sGW[lane].y, 1);             // face right of row R-1
+    float gprev = __shfl_up_sync(FULL, sGL[(R - 1) * 32 + lane].x, 1);   // G_{R-1} of lane-1
+    float wd_right = __shfl_down_sync(FULL, sWD[lane], 1);              // face right of row R-1
     if (lane == 0) gprev = 0.f;
     if (lane == 31) wd_right = 0.f;
+    const int flux_every = in_mode == 0 ? 1 : kFluxEvery;
     const float src = in_mode == 0 ? dt_f : 0.f;
 
     float v[QS][R], w[QS][R];
@@ -171,12 +191,12 @@ __global__ void __launch_bounds__(128) k_fine32(
         float vr = __shfl_down_sync(FULL, v[q][0], 1);
         if (lane == 0) vl = 0.f;
         if (lane == 31) vr = 0.f;
-        float fprev = sGW[lane].y * (v[q][0] - vl);
+        float fprev = sWD[lane] * (v[q][0] - vl);
         float yprev = 0.f;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
-            const float lj = sL[j * 32 + lane];
-            const float wr = (j + 1 < R) ? sGW[(j + 1) * 32 + lane].y : wd_right;
+            const float lj = sGL[j * 32 + lane].y;
+            const float wr = (j + 1 < R) ? sWD[(j + 1) * 32 + lane] : wd_right;
             const float vn = (j + 1 < R) ? v[q][j + 1] : vr;
             const float f = wr * (vn - v[q][j]);
             float rhs = f - fprev;
@@ -214,7 +234,8 @@ __global__ void __launch_bounds__(128) k_fine32(
                 xn[q] = xh;
             }
         }
-        // backward carries: z = true x at this lane's first row
+        // backward carries: z = true x at this lane's first row, zin = the
+        // next lane's
         float z[QS], zin[QS];
 #pragma unroll
         for (int q = 0; q < QS; ++q) {
@@ -226,45 +247,63 @@ __global__ void __launch_bounds__(128) k_fine32(
             zin[q] = lane < 31 ? t : 0.f;
         }
         const bool more = step + 1 < J;
+        if (!more || (step + 1) % flux_every == 0) {
+            // v += delta, then the next right-hand side in flux form from v
 #pragma unroll
-        for (int q = 0; q < QS; ++q) {
-            // neighbour values after this step's update, for the next rhs
-            float pl = __shfl_up_sync(FULL, v[q][R - 1] + w[q][R - 1], 1);
-            float pr = __shfl_down_sync(FULL, v[q][0], 1);
-            const float vl = lane ? fmaf(gprev, z[q], pl) : 0.f;
-            const float vr = lane < 31 ? pr + zin[q] : 0.f;
-            float fprev = 0.f, yprev = 0.f, lprev = 0.f;
+            for (int q = 0; q < QS; ++q) {
+                // neighbour values after this step's update, for the next rhs
+                float pl = __shfl_up_sync(FULL, v[q][R - 1] + w[q][R - 1], 1);
+                float pr = __shfl_down_sync(FULL, v[q][0], 1);
+                const float vl = lane ? fmaf(gprev, z[q], pl) : 0.f;
+                const float vr = lane < 31 ? pr + zin[q] : 0.f;
+                float fprev = 0.f, yprev = 0.f, lprev = 0.f;
 #pragma unroll
-            for (int j = 0; j < R; ++j) {
-                const float2 gw = sGW[j * 32 + lane];
-                // The two rows next to a lane boundary must see bitwise-equal
-                // values there, or the flux through that face differs between
-                // them and the flux form stops being conservative.  The
-                // boundary rows are therefore updated by exactly the formulas
-                // the neighbouring lanes used for vl / vr above.
-                if (j == 0)
-                    v[q][0] = v[q][0] + z[q];
-                else if (j == R - 1)
-                    v[q][R - 1] = fmaf(gw.x, zin[q], v[q][R - 1] + w[q][R - 1]);
-                else
-                    v[q][j] += fmaf(gw.x, zin[q], w[q][j]);
-                if (more) {
-                    const float f = gw.y * (v[q][j] - (j ? v[q][j - 1] : vl));
-                    if (j) {
-                        float rhs = f - fprev;
-                        if (REACT) rhs += src - dt_react * v[q][j - 1];
-                        yprev = fmaf(-lprev, yprev, rhs);
-                        w[q][j - 1] = yprev;
+                for (int j = 0; j < R; ++j) {
+                    const float2 gl = sGL[j * 32 + lane];
+                    // The two rows next to a lane boundary must see bitwise-equal
+                    // values there, or the flux through that face differs between
+                    // them and the flux form stops being conservative.  The
+                    // boundary rows are therefore updated by exactly the formulas
+                    // the neighbouring lanes used for vl / vr above.
+                    if (j == 0)
+                        v[q][0] = v[q][0] + z[q];
+                    else if (j == R - 1)
+                        v[q][R - 1] = fmaf(gl.x, zin[q], v[q][R - 1] + w[q][R - 1]);
+                    else
+                        v[q][j] += fmaf(gl.x, zin[q], w[q][j]);
+                    if (more) {
+                        const float f = sWD[j * 32 + lane] * (v[q][j] - (j ? v[q][j - 1] : vl));
+                        if (j) {
+                            float rhs = f - fprev;
+                            if (REACT) rhs += src - dt_react * v[q][j - 1];
+                            yprev = fmaf(-lprev, yprev, rhs);
+                            w[q][j - 1] = yprev;
+                        }
+                        fprev = f;
+                        lprev = gl.y;
                     }
-                    fprev = f;
-                    lprev = sL[j * 32 + lane];
+                }
+                if (more) {
+                    const float f = wd_right * (vr - v[q][R - 1]);
+                    float rhs = f - fprev;
+                    if (REACT) rhs += src - dt_react * v[q][R - 1];
+                    w[q][R - 1] = fmaf(-lprev, yprev, rhs);
                 }
             }
-            if (more) {
-                const float f = wd_right * (vr - v[q][R - 1]);
-                float rhs = f - fprev;
-                if (REACT) rhs += src - dt_react * v[q][R - 1];
-                w[q][R - 1] = fmaf(-lprev, yprev, rhs);
+        } else {
+            // delta_j = xhat_j + G_j zin, v += delta, and the next step's
+            // local forward sweep on the right-hand side delta
+#pragma unroll
+            for (int q = 0; q < QS; ++q) {
+                float yprev = 0.f;
+#pragma unroll
+                for (int j = 0; j < R; ++j) {
+                    const float2 gl = sGL[j * 32 + lane];
+                    const float d = fmaf(gl.x, zin[q], w[q][j]);
+                    v[q][j] += d;
+                    yprev = fmaf(-gl.y, yprev, d);
+                    w[q][j] = yprev;
+                }
             }
         }
     }
@@ -299,8 +338,8 @@ void launch_fine_table32(const double* a, int64_t S, int nx, int R, double h, do
     if (S == 0) return;
     const int64_t n = S * (int64_t)R * 32;
     char* p = static_cast<char*>(table);
-    Table32 tb{reinterpret_cast<float2*>(p), reinterpret_cast<float*>(p + 16 * n),
-               reinterpret_cast<float2*>(p + 8 * n), reinterpret_cast<float*>(p + 20 * n)};
+    Table32 tb{reinterpret_cast<float2*>(p), reinterpret_cast<float2*>(p + 8 * n),
+               reinterpret_cast<float*>(p + 16 * n), reinterpret_cast<float*>(p + 20 * n)};
     k_fine_table32<<<(unsigned)((S + 63) / 64), 64, 0, st>>>(a, S, nx, R, 1.0 / (h * h), dt, react,
                                                              tb);
 }
@@ -316,8 +355,8 @@ static void launch_r(int64_t S, int N, int nx, int J, double dt, double react, d
     const size_t smem = (size_t)R * 32 * 24;
     const int64_t n = S * (int64_t)R * 32;
     char* p = const_cast<char*>(static_cast<const char*>(table));
-    Table32 tb{reinterpret_cast<float2*>(p), reinterpret_cast<float*>(p + 16 * n),
-               reinterpret_cast<float2*>(p + 8 * n), reinterpret_cast<float*>(p + 20 * n)};
+    Table32 tb{reinterpret_cast<float2*>(p), reinterpret_cast<float2*>(p + 8 * n),
+               reinterpret_cast<float*>(p + 16 * n), reinterpret_cast<float*>(p + 20 * n)};
     static bool attr = false;
     if (!attr && smem > 48 * 1024) {
         cudaFuncSetAttribute(k_fine32<R, QS, REACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
