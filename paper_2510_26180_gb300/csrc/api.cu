@@ -78,6 +78,7 @@ struct klecgc_ctx {
     double* u0 = nullptr;      // [ns]
     int* degrees = nullptr;    // [P][M]
     double* ubar = nullptr;    // [ns*N]  internal order c = i*N + n
+    float2* ubar_df = nullptr; // the same as FP32 pairs (hi, lo) (guess in pair format)
     double* W = nullptr;       // [P][ns*N]
     float* W32 = nullptr;      // FP32 copy of W
     float* W32t = nullptr;     // [ns*N][Kp] TF32 head of W^T, zero-padded (tensor-core guess)
@@ -516,7 +517,7 @@ klecgc_status check_tc(klecgc_ctx* ctx, cudaStream_t st) {
 
 // U^0 = ubar + psi(xi) W into U (internal layout [S][nx][N]).
 klecgc_status gpc_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S, bool fp64,
-                                 double* U, cudaStream_t st) {
+                                 double* U, cudaStream_t st, bool pairs = false) {
     const int64_t NC = (int64_t)ctx->ns * ctx->N;
     if (fp64) {
         WS(double, psi, "psi64", S * ctx->P);
@@ -530,8 +531,8 @@ klecgc_status gpc_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S,
         ctx->launch(KLECGC_K_GUESS, st, [&] { launch_split_tf32(psi, S * ctx->Kp, psi, psi_lo, st); });
         cudaError_t e = cudaSuccess;
         ctx->launch(KLECGC_K_GUESS, st, [&] {
-            e = launch_guess_tc(S, NC, ctx->Kp, psi, psi_lo, ctx->W32t, ctx->W32t_lo, ctx->ubar, U,
-                                ctx->tc_err, st);
+            e = launch_guess_tc(S, NC, ctx->Kp, psi, psi_lo, ctx->W32t, ctx->W32t_lo, ctx->ubar,
+                                pairs ? ctx->ubar_df : nullptr, U, ctx->tc_err, st);
         });
         TRY(e);
     }
@@ -907,6 +908,10 @@ klecgc_status klecgc_load(const char* path, klecgc_ctx** out, void* stream) {
     launch_to_float(ctx->W, ctx->W32, (int64_t)ctx->P * NC, st);
     launch_pad_transpose(ctx->W32, ctx->P, NC, ctx->Kp, ctx->W32t, st);
     launch_split_tf32(ctx->W32t, (int64_t)ctx->Kp * NC, ctx->W32t, ctx->W32t_lo, st);
+    if (ctx->alloc_owned(&ctx->ubar_df, NC) != cudaSuccess)
+        return bail(fail(KLECGC_E_OUT_OF_MEMORY, "ubar pairs"));
+    cudaMemcpyAsync(ctx->ubar_df, ctx->ubar, NC * sizeof(double), cudaMemcpyDeviceToDevice, st);
+    launch_to_pairs(reinterpret_cast<double*>(ctx->ubar_df), (int64_t)NC, st);
     if (hd.mlp_ready) {
         if ((s = mlp_alloc(ctx)) != KLECGC_OK) return bail(s);
         MlpState& q = ctx->mlp;
@@ -1233,6 +1238,9 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
     launch_to_float(ctx->W, ctx->W32, (int64_t)P * NC, st);
     launch_pad_transpose(ctx->W32, P, NC, ctx->Kp, ctx->W32t, st);
     launch_split_tf32(ctx->W32t, (int64_t)ctx->Kp * NC, ctx->W32t, ctx->W32t_lo, st);
+    STRY(ctx->alloc_owned(&ctx->ubar_df, NC));
+    STRY(cudaMemcpyAsync(ctx->ubar_df, ctx->ubar, NC * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    launch_to_pairs(reinterpret_cast<double*>(ctx->ubar_df), (int64_t)NC, st);
     STRY(cudaGetLastError());
     STRY(cudaStreamSynchronize(st));
     // release the training-sized scratch
@@ -1746,9 +1754,13 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
     if (guess == KLECGC_GUESS_MLP) {
         if ((s = mlp_guess_internal(ctx, xi_d, S, U, st, &mlp_ok)) != KLECGC_OK) return s;
     }
+    // the defect path keeps U as FP32 pairs; the tensor-core guess writes them
+    // directly (1D)
+    const bool guess_pairs = defect && ctx->dim == 1 && guess == KLECGC_GUESS_GPC;
     if (guess == KLECGC_GUESS_GPC || (guess == KLECGC_GUESS_MLP && !mlp_ok)) {
         // the surrogate is also the fallback of the learned guess (non-finite output)
-        if ((s = gpc_guess_internal(ctx, xi_d, S, f64, U, st)) != KLECGC_OK) return s;
+        if ((s = gpc_guess_internal(ctx, xi_d, S, f64, U, st, guess_pairs)) != KLECGC_OK)
+            return s;
     } else if (guess == KLECGC_GUESS_MLP) {
     } else if (guess == KLECGC_GUESS_ZERO) {
         TRY(cudaMemsetAsync(U, 0, NS * sizeof(double), st));
@@ -1800,7 +1812,8 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
             WS(float2, fb, "FaccB2", NS);
             Facc2[0] = fa;
             Facc2[1] = fb;
-            ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_to_pairs(U, NS, st); });
+            if (!guess_pairs)
+                ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_to_pairs(U, NS, st); });
             Udf = reinterpret_cast<float2*>(U);
         } else {
             WS(double, fa, "FaccA", NS);

@@ -168,11 +168,14 @@ void launch_pad_transpose(const float* W, int P, int64_t NC, int Kp, float* Wt, 
 void launch_split_tf32(const float* x, int64_t n, float* hi, float* lo, cudaStream_t st);
 // U[s][c] = ubar[c] + sum_j psi[s][j] Wt[c][j] with psi and Wt split into TF32
 // head and tail ([S][Kp], [NC][Kp], zero-padded, 16-byte aligned; NC even),
-// loaded by TMA; *err = 1 if a pipeline wait ran out of its budget.
-// Returns an error if the tensor maps cannot be encoded.
+// loaded by TMA; *err = 1 if a pipeline wait ran out of its budget.  With
+// ubar_df (ubar as FP32 pairs) non-null, each U value is stored as the FP32
+// pair (hi, lo) in its 8 bytes.  Returns an error if the tensor maps cannot
+// be encoded.
 cudaError_t launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi_hi,
                             const float* psi_lo, const float* Wt_hi, const float* Wt_lo,
-                            const double* ubar, double* U, int* err, cudaStream_t st);
+                            const double* ubar, const float2* ubar_df, double* U, int* err,
+                            cudaStream_t st);
 
 // ---- k_nonlinear.cu ---- (kind 1 cubic reaction, kind 2 Burgers-type
 // convection; simplified-Newton CGC; wf = a / h^2; c the problem's coefficient)

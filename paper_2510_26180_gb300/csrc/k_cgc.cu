@@ -583,9 +583,14 @@ __global__ void __launch_bounds__(kTX) k_cgc_inverse_df(int64_t S, int nx,
                                                          float* __restrict__ c32,
                                                          const int* __restrict__ active) {
     constexpr int L = N / 2, K = N / 2 + 1;
-    __shared__ Cplx<float> sq[kTX * K];
+    // The row of q a thread transforms and the row of increments it writes
+    // share storage (2K >= N + 1 floats per row): each thread reads its whole
+    // q row before it writes its increments, and touches no other row between
+    // the barriers; this keeps shared memory at 25 KB per CTA (9 CTAs per SM).
+    __shared__ __align__(16) float sqc[kTX * 2 * K];
     __shared__ float2 su[kTX][N + 1];
-    __shared__ float sc[kTX][N + 1];
+    Cplx<float>* sq = reinterpret_cast<Cplx<float>*>(sqc);   // [kTX][K]
+    auto sc = [&](int row, int c) -> float& { return sqc[row * 2 * K + c]; };
     const int64_t s = blockIdx.x;
     if (!active[s]) return;
     const int x0 = blockIdx.y * kTX;
@@ -632,8 +637,8 @@ __global__ void __launch_bounds__(kTX) k_cgc_inverse_df(int64_t S, int nx,
             bad |= (u0 != u0) || (u1 != u1);
             su[tid][2 * m] = df_add(su[tid][2 * m], u0);
             su[tid][2 * m + 1] = df_add(su[tid][2 * m + 1], u1);
-            sc[tid][2 * m] = u0;
-            sc[tid][2 * m + 1] = u1;
+            sc(tid, 2 * m) = u0;
+            sc(tid, 2 * m + 1) = u1;
         }
     }
     __syncthreads();
@@ -644,7 +649,7 @@ __global__ void __launch_bounds__(kTX) k_cgc_inverse_df(int64_t S, int nx,
             const int row = e / G, c = (e - row * G) * 2;
             const float2 a = su[row][c], b = su[row][c + 1];
             *reinterpret_cast<float4*>(Ut + (int64_t)row * N + c) = make_float4(a.x, a.y, b.x, b.y);
-            *reinterpret_cast<float2*>(ct + (int64_t)row * N + c) = make_float2(sc[row][c], sc[row][c + 1]);
+            *reinterpret_cast<float2*>(ct + (int64_t)row * N + c) = make_float2(sc(row, c), sc(row, c + 1));
         }
     }
     // a NaN increment must reach the stopping rule (fmaxf drops NaNs)

@@ -62,25 +62,79 @@ struct Table32 {
     float* WD;
 };
 
-__global__ void k_fine_table32(const double* __restrict__ a, int64_t S, int nx, int R,
-                               double inv_h2, double dt, double react, Table32 tb) {
-    int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (s >= S) return;
+// One warp per sample; lane k owns rows [kR, kR + R).  The pivots of the LU
+// factorization of M, piv_i = m_i - wl_i^2 / piv_{i-1} with m_i = 1 + wl_i +
+// wr_i + dt c, form a continued fraction: (p_i, q_i) = (m_i p_{i-1} -
+// wl_i^2 q_{i-1}, p_{i-1}) and piv_i = p_i / q_i.  Each lane multiplies the
+// 2 x 2 maps of its rows (rescaled by powers of two, which is exact), an
+// exclusive warp scan of these products gives every lane the pivot entering
+// its first row, and each lane then runs the recurrence over its own rows
+// in FP64 and writes their entries (consecutive lanes write consecutive
+// words).  Padded rows (i >= nx) get l = u = dinv = 0.
+__device__ __forceinline__ void mat2_rescale(double& a, double& b, double& c, double& d) {
+    const double mx = fmax(fmax(fabs(a), fabs(b)), fmax(fabs(c), fabs(d)));
+    if (mx > 0.0 && (mx > 0x1p+64 || mx < 0x1p-64)) {
+        const int e = ilogb(mx);
+        a = scalbn(a, -e);
+        b = scalbn(b, -e);
+        c = scalbn(c, -e);
+        d = scalbn(d, -e);
+    }
+}
+
+__global__ void __launch_bounds__(128) k_fine_table32(const double* __restrict__ a, int64_t S,
+                                                      int nx, int R, double inv_h2, double dt,
+                                                      double react, Table32 tb) {
+    const int64_t s = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5;
+    const int lane = threadIdx.x & 31;
+    if (s >= S) return;   // whole warps
+    constexpr unsigned FULL = 0xffffffffu;
     const int Rt = 32 * R;
     const double* as = a + s * (nx + 1);
     float2* GL = tb.GL + s * (int64_t)Rt;
     float2* FD = tb.FD + s * (int64_t)Rt;
     float* Uu = tb.U + s * (int64_t)Rt;
     float* WD = tb.WD + s * (int64_t)Rt;
-    // pass 1: l, dinv, u, wd by row
-    double piv = 1.0;
-    for (int i = 0; i < Rt; ++i) {
-        const int lane = i / R, j = i - lane * R;
+    const int i0 = lane * R;
+    // product of this lane's maps, later rows on the left: T = M_{i0+R-1} ... M_{i0}
+    double t00 = 1.0, t01 = 0.0, t10 = 0.0, t11 = 1.0;
+    for (int j = 0; j < R; ++j) {
+        const int i = i0 + j;
+        if (i >= nx) break;
+        const double wl = dt * as[i] * inv_h2, wr = dt * as[i + 1] * inv_h2;
+        const double m = 1.0 + wl + wr + dt * react;
+        const double c = i > 0 ? -wl * wl : 0.0;
+        const double n00 = m * t00 + c * t10, n01 = m * t01 + c * t11;
+        t10 = t00;
+        t11 = t01;
+        t00 = n00;
+        t01 = n01;
+        mat2_rescale(t00, t01, t10, t11);
+    }
+    // inclusive scan over lanes: X_k <- X_k X_{k-d}
+    for (int d = 1; d < 32; d <<= 1) {
+        const double b00 = __shfl_up_sync(FULL, t00, d), b01 = __shfl_up_sync(FULL, t01, d);
+        const double b10 = __shfl_up_sync(FULL, t10, d), b11 = __shfl_up_sync(FULL, t11, d);
+        if (lane >= d) {
+            const double n00 = t00 * b00 + t01 * b10, n01 = t00 * b01 + t01 * b11;
+            const double n10 = t10 * b00 + t11 * b10, n11 = t10 * b01 + t11 * b11;
+            t00 = n00;
+            t01 = n01;
+            t10 = n10;
+            t11 = n11;
+            mat2_rescale(t00, t01, t10, t11);
+        }
+    }
+    // exclusive prefix applied to (1, 0): the pivot before row i0 is p / q
+    const double p = __shfl_up_sync(FULL, t00, 1), q = __shfl_up_sync(FULL, t10, 1);
+    double piv = lane > 0 && q != 0.0 ? p / q : 1.0;
+    for (int j = 0; j < R; ++j) {
+        const int i = i0 + j;
         const int o = j * 32 + lane;
-        double wl = i <= nx ? dt * as[i] * inv_h2 : 0.0;
+        const double wl = i <= nx ? dt * as[i] * inv_h2 : 0.0;
         double l = 0.0, dinv = 0.0, u = 0.0;
         if (i < nx) {
-            double wr = dt * as[i + 1] * inv_h2;
+            const double wr = dt * as[i + 1] * inv_h2;
             double m = 1.0 + wl + wr + dt * react;
             if (i > 0) {
                 l = -wl / piv;
@@ -95,19 +149,17 @@ __global__ void k_fine_table32(const double* __restrict__ a, int64_t S, int nx, 
         FD[o] = make_float2(0.f, (float)dinv);
         Uu[o] = (float)u;
     }
-    // pass 2: within-lane products of the FP32-rounded multipliers (they must
-    // match the local sweeps): F forward, G backward, formed in FP64
-    for (int lane = 0; lane < 32; ++lane) {
-        double F = 1.0;
-        for (int j = 0; j < R; ++j) {
-            F *= -(double)GL[j * 32 + lane].y;
-            FD[j * 32 + lane].x = (float)F;
-        }
-        double G = 1.0;
-        for (int j = R - 1; j >= 0; --j) {
-            G *= -(double)Uu[j * 32 + lane];
-            GL[j * 32 + lane].x = (float)G;
-        }
+    // within-lane products of the FP32-rounded multipliers (they must match
+    // the local sweeps): F forward, G backward, formed in FP64
+    double F = 1.0;
+    for (int j = 0; j < R; ++j) {
+        F *= -(double)GL[j * 32 + lane].y;
+        FD[j * 32 + lane].x = (float)F;
+    }
+    double G = 1.0;
+    for (int j = R - 1; j >= 0; --j) {
+        G *= -(double)Uu[j * 32 + lane];
+        GL[j * 32 + lane].x = (float)G;
     }
 }
 
@@ -340,8 +392,8 @@ void launch_fine_table32(const double* a, int64_t S, int nx, int R, double h, do
     char* p = static_cast<char*>(table);
     Table32 tb{reinterpret_cast<float2*>(p), reinterpret_cast<float2*>(p + 8 * n),
                reinterpret_cast<float*>(p + 16 * n), reinterpret_cast<float*>(p + 20 * n)};
-    k_fine_table32<<<(unsigned)((S + 63) / 64), 64, 0, st>>>(a, S, nx, R, 1.0 / (h * h), dt, react,
-                                                             tb);
+    k_fine_table32<<<(unsigned)((S * 32 + 127) / 128), 128, 0, st>>>(a, S, nx, R, 1.0 / (h * h), dt,
+                                                                      react, tb);
 }
 
 template <int R, int QS, bool REACT>

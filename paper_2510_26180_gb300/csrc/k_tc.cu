@@ -151,7 +151,9 @@ __global__ void __launch_bounds__(128, 1) k_guess_tc(int64_t S, int64_t NC, int 
                                                     const __grid_constant__ CUtensorMap mBh,
                                                     const __grid_constant__ CUtensorMap mBl,
                                                     const double* __restrict__ ubar,
-                                                    double* __restrict__ U, int* __restrict__ err) {
+                                                    const float2* __restrict__ ubar_df,
+                                                    double* __restrict__ U,
+                                                    int* __restrict__ err) {
     extern __shared__ __align__(1024) char smem_raw[];
     // 1024-byte alignment of the stages (the swizzle atoms)
     char* smem = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
@@ -257,7 +259,21 @@ __global__ void __launch_bounds__(128, 1) k_guess_tc(int64_t S, int64_t NC, int 
             tmem_ld32(lane_addr + cb, v);
             if (row < S) {
                 double* out = U + row * NC + n0 + cb;
-                if (n0 + cb + 32 <= NC) {
+                if (ubar_df && n0 + cb + 32 <= NC) {
+                    // U as FP32 pairs: ubar's pair plus the FP32 accumulator,
+                    // added in double-float arithmetic (FP32 pipes only)
+#pragma unroll
+                    for (int i = 0; i < 32; i += 2) {
+                        const float4 b = *reinterpret_cast<const float4*>(ubar_df + n0 + cb + i);
+                        const float2 p0 = df_add(make_float2(b.x, b.y), v[i]);
+                        const float2 p1 = df_add(make_float2(b.z, b.w), v[i + 1]);
+                        *reinterpret_cast<float4*>(out + i) = make_float4(p0.x, p0.y, p1.x, p1.y);
+                    }
+                } else if (ubar_df) {
+                    float2* outp = reinterpret_cast<float2*>(out);
+                    for (int i = 0; i < 32 && n0 + cb + i < NC; ++i)
+                        outp[i] = df_add(ubar_df[n0 + cb + i], v[i]);
+                } else if (n0 + cb + 32 <= NC) {
 #pragma unroll
                     for (int i = 0; i < 32; i += 2) {
                         const double2 b = *reinterpret_cast<const double2*>(ubar + n0 + cb + i);
@@ -363,7 +379,8 @@ bool make_map(CUtensorMap* m, const float* base, int64_t rows, int Kp, int box_r
 
 cudaError_t launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi_hi,
                             const float* psi_lo, const float* Wt_hi, const float* Wt_lo,
-                            const double* ubar, double* U, int* err, cudaStream_t st) {
+                            const double* ubar, const float2* ubar_df, double* U, int* err,
+                            cudaStream_t st) {
     if (S == 0 || NC == 0) return cudaSuccess;
     CUtensorMap mAh, mAl, mBh, mBl;
     if (!make_map(&mAh, psi_hi, S, Kp, TM) || !make_map(&mAl, psi_lo, S, Kp, TM) ||
@@ -377,7 +394,7 @@ cudaError_t launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi_hi,
     const int64_t tiles_n = (NC + TN - 1) / TN;
     if (tiles_n > 65535) return cudaErrorInvalidValue;
     dim3 grid((unsigned)((S + TM - 1) / TM), (unsigned)tiles_n);
-    k_guess_tc<<<grid, 128, SMEM_BYTES, st>>>(S, NC, Kp, mAh, mAl, mBh, mBl, ubar, U, err);
+    k_guess_tc<<<grid, 128, SMEM_BYTES, st>>>(S, NC, Kp, mAh, mAl, mBh, mBl, ubar, ubar_df, U, err);
     return cudaGetLastError();
 }
 
