@@ -11,7 +11,10 @@
 // one thread issues the MMAs and commits them to the stage's "empty"
 // mbarrier.  Every wait on an mbarrier is bounded by a clock budget, after
 // which the CTA sets the error flag, drains its copies and MMAs in flight
-// (again bounded) and frees its tensor memory before it returns.
+// (again bounded) and frees its tensor memory before it returns.  The
+// epilogue adds ubar in FP64, or, for the mixed-defect path, adds the FP32
+// accumulator to a pair copy of ubar in double-float arithmetic and stores
+// U directly as FP32 pairs (hi, lo).
 //
 // Shared-memory layout of one operand chunk (R rows of 32 FP32 = 128 bytes):
 // row r at byte 128 r with its eight 16-byte pieces permuted by the 128-byte
