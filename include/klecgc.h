@@ -31,8 +31,10 @@
  *  - dim = 2 uses the five-point flux-form operator with the coefficient at
  *    the edge midpoints; its linear systems (the backward-Euler steps of F
  *    and the shifted CGC systems of eq. three steps (b)) are solved by
- *    Jacobi-preconditioned CG / COCG to a relative residual (see
- *    klecgc_set_krylov) instead of the 1D direct factorizations.  2D takes
+ *    Jacobi-preconditioned CG / COCG (BiCGStab with convection) to a
+ *    relative residual (see klecgc_set_krylov), or, in FP64 on grids with
+ *    nx <= 64, by banded LU factorizations made once per call (see
+ *    klecgc_set_2d_method).  2D takes
  *    precision KLECGC_FP64 (FP64 Krylov solves) or KLECGC_MIXED (each step of
  *    F by FP64 iterative refinement around an FP32 Jacobi-PCG: the residual
  *    is kept in FP64, so the result meets the same FP64 residual test; the
@@ -374,6 +376,19 @@ klecgc_status klecgc_downsample(klecgc_ctx* ctx, const double* U, int64_t S, int
  */
 klecgc_status klecgc_set_krylov(klecgc_ctx* ctx, double rtol_fine, double rtol_cgc,
                                 int32_t maxit);
+
+/*
+ * 2D linear-solve method: 0 (default) banded LU in FP64 for nx <= 64 and
+ * Krylov otherwise (and on the MIXED path); 1 Krylov always; 2 banded LU
+ * (FP64; UNSUPPORTED for dim = 1 or nx > 64).  Banded LU factors each
+ * backward-Euler matrix I + dt(A + cI) once per sample and each shifted
+ * matrix lambda_k I + dT(A + cI) once per (sample, k) per call (bandwidth
+ * nx, no pivoting: the matrices are diagonally dominant), then every step
+ * or shifted solve is one forward and one backward substitution; the
+ * result is the exact solve up to rounding (no Krylov tolerance).
+ * INVALID_ARG for another method.
+ */
+klecgc_status klecgc_set_2d_method(klecgc_ctx* ctx, int32_t method);
 
 /* Krylov iterations of the last 2D call (klecgc_solve, klecgc_fine_sweep,
  * klecgc_cgc_apply, klecgc_reference), summed over all linear systems, for

@@ -85,6 +85,7 @@ struct klecgc_ctx {
     float* W32t_lo = nullptr;  // [ns*N][Kp] its tail W^T - head
     int Kp = 0;
     int* tc_err = nullptr;     // set by the tensor-core guess when a wait timed out
+    int method2d = 0;          // 2D linear solves: 0 auto, 1 Krylov, 2 banded LU
     std::map<std::string, DevBuf> ws;  // grow-only scratch
     std::string ws_tag;                // appended to scratch names (one batch class each)
     std::vector<void*> owned;
@@ -383,6 +384,42 @@ klecgc_status krylov_read(klecgc_ctx* ctx, int64_t S, const int* ifail,
     return KLECGC_OK;
 }
 
+constexpr int kBandMaxNx = 64;
+
+// 2D FP64 linear solves by banded LU (one factorization per solve, one
+// substitution per step) instead of Krylov iterations: on grids up to
+// kBandMaxNx unless the context forces a method.
+bool use_band(const klecgc_ctx* ctx, bool fp64) {
+    if (ctx->dim != 2 || !fp64 || ctx->method2d == 1) return false;
+    return ctx->method2d == 2 || ctx->nx <= kBandMaxNx;
+}
+
+// Factors of I + step (A + cI) + convection from step-weighted faces w.
+klecgc_status band_factors_fine(klecgc_ctx* ctx, const double* w, int64_t S, double step,
+                                cudaStream_t st, double** Bf_out) {
+    WS(double, Bf, "band_fine", S * band_doubles(ctx->nx));
+    ctx->launch(KLECGC_K_FACTORS, st, [&] {
+        launch_band_factor_fine(S, ctx->nx, w, step * ctx->prob.reaction,
+                                step * ctx->prob.advection, Bf, st);
+    });
+    TRY(cudaGetLastError());
+    *Bf_out = Bf;
+    return KLECGC_OK;
+}
+
+// Factors of lambda_k I + dT (A + cI) + convection, k = 0..K-1.
+klecgc_status band_factors_cgc(klecgc_ctx* ctx, const double* wdT, int64_t S, int K, double dT,
+                               const double2* lam_d, cudaStream_t st, double2** Bc_out) {
+    WS(double2, Bc, "band_cgc", S * K * band_doubles(ctx->nx));
+    ctx->launch(KLECGC_K_FACTORS, st, [&] {
+        launch_band_factor_cgc(S, K, ctx->nx, wdT, dT * ctx->prob.reaction,
+                               dT * ctx->prob.advection, lam_d, Bc, st);
+    });
+    TRY(cudaGetLastError());
+    *Bc_out = Bc;
+    return KLECGC_OK;
+}
+
 // 2D plan kinds: BiCGStab with advection, else CG / COCG (or their mixed forms).
 int fine_kind(const klecgc_ctx* ctx, bool mixed) {
     return ctx->prob.advection > 0 ? 4 : (mixed ? 2 : 0);
@@ -398,6 +435,22 @@ klecgc_status sequential_2d(klecgc_ctx* ctx, const double* xi_d, int64_t S, int 
     double* wdt = nullptr;
     klecgc_status s = build_weights_2d(ctx, xi_d, S, dt, dT, st, &wdt, nullptr);
     if (s != KLECGC_OK) return s;
+    if (use_band(ctx, true)) {
+        double* Bf = nullptr;
+        if ((s = band_factors_fine(ctx, wdt, S, dt, st, &Bf)) != KLECGC_OK) return s;
+        WS(int, act, "act_all", S);
+        WS(double, xs, "band_x", S * (int64_t)ctx->ns);
+        TRY(cudaMemsetAsync(act, 0xff, S * sizeof(int), st));
+        ctx->launch(KLECGC_K_FINE, st, [&] {
+            launch_band_fine(S, N, ctx->nx, J, dt * ctx->prob.reaction, dt * ctx->prob.forcing,
+                             dt * ctx->prob.advection, 0.0, 1, nullptr, ctx->u0, wdt, Bf, xs, out,
+                             act, st);
+        });
+        TRY(cudaGetLastError());
+        ctx->kry_it_fine = ctx->kry_it_cgc = 0;
+        *capped = false;
+        return KLECGC_OK;
+    }
     int* ifail = nullptr;
     unsigned long long* its = nullptr;
     if ((s = krylov_flags(ctx, S, st, &ifail, &its)) != KLECGC_OK) return s;
@@ -486,6 +539,17 @@ klecgc_status coarse_guess_internal(klecgc_ctx* ctx, int64_t S, int N, double dT
         WS(double, scr, "seq_scratch", S * (int64_t)ctx->nx);
         ctx->launch(KLECGC_K_GUESS, st, [&] { launch_fine_factors(field, S, ctx->nx, ctx->h, dT, react, fc, nullptr, st); });
         ctx->launch(KLECGC_K_GUESS, st, [&] { launch_fine_sequential(S, N, ctx->nx, 1, dT * forcing, ctx->u0, fc, scr, U, st); });
+    } else if (use_band(ctx, true)) {
+        double* Bf = nullptr;
+        klecgc_status s = band_factors_fine(ctx, field, S, dT, st, &Bf);
+        if (s != KLECGC_OK) return s;
+        WS(int, act, "act_all", S);
+        WS(double, xs, "band_x", S * (int64_t)ctx->ns);
+        TRY(cudaMemsetAsync(act, 0xff, S * sizeof(int), st));
+        ctx->launch(KLECGC_K_GUESS, st, [&] {
+            launch_band_fine(S, N, ctx->nx, 1, dT * react, dT * forcing, dT * ctx->prob.advection,
+                             0.0, 1, nullptr, ctx->u0, field, Bf, xs, U, act, st);
+        });
     } else {
         WS(int, act, "act_all", S);
         WS(int, gfail, "coarse_fail", S);
@@ -962,6 +1026,15 @@ klecgc_status klecgc_set_krylov(klecgc_ctx* ctx, double rtol_fine, double rtol_c
     ctx->kry_rtol_fine = rtol_fine;
     ctx->kry_rtol_cgc = rtol_cgc;
     ctx->kry_maxit = maxit;
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_set_2d_method(klecgc_ctx* ctx, int32_t method) {
+    set_error("");
+    if (!ctx || method < 0 || method > 2) return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (method == 2 && (ctx->dim != 2 || ctx->nx > kBandMaxNx))
+        return fail(KLECGC_E_UNSUPPORTED, "banded LU: 2D grids with nx <= 64");
+    ctx->method2d = method;
     return KLECGC_OK;
 }
 
@@ -1531,13 +1604,26 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
         WS(double, r, "r", S * (int64_t)nx * N);
         WS(int, active, "active", S);
         TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
+        const double dt = dT / J;
+        if (use_band(ctx, precision == KLECGC_FP64)) {
+            double* Bf = nullptr;
+            if ((s = band_factors_fine(ctx, wdt, S, dt, st, &Bf)) != KLECGC_OK) return s;
+            WS(double, xs, "band_xN", S * (int64_t)nx * N);
+            ctx->launch(KLECGC_K_FINE, st, [&] {
+                launch_band_fine(S, N, ctx->nx, J, dt * ctx->prob.reaction, dt * ctx->prob.forcing,
+                                 dt * ctx->prob.advection, alpha, 0, U, ctx->u0, wdt, Bf, xs, r,
+                                 active, st);
+            });
+            TRY(cudaGetLastError());
+            ctx->kry_it_fine = ctx->kry_it_cgc = 0;
+            return export_batch(ctx, r, S, N, r_out, st);
+        }
         int* ifail = nullptr;
         unsigned long long* its = nullptr;
         if ((s = krylov_flags(ctx, S, st, &ifail, &its)) != KLECGC_OK) return s;
         const bool mixed = precision == KLECGC_MIXED;
         const Plan2D pl = plan_2d(fine_kind(ctx, mixed), ctx->nx, S * N);
         WS(double, scr, "k2d_scratch", pl.scratch_doubles);
-        const double dt = dT / J;
         ctx->launch(KLECGC_K_FINE, st, [&] {
             if (mixed)
                 launch_fine2d_mixed(pl, S, N, ctx->nx, J, dt * ctx->prob.reaction,
@@ -1617,12 +1703,22 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
         WS(double, U, "U", S * (int64_t)nx * N);
         WS(int, active, "active", S);
         TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
-        int* ifail = nullptr;
-        unsigned long long* its = nullptr;
-        if ((s = krylov_flags(ctx, S, st, &ifail, &its)) != KLECGC_OK) return s;
         double *sc, *isc;
         if ((s = scale_tables<double>(ctx, N, alpha, st, &sc, &isc)) != KLECGC_OK) return s;
         WS(Cplx<double>, p, "p64", S * (int64_t)nx * K);
+        if (use_band(ctx, !mixed)) {
+            double2* Bc = nullptr;
+            if ((s = band_factors_cgc(ctx, wdT, S, K, dT, lam_d, st, &Bc)) != KLECGC_OK) return s;
+            launch_cgc_forward<double, double>(S, N, nx, r, sc, p, active, st);
+            ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_band_cgc(S, K, ctx->nx, Bc, p, active, st); });
+            launch_cgc_inverse<double>(S, N, nx, p, isc, U, 2, nullptr, nullptr, active, st);
+            TRY(cudaGetLastError());
+            ctx->kry_it_fine = ctx->kry_it_cgc = 0;
+            return export_batch(ctx, U, S, N, u_out, st);
+        }
+        int* ifail = nullptr;
+        unsigned long long* its = nullptr;
+        if ((s = krylov_flags(ctx, S, st, &ifail, &its)) != KLECGC_OK) return s;
         const Plan2D pl = plan_2d(cgc_kind(ctx, mixed), ctx->nx, S * K);
         WS(double, scr, "k2d_scratch_c", pl.scratch_doubles);
         launch_cgc_forward<double, double>(S, N, nx, r, sc, p, active, st);
@@ -1721,6 +1817,10 @@ struct SolveRun {
     unsigned long long* kits = nullptr;
     double2* lam_d = nullptr;
     Plan2D plF, plC;
+    bool band = false;                         // 2D: banded LU instead of Krylov
+    double* Bf = nullptr;                      // band factors of the fine step
+    double2* Bc = nullptr;                     // band factors of the shifted systems
+    double* xband = nullptr;                   // band: fine-sweep vectors
     double *scrF = nullptr, *scrC = nullptr;
     int* h_active = nullptr;                   // pinned, one int (owned by the caller)
     int k_next = 0;
@@ -1823,10 +1923,21 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
         }
     }
     if (ctx->dim == 2) {
-        // Krylov solves instead of factorizations
+        // Krylov solves, or banded LU factors (FP64 on small grids)
         if ((s = krylov_flags(ctx, S, st, &ifail, &kits)) != KLECGC_OK) return s;
         std::vector<double2> lam;
         if ((s = upload_lambda(ctx, N, alpha, st, lam, &lam_d)) != KLECGC_OK) return s;
+        band = use_band(ctx, f64);
+        if (band) {
+            if ((s = band_factors_fine(ctx, wdt2, S, dT / J, st, &Bf)) != KLECGC_OK) return s;
+            if ((s = band_factors_cgc(ctx, wdT2, S, K, dT, lam_d, st, &Bc)) != KLECGC_OK) return s;
+            WS(double, xb, "band_xN", S * (int64_t)nx * N);
+            xband = xb;
+            TRY(cudaGetLastError());
+            k_next = 0;
+            *h_active = 1;
+            return KLECGC_OK;
+        }
         plF = plan_2d(fine_kind(ctx, precision == KLECGC_MIXED), ctx->nx, S * N);
         plC = plan_2d(cgc_kind(ctx, precision == KLECGC_MIXED), ctx->nx, S * K);
         WS(double, a1, "k2d_scratch", plF.scratch_doubles);
@@ -1844,7 +1955,17 @@ klecgc_status SolveRun::step() {
     TagScope ts(ctx, tag);
     const int k = k_next++;
     const double dTreact = dT * ctx->prob.reaction;
-    if (ctx->dim == 2) {
+    if (ctx->dim == 2 && band) {
+        const double dt = dT / J;
+        ctx->launch(KLECGC_K_FINE, st, [&] {
+            launch_band_fine(S, N, ctx->nx, J, dt * ctx->prob.reaction, dt * ctx->prob.forcing,
+                             dt * ctx->prob.advection, alpha, 0, U, ctx->u0, wdt2, Bf, xband, r,
+                             active, st);
+        });
+        ctx->launch(KLECGC_K_CGC_FWD, st, [&] { launch_cgc_forward<double, double>(S, N, nx, r, sc64, p64, active, st); });
+        ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_band_cgc(S, K, ctx->nx, Bc, p64, active, st); });
+        ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc64, U, 0, delta, nullptr, active, st); });
+    } else if (ctx->dim == 2) {
         const double dt = dT / J;
         if (precision == KLECGC_MIXED)
             ctx->launch(KLECGC_K_FINE, st, [&] {

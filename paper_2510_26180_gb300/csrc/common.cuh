@@ -209,6 +209,26 @@ void launch_nl_prep(int64_t S, int N, int nx, double dT, double c, double f0, co
                     const double* b, const double* wf, double* rhs, double* e, const int* active,
                     cudaStream_t st);
 
+// ---- k_band.cu ---- (2D banded LU, small grids)
+// Doubles (complex values for the CGC) of one band matrix: nx^2 (2 nx + 1).
+int64_t band_doubles(int nx);
+// Factors of I + step (A + cI) + convection per sample; w: step a / h^2
+// faces [S][2 nx (nx+1)], dtc = step c, adv = step b0; Bf: [S][band].
+void launch_band_factor_fine(int64_t S, int nx, const double* wdt, double dtc, double adv_dt,
+                             double* Bf, cudaStream_t st);
+// Factors of lambda_k I + dT (A + cI) + convection per (s, k); Bc: [S][K][band].
+void launch_band_factor_cgc(int64_t S, int K, int nx, const double* wdT, double dTc,
+                            double adv_dT, const double2* lam, double2* Bc, cudaStream_t st);
+// F by banded solves, modes and outputs as launch_fine2d; x: scratch
+// [S][nx^2][N] (mode 0) or [nx^2][S] (mode 1).
+void launch_band_fine(int64_t S, int N, int nx, int J, double dtc, double dtf, double adv_dt,
+                      double alpha, int mode, const double* U, const double* u0,
+                      const double* wdt, const double* Bf, double* x, double* out,
+                      const int* active, cudaStream_t st);
+// (lambda_k I + L_dT) q = p in place, p: [S][nx^2][K].
+void launch_band_cgc(int64_t S, int K, int nx, const double2* Bc, Cplx<double>* p,
+                     const int* active, cudaStream_t st);
+
 // ---- k_offline.cu ---- (Algorithm 3 steps 2-5 on the device)
 // Eigenpairs of the symmetric n x n A (overwritten; its diagonal ends as the
 // eigenvalues) by parallel cyclic threshold Jacobi, eigenvectors as the rows

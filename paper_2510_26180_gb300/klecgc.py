@@ -25,7 +25,7 @@ EXPORTS = ["klecgc_setup", "klecgc_solve", "klecgc_field", "klecgc_guess", "klec
            "klecgc_status_string", "klecgc_last_error", "klecgc_profile_enable",
            "klecgc_profile_read", "klecgc_reference_noalloc", "klecgc_mlp_set", "klecgc_mlp_get",
            "klecgc_mlp_loss_grad", "klecgc_mlp_train", "klecgc_mlp_guess", "klecgc_downsample",
-           "klecgc_set_krylov", "klecgc_krylov_stats", "klecgc_save", "klecgc_load",
+           "klecgc_set_krylov", "klecgc_set_2d_method", "klecgc_krylov_stats", "klecgc_save", "klecgc_load",
            "klecgc_solve_batch", "klecgc_solve_parareal"]
 PROFILE_CLASSES = ["field", "factors", "guess", "fine", "cgc_fwd", "cgc_solve", "cgc_inv",
                    "conv", "layout"]
@@ -105,6 +105,7 @@ def load() -> ctypes.CDLL:
         "klecgc_downsample": [P, P, I64, I32, P, P],
         "klecgc_profile_read": [P, ctypes.POINTER(Profile)],
         "klecgc_set_krylov": [P, D, D, I32],
+        "klecgc_set_2d_method": [P, I32],
         "klecgc_solve_parareal": [P, P, I64, D, I32, I32, D, I32, I32, P, P, P, P, P],
         "klecgc_save": [P, ctypes.c_char_p],
         "klecgc_load": [ctypes.c_char_p, ctypes.POINTER(P), P],
@@ -276,6 +277,10 @@ class Solver:
     # ---- 2D Krylov solves
     def set_krylov(self, rtol_fine, rtol_cgc, maxit) -> int:
         return _check(self.lib.klecgc_set_krylov(self.h, rtol_fine, rtol_cgc, maxit))
+
+    def set_2d_method(self, method) -> int:
+        """0 auto (banded LU in FP64 for nx <= 64), 1 Krylov, 2 banded LU."""
+        return _check(self.lib.klecgc_set_2d_method(self.h, method))
 
     def krylov_stats(self) -> tuple:
         """(fine, CGC) Krylov iterations summed over the systems of the last call."""

@@ -48,10 +48,15 @@ def T(x):
     return torch.from_numpy(np.ascontiguousarray(x)).to(dev())
 
 
-def solver2d(over):
+def solver2d(over, method=1):
+    """method 1: Krylov solves, 2: banded LU (FP64 paths)."""
     solver, w = gpu_solver("rd2d_255", **over)
     solver.set_krylov(RTOL, RTOL, 20000)
+    solver.set_2d_method(method)
     return solver, w
+
+
+METHODS = pytest.mark.parametrize("method", [1, 2], ids=["krylov", "band"])
 
 
 def test_2d_field_matches_input_kl():
@@ -69,16 +74,17 @@ def test_2d_field_matches_input_kl():
         assert rel(a[s, nx * (nx + 1):], ay.ravel()) < 1e-14
 
 
+@METHODS
 @pytest.mark.parametrize("over", [SMALL, MID, BIG], ids=["nx15", "nx31", "nx63_global"])
-def test_2d_reference_matches_sparse_direct(over):
-    solver, w = solver2d(over)
+def test_2d_reference_matches_sparse_direct(over, method):
+    solver, w = solver2d(over, method)
     st = oracle_setup2d("rd2d_255", **over)
     S = 3
     xi = draw_xi(S, w.M, 32)
     U = torch.empty((S, w.N, w.nx * w.nx), dtype=torch.float64, device=dev())
     solver.reference(T(xi), S, w.N, w.J, U)
     its, _ = solver.krylov_stats()
-    assert its > 0
+    assert (its > 0) == (method == 1)
     for s in range(S):
         ref = st.reference(xi[s])
         op_p = st.operator(xi[s], 4.0)
@@ -88,10 +94,11 @@ def test_2d_reference_matches_sparse_direct(over):
         assert d < max(1e-12, 4 * floor), (s, d, floor)
 
 
+@METHODS
 @pytest.mark.parametrize("over", [SMALL, BIG], ids=["nx15", "nx63_global"])
-def test_2d_fine_sweep_matches_oracle(over):
+def test_2d_fine_sweep_matches_oracle(over, method):
     from oracle import pcgc
-    solver, w = solver2d(over)
+    solver, w = solver2d(over, method)
     st = oracle_setup2d("rd2d_255", **over)
     S, dT = 3, w.T / w.N
     xi = draw_xi(S, w.M, 33)
@@ -114,9 +121,10 @@ def test_2d_fine_sweep_matches_oracle(over):
 @pytest.mark.parametrize("over,alpha", [(SMALL, 1e-3), (SMALL, 0.2), (MID, 1e-2),
                                         (BIG, 1e-3)],
                          ids=["nx15_a1e-3", "nx15_a0.2", "nx31", "nx63_global"])
-def test_2d_cgc_apply_matches_oracle(over, alpha):
+@METHODS
+def test_2d_cgc_apply_matches_oracle(over, alpha, method):
     from oracle import pcgc
-    solver, w = solver2d(over)
+    solver, w = solver2d(over, method)
     st = oracle_setup2d("rd2d_255", **over)
     S, N, dT = 3, w.N, w.T / w.N
     n = w.nx * w.nx
@@ -125,7 +133,7 @@ def test_2d_cgc_apply_matches_oracle(over, alpha):
     u = torch.empty_like(T(r))
     solver.cgc_apply(T(xi), S, N, T(r), dT, alpha, 0, u)
     its = solver.krylov_stats()[1]
-    assert its > 0
+    assert (its > 0) == (method == 1)
     for s in range(S):
         op = st.operator(xi[s])
         ref = pcgc.cgc_diagonalized(op, r[s], dT, alpha)
@@ -142,10 +150,11 @@ def test_2d_cgc_apply_matches_oracle(over, alpha):
         assert d < max(1e-12, 4 * floor, kry), (s, d, floor, kry)
 
 
+@METHODS
 @pytest.mark.parametrize("over", [SMALL, MID], ids=["nx15", "nx31"])
-def test_2d_solve_matches_oracle(over):
+def test_2d_solve_matches_oracle(over, method):
     import paper_2510_26180_gb300 as pkg
-    solver, w = solver2d(over)
+    solver, w = solver2d(over, method)
     st = oracle_setup2d("rd2d_255", **over)
     S = 6
     xi = draw_xi(S, w.M, 35)
@@ -281,3 +290,16 @@ def test_2d_cgc_apply_mixed_refinement_matches_oracle(over, alpha):
         kry = 4 * 2.2e-16 * shifted_cond(op, dT, alpha, N) * alpha ** (-(N - 1) / N)
         d = rel(u[s].cpu().numpy(), ref)
         assert d < max(1e-12, 4 * floor, kry), (s, d, floor, kry)
+
+
+def test_2d_method_argument_checks():
+    import paper_2510_26180_gb300 as pkg
+    solver, _ = solver2d(SMALL)
+    with pytest.raises(pkg.KlecgcError) as e:
+        solver.set_2d_method(3)
+    assert e.value.status == pkg.E_INVALID_ARG
+    big, _ = gpu_solver("rd2d_255", nx=95, N=4, J=1, M=4, gpc_degree=1, n_train=10)
+    with pytest.raises(pkg.KlecgcError) as e:
+        big.set_2d_method(2)
+    assert e.value.status == pkg.E_UNSUPPORTED
+    solver.set_2d_method(1)

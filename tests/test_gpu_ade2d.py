@@ -38,10 +38,15 @@ def T(x):
     return torch.from_numpy(np.ascontiguousarray(x)).to(dev())
 
 
-def solver_ade(over):
+def solver_ade(over, method=1):
+    """method 1: BiCGStab, 2: banded LU."""
     solver, w = gpu_solver(NAME, **over)
     solver.set_krylov(RTOL, RTOL, 20000)
+    solver.set_2d_method(method)
     return solver, w
+
+
+METHODS = pytest.mark.parametrize("method", [1, 2], ids=["bicgstab", "band"])
 
 
 def shifted_cond_dense(op, dT, alpha, N):
@@ -51,16 +56,17 @@ def shifted_cond_dense(op, dT, alpha, N):
     return max(np.linalg.cond(l * np.eye(A.shape[0]) + dT * A) for l in lam)
 
 
+@METHODS
 @pytest.mark.parametrize("over", [SMALL, PAPER, BIG], ids=["nx19", "nx19_b0.1", "nx63_global"])
-def test_ade_reference_matches_sparse_direct(over):
+def test_ade_reference_matches_sparse_direct(over, method):
     from oracle import heat1d
-    solver, w = solver_ade(over)
+    solver, w = solver_ade(over, method)
     st = oracle_setup2d(NAME, **over)
     S = 3
     xi = draw_xi(S, w.M, 91)
     U = torch.empty((S, w.N, w.nx * w.nx), dtype=torch.float64, device=dev())
     solver.reference(T(xi), S, w.N, w.J, U)
-    assert solver.krylov_stats()[0] > 0
+    assert (solver.krylov_stats()[0] > 0) == (method == 1)
     for s in range(S):
         ref = st.reference(xi[s])
         floor = rel(heat1d.fine_sequential(st.operator(xi[s], 4.0), st.u0, w.N, w.J, w.T), ref)
@@ -68,10 +74,11 @@ def test_ade_reference_matches_sparse_direct(over):
         assert d < max(1e-12, 4 * floor), (s, d, floor)
 
 
+@METHODS
 @pytest.mark.parametrize("over", [SMALL, BIG], ids=["nx19", "nx63_global"])
-def test_ade_fine_sweep_matches_oracle(over):
+def test_ade_fine_sweep_matches_oracle(over, method):
     from oracle import pcgc
-    solver, w = solver_ade(over)
+    solver, w = solver_ade(over, method)
     st = oracle_setup2d(NAME, **over)
     S, dT = 3, w.T / w.N
     xi = draw_xi(S, w.M, 92)
@@ -92,9 +99,10 @@ def test_ade_fine_sweep_matches_oracle(over):
 
 @pytest.mark.parametrize("over,alpha", [(SMALL, 1e-3), (SMALL, 0.2), (MID, 1e-2), (BIG, 1e-3)],
                          ids=["nx19_a1e-3", "nx19_a0.2", "nx31", "nx63_global"])
-def test_ade_cgc_apply_matches_oracle(over, alpha):
+@METHODS
+def test_ade_cgc_apply_matches_oracle(over, alpha, method):
     from oracle import pcgc
-    solver, w = solver_ade(over)
+    solver, w = solver_ade(over, method)
     st = oracle_setup2d(NAME, **over)
     S, N, dT = 3, w.N, w.T / w.N
     n = w.nx * w.nx
@@ -102,7 +110,7 @@ def test_ade_cgc_apply_matches_oracle(over, alpha):
     r = np.random.default_rng(9).standard_normal((S, N, n))
     u = torch.empty_like(T(r))
     solver.cgc_apply(T(xi), S, N, T(r), dT, alpha, 0, u)
-    assert solver.krylov_stats()[1] > 0
+    assert (solver.krylov_stats()[1] > 0) == (method == 1)
     for s in range(S):
         op = st.operator(xi[s])
         ref = pcgc.cgc_diagonalized(op, r[s], dT, alpha)
@@ -116,10 +124,11 @@ def test_ade_cgc_apply_matches_oracle(over, alpha):
 @pytest.mark.parametrize("over,guess", [(SMALL, "gpc"), (PAPER, "gpc"), (SMALL, "coarse"),
                                         (MID, "gpc")],
                          ids=["nx19_gpc", "nx19_b0.1_gpc", "nx19_coarse", "nx31_gpc"])
-def test_ade_solve_matches_oracle(over, guess):
+@METHODS
+def test_ade_solve_matches_oracle(over, guess, method):
     import paper_2510_26180_gb300 as pkg
     from oracle import pcgc
-    solver, w = solver_ade(over)
+    solver, w = solver_ade(over, method)
     st = oracle_setup2d(NAME, **over)
     S = 4
     xi = draw_xi(S, w.M, 94)
