@@ -222,7 +222,7 @@ def traffic_per_launch(cls, prec, points, launches):
     return MEASURED_TRAFFIC_B_PER_POINT[cls] * points / max(launches, 1)
 
 
-def roofline_2d(cls, ms, launches, units, prec, adv=False):
+def roofline_2d(cls, ms, launches, units, prec, adv=False, band_nx=0):
     """2D Krylov kernels: floating-point operations (an FMA counts 2) per unknown.
 
     CG iteration of F: 9 (x, r, z updates, two dot products) + 20 (stencil
@@ -232,9 +232,22 @@ def roofline_2d(cls, ms, launches, units, prec, adv=False):
     unknown per step, is left out), so the roof is the FP32 one.
     Advection-diffusion (BiCGStab, two stencil applications of 22 flop with
     the upwind terms per iteration): 70 per iteration + 28 per step (real);
-    ~196 per iteration of the complex shifted solves."""
+    ~196 per iteration of the complex shifted solves.
+    Banded LU (FP64, nx <= 32 by default, band_nx = nx): a backward-Euler
+    step is one forward and one backward substitution of bandwidth nx, 4 nx
+    flop per unknown; a shifted solve the same in complex arithmetic, 16 nx."""
     ns = units["ns"]
     fp32 = prec == "mixed" and cls == "fine"
+    if band_nx and cls in ("fine", "cgc_solve"):
+        if cls == "fine":
+            flops = 4.0 * band_nx * ns * units["fine_steps"]
+        else:
+            flops = 16.0 * band_nx * ns * units["cgc_systems"]
+        ach = flops / (ms / 1e3) / 1e12
+        return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK,
+                "unit": "TFLOP/s", "frac": ach / FP64_ALU_PEAK, "traffic": None,
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s",
+                "work": f"{flops / max(launches, 1):.3e} FP64 flop per launch (banded LU)"}
     if cls == "fine":
         per_it, per_step = (70.0, 28.0) if adv else (29.0, 38.0)
         flops = (per_it * units["kry_fine"] + per_step * units["fine_steps"]) * ns
@@ -256,7 +269,8 @@ def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
     if ms <= 0:
         return None
     if w.dim == 2:
-        return roofline_2d(cls, ms, launches, units, prec, w.advection > 0)
+        band_nx = w.nx if (prec == "fp64" and w.nx <= 32) else 0
+        return roofline_2d(cls, ms, launches, units, prec, w.advection > 0, band_nx)
     if w.reaction_kind:
         if cls != "fine":
             return None
@@ -486,7 +500,8 @@ def run_gpu(args, w):
     hbm_peak, peak_kind = peaks()
     units = {"row_steps": row_steps, "points": points, "ns": ns,
              "kry_fine": kry[0] * args.steps, "kry_cgc": kry[1] * args.steps,
-             "fine_steps": float(np.clip(iters, 0, None).sum()) * w.N * w.J * args.steps}
+             "fine_steps": float(np.clip(iters, 0, None).sum()) * w.N * w.J * args.steps,
+             "cgc_systems": float(np.clip(iters, 0, None).sum()) * (w.N // 2 + 1) * args.steps}
     kernels = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}
     tot_ms = sum(v["ms"] for v in kernels.values()) or 1.0
     for v in kernels.values():

@@ -33,8 +33,8 @@
  *    and the shifted CGC systems of eq. three steps (b)) are solved by
  *    Jacobi-preconditioned CG / COCG (BiCGStab with convection) to a
  *    relative residual (see klecgc_set_krylov), or, in FP64 on grids with
- *    nx <= 64, by banded LU factorizations made once per call (see
- *    klecgc_set_2d_method).  2D takes
+ *    nx <= 32 (64 on request), by banded LU factorizations made once per
+ *    call (see klecgc_set_2d_method).  2D takes
  *    precision KLECGC_FP64 (FP64 Krylov solves) or KLECGC_MIXED (each step of
  *    F by FP64 iterative refinement around an FP32 Jacobi-PCG: the residual
  *    is kept in FP64, so the result meets the same FP64 residual test; the
@@ -378,7 +378,7 @@ klecgc_status klecgc_set_krylov(klecgc_ctx* ctx, double rtol_fine, double rtol_c
                                 int32_t maxit);
 
 /*
- * 2D linear-solve method: 0 (default) banded LU in FP64 for nx <= 64 and
+ * 2D linear-solve method: 0 (default) banded LU in FP64 for nx <= 32 and
  * Krylov otherwise (and on the MIXED path); 1 Krylov always; 2 banded LU
  * (FP64; UNSUPPORTED for dim = 1 or nx > 64).  Banded LU factors each
  * backward-Euler matrix I + dt(A + cI) once per sample and each shifted

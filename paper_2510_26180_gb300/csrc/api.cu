@@ -384,14 +384,18 @@ klecgc_status krylov_read(klecgc_ctx* ctx, int64_t S, const int* ifail,
     return KLECGC_OK;
 }
 
-constexpr int kBandMaxNx = 64;
+constexpr int kBandMaxNx = 64;    // largest grid the banded LU accepts
+constexpr int kBandAutoNx = 32;   // largest grid it is chosen for by default
 
 // 2D FP64 linear solves by banded LU (one factorization per solve, one
-// substitution per step) instead of Krylov iterations: on grids up to
-// kBandMaxNx unless the context forces a method.
+// substitution per step) instead of Krylov iterations: by default on grids
+// up to kBandAutoNx (above it the factors, nx^3 values per matrix, are
+// streamed from memory in every step by too few threads to pay off; at
+// nx = 63 with 64 samples the banded path measured 10x slower than Krylov),
+// or as the context forces.
 bool use_band(const klecgc_ctx* ctx, bool fp64) {
     if (ctx->dim != 2 || !fp64 || ctx->method2d == 1) return false;
-    return ctx->method2d == 2 || ctx->nx <= kBandMaxNx;
+    return ctx->method2d == 2 || ctx->nx <= kBandAutoNx;
 }
 
 // Factors of I + step (A + cI) + convection from step-weighted faces w.

@@ -279,7 +279,7 @@ class Solver:
         return _check(self.lib.klecgc_set_krylov(self.h, rtol_fine, rtol_cgc, maxit))
 
     def set_2d_method(self, method) -> int:
-        """0 auto (banded LU in FP64 for nx <= 64), 1 Krylov, 2 banded LU."""
+        """0 auto (banded LU in FP64 for nx <= 32), 1 Krylov, 2 banded LU (nx <= 64)."""
         return _check(self.lib.klecgc_set_2d_method(self.h, method))
 
     def krylov_stats(self) -> tuple:
