@@ -391,7 +391,8 @@ constexpr int kBandAutoNx = 32;   // largest grid it is chosen for by default
 // substitution per step) instead of Krylov iterations: by default on grids
 // up to kBandAutoNx (above it the factors, nx^3 values per matrix, are
 // streamed from memory in every step by too few threads to pay off; at
-// nx = 63 with 64 samples the banded path measured 10x slower than Krylov),
+// nx = 63 with 64 samples the banded path measured 2.8x slower than FP64
+// Krylov),
 // or as the context forces.
 bool use_band(const klecgc_ctx* ctx, bool fp64) {
     if (ctx->dim != 2 || !fp64 || ctx->method2d == 1) return false;
