@@ -44,6 +44,9 @@ MEASURED_TRAFFIC_B_PER_POINT = {"fine": 239.96e6 / 33.52e6, "cgc_fwd": 1047.6e6 
                                 "cgc_solve": 725.9e6 / 33.52e6, "cgc_inv": 751.0e6 / 33.52e6}
 
 
+METHOD2D = [0]   # the 2D solve method of this run (set in main)
+
+
 def peaks():
     p = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(p):
@@ -269,7 +272,8 @@ def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
     if ms <= 0:
         return None
     if w.dim == 2:
-        band_nx = w.nx if (prec == "fp64" and w.nx <= 32) else 0
+        band_nx = w.nx if (prec == "fp64" and (w.nx <= 32 or METHOD2D[0] == 2)
+                           and METHOD2D[0] != 1) else 0
         return roofline_2d(cls, ms, launches, units, prec, w.advection > 0, band_nx)
     if w.reaction_kind:
         if cls != "fine":
@@ -392,6 +396,8 @@ def run_gpu(args, w):
         osetup, pool = oracle_pool(w, cores)
 
     solver = pkg.Solver(pkg.Problem.from_workload(w), draw_train(w))
+    if w.dim == 2 and args.method2d:
+        solver.set_2d_method(args.method2d)
     info = solver.info()
     xi_h = draw_xi(S, w.M, w.seed + 1000 * rank)
     xi = torch.from_numpy(xi_h).to(dev)
@@ -778,6 +784,8 @@ def main():
     ap.add_argument("--samples", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--method2d", type=int, default=0, choices=[0, 1, 2],
+                    help="2D linear solves: 0 auto, 1 Krylov, 2 banded LU")
     ap.add_argument("--offline", default="", metavar="MULTS",
                     help="offline-stage scan: training sets of these multiples of P, e.g. 1,2,8")
     ap.add_argument("--set", action="append", default=[], metavar="FIELD=VALUE",
@@ -790,6 +798,7 @@ def main():
         over[k] = float(v) if any(c in v for c in ".e") else int(v)
     w = workload(args.workload, **over)
     args.overrides = over
+    METHOD2D[0] = args.method2d
     if w.reaction_kind:
         args.precision = "fp64"      # the nonlinear paths are FP64
         args.skip_fp64 = True
