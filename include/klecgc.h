@@ -400,7 +400,8 @@ klecgc_status klecgc_krylov_stats(const klecgc_ctx* ctx, int64_t* its_fine, int6
 /*
  * Context persistence (a library facility; the paper's offline stage is
  * re-run otherwise).  klecgc_save writes the problem, the surrogate tables
- * (input-KL basis, u0, gPC multi-indices, ubar, W), the Krylov settings and,
+ * (input-KL basis, u0, gPC multi-indices, ubar, W), the Krylov settings, the
+ * 2D solve method and,
  * when set, the learned network to `path` (a binary file of this library's
  * own format, native byte order).  klecgc_load creates a context on the
  * current CUDA device from such a file: its guesses and solves equal those

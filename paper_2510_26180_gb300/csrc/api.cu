@@ -834,7 +834,7 @@ void klecgc_free(klecgc_ctx* ctx) {
 }  // extern "C"
 namespace {
 constexpr char kMagic[8] = {'K', 'L', 'E', 'C', 'G', 'C', 'v', '1'};
-constexpr int32_t kVersion = 3;   // 3: problem with advection
+constexpr int32_t kVersion = 4;   // 4: 2D solve method
 
 struct FileHead {
     char magic[8];
@@ -843,7 +843,7 @@ struct FileHead {
     int32_t mlp_ready, kry_maxit;
     double h, dT, lambda_sum, lambda_kept, kry_rtol_fine, kry_rtol_cgc;
     int64_t mlp_P;
-    int32_t mlp_D, pad;
+    int32_t mlp_D, method2d;
 };
 
 template <typename T>
@@ -884,6 +884,7 @@ klecgc_status klecgc_save(const klecgc_ctx* ctx, const char* path) {
     hd.nf = ctx->nf;
     hd.mlp_ready = ctx->mlp.ready ? 1 : 0;
     hd.kry_maxit = ctx->kry_maxit;
+    hd.method2d = ctx->method2d;
     hd.h = ctx->h;
     hd.dT = ctx->dT;
     hd.lambda_sum = ctx->lambda_sum;
@@ -957,6 +958,7 @@ klecgc_status klecgc_load(const char* path, klecgc_ctx** out, void* stream) {
     ctx->kry_rtol_fine = hd.kry_rtol_fine;
     ctx->kry_rtol_cgc = hd.kry_rtol_cgc;
     ctx->kry_maxit = hd.kry_maxit;
+    ctx->method2d = hd.method2d >= 0 && hd.method2d <= 2 ? hd.method2d : 0;
     if (ensure_twiddles(ctx->device) != cudaSuccess) return bail(fail(KLECGC_E_CUDA, "twiddles"));
     const size_t NC = (size_t)ctx->ns * ctx->N;
     klecgc_status s;
