@@ -30,6 +30,7 @@ sys.path.insert(0, ROOT)
 import numpy as np  # noqa: E402
 
 from synth import draw_uneven_shapes, draw_xi  # noqa: E402
+from paper_2510_26180_gb300.ranks import job_rate, rank_seed  # noqa: E402
 
 METRIC = "converged samples/sec at rel err ≤1e-6 vs FP64 oracle; mean parareal iters"
 PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_defect": 2}
@@ -399,7 +400,7 @@ def run_gpu(args, w):
     if w.dim == 2 and args.method2d:
         solver.set_2d_method(args.method2d)
     info = solver.info()
-    xi_h = draw_xi(S, w.M, w.seed + 1000 * rank)
+    xi_h = draw_xi(S, w.M, rank_seed(w.seed, rank))
     xi = torch.from_numpy(xi_h).to(dev)
     ns = w.nx ** w.dim
     U = torch.empty((S, w.N, ns), dtype=torch.float64, device=dev)
@@ -453,13 +454,7 @@ def run_gpu(args, w):
     row_steps = float(np.clip(iters, 0, None).sum()) * w.N * ns * w.J * args.steps
     points = float(np.clip(iters, 0, None).sum()) * w.N * ns * args.steps
 
-    ms_t = torch.tensor([ms], dtype=torch.float64, device=dev)
-    nok_t = torch.tensor([float(n_ok)], dtype=torch.float64, device=dev)
-    if world > 1:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-        dist.all_reduce(nok_t, op=dist.ReduceOp.SUM)
-    ms_max = float(ms_t.item())
-    value = float(nok_t.item()) / (ms_max / 1e3)
+    value, ms_max, _ = job_rate(n_ok, ms, device=dev)
 
     # end-to-end through the C ABI with pinned host buffers (copies timed)
     xi_pin = torch.from_numpy(xi_h).pin_memory()
@@ -646,11 +641,14 @@ def run_gpu_batch(args, w):
     local = int(os.environ.get("LOCAL_RANK", "0"))
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
     prec = args.precision
     cores = os.cpu_count() or 1
     shapes, keys, ci = batch_groups(w)
     n = w.S
-    xi_h = draw_xi(n, w.M, w.seed + 1 + 1000 * rank)
+    xi_h = draw_xi(n, w.M, rank_seed(w.seed + 1, rank))
     do_cpu = (not args.no_cpu_baseline) and world == 1 and rank == 0
     cpu = None
     if do_cpu:
@@ -680,6 +678,8 @@ def run_gpu_batch(args, w):
     sampler = ClockSampler(f"GPU-{uuid}" if uuid is not None else str(local))
     for s in solvers:
         s.profile_enable(True)
+    if world > 1:
+        dist.barrier()
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
@@ -687,6 +687,8 @@ def run_gpu_batch(args, w):
         step()
     e1.record(stream)
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     clocks = sampler.stop()
     prof = {}
     for s in solvers:
@@ -713,7 +715,7 @@ def run_gpu_batch(args, w):
                 err[i] = np.linalg.norm(blk - R[q].ravel()) / np.linalg.norm(R[q])
     ok = (status == 0) & (err <= 1e-6)
     n_ok = int(ok.sum())
-    value = n_ok / (ms / 1e3)
+    value, ms, _ = job_rate(n_ok, ms, device=dev)
     # end to end with pinned host buffers
     xi_pin = torch.from_numpy(xi_h).pin_memory()
     U_pin = torch.empty(int(off[-1]), dtype=torch.float64).pin_memory()
@@ -728,7 +730,8 @@ def run_gpu_batch(args, w):
     torch.cuda.synchronize()
     e2e_s = (time.perf_counter() - t0) / e_steps
     e2e_ok = int(((st_pin.numpy() == 0) & ok).sum())
-    e2e = {"value": e2e_ok / e2e_s, "unit": "samples/s", "h2d_bytes_per_step": int(xi_h.nbytes),
+    e2e = {"value": e2e_ok * world / e2e_s, "unit": "samples/s",
+           "h2d_bytes_per_step": int(xi_h.nbytes),
            "d2h_bytes_per_step": int(U_pin.numel() * 8 + 8 * n)}
     # roofline of the dominant class (fine: FP32 ALU on the mixed path)
     kernels = {k: {"launches": v[0], "ms": v[1]} for k, v in prof.items() if v[0]}
@@ -768,6 +771,8 @@ def run_gpu_batch(args, w):
             "gpu_launches": int(sum(v["launches"] for v in kernels.values())), "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
     for s in solvers:
         s.close()
     return 0
