@@ -154,3 +154,30 @@ def test_burgers_parareal_terminates_and_pcgc_converges_to_the_fine_solution():
         assert np.max(np.abs(its[k][:k] - Ustar[:k])) < 1e-13
     U, k = nl.pcgc_solve(op, u0, np.zeros_like(Ustar), T / N, J, alpha, 1e-12, 80, 3)[:2]
     assert k > 0 and np.max(np.abs(U - Ustar)) < 1e-10
+
+
+def test_nonlinear_contraction_within_theorem_bound():
+    # Theorem thm2: under the one-sided Lipschitz condition with constant L
+    # (Assumption assump; for f = -A u - c (u^3 - u), L = mu_min(A) - c since
+    # u^3 is monotone), the max-over-intervals error contracts per iteration by
+    #   rho(alpha) = max{alpha (1 + e^{-x}) / x, (e^{-x} + 1/(1+x)) / (1 - 1/(1+x))},
+    # x = L dT.  The CGC is solved to convergence (25 simplified Newton steps).
+    rng = np.random.default_rng(21)
+    nx = 20
+    a = np.exp(0.3 * rng.standard_normal(nx + 1))
+    for c, T, N, alpha in ((1.0, 4.0, 4, 0.1), (1.0, 4.0, 8, 0.1), (2.0, 6.0, 6, 0.3)):
+        op = nl.CubicRD1D(a, c, 0.0)
+        L = np.linalg.eigvalsh(op.dense()).min() - c
+        x = L * T / N
+        rho = max(alpha * (1 + np.exp(-x)) / x, (np.exp(-x) + 1 / (1 + x)) / (1 - 1 / (1 + x)))
+        assert rho < 1
+        u0 = heat1d.u0_sine(nx) * 1.5
+        J = 8
+        Ustar = nl.fine_sequential(op, u0, N, J, T)
+        U = np.zeros_like(Ustar)
+        err = np.max(np.linalg.norm(U - Ustar, axis=1))
+        for _ in range(3):
+            U = nl.pcgc_iteration(op, u0, U, T / N, J, alpha, 25)
+            e = np.max(np.linalg.norm(U - Ustar, axis=1))
+            assert e <= rho * err * (1 + 1e-9), (c, T, N, alpha, e / err, rho)
+            err = e
