@@ -16,7 +16,7 @@
 // on the start values, in_mode 0, whose magnitude is that of the solution),
 // which bounds the recount by kFluxEvery; on the increments of in_mode 1,
 // whose size shrinks with the iteration, that keeps F0's rounding well below
-// the solve's tolerance while 7 of 8 steps skip the operator.
+// the solve's tolerance while 15 of 16 steps skip the operator.
 // M is the same for every step, interval and iteration of a sample, so its
 // LU factors are computed once per solve (FP64, rounded):
 //     forward   y_i = rhs_i - l_i y_{i-1}
@@ -49,7 +49,7 @@
 
 namespace klecgc {
 
-constexpr int kFluxEvery = 8;
+constexpr int kFluxEvery = 16;
 
 // Per-sample factor table, four arrays of [S][R][32] entries (row i = lane*R + j
 // at index j*32 + lane):  GL = {G_j, l_j} for the ascending pass, FD =
