@@ -41,7 +41,7 @@ FP64_ALU_PEAK = 1.25                              # TFLOP/s, GB300 nominal FP64
 # capture each on 512 samples of heat1d_nx1023 (profiles/k_fine32_*.md,
 # profiles/k_cgc_*.md); the roofline's traffic scales them to a launch by its
 # points.  Valid while those kernels are unchanged.
-MEASURED_TRAFFIC_B_PER_POINT = {"fine": 239.96e6 / 33.52e6, "cgc_fwd": 1047.6e6 / 33.52e6,
+MEASURED_TRAFFIC_B_PER_POINT = {"fine": 241.90e6 / 33.52e6, "cgc_fwd": 1047.6e6 / 33.52e6,
                                 "cgc_solve": 725.9e6 / 33.52e6, "cgc_inv": 751.0e6 / 33.52e6}
 
 
