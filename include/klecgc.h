@@ -14,6 +14,12 @@
  * g = sum_m sqrt(lambda_m) phi_m(x) xi_m the KL expansion of a Gaussian
  * field with covariance sigma^2 exp(-|x - y| / corr_len).  Both propagators
  * are backward Euler (Section 5): G with step dT, F with J steps dT/J.
+ * Variants selected by klecgc_problem: a 2D upwind convection b . grad u
+ * with b = b0 (x2, x1) (advection-diffusion, Section 5), and the nonlinear
+ * reactions of reaction_kind 1 (cubic, Allen-Cahn type) and 2 (convection
+ * (u^2/2)_x, Burgers type) with Newton propagators and the simplified-Newton
+ * CGC (Section 3.2).  The offline part of Algorithm 3 (snapshots, snapshot
+ * KL, gPC least squares) runs in klecgc_setup, on the device.
  *
  * Conventions shared by every entry point
  *  - Every array is owned by the caller.  The library owns the context and
