@@ -369,6 +369,21 @@ klecgc_status klecgc_mlp_guess(klecgc_ctx* ctx, const double* xi, int64_t S, dou
 klecgc_status klecgc_downsample(klecgc_ctx* ctx, const double* U, int64_t S, int32_t N,
                                 float* T_out, void* stream);
 
+/* Learned-guess mode: residual = 0 (default) the guess is the network's
+ * output as above; residual = 1 the network's output (de-normalized,
+ * interpolated) is a correction added to the gPC surrogate guess of the
+ * same xi, U0 = ubar + psi(xi) W + network(xi), so the network only has to
+ * learn what the surrogate misses (kept in context files).  INVALID_ARG for
+ * another value; UNSUPPORTED outside the linear 1D problem. */
+klecgc_status klecgc_mlp_set_residual(klecgc_ctx* ctx, int32_t residual);
+
+/* Training targets for the current mode: T_out [S][N][64] FP32 = the
+ * reference solutions U [S][N][nx] (FP64) at the network points, minus the
+ * gPC surrogate guess of xi [S][M] there in residual mode (arrays host or
+ * device; the stream is synchronized). */
+klecgc_status klecgc_mlp_targets(klecgc_ctx* ctx, const double* xi, const double* U, int64_t S,
+                                 float* T_out, void* stream);
+
 /*
  * 2D Krylov solves (dim = 2 only; 1D uses direct factorizations).
  * Each backward-Euler step (I + dt(A + cI)) v' = v + dt f0 of F is solved by

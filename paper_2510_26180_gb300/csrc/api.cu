@@ -54,6 +54,7 @@ struct MlpState {
     float* inv_std = nullptr;
     int adam_t = 0;
     bool ready = false;
+    bool residual = false;       // output is a correction added to the gPC guess
 };
 
 }  // namespace klecgc
@@ -742,7 +743,11 @@ klecgc_status mlp_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S,
                           nullptr, st);
     });
     mlp_forward(ctx, B, X, b, Y, st);
-    ctx->launch(KLECGC_K_GUESS, st, [&] { launch_upsample(S, ctx->N, ctx->nx, Y, q.mean, q.stdv, U, st); });
+    if (q.residual) {
+        // U0 = gPC surrogate guess + the network's correction
+        if ((s = gpc_guess_internal(ctx, xi_d, S, true, U, st)) != KLECGC_OK) return s;
+    }
+    ctx->launch(KLECGC_K_GUESS, st, [&] { launch_upsample(S, ctx->N, ctx->nx, Y, q.mean, q.stdv, U, q.residual, st); });
     WS(int, flag, "mlp_flag", 1);
     TRY(cudaMemsetAsync(flag, 0, sizeof(int), st));
     launch_nonfinite_f32((int64_t)B * q.D, Y, flag, st);
@@ -834,7 +839,7 @@ void klecgc_free(klecgc_ctx* ctx) {
 }  // extern "C"
 namespace {
 constexpr char kMagic[8] = {'K', 'L', 'E', 'C', 'G', 'C', 'v', '1'};
-constexpr int32_t kVersion = 4;   // 4: 2D solve method
+constexpr int32_t kVersion = 5;   // 5: learned-guess mode
 
 struct FileHead {
     char magic[8];
@@ -844,6 +849,7 @@ struct FileHead {
     double h, dT, lambda_sum, lambda_kept, kry_rtol_fine, kry_rtol_cgc;
     int64_t mlp_P;
     int32_t mlp_D, method2d;
+    int32_t mlp_residual, pad;
 };
 
 template <typename T>
@@ -893,6 +899,7 @@ klecgc_status klecgc_save(const klecgc_ctx* ctx, const char* path) {
     hd.kry_rtol_cgc = ctx->kry_rtol_cgc;
     hd.mlp_P = ctx->mlp.ready ? ctx->mlp.P : 0;
     hd.mlp_D = ctx->mlp.ready ? ctx->mlp.D : 0;
+    hd.mlp_residual = ctx->mlp.residual ? 1 : 0;
     int cur = 0;
     cudaGetDevice(&cur);
     cudaSetDevice(ctx->device);
@@ -959,6 +966,7 @@ klecgc_status klecgc_load(const char* path, klecgc_ctx** out, void* stream) {
     ctx->kry_rtol_cgc = hd.kry_rtol_cgc;
     ctx->kry_maxit = hd.kry_maxit;
     ctx->method2d = hd.method2d >= 0 && hd.method2d <= 2 ? hd.method2d : 0;
+    ctx->mlp.residual = hd.mlp_residual == 1;
     if (ensure_twiddles(ctx->device) != cudaSuccess) return bail(fail(KLECGC_E_CUDA, "twiddles"));
     const size_t NC = (size_t)ctx->ns * ctx->N;
     klecgc_status s;
@@ -1577,6 +1585,51 @@ klecgc_status klecgc_downsample(klecgc_ctx* ctx, const double* U, int64_t S, int
         T = t;
     }
     launch_downsample(S * (int64_t)N, ctx->nx, Ud, T, st);
+    TRY(cudaGetLastError());
+    if (!dev) TRY(cudaMemcpyAsync(T_out, T, (size_t)S * N * 64 * 4, cudaMemcpyDeviceToHost, st));
+    TRY(cudaStreamSynchronize(st));
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_mlp_set_residual(klecgc_ctx* ctx, int32_t residual) {
+    set_error("");
+    if (!ctx || residual < 0 || residual > 1) return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (ctx->dim != 1 || nonlinear(ctx))
+        return fail(KLECGC_E_UNSUPPORTED, "the learned guess is for the linear 1D problem only");
+    ctx->mlp.residual = residual != 0;
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_mlp_targets(klecgc_ctx* ctx, const double* xi, const double* U, int64_t S,
+                                 float* T_out, void* stream) {
+    set_error("");
+    if (!ctx || !xi || !U || !T_out || S < 0) return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (ctx->dim != 1 || nonlinear(ctx))
+        return fail(KLECGC_E_UNSUPPORTED, "the learned guess is for the linear 1D problem only");
+    if (S == 0) return KLECGC_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int N = ctx->N;
+    const double* Ud = nullptr;
+    klecgc_status s = stage_in(ctx, U, (size_t)S * N * ctx->nx, "ds_in", st, &Ud);
+    if (s != KLECGC_OK) return s;
+    float* T = T_out;
+    const bool dev = is_device_ptr(T_out);
+    if (!dev) {
+        WS(float, t, "ds_out", (size_t)S * N * 64);
+        T = t;
+    }
+    launch_downsample(S * (int64_t)N, ctx->nx, Ud, T, st);
+    if (ctx->mlp.residual) {
+        const double* xi_d = nullptr;
+        if ((s = stage_in(ctx, xi, (size_t)S * ctx->M, "xi", st, &xi_d)) != KLECGC_OK) return s;
+        WS(double, Ug, "U", S * (int64_t)ctx->nx * N);
+        WS(double, Uc, "mlp_gpc", S * (int64_t)ctx->nx * N);
+        WS(float, Tg, "mlp_gpc_ds", (size_t)S * N * 64);
+        if ((s = gpc_guess_internal(ctx, xi_d, S, true, Ug, st)) != KLECGC_OK) return s;
+        if ((s = export_batch(ctx, Ug, S, N, Uc, st)) != KLECGC_OK) return s;
+        launch_downsample(S * (int64_t)N, ctx->nx, Uc, Tg, st);
+        launch_sub_f32((int64_t)S * N * 64, T, Tg, st);
+    }
     TRY(cudaGetLastError());
     if (!dev) TRY(cudaMemcpyAsync(T_out, T, (size_t)S * N * 64 * 4, cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));

@@ -310,7 +310,9 @@ void launch_adam(int64_t n, float lr, int t, float* th, const float* g, float* m
 void launch_f32_to_bf16(int64_t n, const float* x, __nv_bfloat16* y, cudaStream_t st);
 void launch_downsample(int64_t rows, int nx, const double* U, float* T, cudaStream_t st);
 void launch_upsample(int64_t S, int N, int nx, const float* Y, const float* mean,
-                     const float* stdv, double* U, cudaStream_t st);
+                     const float* stdv, double* U, bool accumulate, cudaStream_t st);
+// a -= b elementwise (FP32).
+void launch_sub_f32(int64_t n, float* a, const float* b, cudaStream_t st);
 void launch_colstats(int64_t n, int D, const float* T, float* mean, float* stdv, float* inv_std,
                      cudaStream_t st);
 void launch_nonfinite_f32(int64_t n, const float* x, int* flag, cudaStream_t st);

@@ -269,7 +269,7 @@ void launch_downsample(int64_t rows, int nx, const double* U, float* T, cudaStre
 // de-normalize, then linear interpolation from (0, x_1..x_64, 1) to x_i = (i+1)/(nx+1).
 __global__ void k_upsample(int64_t S, int N, int nx, const float* __restrict__ Y,
                            const float* __restrict__ mean, const float* __restrict__ stdv,
-                           double* __restrict__ U) {
+                           double* __restrict__ U, int accumulate) {
     int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (e >= S * (int64_t)nx * N) return;
     const int n = (int)(e % N);
@@ -287,14 +287,26 @@ __global__ void k_upsample(int64_t S, int N, int nx, const float* __restrict__ Y
         return (k >= 1 && k <= 64) ? (double)(mu[k - 1] + sd[k - 1] * y[k - 1]) : 0.0;
     };
     const double a = node(m), b = node(m + 1);
-    U[e] = a + f * (b - a);
+    const double v = a + f * (b - a);
+    U[e] = accumulate ? U[e] + v : v;
+}
+
+__global__ void k_sub_f32(int64_t n, float* __restrict__ a, const float* __restrict__ b) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t < n) a[t] -= b[t];
 }
 
 void launch_upsample(int64_t S, int N, int nx, const float* Y, const float* mean,
-                     const float* stdv, double* U, cudaStream_t st) {
+                     const float* stdv, double* U, bool accumulate, cudaStream_t st) {
     const int64_t n = S * (int64_t)nx * N;
     if (n == 0) return;
-    k_upsample<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, N, nx, Y, mean, stdv, U);
+    k_upsample<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(S, N, nx, Y, mean, stdv, U,
+                                                          accumulate ? 1 : 0);
+}
+
+void launch_sub_f32(int64_t n, float* a, const float* b, cudaStream_t st) {
+    if (n == 0) return;
+    k_sub_f32<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(n, a, b);
 }
 
 // Per-column mean and 1/std of targets [n][D].

@@ -25,6 +25,7 @@ EXPORTS = ["klecgc_setup", "klecgc_solve", "klecgc_field", "klecgc_guess", "klec
            "klecgc_status_string", "klecgc_last_error", "klecgc_profile_enable",
            "klecgc_profile_read", "klecgc_reference_noalloc", "klecgc_mlp_set", "klecgc_mlp_get",
            "klecgc_mlp_loss_grad", "klecgc_mlp_train", "klecgc_mlp_guess", "klecgc_downsample",
+           "klecgc_mlp_set_residual", "klecgc_mlp_targets",
            "klecgc_set_krylov", "klecgc_set_2d_method", "klecgc_krylov_stats", "klecgc_save", "klecgc_load",
            "klecgc_solve_batch", "klecgc_solve_parareal"]
 PROFILE_CLASSES = ["field", "factors", "guess", "fine", "cgc_fwd", "cgc_solve", "cgc_inv",
@@ -103,6 +104,8 @@ def load() -> ctypes.CDLL:
         "klecgc_mlp_train": [P, P, P, I64, I32, I32, D, D, ctypes.c_uint64, I32, P, P],
         "klecgc_mlp_guess": [P, P, I64, P, P],
         "klecgc_downsample": [P, P, I64, I32, P, P],
+        "klecgc_mlp_set_residual": [P, I32],
+        "klecgc_mlp_targets": [P, P, P, I64, P, P],
         "klecgc_profile_read": [P, ctypes.POINTER(Profile)],
         "klecgc_set_krylov": [P, D, D, I32],
         "klecgc_set_2d_method": [P, I32],
@@ -329,6 +332,16 @@ class Solver:
     def downsample(self, U, S, N, T_out, stream=None) -> int:
         return _check(self.lib.klecgc_downsample(self.h, _ptr(U, np.float64), S, N,
                                                  _ptr(T_out, np.float32), _stream(stream)))
+
+    def mlp_set_residual(self, residual) -> int:
+        """1: the network corrects the gPC surrogate guess; 0: it is the guess."""
+        return _check(self.lib.klecgc_mlp_set_residual(self.h, int(residual)))
+
+    def mlp_targets(self, xi, U, S, T_out, stream=None) -> int:
+        """Training targets of the current mode at the 64 network points."""
+        return _check(self.lib.klecgc_mlp_targets(self.h, _ptr(xi, np.float64),
+                                                  _ptr(U, np.float64), S,
+                                                  _ptr(T_out, np.float32), _stream(stream)))
 
     def reference_noalloc(self, xi, S, N, J, U_out, stream=None) -> int:
         """klecgc_reference without device allocation (device arrays only)."""

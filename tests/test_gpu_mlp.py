@@ -100,12 +100,23 @@ def test_nonfinite_network_falls_back_to_gpc():
     assert torch.equal(it_m, it_g) and torch.equal(U, U2)
 
 
-def test_training_learns_and_the_learned_guess_converges():
+@pytest.mark.parametrize("residual", [0, 1], ids=["direct", "residual"])
+def test_training_learns_and_the_learned_guess_converges(residual):
     """Trains on 2048 references of the Nx=1023, N=64 problem and reports
     what the learned guess gains over the method's own surrogate and over a
-    zero guess on 128 held-out samples (printed; the fixed point is the same)."""
+    zero guess on 128 held-out samples (printed; the fixed point is the same).
+    In residual mode the network learns the surrogate's error, and its guess
+    must beat the surrogate's."""
     import paper_2510_26180_gb300 as pkg
     solver, w = gpu_solver("heat1d_nx1023")
+    solver.mlp_set_residual(residual)
+    try:
+        _train_and_compare(pkg, solver, w, residual)
+    finally:
+        solver.mlp_set_residual(0)
+
+
+def _train_and_compare(pkg, solver, w, residual):
     sizes = omlp.layer_sizes(w.M, w.N)
     ntr, nte = 2048, 128
     xtr, xte = T(draw_xi(ntr, w.M, 5)), T(draw_xi(nte, w.M, 6))
@@ -114,7 +125,11 @@ def test_training_learns_and_the_learned_guess_converges():
     solver.reference(xtr, ntr, w.N, w.J, Utr)
     solver.reference(xte, nte, w.N, w.J, Ute)
     Ttr = torch.empty((ntr, w.N, 64), dtype=torch.float32, device="cuda")
-    solver.downsample(Utr, ntr, w.N, Ttr)
+    solver.mlp_targets(xtr, Utr, ntr, Ttr)
+    if not residual:
+        Tds = torch.empty_like(Ttr)
+        solver.downsample(Utr, ntr, w.N, Tds)
+        assert torch.equal(Ttr, Tds)
     solver.mlp_set(omlp.init_params(sizes, 11).astype(np.float32))
     losses = solver.mlp_train(xtr, Ttr, ntr, 60, 256, 1e-3, 1e-5, 1, True)
     assert np.all(np.isfinite(losses)) and losses[-1] < losses[0] / 20
@@ -122,6 +137,11 @@ def test_training_learns_and_the_learned_guess_converges():
     assert solver.mlp_guess(xte, nte, G) == 0
     err = ((G - Ute).flatten(1).norm(dim=1) / Ute.flatten(1).norm(dim=1)).cpu().numpy()
     assert err.mean() < 0.1
+    Gg = torch.empty_like(Ute)
+    solver.guess(xte, nte, 0, Gg)
+    err_gpc = ((Gg - Ute).flatten(1).norm(dim=1) / Ute.flatten(1).norm(dim=1)).cpu().numpy()
+    if residual:
+        assert err.mean() < err_gpc.mean(), (err.mean(), err_gpc.mean())
     U = torch.empty_like(Ute)
     it = torch.empty(nte, dtype=torch.int32, device="cuda")
     dT = w.T / w.N
@@ -132,4 +152,5 @@ def test_training_learns_and_the_learned_guess_converges():
         e = ((U - Ute).flatten(1).norm(dim=1) / Ute.flatten(1).norm(dim=1)).max().item()
         assert e <= 1e-6
         means[name] = float(it.float().mean())
-    print(f"held-out: learned-guess error {err.mean():.3e}, mean iterations {means}")
+    print(f"held-out ({'residual' if residual else 'direct'}): learned-guess error "
+          f"{err.mean():.3e}, gPC {err_gpc.mean():.3e}, mean iterations {means}")
