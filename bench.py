@@ -371,6 +371,119 @@ def run_offline(args, w):
     return 0
 
 
+def run_mlp(args, w):
+    """Learned guess (mlp_guess workload): trains the network in residual mode
+    (a correction of the gPC guess) on reference solves of the workload's
+    training seed, then solves the held-out batch from the learned guess;
+    value = converged samples/s of those solves.  The surrogate and zero
+    starts are solved once each for the iteration comparison."""
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    import paper_2510_26180_gb300 as pkg
+    from synth import draw_train, draw_xi
+    torch.cuda.set_device(0)
+    dev = torch.device("cuda", 0)
+    e = w.extra
+    ntr, S = int(e["mlp_train"]), args.samples or w.S
+    solver = pkg.Solver(pkg.Problem.from_workload(w), draw_train(w))
+    xtr = torch.from_numpy(draw_xi(ntr, w.M, int(e["mlp_train_seed"]))).to(dev)
+    xte_h = draw_xi(S, w.M, w.seed)
+    xte = torch.from_numpy(xte_h).to(dev)
+    Utr = torch.empty((ntr, w.N, w.nx), dtype=torch.float64, device=dev)
+    Ute = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev)
+    solver.reference(xtr, ntr, w.N, w.J, Utr)
+    solver.reference(xte, S, w.N, w.J, Ute)
+    solver.mlp_set_residual(1)
+    Ttr = torch.empty((ntr, w.N, 64), dtype=torch.float32, device=dev)
+    solver.mlp_targets(xtr, Utr, ntr, Ttr)
+    del Utr
+    # He-initialized weights (seeded), zero biases
+    width = int(e.get("mlp_width", 256))
+    sizes = [w.M, width, width, width, 64 * w.N]
+    rng = np.random.default_rng(11)
+    parts = []
+    for a, b in zip(sizes[:-1], sizes[1:]):
+        parts.append((rng.standard_normal((b, a)) * np.sqrt(2.0 / a)).ravel())
+        parts.append(np.zeros(b))
+    solver.mlp_set(np.concatenate(parts).astype(np.float32))
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    losses = solver.mlp_train(xtr, Ttr, ntr, 60, 256, 1e-3, 1e-5, 1)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+
+    def rel(G):
+        return ((G - Ute).flatten(1).norm(dim=1) / Ute.flatten(1).norm(dim=1)).cpu().numpy()
+
+    Gm, Gg = torch.empty_like(Ute), torch.empty_like(Ute)
+    solver.mlp_guess(xte, S, Gm)
+    solver.guess(xte, S, 0, Gg)
+    em, eg = rel(Gm), rel(Gg)
+    U = torch.empty_like(Ute)
+    it = torch.empty(S, dtype=torch.int32, device=dev)
+    stt = torch.empty(S, dtype=torch.int32, device=dev)
+    prec = PRECISIONS[args.precision]
+    dT = w.T / w.N
+    iters = {}
+    for name, gk in (("gpc", pkg.GUESS_GPC), ("zero", pkg.GUESS_ZERO)):
+        solver.solve(xte, S, dT, w.J, w.N, w.alpha, w.tol, w.kmax, prec, gk, U, it, stt)
+        iters[name] = float(it.float().mean())
+
+    def step():
+        return solver.solve(xte, S, dT, w.J, w.N, w.alpha, w.tol, w.kmax, prec, pkg.GUESS_MLP,
+                            U, it, stt)
+
+    for _ in range(args.warmup):
+        step()
+    sampler = ClockSampler("0")
+    stream = torch.cuda.current_stream()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    clocks = sampler.stop()
+    ms = e0.elapsed_time(e1) / args.steps
+    err = rel(U)
+    ok = int(((stt.cpu().numpy() == 0) & (err <= 1e-6)).sum())
+    iters["mlp"] = float(it.float().mean())
+    value = ok / (ms / 1e3)
+    # end to end with pinned host buffers
+    xi_pin = torch.from_numpy(xte_h).pin_memory()
+    U_pin = torch.empty((S, w.N, w.nx), dtype=torch.float64).pin_memory()
+    it_pin = torch.empty(S, dtype=torch.int32).pin_memory()
+    st_pin = torch.empty(S, dtype=torch.int32).pin_memory()
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    solver.solve(xi_pin, S, dT, w.J, w.N, w.alpha, w.tol, w.kmax, prec, pkg.GUESS_MLP, U_pin,
+                 it_pin, st_pin)
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPES[args.precision], "data": "synthetic",
+            "config": dict(workload_desc(w, S, args.precision),
+                           guess=f"learned, residual on the gPC guess; MLP {sizes}, "
+                                 f"{ntr} training references, 60 epochs"),
+            "mean_iters": iters["mlp"], "converged": ok, "samples": S,
+            "max_rel_err": float(err.max()),
+            "mlp": {"train_s": train_s, "loss_first": float(losses[0]),
+                    "loss_last": float(losses[-1]), "guess_rel_err_mean": float(em.mean()),
+                    "gpc_guess_rel_err_mean": float(eg.mean()), "mean_iters": iters},
+            "roofline": None, "cpu_baseline": None,
+            "e2e": {"value": int((st_pin.numpy() == 0).sum()) / e2e_s, "unit": "samples/s",
+                    "h2d_bytes_per_step": int(xte_h.nbytes),
+                    "d2h_bytes_per_step": int(U_pin.numel() * 8 + 8 * S)},
+            "gpu_launches": None, "clocks": clocks}
+    print(json.dumps(line))
+    solver.close()
+    return 0
+
+
 def run_gpu(args, w):
     import torch
     import torch.distributed as dist
@@ -818,6 +931,8 @@ def main():
         args.skip_fp64 = True
     if args.offline:
         return run_offline(args, w)
+    if w.name == "mlp_guess" and args.impl != "reference":
+        return run_mlp(args, w)
     if w.name == "heat1d_uneven":
         if args.impl == "reference":
             return run_batch_reference(args, w)

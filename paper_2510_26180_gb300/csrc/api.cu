@@ -744,8 +744,9 @@ klecgc_status mlp_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S,
     });
     mlp_forward(ctx, B, X, b, Y, st);
     if (q.residual) {
-        // U0 = gPC surrogate guess + the network's correction
-        if ((s = gpc_guess_internal(ctx, xi_d, S, true, U, st)) != KLECGC_OK) return s;
+        // U0 = gPC surrogate guess (tensor-core contraction, FP32-accurate) +
+        // the network's correction
+        if ((s = gpc_guess_internal(ctx, xi_d, S, false, U, st)) != KLECGC_OK) return s;
     }
     ctx->launch(KLECGC_K_GUESS, st, [&] { launch_upsample(S, ctx->N, ctx->nx, Y, q.mean, q.stdv, U, q.residual, st); });
     WS(int, flag, "mlp_flag", 1);
@@ -1625,7 +1626,7 @@ klecgc_status klecgc_mlp_targets(klecgc_ctx* ctx, const double* xi, const double
         WS(double, Ug, "U", S * (int64_t)ctx->nx * N);
         WS(double, Uc, "mlp_gpc", S * (int64_t)ctx->nx * N);
         WS(float, Tg, "mlp_gpc_ds", (size_t)S * N * 64);
-        if ((s = gpc_guess_internal(ctx, xi_d, S, true, Ug, st)) != KLECGC_OK) return s;
+        if ((s = gpc_guess_internal(ctx, xi_d, S, false, Ug, st)) != KLECGC_OK) return s;
         if ((s = export_batch(ctx, Ug, S, N, Uc, st)) != KLECGC_OK) return s;
         launch_downsample(S * (int64_t)N, ctx->nx, Uc, Tg, st);
         launch_sub_f32((int64_t)S * N * 64, T, Tg, st);

@@ -132,7 +132,9 @@ def _train_and_compare(pkg, solver, w, residual):
         assert torch.equal(Ttr, Tds)
     solver.mlp_set(omlp.init_params(sizes, 11).astype(np.float32))
     losses = solver.mlp_train(xtr, Ttr, ntr, 60, 256, 1e-3, 1e-5, 1, True)
-    assert np.all(np.isfinite(losses)) and losses[-1] < losses[0] / 20
+    # the surrogate's error is the harder target (what a degree-3 polynomial
+    # in xi misses): its normalized loss falls less
+    assert np.all(np.isfinite(losses)) and losses[-1] < losses[0] / (2 if residual else 20)
     G = torch.empty_like(Ute)
     assert solver.mlp_guess(xte, nte, G) == 0
     err = ((G - Ute).flatten(1).norm(dim=1) / Ute.flatten(1).norm(dim=1)).cpu().numpy()
