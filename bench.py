@@ -79,14 +79,15 @@ def workload_desc(w, S, precision, overrides=None):
     else:
         name = (f"{w.name}: 1D u_t=(a u_x)_x, a=exp(KL, M={w.M}), Nx={w.nx}, N={w.N}, "
                 f"J={w.J}, gPC p={w.gpc_degree}, alpha={w.alpha}, tol={w.tol}")
+    state = S * w.N * w.nx ** w.dim * 8 * 4     # the same rule as the timed loop's L2 flush
     d = {"workload": name,
             "samples_per_gpu": S, "nx": w.nx, "N": w.N, "J": w.J, "M": w.M,
             "gpc_degree": w.gpc_degree, "n_train": w.n_train, "alpha": w.alpha, "tol": w.tol,
             "precision": precision,
-            "l2": "inputs larger than L2: per-step working set ~12 GB (U, r, p, factors)"
-                  if w.dim == 1 else
-                  f"per-step state {S * w.N * w.nx ** 2 * 8 * 4 / 1e9:.2f} GB (U, r, p); "
-                  "L2 not flushed",
+            "l2": (f"inputs larger than L2: per-step working set ~{state / 1e9:.1f} GB "
+                   "(U, r, p, factors)" if state >= 2 * 129e6 else
+                   f"per-step working set {state / 1e6:.0f} MB: a 256 MB buffer is written "
+                   "between timed steps to flush L2"),
             "parallelism": "sample shards per GPU, no collective"}
     if overrides:
         d["overrides"] = overrides
