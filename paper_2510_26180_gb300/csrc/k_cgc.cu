@@ -374,7 +374,9 @@ __global__ void __launch_bounds__(128) k_cgc_solve(int64_t S, int K, int nx,
                                                    const TW* __restrict__ wT,
                                                    Cplx<T>* __restrict__ p,
                                                    const int* __restrict__ active) {
-    constexpr int CH = 4;   // rows per load batch (swept 4, 8, 16: 1.049, 1.093, 1.082 ms per 4096-sample launch)
+    // rows per load batch (swept 4, 8, 16: 1.049, 1.093, 1.082 ms per
+    // launch at 4096 samples; the results do not depend on it)
+    constexpr int CH = 4;
     int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     if (t >= S * K) return;
     int64_t s = t / K;
