@@ -399,6 +399,15 @@ klecgc_status klecgc_set_krylov(klecgc_ctx* ctx, double rtol_fine, double rtol_c
                                 int32_t maxit);
 
 /*
+ * Scratch budget: the device scratch the context grows for its calls (the
+ * batch-sized buffers; not the set-up tables it owns) may total at most
+ * `bytes` (0 = no limit, the default).  A call that would exceed it fails
+ * with OUT_OF_MEMORY before allocating, and the context stays usable for
+ * smaller calls.  INVALID_ARG for a negative budget.
+ */
+klecgc_status klecgc_set_scratch_limit(klecgc_ctx* ctx, int64_t bytes);
+
+/*
  * 2D linear-solve method: 0 (default) banded LU in FP64 for nx <= 32 and
  * Krylov otherwise (and on the MIXED path); 1 Krylov always; 2 banded LU
  * (FP64; UNSUPPORTED for dim = 1 or nx > 64).  Banded LU factors each

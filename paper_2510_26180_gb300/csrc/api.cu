@@ -88,6 +88,7 @@ struct klecgc_ctx {
     int* tc_err = nullptr;     // set by the tensor-core guess when a wait timed out
     int method2d = 0;          // 2D linear solves: 0 auto, 1 Krylov, 2 banded LU
     std::map<std::string, DevBuf> ws;  // grow-only scratch
+    size_t ws_limit = 0;               // bytes of scratch allowed (0: no limit)
     std::string ws_tag;                // appended to scratch names (one batch class each)
     std::vector<void*> owned;
     MlpState mlp;
@@ -143,6 +144,15 @@ struct klecgc_ctx {
         size_t bytes = count * sizeof(T);
         if (bytes == 0) bytes = 16;
         if (b.bytes < bytes) {
+            if (ws_limit) {
+                // the caller's budget for the scratch: the sum after growing this buffer
+                size_t total = 0;
+                for (auto& kv : ws) total += kv.second.bytes;
+                if (total - b.bytes + bytes > ws_limit) {
+                    *err = cudaErrorMemoryAllocation;
+                    return nullptr;
+                }
+            }
             if (b.ptr) cudaFree(b.ptr);
             b.ptr = nullptr;
             b.bytes = 0;
@@ -1042,6 +1052,13 @@ klecgc_status klecgc_set_krylov(klecgc_ctx* ctx, double rtol_fine, double rtol_c
     ctx->kry_rtol_fine = rtol_fine;
     ctx->kry_rtol_cgc = rtol_cgc;
     ctx->kry_maxit = maxit;
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_set_scratch_limit(klecgc_ctx* ctx, int64_t bytes) {
+    set_error("");
+    if (!ctx || bytes < 0) return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    ctx->ws_limit = (size_t)bytes;
     return KLECGC_OK;
 }
 

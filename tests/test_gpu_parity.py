@@ -18,7 +18,7 @@ sequential fine solution U*, the accuracy the method is measured at.
 import numpy as np
 import pytest
 
-from synth import draw_xi
+from synth import draw_train, draw_xi, workload
 from tests.gpu_util import gpu_solver, oracle_setup, rel
 
 pytestmark = pytest.mark.gpu
@@ -291,3 +291,51 @@ def test_guess_tensor_core_matches_fp64(S, over):
     assert rel(G32.cpu().numpy(), G64.cpu().numpy()) < 2e-6
     if over.get("gpc_degree"):
         assert solver.info().P == 70
+
+
+def test_sharded_solve_equals_one_solve():
+    """Samples are independent: solving a batch in three shards gives bitwise
+    the same iterates and counts as one solve (the multi-GPU layout's
+    premise, checked on one GPU)."""
+    import paper_2510_26180_gb300 as pkg
+    solver, w = gpu_solver("heat1d_nx63")
+    S = 40
+    xi = draw_xi(S, w.M, 23)
+    dT = w.T / w.N
+    for prec in (pkg.FP64, pkg.MIXED_DEFECT):
+        U = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
+        it = torch.empty(S, dtype=torch.int32, device=dev())
+        solver.solve(T(xi), S, dT, w.J, w.N, w.alpha, w.tol, w.kmax, prec, pkg.GUESS_GPC, U, it)
+        parts = []
+        for a, b in ((0, 7), (7, 29), (29, 40)):
+            Us = torch.empty((b - a, w.N, w.nx), dtype=torch.float64, device=dev())
+            its = torch.empty(b - a, dtype=torch.int32, device=dev())
+            solver.solve(T(xi[a:b]), b - a, dT, w.J, w.N, w.alpha, w.tol, w.kmax, prec,
+                         pkg.GUESS_GPC, Us, its)
+            parts.append((Us, its))
+        assert torch.equal(torch.cat([p[0] for p in parts]), U)
+        assert torch.equal(torch.cat([p[1] for p in parts]), it)
+
+
+def test_scratch_limit_reports_out_of_memory():
+    """A scratch budget too small for a batch gives OUT_OF_MEMORY before any
+    allocation; the context then still solves within (or without) a budget."""
+    import paper_2510_26180_gb300 as pkg
+    w = workload("heat1d_nx63")
+    solver = pkg.Solver(pkg.Problem.from_workload(w), draw_train(w))
+    S = 8
+    xi = draw_xi(S, w.M, 24)
+    U = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
+    dT = w.T / w.N
+    solver.set_scratch_limit(4096)
+    with pytest.raises(pkg.KlecgcError) as e:
+        solver.solve(T(xi), S, dT, w.J, w.N, w.alpha, w.tol, w.kmax, pkg.FP64, pkg.GUESS_GPC, U)
+    assert e.value.status == pkg.E_OUT_OF_MEMORY
+    with pytest.raises(pkg.KlecgcError) as e:
+        solver.set_scratch_limit(-1)
+    assert e.value.status == pkg.E_INVALID_ARG
+    solver.set_scratch_limit(1 << 30)
+    assert solver.solve(T(xi), S, dT, w.J, w.N, w.alpha, w.tol, w.kmax, pkg.FP64,
+                        pkg.GUESS_GPC, U) == pkg.OK
+    solver.set_scratch_limit(0)
+    solver.close()
