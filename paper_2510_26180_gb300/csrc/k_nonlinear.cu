@@ -161,15 +161,19 @@ void launch_fine_newton(int kind, int64_t S, int N, int nx, int J, double dT, do
     if (n == 0) return;
     const int64_t NS = n * nx;
     const double ck = kind_coef(kind, nx, c);
-    const unsigned grid = (unsigned)((n + 127) / 128);
+    // One warp per CTA: each thread runs a long dependent FP64 chain, and the
+    // FP64 pipe of an SM saturates at a few warps, so a batch of a few
+    // thousand columns is spread over all SMs (128-thread CTAs put 256
+    // samples x 32 intervals on 64 of the 152 SMs).
+    const unsigned grid = (unsigned)((n + 31) / 32);
     if (kind == 2)
-        k_fine_newton<2><<<grid, 128, 0, st>>>(S, N, nx, J, dT, alpha, ck, f0, jump, U, u0, wf, b,
-                                               scratch, scratch + NS, scratch + 2 * NS,
-                                               scratch + 3 * NS, active, ifail, itcount);
+        k_fine_newton<2><<<grid, 32, 0, st>>>(S, N, nx, J, dT, alpha, ck, f0, jump, U, u0, wf, b,
+                                              scratch, scratch + NS, scratch + 2 * NS,
+                                              scratch + 3 * NS, active, ifail, itcount);
     else
-        k_fine_newton<1><<<grid, 128, 0, st>>>(S, N, nx, J, dT, alpha, ck, f0, jump, U, u0, wf, b,
-                                               scratch, scratch + NS, scratch + 2 * NS,
-                                               scratch + 3 * NS, active, ifail, itcount);
+        k_fine_newton<1><<<grid, 32, 0, st>>>(S, N, nx, J, dT, alpha, ck, f0, jump, U, u0, wf, b,
+                                              scratch, scratch + NS, scratch + 2 * NS,
+                                              scratch + 3 * NS, active, ifail, itcount);
 }
 
 // Sequential fine solution with Newton steps (reference, snapshots, the
@@ -206,12 +210,12 @@ void launch_sequential_newton(int kind, int64_t S, int N, int nx, int J, double 
                               double* U, int* ifail, cudaStream_t st) {
     if (S == 0) return;
     const double ck = kind_coef(kind, nx, c);
-    const unsigned grid = (unsigned)((S + 63) / 64);
+    const unsigned grid = (unsigned)((S + 31) / 32);   // one warp per CTA (see above)
     if (kind == 2)
-        k_sequential_newton<2><<<grid, 64, 0, st>>>(S, N, nx, J, dt, ck, f0, u0, wf, scratch, U,
+        k_sequential_newton<2><<<grid, 32, 0, st>>>(S, N, nx, J, dt, ck, f0, u0, wf, scratch, U,
                                                     ifail);
     else
-        k_sequential_newton<1><<<grid, 64, 0, st>>>(S, N, nx, J, dt, ck, f0, u0, wf, scratch, U,
+        k_sequential_newton<1><<<grid, 32, 0, st>>>(S, N, nx, J, dt, ck, f0, u0, wf, scratch, U,
                                                     ifail);
 }
 
@@ -431,12 +435,12 @@ void launch_parareal_correct_newton(int kind, int64_t S, int N, int nx, double d
                                     cudaStream_t st) {
     if (S == 0) return;
     const double ck = kind_coef(kind, nx, c);
-    const unsigned grid = (unsigned)((S + 63) / 64);
+    const unsigned grid = (unsigned)((S + 31) / 32);   // one warp per CTA (see above)
     if (kind == 2)
-        k_parareal_correct_newton<2><<<grid, 64, 0, st>>>(S, N, nx, dT, ck, f0, u0, wf, F, U,
+        k_parareal_correct_newton<2><<<grid, 32, 0, st>>>(S, N, nx, dT, ck, f0, u0, wf, F, U,
                                                           scratch, delta, active, ifail);
     else
-        k_parareal_correct_newton<1><<<grid, 64, 0, st>>>(S, N, nx, dT, ck, f0, u0, wf, F, U,
+        k_parareal_correct_newton<1><<<grid, 32, 0, st>>>(S, N, nx, dT, ck, f0, u0, wf, F, U,
                                                           scratch, delta, active, ifail);
 }
 
