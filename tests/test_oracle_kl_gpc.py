@@ -110,3 +110,19 @@ def test_gpc_orthonormal_by_gauss_hermite(M, p):
     B = gpc.psi_matrix(pts, p)
     Gram = (B * w[:, None]).T @ B
     assert np.allclose(Gram, np.eye(B.shape[1]), atol=1e-12)
+
+
+def test_field_basis_rebuilds_the_covariance_kernel():
+    # Mercer: sum_m sqrt(lam_m) phi_m(x) sqrt(lam_m) phi_m(y) -> sigma^2 exp(-|x-y|/ell)
+    # uniformly on [0,1]; the truncation error at K modes is at most
+    # max|phi|^2 * (tail of sum lam) <= 2 * 2 c sigma^2 / (pi^2 K).  Pins the
+    # sqrt(lambda) scaling, the normalization of phi and the [0,1] placement.
+    sigma, ell, K = 0.3, 0.3, 2000
+    x = np.array([0.0, 0.05, 0.3, 0.5, 0.77, 1.0])
+    B = kl_input.field_basis_1d(sigma, ell, K, x)
+    C = B.T @ B
+    exact = sigma ** 2 * np.exp(-np.abs(x[:, None] - x[None, :]) / ell)
+    tail = 2 * 2 * sigma ** 2 / (ell * math.pi ** 2 * K)
+    err = np.abs(C - exact)
+    assert err.max() < 1.5 * tail
+    assert err[~np.eye(len(x), dtype=bool)].max() < 1e-6

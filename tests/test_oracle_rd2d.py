@@ -115,3 +115,56 @@ def test_advection_diffusion_converges_to_the_manufactured_solution():
     assert errs[0] < 0.1
     for e1, e2 in zip(errs, errs[1:]):
         assert 1.7 < e1 / e2 < 2.3, errs
+
+
+def test_field_basis_2d_rebuilds_the_separable_covariance():
+    # Mercer for the separable kernel sigma^2 exp(-|x1-y1|/ell - |x2-y2|/ell):
+    # the top-400 product modes rebuild it to ~4e-5 between distinct points and
+    # to the (slower) truncation tail on the diagonal.  A lambda for
+    # sqrt(lambda), a dropped sigma or a unit-variance mix-up is off by ~sigma^2.
+    from oracle import rd2d
+    sigma, ell, M = 0.3, 0.3, 400
+    P1 = np.array([0.1, 0.2, 0.5, 0.9, 0.33])
+    P2 = np.array([0.7, 0.2, 0.5, 0.1, 0.61])
+    B = rd2d.field_basis_2d(sigma, ell, M, (P1[None, :], P2[None, :])).reshape(M, -1)
+    C = B.T @ B
+    exact = sigma ** 2 * np.exp(-np.abs(P1[:, None] - P1[None, :]) / ell
+                                - np.abs(P2[:, None] - P2[None, :]) / ell)
+    err = np.abs(C - exact)
+    assert err[~np.eye(5, dtype=bool)].max() < 2e-4
+    assert err.max() < 0.1 * sigma ** 2
+
+
+def test_variable_coefficient_2d_operator_is_second_order_consistent():
+    # A u against -div(a grad u) for u = sin(pi x1) sin(2 pi x2) and a sample's
+    # separable-KL field: with a at the edge midpoints the five-point flux form
+    # is O(h^2) (ratio 4 per halving of h); x-faces shifted by h/2 give ~2.
+    # Pins the face points of both directions, the index order (rows are x2)
+    # and the flux signs with a non-constant coefficient.
+    from synth import draw_xi, workload
+    from oracle.klecgc import Setup2D
+    errs = []
+    for nx in (15, 31, 63):
+        w = workload("ade2d_nx19", nx=nx, advection=0.0)
+        st = Setup2D(w, build=False)
+        xi = 2.0 * draw_xi(1, w.M, 6)[0]
+        op = st.operator(xi)
+        x = (np.arange(nx) + 1) / (nx + 1)
+        X1, X2 = np.meshgrid(x, x)
+        u = np.sin(np.pi * X1) * np.sin(2 * np.pi * X2)
+        Au = (op.apply(u.ravel()) - op.reaction * u.ravel()).reshape(nx, nx)
+
+        def a_of(P1, P2):
+            B = rd2d.field_basis_2d(w.sigma, w.corr_len, w.M, (P1, P2))
+            return np.exp(np.tensordot(xi, B, axes=1))
+
+        d = 1e-5
+        a1 = (a_of(X1 + d, X2) - a_of(X1 - d, X2)) / (2 * d)
+        a2 = (a_of(X1, X2 + d) - a_of(X1, X2 - d)) / (2 * d)
+        u1 = np.pi * np.cos(np.pi * X1) * np.sin(2 * np.pi * X2)
+        u2 = 2 * np.pi * np.sin(np.pi * X1) * np.cos(2 * np.pi * X2)
+        exact = -(a1 * u1 + a2 * u2 - 5 * np.pi ** 2 * a_of(X1, X2) * u)
+        errs.append(np.abs(Au - exact).max() / np.abs(exact).max())
+    assert errs[-1] < 2e-3
+    for e1, e2 in zip(errs, errs[1:]):
+        assert 3.6 < e1 / e2 < 4.4, errs
