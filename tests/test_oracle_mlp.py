@@ -51,3 +51,21 @@ def test_grid_maps_interpolation_error_bound():
     up = mlp.upsample(y, 64 * 65 - 1)   # grid containing every coarse node
     idx = (np.arange(64) + 1) * 64 - 1
     assert np.allclose(up[idx], y, atol=1e-14)
+
+
+def test_forward_on_hand_set_weights():
+    # M = 1 -> 2 -> 2 -> 2 -> 1 with r1 = relu(x - 1/2), r2 = relu(-x):
+    # W2 = [[1, 0], [1, 1]] (stored [out][in]) gives (r1, r1 + r2), W3 = I,
+    # W4 = [2, 3], b4 = -10: f(x) = 5 r1 + 3 r2 - 10, negative (no ReLU on the
+    # output).  A transposed W2 would give 2 r1 + 5 r2 - 10.
+    sizes = [1, 2, 2, 2, 1]
+    theta = np.concatenate([
+        [1.0, -1.0], [-0.5, 0.0],                 # W1 [2][1], b1
+        [1.0, 0.0, 1.0, 1.0], [0.0, 0.0],         # W2 [2][2], b2
+        [1.0, 0.0, 0.0, 1.0], [0.0, 0.0],         # W3, b3
+        [2.0, 3.0], [-10.0],                      # W4 [1][2], b4
+    ])
+    assert theta.size == mlp.n_params(sizes)
+    X = np.array([[1.0], [-2.0], [0.2], [0.5]])
+    _, _, Y = mlp.forward(theta, sizes, X)
+    assert np.array_equal(Y[:, 0], np.array([-7.5, -4.0, -10.0, -10.0]))
