@@ -6,7 +6,7 @@ allocation after start-up); its working memory is a fixed array compiled into
 the library.  Here its output is checked against klecgc_reference through the
 C ABI on two calls in a row (the second reuses the array the first one left
 behind), and its size limit and argument checks are exercised.  The file is
-named to be collected last.
+named to be collected after the parity tests.
 """
 import numpy as np
 import pytest
