@@ -1,4 +1,6 @@
 """Convergence factors of parareal with diagonalized CGC (oracle), Section 4.1.
+TEST INFRASTRUCTURE ONLY: part of the CPU oracle (imported by tests/,
+__graft_entry__.smoke() and bench.py's CPU legs, never by the library).
 
 For one-step methods with stability functions R_g (coarse, step dT) and R_f
 (fine, step dT/J), Theorem linearthm gives the per-eigenvalue contraction

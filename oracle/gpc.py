@@ -1,4 +1,6 @@
 """Total-degree Hermite gPC basis (oracle), Section 2.2.
+TEST INFRASTRUCTURE ONLY: part of the CPU oracle (imported by tests/,
+__graft_entry__.smoke() and bench.py's CPU legs, never by the library).
 
 psi_k(xi) = prod_l psi_{k_l}(xi_l) over the multi-indices with |k|_1 <= p
 (eq. complete), P = (p + N_p)! / (p! N_p!).  xi ~ N(0, I) selects the

@@ -1,4 +1,6 @@
 """1D random-diffusion problem and backward-Euler propagators (oracle).
+TEST INFRASTRUCTURE ONLY: part of the CPU oracle (imported by tests/,
+__graft_entry__.smoke() and bench.py's CPU legs, never by the library).
 
 PDE (eq. psys with f(u) = (a u_x)_x - c u + f0): on (0, 1) with zero Dirichlet
 boundary values, u_t = (a(x; xi) u_x)_x - c u + f0.  Finite differences on

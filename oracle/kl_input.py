@@ -1,4 +1,6 @@
 """Karhunen-Loeve expansion of the random input field (oracle).
+TEST INFRASTRUCTURE ONLY: part of the CPU oracle (imported by tests/,
+__graft_entry__.smoke() and bench.py's CPU legs, never by the library).
 
 The paper parameterizes the random coefficient field by a KL expansion
 (Section 1; Section 2 assumes i.i.d. entries of xi) but never states the

@@ -1,4 +1,6 @@
 """End-to-end KLE-PCGC on a workload (oracle): setup + per-sample solves.
+TEST INFRASTRUCTURE ONLY: part of the CPU oracle (imported by tests/,
+__graft_entry__.smoke() and bench.py's CPU legs, never by the library).
 
 setup(w, xi_train)  input-KL basis at the faces, sequential fine snapshots of
                     the training set, surrogate (Algorithm 3 offline part)

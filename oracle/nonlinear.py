@@ -1,4 +1,6 @@
 """Nonlinear problems and the nonlinear coarse grid correction (oracle).
+TEST INFRASTRUCTURE ONLY: part of the CPU oracle (imported by tests/,
+__graft_entry__.smoke() and bench.py's CPU legs, never by the library).
 
 Test infrastructure only (imported by tests/, smoke() and bench.py's CPU
 legs); shares no code with the library.

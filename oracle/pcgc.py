@@ -1,4 +1,6 @@
 """Parareal with sequential and with diagonalized coarse grid correction (oracle).
+TEST INFRASTRUCTURE ONLY: part of the CPU oracle (imported by tests/,
+__graft_entry__.smoke() and bench.py's CPU legs, never by the library).
 
 Storage: an iterate u^k holds U^k_1..U^k_N as rows of an [N, n] array
 (Section 3.2, the stacked vector u^k).  Index n-1 of the array is U_n.

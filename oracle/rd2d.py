@@ -1,4 +1,6 @@
 """2D random reaction-diffusion problem (oracle).
+TEST INFRASTRUCTURE ONLY: part of the CPU oracle (imported by tests/,
+__graft_entry__.smoke() and bench.py's CPU legs, never by the library).
 
 PDE (eq. psys with f(u) = div(a grad u) - c u + f0) on (0,1)^2 with zero
 Dirichlet values, five-point finite differences on an nx x nx interior grid,

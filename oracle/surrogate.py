@@ -1,4 +1,6 @@
 """Offline part of Algorithm 3: snapshot KL + gPC least squares (oracle).
+TEST INFRASTRUCTURE ONLY: part of the CPU oracle (imported by tests/,
+__graft_entry__.smoke() and bench.py's CPU legs, never by the library).
 
 Steps (Section 2.1, eqs. KLE basis, KLE parameter, KLE Snapshots, least
 square A/F/problem; Algorithm 3 steps 1-6):
