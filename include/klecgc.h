@@ -146,9 +146,16 @@ typedef struct {
  *      U^0(xi) = ubar + psi(xi) W (step 6's double sum, regrouped).
  * xi_train: [n_train][M] FP64, host or device.  Runs on the current CUDA
  * device.  On success *out owns the context (free with klecgc_free).
- * Errors: INVALID_ARG (bad problem fields, NULL pointers),
- * OUT_OF_MEMORY, NONFINITE (xi_train), CUDA, UNSUPPORTED (dim not 1 or 2),
- * NOT_CONVERGED (2D: a snapshot's Krylov solve reached the iteration cap).
+ * Errors: INVALID_ARG (NULL pointers; a problem field out of range: nx,
+ * M or J below 1, n_train below 2, gpc_degree < 0, T or corr_len not > 0,
+ * sigma, eps_kl or reaction negative or NaN, advection negative or not
+ * finite, forcing not finite, u0_kind or reaction_kind outside 0..2,
+ * cgc_newton < 0), all
+ * checked before any CUDA call; OUT_OF_MEMORY, NONFINITE (xi_train), CUDA,
+ * UNSUPPORTED (dim not 1 or 2, 2D with nx > 2047, N not a power of 2 in
+ * [2, 64], u0_kind 2 or advection in 1D, advection with reaction_kind 1 or
+ * 2, reaction_kind 1 or 2 in 2D), NOT_CONVERGED (2D: a snapshot's Krylov
+ * solve reached the iteration cap).  On any error *out is NULL.
  * 2D input KL: the covariance sigma^2 exp(-|x1-y1|/l) exp(-|x2-y2|/l) is
  * separable; its eigenpairs are (sigma^2 mu_i mu_j, phi_i(x1) phi_j(x2)) of the
  * unit-variance 1D pairs, ordered by decreasing eigenvalue, ties (i, j) /

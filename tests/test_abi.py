@@ -73,3 +73,46 @@ def test_batch_rejects_bad_arguments_before_any_cuda_call():
     ctxs = (ctypes.c_void_p * 1)(None)
     assert lib.klecgc_solve_batch(ctxs, 0, inst, 1, None, 0.1, 1e-8, 5, 0, 0, None, None, None,
                                   None) == pkg.E_INVALID_ARG
+
+
+def test_setup_validates_problem_fields_before_any_cuda_call():
+    # every rule of klecgc_setup's argument check, through the C ABI; the
+    # check runs before the first CUDA call, so none of these touches a GPU
+    import ctypes
+    import math
+    import numpy as np
+    import paper_2510_26180_gb300 as pkg
+    from synth import workload
+    lib = pkg.load()
+    w = workload("heat1d_nx63")
+    xi_t = np.zeros((w.n_train, w.M))
+    xp = xi_t.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+    INV, UNS = pkg.E_INVALID_ARG, pkg.E_UNSUPPORTED
+    cases = [
+        (dict(dim=3), UNS), (dict(dim=0), UNS), (dict(dim=2, nx=2048), UNS),
+        (dict(nx=0), INV), (dict(M=0), INV), (dict(gpc_degree=-1), INV),
+        (dict(n_train=1), INV), (dict(T=0.0), INV), (dict(T=math.nan), INV),
+        (dict(sigma=-0.1), INV), (dict(corr_len=0.0), INV), (dict(eps_kl=-1e-3), INV),
+        (dict(J=0), INV), (dict(reaction=-1.0), INV), (dict(forcing=math.inf), INV),
+        (dict(u0_kind=-1), INV), (dict(u0_kind=3), INV), (dict(reaction_kind=3), INV),
+        (dict(reaction_kind=-1), INV), (dict(cgc_newton=-1), INV),
+        (dict(advection=-0.1), INV), (dict(advection=math.inf), INV),
+        (dict(u0_kind=2), UNS), (dict(advection=0.1), UNS),
+        (dict(dim=2, nx=15, advection=0.1, reaction_kind=1), UNS),
+        (dict(dim=2, nx=15, reaction_kind=1), UNS),
+        (dict(N=12), UNS), (dict(N=1), UNS), (dict(N=128), UNS),
+    ]
+    for over, want in cases:
+        pr = pkg.Problem.from_workload(w)
+        for k, v in over.items():
+            setattr(pr, k, v)
+        out = ctypes.c_void_p(1)
+        got = lib.klecgc_setup(ctypes.byref(pr), xp, ctypes.byref(out), None)
+        assert got == want, (over, got, lib.klecgc_last_error().decode())
+        assert out.value is None, over
+        assert lib.klecgc_last_error().decode(), over
+    pr = pkg.Problem.from_workload(w)
+    out = ctypes.c_void_p(1)
+    assert lib.klecgc_setup(ctypes.byref(pr), None, ctypes.byref(out), None) == INV
+    assert lib.klecgc_setup(None, xp, ctypes.byref(out), None) == INV
+    assert lib.klecgc_setup(ctypes.byref(pr), xp, None, None) == INV
