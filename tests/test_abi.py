@@ -116,3 +116,31 @@ def test_setup_validates_problem_fields_before_any_cuda_call():
     assert lib.klecgc_setup(ctypes.byref(pr), None, ctypes.byref(out), None) == INV
     assert lib.klecgc_setup(None, xp, ctypes.byref(out), None) == INV
     assert lib.klecgc_setup(ctypes.byref(pr), xp, None, None) == INV
+
+
+def test_every_entry_point_rejects_a_null_context_without_cuda():
+    # ctx = NULL (and NULL / zero for everything else): INVALID_ARG with a
+    # message, checked before any CUDA call; klecgc_free(NULL) is a no-op
+    import ctypes
+    import paper_2510_26180_gb300 as pkg
+    lib = pkg.load()
+    skip = {"klecgc_setup", "klecgc_load", "klecgc_solve_batch"}   # no context argument
+    names = [n for n in pkg.klecgc.EXPORTS if n.startswith("klecgc_") and n not in skip]
+    checked = 0
+    for name in names:
+        f = getattr(lib, name)
+        if f.argtypes is None or f.restype is not ctypes.c_int:
+            continue
+        args = []
+        for t in f.argtypes:
+            if t in (ctypes.c_double,):
+                args.append(0.0)
+            elif t in (ctypes.c_int32, ctypes.c_int64, ctypes.c_uint64, ctypes.c_int):
+                args.append(0)
+            else:
+                args.append(None)
+        assert f(*args) == pkg.E_INVALID_ARG, name
+        assert lib.klecgc_last_error().decode(), name
+        checked += 1
+    assert checked >= 24
+    lib.klecgc_free(None)
