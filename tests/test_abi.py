@@ -73,6 +73,16 @@ def test_batch_rejects_bad_arguments_before_any_cuda_call():
     ctxs = (ctypes.c_void_p * 1)(None)
     assert lib.klecgc_solve_batch(ctxs, 0, inst, 1, None, 0.1, 1e-8, 5, 0, 0, None, None, None,
                                   None) == pkg.E_INVALID_ARG
+    # the range checks of alpha, tol, kmax, precision and guess also come first
+    buf = (ctypes.c_double * 4)()
+    for alpha, tol, kmax, prec, guess in [(0.0, 1e-8, 5, 0, 0), (1.0, 1e-8, 5, 0, 0),
+                                          (0.1, 0.0, 5, 0, 0), (0.1, 1e-8, 0, 0, 0),
+                                          (0.1, 1e-8, 5, 3, 0), (0.1, 1e-8, 5, -1, 0),
+                                          (0.1, 1e-8, 5, 0, pkg.GUESS_USER),
+                                          (0.1, 1e-8, 5, 0, pkg.GUESS_MLP)]:
+        got = lib.klecgc_solve_batch(ctxs, 1, inst, 1, buf, alpha, tol, kmax, prec, guess, buf,
+                                     None, None, None)
+        assert got == pkg.E_INVALID_ARG, (alpha, tol, kmax, prec, guess)
 
 
 def test_setup_validates_problem_fields_before_any_cuda_call():
