@@ -1,6 +1,6 @@
 // 2D problem (five-point operator on an nx x nx interior grid): the fine
-// propagator F (hot-path row a3 with the jump epilogue a4) and the shifted
-// CGC solves of eq. three steps (b) (row a6), both by preconditioned Krylov
+// propagator F (with the CGC right-hand side as its epilogue) and the shifted
+// CGC solves of eq. three steps (b), both by preconditioned Krylov
 // iterations, one CTA per linear system.
 //
 // Operator (flux form, zero Dirichlet values, unknown (ix, iy) at index

@@ -1,4 +1,5 @@
-// Diagonalized coarse grid correction (hot-path rows a5-a9), eq. three steps:
+// Diagonalized coarse grid correction, eq. three steps, with the update and
+// the convergence norm (Algorithm 2 step 3):
 //   (a) p = F_N^* (Lambda_alpha r)            real DFT along the N coarse times
 //   (b) (lambda_k I + dT(A + cI)) q_k = p_k   one complex tridiagonal solve per k
 //   (c) u = Lambda_alpha^{-1} F_N q           inverse DFT, fused with the update

@@ -1,4 +1,4 @@
-// Coefficient field and per-sample factorizations (hot-path row a0).
+// Coefficient field and per-sample factorizations.
 //
 //  a(x_{i+1/2}; xi) = exp(sum_m sqrt(lambda_m) phi_m(x_{i+1/2}) xi_m)  (input KL)
 //  M_F = I + dt (A + c I)                     fine backward-Euler matrix (Section 3.1)

@@ -1,4 +1,4 @@
-// Fine propagator F and the CGC right-hand side (hot-path rows a3, a4).
+// Fine propagator F and the CGC right-hand side.
 //
 // Step 1 of Algorithm 2 (eq. PGC_step1): on every subinterval n, J backward-
 // Euler steps (I + dt(A + cI)) v' = v + dt f0 from start_1 = u0 and

@@ -1,4 +1,5 @@
-// FP32 fine propagator, register-resident (hot-path rows a3, a4; mixed modes).
+// FP32 fine propagator, register-resident (with the CGC right-hand side;
+// mixed modes).
 //
 // Each backward-Euler step of F is taken in increment form: with
 // M = I + dt(A+cI), step m solves M delta_m = rhs_m and sets v += delta_m.

@@ -1,4 +1,4 @@
-// Surrogate guess (hot-path rows a1, a2) and the dense products of the setup.
+// Surrogate guess (gPC basis and contraction) and the dense products of the setup.
 //
 //  psi_j(xi) = prod_l psi_{k_l}(xi_l), |k|_1 <= p              (Section 2.2, eq. complete)
 //  U^0(xi)   = ubar + sum_k sqrt(lambda_k) (sum_j h_kj psi_j(xi)) g_k

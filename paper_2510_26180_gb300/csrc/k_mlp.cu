@@ -1,4 +1,4 @@
-// Learned initial guess (hot-path row a2'): MLP xi -> coarse state at 64
+// Learned initial guess: MLP xi -> coarse state at 64
 // points per coarse time, its training kernels and the grid maps.
 //
 // GEMMs run on the tensor cores with BF16 operands and FP32 accumulation

@@ -1,5 +1,5 @@
-// Surrogate guess on the fifth-generation tensor cores (hot-path row a2,
-// Algorithm 3 step 6):  U[s][c] = ubar[c] + sum_j psi[s][j] W[j][c].
+// Surrogate guess on the fifth-generation tensor cores (Algorithm 3 step 6):
+//   U[s][c] = ubar[c] + sum_j psi[s][j] W[j][c].
 //
 // One CTA computes a 128 x 256 output tile with tcgen05.mma (kind::tf32, FP32
 // accumulation in tensor memory).  To keep FP32 accuracy each operand is
