@@ -451,6 +451,39 @@ klecgc_status klecgc_load(const char* path, klecgc_ctx** out, void* stream);
 /* Sizes of the context (M_Q, P, ...). */
 klecgc_status klecgc_info(const klecgc_ctx* ctx, klecgc_info_t* out);
 
+/*
+ * klecgc_kl_basis - the input-field KL basis b_m(x) = sqrt(lambda_m) phi_m(x),
+ * m = 0..M-1, that klecgc_setup uses for a = exp(sum_m b_m(x) xi_m) (the
+ * problem statement's log-normal coefficient), evaluated at npts points.
+ * dim 1: eigenpairs of sigma^2 exp(-|x - y| / corr_len) on [0,1] (roots of
+ * the transcendental equations, decreasing lambda); dim 2: the separable
+ * product modes on [0,1]^2, ordered as klecgc_setup orders them.  The values
+ * are those klecgc_setup computes at its face points, bit for bit.
+ * Host only: runs on the calling thread and makes no CUDA call.
+ * x: host FP64, [npts] (dim 1) or [npts][2] (dim 2, (x1, x2) pairs);
+ * out: host FP64 [M][npts]; lambda_out: host FP64 [M] or NULL.
+ * Errors: UNSUPPORTED (dim not 1 or 2), INVALID_ARG (M outside 1..65536 in
+ * 1D or 1..1024 in 2D, npts < 0, NULL x or out with npts > 0, corr_len not
+ * finite and > 0, sigma not finite and >= 0).
+ */
+klecgc_status klecgc_kl_basis(int32_t dim, double corr_len, double sigma, int32_t M,
+                              const double* x, int64_t npts, double* out, double* lambda_out);
+
+/*
+ * klecgc_gpc_indices - the multi-indices k of the total-degree Hermite gPC
+ * basis psi_k(xi) = prod_l He_{k_l}(xi_l) / sqrt(k_l!), |k|_1 <= p (Section
+ * 2.2, eq. complete), in the order of the surrogate's coefficient rows: by
+ * total degree, and within a degree in decreasing lexicographic order of
+ * (k_1, ..., k_M).  *P_out = P = (M + p)! / (M! p!).  With out non-NULL,
+ * out (host int32 [P][M], capacity >= P rows) receives the indices.
+ * Host only: makes no CUDA call.
+ * Errors: INVALID_ARG (M < 1, p < 0, capacity < 0, NULL P_out, out non-NULL
+ * and capacity < P), UNSUPPORTED (P > 2^24 or M P > 2^28).
+ */
+klecgc_status klecgc_gpc_indices(int32_t M, int32_t p, int32_t* out, int64_t capacity,
+                                 int64_t* P_out);
+
+
 /* Kernel classes of the profile (index into klecgc_profile_t arrays). */
 enum {
     KLECGC_K_FIELD = 0,     /* coefficient field and face weights          */

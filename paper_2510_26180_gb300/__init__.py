@@ -8,9 +8,9 @@ missing.
 from .klecgc import (FP64, MIXED, MIXED_DEFECT, GUESS_GPC, GUESS_ZERO, GUESS_USER,
                      GUESS_COARSE, GUESS_MLP, OK, E_INVALID_ARG, E_OUT_OF_MEMORY, E_NOT_CONVERGED,
                      E_NONFINITE, E_CUDA, E_UNSUPPORTED, KlecgcError, Problem, Solver, load,
-                     exported_symbols, solve_batch)
+                     exported_symbols, solve_batch, kl_basis, gpc_indices)
 
 __all__ = ["FP64", "MIXED", "MIXED_DEFECT", "GUESS_GPC", "GUESS_ZERO", "GUESS_USER",
            "GUESS_COARSE", "GUESS_MLP", "OK", "E_INVALID_ARG", "E_OUT_OF_MEMORY", "E_NOT_CONVERGED",
            "E_NONFINITE", "E_CUDA", "E_UNSUPPORTED", "KlecgcError", "Problem", "Solver", "load",
-           "exported_symbols", "solve_batch"]
+           "exported_symbols", "solve_batch", "kl_basis", "gpc_indices"]

@@ -1029,6 +1029,58 @@ klecgc_status klecgc_load(const char* path, klecgc_ctx** out, void* stream) {
     return KLECGC_OK;
 }
 
+klecgc_status klecgc_kl_basis(int32_t dim, double corr_len, double sigma, int32_t M,
+                              const double* x, int64_t npts, double* out, double* lambda_out) {
+    set_error("");
+    if (dim != 1 && dim != 2) return fail(KLECGC_E_UNSUPPORTED, "dim must be 1 or 2");
+    if (M < 1 || M > (dim == 1 ? 65536 : 1024) || npts < 0 || (npts > 0 && (!x || !out)) ||
+        !(corr_len > 0) || !std::isfinite(corr_len) || !(sigma >= 0) || !std::isfinite(sigma))
+        return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    // the expressions of klecgc_setup's basis, so the values are identical
+    if (dim == 1) {
+        std::vector<double> lam, om;
+        std::vector<int> par;
+        kl_modes_1d(corr_len, sigma, M, lam, om, par);
+        for (int m = 0; m < M; ++m) {
+            for (int64_t i = 0; i < npts; ++i)
+                out[(size_t)m * npts + i] = std::sqrt(lam[m]) * kl_phi_1d(x[i], om[m], par[m]);
+            if (lambda_out) lambda_out[m] = lam[m];
+        }
+    } else {
+        std::vector<double> lam, mu, om;
+        std::vector<int> mi, mj, par;
+        kl_modes_2d(corr_len, sigma, M, lam, mi, mj, mu, om, par);
+        for (int m = 0; m < M; ++m) {
+            const double sl = std::sqrt(lam[m]);
+            for (int64_t i = 0; i < npts; ++i)
+                out[(size_t)m * npts + i] = sl * kl_phi_1d(x[2 * i], om[mi[m]], par[mi[m]]) *
+                                            kl_phi_1d(x[2 * i + 1], om[mj[m]], par[mj[m]]);
+            if (lambda_out) lambda_out[m] = lam[m];
+        }
+    }
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_gpc_indices(int32_t M, int32_t p, int32_t* out, int64_t capacity,
+                                 int64_t* P_out) {
+    set_error("");
+    if (M < 1 || p < 0 || !P_out || capacity < 0) return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    // P = C(M + p, p), built up as C(M + d, d) = C(M + d - 1, d - 1) (M + d) / d
+    int64_t P = 1;
+    for (int d = 1; d <= p; ++d) {
+        P = P * (M + d) / d;
+        if (P > (int64_t)1 << 24) return fail(KLECGC_E_UNSUPPORTED, "more than 2^24 basis functions");
+    }
+    if ((int64_t)M * P > (int64_t)1 << 28)
+        return fail(KLECGC_E_UNSUPPORTED, "more than 2^28 multi-index entries");
+    *P_out = P;
+    if (!out) return KLECGC_OK;
+    if (capacity < P) return fail(KLECGC_E_INVALID_ARG, "capacity below P");
+    const std::vector<int> deg = gpc_multi_indices(M, p);
+    std::copy(deg.begin(), deg.end(), out);
+    return KLECGC_OK;
+}
+
 klecgc_status klecgc_info(const klecgc_ctx* ctx, klecgc_info_t* out) {
     if (!ctx || !out) return fail(KLECGC_E_INVALID_ARG, "NULL argument");
     out->nx = ctx->nx;

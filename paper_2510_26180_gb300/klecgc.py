@@ -28,7 +28,8 @@ EXPORTS = ["klecgc_setup", "klecgc_solve", "klecgc_field", "klecgc_guess", "klec
            "klecgc_mlp_set_residual", "klecgc_mlp_targets",
            "klecgc_set_krylov", "klecgc_set_2d_method", "klecgc_set_scratch_limit",
            "klecgc_krylov_stats", "klecgc_save", "klecgc_load",
-           "klecgc_solve_batch", "klecgc_solve_parareal"]
+           "klecgc_solve_batch", "klecgc_solve_parareal", "klecgc_kl_basis",
+           "klecgc_gpc_indices"]
 PROFILE_CLASSES = ["field", "factors", "guess", "fine", "cgc_fwd", "cgc_solve", "cgc_inv",
                    "conv", "layout"]
 
@@ -117,6 +118,8 @@ def load() -> ctypes.CDLL:
         "klecgc_solve_batch": [ctypes.POINTER(P), I32, ctypes.POINTER(Instance), I64, P, D, D,
                                I32, I32, I32, P, P, P, P],
         "klecgc_krylov_stats": [P, ctypes.POINTER(ctypes.c_int64), ctypes.POINTER(ctypes.c_int64)],
+        "klecgc_kl_basis": [I32, D, D, I32, P, I64, P, P],
+        "klecgc_gpc_indices": [I32, I32, P, I64, ctypes.POINTER(ctypes.c_int64)],
     }
     for name, args in sig.items():
         f = getattr(lib, name)
@@ -189,6 +192,28 @@ def solve_batch(solvers, ctx_index, J, xi, alpha, tol, kmax, precision, guess, U
                                          _ptr(U_out, np.float64), _ptr(iters_out, np.int32),
                                          _ptr(status_out, np.int32), _stream(stream)), allow)
 
+
+def kl_basis(dim, corr_len, sigma, M, x):
+    """klecgc_kl_basis: the input-KL basis sqrt(lambda_m) phi_m at the points
+    x ([n] in 1D, [n][2] in 2D); returns (basis [M][n], lambda [M])."""
+    lib = load()
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.shape[0] if x.ndim else 0
+    out = np.empty((M, n))
+    lam = np.empty(M)
+    _check(lib.klecgc_kl_basis(dim, corr_len, sigma, M, _ptr(x, np.float64), n,
+                               _ptr(out, np.float64), _ptr(lam, np.float64)))
+    return out, lam
+
+
+def gpc_indices(M, p):
+    """klecgc_gpc_indices: the gPC multi-indices [P][M] in the library's order."""
+    lib = load()
+    P = ctypes.c_int64()
+    _check(lib.klecgc_gpc_indices(M, p, None, 0, ctypes.byref(P)))
+    out = np.empty((P.value, M), dtype=np.int32)
+    _check(lib.klecgc_gpc_indices(M, p, _ptr(out, np.int32), P.value, ctypes.byref(P)))
+    return out
 
 class Solver:
     """Owns one klecgc context (klecgc_setup ... klecgc_free)."""
