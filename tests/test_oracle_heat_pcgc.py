@@ -67,7 +67,8 @@ def test_diagonalization_corrected_and_printed_orientation():
             assert np.min(np.abs(ev - l)) < 1e-10
 
 
-@pytest.mark.parametrize("N,nx,alpha", [(4, 8, 0.1), (6, 5, 1e-3), (8, 7, 1e-2)])
+@pytest.mark.parametrize("N,nx,alpha", [(4, 8, 0.1), (6, 5, 1e-3), (8, 7, 1e-2), (2, 1, 0.5),
+                                        (2, 2, 1e-4)])
 def test_three_step_solve_equals_dense_kron_solve(N, nx, alpha):
     op = _op(nx, seed=N, reaction=0.3)
     r = np.random.default_rng(1).standard_normal((N, nx))
