@@ -16,6 +16,8 @@ Section 5):
   G(v)  one step of Delta T:       (I + dT A) v' = v + dT f0
   F(v)  J steps of dt = dT / J:    (I + dt A) v_{j+1} = v_j + dt f0
 Every linear solve is a banded LAPACK solve (scipy.linalg.solve_banded).
+F_emulated is a precision experiment, not a reference: F with its
+substitutions in a chosen float type (direct or increment form).
 
 The reference ("fine-grid") solution of the paper (Section 2, remark after
 eq. psys) is the sequential fine solution U*_n, n = 1..N.
@@ -33,6 +35,7 @@ class Heat1D:
         self.nx = a_faces.shape[0] - 1
         self.h = 1.0 / (self.nx + 1)
         w = a_faces / self.h ** 2
+        self.wf = w                                  # face weights a_{i+1/2} / h^2
         self.diag = w[:-1] + w[1:] + reaction      # A_ii
         self.off = -w[1:-1]                         # A_{i,i+1} = A_{i+1,i}
         self.forcing = float(forcing)
@@ -99,3 +102,69 @@ def fine_sequential(op, u0: np.ndarray, N: int, J: int, T: float) -> np.ndarray:
         v = F(op, v, dT, J)
         out[n] = v
     return out
+
+
+def F_emulated(op, V: np.ndarray, dT: float, J: int, dtype=np.float32,
+               form: str = "increment", flux_every: int = 1) -> np.ndarray:
+    """F(V) (J backward-Euler steps of dt = dT/J, Section 3.1) with the
+    substitutions carried out in `dtype`: a precision experiment for the fine
+    propagator, not a reference.  V: [nx] or [cols][nx]; returns FP64.
+
+    M = I + dt A is factored in FP64 (Thomas: pivots p_0 = M_00,
+    l_i = M_{i,i-1} / p_{i-1}, p_i = M_ii - l_i M_{i-1,i}); l, M_{i,i+1} and
+    1/p are rounded to `dtype`, and every step's forward and back
+    substitution runs in `dtype`.
+      form "direct":     M v' = v + dt f0
+      form "increment":  M d = rhs, v' = v + d, with rhs the defect
+                         -dt A v + dt f0 (A v in flux form) on every
+                         flux_every-th step (the first included) and the
+                         previous increment d on the others.  For a constant
+                         f0 both right-hand sides are equal in exact
+                         arithmetic: M (v' - v) = v - v_prev.
+    A v in flux form: -(w_{i+1/2} (v_{i+1} - v_i) - w_{i-1/2} (v_i - v_{i-1}))
+    + c v_i with w = a / h^2 and zero boundary values."""
+    dt = dT / J
+    n = op.n
+    lower = -dt * op.wf[1:-1]                     # M_{i,i-1}, i = 1..n-1 (= M_{i-1,i})
+    diag = 1.0 + dt * (op.wf[:-1] + op.wf[1:] + op.reaction)
+    piv = np.empty(n)
+    lmul = np.zeros(n)
+    piv[0] = diag[0]
+    for i in range(1, n):
+        lmul[i] = lower[i - 1] / piv[i - 1]
+        piv[i] = diag[i] - lmul[i] * lower[i - 1]
+    l32 = lmul.astype(dtype)
+    u32 = np.concatenate([lower, [0.0]]).astype(dtype)   # M_{i,i+1}
+    dinv32 = (1.0 / piv).astype(dtype)
+    w = np.asarray(op.wf, dtype=dtype)
+    c, f0, dtt = dtype(op.reaction), dtype(op.forcing), dtype(dt)
+
+    def solve(rhs):
+        y = np.empty_like(rhs)
+        y[..., 0] = rhs[..., 0]
+        for i in range(1, n):
+            y[..., i] = rhs[..., i] - l32[i] * y[..., i - 1]
+        x = np.empty_like(rhs)
+        x[..., n - 1] = dinv32[n - 1] * y[..., n - 1]
+        for i in range(n - 2, -1, -1):
+            x[..., i] = dinv32[i] * (y[..., i] - u32[i] * x[..., i + 1])
+        return x
+
+    def flux_Av(v):
+        z = np.zeros(v.shape[:-1] + (1,), dtype=dtype)
+        vp = np.concatenate([z, v, z], axis=-1)
+        q = w * (vp[..., 1:] - vp[..., :-1])      # w_f (v_f - v_{f-1}) at the n + 1 faces
+        return -(q[..., 1:] - q[..., :-1]) + c * v
+
+    v = np.asarray(V, dtype=dtype)
+    d = None
+    for m in range(J):
+        if form == "direct":
+            v = solve(v + dtt * f0)
+        else:
+            rhs = -dtt * flux_Av(v) + dtt * f0 if d is None or m % flux_every == 0 else d
+            d = solve(rhs)
+            v = v + d
+        assert v.dtype == dtype
+    return v.astype(np.float64)
+

@@ -206,3 +206,40 @@ def test_variable_coefficient_operator_is_second_order_consistent():
     assert errs[-1] < 1e-4
     for e1, e2 in zip(errs, errs[1:]):
         assert 3.6 < e1 / e2 < 4.4, errs
+
+
+def test_emulated_fine_propagator_algebra_in_fp64():
+    # in FP64 the emulation is the propagator F itself, in either form and for
+    # any refresh period: the increment recurrence M (v' - v) = v - v_prev and
+    # the flux-form defect are exact identities of backward Euler
+    op = _op(40, seed=3, reaction=0.3, forcing=0.7)
+    V = np.random.default_rng(6).standard_normal((3, 40))
+    ref = np.stack([heat1d.F(op, v, 0.05, 12) for v in V])
+    for form, K in (("direct", 1), ("increment", 1), ("increment", 5), ("increment", 12)):
+        got = heat1d.F_emulated(op, V, 0.05, 12, np.float64, form, K)
+        assert np.max(np.abs(got - ref)) < 1e-12 * np.max(np.abs(ref)), (form, K)
+
+
+def test_emulated_fp32_increment_form_keeps_accuracy():
+    # FP32 substitutions with FP64-made factors on the Nx = 1023, J = 64 heat
+    # workload: the increment form with the flux defect on every step is far
+    # more accurate than the direct form, and reusing the previous increment
+    # between refreshes costs accuracy monotonically in the refresh period
+    from synth import draw_xi, workload
+    from oracle.klecgc import Setup1D
+    w = workload("heat1d_nx1023")
+    st = Setup1D(w, build=False)
+    op = st.operator(draw_xi(1, w.M, 5)[0])
+    dT = w.T / w.N
+    V = np.stack([st.u0, heat1d.F(op, st.u0, 10 * dT, 10 * w.J)])
+    ref = np.stack([heat1d.F(op, v, dT, w.J) for v in V])
+
+    def err(form, K):
+        got = heat1d.F_emulated(op, V, dT, w.J, np.float32, form, K)
+        return np.max(np.abs(got - ref)) / np.max(np.abs(ref))
+
+    direct, e1, e16, e64 = err("direct", 1), err("increment", 1), err("increment", 16), \
+        err("increment", 64)
+    assert direct > 1e-6 and e1 < 2e-7
+    assert e1 < direct / 20 and e16 < direct / 5
+    assert e1 < e16 < e64
