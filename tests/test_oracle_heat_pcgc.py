@@ -243,3 +243,22 @@ def test_emulated_fp32_increment_form_keeps_accuracy():
     assert direct > 1e-6 and e1 < 2e-7
     assert e1 < direct / 20 and e16 < direct / 5
     assert e1 < e16 < e64
+
+
+def test_coarse_guess_closed_form_a_const():
+    # a == 1, f0 = 0, u0 = sin(pi x): the coarse sweep U0_n = G(U0_{n-1}) is
+    # (1 + dT mu_1)^(-n) sin(pi x_i) (Section 3.1); with f0 = 1 from zero it
+    # tends to the discrete steady state x(1-x)/2
+    nx, N, T = 31, 16, 1.0
+    op = _op(nx, const=True)
+    u0 = heat1d.u0_sine(nx)
+    U0 = pcgc.coarse_guess(op, u0, N, T / N)
+    mu1 = 4 / op.h ** 2 * math.sin(math.pi * op.h / 2) ** 2
+    n = np.arange(1, N + 1)
+    exact = (1 + T / N * mu1) ** (-n.astype(float))[:, None] * u0[None, :]
+    assert U0.shape == (N, nx)
+    assert np.allclose(U0, exact, rtol=1e-12, atol=1e-15)
+    opf = _op(nx, const=True, forcing=1.0)
+    Uf = pcgc.coarse_guess(opf, np.zeros(nx), 400, 0.05)
+    x = opf.grid()
+    assert np.allclose(Uf[-1], x * (1 - x) / 2, rtol=1e-10, atol=1e-13)
