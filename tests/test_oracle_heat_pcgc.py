@@ -262,3 +262,21 @@ def test_coarse_guess_closed_form_a_const():
     Uf = pcgc.coarse_guess(opf, np.zeros(nx), 400, 0.05)
     x = opf.grid()
     assert np.allclose(Uf[-1], x * (1 - x) / 2, rtol=1e-10, atol=1e-13)
+
+
+def test_error_metrics_by_construction():
+    # Section 5's e_n = (1/S) sum_i ||u_n(xi_i) - U_n(xi_i)||_inf: perturb one
+    # entry of each (sample, n) by a chosen t[s, n] and smaller ones elsewhere
+    from oracle.klecgc import mean_inf_error, rel_l2
+    rng = np.random.default_rng(8)
+    S, N, nx = 3, 4, 5
+    Uref = rng.standard_normal((S, N, nx))
+    t = rng.random((S, N)) + 0.5
+    D = rng.uniform(-0.4, 0.4, (S, N, nx))
+    pos = rng.integers(0, nx, (S, N))
+    for s in range(S):
+        for n in range(N):
+            D[s, n, pos[s, n]] = -t[s, n] if (s + n) % 2 else t[s, n]
+    assert np.allclose(mean_inf_error(Uref, Uref + D), t.mean(axis=0), rtol=1e-14)
+    # rel_l2 of a uniform relative scaling is the scaling
+    assert abs(rel_l2(1.25 * Uref, Uref) - 0.25) < 1e-14
