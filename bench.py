@@ -153,6 +153,12 @@ def _oracle_solve(xi):
     return U, k
 
 
+def _oracle_solve_timed(xi):
+    t = time.perf_counter()
+    _ORACLE.solve_sample(xi)
+    return time.perf_counter() - t
+
+
 def oracle_pool(w, cores):
     """Oracle set-up (snapshots on all cores) and a spawn pool holding it.
 
@@ -200,6 +206,8 @@ def run_reference(args, w):
         for _ in range(args.steps):
             dt, outs = oracle_step(pool, xi)
             times.append(dt)
+        # one sample in one worker (single-threaded BLAS): the 1-thread rate
+        t1 = pool.apply(_oracle_solve_timed, (xi[0],))
     iters = [k for _, k in outs]
     t = float(np.mean(times))
     value = n_sub / t
@@ -212,7 +220,10 @@ def run_reference(args, w):
             "config": workload_desc(w, n_sub, "fp64", args.overrides),
             "mean_iters": float(np.mean(iters)),
             "cpu_baseline": {"value": value, "unit": "samples/s", "cores": cores,
-                             "kind": "oracle", "sample": sample},
+                             "kind": "oracle", "sample": sample,
+                             "single_thread": {"value": 1.0 / t1, "unit": "samples/s",
+                                               "sample": "sample 0, one process, "
+                                                         "single-threaded BLAS"}},
             "e2e": {"value": value, "unit": "samples/s", "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line))

@@ -22,4 +22,5 @@ def test_reference_arm_prints_one_contract_line():
         assert k in d, k
     assert d["impl"] == "reference" and d["value"] > 0 and d["higher_is_better"] is True
     assert d["cpu_baseline"]["kind"] == "oracle" and d["cpu_baseline"]["cores"] >= 1
+    assert d["cpu_baseline"]["single_thread"]["value"] > 0
     assert d["e2e"]["h2d_bytes_per_step"] == 0 and "workload" in d["config"]
