@@ -155,3 +155,22 @@ def test_every_entry_point_rejects_a_null_context_without_cuda():
         checked += 1
     assert checked >= 24
     lib.klecgc_free(None)
+
+
+def test_missing_library_fails_loudly(tmp_path):
+    # no CPU fallback: without the compiled library every call path raises
+    import subprocess
+    import sys
+    code = (
+        "import paper_2510_26180_gb300.klecgc as k\n"
+        f"k.LIB_PATH = {str(tmp_path / 'absent.so')!r}\n"
+        "k._lib = None\n"
+        "try:\n"
+        "    k.load()\n"
+        "except RuntimeError as e:\n"
+        "    assert 'missing' in str(e)\n"
+        "    print('raised')\n"
+    )
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT,
+                       timeout=120)
+    assert r.returncode == 0 and r.stdout.strip() == "raised", r.stderr[-2000:]
