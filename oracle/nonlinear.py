@@ -220,7 +220,7 @@ def cgc_newton_step(op, u, b, dT, alpha):
     j = np.arange(N)
     lam = 1.0 - alpha ** (1.0 / N) * np.exp(-2j * np.pi * j / N)
     sr = (alpha ** (j / N))[:, None] * rhs
-    W = np.exp(-2j * np.pi * np.outer(j, j) / N)    # F_N^* sqrt(N): p_k = sum_j w^{jk} r_j
+    W = np.exp(-2j * np.pi * (np.outer(j, j) % N) / N)  # F_N^* sqrt(N) (omega^N = 1)
     p = W @ sr
     q = np.stack([np.linalg.solve(lam[k] * np.eye(n) + dT * K, p[k]) for k in range(N)])
     u_new = (np.conj(W) @ q) / N

@@ -49,9 +49,14 @@ def calpha(N: int, alpha: float) -> np.ndarray:
 
 
 def dft_matrix(N: int) -> np.ndarray:
-    """F_N with entries omega^{jk} / sqrt(N), omega = exp(2 pi i / N)."""
+    """F_N with entries omega^{jk} / sqrt(N), omega = exp(2 pi i / N).
+
+    omega^N = 1, so omega^{jk} = omega^{(jk mod N)}: the exponent is reduced
+    before the angle is formed, so that every entry is exp of an angle below
+    2 pi (for jk up to (N-1)^2 the unreduced angle carries a rounding error of
+    eps jk, which step (c)'s alpha^{-(n-1)/N} scaling would amplify)."""
     j = np.arange(N)
-    return np.exp(2j * np.pi * np.outer(j, j) / N) / np.sqrt(N)
+    return np.exp(2j * np.pi * (np.outer(j, j) % N) / N) / np.sqrt(N)
 
 
 def diag_factors(N: int, alpha: float, printed: bool = False):
@@ -88,10 +93,14 @@ def cgc_diagonalized(op, r: np.ndarray, dT: float, alpha: float,
         FN = dft_matrix(N)
         # (a) p = (V^{-1} (x) I) r = (F_N^* (x) I)(Lambda_alpha (x) I) r
         p = FN.conj().T @ sr
-    # (b) (lambda_n I + dT A) q_n = p_n for every n (all N frequencies)
+    # (b) (lambda_n I + dT A) q_n = p_n for every n (all N frequencies), with
+    # iterative refinement where the operator offers it (1D): the plain banded
+    # solve loses the smooth modes to pivot cancellation at large dT w, and
+    # step (c) amplifies that loss by up to 1/alpha
+    solve = getattr(op, "shifted_solve_refined", op.shifted_solve)
     q = np.empty_like(p)
     for k in range(N):
-        q[k] = op.shifted_solve(lam[k], dT, p[k])
+        q[k] = solve(lam[k], dT, p[k])
     # (c) u = (V (x) I) q = (Lambda_alpha^{-1} (x) I)(F_N (x) I) q
     Fq = np.fft.ifft(q, axis=0) * np.sqrt(N) if fft else dft_matrix(N) @ q
     u = (alpha ** (-n / N))[:, None] * Fq

@@ -43,6 +43,12 @@ void launch_face_weights(const double* a, int64_t S, int nf, double scale, doubl
 // One thread per sample: LU of the symmetric tridiagonal M_F.  Row i couples
 // to row i-1 through face i: M_{i,i-1} = M_{i-1,i} = -wd_i, wd_f = dt a_f / h^2.
 // Entry nx of each sample holds only wd_nx (the right boundary face).
+// The pivots are formed without cancellation: with lambda' = 1 + dt c,
+//     piv_i = wd_{i+1} + sigma_i,  sigma_0 = lambda' + wd_0,
+//     sigma_i = lambda' + wd_i sigma_{i-1} / piv_{i-1}  (piv_{i-1} = wd_i + sigma_{i-1}),
+// which equals piv_i = M_ii - wd_i^2 / piv_{i-1} in exact arithmetic but never
+// subtracts O(wd) numbers: the small part sigma, which carries the smooth
+// modes, keeps full relative precision however large dt a / h^2 is.
 __global__ void k_fine_factors(const double* __restrict__ a, int64_t S, int nx, double inv_h2,
                                double dt, double react, FineCoef64* __restrict__ f64,
                                FineCoef32* __restrict__ f32) {
@@ -51,18 +57,18 @@ __global__ void k_fine_factors(const double* __restrict__ a, int64_t S, int nx, 
     const double* as = a + s * (nx + 1);
     FineCoef64* o64 = f64 + s * (nx + 1);
     FineCoef32* o32 = f32 ? f32 + s * (nx + 1) : nullptr;
-    double piv = 1.0;
+    const double lam = 1.0 + dt * react;
     double wl = dt * as[0] * inv_h2;
+    double sig = lam + wl, piv = 1.0;
     for (int i = 0; i < nx; ++i) {
-        double wr = dt * as[i + 1] * inv_h2;
-        double diag = 1.0 + wl + wr + dt * react;
+        const double wr = dt * as[i + 1] * inv_h2;
         double l = 0.0;
         if (i > 0) {
-            l = -wl / piv;
-            diag = diag + l * wl;  // diag - l * M_{i-1,i}, M_{i-1,i} = -wl
+            l = -wl / piv;           // M_{i,i-1} / piv_{i-1}
+            sig = lam - l * sig;     // lambda' + wl sigma_{i-1} / piv_{i-1}
         }
-        piv = diag;
-        double dinv = 1.0 / piv;
+        piv = wr + sig;
+        const double dinv = 1.0 / piv;
         o64[i] = FineCoef64{l, dinv, wl, 0.0};
         if (o32) o32[i] = FineCoef32{(float)l, (float)dinv, (float)wl, 0.0f};
         wl = wr;
@@ -84,6 +90,14 @@ void launch_fine_factors(const double* a, int64_t S, int nx, double h, double dt
 // [S][nx][K] so that the K systems of one sample are contiguous per row.
 // ext (optional, [S][nx]): a per-row addition dT ext_i to the diagonal (the
 // averaged Jacobian of the nonlinear CGC).
+// Pivots without cancellation (lambda'_i = lambda_k + dT c + dT ext_i,
+// W_i = dT w_i):  piv_i = W_{i+1} + sigma_i,  sigma_0 = lambda'_0 + W_0,
+//     sigma_i = lambda'_i + W_i sigma_{i-1} / piv_{i-1}.
+// The textbook form piv_i = delta_i - W_i^2 / piv_{i-1} subtracts numbers of
+// size W (~1e4 at nx = 1023, dT = 1/64) to leave sigma (~|lambda_k|^{1/2} W^{1/2}):
+// in FP64 that kept ~1e-11 of the smooth modes, and step (c) multiplies the
+// loss by up to alpha^{-(N-1)/N} (1e4 at alpha = 1e-4, N = 64): a 2e-9
+// relative error of one CGC application there; this form leaves 6e-12.
 template <typename T>
 __global__ void k_cgc_factors(const double* __restrict__ a, int64_t S, int nx, double wscale,
                               double dTreact, const double2* __restrict__ lam, int K,
@@ -94,24 +108,27 @@ __global__ void k_cgc_factors(const double* __restrict__ a, int64_t S, int nx, d
     int64_t s = t / K;
     int k = (int)(t - s * K);
     const double* as = a + s * (nx + 1);
-    double2 lk = lam[k];
-    double pr = 1.0, pi = 0.0;  // previous pivot
+    const double2 lk = lam[k];
     double wl = wscale * as[0];
+    double sr = 0.0, si = 0.0;   // sigma_{i-1}
+    double ir = 0.0, ii = 0.0;   // 1 / piv_{i-1}
     for (int i = 0; i < nx; ++i) {
-        double wr = wscale * as[i + 1];
-        double dr = lk.x + wl + wr + dTreact, di = lk.y;
-        if (ext) dr += dT * ext[s * nx + i];
-        if (i > 0) {
-            // piv_i = delta_i - wl^2 / piv_{i-1}
-            double den = pr * pr + pi * pi;
-            double q = wl * wl / den;
-            dr -= q * pr;
-            di += q * pi;
+        const double wr = wscale * as[i + 1];
+        double lr = lk.x + dTreact, li = lk.y;
+        if (ext) lr += dT * ext[s * nx + i];
+        if (i == 0) {
+            sr = lr + wl;
+            si = li;
+        } else {
+            // sigma_i = lambda'_i + wl * sigma_{i-1} / piv_{i-1}
+            const double qr = sr * ir - si * ii, qi = sr * ii + si * ir;
+            sr = lr + wl * qr;
+            si = li + wl * qi;
         }
-        pr = dr;
-        pi = di;
-        double den = pr * pr + pi * pi;
-        double ir = pr / den, ii = -pi / den;
+        const double pr = wr + sr, pi = si;  // piv_i
+        const double den = pr * pr + pi * pi;
+        ir = pr / den;
+        ii = -pi / den;
         int64_t o = (s * nx + i) * K + k;
         dinv[o] = Cplx<T>{(T)ir, (T)ii};
         double ur = (i + 1 < nx) ? -wr * ir : 0.0, ui = (i + 1 < nx) ? -wr * ii : 0.0;

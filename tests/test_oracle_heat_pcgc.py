@@ -280,3 +280,93 @@ def test_error_metrics_by_construction():
     assert np.allclose(mean_inf_error(Uref, Uref + D), t.mean(axis=0), rtol=1e-14)
     # rel_l2 of a uniform relative scaling is the scaling
     assert abs(rel_l2(1.25 * Uref, Uref) - 0.25) < 1e-14
+
+
+def _cgc_extended(op, r, dT, alpha):
+    """Steps (a)-(c) of the diagonalized CGC carried out in long double
+    (x86 80-bit or IEEE quad): the direct DFT with exponents reduced mod N,
+    a Thomas solve by divisions, the alpha^{+-j/N} scalings.  A reference for
+    the FP64 rounding, not a second oracle: it shares the three steps' algebra
+    (pinned by the dense Kronecker test) and differs in precision only."""
+    LD = np.longdouble
+    N, n = r.shape
+    j = np.arange(N)
+    two_pi = 2 * LD("3.141592653589793238462643383279502884")
+    ang = two_pi * (np.outer(j, j) % N).astype(LD) / LD(N)
+    Wr, Wi = np.cos(ang), np.sin(ang)                           # omega^{jk}
+    a = LD(alpha)
+    sc = a ** (j.astype(LD) / LD(N))
+    sr = sc[:, None] * r.astype(LD)
+    inv_sqrt_n = LD(1) / np.sqrt(LD(N))
+    pr, pi = (Wr.T @ sr) * inv_sqrt_n, -(Wi.T @ sr) * inv_sqrt_n   # F_N^* (Lambda r)
+    th = two_pi * j.astype(LD) / LD(N)
+    root = a ** (LD(1) / LD(N))
+    lr, li = 1 - root * np.cos(th), root * np.sin(th)            # lambda_k = 1 - a^{1/N} e^{-i th}
+    w = LD(dT) * op.wf.astype(LD)                                # dT a / h^2 at the n + 1 faces
+    c = LD(dT) * LD(op.reaction)
+    # Thomas over rows, vectorized over the N frequencies (complex as pairs)
+    yr, yi = np.empty((n, N), LD), np.empty((n, N), LD)
+    gr, gi = np.empty((n, N), LD), np.empty((n, N), LD)            # pivots
+    for i in range(n):
+        dr, di = lr + w[i] + w[i + 1] + c, li.copy()
+        br, bi = pr[:, i].copy(), pi[:, i].copy()
+        if i > 0:
+            den = gr[i - 1] ** 2 + gi[i - 1] ** 2
+            mr, mi = -w[i] * gr[i - 1] / den, w[i] * gi[i - 1] / den   # l = -w_i / piv_{i-1}
+            dr, di = dr + mr * w[i], di + mi * w[i]
+            br, bi = br - (mr * yr[i - 1] - mi * yi[i - 1]), bi - (mr * yi[i - 1] + mi * yr[i - 1])
+        gr[i], gi[i], yr[i], yi[i] = dr, di, br, bi
+    qr, qi = np.empty((n, N), LD), np.empty((n, N), LD)
+    xr, xi = np.zeros(N, LD), np.zeros(N, LD)
+    for i in range(n - 1, -1, -1):
+        tr, ti = yr[i] + w[i + 1] * xr, yi[i] + w[i + 1] * xi         # y_i - M_{i,i+1} x_{i+1}
+        if i == n - 1:
+            tr, ti = yr[i], yi[i]
+        den = gr[i] ** 2 + gi[i] ** 2
+        xr, xi = (tr * gr[i] + ti * gi[i]) / den, (ti * gr[i] - tr * gi[i]) / den
+        qr[i], qi[i] = xr, xi
+    # (c) u = Lambda^{-1} F_N q, real part
+    ur = (Wr @ qr.T - Wi @ qi.T) * inv_sqrt_n
+    return ((LD(1) / sc)[:, None] * ur).astype(np.float64)
+
+
+@pytest.mark.skipif(np.finfo(np.longdouble).eps > 1e-18,
+                    reason="long double is not wider than double on this host")
+def test_cgc_fp64_accuracy_at_alpha_1e4_against_extended_precision():
+    # Nx = 1023, N = 64, dT = 1/64, alpha = 1e-4: the shifted systems have
+    # dT a / h^2 ~ 1e4, and step (c) multiplies rounding by up to alpha^{-63/64}
+    # (Section 3.2, the paragraph on choosing alpha).  The oracle's FP64 result
+    # must be within 1e-11 (relative L2) of the same three steps in extended
+    # precision; without the refinement of step (b) it is off by ~3e-9.
+    from oracle import kl_input
+    nx, N, alpha = 1023, 64, 1e-4
+    dT = 1.0 / N
+    faces = (np.arange(nx + 1) + 0.5) / (nx + 1)
+    basis = kl_input.field_basis_1d(0.5, 0.5, 10, faces)
+    xi = np.random.default_rng(93).standard_normal(10)
+    op = heat1d.Heat1D(np.exp(kl_input.log_coefficient_1d(xi, basis)))
+    u0 = heat1d.u0_sine(nx)
+    U0 = pcgc.coarse_guess(op, u0, N, dT)
+    Fend = pcgc.fine_sweep(op, u0, U0, dT, 4)
+    r = pcgc.cgc_rhs(op, U0, pcgc.jump_b(op, Fend, U0, dT, alpha), dT)
+    ref = _cgc_extended(op, r, dT, alpha)
+    got = pcgc.cgc_diagonalized(op, r, dT, alpha)
+    d = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert d < 1e-11, d
+    # the extended evaluation itself agrees with the FP64 one where rounding is
+    # not amplified (the first coarse time), i.e. it computes the same thing
+    assert np.linalg.norm(got[0] - ref[0]) / np.linalg.norm(ref[0]) < 1e-14
+
+
+def test_refined_shifted_solve_residual_and_dense_agreement():
+    # the refined solve satisfies the system: dense LU on a small grid agrees,
+    # and the flux-form operator equals the matrix form (exact algebra)
+    op = _op(40, seed=3, reaction=0.4)
+    rng = np.random.default_rng(5)
+    R = rng.standard_normal((3, 40)) + 1j * rng.standard_normal((3, 40))
+    shift, scale = 0.2 - 0.3j, 0.05
+    X = op.shifted_solve_refined(shift, scale, R)
+    M = shift * np.eye(40) + scale * op.dense()
+    assert np.allclose(X, np.linalg.solve(M, R.T).T, rtol=1e-13, atol=1e-13)
+    V = rng.standard_normal((2, 40))
+    assert np.allclose(op.apply_flux(V), op.apply(V), rtol=1e-13, atol=1e-12)
