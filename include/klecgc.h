@@ -311,8 +311,9 @@ klecgc_status klecgc_reference(klecgc_ctx* ctx, const double* xi, int64_t S, int
  * the library, which every GPU that loads the library holds until exit.
  *   xi:    [S][M] FP64 device array; U_out: [S][N][nx] FP64 device array.
  *   Requires S * (6 nx + 5) <= 4194304 (32 MiB of doubles), else
- *   INVALID_ARG with the sizes in klecgc_last_error(); host arrays and a
- *   device other than the context's also give INVALID_ARG.
+ *   INVALID_ARG with the sizes in klecgc_last_error(); host arrays, arrays
+ *   on a device other than the context's, and a current device other than
+ *   the context's also give INVALID_ARG (managed arrays are accepted).
  * Allocates nothing (no cudaMalloc/cudaFree, no allocating library call).
  * 1D contexts only (UNSUPPORTED for dim = 2).
  * The first call on a device looks up the array's device address with

@@ -14,6 +14,7 @@
 
 #include "../../include/klecgc.h"
 #include "common.cuh"
+#include "ptr_rule.h"
 
 namespace klecgc {
 
@@ -44,13 +45,14 @@ cudaError_t scratch_address(int dev, double** out) {
     return cudaSuccess;
 }
 
-bool on_device(const void* p) {
+// true for device memory of device `dev` and for managed memory
+bool on_device(const void* p, int dev) {
     cudaPointerAttributes a;
     if (!p || cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    return device_array_usable((int)a.type, a.device, dev);
 }
 
 // N*J sequential backward-Euler steps per sample (one thread per sample), the
@@ -103,19 +105,24 @@ extern "C" klecgc_status klecgc_reference_noalloc(klecgc_ctx* ctx, const double*
         return fail_na(KLECGC_E_UNSUPPORTED,
                        "the allocation-free entry point takes the linear 1D problem only");
     if (S == 0) return KLECGC_OK;
-    if (!on_device(xi) || !on_device(U_out))
-        return fail_na(KLECGC_E_INVALID_ARG, "xi and U_out must be device arrays");
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess || dev != cv.device || dev >= kMaxDevices)
         return fail_na(KLECGC_E_INVALID_ARG, "the context's device must be current");
-    // scratch: fine factors [S][nx+1] (4 doubles each), field a [S][nx+1], state [nx][S]
-    const int64_t nf = cv.nx + 1;
-    const unsigned long long need = (unsigned long long)S * (unsigned long long)(5 * nf + cv.nx);
-    if (need > kScratchDoubles)
+    if (!on_device(xi, cv.device) || !on_device(U_out, cv.device))
         return fail_na(KLECGC_E_INVALID_ARG,
-                       "S * (6 nx + 5) = " + std::to_string(need) +
-                           " doubles exceeds the static scratch of " +
-                           std::to_string(kScratchDoubles) + " doubles (32 MiB)");
+                       "xi and U_out must be device (or managed) arrays of the context's device");
+    // scratch: fine factors [S][nx+1] (4 doubles each), field a [S][nx+1], state [nx][S]:
+    // S (6 nx + 5) doubles.  Compared as S against the largest admissible
+    // count, so that no product can wrap.
+    const int64_t nf = cv.nx + 1;
+    const int64_t per_sample = 5 * nf + cv.nx;
+    const int64_t s_max = (int64_t)(kScratchDoubles / (size_t)per_sample);
+    if (S > s_max)
+        return fail_na(KLECGC_E_INVALID_ARG,
+                       "S = " + std::to_string(S) + " at nx = " + std::to_string(cv.nx) +
+                           " exceeds the static scratch: S * (6 nx + 5) must be at most " +
+                           std::to_string(kScratchDoubles) + " doubles (32 MiB), S at most " +
+                           std::to_string(s_max));
     double* base = nullptr;
     cudaError_t e = scratch_address(dev, &base);
     if (e != cudaSuccess)

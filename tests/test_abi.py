@@ -3,6 +3,8 @@ every function declared in include/klecgc.h (no compute calls here)."""
 import os
 import re
 
+import pytest
+
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
@@ -174,3 +176,30 @@ def test_missing_library_fails_loudly(tmp_path):
     r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, cwd=ROOT,
                        timeout=120)
     assert r.returncode == 0 and r.stdout.strip() == "raised", r.stderr[-2000:]
+
+
+def test_noalloc_device_array_rule_on_the_host(tmp_path):
+    # the allocation-free entry point accepts device memory of the context's
+    # own device and managed memory only; an array on another GPU would make
+    # its kernel read that GPU's memory (a fault with peer access off).  The
+    # rule is plain host code, checked here with g++ and no GPU.
+    import shutil
+    import subprocess
+    gxx = shutil.which("g++")
+    if gxx is None:
+        pytest.skip("g++ not available")
+    src = tmp_path / "rule.cpp"
+    src.write_text(
+        '#include "ptr_rule.h"\n#include <cstdio>\n'
+        "int main() {\n"
+        "  using klecgc::device_array_usable;\n"
+        "  int ok = device_array_usable(2, 0, 0) && device_array_usable(2, 3, 3)\n"
+        "        && !device_array_usable(2, 1, 0) && !device_array_usable(2, 0, 1)\n"
+        "        && device_array_usable(3, 1, 0) && device_array_usable(3, -2, 0)\n"
+        "        && !device_array_usable(1, 0, 0) && !device_array_usable(0, 0, 0);\n"
+        '  std::printf("%d\\n", ok);\n  return ok ? 0 : 1;\n}\n')
+    exe = tmp_path / "rule"
+    csrc = os.path.join(ROOT, "paper_2510_26180_gb300", "csrc")
+    subprocess.run([gxx, "-std=c++17", "-I", csrc, str(src), "-o", str(exe)], check=True)
+    r = subprocess.run([str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0 and r.stdout.strip() == "1"
