@@ -5,9 +5,13 @@ field and factorizations, surrogate guess, then parareal iterations with the
 diagonalized CGC until every sample meets tol.  A sample counts as converged
 when it reached tol and its relative L2 distance to the FP64 sequential fine
 solution U* is <= 1e-6 (U* from the library's FP64 reference kernel, which the
-test-suite pins to the CPU oracle).
+test-suite pins to the CPU oracle; the CPU leg re-checks it and the timed
+result against the oracle's U* on four samples).  The default precision is
+the split the workload states: FP32 fine propagator, diagonalized CGC, update
+and norms in FP64 ("mixed"); the FP64 path and the FP32-defect CGC variant
+("mixed_defect") are measured on the same batch and reported beside it.
 
-  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed_defect]
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--precision mixed|mixed_defect|fp64]
   python bench.py --impl reference      (the CPU oracle on the host cores)
 
 Under torchrun (N > 1) every rank solves its own batch (different seed):
@@ -37,12 +41,15 @@ PRECISIONS = {"fp64": 0, "mixed": 1, "mixed_defect": 2}
 DTYPES = {"fp64": "f64", "mixed": "f32+f64", "mixed_defect": "f32+f64"}
 FP32_ALU_PEAK = 152 * 128 * 2 * 2.070e9 / 1e12   # TFLOP/s: SMs x FP32 lanes x FMA x max clock
 FP64_ALU_PEAK = 1.25                              # TFLOP/s, GB300 nominal FP64
-# DRAM bytes per point (read + write) of the mixed-defect kernels, from one ncu
-# capture each on 512 samples of heat1d_nx1023 (profiles/k_fine32_*.md,
-# profiles/k_cgc_*.md); the roofline's traffic scales them to a launch by its
-# points.  Valid while those kernels are unchanged.
-MEASURED_TRAFFIC_B_PER_POINT = {"fine": 241.90e6 / 33.52e6, "cgc_fwd": 1047.6e6 / 33.52e6,
-                                "cgc_solve": 725.9e6 / 33.52e6, "cgc_inv": 751.0e6 / 33.52e6}
+# DRAM bytes per point (read + write) per precision and kernel class, from one
+# ncu capture each (dram__bytes_read.sum + dram__bytes_write.sum) on 512
+# samples of heat1d_nx1023, divided by the points of the captured launch; the
+# roofline's traffic scales them to a launch by its points.  Valid while those
+# kernels are unchanged; a class without a capture reports traffic null.
+MEASURED_TRAFFIC_B_PER_POINT = {
+    "mixed_defect": {"fine": 241.90e6 / 33.52e6, "cgc_fwd": 1047.6e6 / 33.52e6,
+                     "cgc_solve": 725.9e6 / 33.52e6, "cgc_inv": 751.0e6 / 33.52e6},
+}
 
 
 METHOD2D = [0]   # the 2D solve method of this run (set in main)
@@ -232,10 +239,11 @@ def run_reference(args, w):
 
 # ---------------------------------------------------------------- GPU arm
 def traffic_per_launch(cls, prec, points, launches):
-    """Measured DRAM bytes per launch (mixed-defect kernels only), else None."""
-    if prec != "mixed_defect" or cls not in MEASURED_TRAFFIC_B_PER_POINT:
+    """Measured DRAM bytes per launch (classes with an ncu capture), else None."""
+    per_pt = MEASURED_TRAFFIC_B_PER_POINT.get(prec, {}).get(cls)
+    if per_pt is None:
         return None
-    return MEASURED_TRAFFIC_B_PER_POINT[cls] * points / max(launches, 1)
+    return per_pt * points / max(launches, 1)
 
 
 def roofline_2d(cls, ms, launches, units, prec, adv=False, band_nx=0):
@@ -304,26 +312,36 @@ def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
     row_steps = units["row_steps"]
     pts = units["points"]
     if cls == "fine":
-        if prec == "fp64":
-            flops = 5.0 * row_steps          # forward FMA; backward FMA + multiply
-            peak, unit = FP64_ALU_PEAK, "TFLOP/s"
-        else:
-            flops = 11.0 * row_steps         # flux rhs 5, forward 2, backward 3, update 1
-            peak, unit = FP32_ALU_PEAK, "TFLOP/s"
+        # the method's work per row and backward-Euler step of a tridiagonal
+        # solve with precomputed factors: forward substitution 1 FMA (2 flop),
+        # back substitution 1 FMA + 1 multiply (3 flop) = 5 flop, FP32 on the
+        # mixed paths, FP64 on the FP64 path (the kernels' increment form and
+        # flux right-hand sides are implementation, not counted)
+        flops = 5.0 * row_steps
+        peak = FP64_ALU_PEAK if prec == "fp64" else FP32_ALU_PEAK
         ach = flops / (ms / 1e3) / 1e12
-        return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": peak, "unit": unit,
+        return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": peak, "unit": "TFLOP/s",
                 "frac": ach / peak, "traffic": traffic_per_launch(cls, prec, pts, launches),
                 "peak_source": "derived: 152 SMs x lanes x 2 x 2070 MHz" if prec != "fp64"
                 else "nominal GB300 FP64 1.25 TFLOP/s",
-                "work": f"{flops / max(launches, 1):.3e} flop per launch"}
+                "work": f"{flops / max(launches, 1):.3e} flop per launch "
+                        f"(5 per row and fine step)"}
+    # algorithmic HBM bytes per point (per (sample, n, x)) of the CGC kernels;
+    # a spectrum value counts K/N per point (k <= N/2 only):
+    #   fp64          forward: r 8 in, p 16K/N out; inverse: q 16K/N, U 8 in + 8 out
+    #   mixed         forward: F increment 4, F accumulator 8 in + 8 out, U 8,
+    #                 p 16K/N; inverse: q 16K/N, U 8 + 8, FP32 increment 4
+    #   mixed_defect  the same with FP32 pairs (8 B) for U and F, FP32 spectra
+    #   solve         p in + out, dinv, lu: 4 spectra
+    if cls not in ("cgc_fwd", "cgc_solve", "cgc_inv"):
+        return None
     K = w.N // 2 + 1
     cb = 16 if prec != "mixed_defect" else 8      # complex value bytes
-    rb = 8 if prec != "mixed_defect" else 4       # r / d bytes
-    per_pt = {"cgc_fwd": rb + cb * K / w.N,
-              "cgc_solve": (2 * cb + 2 * cb) * K / w.N,
-              "cgc_inv": cb * K / w.N + 16}[cls] if cls in ("cgc_fwd", "cgc_solve", "cgc_inv") else None
-    if per_pt is None:
-        return None
+    spec = cb * K / w.N
+    per_pt = {"fp64": {"cgc_fwd": 8 + spec, "cgc_inv": spec + 16},
+              "mixed": {"cgc_fwd": 28 + spec, "cgc_inv": spec + 20},
+              "mixed_defect": {"cgc_fwd": 28 + spec, "cgc_inv": spec + 20}}[prec].get(cls,
+                                                                                     4 * spec)
     byts = per_pt * pts
     ach = byts / (ms / 1e3) / 1e9
     return {"kernel": cls, "bound": "hbm", "achieved": ach, "peak": hbm_peak, "unit": "GB/s",
@@ -544,29 +562,39 @@ def run_gpu(args, w):
     props = torch.cuda.get_device_properties(dev)
     uuid = getattr(props, "uuid", None)
     sampler = ClockSampler(f"GPU-{uuid}" if uuid is not None else str(local))
-    solver.profile_enable(True)
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
     # inputs smaller than L2 (129 MB): overwrite a 256 MB buffer between steps
     flush = None
     if S * w.N * ns * 8 * 4 < 2 * 129e6:
         flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for i in range(args.steps):
-        if flush is not None and i:
-            flush.fill_(i & 0xff)
-        step()
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if world > 1:
-        dist.barrier()
+
+    def timed(n_steps):
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for i in range(n_steps):
+            if flush is not None and i:
+                flush.fill_(i & 0xff)
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        return e0.elapsed_time(e1) / n_steps
+
+    # the timed region: the library as a caller runs it (parareal loop as a
+    # CUDA graph, no per-kernel events)
+    ms = timed(args.steps)
     clocks = sampler.stop()
+    kry = solver.krylov_stats() if (w.dim == 2 or w.reaction_kind) else (0, 0)
+    # the same number of steps again with CUDA events around every kernel
+    # launch (this drives the loop from the host): the kernel split, launch
+    # counts and per-kernel durations of the roofline
+    solver.profile_enable(True)
+    ms_prof = timed(args.steps)
     prof = solver.profile_read()
     solver.profile_enable(False)
-    kry = solver.krylov_stats() if (w.dim == 2 or w.reaction_kind) else (0, 0)
-    ms = e0.elapsed_time(e1) / args.steps
 
     # accuracy of the last timed step against U* (FP64 reference kernel)
     Uref = torch.empty_like(U)
@@ -602,28 +630,45 @@ def run_gpu(args, w):
            "h2d_bytes_per_step": int(xi_h.nbytes),
            "d2h_bytes_per_step": int(U_pin.numel() * 8 + 2 * 4 * S)}
 
-    # plain FP64 path on the same batch (the >= 5x comparison of the method's
-    # precision variants)
-    fp64 = None
-    if prec != "fp64" and not args.skip_fp64:
-        U64 = torch.empty_like(U)
-        it64 = torch.empty_like(it)
-        st64 = torch.empty_like(stt)
-        step("fp64", Uo=U64, ito=it64, sto=st64)
-        torch.cuda.synchronize()
-        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        f0.record(stream)
-        step("fp64", Uo=U64, ito=it64, sto=st64)
-        f1.record(stream)
-        torch.cuda.synchronize()
-        ms64 = f0.elapsed_time(f1)
-        err64 = ((U64 - Uref).flatten(1).norm(dim=1) / Uref.flatten(1).norm(dim=1)).cpu().numpy()
-        ok64 = int(((st64.cpu().numpy() == 0) & (err64 <= 1e-6)).sum())
-        fp64 = {"value": ok64 / (ms64 / 1e3), "ms_per_step": ms64,
-                "mean_iters": float(it64.cpu().numpy().mean()), "max_rel_err": float(err64.max()),
-                "speedup_of_headline": value / (ok64 * world / (ms64 / 1e3)) if ok64 else None}
-
+    # the other precision variants on the same batch: the plain FP64 path (the
+    # >= 5x comparison) and, beside the headline, the other mixed split; each
+    # one untimed warm-up solve and one timed solve, with its own kernel split
     hbm_peak, peak_kind = peaks()
+    variants = {}
+    if not args.skip_fp64:
+        for p in [q for q in ("mixed_defect", "mixed", "fp64") if q != prec]:
+            Uv, itv, stv = torch.empty_like(U), torch.empty_like(it), torch.empty_like(stt)
+            step(p, Uo=Uv, ito=itv, sto=stv)
+            torch.cuda.synchronize()
+            f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            f0.record(stream)
+            step(p, Uo=Uv, ito=itv, sto=stv)
+            f1.record(stream)
+            torch.cuda.synchronize()
+            msv = f0.elapsed_time(f1)
+            solver.profile_enable(True)      # kernel split: one more solve with events
+            step(p, Uo=Uv, ito=itv, sto=stv)
+            pv = {k: {"launches": v[0], "ms": v[1]} for k, v in solver.profile_read().items()
+                  if v[0]}
+            solver.profile_enable(False)
+            errv = ((Uv - Uref).flatten(1).norm(dim=1) / Uref.flatten(1).norm(dim=1)).cpu().numpy()
+            itsv = itv.cpu().numpy()
+            okv = int(((stv.cpu().numpy() == 0) & (errv <= 1e-6)).sum())
+            tv = sum(v["ms"] for v in pv.values()) or 1.0
+            for v in pv.values():
+                v["share"] = v["ms"] / tv
+            uv = {"row_steps": float(np.clip(itsv, 0, None).sum()) * w.N * ns * w.J,
+                  "points": float(np.clip(itsv, 0, None).sum()) * w.N * ns}
+            variants[p] = {
+                "value": okv * world / (msv / 1e3), "ms_per_step": msv, "converged": okv,
+                "mean_iters": float(itsv.mean()), "max_rel_err": float(errv.max()),
+                "headline_over_this": value / (okv * world / (msv / 1e3)) if okv else None,
+                "kernels": pv,
+                "rooflines": [r for r in (roofline_entry(k, pv[k]["ms"], pv[k]["launches"], uv,
+                                                         p, w, hbm_peak, peak_kind)
+                                          for k in pv) if r]}
+            del Uv
+
     units = {"row_steps": row_steps, "points": points, "ns": ns,
              "kry_fine": kry[0] * args.steps, "kry_cgc": kry[1] * args.steps,
              "fine_steps": float(np.clip(iters, 0, None).sum()) * w.N * w.J * args.steps,
@@ -635,6 +680,8 @@ def run_gpu(args, w):
     dom = max(kernels, key=lambda k: kernels[k]["ms"])
     roof = roofline_entry(dom, kernels[dom]["ms"], kernels[dom]["launches"], units, prec, w,
                           hbm_peak, peak_kind)
+    rooflines = [r for r in (roofline_entry(k, kernels[k]["ms"], kernels[k]["launches"], units,
+                                            prec, w, hbm_peak, peak_kind) for k in kernels) if r]
     launches = int(sum(v["launches"] for v in kernels.values()))
 
     cpu = None
@@ -651,6 +698,19 @@ def run_gpu(args, w):
                "sample": f"first {n_sub} of the {S} samples, Algorithm 2 from the oracle's own "
                          f"surrogate (set-up not timed)",
                "gpu_vs_oracle_max_rel": max(d), "equal_iters": f"{same_it}/{n_sub}"}
+        if w.dim == 1 and not w.reaction_kind:
+            # the samples are scored against U* of the library's FP64 reference
+            # kernel; here that U* and the timed result are checked against the
+            # oracle's own sequential fine solution on spread-out samples
+            Uref_h = Uref.cpu().numpy()
+            chk = sorted({0, S // 3, (2 * S) // 3, S - 1})
+            du, dg = [], []
+            for i in chk:
+                Uo = osetup.reference(xi_h[i]).reshape(Uref_h[i].shape)
+                du.append(float(np.linalg.norm(Uref_h[i] - Uo) / np.linalg.norm(Uo)))
+                dg.append(float(np.linalg.norm(U[i].cpu().numpy() - Uo) / np.linalg.norm(Uo)))
+            cpu["ustar_check"] = {"samples": chk, "reference_kernel_vs_oracle_max_rel": max(du),
+                                  "timed_result_vs_oracle_ustar_max_rel": max(dg)}
 
     line = {"metric": METRIC, "value": value, "unit": "samples/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max,
@@ -659,7 +719,11 @@ def run_gpu(args, w):
             "config": workload_desc(w, S, prec, args.overrides),
             "mean_iters": float(iters.mean()), "converged": n_ok, "samples": S,
             "max_rel_err": float(err.max()), "MQ": info.MQ, "P": info.P,
-            "fp64_path": fp64, "roofline": roof, "kernels": kernels, "cpu_baseline": cpu,
+            "loop": "CUDA graph (conditional WHILE node)",
+            "kernel_split": {"ms_per_step": ms_prof, "how": "the same steps again with CUDA "
+                             "events around each launch (host-driven loop)"},
+            "variants": variants, "roofline": roof, "rooflines": rooflines,
+            "kernels": kernels, "cpu_baseline": cpu,
             "e2e": e2e, "gpu_launches": launches, "clocks": clocks}
     if rank == 0:
         print(json.dumps(line))
@@ -910,7 +974,9 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="heat1d_nx1023")
-    ap.add_argument("--precision", default="mixed_defect", choices=list(PRECISIONS))
+    # default: the split the 1D mixed workload states (FP32 fine propagator;
+    # diagonalized CGC, update and norms in FP64)
+    ap.add_argument("--precision", default="mixed", choices=list(PRECISIONS))
     ap.add_argument("--samples", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")

@@ -428,6 +428,21 @@ klecgc_status klecgc_set_scratch_limit(klecgc_ctx* ctx, int64_t bytes);
  */
 klecgc_status klecgc_set_2d_method(klecgc_ctx* ctx, int32_t method);
 
+/*
+ * How the parareal iterations of Algorithms 1 and 2 (the loop that ends at
+ * the stopping rule of Step 3) are driven, for klecgc_solve and
+ * klecgc_solve_parareal: 0 (default) on the device, as a CUDA graph whose
+ * conditional WHILE node repeats one captured iteration while a sample is
+ * active and fewer than kmax iterations have run (no host round trip per
+ * iteration); 1 from the host, with a readback of the active count after
+ * each iteration.  Both launch the same kernels in the same order and give
+ * bitwise-equal results.  With CUDA-event timing enabled
+ * (klecgc_profile_enable(ctx, 1)) the host loop is used, since per-launch
+ * events cannot sit inside a graph loop.  klecgc_solve_batch always drives
+ * its classes from the host.  INVALID_ARG for another mode.
+ */
+klecgc_status klecgc_set_loop(klecgc_ctx* ctx, int32_t mode);
+
 /* Krylov iterations of the last 2D call (klecgc_solve, klecgc_fine_sweep,
  * klecgc_cgc_apply, klecgc_reference), summed over all linear systems, for
  * F and for the CGC solves; for the cubic reaction (reaction_kind 1) the

@@ -87,6 +87,7 @@ struct klecgc_ctx {
     int Kp = 0;
     int* tc_err = nullptr;     // set by the tensor-core guess when a wait timed out
     int method2d = 0;          // 2D linear solves: 0 auto, 1 Krylov, 2 banded LU
+    int loop_mode = 0;         // parareal loop: 0 CUDA graph (WHILE node), 1 host-driven
     std::map<std::string, DevBuf> ws;  // grow-only scratch
     size_t ws_limit = 0;               // bytes of scratch allowed (0: no limit)
     std::string ws_tag;                // appended to scratch names (one batch class each)
@@ -530,7 +531,7 @@ klecgc_status scale_tables(klecgc_ctx* ctx, int N, double alpha, cudaStream_t st
     std::vector<T> a(N), b(N);
     for (int j = 0; j < N; ++j) {
         a[j] = (T)std::pow(alpha, (double)j / N);
-        b[j] = (T)(std::pow(alpha, -(double)j / N) / (N / 2));
+        b[j] = (T)(std::pow(alpha, -(double)j / N) / (2 * N));  // 1/N and the transforms' 2 x 2
     }
     const char* n1 = sizeof(T) == 8 ? "scale64" : "scale32";
     const char* n2 = sizeof(T) == 8 ? "iscale64" : "iscale32";
@@ -1120,6 +1121,14 @@ klecgc_status klecgc_set_2d_method(klecgc_ctx* ctx, int32_t method) {
     if (method == 2 && (ctx->dim != 2 || ctx->nx > kBandMaxNx))
         return fail(KLECGC_E_UNSUPPORTED, "banded LU: 2D grids with nx <= 64");
     ctx->method2d = method;
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_set_loop(klecgc_ctx* ctx, int32_t mode) {
+    set_error("");
+    if (!ctx) return fail(KLECGC_E_INVALID_ARG, "NULL context");
+    if (mode != 0 && mode != 1) return fail(KLECGC_E_INVALID_ARG, "loop mode must be 0 or 1");
+    ctx->loop_mode = mode;
     return KLECGC_OK;
 }
 
@@ -1904,6 +1913,90 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
 
 namespace {
 
+struct PinnedInts {
+    int* p = nullptr;
+    ~PinnedInts() {
+        if (p) cudaFreeHost(p);
+    }
+};
+
+// Runs parareal iterations k0, k0 + 1, ... until no sample is active or kmax
+// iterations have run (Algorithms 1 and 2: the loop of Step 3).
+// iterate(stream, k, kdev) launches one iteration that ends with the stopping
+// rule counting the active samples into n_active; with kdev == nullptr the
+// iteration number is the host's k, otherwise it is *kdev on the device.
+// Loop mode 0 runs the iterations as a CUDA graph whose WHILE node repeats
+// the captured iteration while k_loop_tail finds active samples and k < kmax,
+// with no host round trip per iteration; loop mode 1, and CUDA-event timing
+// of the kernel classes (per-launch events cannot sit in a graph loop), run
+// them from the host with a readback of n_active after each.  The iteration
+// is captured once, on a private stream, and only launches kernels and
+// memsets.  If the graph cannot be built (before anything of it was
+// launched), the host loop runs instead.
+template <class It>
+klecgc_status iterate_loop(klecgc_ctx* ctx, cudaStream_t st, int* kdev, int* n_active, int k0,
+                           int kmax, It&& iterate) {
+    if (k0 >= kmax) return KLECGC_OK;
+    klecgc_status s;
+    if (ctx->loop_mode == 0 && !ctx->prof_timing) {
+        cudaGraph_t g = nullptr;
+        cudaGraphExec_t ex = nullptr;
+        cudaStream_t cs = nullptr;
+        bool built = false;
+        s = KLECGC_OK;
+        do {
+            if (cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking) != cudaSuccess) break;
+            if (cudaGraphCreate(&g, 0) != cudaSuccess) break;
+            cudaGraphConditionalHandle h;
+            if (cudaGraphConditionalHandleCreate(&h, g, 1, cudaGraphCondAssignDefault) != cudaSuccess)
+                break;
+            cudaGraphNodeParams np = {};
+            np.type = cudaGraphNodeTypeConditional;
+            np.conditional.handle = h;
+            np.conditional.type = cudaGraphCondTypeWhile;
+            np.conditional.size = 1;
+            cudaGraphNode_t node;
+            if (cudaGraphAddNode(&node, g, nullptr, nullptr, 0, &np) != cudaSuccess) break;
+            cudaGraph_t body = np.conditional.phGraph_out[0];
+            if (cudaStreamBeginCaptureToGraph(cs, body, nullptr, nullptr, 0,
+                                              cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+                break;
+            s = iterate(cs, k0, (const int*)kdev);
+            launch_loop_tail(kdev, n_active, kmax, h, cs);
+            cudaGraph_t captured = nullptr;
+            const cudaError_t ec = cudaStreamEndCapture(cs, &captured);
+            if (s != KLECGC_OK || ec != cudaSuccess) break;
+            if (cudaGraphInstantiate(&ex, g, 0) != cudaSuccess) break;
+            built = true;
+        } while (false);
+        if (built) {
+            launch_set_int(kdev, k0, st);
+            cudaError_t e = cudaGraphLaunch(ex, st);
+            cudaGraphExecDestroy(ex);   // released once the launch completes
+            cudaGraphDestroy(g);
+            cudaStreamDestroy(cs);
+            if (e != cudaSuccess) return fail(KLECGC_E_CUDA, cudaGetErrorString(e));
+            TRY(cudaGetLastError());
+            return KLECGC_OK;
+        }
+        if (ex) cudaGraphExecDestroy(ex);
+        if (g) cudaGraphDestroy(g);
+        if (cs) cudaStreamDestroy(cs);
+        if (s != KLECGC_OK) return s;
+        cudaGetLastError();   // graph not available: the host loop below
+    }
+    PinnedInts pin;
+    TRY(cudaMallocHost(&pin.p, sizeof(int)));
+    for (int k = k0; k < kmax; ++k) {
+        if ((s = iterate(st, k, (const int*)nullptr)) != KLECGC_OK) return s;
+        TRY(cudaGetLastError());
+        TRY(cudaMemcpyAsync(pin.p, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TRY(cudaStreamSynchronize(st));
+        if (*pin.p == 0) break;
+    }
+    return KLECGC_OK;
+}
+
 // Scratch names carry `tag` while a run's code executes.
 struct TagScope {
     klecgc_ctx* ctx;
@@ -1940,7 +2033,6 @@ struct SolveRun {
     Cplx<float>* p32 = nullptr;
     float* fout = nullptr;                     // mixed paths: FP32 fine result
     float* c32 = nullptr;                      // mixed paths: FP32 increment of U
-    double* Facc64[2] = {nullptr, nullptr};    // mixed: F(U_{n-1}) in FP64, two buffers
     float2* Facc2[2] = {nullptr, nullptr};     // defect: F(U_{n-1}) as pairs, two buffers
     float2* Udf = nullptr;                     // defect: the iterate as pairs (aliases U)
     int* ifail = nullptr;                      // 2D: Krylov cap flags and counters
@@ -1955,7 +2047,13 @@ struct SolveRun {
     int* h_active = nullptr;                   // pinned, one int (owned by the caller)
     int k_next = 0;
 
+    int* kdev = nullptr;                       // device iteration counter (graph loop)
+
     klecgc_status begin(const double* xi_d, const double* U_guess);
+    // one parareal iteration on stream `s`: the host's k, or *kdev when kdev
+    // is given (k then only tells k >= 1 from the first iteration)
+    klecgc_status iterate(cudaStream_t s, int k, const int* kd);
+    // host-driven: iteration k_next on st, active count copied to *h_active
     klecgc_status step();
     bool finished() const { return *h_active == 0 || k_next >= kmax; }
     klecgc_status finish(double* U_out, std::vector<int32_t>& hs, std::vector<int32_t>& hi,
@@ -2006,22 +2104,27 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
         WS(int32_t, sta, "status", S);
         WS(unsigned long long, de, "delta", S);
         WS(int, na, "n_active", 1);
+        WS(int, kd, "kdev", 1);
         active = a;
         iters = it;
         status = sta;
         delta = de;
         n_active = na;
+        kdev = kd;
     }
     TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
     TRY(cudaMemsetAsync(iters, 0xff, S * sizeof(int32_t), st));
     TRY(cudaMemsetAsync(status, 0, S * sizeof(int32_t), st));
     TRY(cudaMemsetAsync(delta, 0, S * sizeof(unsigned long long), st));
-    if (defect) {
+    if (defect || (!f64 && ctx->dim == 1)) {
         if ((s = scale_tables<float>(ctx, N, alpha, st, &sc32, &isc32)) != KLECGC_OK) return s;
-    } else {
+    }
+    if (!defect) {
         if ((s = scale_tables<double>(ctx, N, alpha, st, &sc64, &isc64)) != KLECGC_OK) return s;
     }
-    if (f64 || ctx->dim == 2) {
+    if (!defect) {
+        // FP64 path: the CGC right-hand side; mixed path (1D): its scaled
+        // FP64 accumulation
         WS(double, rr, "r", NS);
         r = rr;
     }
@@ -2045,11 +2148,6 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
             if (!guess_pairs)
                 ctx->launch(KLECGC_K_LAYOUT, st, [&] { launch_to_pairs(U, NS, st); });
             Udf = reinterpret_cast<float2*>(U);
-        } else {
-            WS(double, fa, "FaccA", NS);
-            WS(double, fb, "FaccB", NS);
-            Facc64[0] = fa;
-            Facc64[1] = fb;
         }
     }
     if (ctx->dim == 2) {
@@ -2082,8 +2180,14 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
 }
 
 klecgc_status SolveRun::step() {
+    klecgc_status s = iterate(st, k_next++, nullptr);
+    if (s != KLECGC_OK) return s;
+    TRY(cudaMemcpyAsync(h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
+    return KLECGC_OK;
+}
+
+klecgc_status SolveRun::iterate(cudaStream_t st, int k, const int* kd) {
     TagScope ts(ctx, tag);
-    const int k = k_next++;
     const double dTreact = dT * ctx->prob.reaction;
     if (ctx->dim == 2 && band) {
         const double dt = dT / J;
@@ -2124,7 +2228,6 @@ klecgc_status SolveRun::step() {
         });
         ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc64, U, 0, delta, nullptr, active, st); });
     } else {
-        const int cur = k & 1, prv = cur ^ 1;
         if (f64) {
             ctx->launch(KLECGC_K_FINE, st, [&] {
                 launch_fine_sweep_fp64(S, N, nx, J, dT, alpha, ctx->prob.reaction,
@@ -2140,14 +2243,13 @@ klecgc_status SolveRun::step() {
             });
             if (defect)
                 ctx->launch(KLECGC_K_CGC_FWD, st, [&] {
-                    launch_cgc_forward_df(S, N, nx, fout, k == 0 ? nullptr : Facc2[prv], Facc2[cur],
-                                          Udf, op.wT, dTreact, sc32, p32, active, st);
+                    launch_cgc_forward_df(S, N, nx, fout, Facc2[0], Facc2[1], k, kd, Udf, op.wT,
+                                          dTreact, sc32, p32, active, st);
                 });
             else
                 ctx->launch(KLECGC_K_CGC_FWD, st, [&] {
-                    launch_cgc_forward_mixed(S, N, nx, fout, k == 0 ? nullptr : Facc64[prv],
-                                             Facc64[cur], U, op.wT, dTreact, alpha, sc64, p64,
-                                             active, st);
+                    launch_cgc_forward_acc(S, N, nx, fout, k == 0 ? nullptr : c32, U, op.wT,
+                                           dTreact, alpha, sc64, sc32, r, p64, active, st);
                 });
         }
         if (!defect) {
@@ -2159,9 +2261,8 @@ klecgc_status SolveRun::step() {
         }
     }
     TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
-    ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
+    ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st, kd); });
     TRY(cudaGetLastError());
-    TRY(cudaMemcpyAsync(h_active, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
     return KLECGC_OK;
 }
 
@@ -2215,12 +2316,6 @@ klecgc_status status_summary(const std::vector<int32_t>& hs, bool capped) {
     return KLECGC_OK;
 }
 
-struct PinnedInts {
-    int* p = nullptr;
-    ~PinnedInts() {
-        if (p) cudaFreeHost(p);
-    }
-};
 
 // Algorithm 2 with the nonlinear CGC (reaction_kind 1 or 2, FP64): per
 // iteration, F by Newton steps and the jump b (k_fine_newton), then
@@ -2281,9 +2376,8 @@ klecgc_status solve_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S, do
     TRY(cudaMemsetAsync(status, 0, S * sizeof(int32_t), st));
     TRY(cudaMemsetAsync(delta, 0, S * sizeof(unsigned long long), st));
     TRY(cudaMemsetAsync(ifail, 0, S * sizeof(int), st));
-    PinnedInts pin;
-    TRY(cudaMallocHost(&pin.p, sizeof(int)));
-    for (int k = 0; k < kmax; ++k) {
+    WS(int, kdev, "kdev", 1);
+    auto iteration = [&](cudaStream_t st, int k, const int* kd) -> klecgc_status {
         ctx->launch(KLECGC_K_FINE, st, [&] {
             launch_fine_newton(kind, S, N, nx, J, dT, alpha, c, f0, 1, U, ctx->u0, wf, b, scr,
                                active, ifail, nits, st);
@@ -2306,12 +2400,10 @@ klecgc_status solve_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S, do
                 ctx->launch(KLECGC_K_CGC_INV, st, [&] { launch_cgc_inverse<double>(S, N, nx, p64, isc, ul, 2, nullptr, nullptr, active, st); });
         }
         TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
-        ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
-        TRY(cudaGetLastError());
-        TRY(cudaMemcpyAsync(pin.p, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-        TRY(cudaStreamSynchronize(st));
-        if (*pin.p == 0) break;
-    }
+        ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st, kd); });
+        return KLECGC_OK;
+    };
+    if ((s = iterate_loop(ctx, st, kdev, n_active, 0, kmax, iteration)) != KLECGC_OK) return s;
     if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) return s;
     hs.assign(S, 0);
     hi.assign(S, 0);
@@ -2372,9 +2464,8 @@ klecgc_status parareal_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S,
     TRY(cudaMemsetAsync(iters, 0xff, S * sizeof(int32_t), st));
     TRY(cudaMemsetAsync(status, 0, S * sizeof(int32_t), st));
     TRY(cudaMemsetAsync(ifail, 0, S * sizeof(int), st));
-    PinnedInts pin;
-    TRY(cudaMallocHost(&pin.p, sizeof(int)));
-    for (int k = 0; k < kmax; ++k) {
+    WS(int, kdev, "kdev", 1);
+    auto iteration = [&](cudaStream_t st, int k, const int* kd) -> klecgc_status {
         ctx->launch(KLECGC_K_FINE, st, [&] {
             launch_fine_newton(kind, S, N, nx, J, dT, 0.0, c, f0, 0, U, ctx->u0, wf, Fend, scr,
                                active, ifail, nits, st);
@@ -2384,12 +2475,10 @@ klecgc_status parareal_nonlinear(klecgc_ctx* ctx, const double* xi_d, int64_t S,
                                            delta, active, ifail, st);
         });
         TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
-        ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
-        TRY(cudaGetLastError());
-        TRY(cudaMemcpyAsync(pin.p, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-        TRY(cudaStreamSynchronize(st));
-        if (*pin.p == 0) break;
-    }
+        ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st, kd); });
+        return KLECGC_OK;
+    };
+    if ((s = iterate_loop(ctx, st, kdev, n_active, 0, kmax, iteration)) != KLECGC_OK) return s;
     if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) return s;
     hs.assign(S, 0);
     hi.assign(S, 0);
@@ -2472,11 +2561,15 @@ klecgc_status klecgc_solve(klecgc_ctx* ctx, const double* xi, int64_t S, double 
     run.tol = tol;
     run.h_active = pin.p;
     if ((s = run.begin(xi_d, U_guess)) != KLECGC_OK) return s;
-    while (true) {
-        if ((s = run.step()) != KLECGC_OK) return s;
-        TRY(cudaStreamSynchronize(st));
-        if (run.finished()) break;
-    }
+    // the first iteration differs (F of the start values, the right-hand side
+    // formed rather than accumulated): it runs on its own; iterations k >= 1
+    // are one repeated body
+    if ((s = run.iterate(st, 0, nullptr)) != KLECGC_OK) return s;
+    if ((s = iterate_loop(ctx, st, run.kdev, run.n_active, 1, kmax,
+                          [&](cudaStream_t cs, int k, const int* kd) {
+                              return run.iterate(cs, k, kd);
+                          })) != KLECGC_OK)
+        return s;
     std::vector<int32_t> hs, hi;
     bool capped = false;
     if ((s = run.finish(U_out, hs, hi, &capped)) != KLECGC_OK) return s;
@@ -2544,22 +2637,19 @@ klecgc_status klecgc_solve_parareal(klecgc_ctx* ctx, const double* xi, int64_t S
     TRY(cudaMemsetAsync(active, 0xff, S * sizeof(int), st));
     TRY(cudaMemsetAsync(iters, 0xff, S * sizeof(int32_t), st));
     TRY(cudaMemsetAsync(status, 0, S * sizeof(int32_t), st));
-    PinnedInts pin;
-    TRY(cudaMallocHost(&pin.p, sizeof(int)));
+    WS(int, kdev, "kdev", 1);
     const double dTf = dT * ctx->prob.forcing;
-    for (int k = 0; k < kmax; ++k) {
+    auto iteration = [&](cudaStream_t st, int k, const int* kd) -> klecgc_status {
         ctx->launch(KLECGC_K_FINE, st, [&] {
             launch_fine_sweep_fp64(S, N, nx, J, dT, 0.5, ctx->prob.reaction, ctx->prob.forcing, U,
                                    ctx->u0, op.f64, op.wT, F, active, st, 0);
         });
         ctx->launch(KLECGC_K_CGC_SOLVE, st, [&] { launch_parareal_correct(S, N, nx, dTf, ctx->u0, gc, F, U, scr, delta, active, st); });
         TRY(cudaMemsetAsync(n_active, 0, sizeof(int), st));
-        ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st); });
-        TRY(cudaGetLastError());
-        TRY(cudaMemcpyAsync(pin.p, n_active, sizeof(int), cudaMemcpyDeviceToHost, st));
-        TRY(cudaStreamSynchronize(st));
-        if (*pin.p == 0) break;
-    }
+        ctx->launch(KLECGC_K_CONV, st, [&] { launch_convergence(S, k, kmax, tol, delta, active, iters, status, n_active, st, kd); });
+        return KLECGC_OK;
+    };
+    if ((s = iterate_loop(ctx, st, kdev, n_active, 0, kmax, iteration)) != KLECGC_OK) return s;
     if ((s = export_batch(ctx, U, S, N, U_out, st)) != KLECGC_OK) return s;
     std::vector<int32_t> hs(S), hi(S);
     TRY(cudaMemcpyAsync(hs.data(), status, S * 4, cudaMemcpyDeviceToHost, st));

@@ -256,18 +256,23 @@ void launch_cgc_forward(int64_t S, int N, int nx, const TIN* r, const T* scale, 
 template <typename T, typename TW>
 void launch_cgc_solve(int64_t S, int K, int nx, const Cplx<T>* dinv, const Cplx<T>* lu,
                       const TW* wT, Cplx<T>* p, const int* active, cudaStream_t st);
-// Step (a) with the FP32 fine result folded in (mixed paths).  Facc_out =
+// Step (a) with the FP32 fine result folded in (defect path).  Facc_out =
 // Facc_in + fout (Facc_in null on the first iteration); then
-//  defect: d = (I + dT(A+cI)) (Facc_out - U) on pairs U, Facc (FP32 ops only);
-//  mixed:  r = (I + dT(A+cI)) Facc_out - prev in FP64.
-void launch_cgc_forward_df(int64_t S, int N, int nx, const float* fout, const float2* Facc_in,
-                           float2* Facc_out, const float2* Udf, const double* wT, double dTreact,
-                           const float* scale, Cplx<float>* p, const int* active,
-                           cudaStream_t st);
-void launch_cgc_forward_mixed(int64_t S, int N, int nx, const float* fout, const double* Facc_in,
-                              double* Facc_out, const double* U, const double* wT,
-                              double dTreact, double alpha, const double* scale,
-                              Cplx<double>* p, const int* active, cudaStream_t st);
+// d = (I + dT(A+cI)) (Facc_out - U) on pairs U, Facc (FP32 ops only).
+// Iteration k (kdev ? *kdev : k) reads F(U^{k-1}) from Facc[(k-1) & 1] (none at
+// k = 0) and writes F(U^k) to Facc[k & 1].
+void launch_cgc_forward_df(int64_t S, int N, int nx, const float* fout, float2* Facc0,
+                           float2* Facc1, int k, const int* kdev, const float2* Udf,
+                           const double* wT, double dTreact, const float* scale, Cplx<float>* p,
+                           const int* active, cudaStream_t st);
+// Step (a) for the mixed path: the CGC right-hand side accumulated in FP64,
+// pre-scaled (rs = alpha^{n/N} r): formed in FP64 from F(start) = fout when
+// c32 is NULL (first iteration), else incremented by the FP32 flux-form
+// (I + dT(A + cI)) F0(c_{n-1}) - c_{n-1}; then p = 2 DFT_n(rs).
+void launch_cgc_forward_acc(int64_t S, int N, int nx, const float* fout, const float* c32,
+                            const double* U, const double* wT, double dTreact, double alpha,
+                            const double* scale, const float* scale32, double* rs,
+                            Cplx<double>* p, const int* active, cudaStream_t st);
 // Step (c) + pair update (defect path): Udf += u, c32 = u, delta = max|u|.
 void launch_cgc_inverse_df(int64_t S, int N, int nx, const Cplx<float>* q, const float* iscale,
                            float2* Udf, unsigned long long* delta, float* c32, const int* active,
@@ -287,7 +292,12 @@ void launch_cgc_inverse(int64_t S, int N, int nx, const Cplx<T>* q, const T* isc
                         cudaStream_t st);
 void launch_convergence(int64_t S, int iter, int kmax, double tol, unsigned long long* delta,
                         int* active, int32_t* iters, int32_t* status, int* n_active,
-                        cudaStream_t st);
+                        cudaStream_t st, const int* kdev = nullptr);
+// Device-driven loop: the tail of a WHILE-node body (k += 1; continue while
+// any sample is active and k < kmax) and a one-value setter.
+void launch_loop_tail(int* kdev, const int* n_active, int kmax, cudaGraphConditionalHandle h,
+                      cudaStream_t st);
+void launch_set_int(int* p, int v, cudaStream_t st);
 // [S][A][B] -> [S][B][A] (FP64).
 void launch_transpose(const double* in, double* out, int64_t S, int A, int B, cudaStream_t st);
 

@@ -8,7 +8,9 @@
 // (The eigenvector matrix is Lambda_alpha^{-1} F_N: the printed Lambda_alpha F_N
 // does not diagonalize C_alpha.)  Real r makes p Hermitian, p_{N-k} = conj(p_k),
 // and since A is real the same holds for q, so only k = 0..N/2 are solved.
-// The 1/sqrt(N) factors of F_N and F_N^* are combined into one 1/N in (c).
+// The 1/sqrt(N) factors of F_N and F_N^* are combined into one 1/N in (c), and
+// the transforms' factors 2 (one each way) into 1/4 there: the inverse scale
+// table holds alpha^{-j/N} / (2N).
 //
 // Layouts: r, U: [S][nx][N]; p, q and the factors: [S][nx][K], K = N/2 + 1.
 #include <cmath>
@@ -106,8 +108,13 @@ __device__ __forceinline__ void cfft(T (&re)[L], T (&im)[L]) {
 
 constexpr int kTX = 32;  // x points per CTA in the transform kernels
 
-// Real DFT of one time series x[0..N-1] (unnormalized, sign -1) into
-// o[0..N/2]: complex FFT of the N/2 packed pairs, then the even/odd split.
+// Real DFT of one time series x[0..N-1] (unnormalized, sign -1), times 2,
+// into o[0..N/2]: complex FFT of the N/2 packed pairs z_m = x_2m + i x_2m+1,
+// then the even/odd split.  With E' = Z_k + conj Z_{L-k} and
+// O' = -i (Z_k - conj Z_{L-k}) (twice the even and odd spectra) and
+// w = e^{-2 pi i k/N}:  2 X_k = E' + w O'  and  2 X_{L-k} = conj(E' - w O'),
+// so one twiddle product serves both outputs of a mirrored pair.  The factor
+// 2 (and the inverse's) is removed by the inverse scale table (exact).
 template <typename T, int N>
 __device__ __forceinline__ void rfft_row(const T (&x)[N], Cplx<T>* o) {
     constexpr int L = N / 2;
@@ -118,19 +125,53 @@ __device__ __forceinline__ void rfft_row(const T (&x)[N], Cplx<T>* o) {
         zi[m] = x[2 * m + 1];
     }
     cfft<T, L, false>(zr, zi);
+    // k = 0 and k = L: E' = 2 Re Z_0, O' = 2 Im Z_0, w = 1 and -1
+    o[0] = Cplx<T>{(T)2 * (zr[0] + zi[0]), (T)0};
+    o[L] = Cplx<T>{(T)2 * (zr[0] - zi[0]), (T)0};
 #pragma unroll
-    for (int k = 0; k <= L; ++k) {
-        const int kk = k % L, km = (L - k) % L;
-        T Er = (T)0.5 * (zr[kk] + zr[km]), Ei = (T)0.5 * (zi[kk] - zi[km]);
-        T Or = (T)0.5 * (zi[kk] + zi[km]), Oi = (T)-0.5 * (zr[kk] - zr[km]);
-        T wr = (T)1, wi = (T)0;
-        if (k != 0) {
-            const int t = k * (kTwiddleN / N);
-            wr = tw_cos<T>(t);
-            wi = -tw_sin<T>(t);
-        }
-        o[k] = Cplx<T>{Er + wr * Or - wi * Oi, Ei + wr * Oi + wi * Or};
+    for (int k = 1; k <= L / 2; ++k) {
+        const int km = L - k;
+        const T Er = zr[k] + zr[km], Ei = zi[k] - zi[km];
+        const T Or = zi[k] + zi[km], Oi = zr[km] - zr[k];
+        const int t = k * (kTwiddleN / N);
+        const T wr = tw_cos<T>(t), wi = -tw_sin<T>(t);
+        const T tr = wr * Or - wi * Oi, ti = wr * Oi + wi * Or;
+        o[k] = Cplx<T>{Er + tr, Ei + ti};
+        if (km != k) o[km] = Cplx<T>{Er - tr, ti - Ei};
     }
+}
+
+// Inverse of rfft_row up to the scale table: X[0..L] (the k <= N/2 half of a
+// Hermitian spectrum) to the packed sequence, returned in zr/zi after the
+// length-L inverse FFT (4 L (x_2m + i x_2m+1) when X = 2 DFT(x)).
+// With E' = X_k + conj X_{L-k}, D' = X_k - conj X_{L-k}, O' = D' e^{+2 pi i k/N}:
+// Z'_k = E' + i O' and Z'_{L-k} = conj(E' - i O').
+template <typename T, int N>
+__device__ __forceinline__ void irfft_row(const Cplx<T>* X, T (&zr)[N / 2], T (&zi)[N / 2]) {
+    constexpr int L = N / 2;
+    {
+        const Cplx<T> A = X[0], B = X[L];
+        // k = 0: E' = A + conj B, D' = A - conj B (w = 1)
+        const T Er = A.x + B.x, Ei = A.y - B.y, Dr = A.x - B.x, Di = A.y + B.y;
+        zr[0] = Er - Di;
+        zi[0] = Ei + Dr;
+    }
+#pragma unroll
+    for (int k = 1; k <= L / 2; ++k) {
+        const int km = L - k;
+        const Cplx<T> A = X[k], B = X[km];
+        const T Er = A.x + B.x, Ei = A.y - B.y, Dr = A.x - B.x, Di = A.y + B.y;
+        const int t = k * (kTwiddleN / N);
+        const T wr = tw_cos<T>(t), wi = tw_sin<T>(t);
+        const T Or = Dr * wr - Di * wi, Oi = Dr * wi + Di * wr;
+        zr[k] = Er - Oi;
+        zi[k] = Ei + Or;
+        if (km != k) {
+            zr[km] = Er + Oi;
+            zi[km] = Or - Ei;
+        }
+    }
+    cfft<T, L, true>(zr, zi);
 }
 
 // (a) for the defect path, fused with the accumulation of F and the defect:
@@ -143,11 +184,17 @@ constexpr int kTXF = 64;  // x points (= threads) per CTA in the FP32 transform 
 
 template <int N>
 __global__ void __launch_bounds__(kTXF) k_cgc_forward_df(
-    int64_t S, int nx, const float* __restrict__ fout, const float2* __restrict__ Facc_in,
-    float2* __restrict__ Facc_out, const float2* __restrict__ Udf, const double* __restrict__ wT,
-    float dTreact, const float* __restrict__ scale, Cplx<float>* __restrict__ p,
+    int64_t S, int nx, const float* __restrict__ fout, float2* __restrict__ Facc0,
+    float2* __restrict__ Facc1, int k_host, const int* __restrict__ kdev,
+    const float2* __restrict__ Udf, const double* __restrict__ wT, float dTreact,
+    const float* __restrict__ scale, Cplx<float>* __restrict__ p,
     const int* __restrict__ active) {
     constexpr int K = N / 2 + 1;
+    // iteration k reads F(U^{k-1}) from buffer (k - 1) & 1 (none at k = 0)
+    // and writes F(U^k) to buffer k & 1
+    const int kit = kdev ? *kdev : k_host;
+    const float2* __restrict__ Facc_in = kit == 0 ? nullptr : ((kit & 1) ? Facc0 : Facc1);
+    float2* __restrict__ Facc_out = (kit & 1) ? Facc1 : Facc0;
     __shared__ float sD[kTXF + 2][N + 1];
     __shared__ float sw[kTXF + 1];
     __shared__ Cplx<float> sout[kTXF * K];
@@ -223,51 +270,92 @@ __global__ void __launch_bounds__(kTXF) k_cgc_forward_df(
     for (int e = tid; e < rows * K; e += kTXF) pout[e] = sout[e];
 }
 
-// (a) for the mixed path (FP64 CGC): F_new = F_old + fout (FP64),
-// r = (I + dT(A + cI)) F_new - prev, prev_0 = alpha U_{N-1}, prev_n = U_{n-1}.
+// (a) for the mixed path (FP32 fine propagator; CGC, update and norms in
+// FP64).  The CGC right-hand side is kept in FP64, pre-scaled by the step (a)
+// weights: rs_n = alpha^{n/N} r_n.
+//   first iteration (c32 == nullptr): r_n = (I + dT(A + cI)) F_n - prev_n with
+//     F = fout (F of the start values, FP32 storage), prev_0 = alpha U_{N-1},
+//     prev_n = U_{n-1}, formed in FP64;
+//   later iterations: F is affine, F(U^k_{n-1}) - F(U^{k-1}_{n-1}) = F0(c_{n-1})
+//     with c = U^k - U^{k-1} and fout = F0(c_{n-1}), so
+//       r^k_n - r^{k-1}_n = (I + dT(A + cI)) F0(c_{n-1}) - c_{n-1}  (c_{-1} := alpha c_{N-1}),
+//     an increment formed in FP32 flux form from the FP32 values it is made
+//     of and added to rs in FP64.
+// Then p = DFT_n(rs) (times 2, see rfft_row).  rs is updated in place (no
+// halo on rs); the halo rows of fout give the x-neighbours of the flux.
 template <int N>
-__global__ void __launch_bounds__(kTX) k_cgc_forward_mixed(
-    int64_t S, int nx, const float* __restrict__ fout, const double* __restrict__ Facc_in,
-    double* __restrict__ Facc_out, const double* __restrict__ U, const double* __restrict__ wT,
-    double dTreact, double alpha, const double* __restrict__ scale, Cplx<double>* __restrict__ p,
-    const int* __restrict__ active) {
+__global__ void __launch_bounds__(kTX) k_cgc_forward_acc(
+    int64_t S, int nx, const float* __restrict__ fout, const float* __restrict__ c32,
+    const double* __restrict__ U, const double* __restrict__ wT, double dTreact, double alpha,
+    const double* __restrict__ scale, const float* __restrict__ scale32, double* __restrict__ rs,
+    Cplx<double>* __restrict__ p, const int* __restrict__ active) {
     constexpr int K = N / 2 + 1;
-    __shared__ double sF[kTX + 2][N + 1];
+    // sF: fout rows x0-1 .. x0+rows (halo); sC: c rows; sR: rs (or U) rows.
+    // sout (the spectra of the tile) reuses sF + sC once every thread has
+    // formed its right-hand side.
+    constexpr int kFC = (kTX + 2) * (N + 1) + kTX * (N + 1);
+    constexpr int kOutF = 2 * kTX * K * 2;   // floats of kTX * K Cplx<double>
+    __shared__ __align__(16) float sFC[kFC > kOutF ? kFC : kOutF];
+    __shared__ double sR[kTX][N + 1];
     __shared__ double sw[kTX + 1];
-    __shared__ Cplx<double> sout[kTX * K];
+    float (*sF)[N + 1] = reinterpret_cast<float (*)[N + 1]>(sFC);
+    float (*sC)[N + 1] = reinterpret_cast<float (*)[N + 1]>(sFC + (kTX + 2) * (N + 1));
+    Cplx<double>* sout = reinterpret_cast<Cplx<double>*>(sFC);
     const int64_t s = blockIdx.x;
     if (!active[s]) return;
+    const bool first = c32 == nullptr;
     const int x0 = blockIdx.y * kTX;
     const int rows = min(kTX, nx - x0);
     const int tid = threadIdx.x;
     const int64_t base = s * (int64_t)nx * N;
     for (int e = tid; e < (rows + 2) * N; e += kTX) {
         const int row = e / N, col = e - row * N, x = x0 - 1 + row;
-        double F = 0.0;
-        if (x >= 0 && x < nx) {
-            const int64_t o = base + (int64_t)x * N + col;
-            F = (double)fout[o];
-            if (Facc_in) F += Facc_in[o];
-            if (row >= 1 && row <= rows) Facc_out[o] = F;
-        }
-        sF[row][col] = F;
+        sF[row][col] = (x >= 0 && x < nx) ? fout[base + (int64_t)x * N + col] : 0.f;
+    }
+    const double* own = (first ? U : rs) + base + (int64_t)x0 * N;
+    for (int e = tid; e < rows * N; e += kTX) {
+        const int row = e / N, col = e - row * N;
+        sR[row][col] = own[e];
+        if (!first) sC[row][col] = c32[base + (int64_t)x0 * N + e];
     }
     for (int e = tid; e <= rows; e += kTX) sw[e] = wT[s * (nx + 1) + x0 + e];
     __syncthreads();
+    double xs[N];
     if (tid < rows) {
         const double wl = sw[tid], wr = sw[tid + 1];
-        const double* Ux = U + base + (int64_t)(x0 + tid) * N;
-        double xs[N];
+        if (first) {
 #pragma unroll
-        for (int n = 0; n < N; ++n) {
-            const double F = sF[tid + 1][n];
-            const double prev = n == 0 ? alpha * Ux[N - 1] : Ux[n - 1];
-            const double r = F + wl * (F - sF[tid][n]) - wr * (sF[tid + 2][n] - F) + dTreact * F;
-            xs[n] = (r - prev) * scale[n];
+            for (int n = 0; n < N; ++n) {
+                const double F = sF[tid + 1][n];
+                const double Fm = sF[tid][n], Fp = sF[tid + 2][n];
+                const double prev = n == 0 ? alpha * sR[tid][N - 1] : sR[tid][n - 1];
+                const double r = F + wl * (F - Fm) - wr * (Fp - F) + dTreact * F;
+                xs[n] = scale[n] * (r - prev);
+            }
+        } else {
+            const float wlf = (float)wl, wrf = (float)wr, rf = (float)dTreact;
+            const float af = (float)alpha;
+#pragma unroll
+            for (int n = 0; n < N; ++n) {
+                const float D = sF[tid + 1][n];
+                const float prev = n == 0 ? af * sC[tid][N - 1] : sC[tid][n - 1];
+                const float d = D + wlf * (D - sF[tid][n]) - wrf * (sF[tid + 2][n] - D) + rf * D - prev;
+                xs[n] = sR[tid][n] + (double)(scale32[n] * d);
+            }
         }
+    }
+    __syncthreads();   // sF / sC are free: the spectra and rs go to shared memory
+    if (tid < rows) {
+#pragma unroll
+        for (int n = 0; n < N; ++n) sR[tid][n] = xs[n];
         rfft_row<double, N>(xs, sout + tid * K);
     }
     __syncthreads();
+    double* rout = rs + base + (int64_t)x0 * N;
+    for (int e = tid; e < rows * N; e += kTX) {
+        const int row = e / N, col = e - row * N;
+        rout[e] = sR[row][col];
+    }
     Cplx<double>* pout = p + (s * nx + x0) * (int64_t)K;
     for (int e = tid; e < rows * K; e += kTX) pout[e] = sout[e];
 }
@@ -283,30 +371,30 @@ __global__ void __launch_bounds__(kTX) k_cgc_forward_mixed(
         default: break;               \
     }
 
-void launch_cgc_forward_df(int64_t S, int N, int nx, const float* fout, const float2* Facc_in,
-                           float2* Facc_out, const float2* Udf, const double* wT, double dTreact,
-                           const float* scale, Cplx<float>* p, const int* active,
-                           cudaStream_t st) {
+void launch_cgc_forward_df(int64_t S, int N, int nx, const float* fout, float2* Facc0,
+                           float2* Facc1, int k, const int* kdev, const float2* Udf,
+                           const double* wT, double dTreact, const float* scale, Cplx<float>* p,
+                           const int* active, cudaStream_t st) {
     if (S == 0) return;
     dim3 grid((unsigned)S, (unsigned)((nx + kTXF - 1) / kTXF));
-#define KLECGC_FDF(NN)                                                                     \
-    k_cgc_forward_df<NN><<<grid, kTXF, 0, st>>>(S, nx, fout, Facc_in, Facc_out, Udf, wT,   \
+#define KLECGC_FDF(NN)                                                                          \
+    k_cgc_forward_df<NN><<<grid, kTXF, 0, st>>>(S, nx, fout, Facc0, Facc1, k, kdev, Udf, wT,   \
                                                (float)dTreact, scale, p, active)
     KLECGC_N_SWITCH(N, KLECGC_FDF)
 #undef KLECGC_FDF
 }
 
-void launch_cgc_forward_mixed(int64_t S, int N, int nx, const float* fout, const double* Facc_in,
-                              double* Facc_out, const double* U, const double* wT,
-                              double dTreact, double alpha, const double* scale,
-                              Cplx<double>* p, const int* active, cudaStream_t st) {
+void launch_cgc_forward_acc(int64_t S, int N, int nx, const float* fout, const float* c32,
+                            const double* U, const double* wT, double dTreact, double alpha,
+                            const double* scale, const float* scale32, double* rs,
+                            Cplx<double>* p, const int* active, cudaStream_t st) {
     if (S == 0) return;
     dim3 grid((unsigned)S, (unsigned)((nx + kTX - 1) / kTX));
-#define KLECGC_FMX(NN)                                                                        \
-    k_cgc_forward_mixed<NN><<<grid, kTX, 0, st>>>(S, nx, fout, Facc_in, Facc_out, U, wT,     \
-                                                  dTreact, alpha, scale, p, active)
-    KLECGC_N_SWITCH(N, KLECGC_FMX)
-#undef KLECGC_FMX
+#define KLECGC_FACC(NN)                                                                       \
+    k_cgc_forward_acc<NN><<<grid, kTX, 0, st>>>(S, nx, fout, c32, U, wT, dTreact, alpha, scale, \
+                                                scale32, rs, p, active)
+    KLECGC_N_SWITCH(N, KLECGC_FACC)
+#undef KLECGC_FACC
 }
 
 // (a): thread x of the tile transforms its own time series.
@@ -485,25 +573,8 @@ __global__ void __launch_bounds__(kTX) k_cgc_inverse(int64_t S, int nx,
     __syncthreads();
     unsigned long long dmax = 0ull;
     if (tid < rows) {
-        const Cplx<T>* X = sq + tid * K;
         T zr[L], zi[L];
-#pragma unroll
-        for (int k = 0; k < L; ++k) {
-            Cplx<T> A = X[k], B = X[L - k];
-            // E_k = (A + conj B)/2, O_k = (A - conj B) e^{+2 pi i k/N} / 2, Z_k = E_k + i O_k
-            T Er = (T)0.5 * (A.x + B.x), Ei = (T)0.5 * (A.y - B.y);
-            T Dr = (T)0.5 * (A.x - B.x), Di = (T)0.5 * (A.y + B.y);
-            T wr = (T)1, wi = (T)0;
-            if (k != 0) {
-                const int t = k * (kTwiddleN / N);
-                wr = tw_cos<T>(t);
-                wi = tw_sin<T>(t);
-            }
-            T Or = Dr * wr - Di * wi, Oi = Dr * wi + Di * wr;
-            zr[k] = Er - Oi;
-            zi[k] = Ei + Or;
-        }
-        cfft<T, L, true>(zr, zi);
+        irfft_row<T, N>(sq + tid * K, zr, zi);
 #pragma unroll
         for (int m = 0; m < L; ++m) {
             double u0 = (double)(zr[m] * iscale[2 * m]);
@@ -615,24 +686,8 @@ __global__ void __launch_bounds__(kTX) k_cgc_inverse_df(int64_t S, int nx,
     float umax = 0.f;
     bool bad = false;
     if (tid < rows) {
-        const Cplx<float>* X = sq + tid * K;
         float zr[L], zi[L];
-#pragma unroll
-        for (int k = 0; k < L; ++k) {
-            Cplx<float> A = X[k], B = X[L - k];
-            float Er = 0.5f * (A.x + B.x), Ei = 0.5f * (A.y - B.y);
-            float Dr = 0.5f * (A.x - B.x), Di = 0.5f * (A.y + B.y);
-            float wr = 1.f, wi = 0.f;
-            if (k != 0) {
-                const int t = k * (kTwiddleN / N);
-                wr = tw_cos<float>(t);
-                wi = tw_sin<float>(t);
-            }
-            float Or = Dr * wr - Di * wi, Oi = Dr * wi + Di * wr;
-            zr[k] = Er - Oi;
-            zi[k] = Ei + Or;
-        }
-        cfft<float, L, true>(zr, zi);
+        irfft_row<float, N>(sq + tid * K, zr, zi);
 #pragma unroll
         for (int m = 0; m < L; ++m) {
             const float u0 = zr[m] * iscale[2 * m], u1 = zi[m] * iscale[2 * m + 1];
@@ -717,10 +772,11 @@ void launch_pairs_transpose_out(const float2* in, double* out, int64_t S, int nx
 
 // Stopping rule per sample (Algorithm 2, Step 3): stop after the first
 // iteration whose increment max-norm is <= tol.
-__global__ void k_convergence(int64_t S, int iter, int kmax, double tol,
-                              unsigned long long* __restrict__ delta, int* __restrict__ active,
-                              int32_t* __restrict__ iters, int32_t* __restrict__ status,
-                              int* __restrict__ n_active) {
+__global__ void k_convergence(int64_t S, int iter_host, const int* __restrict__ kdev, int kmax,
+                              double tol, unsigned long long* __restrict__ delta,
+                              int* __restrict__ active, int32_t* __restrict__ iters,
+                              int32_t* __restrict__ status, int* __restrict__ n_active) {
+    const int iter = kdev ? *kdev : iter_host;
     int64_t s = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
     bool still = false;
     if (s < S && active[s]) {
@@ -748,11 +804,34 @@ __global__ void k_convergence(int64_t S, int iter, int kmax, double tol,
 
 void launch_convergence(int64_t S, int iter, int kmax, double tol, unsigned long long* delta,
                         int* active, int32_t* iters, int32_t* status, int* n_active,
-                        cudaStream_t st) {
+                        cudaStream_t st, const int* kdev) {
     if (S == 0) return;
-    k_convergence<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(S, iter, kmax, tol, delta, active,
-                                                                iters, status, n_active);
+    k_convergence<<<(unsigned)((S + 255) / 256), 256, 0, st>>>(S, iter, kdev, kmax, tol, delta,
+                                                                active, iters, status, n_active);
 }
+
+// End of one iteration of a device-driven parareal loop (the body of a CUDA
+// graph WHILE node): the iteration counter advances, and the loop continues
+// while some sample is active and fewer than kmax iterations have run.
+__global__ void k_loop_tail(int* __restrict__ kdev, const int* __restrict__ n_active, int kmax,
+                            cudaGraphConditionalHandle handle) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) {
+        const int k = *kdev + 1;
+        *kdev = k;
+        cudaGraphSetConditional(handle, (*n_active > 0 && k < kmax) ? 1u : 0u);
+    }
+}
+
+void launch_loop_tail(int* kdev, const int* n_active, int kmax, cudaGraphConditionalHandle h,
+                      cudaStream_t st) {
+    k_loop_tail<<<1, 32, 0, st>>>(kdev, n_active, kmax, h);
+}
+
+__global__ void k_set_int(int* p, int v) {
+    if (threadIdx.x == 0 && blockIdx.x == 0) *p = v;
+}
+
+void launch_set_int(int* p, int v, cudaStream_t st) { k_set_int<<<1, 32, 0, st>>>(p, v); }
 
 __global__ void k_transpose(const double* __restrict__ in, double* __restrict__ out, int A, int B) {
     __shared__ double tile[32][33];

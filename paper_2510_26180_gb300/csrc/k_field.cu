@@ -126,9 +126,9 @@ __global__ void k_cgc_factors(const double* __restrict__ a, int64_t S, int nx, d
             si = li + wl * qi;
         }
         const double pr = wr + sr, pi = si;  // piv_i
-        const double den = pr * pr + pi * pi;
-        ir = pr / den;
-        ii = -pi / den;
+        const double inv = 1.0 / (pr * pr + pi * pi);
+        ir = pr * inv;
+        ii = -pi * inv;
         int64_t o = (s * nx + i) * K + k;
         dinv[o] = Cplx<T>{(T)ir, (T)ii};
         double ur = (i + 1 < nx) ? -wr * ir : 0.0, ui = (i + 1 < nx) ? -wr * ii : 0.0;

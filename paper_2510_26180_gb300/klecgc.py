@@ -26,7 +26,8 @@ EXPORTS = ["klecgc_setup", "klecgc_solve", "klecgc_field", "klecgc_guess", "klec
            "klecgc_profile_read", "klecgc_reference_noalloc", "klecgc_mlp_set", "klecgc_mlp_get",
            "klecgc_mlp_loss_grad", "klecgc_mlp_train", "klecgc_mlp_guess", "klecgc_downsample",
            "klecgc_mlp_set_residual", "klecgc_mlp_targets",
-           "klecgc_set_krylov", "klecgc_set_2d_method", "klecgc_set_scratch_limit",
+           "klecgc_set_krylov", "klecgc_set_2d_method", "klecgc_set_loop",
+           "klecgc_set_scratch_limit",
            "klecgc_krylov_stats", "klecgc_save", "klecgc_load",
            "klecgc_solve_batch", "klecgc_solve_parareal", "klecgc_kl_basis",
            "klecgc_gpc_indices"]
@@ -111,6 +112,7 @@ def load() -> ctypes.CDLL:
         "klecgc_profile_read": [P, ctypes.POINTER(Profile)],
         "klecgc_set_krylov": [P, D, D, I32],
         "klecgc_set_2d_method": [P, I32],
+        "klecgc_set_loop": [P, I32],
         "klecgc_set_scratch_limit": [P, I64],
         "klecgc_solve_parareal": [P, P, I64, D, I32, I32, D, I32, I32, P, P, P, P, P],
         "klecgc_save": [P, ctypes.c_char_p],
@@ -311,6 +313,10 @@ class Solver:
     def set_scratch_limit(self, nbytes) -> int:
         """Budget for the context's device scratch in bytes (0: none)."""
         return _check(self.lib.klecgc_set_scratch_limit(self.h, int(nbytes)))
+
+    def set_loop(self, mode) -> int:
+        """Parareal loop: 0 CUDA graph with a WHILE node (default), 1 host-driven."""
+        return _check(self.lib.klecgc_set_loop(self.h, mode))
 
     def set_2d_method(self, method) -> int:
         """0 auto (banded LU in FP64 for nx <= 32), 1 Krylov, 2 banded LU (nx <= 64)."""
