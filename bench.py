@@ -720,6 +720,7 @@ def run_gpu(args, w):
             "mean_iters": float(iters.mean()), "converged": n_ok, "samples": S,
             "max_rel_err": float(err.max()), "MQ": info.MQ, "P": info.P,
             "loop": "CUDA graph (conditional WHILE node)",
+            "tuning": solver.tuning_report(),
             "kernel_split": {"ms_per_step": ms_prof, "how": "the same steps again with CUDA "
                              "events around each launch (host-driven loop)"},
             "variants": variants, "roofline": roof, "rooflines": rooflines,

@@ -443,6 +443,29 @@ klecgc_status klecgc_set_2d_method(klecgc_ctx* ctx, int32_t method);
  */
 klecgc_status klecgc_set_loop(klecgc_ctx* ctx, int32_t mode);
 
+/*
+ * Launch-shape autotuner (a library facility; the paper has no counterpart).
+ * mode 1 (default): the first solve of a context for a given (nx, N, J) on a
+ * given GPU times every candidate launch shape of the FP32 fine propagator
+ * (W warps per pair of intervals, R rows per lane, 32 W R >= nx + 1) on up
+ * to 512 of its samples and keeps the fastest; later solves reuse the choice.
+ * Every shape computes the same backward-Euler steps; the shapes split the
+ * rows of a system differently between lanes, so results agree to FP32
+ * rounding of the fine propagator, not bit for bit: a solve is reproducible
+ * for a fixed choice (pin it with cache_path).  mode 0: fixed rules, no
+ * timing.
+ * cache_path (may be NULL): a JSON file of the choices, read now and
+ * rewritten after every new choice, so that other processes and contexts can
+ * skip the timing.  INVALID_ARG for another mode.
+ */
+klecgc_status klecgc_set_tuning(klecgc_ctx* ctx, int32_t mode, const char* cache_path);
+
+/* The autotuner's choices as a JSON object of "<GPU>|<kernel>|nx=..|N=..|J=..":
+ * "<shape>" strings, NUL-terminated into buf (capacity bytes, truncated if
+ * short; buf may be NULL); *length receives the full length. */
+klecgc_status klecgc_tuning_report(const klecgc_ctx* ctx, char* buf, int64_t capacity,
+                                   int64_t* length);
+
 /* Krylov iterations of the last 2D call (klecgc_solve, klecgc_fine_sweep,
  * klecgc_cgc_apply, klecgc_reference), summed over all linear systems, for
  * F and for the CGC solves; for the cubic reaction (reaction_kind 1) the

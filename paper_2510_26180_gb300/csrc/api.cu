@@ -23,20 +23,6 @@ struct DevBuf {
     size_t bytes = 0;
 };
 
-static std::mutex g_tw_mutex;
-static std::map<int, bool> g_tw_done;
-
-static cudaError_t ensure_twiddles(int dev) {
-    std::lock_guard<std::mutex> lk(g_tw_mutex);
-    if (!g_tw_done[dev]) {
-        upload_twiddles();
-        cudaError_t e = cudaGetLastError();
-        if (e != cudaSuccess) return e;
-        g_tw_done[dev] = true;
-    }
-    return cudaSuccess;
-}
-
 // Learned-guess network M -> W -> W -> W -> D (D = 64 N), flat FP32 parameters
 // [W1, b1, W2, b2, W3, b3, W4, b4] with W_l stored [out][in].
 struct MlpState {
@@ -88,6 +74,12 @@ struct klecgc_ctx {
     int* tc_err = nullptr;     // set by the tensor-core guess when a wait timed out
     int method2d = 0;          // 2D linear solves: 0 auto, 1 Krylov, 2 banded LU
     int loop_mode = 0;         // parareal loop: 0 CUDA graph (WHILE node), 1 host-driven
+    // launch-shape autotuner: 1 times the candidate shapes once per problem
+    // shape (and GPU) and keeps the fastest; 0 uses the fixed rules
+    int tune_mode = 1;
+    std::map<std::string, std::string> tuned;   // key -> chosen shape
+    std::string tune_path;                      // JSON cache file ("" = none)
+    std::string gpu_name;                       // the device's name (tuner keys), read once
     std::map<std::string, DevBuf> ws;  // grow-only scratch
     size_t ws_limit = 0;               // bytes of scratch allowed (0: no limit)
     std::string ws_tag;                // appended to scratch names (one batch class each)
@@ -255,7 +247,8 @@ struct Operators {
     double* wT = nullptr;
     FineCoef64* f64 = nullptr;
     FineCoef32* f32 = nullptr;
-    void* tab32 = nullptr;
+    float* tab32 = nullptr;
+    Fine32wShape sh32{0, 0};
     Cplx<double>* dinv64 = nullptr;
     Cplx<double>* lu64 = nullptr;
     Cplx<float>* dinv32 = nullptr;
@@ -291,6 +284,140 @@ klecgc_status upload_lambda(klecgc_ctx* ctx, int N, double alpha, cudaStream_t s
 }
 
 // want_fine: 0 none, 1 FP64, 2 FP64+FP32; want_cgc: 0 none, 1 FP64, 2 FP32.
+// ---- launch-shape autotuner
+// Keys are "<GPU name>|<kernel>|nx=..|N=..|J=.."; values the chosen shape.
+// The cache file is a flat JSON object of such strings.
+std::string tune_key(klecgc_ctx* ctx, const char* kernel, int nx, int N, int J) {
+    if (ctx->gpu_name.empty()) {
+        cudaDeviceProp prop;
+        ctx->gpu_name = cudaGetDeviceProperties(&prop, ctx->device) == cudaSuccess ? prop.name : "?";
+    }
+    return ctx->gpu_name + "|" + kernel + "|nx=" + std::to_string(nx) + "|N=" +
+           std::to_string(N) + "|J=" + std::to_string(J);
+}
+
+std::string tune_json(const klecgc_ctx* ctx) {
+    std::string out = "{";
+    bool first = true;
+    for (auto& kv : ctx->tuned) {
+        out += first ? "\n" : ",\n";
+        out += "  \"" + kv.first + "\": \"" + kv.second + "\"";
+        first = false;
+    }
+    return out + (first ? "}" : "\n}");
+}
+
+// Reads "key": "value" pairs of a flat JSON object (the format tune_json writes).
+void tune_load(klecgc_ctx* ctx) {
+    if (ctx->tune_path.empty()) return;
+    FILE* f = std::fopen(ctx->tune_path.c_str(), "rb");
+    if (!f) return;
+    std::string txt;
+    char buf[4096];
+    size_t n;
+    while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, n);
+    std::fclose(f);
+    size_t pos = 0;
+    std::vector<std::string> strs;
+    while ((pos = txt.find('"', pos)) != std::string::npos) {
+        const size_t end = txt.find('"', pos + 1);
+        if (end == std::string::npos) break;
+        strs.push_back(txt.substr(pos + 1, end - pos - 1));
+        pos = end + 1;
+    }
+    for (size_t i = 0; i + 1 < strs.size(); i += 2) ctx->tuned[strs[i]] = strs[i + 1];
+}
+
+void tune_save(const klecgc_ctx* ctx) {
+    if (ctx->tune_path.empty()) return;
+    FILE* f = std::fopen(ctx->tune_path.c_str(), "wb");
+    if (!f) return;
+    const std::string j = tune_json(ctx);
+    std::fwrite(j.data(), 1, j.size(), f);
+    std::fclose(f);
+}
+
+// Launch shape of the FP32 fine propagator for (nx, N, J): with tuning on,
+// the first call for a shape times every candidate (W warps per pair of
+// intervals, R rows per lane) on up to 512 samples of this solve (F0 of zero
+// increments, in_mode 1: the work does not depend on the values) and keeps
+// the fastest; afterwards, and with tuning off, it is a lookup or the rule.
+klecgc_status choose_fine32w(klecgc_ctx* ctx, int64_t S, int N, int nx, int J, double dt,
+                             const double* a, const FineCoef64* f64, cudaStream_t st,
+                             Fine32wShape* out) {
+    // candidate W = 0: k_fine32 (one warp per pair of intervals, the factors
+    // in shared memory, R rows per lane by its own rule); W >= 1: k_fine32w
+    const int R0 = fine32_rows_per_lane(nx);
+    *out = {0, R0};
+    std::vector<Fine32wShape> cands;
+    if (R0) cands.push_back({0, R0});
+    for (const Fine32wShape& c : fine32w_candidates(nx)) cands.push_back(c);
+    if (ctx->tune_mode == 0 || cands.size() < 2 || S == 0) return KLECGC_OK;
+    const std::string key = tune_key(ctx, "fine32", nx, N, J);
+    auto decode = [&](const std::string& v, Fine32wShape* sh) {
+        int W = 0, R = 0;
+        if (std::sscanf(v.c_str(), "W%dR%d", &W, &R) == 2) {
+            *sh = {W, R};
+            return W == 0 ? R == R0 : fine32w_supported(*sh);
+        }
+        return false;
+    };
+    auto it = ctx->tuned.find(key);
+    if (it != ctx->tuned.end() && decode(it->second, out)) return KLECGC_OK;
+    const int64_t St = std::min<int64_t>(S, 512);
+    size_t tab = R0 ? fine_table32_bytes(St, R0) : 0;
+    for (auto& c : cands)
+        if (c.W) tab = std::max(tab, fine_table32w_bytes(St, c));
+    WS(float, tb, "tune_table", tab / sizeof(float));
+    WS(float, cz, "tune_c", St * (int64_t)nx * N);
+    WS(float, fo, "tune_out", St * (int64_t)nx * N);
+    WS(int, act, "tune_active", St);
+    TRY(cudaMemsetAsync(cz, 0, St * (int64_t)nx * N * sizeof(float), st));
+    TRY(cudaMemsetAsync(act, 0xff, St * sizeof(int), st));
+    cudaEvent_t e0, e1;
+    TRY(cudaEventCreate(&e0));
+    TRY(cudaEventCreate(&e1));
+    float best = 0.f;
+    Fine32wShape pick = *out;
+    auto run = [&](const Fine32wShape& c) {
+        if (c.W == 0)
+            launch_fine32(St, N, nx, J, dt, 0.0, 0.0, 1, nullptr, nullptr, ctx->u0, cz, tb, fo,
+                          act, st);
+        else
+            launch_fine32w(c, St, N, nx, J, dt, 0.0, 0.0, 1, nullptr, nullptr, ctx->u0, cz, tb,
+                           fo, act, st);
+    };
+    for (const Fine32wShape& c : cands) {
+        if (c.W == 0)
+            launch_fine_table32(a, St, nx, c.R, ctx->h, dt, ctx->prob.reaction, tb, st);
+        else
+            launch_fine_table32w(f64, St, nx, c, tb, st);
+        run(c);   // warm-up
+        cudaEventRecord(e0, st);
+        for (int r = 0; r < 2; ++r) run(c);
+        cudaEventRecord(e1, st);
+        float ms = 0.f;
+        cudaError_t e = cudaEventSynchronize(e1);
+        if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+        if (e != cudaSuccess) {
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+            return fail(KLECGC_E_CUDA, std::string("autotuner: ") + cudaGetErrorString(e));
+        }
+        if (best == 0.f || ms < best) {
+            best = ms;
+            pick = c;
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    TRY(cudaGetLastError());
+    *out = pick;
+    ctx->tuned[key] = "W" + std::to_string(pick.W) + "R" + std::to_string(pick.R);
+    tune_save(ctx);
+    return KLECGC_OK;
+}
+
 klecgc_status build_operators(klecgc_ctx* ctx, const double* xi_d, int64_t S, int N, int J,
                               double dT, double alpha, int want_fine, int want_cgc,
                               cudaStream_t st, Operators* op) {
@@ -307,11 +434,23 @@ klecgc_status build_operators(klecgc_ctx* ctx, const double* xi_d, int64_t S, in
         ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_factors(op->a, S, nx, ctx->h, dT / J, ctx->prob.reaction, f64, nullptr, st); });
         op->f64 = f64;
     } else if (want_fine == 2) {
-        const int R = fine32_rows_per_lane(nx);
-        if (R == 0) return fail(KLECGC_E_UNSUPPORTED, "mixed precision needs nx <= 2047");
-        WS(char, tb, "tab32", fine_table32_bytes(S, R));
-        ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_table32(op->a, S, nx, R, ctx->h, dT / J, ctx->prob.reaction, tb, st); });
+        // FP32 fine propagator: its factors in FP32, in the layout of the
+        // kernel and launch shape the autotuner (or the rule) picks
+        if (!fine32_rows_per_lane(nx))
+            return fail(KLECGC_E_UNSUPPORTED, "mixed precision needs nx <= 2047");
+        WS(FineCoef64, f64, "fine64", S * nf);
+        ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_factors(op->a, S, nx, ctx->h, dT / J, ctx->prob.reaction, f64, nullptr, st); });
+        Fine32wShape sh;
+        if ((s = choose_fine32w(ctx, S, N, nx, J, dT / J, op->a, f64, st, &sh)) != KLECGC_OK)
+            return s;
+        const size_t tbytes = sh.W ? fine_table32w_bytes(S, sh) : fine_table32_bytes(S, sh.R);
+        WS(float, tb, "tab32w", tbytes / sizeof(float));
+        if (sh.W)
+            ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_table32w(f64, S, nx, sh, tb, st); });
+        else
+            ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_table32(op->a, S, nx, sh.R, ctx->h, dT / J, ctx->prob.reaction, tb, st); });
         op->tab32 = tb;
+        op->sh32 = sh;
     }
     if (want_cgc) {
         std::vector<double2> lam;
@@ -979,7 +1118,6 @@ klecgc_status klecgc_load(const char* path, klecgc_ctx** out, void* stream) {
     ctx->kry_maxit = hd.kry_maxit;
     ctx->method2d = hd.method2d >= 0 && hd.method2d <= 2 ? hd.method2d : 0;
     ctx->mlp.residual = hd.mlp_residual == 1;
-    if (ensure_twiddles(ctx->device) != cudaSuccess) return bail(fail(KLECGC_E_CUDA, "twiddles"));
     const size_t NC = (size_t)ctx->ns * ctx->N;
     klecgc_status s;
     if ((s = get_dev(f, ctx, &ctx->basis, (size_t)ctx->M * ctx->nf)) != KLECGC_OK ||
@@ -1124,6 +1262,30 @@ klecgc_status klecgc_set_2d_method(klecgc_ctx* ctx, int32_t method) {
     return KLECGC_OK;
 }
 
+klecgc_status klecgc_set_tuning(klecgc_ctx* ctx, int32_t mode, const char* cache_path) {
+    set_error("");
+    if (!ctx) return fail(KLECGC_E_INVALID_ARG, "NULL context");
+    if (mode != 0 && mode != 1) return fail(KLECGC_E_INVALID_ARG, "tuning mode must be 0 or 1");
+    ctx->tune_mode = mode;
+    ctx->tune_path = cache_path ? cache_path : "";
+    tune_load(ctx);
+    return KLECGC_OK;
+}
+
+klecgc_status klecgc_tuning_report(const klecgc_ctx* ctx, char* buf, int64_t capacity,
+                                   int64_t* length) {
+    set_error("");
+    if (!ctx) return fail(KLECGC_E_INVALID_ARG, "NULL context");
+    const std::string j = tune_json(ctx);
+    if (length) *length = (int64_t)j.size();
+    if (buf && capacity > 0) {
+        const size_t n = std::min<size_t>(j.size(), (size_t)capacity - 1);
+        std::memcpy(buf, j.data(), n);
+        buf[n] = 0;
+    }
+    return KLECGC_OK;
+}
+
 klecgc_status klecgc_set_loop(klecgc_ctx* ctx, int32_t mode) {
     set_error("");
     if (!ctx) return fail(KLECGC_E_INVALID_ARG, "NULL context");
@@ -1213,7 +1375,6 @@ klecgc_status klecgc_setup(const klecgc_problem* pr, const double* xi_train, kle
         klecgc_status s_ = (expr);          \
         if (s_ != KLECGC_OK) return bail(s_); \
     } while (0)
-    STRY(ensure_twiddles(ctx->device));
     const int nx = ctx->nx, nf = ctx->nf, ns = ctx->ns, N = ctx->N, M = ctx->M, nt = pr->n_train;
     const int64_t NC = (int64_t)ns * N;
     const double pi = 3.14159265358979323846, h = ctx->h;
@@ -1797,8 +1958,8 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
                                ctx->u0, op.f64, op.wT, r, active, st);
     } else {
         WS(float, fo, "fout", S * (int64_t)nx * N);
-        launch_fine32(S, N, nx, J, dT / J, ctx->prob.reaction, ctx->prob.forcing, 0, U, nullptr,
-                      ctx->u0, nullptr, op.tab32, fo, active, st);
+        launch_fine_any(op.sh32, S, N, nx, J, dT / J, ctx->prob.reaction, ctx->prob.forcing, 0, U,
+                        nullptr, ctx->u0, nullptr, op.tab32, fo, active, st);
         launch_jump_from_f32(S, N, nx, alpha, dT * ctx->prob.reaction, fo, U, op.wT, r, st);
     }
     TRY(cudaGetLastError());
@@ -2237,7 +2398,7 @@ klecgc_status SolveRun::iterate(cudaStream_t st, int k, const int* kd) {
         } else {
             // F(start) on the first iteration, F0(increment) afterwards
             ctx->launch(KLECGC_K_FINE, st, [&] {
-                launch_fine32(S, N, nx, J, dT / J, ctx->prob.reaction, ctx->prob.forcing,
+                launch_fine_any(op.sh32, S, N, nx, J, dT / J, ctx->prob.reaction, ctx->prob.forcing,
                               k == 0 ? 0 : 1, defect ? nullptr : U, Udf, ctx->u0, c32, op.tab32,
                               fout, active, st);
             });

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <vector>
 
 namespace klecgc {
 
@@ -26,8 +27,6 @@ struct alignas(16) FineCoef32 {
     float l, dinv, wd, pad;
 };
 
-// cos/sin(2 pi t / 128) in constant memory (set once per device).
-void upload_twiddles();
 
 // Unevaluated sums of two floats (hi + lo, |lo| <= ulp(hi)/2): about 48-bit
 // values built from FP32 operations only (Knuth's TwoSum / Dekker's
@@ -110,6 +109,28 @@ void launch_fine32(int64_t S, int N, int nx, int J, double dt, double react, dou
                    int in_mode, const double* U64, const float2* Udf, const double* u0,
                    const float* c32, const void* table, float* fout, const int* active,
                    cudaStream_t st);
+// The same with every factor in registers: W warps per pair of intervals,
+// R rows per lane (32 W R >= nx + 1); the table is built from the FP64
+// factors of launch_fine_factors (fine step dt).
+struct Fine32wShape {
+    int W, R;
+};
+Fine32wShape fine32w_shape(int nx);
+std::vector<Fine32wShape> fine32w_candidates(int nx);
+bool fine32w_supported(Fine32wShape sh);
+size_t fine_table32w_bytes(int64_t S, Fine32wShape sh);
+void launch_fine_table32w(const FineCoef64* fc, int64_t S, int nx, Fine32wShape sh, float* table,
+                          cudaStream_t st);
+void launch_fine32w(Fine32wShape sh, int64_t S, int N, int nx, int J, double dt, double react,
+                    double forcing, int in_mode, const double* U64, const float2* Udf,
+                    const double* u0, const float* c32, const float* table, float* fout,
+                    const int* active, cudaStream_t st);
+// Either kernel: sh.W == 0 is k_fine32 (table of launch_fine_table32 with
+// sh.R rows per lane), sh.W >= 1 is k_fine32w.
+void launch_fine_any(Fine32wShape sh, int64_t S, int N, int nx, int J, double dt, double react,
+                     double forcing, int in_mode, const double* U64, const float2* Udf,
+                     const double* u0, const float* c32, const float* table, float* fout,
+                     const int* active, cudaStream_t st);
 // r = (I + dT(A + cI)) F - prev in FP64 from an FP32 F ([S][nx][N]).
 void launch_jump_from_f32(int64_t S, int N, int nx, double alpha, double dTreact, const float* F,
                           const double* U, const double* wT, double* r, cudaStream_t st);

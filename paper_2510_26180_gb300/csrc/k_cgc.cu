@@ -16,43 +16,29 @@
 #include <cmath>
 
 #include "common.cuh"
+#include "twiddles.h"
 
 namespace klecgc {
 
-__constant__ double c_cos64[kTwiddleN];
-__constant__ double c_sin64[kTwiddleN];
-__constant__ float c_cos32[kTwiddleN];
-__constant__ float c_sin32[kTwiddleN];
-
-void upload_twiddles() {
-    double c[kTwiddleN], s[kTwiddleN];
-    float cf[kTwiddleN], sf[kTwiddleN];
-    for (int t = 0; t < kTwiddleN; ++t) {
-        // exact values at the quarter points keep the trivial twiddles exact
-        double ang = 2.0 * 3.14159265358979323846 * t / kTwiddleN;
-        c[t] = (t == 32 || t == 96) ? 0.0 : std::cos(ang);
-        s[t] = (t == 0 || t == 64) ? 0.0 : std::sin(ang);
-        cf[t] = (float)c[t];
-        sf[t] = (float)s[t];
-    }
-    cudaMemcpyToSymbol(c_cos64, c, sizeof(c));
-    cudaMemcpyToSymbol(c_sin64, s, sizeof(s));
-    cudaMemcpyToSymbol(c_cos32, cf, sizeof(cf));
-    cudaMemcpyToSymbol(c_sin32, sf, sizeof(sf));
+// cos / sin (2 pi t / 128), t in [0, 128), from the first-quadrant literals
+// by symmetry.  Every caller passes a compile-time index (fully unrolled
+// loops), so each use folds to a literal: no table in memory.
+__host__ __device__ constexpr double tw_cos_d(int t) {
+    return t <= 32 ? twiddle_cos_q1(t)
+         : t <= 64 ? -twiddle_cos_q1(64 - t)
+         : t <= 96 ? -twiddle_cos_q1(t - 64)
+                   : twiddle_cos_q1(128 - t);
 }
-
+__host__ __device__ constexpr double tw_sin_d(int t) {
+    return t <= 32 ? twiddle_cos_q1(32 - t)
+         : t <= 64 ? twiddle_cos_q1(t - 32)
+         : t <= 96 ? -twiddle_cos_q1(96 - t)
+                   : -twiddle_cos_q1(t - 96);
+}
 template <typename T>
-__device__ __forceinline__ T tw_cos(int t);
+__device__ __forceinline__ T tw_cos(int t) { return (T)tw_cos_d(t); }
 template <typename T>
-__device__ __forceinline__ T tw_sin(int t);
-template <>
-__device__ __forceinline__ double tw_cos<double>(int t) { return c_cos64[t]; }
-template <>
-__device__ __forceinline__ double tw_sin<double>(int t) { return c_sin64[t]; }
-template <>
-__device__ __forceinline__ float tw_cos<float>(int t) { return c_cos32[t]; }
-template <>
-__device__ __forceinline__ float tw_sin<float>(int t) { return c_sin32[t]; }
+__device__ __forceinline__ T tw_sin(int t) { return (T)tw_sin_d(t); }
 
 template <int L>
 __host__ __device__ constexpr int bitrev(int i) {
@@ -93,6 +79,10 @@ __device__ __forceinline__ void cfft(T (&re)[L], T (&im)[L]) {
                 if (k == 0) {
                     xr = re[i1];
                     xi = im[i1];
+                } else if (t == kTwiddleN / 4) {
+                    // w = -i (forward) or +i (inverse): a swap and a sign
+                    xr = INV ? -im[i1] : im[i1];
+                    xi = INV ? re[i1] : -re[i1];
                 } else {
                     xr = re[i1] * wr - im[i1] * wi;
                     xi = re[i1] * wi + im[i1] * wr;
@@ -134,8 +124,15 @@ __device__ __forceinline__ void rfft_row(const T (&x)[N], Cplx<T>* o) {
         const T Er = zr[k] + zr[km], Ei = zi[k] - zi[km];
         const T Or = zi[k] + zi[km], Oi = zr[km] - zr[k];
         const int t = k * (kTwiddleN / N);
-        const T wr = tw_cos<T>(t), wi = -tw_sin<T>(t);
-        const T tr = wr * Or - wi * Oi, ti = wr * Oi + wi * Or;
+        T tr, ti;
+        if (t == kTwiddleN / 4) {   // w = -i
+            tr = Oi;
+            ti = -Or;
+        } else {
+            const T wr = tw_cos<T>(t), wi = -tw_sin<T>(t);
+            tr = wr * Or - wi * Oi;
+            ti = wr * Oi + wi * Or;
+        }
         o[k] = Cplx<T>{Er + tr, Ei + ti};
         if (km != k) o[km] = Cplx<T>{Er - tr, ti - Ei};
     }
@@ -162,8 +159,15 @@ __device__ __forceinline__ void irfft_row(const Cplx<T>* X, T (&zr)[N / 2], T (&
         const Cplx<T> A = X[k], B = X[km];
         const T Er = A.x + B.x, Ei = A.y - B.y, Dr = A.x - B.x, Di = A.y + B.y;
         const int t = k * (kTwiddleN / N);
-        const T wr = tw_cos<T>(t), wi = tw_sin<T>(t);
-        const T Or = Dr * wr - Di * wi, Oi = Dr * wi + Di * wr;
+        T Or, Oi;
+        if (t == kTwiddleN / 4) {   // w = +i
+            Or = -Di;
+            Oi = Dr;
+        } else {
+            const T wr = tw_cos<T>(t), wi = tw_sin<T>(t);
+            Or = Dr * wr - Di * wi;
+            Oi = Dr * wi + Di * wr;
+        }
         zr[k] = Er - Oi;
         zi[k] = Ei + Or;
         if (km != k) {
@@ -290,17 +294,10 @@ __global__ void __launch_bounds__(kTX) k_cgc_forward_acc(
     const double* __restrict__ scale, const float* __restrict__ scale32, double* __restrict__ rs,
     Cplx<double>* __restrict__ p, const int* __restrict__ active) {
     constexpr int K = N / 2 + 1;
-    // sF: fout rows x0-1 .. x0+rows (halo); sC: c rows; sR: rs (or U) rows.
-    // sout (the spectra of the tile) reuses sF + sC once every thread has
-    // formed its right-hand side.
-    constexpr int kFC = (kTX + 2) * (N + 1) + kTX * (N + 1);
-    constexpr int kOutF = 2 * kTX * K * 2;   // floats of kTX * K Cplx<double>
-    __shared__ __align__(16) float sFC[kFC > kOutF ? kFC : kOutF];
-    __shared__ double sR[kTX][N + 1];
+    // fout rows x0-1 .. x0+rows (the x-neighbours of the flux form); every
+    // other row a thread touches is its own and is accessed directly
+    __shared__ float sF[kTX + 2][N + 1];
     __shared__ double sw[kTX + 1];
-    float (*sF)[N + 1] = reinterpret_cast<float (*)[N + 1]>(sFC);
-    float (*sC)[N + 1] = reinterpret_cast<float (*)[N + 1]>(sFC + (kTX + 2) * (N + 1));
-    Cplx<double>* sout = reinterpret_cast<Cplx<double>*>(sFC);
     const int64_t s = blockIdx.x;
     if (!active[s]) return;
     const bool first = c32 == nullptr;
@@ -312,52 +309,39 @@ __global__ void __launch_bounds__(kTX) k_cgc_forward_acc(
         const int row = e / N, col = e - row * N, x = x0 - 1 + row;
         sF[row][col] = (x >= 0 && x < nx) ? fout[base + (int64_t)x * N + col] : 0.f;
     }
-    const double* own = (first ? U : rs) + base + (int64_t)x0 * N;
-    for (int e = tid; e < rows * N; e += kTX) {
-        const int row = e / N, col = e - row * N;
-        sR[row][col] = own[e];
-        if (!first) sC[row][col] = c32[base + (int64_t)x0 * N + e];
-    }
     for (int e = tid; e <= rows; e += kTX) sw[e] = wT[s * (nx + 1) + x0 + e];
     __syncthreads();
+    if (tid >= rows) return;
+    const int64_t row = s * (int64_t)nx + x0 + tid;
+    const double wl = sw[tid], wr = sw[tid + 1];
     double xs[N];
-    if (tid < rows) {
-        const double wl = sw[tid], wr = sw[tid + 1];
-        if (first) {
+    if (first) {
+        const double* Ur = U + row * N;
 #pragma unroll
-            for (int n = 0; n < N; ++n) {
-                const double F = sF[tid + 1][n];
-                const double Fm = sF[tid][n], Fp = sF[tid + 2][n];
-                const double prev = n == 0 ? alpha * sR[tid][N - 1] : sR[tid][n - 1];
-                const double r = F + wl * (F - Fm) - wr * (Fp - F) + dTreact * F;
-                xs[n] = scale[n] * (r - prev);
-            }
-        } else {
-            const float wlf = (float)wl, wrf = (float)wr, rf = (float)dTreact;
-            const float af = (float)alpha;
+        for (int n = 0; n < N; ++n) {
+            const double F = sF[tid + 1][n];
+            const double Fm = sF[tid][n], Fp = sF[tid + 2][n];
+            const double prev = n == 0 ? alpha * Ur[N - 1] : Ur[n - 1];
+            const double r = F + wl * (F - Fm) - wr * (Fp - F) + dTreact * F;
+            xs[n] = scale[n] * (r - prev);
+        }
+    } else {
+        const float* cr = c32 + row * N;
+        const double* rr = rs + row * N;
+        const float wlf = (float)wl, wrf = (float)wr, rf = (float)dTreact;
+        const float af = (float)alpha;
 #pragma unroll
-            for (int n = 0; n < N; ++n) {
-                const float D = sF[tid + 1][n];
-                const float prev = n == 0 ? af * sC[tid][N - 1] : sC[tid][n - 1];
-                const float d = D + wlf * (D - sF[tid][n]) - wrf * (sF[tid + 2][n] - D) + rf * D - prev;
-                xs[n] = sR[tid][n] + (double)(scale32[n] * d);
-            }
+        for (int n = 0; n < N; ++n) {
+            const float D = sF[tid + 1][n];
+            const float prev = n == 0 ? af * cr[N - 1] : cr[n - 1];
+            const float d = D + wlf * (D - sF[tid][n]) - wrf * (sF[tid + 2][n] - D) + rf * D - prev;
+            xs[n] = rr[n] + (double)(scale32[n] * d);
         }
     }
-    __syncthreads();   // sF / sC are free: the spectra and rs go to shared memory
-    if (tid < rows) {
+    double* rw = rs + row * N;
 #pragma unroll
-        for (int n = 0; n < N; ++n) sR[tid][n] = xs[n];
-        rfft_row<double, N>(xs, sout + tid * K);
-    }
-    __syncthreads();
-    double* rout = rs + base + (int64_t)x0 * N;
-    for (int e = tid; e < rows * N; e += kTX) {
-        const int row = e / N, col = e - row * N;
-        rout[e] = sR[row][col];
-    }
-    Cplx<double>* pout = p + (s * nx + x0) * (int64_t)K;
-    for (int e = tid; e < rows * K; e += kTX) pout[e] = sout[e];
+    for (int n = 0; n < N; ++n) rw[n] = xs[n];
+    rfft_row<double, N>(xs, p + row * K);
 }
 
 #define KLECGC_N_SWITCH(N, CALL)      \
@@ -397,35 +381,25 @@ void launch_cgc_forward_acc(int64_t S, int N, int nx, const float* fout, const f
 #undef KLECGC_FACC
 }
 
-// (a): thread x of the tile transforms its own time series.
+// (a): thread x transforms its own time series (the row r[s][x][.] is
+// contiguous, and so is its spectrum row): direct loads and stores, no
+// shared memory.
 template <typename T, typename TIN, int N>
 __global__ void __launch_bounds__(kTX) k_cgc_forward(int64_t S, int nx, const TIN* __restrict__ r,
                                                      const T* __restrict__ scale,
                                                      Cplx<T>* __restrict__ p,
                                                      const int* __restrict__ active) {
     constexpr int K = N / 2 + 1;
-    __shared__ T sin_[kTX][N + 1];
-    __shared__ Cplx<T> sout[kTX * K];
     const int64_t s = blockIdx.x;
     if (!active[s]) return;
-    const int x0 = blockIdx.y * kTX;
-    const int rows = min(kTX, nx - x0);
-    const int tid = threadIdx.x;
-    const TIN* rin = r + (s * nx + x0) * (int64_t)N;
-    for (int e = tid; e < rows * N; e += kTX) {
-        int row = e / N, col = e - row * N;
-        sin_[row][col] = (T)rin[e] * scale[col];
-    }
-    __syncthreads();
-    if (tid < rows) {
-        T xs[N];
+    const int x = blockIdx.y * kTX + threadIdx.x;
+    if (x >= nx) return;
+    const int64_t row = s * nx + x;
+    const TIN* rin = r + row * N;
+    T xs[N];
 #pragma unroll
-        for (int n = 0; n < N; ++n) xs[n] = sin_[tid][n];
-        rfft_row<T, N>(xs, sout + tid * K);
-    }
-    __syncthreads();
-    Cplx<T>* pout = p + (s * nx + x0) * (int64_t)K;
-    for (int e = tid; e < rows * K; e += kTX) pout[e] = sout[e];
+    for (int n = 0; n < N; ++n) xs[n] = (T)rin[n] * scale[n];
+    rfft_row<T, N>(xs, p + row * K);
 }
 
 template <typename T, typename TIN>
@@ -544,7 +518,13 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
     return (unsigned long long)__double_as_longlong(fabs(v));
 }
 
-// (c) + update + increment norm.
+// (c) + update + increment norm.  Thread x of the tile transforms its own
+// spectrum row, read directly (read-only, contiguous); U and the FP32
+// increments pass through shared memory so that their global reads and
+// writes are coalesced (a thread's own rows read and written in place would
+// serialize each load behind the store before it).
+// mode 0: U = u, c32 = u - U_old, delta = max |u - U_old|;
+// mode 1: U += u, c32 = u, delta = max |u|;  mode 2: U = u.
 template <typename T, int N>
 __global__ void __launch_bounds__(kTX) k_cgc_inverse(int64_t S, int nx,
                                                      const Cplx<T>* __restrict__ q,
@@ -554,7 +534,6 @@ __global__ void __launch_bounds__(kTX) k_cgc_inverse(int64_t S, int nx,
                                                      float* __restrict__ c32,
                                                      const int* __restrict__ active) {
     constexpr int L = N / 2, K = N / 2 + 1;
-    __shared__ Cplx<T> sq[kTX * K];
     __shared__ double su[kTX][N + 1];
     __shared__ float sc[kTX][N + 1];
     const int64_t s = blockIdx.x;
@@ -562,25 +541,23 @@ __global__ void __launch_bounds__(kTX) k_cgc_inverse(int64_t S, int nx,
     const int x0 = blockIdx.y * kTX;
     const int rows = min(kTX, nx - x0);
     const int tid = threadIdx.x;
-    const Cplx<T>* qin = q + (s * nx + x0) * (int64_t)K;
-    for (int e = tid; e < rows * K; e += kTX) sq[e] = qin[e];
     double* Ut = U + (s * nx + x0) * (int64_t)N;
     if (mode != 2)
         for (int e = tid; e < rows * N; e += kTX) {
-            int row = e / N, col = e - row * N;
+            const int row = e / N, col = e - row * N;
             su[row][col] = Ut[e];
         }
     __syncthreads();
     unsigned long long dmax = 0ull;
     if (tid < rows) {
         T zr[L], zi[L];
-        irfft_row<T, N>(sq + tid * K, zr, zi);
+        irfft_row<T, N>(q + (s * nx + x0 + tid) * (int64_t)K, zr, zi);
 #pragma unroll
         for (int m = 0; m < L; ++m) {
-            double u0 = (double)(zr[m] * iscale[2 * m]);
-            double u1 = (double)(zi[m] * iscale[2 * m + 1]);
+            const double u0 = (double)(zr[m] * iscale[2 * m]);
+            const double u1 = (double)(zi[m] * iscale[2 * m + 1]);
             if (mode == 0) {
-                double c0 = u0 - su[tid][2 * m], c1 = u1 - su[tid][2 * m + 1];
+                const double c0 = u0 - su[tid][2 * m], c1 = u1 - su[tid][2 * m + 1];
                 dmax = max(dmax, abs_bits(c0));
                 dmax = max(dmax, abs_bits(c1));
                 sc[tid][2 * m] = (float)c0;
@@ -602,13 +579,13 @@ __global__ void __launch_bounds__(kTX) k_cgc_inverse(int64_t S, int nx,
     }
     __syncthreads();
     for (int e = tid; e < rows * N; e += kTX) {
-        int row = e / N, col = e - row * N;
+        const int row = e / N, col = e - row * N;
         Ut[e] = su[row][col];
     }
     if (mode != 2 && c32) {
         float* ct = c32 + (s * nx + x0) * (int64_t)N;
         for (int e = tid; e < rows * N; e += kTX) {
-            int row = e / N, col = e - row * N;
+            const int row = e / N, col = e - row * N;
             ct[e] = sc[row][col];
         }
     }

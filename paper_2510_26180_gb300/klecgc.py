@@ -27,6 +27,7 @@ EXPORTS = ["klecgc_setup", "klecgc_solve", "klecgc_field", "klecgc_guess", "klec
            "klecgc_mlp_loss_grad", "klecgc_mlp_train", "klecgc_mlp_guess", "klecgc_downsample",
            "klecgc_mlp_set_residual", "klecgc_mlp_targets",
            "klecgc_set_krylov", "klecgc_set_2d_method", "klecgc_set_loop",
+           "klecgc_set_tuning", "klecgc_tuning_report",
            "klecgc_set_scratch_limit",
            "klecgc_krylov_stats", "klecgc_save", "klecgc_load",
            "klecgc_solve_batch", "klecgc_solve_parareal", "klecgc_kl_basis",
@@ -113,6 +114,8 @@ def load() -> ctypes.CDLL:
         "klecgc_set_krylov": [P, D, D, I32],
         "klecgc_set_2d_method": [P, I32],
         "klecgc_set_loop": [P, I32],
+        "klecgc_set_tuning": [P, I32, ctypes.c_char_p],
+        "klecgc_tuning_report": [P, ctypes.c_char_p, I64, P],
         "klecgc_set_scratch_limit": [P, I64],
         "klecgc_solve_parareal": [P, P, I64, D, I32, I32, D, I32, I32, P, P, P, P, P],
         "klecgc_save": [P, ctypes.c_char_p],
@@ -313,6 +316,20 @@ class Solver:
     def set_scratch_limit(self, nbytes) -> int:
         """Budget for the context's device scratch in bytes (0: none)."""
         return _check(self.lib.klecgc_set_scratch_limit(self.h, int(nbytes)))
+
+    def set_tuning(self, mode, cache_path=None) -> int:
+        """Launch-shape autotuner: 1 time the candidates once per shape, 0 fixed rules."""
+        path = cache_path.encode() if cache_path else None
+        return _check(self.lib.klecgc_set_tuning(self.h, mode, path))
+
+    def tuning_report(self) -> dict:
+        """The autotuner's choices, {key: shape}."""
+        import json
+        n = ctypes.c_int64(0)
+        _check(self.lib.klecgc_tuning_report(self.h, None, 0, ctypes.byref(n)))
+        buf = ctypes.create_string_buffer(n.value + 1)
+        _check(self.lib.klecgc_tuning_report(self.h, buf, n.value + 1, ctypes.byref(n)))
+        return json.loads(buf.value.decode())
 
     def set_loop(self, mode) -> int:
         """Parareal loop: 0 CUDA graph with a WHILE node (default), 1 host-driven."""
