@@ -80,6 +80,8 @@ struct klecgc_ctx {
     std::map<std::string, std::string> tuned;   // key -> chosen shape
     std::string tune_path;                      // JSON cache file ("" = none)
     std::string gpu_name;                       // the device's name (tuner keys), read once
+    bool fine_smem_only = false;                // the batch's persistent fine stage runs k_fine32
+    bool mlp_tc = true;                         // network GEMMs on tcgen05 where the shape allows
     std::map<std::string, DevBuf> ws;  // grow-only scratch
     size_t ws_limit = 0;               // bytes of scratch allowed (0: no limit)
     std::string ws_tag;                // appended to scratch names (one batch class each)
@@ -351,7 +353,8 @@ klecgc_status choose_fine32w(klecgc_ctx* ctx, int64_t S, int N, int nx, int J, d
     *out = {0, R0};
     std::vector<Fine32wShape> cands;
     if (R0) cands.push_back({0, R0});
-    for (const Fine32wShape& c : fine32w_candidates(nx)) cands.push_back(c);
+    if (!ctx->fine_smem_only)
+        for (const Fine32wShape& c : fine32w_candidates(nx)) cands.push_back(c);
     if (ctx->tune_mode == 0 || cands.size() < 2 || S == 0) return KLECGC_OK;
     const std::string key = tune_key(ctx, "fine32", nx, N, J);
     auto decode = [&](const std::string& v, Fine32wShape* sh) {
@@ -730,7 +733,7 @@ klecgc_status check_tc(klecgc_ctx* ctx, cudaStream_t st) {
     TRY(cudaStreamSynchronize(st));
     if (h) {
         TRY(cudaMemsetAsync(ctx->tc_err, 0, sizeof(int), st));
-        return fail(KLECGC_E_CUDA, "the tensor-core guess pipeline timed out");
+        return fail(KLECGC_E_CUDA, "a tensor-core (tcgen05) pipeline timed out");
     }
     return KLECGC_OK;
 }
@@ -824,9 +827,44 @@ klecgc_status mlp_buffers(klecgc_ctx* ctx, int B, MlpBuffers* b) {
     return KLECGC_OK;
 }
 
+// One GEMM of the network: C = op(A) op(B) (op = transpose when ta / tb;
+// A(m,k) = ta ? A[k lda + m] : A[m lda + k], B(k,n) = tb ? B[n ldb + k] : B[k ldb + n]).
+// On the tcgen05 tensor cores when the shape allows TMA (K-major operands,
+// transposed into scratch where op needs it), else on the warp-level MMA
+// kernel (the first layer, with K = M = 10, and short tails).
+klecgc_status mlp_gemm(klecgc_ctx* ctx, bool ta, bool tb, int M, int N, int K,
+                       const __nv_bfloat16* A, int lda, const __nv_bfloat16* B, int ldb,
+                       const float* bias, const float* zmask, int ldz, float* C, int ldc,
+                       __nv_bfloat16* Cb, int ldcb, bool relu, cudaStream_t st) {
+    const __nv_bfloat16* Ak = A;
+    const __nv_bfloat16* Bk = B;
+    int la = lda, lb = ldb;
+    bool tc = ctx->mlp_tc && M >= 64 && N >= 32 && K >= 64 && (K % 8) == 0;
+    if (tc && ta) {
+        WS(__nv_bfloat16, t, "mlp_tA", (size_t)M * K);
+        launch_transpose_bf16(A, K, M, lda, t, st);   // [K][M] -> [M][K]
+        Ak = t;
+        la = K;
+    }
+    if (tc && !tb) {
+        WS(__nv_bfloat16, t, "mlp_tB", (size_t)N * K);
+        launch_transpose_bf16(B, K, N, ldb, t, st);   // [K][N] -> [N][K]
+        Bk = t;
+        lb = K;
+    }
+    if (tc && gemm_bf16_tc_ok(M, N, K, Ak, la, Bk, lb)) {
+        TRY(launch_gemm_bf16_tc(M, N, K, Ak, la, Bk, lb, bias, zmask, ldz, C, ldc, Cb, ldcb, relu,
+                                ctx->tc_err, st));
+        return KLECGC_OK;
+    }
+    launch_gemm_bf16(ta, tb, M, N, K, A, lda, B, ldb, bias, zmask, ldz, C, ldc, Cb, ldcb, relu, st);
+    return KLECGC_OK;
+}
+
 // Y = net(X), X BF16 [B][M]; hidden pre-activations and activations kept in b.
-void mlp_forward(klecgc_ctx* ctx, int B, const __nv_bfloat16* X, const MlpBuffers& b, float* Y,
-                 cudaStream_t st) {
+klecgc_status mlp_forward(klecgc_ctx* ctx, int B, const __nv_bfloat16* X, const MlpBuffers& b,
+                          float* Y, cudaStream_t st) {
+    klecgc_status s = KLECGC_OK;
     MlpState& q = ctx->mlp;
     const __nv_bfloat16* in = X;
     int kin = q.sizes[0];
@@ -836,23 +874,26 @@ void mlp_forward(klecgc_ctx* ctx, int B, const __nv_bfloat16* X, const MlpBuffer
         const float* bias = q.theta + q.boff[l];
         if (l < 3) {
             ctx->launch(KLECGC_K_GUESS, st, [&] {
-                launch_gemm_bf16(false, true, B, out, kin, in, kin, W, kin, bias, nullptr, 0,
-                                 b.Z[l], out, b.A[l], out, true, st);
+                s = mlp_gemm(ctx, false, true, B, out, kin, in, kin, W, kin, bias, nullptr, 0,
+                             b.Z[l], out, b.A[l], out, true, st);
             });
             in = b.A[l];
             kin = out;
         } else {
             ctx->launch(KLECGC_K_GUESS, st, [&] {
-                launch_gemm_bf16(false, true, B, out, kin, in, kin, W, kin, bias, nullptr, 0, Y,
-                                 out, nullptr, 0, false, st);
+                s = mlp_gemm(ctx, false, true, B, out, kin, in, kin, W, kin, bias, nullptr, 0, Y,
+                             out, nullptr, 0, false, st);
             });
         }
+        if (s != KLECGC_OK) return s;
     }
+    return KLECGC_OK;
 }
 
 // Gradient of the loss w.r.t. all parameters into q.grad, from dY (FP32 and BF16).
-void mlp_backward(klecgc_ctx* ctx, int B, const __nv_bfloat16* X, const MlpBuffers& b,
-                  const float* dY, const __nv_bfloat16* dYb, cudaStream_t st) {
+klecgc_status mlp_backward(klecgc_ctx* ctx, int B, const __nv_bfloat16* X, const MlpBuffers& b,
+                           const float* dY, const __nv_bfloat16* dYb, cudaStream_t st) {
+    klecgc_status s = KLECGC_OK;
     MlpState& q = ctx->mlp;
     const float* dZf = dY;
     const __nv_bfloat16* dZb = dYb;
@@ -860,21 +901,23 @@ void mlp_backward(klecgc_ctx* ctx, int B, const __nv_bfloat16* X, const MlpBuffe
         const int out = q.sizes[l + 1], kin = q.sizes[l];
         const __nv_bfloat16* Ain = l == 0 ? X : b.A[l - 1];
         ctx->launch(KLECGC_K_GUESS, st, [&] {
-            launch_gemm_bf16(true, false, out, kin, B, dZb, out, Ain, kin, nullptr, nullptr, 0,
-                             q.grad + q.woff[l], kin, nullptr, 0, false, st);
+            s = mlp_gemm(ctx, true, false, out, kin, B, dZb, out, Ain, kin, nullptr, nullptr, 0,
+                         q.grad + q.woff[l], kin, nullptr, 0, false, st);
         });
+        if (s != KLECGC_OK) return s;
         ctx->launch(KLECGC_K_GUESS, st, [&] { launch_colsum(B, out, dZf, q.grad + q.boff[l], st); });
         if (l > 0) {
             const int nb = l & 1;
             ctx->launch(KLECGC_K_GUESS, st, [&] {
-                launch_gemm_bf16(false, false, B, kin, out, dZb, out, q.thb + q.woff[l], kin,
-                                 nullptr, b.Z[l - 1], kin, b.dZ[nb], kin, b.dZb[nb], kin, false,
-                                 st);
+                s = mlp_gemm(ctx, false, false, B, kin, out, dZb, out, q.thb + q.woff[l], kin,
+                             nullptr, b.Z[l - 1], kin, b.dZ[nb], kin, b.dZb[nb], kin, false, st);
             });
+            if (s != KLECGC_OK) return s;
             dZf = b.dZ[nb];
             dZb = b.dZb[nb];
         }
     }
+    return KLECGC_OK;
 }
 
 // Learned guess of S samples into U (internal layout [S][nx][N]); *finite
@@ -892,7 +935,10 @@ klecgc_status mlp_guess_internal(klecgc_ctx* ctx, const double* xi_d, int64_t S,
         launch_mlp_gather(B, q.sizes[0], q.D, nullptr, 0, xi_d, nullptr, nullptr, nullptr, X,
                           nullptr, st);
     });
-    mlp_forward(ctx, B, X, b, Y, st);
+    {
+        const klecgc_status ms_ = mlp_forward(ctx, B, X, b, Y, st);
+        if (ms_ != KLECGC_OK) return ms_;
+    }
     if (q.residual) {
         // U0 = gPC surrogate guess (tensor-core contraction, FP32-accurate) +
         // the network's correction
@@ -1712,16 +1758,22 @@ klecgc_status klecgc_mlp_loss_grad(klecgc_ctx* ctx, const double* xi, const floa
     WS(float, lsum, "mlp_loss", 1);
     TRY(cudaMemsetAsync(lsum, 0, sizeof(float), st));
     launch_mlp_gather((int)B, q.sizes[0], q.D, nullptr, 0, xi_d, tg, q.mean, q.inv_std, X, T, st);
-    mlp_forward(ctx, (int)B, X, b, Y, st);
+    {
+        const klecgc_status ms_ = mlp_forward(ctx, (int)B, X, b, Y, st);
+        if (ms_ != KLECGC_OK) return ms_;
+    }
     launch_mse(B * q.D, 1.f / (float)(B * q.D), 1.f / (float)(B * q.D), Y, T, dY, dYb, lsum, st);
-    mlp_backward(ctx, (int)B, X, b, dY, dYb, st);
+    {
+        const klecgc_status ms_ = mlp_backward(ctx, (int)B, X, b, dY, dYb, st);
+        if (ms_ != KLECGC_OK) return ms_;
+    }
     TRY(cudaGetLastError());
     float lh = 0.f;
     TRY(cudaMemcpyAsync(&lh, lsum, sizeof(float), cudaMemcpyDeviceToHost, st));
     TRY(cudaStreamSynchronize(st));
     if (loss_out) *loss_out = lh;
     if (grad_out) TRY(cudaMemcpy(grad_out, q.grad, q.P * 4, cudaMemcpyDefault));
-    return KLECGC_OK;
+    return check_tc(ctx, st);
 }
 
 klecgc_status klecgc_mlp_train(klecgc_ctx* ctx, const double* xi, const float* targets, int64_t n,
@@ -1774,10 +1826,16 @@ klecgc_status klecgc_mlp_train(klecgc_ctx* ctx, const double* xi, const float* t
             const float lr_t = (float)(lr_final + 0.5 * (lr - lr_final) * (1.0 + std::cos(3.14159265358979 * frac)));
             launch_mlp_gather(B, q.sizes[0], q.D, perm_d, (int)(bi * B), xi_d, tg, q.mean,
                               q.inv_std, X, T, st);
-            mlp_forward(ctx, B, X, b, Y, st);
+            {
+                const klecgc_status ms_ = mlp_forward(ctx, B, X, b, Y, st);
+                if (ms_ != KLECGC_OK) return ms_;
+            }
             const float sc = 1.f / (float)((int64_t)B * q.D);
             launch_mse((int64_t)B * q.D, sc, sc / (float)nb, Y, T, dY, dYb, lsum, st);
-            mlp_backward(ctx, B, X, b, dY, dYb, st);
+            {
+                const klecgc_status ms_ = mlp_backward(ctx, B, X, b, dY, dYb, st);
+                if (ms_ != KLECGC_OK) return ms_;
+            }
             launch_adam(q.P, lr_t, q.adam_t, q.theta, q.grad, q.m, q.v, q.thb, st);
         }
         TRY(cudaGetLastError());
@@ -1786,6 +1844,8 @@ klecgc_status klecgc_mlp_train(klecgc_ctx* ctx, const double* xi, const float* t
         TRY(cudaStreamSynchronize(st));
         if (epoch_loss) epoch_loss[ep] = lh;
         if (!std::isfinite(lh)) return fail(KLECGC_E_NONFINITE, "training loss is not finite");
+        klecgc_status ts = check_tc(ctx, st);
+        if (ts != KLECGC_OK) return ts;
     }
     return KLECGC_OK;
 }
@@ -1805,6 +1865,7 @@ klecgc_status klecgc_mlp_guess(klecgc_ctx* ctx, const double* xi, int64_t S, dou
     if ((s = mlp_guess_internal(ctx, xi_d, S, U, st, &finite)) != KLECGC_OK) return s;
     if ((s = export_batch(ctx, U, S, ctx->N, U0_out, st)) != KLECGC_OK) return s;
     TRY(cudaStreamSynchronize(st));
+    if ((s = check_tc(ctx, st)) != KLECGC_OK) return s;
     return finite ? KLECGC_OK : fail(KLECGC_E_NONFINITE, "network output is not finite");
 }
 
@@ -2464,6 +2525,177 @@ klecgc_status SolveRun::finish(double* U_out, std::vector<int32_t>& hs, std::vec
     return KLECGC_OK;
 }
 
+// The uneven batch with every class advancing together (Algorithm 2 for all
+// instances at once): each parareal iteration is one persistent launch per
+// stage over all classes (the fine stage one per rows-per-lane group), whose
+// CTAs pull (class, sample, part) tasks from a work queue ordered longest
+// first; the iterations run as a CUDA graph WHILE loop (iterate_loop).  The
+// classes were set up by SolveRun::begin on the pool streams.
+klecgc_status batch_persistent(klecgc_ctx* c0, std::vector<SolveRun>& runs, int64_t n, int kmax,
+                               double tol, cudaStream_t st, const std::vector<cudaStream_t>& pool) {
+    klecgc_ctx* ctx = c0;
+    const int nc = (int)runs.size();
+    const int defect = runs[0].defect ? 1 : 0;
+    // order after the set-up on the pool streams
+    {
+        cudaEvent_t ev;
+        TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        for (cudaStream_t x : pool) {
+            cudaEventRecord(ev, x);
+            cudaStreamWaitEvent(st, ev, 0);
+        }
+        cudaEventDestroy(ev);
+    }
+    std::vector<BatchClass> hc(nc);
+    for (int c = 0; c < nc; ++c) {
+        SolveRun& R = runs[c];
+        klecgc_ctx* x = R.ctx;
+        BatchClass& C = hc[c];
+        C = BatchClass{};
+        C.S = R.S;
+        C.nx = R.nx;
+        C.N = R.N;
+        C.K = R.K;
+        C.J = R.J;
+        C.R = R.op.sh32.R;
+        C.QS = C.R >= 64 ? 1 : 2;
+        C.defect = defect;
+        C.react = x->prob.reaction != 0.0;
+        C.force = x->prob.forcing != 0.0;
+        const double dt = R.dT / R.J;
+        C.dt_react = (float)(dt * x->prob.reaction);
+        C.dt_f = (float)(dt * x->prob.forcing);
+        C.dTreact = R.dT * x->prob.reaction;
+        C.alpha = R.alpha;
+        C.tol = tol;
+        C.kmax = kmax;
+        C.U = R.U;
+        C.Udf = R.Udf;
+        C.fout = R.fout;
+        C.c32 = R.c32;
+        C.rs = R.r;
+        C.Facc0 = R.Facc2[0];
+        C.Facc1 = R.Facc2[1];
+        C.p64 = R.p64;
+        C.p32 = R.p32;
+        C.tab32 = reinterpret_cast<const char*>(R.op.tab32);
+        C.u0 = x->u0;
+        C.wT = R.op.wT;
+        C.dinv64 = R.op.dinv64;
+        C.lu64 = R.op.lu64;
+        C.dinv32 = R.op.dinv32;
+        C.lu32 = R.op.lu32;
+        C.wT32 = R.op.wT32;
+        C.sc64 = R.sc64;
+        C.isc64 = R.isc64;
+        C.sc32 = R.sc32;
+        C.isc32 = R.isc32;
+        C.active = R.active;
+        C.iters = R.iters;
+        C.status = R.status;
+        C.delta = R.delta;
+        if (R.op.sh32.W != 0 || !C.R) return fail(KLECGC_E_CUDA, "batch: a class without the shared-memory fine kernel");
+    }
+    // task lists, longest first within each stage
+    struct Group {
+        int R, rt;
+        std::vector<BatchTask> t;
+    };
+    std::vector<Group> fine;
+    std::vector<std::pair<double, int>> order(nc);
+    for (int c = 0; c < nc; ++c) order[c] = {-(double)hc[c].nx * hc[c].J * hc[c].N, c};
+    std::sort(order.begin(), order.end());
+    for (auto& oc : order) {
+        const BatchClass& C = hc[oc.second];
+        const int rt = (C.react || C.force) ? 1 : 0;
+        Group* g = nullptr;
+        for (auto& x : fine)
+            if (x.R == C.R && x.rt == rt) g = &x;
+        if (!g) {
+            fine.push_back({C.R, rt, {}});
+            g = &fine.back();
+        }
+        const int parts = batch_fine_parts(C.N, C.R);
+        for (int64_t s2 = 0; s2 < C.S; ++s2)
+            for (int p = 0; p < parts; ++p) g->t.push_back({oc.second, p, s2});
+    }
+    const int tile = batch_transform_tile(defect);
+    std::vector<BatchTask> fwd, inv, solve, inst;
+    for (auto& oc : order) {
+        const BatchClass& C = hc[oc.second];
+        const int tf = (C.nx + tile - 1) / tile, ti = (C.nx + 31) / 32;
+        for (int64_t s2 = 0; s2 < C.S; ++s2) {
+            for (int p = 0; p < tf; ++p) fwd.push_back({oc.second, p, s2});
+            for (int p = 0; p < ti; ++p) inv.push_back({oc.second, p, s2});
+            inst.push_back({oc.second, 0, s2});
+        }
+    }
+    {
+        std::vector<std::pair<double, int>> byn(nc);
+        for (int c = 0; c < nc; ++c) byn[c] = {-(double)hc[c].nx, c};
+        std::sort(byn.begin(), byn.end());
+        for (auto& oc : byn) {
+            const BatchClass& C = hc[oc.second];
+            for (int64_t q = 0; q < C.S * C.K; q += 128) solve.push_back({oc.second, (int)q, 0});
+        }
+    }
+    size_t total = fwd.size() + inv.size() + solve.size() + inst.size();
+    for (auto& g : fine) total += g.t.size();
+    WS(BatchClass, dcls, "batch_cls", nc);
+    WS(BatchTask, dtask, "batch_tasks", total);
+    const int nq = 3 + (int)fine.size();
+    WS(int, queues, "batch_queues", nq);
+    WS(int, kdev, "batch_k", 1);
+    WS(int, nact, "batch_active", 1);
+    TRY(cudaMemcpyAsync(dcls, hc.data(), nc * sizeof(BatchClass), cudaMemcpyHostToDevice, st));
+    std::vector<BatchTask> all;
+    all.reserve(total);
+    std::vector<const BatchTask*> fine_ptr;
+    std::vector<int64_t> fine_off;
+    for (auto& g : fine) {
+        fine_off.push_back((int64_t)all.size());
+        all.insert(all.end(), g.t.begin(), g.t.end());
+    }
+    const int64_t o_fwd = all.size();
+    all.insert(all.end(), fwd.begin(), fwd.end());
+    const int64_t o_solve = all.size();
+    all.insert(all.end(), solve.begin(), solve.end());
+    const int64_t o_inv = all.size();
+    all.insert(all.end(), inv.begin(), inv.end());
+    const int64_t o_inst = all.size();
+    all.insert(all.end(), inst.begin(), inst.end());
+    TRY(cudaMemcpyAsync(dtask, all.data(), all.size() * sizeof(BatchTask), cudaMemcpyHostToDevice, st));
+    const int g_fwd = batch_grid(0, defect), g_solve = batch_grid(1, defect),
+              g_inv = batch_grid(2, defect);
+    auto iteration = [&](cudaStream_t s2, int k, const int* kd) -> klecgc_status {
+        TRY(cudaMemsetAsync(queues, 0, nq * sizeof(int), s2));
+        for (size_t g = 0; g < fine.size(); ++g)
+            ctx->launch(KLECGC_K_FINE, s2, [&] {
+                launch_batch_fine(dcls, dtask + fine_off[g], (int)fine[g].t.size(), queues + 3 + g,
+                                  k, kd, fine[g].R, fine[g].rt, 0, s2);
+            });
+        ctx->launch(KLECGC_K_CGC_FWD, s2, [&] { launch_batch_fwd(defect, dcls, dtask + o_fwd, (int)fwd.size(), queues, k, kd, g_fwd, s2); });
+        ctx->launch(KLECGC_K_CGC_SOLVE, s2, [&] { launch_batch_solve(defect, dcls, dtask + o_solve, (int)solve.size(), queues + 1, g_solve, s2); });
+        ctx->launch(KLECGC_K_CGC_INV, s2, [&] { launch_batch_inv(defect, dcls, dtask + o_inv, (int)inv.size(), queues + 2, g_inv, s2); });
+        TRY(cudaMemsetAsync(nact, 0, sizeof(int), s2));
+        ctx->launch(KLECGC_K_CONV, s2, [&] { launch_batch_conv(dcls, dtask + o_inst, (int64_t)inst.size(), k, kd, nact, s2); });
+        TRY(cudaGetLastError());
+        return KLECGC_OK;
+    };
+    klecgc_status s = iterate_loop(ctx, st, kdev, nact, 0, kmax, iteration);
+    if (s != KLECGC_OK) return s;
+    // the classes' results are read on their pool streams
+    {
+        cudaEvent_t ev;
+        TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+        TRY(cudaEventRecord(ev, st));
+        for (cudaStream_t x : pool) cudaStreamWaitEvent(x, ev, 0);
+        cudaEventDestroy(ev);
+    }
+    (void)n;
+    return KLECGC_OK;
+}
+
 klecgc_status status_summary(const std::vector<int32_t>& hs, bool capped) {
     bool any_nf = false, any_nc = false;
     for (int32_t v : hs) {
@@ -2911,6 +3143,11 @@ klecgc_status klecgc_solve_batch(klecgc_ctx* const* ctxs, int32_t n_ctx,
     }
     PinnedInts pin;
     TRY(cudaMallocHost(&pin.p, nc * sizeof(int)));
+    // MIXED / MIXED_DEFECT in 1D: all classes advance together, each stage one
+    // persistent launch over every class (batch_persistent); otherwise the
+    // classes step in lockstep on the stream pool
+    bool persistent = precision != KLECGC_FP64;
+    for (int c = 0; c < n_ctx; ++c) persistent &= ctxs[c]->dim == 1;
     std::vector<SolveRun> runs(nc);
     for (int c = 0; c < nc; ++c) {
         SolveRun& R = runs[c];
@@ -2937,20 +3174,27 @@ klecgc_status klecgc_solve_batch(klecgc_ctx* const* ctxs, int32_t n_ctx,
             launch_gather_rows(xi_d, idx, R.S, M, xg, R.st);
             xic = xg;
         }
-        if ((s = R.begin(xic, nullptr)) != KLECGC_OK) return s;
+        ctx->fine_smem_only = persistent;
+        s = R.begin(xic, nullptr);
+        ctx->fine_smem_only = false;
+        if (s != KLECGC_OK) return s;
     }
-    // iterations in lockstep: every class still active enqueues one step,
-    // then the host reads each class's active count
-    std::vector<char> done(nc, 0);
-    for (int left = nc; left > 0;) {
-        for (int c = 0; c < nc; ++c)
-            if (!done[c] && (s = runs[c].step()) != KLECGC_OK) return s;
-        for (int c = 0; c < nc; ++c) {
-            if (done[c]) continue;
-            TRY(cudaStreamSynchronize(runs[c].st));
-            if (runs[c].finished()) {
-                done[c] = 1;
-                --left;
+    if (persistent) {
+        if ((s = batch_persistent(c0, runs, n, kmax, tol, st, pool.s)) != KLECGC_OK) return s;
+    } else {
+        // iterations in lockstep: every class still active enqueues one step,
+        // then the host reads each class's active count
+        std::vector<char> done(nc, 0);
+        for (int left = nc; left > 0;) {
+            for (int c = 0; c < nc; ++c)
+                if (!done[c] && (s = runs[c].step()) != KLECGC_OK) return s;
+            for (int c = 0; c < nc; ++c) {
+                if (done[c]) continue;
+                TRY(cudaStreamSynchronize(runs[c].st));
+                if (runs[c].finished()) {
+                    done[c] = 1;
+                    --left;
+                }
             }
         }
     }

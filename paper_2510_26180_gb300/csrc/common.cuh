@@ -53,6 +53,70 @@ __device__ __forceinline__ float df_sub(float2 x, float2 y) {
     return s.x + (s.y + (x.y - y.y));
 }
 
+// ---- the uneven batch as persistent stage kernels (k_fine32.cu, k_cgc.cu) ----
+// One class of instances of equal (context, J): the device pointers and
+// sizes that the stage bodies need (the arrays of one SolveRun).
+struct BatchClass {
+    int64_t S;                    // instances of the class
+    int nx, N, K, J, R, QS;       // R, QS: rows per lane and intervals per warp of k_fine32
+    int defect;                   // 1: MIXED_DEFECT (FP32 pairs), 0: MIXED
+    int react, force;             // reaction / forcing terms present
+    float dt_react, dt_f;         // fine step: dt c, dt f0
+    double dTreact, alpha, tol;
+    int kmax;
+    double* U;                    // MIXED: FP64 iterate (the defect path aliases it as Udf)
+    float2* Udf;
+    float* fout;
+    float* c32;
+    double* rs;                   // MIXED: scaled CGC right-hand side
+    float2* Facc0;                // MIXED_DEFECT: F accumulators (by iteration parity)
+    float2* Facc1;
+    Cplx<double>* p64;
+    Cplx<float>* p32;
+    const char* tab32;            // k_fine32 table ([S][R][32] x 24 bytes)
+    const double* u0;
+    const double* wT;
+    const Cplx<double>* dinv64;
+    const Cplx<double>* lu64;
+    const Cplx<float>* dinv32;
+    const Cplx<float>* lu32;
+    const float* wT32;
+    const double* sc64;
+    const double* isc64;
+    const float* sc32;
+    const float* isc32;
+    int* active;
+    int32_t* iters;
+    int32_t* status;
+    unsigned long long* delta;
+};
+// A work item of a stage: class c, sample s of the class, and the part
+// (interval group of the fine stage, x tile of the transforms, first system
+// of a 128-system chunk of the shifted solves).
+struct BatchTask {
+    int c, part;
+    int64_t s;
+};
+// Persistent stage kernels: grid-size CTAs pull tasks from *queue (a counter
+// the caller zeroes before the launch) in list order, longest first.
+// k: iteration (kdev ? *kdev : k_host).
+int batch_fine_parts(int N, int R);              // fine tasks per instance
+size_t batch_fine_smem(int R);
+// one launch per (R, rt) group; grid <= 0: the SM count times the occupancy
+void launch_batch_fine(const BatchClass* cls, const BatchTask* tasks, int ntasks, int* queue,
+                       int k_host, const int* kdev, int R, int rt, int grid, cudaStream_t st);
+void launch_batch_fwd(int defect, const BatchClass* cls, const BatchTask* tasks, int ntasks,
+                      int* queue, int k_host, const int* kdev, int grid, cudaStream_t st);
+void launch_batch_solve(int defect, const BatchClass* cls, const BatchTask* tasks, int ntasks,
+                        int* queue, int grid, cudaStream_t st);
+void launch_batch_inv(int defect, const BatchClass* cls, const BatchTask* tasks, int ntasks,
+                      int* queue, int grid, cudaStream_t st);
+// stopping rule for every instance (tasks: one per instance, part unused)
+void launch_batch_conv(const BatchClass* cls, const BatchTask* inst, int64_t n, int k_host,
+                       const int* kdev, int* n_active, cudaStream_t st);
+int batch_transform_tile(int defect);           // x rows per transform task
+int batch_grid(int kind, int defect);           // persistent grid size per stage (0 fwd, 1 solve, 2 inv)
+
 // ---- k_field.cu ----
 void launch_field(const double* xi, int64_t S, int M, const double* basis, int nf, double* a,
                   cudaStream_t st);
@@ -330,6 +394,18 @@ void launch_gemm_bf16(bool ta, bool tb, int M, int N, int K, const __nv_bfloat16
                       const __nv_bfloat16* B, int ldb, const float* bias, const float* zmask,
                       int ldz, float* C, int ldc, __nv_bfloat16* Cb, int ldcb, bool relu,
                       cudaStream_t st);
+// C = A B^T on the tcgen05 tensor cores (BF16 K-major operands [M][K], [N][K],
+// FP32 accumulation in tensor memory), same epilogue as launch_gemm_bf16;
+// err: the bounded-wait flag (set on a timeout).  gemm_bf16_tc_ok: the sizes
+// and alignments TMA needs.
+bool gemm_bf16_tc_ok(int M, int N, int K, const void* A, int lda, const void* B, int ldb);
+cudaError_t launch_gemm_bf16_tc(int M, int N, int K, const __nv_bfloat16* A, int lda,
+                                const __nv_bfloat16* B, int ldb, const float* bias,
+                                const float* zmask, int ldz, float* C, int ldc,
+                                __nv_bfloat16* Cb, int ldcb, bool relu, int* err,
+                                cudaStream_t st);
+void launch_transpose_bf16(const __nv_bfloat16* in, int R, int Cc, int ld_in, __nv_bfloat16* out,
+                           cudaStream_t st);
 void launch_mlp_gather(int B, int M, int D, const int* perm, int b0, const double* xi,
                        const float* targ, const float* mean, const float* inv_std,
                        __nv_bfloat16* X, float* T, cudaStream_t st);

@@ -186,25 +186,35 @@ __device__ __forceinline__ void irfft_row(const Cplx<T>* X, T (&zr)[N / 2], T (&
 // written by the neighbouring tile, so an in-place update would race.
 constexpr int kTXF = 64;  // x points (= threads) per CTA in the FP32 transform kernels
 
+__host__ __device__ constexpr size_t align16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+// The transform and solve kernels are thin wrappers around per-tile device
+// bodies that take their sample and tile and a shared-memory buffer: the
+// same bodies serve the persistent stage kernels of the uneven batch, which
+// pick the tile from a work queue and carve the buffer from one dynamic
+// allocation (static arrays in each instantiation would add up).
+
 template <int N>
-__global__ void __launch_bounds__(kTXF) k_cgc_forward_df(
-    int64_t S, int nx, const float* __restrict__ fout, float2* __restrict__ Facc0,
-    float2* __restrict__ Facc1, int k_host, const int* __restrict__ kdev,
-    const float2* __restrict__ Udf, const double* __restrict__ wT, float dTreact,
-    const float* __restrict__ scale, Cplx<float>* __restrict__ p,
-    const int* __restrict__ active) {
+__host__ __device__ constexpr size_t fwd_df_smem() {
+    return align16((kTXF + 2) * (N + 1) * sizeof(float) + (kTXF + 1) * sizeof(float)) +
+           kTXF * (N / 2 + 1) * sizeof(Cplx<float>);
+}
+
+template <int N>
+__device__ __forceinline__ void fwd_df_tile(
+    int64_t s, int x0, int nx, const float* __restrict__ fout, float2* __restrict__ Facc0,
+    float2* __restrict__ Facc1, int kit, const float2* __restrict__ Udf,
+    const double* __restrict__ wT, float dTreact, const float* __restrict__ scale,
+    Cplx<float>* __restrict__ p, char* smem) {
     constexpr int K = N / 2 + 1;
     // iteration k reads F(U^{k-1}) from buffer (k - 1) & 1 (none at k = 0)
     // and writes F(U^k) to buffer k & 1
-    const int kit = kdev ? *kdev : k_host;
     const float2* __restrict__ Facc_in = kit == 0 ? nullptr : ((kit & 1) ? Facc0 : Facc1);
     float2* __restrict__ Facc_out = (kit & 1) ? Facc1 : Facc0;
-    __shared__ float sD[kTXF + 2][N + 1];
-    __shared__ float sw[kTXF + 1];
-    __shared__ Cplx<float> sout[kTXF * K];
-    const int64_t s = blockIdx.x;
-    if (!active[s]) return;
-    const int x0 = blockIdx.y * kTXF;
+    float (*sD)[N + 1] = reinterpret_cast<float (*)[N + 1]>(smem);
+    float* sw = reinterpret_cast<float*>(smem + (kTXF + 2) * (N + 1) * sizeof(float));
+    Cplx<float>* sout = reinterpret_cast<Cplx<float>*>(
+        smem + align16((kTXF + 2) * (N + 1) * sizeof(float) + (kTXF + 1) * sizeof(float)));
     const int rows = min(kTXF, nx - x0);
     const int tid = threadIdx.x;
     const int64_t base = s * (int64_t)nx * N;
@@ -274,6 +284,20 @@ __global__ void __launch_bounds__(kTXF) k_cgc_forward_df(
     for (int e = tid; e < rows * K; e += kTXF) pout[e] = sout[e];
 }
 
+template <int N>
+__global__ void __launch_bounds__(kTXF) k_cgc_forward_df(
+    int64_t S, int nx, const float* __restrict__ fout, float2* __restrict__ Facc0,
+    float2* __restrict__ Facc1, int k_host, const int* __restrict__ kdev,
+    const float2* __restrict__ Udf, const double* __restrict__ wT, float dTreact,
+    const float* __restrict__ scale, Cplx<float>* __restrict__ p,
+    const int* __restrict__ active) {
+    __shared__ __align__(16) char smem[fwd_df_smem<N>()];
+    const int64_t s = blockIdx.x;
+    if (!active[s]) return;
+    fwd_df_tile<N>(s, blockIdx.y * kTXF, nx, fout, Facc0, Facc1, kdev ? *kdev : k_host, Udf, wT,
+                   dTreact, scale, p, smem);
+}
+
 // (a) for the mixed path (FP32 fine propagator; CGC, update and norms in
 // FP64).  The CGC right-hand side is kept in FP64, pre-scaled by the step (a)
 // weights: rs_n = alpha^{n/N} r_n.
@@ -288,20 +312,22 @@ __global__ void __launch_bounds__(kTXF) k_cgc_forward_df(
 // Then p = DFT_n(rs) (times 2, see rfft_row).  rs is updated in place (no
 // halo on rs); the halo rows of fout give the x-neighbours of the flux.
 template <int N>
-__global__ void __launch_bounds__(kTX) k_cgc_forward_acc(
-    int64_t S, int nx, const float* __restrict__ fout, const float* __restrict__ c32,
+__host__ __device__ constexpr size_t fwd_acc_smem() {
+    return align16((kTX + 2) * (N + 1) * sizeof(float)) + (kTX + 1) * sizeof(double);
+}
+
+template <int N>
+__device__ __forceinline__ void fwd_acc_tile(
+    int64_t s, int x0, int nx, const float* __restrict__ fout, const float* __restrict__ c32,
     const double* __restrict__ U, const double* __restrict__ wT, double dTreact, double alpha,
     const double* __restrict__ scale, const float* __restrict__ scale32, double* __restrict__ rs,
-    Cplx<double>* __restrict__ p, const int* __restrict__ active) {
+    Cplx<double>* __restrict__ p, char* smem) {
     constexpr int K = N / 2 + 1;
     // fout rows x0-1 .. x0+rows (the x-neighbours of the flux form); every
     // other row a thread touches is its own and is accessed directly
-    __shared__ float sF[kTX + 2][N + 1];
-    __shared__ double sw[kTX + 1];
-    const int64_t s = blockIdx.x;
-    if (!active[s]) return;
+    float (*sF)[N + 1] = reinterpret_cast<float (*)[N + 1]>(smem);
+    double* sw = reinterpret_cast<double*>(smem + align16((kTX + 2) * (N + 1) * sizeof(float)));
     const bool first = c32 == nullptr;
-    const int x0 = blockIdx.y * kTX;
     const int rows = min(kTX, nx - x0);
     const int tid = threadIdx.x;
     const int64_t base = s * (int64_t)nx * N;
@@ -342,6 +368,19 @@ __global__ void __launch_bounds__(kTX) k_cgc_forward_acc(
 #pragma unroll
     for (int n = 0; n < N; ++n) rw[n] = xs[n];
     rfft_row<double, N>(xs, p + row * K);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kTX) k_cgc_forward_acc(
+    int64_t S, int nx, const float* __restrict__ fout, const float* __restrict__ c32,
+    const double* __restrict__ U, const double* __restrict__ wT, double dTreact, double alpha,
+    const double* __restrict__ scale, const float* __restrict__ scale32, double* __restrict__ rs,
+    Cplx<double>* __restrict__ p, const int* __restrict__ active) {
+    __shared__ __align__(16) char smem[fwd_acc_smem<N>()];
+    const int64_t s = blockIdx.x;
+    if (!active[s]) return;
+    fwd_acc_tile<N>(s, blockIdx.y * kTX, nx, fout, c32, U, wT, dTreact, alpha, scale, scale32, rs,
+                    p, smem);
 }
 
 #define KLECGC_N_SWITCH(N, CALL)      \
@@ -431,20 +470,14 @@ template void launch_cgc_forward<float, float>(int64_t, int, int, const float*, 
 // loads per thread are in flight instead of one.  TW is the type of the face
 // weights (FP32 for the FP32 solve: no FP64 conversion in the loop).
 template <typename T, typename TW>
-__global__ void __launch_bounds__(128) k_cgc_solve(int64_t S, int K, int nx,
-                                                   const Cplx<T>* __restrict__ dinv,
-                                                   const Cplx<T>* __restrict__ lu,
-                                                   const TW* __restrict__ wT,
-                                                   Cplx<T>* __restrict__ p,
-                                                   const int* __restrict__ active) {
+__device__ __forceinline__ void cgc_solve_one(int64_t s, int k, int K, int nx,
+                                              const Cplx<T>* __restrict__ dinv,
+                                              const Cplx<T>* __restrict__ lu,
+                                              const TW* __restrict__ wT,
+                                              Cplx<T>* __restrict__ p) {
     // rows per load batch (swept 4, 8, 16: 1.049, 1.093, 1.082 ms per
     // launch at 4096 samples; the results do not depend on it)
     constexpr int CH = 4;
-    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-    if (t >= S * K) return;
-    int64_t s = t / K;
-    int k = (int)(t - s * K);
-    if (!active[s]) return;
     const int64_t base = s * (int64_t)nx * K + k;
     const TW* w = wT + s * (nx + 1);
     T wr = 0, wi = 0;
@@ -500,6 +533,21 @@ __global__ void __launch_bounds__(128) k_cgc_solve(int64_t S, int K, int nx,
 }
 
 template <typename T, typename TW>
+__global__ void __launch_bounds__(128) k_cgc_solve(int64_t S, int K, int nx,
+                                                   const Cplx<T>* __restrict__ dinv,
+                                                   const Cplx<T>* __restrict__ lu,
+                                                   const TW* __restrict__ wT,
+                                                   Cplx<T>* __restrict__ p,
+                                                   const int* __restrict__ active) {
+    int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    if (t >= S * K) return;
+    int64_t s = t / K;
+    int k = (int)(t - s * K);
+    if (!active[s]) return;
+    cgc_solve_one<T, TW>(s, k, K, nx, dinv, lu, wT, p);
+}
+
+template <typename T, typename TW>
 void launch_cgc_solve(int64_t S, int K, int nx, const Cplx<T>* dinv, const Cplx<T>* lu,
                       const TW* wT, Cplx<T>* p, const int* active, cudaStream_t st) {
     int64_t n = S * K;
@@ -525,20 +573,19 @@ __device__ __forceinline__ unsigned long long abs_bits(double v) {
 // serialize each load behind the store before it).
 // mode 0: U = u, c32 = u - U_old, delta = max |u - U_old|;
 // mode 1: U += u, c32 = u, delta = max |u|;  mode 2: U = u.
+template <int N>
+__host__ __device__ constexpr size_t inv_smem() {
+    return align16(kTX * (N + 1) * sizeof(double)) + kTX * (N + 1) * sizeof(float);
+}
+
 template <typename T, int N>
-__global__ void __launch_bounds__(kTX) k_cgc_inverse(int64_t S, int nx,
-                                                     const Cplx<T>* __restrict__ q,
-                                                     const T* __restrict__ iscale,
-                                                     double* __restrict__ U, int mode,
-                                                     unsigned long long* __restrict__ delta,
-                                                     float* __restrict__ c32,
-                                                     const int* __restrict__ active) {
+__device__ __forceinline__ void inv_tile(int64_t s, int x0, int nx, const Cplx<T>* __restrict__ q,
+                                         const T* __restrict__ iscale, double* __restrict__ U,
+                                         int mode, unsigned long long* __restrict__ delta,
+                                         float* __restrict__ c32, char* smem) {
     constexpr int L = N / 2, K = N / 2 + 1;
-    __shared__ double su[kTX][N + 1];
-    __shared__ float sc[kTX][N + 1];
-    const int64_t s = blockIdx.x;
-    if (!active[s]) return;
-    const int x0 = blockIdx.y * kTX;
+    double (*su)[N + 1] = reinterpret_cast<double (*)[N + 1]>(smem);
+    float (*sc)[N + 1] = reinterpret_cast<float (*)[N + 1]>(smem + align16(kTX * (N + 1) * sizeof(double)));
     const int rows = min(kTX, nx - x0);
     const int tid = threadIdx.x;
     double* Ut = U + (s * nx + x0) * (int64_t)N;
@@ -596,6 +643,20 @@ __global__ void __launch_bounds__(kTX) k_cgc_inverse(int64_t S, int nx,
     }
 }
 
+template <typename T, int N>
+__global__ void __launch_bounds__(kTX) k_cgc_inverse(int64_t S, int nx,
+                                                     const Cplx<T>* __restrict__ q,
+                                                     const T* __restrict__ iscale,
+                                                     double* __restrict__ U, int mode,
+                                                     unsigned long long* __restrict__ delta,
+                                                     float* __restrict__ c32,
+                                                     const int* __restrict__ active) {
+    __shared__ __align__(16) char smem[inv_smem<N>()];
+    const int64_t s = blockIdx.x;
+    if (!active[s]) return;
+    inv_tile<T, N>(s, blockIdx.y * kTX, nx, q, iscale, U, mode, delta, c32, smem);
+}
+
 template <typename T>
 void launch_cgc_inverse(int64_t S, int N, int nx, const Cplx<T>* q, const T* iscale, double* U,
                         int mode, unsigned long long* delta, float* c32, const int* active,
@@ -626,25 +687,26 @@ template void launch_cgc_inverse<float>(int64_t, int, int, const Cplx<float>*, c
 
 // (c) + update for the defect path: U (pairs) += u, c32 = u, delta = max|u|.
 template <int N>
-__global__ void __launch_bounds__(kTX) k_cgc_inverse_df(int64_t S, int nx,
-                                                         const Cplx<float>* __restrict__ q,
-                                                         const float* __restrict__ iscale,
-                                                         float2* __restrict__ Udf,
-                                                         unsigned long long* __restrict__ delta,
-                                                         float* __restrict__ c32,
-                                                         const int* __restrict__ active) {
+__host__ __device__ constexpr size_t inv_df_smem() {
+    return align16(kTX * 2 * (N / 2 + 1) * sizeof(float)) + kTX * (N + 1) * sizeof(float2);
+}
+
+template <int N>
+__device__ __forceinline__ void inv_df_tile(int64_t s, int x0, int nx,
+                                            const Cplx<float>* __restrict__ q,
+                                            const float* __restrict__ iscale,
+                                            float2* __restrict__ Udf,
+                                            unsigned long long* __restrict__ delta,
+                                            float* __restrict__ c32, char* smem) {
     constexpr int L = N / 2, K = N / 2 + 1;
     // The row of q a thread transforms and the row of increments it writes
     // share storage (2K >= N + 1 floats per row): each thread reads its whole
     // q row before it writes its increments, and touches no other row between
     // the barriers; this keeps shared memory at 25 KB per CTA (9 CTAs per SM).
-    __shared__ __align__(16) float sqc[kTX * 2 * K];
-    __shared__ float2 su[kTX][N + 1];
+    float* sqc = reinterpret_cast<float*>(smem);
+    float2 (*su)[N + 1] = reinterpret_cast<float2 (*)[N + 1]>(smem + align16(kTX * 2 * K * sizeof(float)));
     Cplx<float>* sq = reinterpret_cast<Cplx<float>*>(sqc);   // [kTX][K]
     auto sc = [&](int row, int c) -> float& { return sqc[row * 2 * K + c]; };
-    const int64_t s = blockIdx.x;
-    if (!active[s]) return;
-    const int x0 = blockIdx.y * kTX;
     const int rows = min(kTX, nx - x0);
     const int tid = threadIdx.x;
     const Cplx<float>* qin = q + (s * nx + x0) * (int64_t)K;
@@ -692,6 +754,20 @@ __global__ void __launch_bounds__(kTX) k_cgc_inverse_df(int64_t S, int nx,
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) dmax = max(dmax, __shfl_xor_sync(0xffffffffu, dmax, off));
     if ((tid & 31) == 0 && dmax) atomicMax(delta + s, dmax);
+}
+
+template <int N>
+__global__ void __launch_bounds__(kTX) k_cgc_inverse_df(int64_t S, int nx,
+                                                         const Cplx<float>* __restrict__ q,
+                                                         const float* __restrict__ iscale,
+                                                         float2* __restrict__ Udf,
+                                                         unsigned long long* __restrict__ delta,
+                                                         float* __restrict__ c32,
+                                                         const int* __restrict__ active) {
+    __shared__ __align__(16) char smem[inv_df_smem<N>()];
+    const int64_t s = blockIdx.x;
+    if (!active[s]) return;
+    inv_df_tile<N>(s, blockIdx.y * kTX, nx, q, iscale, Udf, delta, c32, smem);
 }
 
 void launch_cgc_inverse_df(int64_t S, int N, int nx, const Cplx<float>* q, const float* iscale,
@@ -831,6 +907,211 @@ void launch_transpose(const double* in, double* out, int64_t S, int A, int B, cu
     if (S == 0) return;
     dim3 grid((unsigned)S, (unsigned)((A + 31) / 32), (unsigned)((B + 31) / 32));
     k_transpose<<<grid, dim3(32, 8), 0, st>>>(in, out, A, B);
+}
+
+}  // namespace klecgc
+
+// ---- the uneven batch: persistent stage kernels over all classes
+namespace klecgc {
+
+// Thread 0 takes the next task index; every thread of the CTA returns it.
+__device__ __forceinline__ int batch_next(int* queue, int* s_task) {
+    if (threadIdx.x == 0) *s_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int t = *s_task;
+    __syncthreads();
+    return t;
+}
+
+// (a): tiles of kTX rows (MIXED, FP64 transform of the accumulated right-hand
+// side) or kTXF rows (MIXED_DEFECT, FP32 defect transform).
+template <int DEFECT>
+__global__ void __launch_bounds__(DEFECT ? kTXF : kTX) k_batch_fwd(
+    const BatchClass* __restrict__ cls, const BatchTask* __restrict__ tasks, int ntasks,
+    int* queue, int k_host, const int* __restrict__ kdev) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int s_task;
+    const int k = kdev ? *kdev : k_host;
+    for (;;) {
+        const int t = batch_next(queue, &s_task);
+        if (t >= ntasks) break;
+        const BatchTask tk = tasks[t];
+        const BatchClass& C = cls[tk.c];
+        if (!C.active[tk.s]) continue;
+        if (DEFECT) {
+            const int x0 = tk.part * kTXF;
+#define KLECGC_BF(NN)                                                                          \
+    fwd_df_tile<NN>(tk.s, x0, C.nx, C.fout, C.Facc0, C.Facc1, k, C.Udf, C.wT, (float)C.dTreact, \
+                    C.sc32, C.p32, smem)
+            KLECGC_N_SWITCH(C.N, KLECGC_BF)
+#undef KLECGC_BF
+        } else {
+            const int x0 = tk.part * kTX;
+            const float* c = k == 0 ? nullptr : C.c32;
+#define KLECGC_BA(NN)                                                                          \
+    fwd_acc_tile<NN>(tk.s, x0, C.nx, C.fout, c, C.U, C.wT, C.dTreact, C.alpha, C.sc64, C.sc32, \
+                     C.rs, C.p64, smem)
+            KLECGC_N_SWITCH(C.N, KLECGC_BA)
+#undef KLECGC_BA
+        }
+        __syncthreads();
+    }
+}
+
+// (b): chunks of 128 consecutive (sample, k) systems of one class.
+template <int DEFECT>
+__global__ void __launch_bounds__(128) k_batch_solve(const BatchClass* __restrict__ cls,
+                                                     const BatchTask* __restrict__ tasks,
+                                                     int ntasks, int* queue) {
+    __shared__ int s_task;
+    for (;;) {
+        const int t = batch_next(queue, &s_task);
+        if (t >= ntasks) break;
+        const BatchTask tk = tasks[t];
+        const BatchClass& C = cls[tk.c];
+        const int64_t sys = (int64_t)tk.part + threadIdx.x;
+        if (sys < C.S * C.K) {
+            const int64_t s = sys / C.K;
+            const int kk = (int)(sys - s * C.K);
+            if (C.active[s]) {
+                if (DEFECT)
+                    cgc_solve_one<float, float>(s, kk, C.K, C.nx, C.dinv32, C.lu32, C.wT32, C.p32);
+                else
+                    cgc_solve_one<double, double>(s, kk, C.K, C.nx, C.dinv64, C.lu64, C.wT, C.p64);
+            }
+        }
+    }
+}
+
+// (c) + update + increment norm: tiles of kTX rows.
+template <int DEFECT>
+__global__ void __launch_bounds__(kTX) k_batch_inv(const BatchClass* __restrict__ cls,
+                                                   const BatchTask* __restrict__ tasks, int ntasks,
+                                                   int* queue) {
+    extern __shared__ __align__(16) char smem[];
+    __shared__ int s_task;
+    for (;;) {
+        const int t = batch_next(queue, &s_task);
+        if (t >= ntasks) break;
+        const BatchTask tk = tasks[t];
+        const BatchClass& C = cls[tk.c];
+        if (!C.active[tk.s]) continue;
+        const int x0 = tk.part * kTX;
+        if (DEFECT) {
+#define KLECGC_BI(NN) inv_df_tile<NN>(tk.s, x0, C.nx, C.p32, C.isc32, C.Udf, C.delta, C.c32, smem)
+            KLECGC_N_SWITCH(C.N, KLECGC_BI)
+#undef KLECGC_BI
+        } else {
+#define KLECGC_BI(NN) \
+    inv_tile<double, NN>(tk.s, x0, C.nx, C.p64, C.isc64, C.U, 0, C.delta, C.c32, smem)
+            KLECGC_N_SWITCH(C.N, KLECGC_BI)
+#undef KLECGC_BI
+        }
+        __syncthreads();
+    }
+}
+
+// Stopping rule (Algorithm 2, Step 3) for every instance of the batch.
+__global__ void k_batch_conv(const BatchClass* __restrict__ cls, const BatchTask* __restrict__ inst,
+                             int64_t n, int k_host, const int* __restrict__ kdev,
+                             int* __restrict__ n_active) {
+    const int iter = kdev ? *kdev : k_host;
+    const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    bool still = false;
+    if (i < n) {
+        const BatchTask tk = inst[i];
+        const BatchClass& C = cls[tk.c];
+        const int64_t s = tk.s;
+        if (C.active[s]) {
+            const double d = __longlong_as_double((long long)C.delta[s]);
+            C.delta[s] = 0ull;
+            if (!isfinite(d)) {
+                C.active[s] = 0;
+                C.iters[s] = -2;
+                C.status[s] = 4;  // KLECGC_E_NONFINITE
+            } else if (d <= C.tol) {
+                C.active[s] = 0;
+                C.iters[s] = iter + 1;
+                C.status[s] = 0;
+            } else if (iter + 1 >= C.kmax) {
+                C.active[s] = 0;
+                C.iters[s] = -1;
+                C.status[s] = 3;  // KLECGC_E_NOT_CONVERGED
+            } else {
+                still = true;
+            }
+        }
+    }
+    const unsigned b = __ballot_sync(0xffffffffu, still);
+    if ((threadIdx.x & 31) == 0 && b) atomicAdd(n_active, __popc(b));
+}
+
+int batch_transform_tile(int defect) { return defect ? kTXF : kTX; }
+
+static size_t batch_fwd_smem(int defect) {
+    return defect ? fwd_df_smem<64>() : fwd_acc_smem<64>();
+}
+static size_t batch_inv_smem(int defect) { return defect ? inv_df_smem<64>() : inv_smem<64>(); }
+
+int batch_grid(int kind, int defect) {
+    int dev = 0, sms = 0, per = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    cudaError_t e = cudaSuccess;
+    if (kind == 0) {
+        if (defect) {
+            cudaFuncSetAttribute(k_batch_fwd<1>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 (int)batch_fwd_smem(1));
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_fwd<1>, kTXF,
+                                                              batch_fwd_smem(1));
+        } else {
+            e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_fwd<0>, kTX,
+                                                              batch_fwd_smem(0));
+        }
+    } else if (kind == 1) {
+        e = defect ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_solve<1>, 128, 0)
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_solve<0>, 128, 0);
+    } else {
+        e = defect ? cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_inv<1>, kTX,
+                                                                   batch_inv_smem(1))
+                   : cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_inv<0>, kTX,
+                                                                   batch_inv_smem(0));
+    }
+    if (e != cudaSuccess || per < 1) per = 1;
+    return sms * per;
+}
+
+void launch_batch_fwd(int defect, const BatchClass* cls, const BatchTask* tasks, int ntasks,
+                      int* queue, int k_host, const int* kdev, int grid, cudaStream_t st) {
+    if (ntasks == 0) return;
+    if (defect)
+        k_batch_fwd<1><<<grid, kTXF, batch_fwd_smem(1), st>>>(cls, tasks, ntasks, queue, k_host, kdev);
+    else
+        k_batch_fwd<0><<<grid, kTX, batch_fwd_smem(0), st>>>(cls, tasks, ntasks, queue, k_host, kdev);
+}
+
+void launch_batch_solve(int defect, const BatchClass* cls, const BatchTask* tasks, int ntasks,
+                        int* queue, int grid, cudaStream_t st) {
+    if (ntasks == 0) return;
+    if (defect)
+        k_batch_solve<1><<<grid, 128, 0, st>>>(cls, tasks, ntasks, queue);
+    else
+        k_batch_solve<0><<<grid, 128, 0, st>>>(cls, tasks, ntasks, queue);
+}
+
+void launch_batch_inv(int defect, const BatchClass* cls, const BatchTask* tasks, int ntasks,
+                      int* queue, int grid, cudaStream_t st) {
+    if (ntasks == 0) return;
+    if (defect)
+        k_batch_inv<1><<<grid, kTX, batch_inv_smem(1), st>>>(cls, tasks, ntasks, queue);
+    else
+        k_batch_inv<0><<<grid, kTX, batch_inv_smem(0), st>>>(cls, tasks, ntasks, queue);
+}
+
+void launch_batch_conv(const BatchClass* cls, const BatchTask* inst, int64_t n, int k_host,
+                       const int* kdev, int* n_active, cudaStream_t st) {
+    if (n == 0) return;
+    k_batch_conv<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(cls, inst, n, k_host, kdev, n_active);
 }
 
 }  // namespace klecgc

@@ -48,6 +48,13 @@
 // instead of stalling at FP32 resolution.
 #include "common.cuh"
 
+// Rounding does not depend on where the body is compiled: every product of
+// the flux-form right-hand side is rounded on its own (__fmul_rn and friends
+// are never fused into an FMA by the compiler), and every intended FMA is an
+// explicit fmaf.  The same body runs in the per-solve kernel and in the
+// persistent stage kernel of the uneven batch, whose results must agree bit
+// for bit.
+
 namespace klecgc {
 
 constexpr int kFluxEvery = 16;
@@ -164,20 +171,17 @@ __global__ void __launch_bounds__(128) k_fine_table32(const double* __restrict__
     }
 }
 
+// The work of one CTA of 4 warps: intervals [part * 4 QS, part * 4 QS + 4 QS)
+// of sample s, the sample's table staged in smem2 (R * 32 * 24 bytes).
 template <int R, int QS, bool REACT>
-__global__ void __launch_bounds__(128) k_fine32(
-    int64_t S, int N, int nx, int J, int cps, float dt_react, float dt_f, int in_mode,
+__device__ __forceinline__ void fine32_cta(
+    int64_t s, int part, int N, int nx, int J, float dt_react, float dt_f, int in_mode,
     const double* __restrict__ U64, const float2* __restrict__ Udf, const double* __restrict__ u0,
-    const float* __restrict__ c32, Table32 tb, float* __restrict__ fout,
-    const int* __restrict__ active) {
-    extern __shared__ float2 smem2[];
+    const float* __restrict__ c32, Table32 tb, float* __restrict__ fout, float2* smem2) {
     float2* sGL = smem2;                 // [R][32] {G, l}
     float2* sFD = smem2 + R * 32;        // [R][32] {F, dinv}
     float* sU = reinterpret_cast<float*>(smem2 + 2 * R * 32);
     float* sWD = sU + R * 32;
-    const int64_t s = blockIdx.x / cps;
-    const int part = blockIdx.x - (int)(s * cps);
-    if (!active[s]) return;
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int n0 = (part * (blockDim.x >> 5) + warp) * QS;
     {
@@ -244,16 +248,16 @@ __global__ void __launch_bounds__(128) k_fine32(
         float vr = __shfl_down_sync(FULL, v[q][0], 1);
         if (lane == 0) vl = 0.f;
         if (lane == 31) vr = 0.f;
-        float fprev = sWD[lane] * (v[q][0] - vl);
+        float fprev = __fmul_rn(sWD[lane], v[q][0] - vl);
         float yprev = 0.f;
 #pragma unroll
         for (int j = 0; j < R; ++j) {
             const float lj = sGL[j * 32 + lane].y;
             const float wr = (j + 1 < R) ? sWD[(j + 1) * 32 + lane] : wd_right;
             const float vn = (j + 1 < R) ? v[q][j + 1] : vr;
-            const float f = wr * (vn - v[q][j]);
-            float rhs = f - fprev;
-            if (REACT) rhs += src - dt_react * v[q][j];
+            const float f = __fmul_rn(wr, vn - v[q][j]);
+            float rhs = __fsub_rn(f, fprev);
+            if (REACT) rhs = __fadd_rn(rhs, __fsub_rn(src, __fmul_rn(dt_react, v[q][j])));
             yprev = fmaf(-lj, yprev, rhs);
             w[q][j] = yprev;
             fprev = f;
@@ -282,7 +286,7 @@ __global__ void __launch_bounds__(128) k_fine32(
 #pragma unroll
             for (int q = 0; q < QS; ++q) {
                 float y = fmaf(fd.x, yin[q], w[q][j]);
-                float xh = fmaf(-uj, xn[q], y * fd.y);
+                float xh = fmaf(-uj, xn[q], __fmul_rn(y, fd.y));
                 w[q][j] = xh;
                 xn[q] = xh;
             }
@@ -325,10 +329,10 @@ __global__ void __launch_bounds__(128) k_fine32(
                     else
                         v[q][j] += fmaf(gl.x, zin[q], w[q][j]);
                     if (more) {
-                        const float f = sWD[j * 32 + lane] * (v[q][j] - (j ? v[q][j - 1] : vl));
+                        const float f = __fmul_rn(sWD[j * 32 + lane], v[q][j] - (j ? v[q][j - 1] : vl));
                         if (j) {
-                            float rhs = f - fprev;
-                            if (REACT) rhs += src - dt_react * v[q][j - 1];
+                            float rhs = __fsub_rn(f, fprev);
+                            if (REACT) rhs = __fadd_rn(rhs, __fsub_rn(src, __fmul_rn(dt_react, v[q][j - 1])));
                             yprev = fmaf(-lprev, yprev, rhs);
                             w[q][j - 1] = yprev;
                         }
@@ -337,9 +341,9 @@ __global__ void __launch_bounds__(128) k_fine32(
                     }
                 }
                 if (more) {
-                    const float f = wd_right * (vr - v[q][R - 1]);
-                    float rhs = f - fprev;
-                    if (REACT) rhs += src - dt_react * v[q][R - 1];
+                    const float f = __fmul_rn(wd_right, vr - v[q][R - 1]);
+                    float rhs = __fsub_rn(f, fprev);
+                    if (REACT) rhs = __fadd_rn(rhs, __fsub_rn(src, __fmul_rn(dt_react, v[q][R - 1])));
                     w[q][R - 1] = fmaf(-lprev, yprev, rhs);
                 }
             }
@@ -375,6 +379,20 @@ __global__ void __launch_bounds__(128) k_fine32(
                 if (n0 + q < N) o[q] = v[q][j];
         }
     }
+}
+
+template <int R, int QS, bool REACT>
+__global__ void __launch_bounds__(128) k_fine32(
+    int64_t S, int N, int nx, int J, int cps, float dt_react, float dt_f, int in_mode,
+    const double* __restrict__ U64, const float2* __restrict__ Udf, const double* __restrict__ u0,
+    const float* __restrict__ c32, Table32 tb, float* __restrict__ fout,
+    const int* __restrict__ active) {
+    extern __shared__ float2 smem2[];
+    const int64_t s = blockIdx.x / cps;
+    const int part = blockIdx.x - (int)(s * cps);
+    if (!active[s]) return;
+    fine32_cta<R, QS, REACT>(s, part, N, nx, J, dt_react, dt_f, in_mode, U64, Udf, u0, c32, tb,
+                             fout, smem2);
 }
 
 int fine32_rows_per_lane(int nx) {
@@ -455,6 +473,108 @@ void launch_fine32(int64_t S, int N, int nx, int J, double dt, double react, dou
 #undef KLECGC_F32
         default: break;
     }
+}
+
+}  // namespace klecgc
+
+// ---- the uneven batch: the fine stage as one persistent launch
+namespace klecgc {
+
+// Intervals per CTA task: 4 warps x QS systems (QS = 1 at 64 rows per lane,
+// for registers, else 2).
+static __host__ __device__ int fine32_qs(int R) { return R >= 64 ? 1 : 2; }
+
+int batch_fine_parts(int N, int R) {
+    const int per = 4 * fine32_qs(R);
+    return (N + per - 1) / per;
+}
+
+size_t batch_fine_smem(int R) { return (size_t)R * 32 * 24; }
+
+__device__ __forceinline__ int batch_next_fine(int* queue, int* s_task) {
+    if (threadIdx.x == 0) *s_task = atomicAdd(queue, 1);
+    __syncthreads();
+    const int t = *s_task;
+    __syncthreads();
+    return t;
+}
+
+// One launch per (R, reaction terms) group of classes: the body is compiled
+// for one row count, so its registers are those of the standalone kernel
+// (one kernel over every R spilled).  REACT = true is exact also without the
+// terms (it adds dt f0 - dt c v = 0 exactly), so a class with forcing uses it
+// in every iteration.
+template <int R, bool REACT>
+__global__ void __launch_bounds__(128) k_batch_fine(const BatchClass* __restrict__ cls,
+                                                    const BatchTask* __restrict__ tasks,
+                                                    int ntasks, int* queue, int k_host,
+                                                    const int* __restrict__ kdev) {
+    constexpr int QS = R >= 64 ? 1 : 2;
+    extern __shared__ float2 smem2[];
+    __shared__ int s_task;
+    const int k = kdev ? *kdev : k_host;
+    const int in_mode = k == 0 ? 0 : 1;
+    for (;;) {
+        const int t = batch_next_fine(queue, &s_task);
+        if (t >= ntasks) break;
+        const BatchTask tk = tasks[t];
+        const BatchClass& C = cls[tk.c];
+        if (!C.active[tk.s]) continue;
+        const int64_t n = C.S * (int64_t)R * 32;
+        const char* p = C.tab32;
+        Table32 tb{reinterpret_cast<float2*>(const_cast<char*>(p)),
+                   reinterpret_cast<float2*>(const_cast<char*>(p + 8 * n)),
+                   reinterpret_cast<float*>(const_cast<char*>(p + 16 * n)),
+                   reinterpret_cast<float*>(const_cast<char*>(p + 20 * n))};
+        fine32_cta<R, QS, REACT>(tk.s, tk.part, C.N, C.nx, C.J, C.dt_react, C.dt_f, in_mode,
+                                 C.defect ? nullptr : C.U, C.defect ? C.Udf : nullptr, C.u0,
+                                 C.c32, tb, C.fout, smem2);
+        __syncthreads();
+    }
+}
+
+template <int R, bool REACT>
+static void batch_fine_rr(const BatchClass* cls, const BatchTask* tasks, int ntasks, int* queue,
+                          int k_host, const int* kdev, int grid, cudaStream_t st) {
+    const size_t smem = batch_fine_smem(R);
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_batch_fine<R, REACT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem);
+        attr = true;
+    }
+    if (grid <= 0) {
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_batch_fine<R, REACT>, 128,
+                                                          smem) != cudaSuccess || per < 1)
+            per = 1;
+        grid = sms * per;
+    }
+    k_batch_fine<R, REACT><<<grid, 128, smem, st>>>(cls, tasks, ntasks, queue, k_host, kdev);
+}
+
+void launch_batch_fine(const BatchClass* cls, const BatchTask* tasks, int ntasks, int* queue,
+                       int k_host, const int* kdev, int R, int rt, int grid, cudaStream_t st) {
+    if (ntasks == 0) return;
+#define KLECGC_BFR(RR)                                                                         \
+    case RR:                                                                                   \
+        if (rt)                                                                                \
+            batch_fine_rr<RR, true>(cls, tasks, ntasks, queue, k_host, kdev, grid, st);       \
+        else                                                                                   \
+            batch_fine_rr<RR, false>(cls, tasks, ntasks, queue, k_host, kdev, grid, st);      \
+        break;
+    switch (R) {
+        KLECGC_BFR(2)
+        KLECGC_BFR(4)
+        KLECGC_BFR(8)
+        KLECGC_BFR(16)
+        KLECGC_BFR(32)
+        KLECGC_BFR(64)
+        default: break;
+    }
+#undef KLECGC_BFR
 }
 
 }  // namespace klecgc

@@ -25,6 +25,8 @@
 #include <cstdint>
 #include <mutex>
 
+#include <cuda_bf16.h>
+
 #include "common.cuh"
 
 namespace klecgc {
@@ -379,6 +381,217 @@ bool make_map(CUtensorMap* m, const float* base, int64_t rows, int Kp, int box_r
 }
 
 }  // namespace
+
+// ---- BF16 GEMM on the tensor cores for the learned guess's network
+// C[m][n] = sum_k A[m][k] B[n][k] (both operands BF16, K-major), FP32
+// accumulation in tensor memory (tcgen05.mma kind::f16 with BF16 A and B),
+// one 128 x 128 output tile per CTA, K-chunks of 64 (one 128-byte swizzle
+// row) by TMA into a four-stage ring: the same producer / MMA-issuer /
+// bounded-wait structure as k_guess_tc.  Epilogue: v = acc (+ bias[n]);
+// zmask: v = 0 where zmask[m][n] <= 0 (the ReLU derivative); C (FP32) and/or
+// Cb (BF16, ReLU applied when relu).
+namespace {
+
+constexpr int GM = 128, GN = 128, GK = 64, GSTAGES = 4;
+constexpr int GA_BYTES = GM * GK * 2, GB_BYTES = GN * GK * 2;
+constexpr int GSTAGE_BYTES = GA_BYTES + GB_BYTES;
+constexpr int GSMEM_BYTES = GSTAGES * GSTAGE_BYTES + 128 + 1024;
+
+// Instruction descriptor of kind::f16: D FP32 (bit 4), A and B BF16 (format
+// 1 at bits 7 and 10), both K-major, N >> 3 at bit 17, M >> 4 at bit 24.
+__host__ __device__ constexpr uint32_t make_idesc_bf16(int M, int N) {
+    return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) |
+           ((uint32_t)(M >> 4) << 24);
+}
+
+__device__ __forceinline__ void mma_bf16(uint32_t dtmem, uint64_t adesc, uint64_t bdesc,
+                                         uint32_t idesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dtmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"(accumulate));
+}
+
+__global__ void __launch_bounds__(128, 1) k_gemm_bf16_tc(int M, int N, int K,
+                                                        const __grid_constant__ CUtensorMap mA,
+                                                        const __grid_constant__ CUtensorMap mB,
+                                                        const float* __restrict__ bias,
+                                                        const float* __restrict__ zmask, int ldz,
+                                                        float* __restrict__ C, int ldc,
+                                                        __nv_bfloat16* __restrict__ Cb, int ldcb,
+                                                        int relu, int* __restrict__ err) {
+    extern __shared__ __align__(1024) char smem_raw[];
+    char* smem = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+    uint64_t* full = reinterpret_cast<uint64_t*>(smem + GSTAGES * GSTAGE_BYTES);   // [GSTAGES]
+    uint64_t* empty = full + GSTAGES;                                              // [GSTAGES]
+    uint32_t* tslot = reinterpret_cast<uint32_t*>(empty + GSTAGES);
+    int* flags = reinterpret_cast<int*>(tslot + 1);   // [0] skip, [1] issued, [2] committed
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int m0 = blockIdx.x * GM, n0 = blockIdx.y * GN;
+    if (threadIdx.x == 0) flags[0] = *reinterpret_cast<volatile int*>(err);
+    __syncthreads();
+    if (flags[0]) return;
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(
+                         smem_u32(tslot)),
+                     "r"(GN)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        for (int i = 0; i < GSTAGES; ++i) {
+            mbar_init(&full[i], 1);
+            mbar_init(&empty[i], 1);
+        }
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const uint32_t tmem = *tslot;
+    constexpr uint32_t idesc = make_idesc_bf16(GM, GN);
+    const int nch = (K + GK - 1) / GK;
+    bool ok = true;
+    int issued = 0, committed = 0;
+    if (warp == 0 && lane == 0) {
+        for (int c = 0; c < nch && ok; ++c) {
+            const int st = c % GSTAGES;
+            char* base = smem + st * GSTAGE_BYTES;
+            if (c >= GSTAGES) ok = mbar_wait(&empty[st], ((c - GSTAGES) / GSTAGES) & 1);
+            if (!ok) break;
+            mbar_expect_tx(&full[st], GSTAGE_BYTES);
+            tma_load_2d(base, &mA, c * GK, m0, &full[st]);
+            tma_load_2d(base + GA_BYTES, &mB, c * GK, n0, &full[st]);
+            issued = c + 1;
+        }
+        flags[1] = issued;
+    } else if (warp == 1 && lane == 0) {
+        for (int c = 0; c < nch && ok; ++c) {
+            const int st = c % GSTAGES;
+            char* base = smem + st * GSTAGE_BYTES;
+            ok = mbar_wait(&full[st], (c / GSTAGES) & 1);
+            if (!ok) break;
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const uint32_t a0 = smem_u32(base), b0 = smem_u32(base + GA_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < GK / 16; ++kk) {
+                const uint32_t ko = kk * 32;   // 16 BF16 values per K step
+                mma_bf16(tmem, make_desc_sw128(a0 + ko), make_desc_sw128(b0 + ko), idesc,
+                         (c | kk) ? 1u : 0u);
+            }
+            mma_commit(&empty[st]);
+            committed = c + 1;
+        }
+        flags[2] = committed;
+    }
+    ok = __syncthreads_and(ok);
+    issued = flags[1];
+    committed = flags[2];
+    bool done = true;
+    for (int c = committed - GSTAGES; c < committed; ++c)
+        if (c >= 0) done = mbar_wait(&empty[c % GSTAGES], (c / GSTAGES) & 1) && done;
+    if (!ok)
+        for (int c = issued - GSTAGES; c < issued; ++c)
+            if (c >= committed && c >= 0) done = mbar_wait(&full[c % GSTAGES], (c / GSTAGES) & 1) && done;
+    ok = __syncthreads_and(ok && done && committed == nch);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        const uint32_t lane_addr = tmem + ((uint32_t)(warp * 32) << 16);
+#pragma unroll 1
+        for (int cb = 0; cb < GN; cb += 32) {
+            float v[32];
+            tmem_ld32(lane_addr + cb, v);
+            if (row < M) {
+#pragma unroll
+                for (int i = 0; i < 32; ++i) {
+                    const int n = n0 + cb + i;
+                    if (n >= N) break;
+                    float x = v[i];
+                    if (bias) x += bias[n];
+                    if (zmask && !(zmask[(int64_t)row * ldz + n] > 0.f)) x = 0.f;
+                    if (C) C[(int64_t)row * ldc + n] = x;
+                    if (Cb) Cb[(int64_t)row * ldcb + n] = __float2bfloat16(relu ? fmaxf(x, 0.f) : x);
+                }
+            }
+        }
+    } else if (threadIdx.x == 0) {
+        atomicExch(err, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (warp == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(GN)
+                     : "memory");
+}
+
+// out[c][r] = in[r][c] for an R x Cc BF16 matrix (leading dimension ld_in).
+__global__ void k_transpose_bf16(const __nv_bfloat16* __restrict__ in, int R, int Cc, int ld_in,
+                                 __nv_bfloat16* __restrict__ out) {
+    __shared__ __nv_bfloat16 tile[32][34];
+    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int r = r0 + y, c = c0 + threadIdx.x;
+        tile[y][threadIdx.x] = (r < R && c < Cc) ? in[(int64_t)r * ld_in + c] : __float2bfloat16(0.f);
+    }
+    __syncthreads();
+    for (int y = threadIdx.y; y < 32; y += blockDim.y) {
+        const int c = c0 + y, r = r0 + threadIdx.x;
+        if (c < Cc && r < R) out[(int64_t)c * R + r] = tile[threadIdx.x][y];
+    }
+}
+
+// [rows][K] BF16 (row stride ld elements), box 64 x box_rows, 128-byte swizzle.
+bool make_map_bf16(CUtensorMap* m, const __nv_bfloat16* base, int64_t rows, int K, int ld,
+                   int box_rows) {
+    EncodeTiled fn = encode_fn();
+    if (!fn) return false;
+    const cuuint64_t dims[2] = {(cuuint64_t)K, (cuuint64_t)rows};
+    const cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+    const cuuint32_t box[2] = {(cuuint32_t)GK, (cuuint32_t)box_rows};
+    const cuuint32_t es[2] = {1, 1};
+    return fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<__nv_bfloat16*>(base), dims,
+              strides, box, es, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+              CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) ==
+           CUDA_SUCCESS;
+}
+
+}  // namespace
+
+void launch_transpose_bf16(const __nv_bfloat16* in, int R, int Cc, int ld_in, __nv_bfloat16* out,
+                           cudaStream_t st) {
+    if (R == 0 || Cc == 0) return;
+    dim3 grid((unsigned)((Cc + 31) / 32), (unsigned)((R + 31) / 32));
+    k_transpose_bf16<<<grid, dim3(32, 8), 0, st>>>(in, R, Cc, ld_in, out);
+}
+
+bool gemm_bf16_tc_ok(int M, int N, int K, const void* A, int lda, const void* B, int ldb) {
+    // TMA: 16-byte aligned bases, row strides a multiple of 16 bytes; at least
+    // one full K-chunk and one tile in M
+    return M >= 64 && N >= 32 && K >= GK && (lda % 8) == 0 && (ldb % 8) == 0 &&
+           (reinterpret_cast<uintptr_t>(A) % 16) == 0 && (reinterpret_cast<uintptr_t>(B) % 16) == 0;
+}
+
+cudaError_t launch_gemm_bf16_tc(int M, int N, int K, const __nv_bfloat16* A, int lda,
+                                const __nv_bfloat16* B, int ldb, const float* bias,
+                                const float* zmask, int ldz, float* C, int ldc,
+                                __nv_bfloat16* Cb, int ldcb, bool relu, int* err,
+                                cudaStream_t st) {
+    if (M == 0 || N == 0) return cudaSuccess;
+    CUtensorMap mA, mB;
+    if (!make_map_bf16(&mA, A, M, K, lda, GM) || !make_map_bf16(&mB, B, N, K, ldb, GN))
+        return cudaErrorInvalidValue;
+    static bool attr = false;
+    if (!attr) {
+        cudaFuncSetAttribute(k_gemm_bf16_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             GSMEM_BYTES);
+        attr = true;
+    }
+    dim3 grid((unsigned)((M + GM - 1) / GM), (unsigned)((N + GN - 1) / GN));
+    k_gemm_bf16_tc<<<grid, 128, GSMEM_BYTES, st>>>(M, N, K, mA, mB, bias, zmask, ldz, C, ldc, Cb,
+                                                   ldcb, relu ? 1 : 0, err);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_guess_tc(int64_t S, int64_t NC, int Kp, const float* psi_hi,
                             const float* psi_lo, const float* Wt_hi, const float* Wt_lo,

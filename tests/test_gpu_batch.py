@@ -1,8 +1,11 @@
 """Uneven batch (klecgc_solve_batch): instances with different grids, time
 partitions and fine steps solved together equal the same instances solved
 class by class with klecgc_solve (bit for bit: every sample's arithmetic is
-independent of the batch composition), which the parity tests pin to the
-oracle; a few instances are also checked against the oracle directly."""
+independent of the batch composition; on the mixed paths the batch runs each
+stage as one persistent launch over all classes with the same per-tile
+bodies, and the per-class solves use the same fine kernel with the
+autotuner off), which the parity tests pin to the oracle; a few instances
+are also checked against the oracle directly."""
 import numpy as np
 import pytest
 
@@ -32,11 +35,13 @@ def _solvers():
     return [gpu_solver(name, **over) for name, over in CTXS]
 
 
-@pytest.mark.parametrize("precision", [0, 2], ids=["fp64", "mixed_defect"])
+@pytest.mark.parametrize("precision", [0, 1, 2], ids=["fp64", "mixed", "mixed_defect"])
 @pytest.mark.parametrize("host", [False, True], ids=["device", "host"])
 def test_batch_equals_per_class_solves(precision, host):
     import paper_2510_26180_gb300 as pkg
     sv = _solvers()
+    for s, _ in sv:
+        s.set_tuning(0)
     n = 40
     ci, J = _batch(n, 7)
     M = sv[0][1].M
@@ -71,6 +76,8 @@ def test_batch_equals_per_class_solves(precision, host):
                 blk = U[off[i]:off[i + 1]].reshape(w.N, w.nx)
                 assert np.array_equal(blk, Uc[q]), (c, j, i)
                 assert it[i] == itc[q]
+    for s, _ in sv:
+        s.set_tuning(1)
 
 
 def test_batch_instances_match_oracle():

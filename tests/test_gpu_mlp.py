@@ -156,3 +156,57 @@ def _train_and_compare(pkg, solver, w, residual):
         means[name] = float(it.float().mean())
     print(f"held-out ({'residual' if residual else 'direct'}): learned-guess error "
           f"{err.mean():.3e}, gPC {err_gpc.mean():.3e}, mean iterations {means}")
+
+
+def _block_errors(gg, go, sizes):
+    out = []
+    k = 0
+    for i, o in zip(sizes[:-1], sizes[1:]):
+        for n in (o * i, o):
+            a, b = gg[k:k + n], go[k:k + n]
+            k += n
+            out.append((np.linalg.norm(a - b) / np.linalg.norm(b),
+                        a @ b / (np.linalg.norm(a) * np.linalg.norm(b))))
+    return out
+
+
+def test_gradient_at_batch_256_on_tcgen05_matches_fp64_oracle():
+    # batch 256: the products of the hidden and output layers run on the
+    # tcgen05 tensor cores (M, K >= 64); same bars as the small batch
+    solver, w = gpu_solver("heat1d_nx63")
+    sizes = omlp.layer_sizes(w.M, w.N)
+    theta = _bf16_weights(omlp.init_params(sizes, 8), sizes)
+    solver.mlp_set(theta)
+    B = 256
+    xi = draw_xi(B, w.M, 92)
+    tg = (np.random.default_rng(4).standard_normal((B, w.N * 64)) * 0.5).astype(np.float32)
+    grad = torch.empty(theta.size, dtype=torch.float32, device="cuda")
+    loss = solver.mlp_loss_grad(T(xi), T(tg), B, grad)
+    lo, go = omlp.loss_and_grad(theta.astype(np.float64), sizes, xi, tg.astype(np.float64))
+    assert abs(loss - lo) <= 1e-3 * lo
+    errs = _block_errors(grad.cpu().numpy(), go, sizes)
+    print("per-block relative L2 / cosine:", [(f"{e:.2e}", f"{c:.5f}") for e, c in errs])
+    for e, c in errs:
+        assert e <= 5e-2 and c >= 0.999
+
+
+def test_guess_at_512_samples_on_tcgen05_matches_oracle_forward():
+    solver, w = gpu_solver("heat1d_nx63")
+    sizes = omlp.layer_sizes(w.M, w.N)
+    theta = _bf16_weights(omlp.init_params(sizes, 9), sizes)
+    rng = np.random.default_rng(8)
+    mean = rng.standard_normal(w.N * 64).astype(np.float32)
+    std = (0.5 + rng.random(w.N * 64)).astype(np.float32)
+    solver.mlp_set(theta, mean, std)
+    S = 512
+    xi = draw_xi(S, w.M, 93)
+    G = torch.empty((S, w.N, w.nx), dtype=torch.float64, device="cuda")
+    solver.mlp_guess(T(xi), S, G)
+    G = G.cpu().numpy()
+    Y = omlp.forward(theta.astype(np.float64), sizes, xi)[2]
+    worst = 0.0
+    for s in range(0, S, 37):
+        expect = omlp.upsample((mean + std * Y[s]).reshape(w.N, 64), w.nx)
+        worst = max(worst, rel(G[s], expect))
+    print("worst relative L2 of the guess:", worst)
+    assert worst <= 2e-2
