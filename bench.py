@@ -21,6 +21,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -326,6 +327,31 @@ def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
                 else "nominal GB300 FP64 1.25 TFLOP/s",
                 "work": f"{flops / max(launches, 1):.3e} flop per launch "
                         f"(5 per row and fine step)"}
+    if cls in ("cgc_fwd", "cgc_solve", "cgc_inv") and prec in ("mixed", "fp64"):
+        # the CGC in FP64 is bound by the FP64 pipe (1/64 of the FP32 rate per
+        # SM on this part), not by HBM: algorithmic FP64 flop per point (per
+        # (sample, n, x)), an FMA counted as 2:
+        #   forward  real FFT along n, 2.5 log2 N (radix-2 count), the Lambda
+        #            scale 1 and the right-hand side: its FP64 accumulation 1
+        #            (mixed: the jump is formed in FP32 on the increment) or
+        #            (I + dT A) F - prev, 7 (fp64)
+        #   solve    complex substitutions with stored factors on K = N/2 + 1
+        #            of N spectral values: forward 8 + backward 14 per value
+        #   inverse  real inverse FFT 2.5 log2 N, the Lambda^{-1} scale 1, the
+        #            update 1 and |U^{k+1} - U^k| with its max 2
+        lg = 2.5 * math.log2(w.N)
+        K = w.N // 2 + 1
+        per_pt = {"cgc_fwd": lg + 1 + (1 if prec == "mixed" else 7),
+                  "cgc_solve": 22.0 * K / w.N,
+                  "cgc_inv": lg + 4}[cls]
+        flops = per_pt * pts
+        ach = flops / (ms / 1e3) / 1e12
+        return {"kernel": cls, "bound": "alu", "achieved": ach, "peak": FP64_ALU_PEAK,
+                "unit": "TFLOP/s", "frac": ach / FP64_ALU_PEAK,
+                "traffic": traffic_per_launch(cls, prec, pts, launches),
+                "peak_source": "nominal GB300 FP64 1.25 TFLOP/s",
+                "work": f"{flops / max(launches, 1):.3e} FP64 flop per launch "
+                        f"({per_pt:.1f} per point)"}
     # algorithmic HBM bytes per point (per (sample, n, x)) of the CGC kernels;
     # a spectrum value counts K/N per point (k <= N/2 only):
     #   fp64          forward: r 8 in, p 16K/N out; inverse: q 16K/N, U 8 in + 8 out

@@ -447,8 +447,10 @@ klecgc_status klecgc_set_loop(klecgc_ctx* ctx, int32_t mode);
  * Launch-shape autotuner (a library facility; the paper has no counterpart).
  * mode 1 (default): the first solve of a context for a given (nx, N, J) on a
  * given GPU times every candidate launch shape of the FP32 fine propagator
- * (W warps per pair of intervals, R rows per lane, 32 W R >= nx + 1) on up
- * to 512 of its samples and keeps the fastest; later solves reuse the choice.
+ * ("W<W>R<R>": W warps per pair of intervals, R rows per lane, 32 W R >=
+ * nx + 1, W = 0 the shared-memory kernel; "L<L>R<R>": one interval per warp
+ * with the factors in registers, L intervals per warp in turn) on up to 512
+ * of its samples and keeps the fastest; later solves reuse the choice.
  * Every shape computes the same backward-Euler steps; the shapes split the
  * rows of a system differently between lanes, so results agree to FP32
  * rounding of the fine propagator, not bit for bit: a solve is reproducible
@@ -461,8 +463,10 @@ klecgc_status klecgc_set_loop(klecgc_ctx* ctx, int32_t mode);
 klecgc_status klecgc_set_tuning(klecgc_ctx* ctx, int32_t mode, const char* cache_path);
 
 /* The autotuner's choices as a JSON object of "<GPU>|<kernel>|nx=..|N=..|J=..":
- * "<shape>" strings, NUL-terminated into buf (capacity bytes, truncated if
- * short; buf may be NULL); *length receives the full length. */
+ * "<shape>" strings, plus for each shape timed by this context a
+ * "<same key>|ms@S=<samples>": "<shape>:<ms per launch> ..." record of the
+ * candidates, NUL-terminated into buf (capacity bytes, truncated if short;
+ * buf may be NULL); *length receives the full length. */
 klecgc_status klecgc_tuning_report(const klecgc_ctx* ctx, char* buf, int64_t capacity,
                                    int64_t* length);
 

@@ -348,13 +348,18 @@ klecgc_status choose_fine32w(klecgc_ctx* ctx, int64_t S, int N, int nx, int J, d
                              const double* a, const FineCoef64* f64, cudaStream_t st,
                              Fine32wShape* out) {
     // candidate W = 0: k_fine32 (one warp per pair of intervals, the factors
-    // in shared memory, R rows per lane by its own rule); W >= 1: k_fine32w
+    // in shared memory, R rows per lane by its own rule); W >= 1: k_fine32w;
+    // L >= 1: k_fine32r (one interval per warp, factors in registers, L
+    // intervals per warp in turn)
     const int R0 = fine32_rows_per_lane(nx);
     *out = {0, R0};
     std::vector<Fine32wShape> cands;
     if (R0) cands.push_back({0, R0});
-    if (!ctx->fine_smem_only)
+    if (!ctx->fine_smem_only) {
         for (const Fine32wShape& c : fine32w_candidates(nx)) cands.push_back(c);
+        for (int L : {1, 4})
+            if (fine32r_supported(R0, L)) cands.push_back({0, R0, L});
+    }
     if (ctx->tune_mode == 0 || cands.size() < 2 || S == 0) return KLECGC_OK;
     const std::string key = tune_key(ctx, "fine32", nx, N, J);
     auto decode = [&](const std::string& v, Fine32wShape* sh) {
@@ -363,14 +368,20 @@ klecgc_status choose_fine32w(klecgc_ctx* ctx, int64_t S, int N, int nx, int J, d
             *sh = {W, R};
             return W == 0 ? R == R0 : fine32w_supported(*sh);
         }
+        if (std::sscanf(v.c_str(), "L%dR%d", &W, &R) == 2) {
+            *sh = {0, R, W};
+            return R == R0 && fine32r_supported(R, W);
+        }
         return false;
     };
     auto it = ctx->tuned.find(key);
     if (it != ctx->tuned.end() && decode(it->second, out)) return KLECGC_OK;
     const int64_t St = std::min<int64_t>(S, 512);
     size_t tab = R0 ? fine_table32_bytes(St, R0) : 0;
-    for (auto& c : cands)
-        if (c.W) tab = std::max(tab, fine_table32w_bytes(St, c));
+    for (auto& c : cands) {
+        if (c.L) tab = std::max(tab, fine_table32r_bytes(St, c.R));
+        else if (c.W) tab = std::max(tab, fine_table32w_bytes(St, c));
+    }
     WS(float, tb, "tune_table", tab / sizeof(float));
     WS(float, cz, "tune_c", St * (int64_t)nx * N);
     WS(float, fo, "tune_out", St * (int64_t)nx * N);
@@ -382,16 +393,19 @@ klecgc_status choose_fine32w(klecgc_ctx* ctx, int64_t S, int N, int nx, int J, d
     TRY(cudaEventCreate(&e1));
     float best = 0.f;
     Fine32wShape pick = *out;
+    auto name = [](const Fine32wShape& c) {
+        return c.L ? "L" + std::to_string(c.L) + "R" + std::to_string(c.R)
+                   : "W" + std::to_string(c.W) + "R" + std::to_string(c.R);
+    };
+    std::string times;
     auto run = [&](const Fine32wShape& c) {
-        if (c.W == 0)
-            launch_fine32(St, N, nx, J, dt, 0.0, 0.0, 1, nullptr, nullptr, ctx->u0, cz, tb, fo,
-                          act, st);
-        else
-            launch_fine32w(c, St, N, nx, J, dt, 0.0, 0.0, 1, nullptr, nullptr, ctx->u0, cz, tb,
-                           fo, act, st);
+        launch_fine_any(c, St, N, nx, J, dt, 0.0, 0.0, 1, nullptr, nullptr, ctx->u0, cz, tb, fo,
+                        act, st);
     };
     for (const Fine32wShape& c : cands) {
-        if (c.W == 0)
+        if (c.L)
+            launch_fine_table32r(f64, St, nx, c.R, tb, st);
+        else if (c.W == 0)
             launch_fine_table32(a, St, nx, c.R, ctx->h, dt, ctx->prob.reaction, tb, st);
         else
             launch_fine_table32w(f64, St, nx, c, tb, st);
@@ -411,12 +425,18 @@ klecgc_status choose_fine32w(klecgc_ctx* ctx, int64_t S, int N, int nx, int J, d
             best = ms;
             pick = c;
         }
+        char buf[48];
+        std::snprintf(buf, sizeof(buf), "%s%s:%.4f", times.empty() ? "" : " ", name(c).c_str(),
+                      ms / 2);
+        times += buf;
     }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     TRY(cudaGetLastError());
     *out = pick;
-    ctx->tuned[key] = "W" + std::to_string(pick.W) + "R" + std::to_string(pick.R);
+    ctx->tuned[key] = name(pick);
+    // the measured candidates (ms per launch on St samples), for the record
+    ctx->tuned[key + "|ms@S=" + std::to_string(St)] = times;
     tune_save(ctx);
     return KLECGC_OK;
 }
@@ -446,9 +466,13 @@ klecgc_status build_operators(klecgc_ctx* ctx, const double* xi_d, int64_t S, in
         Fine32wShape sh;
         if ((s = choose_fine32w(ctx, S, N, nx, J, dT / J, op->a, f64, st, &sh)) != KLECGC_OK)
             return s;
-        const size_t tbytes = sh.W ? fine_table32w_bytes(S, sh) : fine_table32_bytes(S, sh.R);
+        const size_t tbytes = sh.L   ? fine_table32r_bytes(S, sh.R)
+                              : sh.W ? fine_table32w_bytes(S, sh)
+                                     : fine_table32_bytes(S, sh.R);
         WS(float, tb, "tab32w", tbytes / sizeof(float));
-        if (sh.W)
+        if (sh.L)
+            ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_table32r(f64, S, nx, sh.R, tb, st); });
+        else if (sh.W)
             ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_table32w(f64, S, nx, sh, tb, st); });
         else
             ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_table32(op->a, S, nx, sh.R, ctx->h, dT / J, ctx->prob.reaction, tb, st); });
@@ -2594,7 +2618,7 @@ klecgc_status batch_persistent(klecgc_ctx* c0, std::vector<SolveRun>& runs, int6
         C.iters = R.iters;
         C.status = R.status;
         C.delta = R.delta;
-        if (R.op.sh32.W != 0 || !C.R) return fail(KLECGC_E_CUDA, "batch: a class without the shared-memory fine kernel");
+        if (R.op.sh32.W != 0 || R.op.sh32.L != 0 || !C.R) return fail(KLECGC_E_CUDA, "batch: a class without the shared-memory fine kernel");
     }
     // task lists, longest first within each stage
     struct Group {

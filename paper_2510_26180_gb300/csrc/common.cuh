@@ -176,8 +176,11 @@ void launch_fine32(int64_t S, int N, int nx, int J, double dt, double react, dou
 // The same with every factor in registers: W warps per pair of intervals,
 // R rows per lane (32 W R >= nx + 1); the table is built from the FP64
 // factors of launch_fine_factors (fine step dt).
+// L >= 1 selects k_fine32r instead: one interval per warp with the factors
+// in registers, L intervals per warp in turn (W unused, R rows per lane).
 struct Fine32wShape {
     int W, R;
+    int L = 0;
 };
 Fine32wShape fine32w_shape(int nx);
 std::vector<Fine32wShape> fine32w_candidates(int nx);
@@ -189,7 +192,15 @@ void launch_fine32w(Fine32wShape sh, int64_t S, int N, int nx, int J, double dt,
                     double forcing, int in_mode, const double* U64, const float2* Udf,
                     const double* u0, const float* c32, const float* table, float* fout,
                     const int* active, cudaStream_t st);
-// Either kernel: sh.W == 0 is k_fine32 (table of launch_fine_table32 with
+size_t fine_table32r_bytes(int64_t S, int R);
+void launch_fine_table32r(const FineCoef64* fc, int64_t S, int nx, int R, float* table,
+                          cudaStream_t st);
+bool fine32r_supported(int R, int L);
+void launch_fine32r(int R, int L, int64_t S, int N, int nx, int J, double dt, double react,
+                    double forcing, int in_mode, const double* U64, const float2* Udf,
+                    const double* u0, const float* c32, const float* table, float* fout,
+                    const int* active, cudaStream_t st);
+// Any of the three: sh.L >= 1 is k_fine32r; else sh.W == 0 is k_fine32 (table of launch_fine_table32 with
 // sh.R rows per lane), sh.W >= 1 is k_fine32w.
 void launch_fine_any(Fine32wShape sh, int64_t S, int N, int nx, int J, double dt, double react,
                      double forcing, int in_mode, const double* U64, const float2* Udf,

@@ -15,8 +15,10 @@ pytestmark = pytest.mark.gpu
 
 torch = pytest.importorskip("torch")
 
-OVER = dict(nx=511, N=16, J=8)   # candidates: factors in shared memory (W0R16) or in
-                                 # registers on 1 warp x 16 rows or 2 warps x 8 rows
+OVER = dict(nx=511, N=16, J=8)   # candidates: factors in shared memory (W0R16), in
+                                 # registers on 1 warp x 16 rows or 2 warps x 8 rows, or
+                                 # one interval per warp (1 or 4 in turn) x 16 rows
+ALL = ("W0R16", "W1R16", "W2R8", "L1R16", "L4R16")
 
 
 def _solve(solver, w, xi, precision):
@@ -42,10 +44,10 @@ def test_tuner_records_a_valid_choice_and_shapes_agree(tmp_path):
     solver.set_tuning(1)
     _solve(solver, w, xi, pkg.MIXED)
     rep = solver.tuning_report()
-    keys = [k for k in rep if "|fine32|nx=511|N=16|J=8" in k]
-    assert len(keys) == 1 and rep[keys[0]] in ("W0R16", "W1R16", "W2R8"), rep
+    keys = [k for k in rep if "|fine32|nx=511|N=16|J=8" in k and "|ms" not in k]
+    assert len(keys) == 1 and rep[keys[0]] in ALL, rep
     results = {}
-    for shape in ("W0R16", "W1R16", "W2R8"):
+    for shape in ALL:
         path = tmp_path / f"{shape}.json"
         path.write_text(json.dumps({keys[0]: shape}))
         solver.set_tuning(1, str(path))
@@ -56,7 +58,7 @@ def test_tuner_records_a_valid_choice_and_shapes_agree(tmp_path):
                 assert rel(U[s], ref[s]) <= 1e-6, (shape, prec, s)
         assert solver.tuning_report()[keys[0]] == shape
     for prec in (pkg.MIXED, pkg.MIXED_DEFECT):
-        for shape in ("W1R16", "W2R8"):
+        for shape in ALL[1:]:
             a, b = results[("W0R16", prec)], results[(shape, prec)]
             assert np.all(np.abs(a - b) <= 1)
     solver.set_tuning(1)
