@@ -481,11 +481,12 @@ klecgc_status klecgc_krylov_stats(const klecgc_ctx* ctx, int64_t* its_fine, int6
  * Context persistence (a library facility; the paper's offline stage is
  * re-run otherwise).  klecgc_save writes the problem, the surrogate tables
  * (input-KL basis, u0, gPC multi-indices, ubar, W), the Krylov settings, the
- * 2D solve method and,
+ * 2D solve method, the autotuner's choices and,
  * when set, the learned network to `path` (a binary file of this library's
  * own format, native byte order).  klecgc_load creates a context on the
  * current CUDA device from such a file: its guesses and solves equal those
- * of the saved context.  Errors: INVALID_ARG (cannot open, not a context
+ * of the saved context (bit for bit on the same GPU model, whose launch
+ * shapes the saved choices name).  Errors: INVALID_ARG (cannot open, not a context
  * file, inconsistent or truncated), OUT_OF_MEMORY, CUDA.
  */
 klecgc_status klecgc_save(const klecgc_ctx* ctx, const char* path);

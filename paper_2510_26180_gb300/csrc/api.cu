@@ -309,16 +309,9 @@ std::string tune_json(const klecgc_ctx* ctx) {
     return out + (first ? "}" : "\n}");
 }
 
-// Reads "key": "value" pairs of a flat JSON object (the format tune_json writes).
-void tune_load(klecgc_ctx* ctx) {
-    if (ctx->tune_path.empty()) return;
-    FILE* f = std::fopen(ctx->tune_path.c_str(), "rb");
-    if (!f) return;
-    std::string txt;
-    char buf[4096];
-    size_t n;
-    while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, n);
-    std::fclose(f);
+// Reads "key": "value" pairs of a flat JSON object (the format tune_json
+// writes) into the choices.
+void tune_parse(klecgc_ctx* ctx, const std::string& txt) {
     size_t pos = 0;
     std::vector<std::string> strs;
     while ((pos = txt.find('"', pos)) != std::string::npos) {
@@ -328,6 +321,18 @@ void tune_load(klecgc_ctx* ctx) {
         pos = end + 1;
     }
     for (size_t i = 0; i + 1 < strs.size(); i += 2) ctx->tuned[strs[i]] = strs[i + 1];
+}
+
+void tune_load(klecgc_ctx* ctx) {
+    if (ctx->tune_path.empty()) return;
+    FILE* f = std::fopen(ctx->tune_path.c_str(), "rb");
+    if (!f) return;
+    std::string txt;
+    char buf[4096];
+    size_t n;
+    while ((n = std::fread(buf, 1, sizeof(buf), f)) > 0) txt.append(buf, n);
+    std::fclose(f);
+    tune_parse(ctx, txt);
 }
 
 void tune_save(const klecgc_ctx* ctx) {
@@ -1060,7 +1065,7 @@ void klecgc_free(klecgc_ctx* ctx) {
 }  // extern "C"
 namespace {
 constexpr char kMagic[8] = {'K', 'L', 'E', 'C', 'G', 'C', 'v', '1'};
-constexpr int32_t kVersion = 5;   // 5: learned-guess mode
+constexpr int32_t kVersion = 6;   // 5: learned-guess mode; 6: autotuner choices
 
 struct FileHead {
     char magic[8];
@@ -1133,6 +1138,14 @@ klecgc_status klecgc_save(const klecgc_ctx* ctx, const char* path) {
     if (ok && ctx->mlp.ready)
         ok = put_dev(f, ctx->mlp.theta, ctx->mlp.P) && put_dev(f, ctx->mlp.mean, ctx->mlp.D) &&
              put_dev(f, ctx->mlp.stdv, ctx->mlp.D);
+    if (ok) {
+        // the autotuner's choices, so that a loaded context reruns the same
+        // kernels (and reproduces solves bit for bit)
+        const std::string tj = tune_json(ctx);
+        const int64_t len = (int64_t)tj.size();
+        ok = std::fwrite(&len, sizeof(len), 1, f) == 1 &&
+             (len == 0 || std::fwrite(tj.data(), 1, (size_t)len, f) == (size_t)len);
+    }
     cudaSetDevice(cur);
     ok = (std::fclose(f) == 0) && ok;
     return ok ? KLECGC_OK : fail(KLECGC_E_CUDA, std::string("writing ") + path + " failed");
@@ -1231,6 +1244,15 @@ klecgc_status klecgc_load(const char* path, klecgc_ctx** out, void* stream) {
             return bail(fail(KLECGC_E_CUDA, "network upload"));
         launch_f32_to_bf16(q.P, q.theta, q.thb, st);
         q.ready = true;
+    }
+    {
+        int64_t len = -1;
+        if (std::fread(&len, sizeof(len), 1, f) != 1 || len < 0 || len > (1 << 24))
+            return bail(fail(KLECGC_E_INVALID_ARG, "truncated file (autotuner choices)"));
+        std::string tj((size_t)len, '\0');
+        if (len && std::fread(&tj[0], 1, (size_t)len, f) != (size_t)len)
+            return bail(fail(KLECGC_E_INVALID_ARG, "truncated file (autotuner choices)"));
+        tune_parse(ctx, tj);
     }
     if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(st) != cudaSuccess)
         return bail(fail(KLECGC_E_CUDA, "upload"));

@@ -40,6 +40,9 @@ __device__ __forceinline__ T tw_cos(int t) { return (T)tw_cos_d(t); }
 template <typename T>
 __device__ __forceinline__ T tw_sin(int t) { return (T)tw_sin_d(t); }
 
+__device__ __forceinline__ float fmat(float a, float b, float c) { return fmaf(a, b, c); }
+__device__ __forceinline__ double fmat(double a, double b, double c) { return fma(a, b, c); }
+
 template <int L>
 __host__ __device__ constexpr int bitrev(int i) {
     int r = 0;
@@ -75,22 +78,33 @@ __device__ __forceinline__ void cfft(T (&re)[L], T (&im)[L]) {
 #pragma unroll
             for (int b = 0; b < L; b += 2 * half) {
                 const int i0 = b + k, i1 = i0 + half;
-                T xr, xi;
-                if (k == 0) {
-                    xr = re[i1];
-                    xi = im[i1];
-                } else if (t == kTwiddleN / 4) {
-                    // w = -i (forward) or +i (inverse): a swap and a sign
-                    xr = INV ? -im[i1] : im[i1];
-                    xi = INV ? re[i1] : -re[i1];
+                if (k == 0 || t == kTwiddleN / 4) {
+                    // w = 1, or w = -i (forward) / +i (inverse): a swap and a sign
+                    T xr, xi;
+                    if (k == 0) {
+                        xr = re[i1];
+                        xi = im[i1];
+                    } else {
+                        xr = INV ? -im[i1] : im[i1];
+                        xi = INV ? re[i1] : -re[i1];
+                    }
+                    re[i1] = re[i0] - xr;
+                    im[i1] = im[i0] - xi;
+                    re[i0] = re[i0] + xr;
+                    im[i0] = im[i0] + xi;
                 } else {
-                    xr = re[i1] * wr - im[i1] * wi;
-                    xi = re[i1] * wi + im[i1] * wr;
+                    // x0 + w x1 by two FMAs per component, x0 - w x1 = 2 x0 -
+                    // (x0 + w x1) by one: six operations where the product
+                    // w x1 first and then the sum and difference take eight;
+                    // each output is still within a few roundings of
+                    // |x0| + |w x1|
+                    const T ar = fmat(wr, re[i1], fmat(-wi, im[i1], re[i0]));
+                    const T ai = fmat(wr, im[i1], fmat(wi, re[i1], im[i0]));
+                    re[i1] = fmat((T)2, re[i0], -ar);
+                    im[i1] = fmat((T)2, im[i0], -ai);
+                    re[i0] = ar;
+                    im[i0] = ai;
                 }
-                re[i1] = re[i0] - xr;
-                im[i1] = im[i0] - xi;
-                re[i0] = re[i0] + xr;
-                im[i0] = im[i0] + xi;
             }
         }
     }
@@ -124,17 +138,17 @@ __device__ __forceinline__ void rfft_row(const T (&x)[N], Cplx<T>* o) {
         const T Er = zr[k] + zr[km], Ei = zi[k] - zi[km];
         const T Or = zi[k] + zi[km], Oi = zr[km] - zr[k];
         const int t = k * (kTwiddleN / N);
-        T tr, ti;
         if (t == kTwiddleN / 4) {   // w = -i
-            tr = Oi;
-            ti = -Or;
+            o[k] = Cplx<T>{Er + Oi, Ei - Or};
+            if (km != k) o[km] = Cplx<T>{Er - Oi, -Or - Ei};
         } else {
+            // E' + w O' by FMAs, and E' - w O' from it: 2 E' - (E' + w O')
             const T wr = tw_cos<T>(t), wi = -tw_sin<T>(t);
-            tr = wr * Or - wi * Oi;
-            ti = wr * Oi + wi * Or;
+            const T ar = fmat(wr, Or, fmat(-wi, Oi, Er));
+            const T ai = fmat(wr, Oi, fmat(wi, Or, Ei));
+            o[k] = Cplx<T>{ar, ai};
+            if (km != k) o[km] = Cplx<T>{fmat((T)2, Er, -ar), fmat((T)-2, Ei, ai)};
         }
-        o[k] = Cplx<T>{Er + tr, Ei + ti};
-        if (km != k) o[km] = Cplx<T>{Er - tr, ti - Ei};
     }
 }
 
@@ -159,20 +173,24 @@ __device__ __forceinline__ void irfft_row(const Cplx<T>* X, T (&zr)[N / 2], T (&
         const Cplx<T> A = X[k], B = X[km];
         const T Er = A.x + B.x, Ei = A.y - B.y, Dr = A.x - B.x, Di = A.y + B.y;
         const int t = k * (kTwiddleN / N);
-        T Or, Oi;
-        if (t == kTwiddleN / 4) {   // w = +i
-            Or = -Di;
-            Oi = Dr;
+        if (t == kTwiddleN / 4) {   // w = +i: O' = i D'
+            zr[k] = Er - Dr;
+            zi[k] = Ei - Di;
+            if (km != k) {
+                zr[km] = Er + Dr;
+                zi[km] = -Di - Ei;
+            }
         } else {
+            // E' + i O' by FMAs, and conj(E' - i O') from it
             const T wr = tw_cos<T>(t), wi = tw_sin<T>(t);
-            Or = Dr * wr - Di * wi;
-            Oi = Dr * wi + Di * wr;
-        }
-        zr[k] = Er - Oi;
-        zi[k] = Ei + Or;
-        if (km != k) {
-            zr[km] = Er + Oi;
-            zi[km] = Or - Ei;
+            const T ar = fmat(-wi, Dr, fmat(-wr, Di, Er));
+            const T ai = fmat(wr, Dr, fmat(-wi, Di, Ei));
+            zr[k] = ar;
+            zi[k] = ai;
+            if (km != k) {
+                zr[km] = fmat((T)2, Er, -ar);
+                zi[km] = fmat((T)-2, Ei, ai);
+            }
         }
     }
     cfft<T, L, true>(zr, zi);

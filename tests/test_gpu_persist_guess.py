@@ -40,15 +40,21 @@ def test_saved_context_reproduces_solves(tmp_path, name, over):
         rng = np.random.default_rng(0)
         solver.mlp_set(torch.from_numpy(0.01 * rng.standard_normal(solver.mlp_n_params())
                                         .astype(np.float32)).to(dev()))
+    xi = draw_xi(8, w.M, 41)
+    precisions = (pkg.FP64,) if w.dim == 2 else (pkg.FP64, pkg.MIXED_DEFECT)
+    # the autotuner's launch-shape choices travel with the file: solve once
+    # before saving so that they exist (a context that has not tuned yet and
+    # its copy would each time the candidates on their own)
+    for prec in precisions:
+        _run(solver, w, xi, prec, pkg.GUESS_GPC)
     path = str(tmp_path / "ctx.klecgc")
     solver.save(path)
     loaded = pkg.Solver.load(path)
+    assert loaded.tuning_report() == solver.tuning_report()
     a, b = solver.info(), loaded.info()
     for f in ("nx", "N", "J", "M", "P", "MQ", "n_unknowns"):
         assert getattr(a, f) == getattr(b, f)
     assert a.lambda_kept == b.lambda_kept
-    xi = draw_xi(8, w.M, 41)
-    precisions = (pkg.FP64,) if w.dim == 2 else (pkg.FP64, pkg.MIXED_DEFECT)
     for prec in precisions:
         c1, U1, i1 = _run(solver, w, xi, prec, pkg.GUESS_GPC)
         c2, U2, i2 = _run(loaded, w, xi, prec, pkg.GUESS_GPC)
