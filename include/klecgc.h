@@ -418,7 +418,10 @@ klecgc_status klecgc_set_scratch_limit(klecgc_ctx* ctx, int64_t bytes);
 /*
  * 2D linear-solve method: 0 (default) banded LU in FP64 for nx <= 32 and
  * Krylov otherwise (and on the MIXED path); 1 Krylov always; 2 banded LU
- * (FP64; UNSUPPORTED for dim = 1 or nx > 64).  Banded LU factors each
+ * (FP64; UNSUPPORTED for dim = 1 or nx > 64); 3 Krylov, with every MIXED
+ * fine-propagator system held by a thread-block cluster (the layout methods
+ * 0 and 1 pick by themselves when a system does not fit one CTA's shared
+ * memory, e.g. nx = 255; UNSUPPORTED for dim = 1).  Banded LU factors each
  * backward-Euler matrix I + dt(A + cI) once per sample and each shifted
  * matrix lambda_k I + dT(A + cI) once per (sample, k) per call (bandwidth
  * nx, no pivoting: the matrices are diagonally dominant), then every step

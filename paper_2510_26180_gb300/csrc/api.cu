@@ -72,7 +72,7 @@ struct klecgc_ctx {
     float* W32t_lo = nullptr;  // [ns*N][Kp] its tail W^T - head
     int Kp = 0;
     int* tc_err = nullptr;     // set by the tensor-core guess when a wait timed out
-    int method2d = 0;          // 2D linear solves: 0 auto, 1 Krylov, 2 banded LU
+    int method2d = 0;          // 2D linear solves: 0 auto, 1 Krylov, 2 banded LU, 3 Krylov on clusters
     int loop_mode = 0;         // parareal loop: 0 CUDA graph (WHILE node), 1 host-driven
     // launch-shape autotuner: 1 times the candidate shapes once per problem
     // shape (and GPU) and keeps the fastest; 0 uses the fixed rules
@@ -578,7 +578,7 @@ constexpr int kBandAutoNx = 32;   // largest grid it is chosen for by default
 // Krylov),
 // or as the context forces.
 bool use_band(const klecgc_ctx* ctx, bool fp64) {
-    if (ctx->dim != 2 || !fp64 || ctx->method2d == 1) return false;
+    if (ctx->dim != 2 || !fp64 || ctx->method2d == 1 || ctx->method2d == 3) return false;
     return ctx->method2d == 2 || ctx->nx <= kBandAutoNx;
 }
 
@@ -1199,7 +1199,7 @@ klecgc_status klecgc_load(const char* path, klecgc_ctx** out, void* stream) {
     ctx->kry_rtol_fine = hd.kry_rtol_fine;
     ctx->kry_rtol_cgc = hd.kry_rtol_cgc;
     ctx->kry_maxit = hd.kry_maxit;
-    ctx->method2d = hd.method2d >= 0 && hd.method2d <= 2 ? hd.method2d : 0;
+    ctx->method2d = hd.method2d >= 0 && hd.method2d <= 3 ? hd.method2d : 0;
     ctx->mlp.residual = hd.mlp_residual == 1;
     const size_t NC = (size_t)ctx->ns * ctx->N;
     klecgc_status s;
@@ -1347,9 +1347,10 @@ klecgc_status klecgc_set_scratch_limit(klecgc_ctx* ctx, int64_t bytes) {
 
 klecgc_status klecgc_set_2d_method(klecgc_ctx* ctx, int32_t method) {
     set_error("");
-    if (!ctx || method < 0 || method > 2) return fail(KLECGC_E_INVALID_ARG, "bad argument");
+    if (!ctx || method < 0 || method > 3) return fail(KLECGC_E_INVALID_ARG, "bad argument");
     if (method == 2 && (ctx->dim != 2 || ctx->nx > kBandMaxNx))
         return fail(KLECGC_E_UNSUPPORTED, "banded LU: 2D grids with nx <= 64");
+    if (method == 3 && ctx->dim != 2) return fail(KLECGC_E_UNSUPPORTED, "clusters: 2D only");
     ctx->method2d = method;
     return KLECGC_OK;
 }
@@ -2029,7 +2030,7 @@ klecgc_status klecgc_fine_sweep(klecgc_ctx* ctx, const double* xi, int64_t S, in
         unsigned long long* its = nullptr;
         if ((s = krylov_flags(ctx, S, st, &ifail, &its)) != KLECGC_OK) return s;
         const bool mixed = precision == KLECGC_MIXED;
-        const Plan2D pl = plan_2d(fine_kind(ctx, mixed), ctx->nx, S * N);
+        const Plan2D pl = plan_2d(fine_kind(ctx, mixed), ctx->nx, S * N, ctx->method2d == 3);
         WS(double, scr, "k2d_scratch", pl.scratch_doubles);
         ctx->launch(KLECGC_K_FINE, st, [&] {
             if (mixed)
@@ -2434,7 +2435,7 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
             *h_active = 1;
             return KLECGC_OK;
         }
-        plF = plan_2d(fine_kind(ctx, precision == KLECGC_MIXED), ctx->nx, S * N);
+        plF = plan_2d(fine_kind(ctx, precision == KLECGC_MIXED), ctx->nx, S * N, ctx->method2d == 3);
         plC = plan_2d(cgc_kind(ctx, precision == KLECGC_MIXED), ctx->nx, S * K);
         WS(double, a1, "k2d_scratch", plF.scratch_doubles);
         WS(double, a2, "k2d_scratch_c", plC.scratch_doubles);

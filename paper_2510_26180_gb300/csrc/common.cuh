@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 #include <string>
+#include <algorithm>
 #include <vector>
 
 namespace klecgc {
@@ -213,15 +214,30 @@ void launch_fine_sequential(int64_t S, int N, int nx, int J, double dt_forcing, 
                             const FineCoef64* fc, double* scratch, double* U, cudaStream_t st);
 
 // ---- k_2d.cu ---- (2D five-point problem; U/out layout [S][nx*nx][N])
+// A system held by a thread-block cluster of CL CTAs (k_2d_cluster.cu).
+struct ClusterPlan2D {
+    int CL = 0;                  // CTAs per cluster (0: no cluster layout fits)
+    int clusters = 0;            // clusters resident on the GPU at once
+    size_t smem = 0;             // dynamic shared memory per CTA
+};
 struct Plan2D {
     int64_t grid = 1;            // CTAs of the persistent launch
     int smem = 0;                // dynamic shared memory per CTA (0: global slices)
     int64_t per_cta = 0;         // doubles of global working storage per CTA
     int64_t scratch_doubles = 0; // total global working storage
+    ClusterPlan2D cl;            // kind 2: the cluster layout, when cl.CL > 0
 };
 // kind 0: fine propagator, 1: shifted CGC solves, 2: mixed fine, 3: mixed CGC,
-// 4 / 5: fine / CGC with advection (BiCGStab); items = work items.
-Plan2D plan_2d(int kind, int nx, int64_t items);
+// 4 / 5: fine / CGC with advection (BiCGStab); items = work items.  Kind 2
+// takes the cluster layout when one system does not fit one CTA's shared
+// memory, or always with force_cluster.
+Plan2D plan_2d(int kind, int nx, int64_t items, bool force_cluster = false);
+ClusterPlan2D fine2d_cluster_plan(int nx);
+void launch_fine2d_mixed_cl(const ClusterPlan2D& p, int64_t S, int N, int nx, int J, double dtc,
+                            double dtf, double alpha, int mode, const double* U, const double* u0,
+                            const double* wdt, double rtol, double tin, int maxit, double* out,
+                            const int* active, int* ifail, unsigned long long* itcount,
+                            cudaStream_t st);
 // mode 0: r = (I + L_dT) F(start) - prev per (s, n); mode 1: sequential fine
 // solution out[s][.][n] per s.  wdt: [S][2 nx (nx+1)] weights dt a / h^2.
 // adv = dt b0 of the upwind convection (advection-diffusion, BiCGStab, plan

@@ -1198,12 +1198,21 @@ int64_t per_system(int kind, int nx) {
 
 }  // namespace
 
-Plan2D plan_2d(int kind, int nx, int64_t items) {
+Plan2D plan_2d(int kind, int nx, int64_t items, bool force_cluster) {
     Plan2D pl;
     const int64_t per = per_system(kind, nx);
     const int64_t bytes = per * 8;
     const int sm = num_sms();
     const int static_bytes = 2 * 3 * 32 * 8;
+    if (kind == 2 && (force_cluster || bytes + static_bytes > max_dyn_smem())) {
+        // the mixed fine system on a thread-block cluster, if one holds it
+        const ClusterPlan2D cp = fine2d_cluster_plan(nx);
+        if (cp.CL > 0) {
+            pl.cl = cp;
+            pl.grid = (int64_t)cp.CL * std::min<int64_t>(cp.clusters, std::max<int64_t>(items, 1));
+            return pl;
+        }
+    }
     if (bytes + static_bytes <= max_dyn_smem()) {
         pl.smem = (int)bytes;
         int occ = 0;
@@ -1269,6 +1278,11 @@ void launch_fine2d_mixed(const Plan2D& pl, int64_t S, int N, int nx, int J, doub
                          const int* active, int* ifail, unsigned long long* itcount,
                          double* scratch, cudaStream_t st) {
     if (S == 0) return;
+    if (pl.cl.CL > 0) {
+        launch_fine2d_mixed_cl(pl.cl, S, N, nx, J, dtc, dtf, alpha, mode, U, u0, wdt, rtol, tin,
+                               maxit, out, active, ifail, itcount, st);
+        return;
+    }
     k_fine2d_mixed<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
         S, N, nx, J, dtc, dtf, alpha, mode, U, u0, wdt, rtol * rtol, (float)(tin * tin), maxit,
         out, active, ifail, itcount, pl.per_cta ? scratch : nullptr, pl.per_cta);

@@ -336,7 +336,8 @@ class Solver:
         return _check(self.lib.klecgc_set_loop(self.h, mode))
 
     def set_2d_method(self, method) -> int:
-        """0 auto (banded LU in FP64 for nx <= 32), 1 Krylov, 2 banded LU (nx <= 64)."""
+        """0 auto (banded LU in FP64 for nx <= 32), 1 Krylov, 2 banded LU (nx <= 64),
+        3 Krylov with the mixed fine systems on thread-block clusters."""
         return _check(self.lib.klecgc_set_2d_method(self.h, method))
 
     def krylov_stats(self) -> tuple:

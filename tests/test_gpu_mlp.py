@@ -32,6 +32,22 @@ def _bf16_weights(theta, sizes):
     return tb
 
 
+def _bars(sizes):
+    """Per-block bars on the relative L2 error of a BF16 gradient (weights,
+    bias of layer l = 1..L).  BF16 keeps 8 significant bits (unit roundoff
+    u = 2^-9); every GEMM rounds both operands to BF16, so the gradient of
+    layer l carries about 2u from its own product and 2u from each of the
+    L - l layers the backward pass crosses (their weights and the incoming
+    gradient), plus the forward activations it multiplies: (L - l + 2) 2u,
+    doubled for the sums' own spread: 2^-8 (L - l + 2), 1.95e-2 for the first
+    of four layers down to 7.8e-3 for the last."""
+    L = len(sizes) - 1
+    out = []
+    for l in range(1, L + 1):
+        out += [2.0 ** -8 * (L - l + 2)] * 2
+    return out
+
+
 def test_gradient_matches_fp64_oracle():
     solver, w = gpu_solver("heat1d_nx63")
     sizes = omlp.layer_sizes(w.M, w.N)
@@ -45,14 +61,10 @@ def test_gradient_matches_fp64_oracle():
     loss = solver.mlp_loss_grad(T(xi), T(tg), B, grad)
     lo, go = omlp.loss_and_grad(theta.astype(np.float64), sizes, xi, tg.astype(np.float64))
     assert abs(loss - lo) <= 1e-3 * lo
-    gg = grad.cpu().numpy()
-    k = 0
-    for i, o in zip(sizes[:-1], sizes[1:]):
-        for n in (o * i, o):
-            a, b = gg[k:k + n], go[k:k + n]
-            k += n
-            assert np.linalg.norm(a - b) <= 5e-2 * np.linalg.norm(b)
-            assert a @ b >= 0.999 * np.linalg.norm(a) * np.linalg.norm(b)
+    errs = _block_errors(grad.cpu().numpy(), go, sizes)
+    print("per-block relative L2 / cosine:", [(f"{e:.2e}", f"{c:.5f}") for e, c in errs])
+    for (e, c), bar in zip(errs, _bars(sizes)):
+        assert e <= bar and c >= 0.999
 
 
 def test_grid_maps_match_oracle():
@@ -172,7 +184,8 @@ def _block_errors(gg, go, sizes):
 
 def test_gradient_at_batch_256_on_tcgen05_matches_fp64_oracle():
     # batch 256: the products of the hidden and output layers run on the
-    # tcgen05 tensor cores (M, K >= 64); same bars as the small batch
+    # tcgen05 tensor cores (M, K >= 64); the same derived bars as the small
+    # batch
     solver, w = gpu_solver("heat1d_nx63")
     sizes = omlp.layer_sizes(w.M, w.N)
     theta = _bf16_weights(omlp.init_params(sizes, 8), sizes)
@@ -186,8 +199,8 @@ def test_gradient_at_batch_256_on_tcgen05_matches_fp64_oracle():
     assert abs(loss - lo) <= 1e-3 * lo
     errs = _block_errors(grad.cpu().numpy(), go, sizes)
     print("per-block relative L2 / cosine:", [(f"{e:.2e}", f"{c:.5f}") for e, c in errs])
-    for e, c in errs:
-        assert e <= 5e-2 and c >= 0.999
+    for (e, c), bar in zip(errs, _bars(sizes)):
+        assert e <= bar and c >= 0.999
 
 
 def test_guess_at_512_samples_on_tcgen05_matches_oracle_forward():
