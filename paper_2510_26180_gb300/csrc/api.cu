@@ -645,12 +645,25 @@ klecgc_status sequential_2d(klecgc_ctx* ctx, const double* xi_d, int64_t S, int 
     WS(int, act, "act_all", S);
     TRY(cudaMemsetAsync(act, 0xff, S * sizeof(int), st));
     const Plan2D pl = plan_2d(fine_kind(ctx, false), ctx->nx, S);
-    WS(double, scr, "k2d_scratch", pl.scratch_doubles);
+    // A system whose FP64 Krylov vectors would stream from global memory
+    // (pl.per_cta > 0) is solved on a thread-block cluster instead, by FP64
+    // iterative refinement around FP32 PCG: the same FP64 residual test
+    // ||b - M x||_2 <= rtol ||b||_2 in every step, so the same accuracy.
+    Plan2D plc;
+    if (ctx->prob.advection == 0 && (pl.per_cta > 0 || ctx->method2d == 3))
+        plc = plan_2d(2, ctx->nx, S, true);
+    WS(double, scr, "k2d_scratch", plc.cl.CL ? 0 : pl.scratch_doubles);
     ctx->launch(KLECGC_K_FINE, st, [&] {
-        launch_fine2d(pl, S, N, ctx->nx, J, dt * ctx->prob.reaction, dt * ctx->prob.forcing,
-                      dt * ctx->prob.advection, 0.0,
-                      1, nullptr, ctx->u0, wdt, ctx->kry_rtol_fine, ctx->kry_maxit, out, act,
-                      ifail, its, scr, st);
+        if (plc.cl.CL)
+            launch_fine2d_mixed(plc, S, N, ctx->nx, J, dt * ctx->prob.reaction,
+                                dt * ctx->prob.forcing, 0.0, 1, nullptr, ctx->u0, wdt,
+                                ctx->kry_rtol_fine, kInnerRtol, ctx->kry_maxit, out, act, ifail,
+                                its, nullptr, st);
+        else
+            launch_fine2d(pl, S, N, ctx->nx, J, dt * ctx->prob.reaction, dt * ctx->prob.forcing,
+                          dt * ctx->prob.advection, 0.0,
+                          1, nullptr, ctx->u0, wdt, ctx->kry_rtol_fine, ctx->kry_maxit, out, act,
+                          ifail, its, scr, st);
     });
     TRY(cudaGetLastError());
     std::vector<int> hf;
@@ -743,12 +756,20 @@ klecgc_status coarse_guess_internal(klecgc_ctx* ctx, int64_t S, int N, double dT
         WS(int, gfail, "coarse_fail", S);
         TRY(cudaMemsetAsync(act, 0xff, S * sizeof(int), st));
         const Plan2D pl = plan_2d(fine_kind(ctx, false), ctx->nx, S);
-        WS(double, scr, "k2d_scratch_g", pl.scratch_doubles);
+        Plan2D plc;   // on a thread-block cluster where FP64 would stream (as the reference)
+        if (ctx->prob.advection == 0 && (pl.per_cta > 0 || ctx->method2d == 3))
+            plc = plan_2d(2, ctx->nx, S, true);
+        WS(double, scr, "k2d_scratch_g", plc.cl.CL ? 0 : pl.scratch_doubles);
         // a guess needs no tight solve: its error only costs iterations
         ctx->launch(KLECGC_K_GUESS, st, [&] {
-            launch_fine2d(pl, S, N, ctx->nx, 1, dT * react, dT * forcing,
-                          dT * ctx->prob.advection, 0.0, 1, nullptr, ctx->u0,
-                          field, ctx->kry_rtol_fine, ctx->kry_maxit, U, act, gfail, nullptr, scr, st);
+            if (plc.cl.CL)
+                launch_fine2d_mixed(plc, S, N, ctx->nx, 1, dT * react, dT * forcing, 0.0, 1,
+                                    nullptr, ctx->u0, field, ctx->kry_rtol_fine, kInnerRtol,
+                                    ctx->kry_maxit, U, act, gfail, nullptr, nullptr, st);
+            else
+                launch_fine2d(pl, S, N, ctx->nx, 1, dT * react, dT * forcing,
+                              dT * ctx->prob.advection, 0.0, 1, nullptr, ctx->u0,
+                              field, ctx->kry_rtol_fine, ctx->kry_maxit, U, act, gfail, nullptr, scr, st);
         });
     }
     TRY(cudaGetLastError());

@@ -207,7 +207,9 @@ __global__ void __launch_bounds__(kThreadsCl) k_fine2d_mixed_cl(
         cl.sync();   // the previous item's halo reads are done
         for (int e = threadIdx.x; e < B.rows * (nx + 1); e += blockDim.x)
             wx[e] = (float)wg[(int64_t)B.r0 * (nx + 1) + e];
-        for (int e = threadIdx.x; e < (B.rows + 1) * nx; e += blockDim.x)
+        // faces r0 .. r0 + rows (a CTA without rows reads none: its r0 may
+        // lie beyond the last face)
+        for (int e = threadIdx.x; B.rows > 0 && e < (B.rows + 1) * nx; e += blockDim.x)
             wy[e] = (float)wg[(int64_t)nx * (nx + 1) + (int64_t)B.r0 * nx + e];
         __syncthreads();
         for (int li = threadIdx.x; li < B.m; li += blockDim.x) {

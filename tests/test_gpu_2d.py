@@ -296,8 +296,12 @@ def test_2d_method_argument_checks():
     import paper_2510_26180_gb300 as pkg
     solver, _ = solver2d(SMALL)
     with pytest.raises(pkg.KlecgcError) as e:
-        solver.set_2d_method(3)
+        solver.set_2d_method(4)
     assert e.value.status == pkg.E_INVALID_ARG
+    one_d, _ = gpu_solver("heat1d_nx63")
+    with pytest.raises(pkg.KlecgcError) as e:
+        one_d.set_2d_method(3)   # thread-block clusters: 2D systems only
+    assert e.value.status == pkg.E_UNSUPPORTED
     big, _ = gpu_solver("rd2d_255", nx=95, N=4, J=1, M=4, gpc_degree=1, n_train=10)
     with pytest.raises(pkg.KlecgcError) as e:
         big.set_2d_method(2)
