@@ -2148,7 +2148,7 @@ klecgc_status klecgc_cgc_apply(klecgc_ctx* ctx, const double* xi, int64_t S, int
         int* ifail = nullptr;
         unsigned long long* its = nullptr;
         if ((s = krylov_flags(ctx, S, st, &ifail, &its)) != KLECGC_OK) return s;
-        const Plan2D pl = plan_2d(cgc_kind(ctx, mixed), ctx->nx, S * K);
+        const Plan2D pl = plan_2d(cgc_kind(ctx, mixed), ctx->nx, S * K, ctx->method2d == 3);
         WS(double, scr, "k2d_scratch_c", pl.scratch_doubles);
         launch_cgc_forward<double, double>(S, N, nx, r, sc, p, active, st);
         if (mixed)
@@ -2457,7 +2457,7 @@ klecgc_status SolveRun::begin(const double* xi_d, const double* U_guess) {
             return KLECGC_OK;
         }
         plF = plan_2d(fine_kind(ctx, precision == KLECGC_MIXED), ctx->nx, S * N, ctx->method2d == 3);
-        plC = plan_2d(cgc_kind(ctx, precision == KLECGC_MIXED), ctx->nx, S * K);
+        plC = plan_2d(cgc_kind(ctx, precision == KLECGC_MIXED), ctx->nx, S * K, ctx->method2d == 3);
         WS(double, a1, "k2d_scratch", plF.scratch_doubles);
         WS(double, a2, "k2d_scratch_c", plC.scratch_doubles);
         scrF = a1;

@@ -219,6 +219,7 @@ struct ClusterPlan2D {
     int CL = 0;                  // CTAs per cluster (0: no cluster layout fits)
     int clusters = 0;            // clusters resident on the GPU at once
     size_t smem = 0;             // dynamic shared memory per CTA
+    int64_t scratch_per_cta = 0; // doubles of global memory per CTA (CGC layout)
 };
 struct Plan2D {
     int64_t grid = 1;            // CTAs of the persistent launch
@@ -230,9 +231,16 @@ struct Plan2D {
 // kind 0: fine propagator, 1: shifted CGC solves, 2: mixed fine, 3: mixed CGC,
 // 4 / 5: fine / CGC with advection (BiCGStab); items = work items.  Kind 2
 // takes the cluster layout when one system does not fit one CTA's shared
-// memory, or always with force_cluster.
+// memory, or always with force_cluster; kind 3 (the mixed CGC) likewise,
+// with its FP64 residual in scratch_doubles of global memory.
 Plan2D plan_2d(int kind, int nx, int64_t items, bool force_cluster = false);
 ClusterPlan2D fine2d_cluster_plan(int nx);
+ClusterPlan2D cgc2d_cluster_plan(int nx);
+void launch_cgc_solve2d_mixed_cl(const ClusterPlan2D& p, int64_t S, int K, int nx, double dTc,
+                                 const double2* lam, const double* wdT, double rtol, double tin,
+                                 int maxit, Cplx<double>* pio, const int* active, int* ifail,
+                                 unsigned long long* itcount, double* scratch, int64_t grid,
+                                 cudaStream_t st);
 void launch_fine2d_mixed_cl(const ClusterPlan2D& p, int64_t S, int N, int nx, int J, double dtc,
                             double dtf, double alpha, int mode, const double* U, const double* u0,
                             const double* wdt, double rtol, double tin, int maxit, double* out,

@@ -1204,12 +1204,13 @@ Plan2D plan_2d(int kind, int nx, int64_t items, bool force_cluster) {
     const int64_t bytes = per * 8;
     const int sm = num_sms();
     const int static_bytes = 2 * 3 * 32 * 8;
-    if (kind == 2 && (force_cluster || bytes + static_bytes > max_dyn_smem())) {
-        // the mixed fine system on a thread-block cluster, if one holds it
-        const ClusterPlan2D cp = fine2d_cluster_plan(nx);
+    if ((kind == 2 || kind == 3) && (force_cluster || bytes + static_bytes > max_dyn_smem())) {
+        // the mixed system on a thread-block cluster, if one holds it
+        const ClusterPlan2D cp = kind == 2 ? fine2d_cluster_plan(nx) : cgc2d_cluster_plan(nx);
         if (cp.CL > 0) {
             pl.cl = cp;
             pl.grid = (int64_t)cp.CL * std::min<int64_t>(cp.clusters, std::max<int64_t>(items, 1));
+            pl.scratch_doubles = cp.scratch_per_cta * pl.grid;
             return pl;
         }
     }
@@ -1293,6 +1294,11 @@ void launch_cgc_solve2d_mixed(const Plan2D& pl, int64_t S, int K, int nx, double
                               int maxit, Cplx<double>* p, const int* active, int* ifail,
                               unsigned long long* itcount, double* scratch, cudaStream_t st) {
     if (S == 0) return;
+    if (pl.cl.CL > 0) {
+        launch_cgc_solve2d_mixed_cl(pl.cl, S, K, nx, dTc, lam, wdT, rtol, tin, maxit, p, active,
+                                    ifail, itcount, scratch, pl.grid, st);
+        return;
+    }
     k_cgc_solve2d_mixed<<<(unsigned)pl.grid, kThreads2d, pl.smem, st>>>(
         S, K, nx, dTc, lam, wdT, rtol * rtol, (float)(tin * tin), maxit,
         reinterpret_cast<double2*>(p), active, ifail, itcount, pl.per_cta ? scratch : nullptr,

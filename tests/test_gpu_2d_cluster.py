@@ -4,7 +4,8 @@ against the sparse-direct CPU oracle.
 klecgc_set_2d_method(3) forces the cluster layout of the mixed fine
 propagator (FP64 iterative refinement around FP32 Jacobi-PCG, the same FP64
 residual test ||b - M x||_2 <= rtol ||b||_2 in every step as the FP64 path)
-also on grids whose system fits one CTA, so that the layout meets the
+and of the mixed shifted CGC solves (the same around FP32 Jacobi-COCG) also
+on grids whose system fits one CTA, so that the layout meets the
 oracle at sizes it solves in seconds: at nx = 15 a 16-CTA cluster gives
 every CTA one grid row (each row is a block boundary and one CTA holds
 none), at nx = 31 two rows, at nx = 63 four.  The reference solution U*
@@ -118,6 +119,46 @@ def test_cluster_solve_matches_oracle(over):
         floor = rel(Up, Uo) + rel(Uf, Uo)
         assert it[s] == ko
         assert rel(U[s], Uo) < max(1e-12, 4 * floor)
+
+
+def shifted_cond(op, dT, alpha, N):
+    from scipy.sparse.linalg import eigsh
+    mu_max = eigsh(op.A, k=1, which="LA", return_eigenvectors=False)[0]
+    mu_min = eigsh(op.A, k=1, sigma=0, which="LM", return_eigenvectors=False)[0]
+    k = np.arange(N // 2 + 1)
+    lam = 1.0 - alpha ** (1.0 / N) * np.exp(-2j * np.pi * k / N)
+    return float(np.max(np.abs(lam + dT * mu_max) / np.abs(lam + dT * mu_min)))
+
+
+@pytest.mark.parametrize("over,alpha", [(SMALL, 1e-3), (MID, 1e-2), (BIG, 1e-3)],
+                         ids=["nx15", "nx31", "nx63"])
+def test_cluster_cgc_apply_matches_oracle(over, alpha):
+    """Eq. three steps on the cluster layout of step (b): bar as for the
+    single-CTA kernels, including the attainable accuracy of an iterative
+    solve (eps x the shifted system's condition number, scaled by step
+    (c)'s alpha^{-(N-1)/N})."""
+    import paper_2510_26180_gb300 as pkg
+    from oracle import pcgc
+    solver, w = cluster_solver(over)
+    st = oracle_setup2d("rd2d_255", **over)
+    S, N, dT = 3, w.N, w.T / w.N
+    n = w.nx * w.nx
+    xi = draw_xi(S, w.M, 65)
+    r = np.random.default_rng(10).standard_normal((S, N, n))
+    u = torch.empty_like(T(r))
+    try:
+        solver.cgc_apply(T(xi), S, N, T(r), dT, alpha, pkg.MIXED, u)
+        assert solver.krylov_stats()[1] > 0
+    finally:
+        solver.set_2d_method(1)
+    for s in range(S):
+        op = st.operator(xi[s])
+        ref = pcgc.cgc_diagonalized(op, r[s], dT, alpha)
+        floor = rel(pcgc.cgc_diagonalized(op, r[s], dT, alpha, fft=True), ref)
+        floor += rel(pcgc.cgc_diagonalized(st.operator(xi[s], 4.0), r[s], dT, alpha), ref)
+        kry = 4 * 2.2e-16 * shifted_cond(op, dT, alpha, N) * alpha ** (-(N - 1) / N)
+        d = rel(u[s].cpu().numpy(), ref)
+        assert d < max(1e-12, 4 * floor, kry), (s, d, floor, kry)
 
 
 def test_cluster_layout_is_bitwise_repeatable():
