@@ -259,7 +259,8 @@ def roofline_2d(cls, ms, launches, units, prec, adv=False, band_nx=0):
     apply of z, p and q recurrences, p.q); per step 38 more (initial residual
     and the first q = M p).  COCG iteration: 34 + 58, complex.  On the mixed
     path the CG iterations are FP32 (the FP64 refinement work, ~40 flop per
-    unknown per step, is left out), so the roof is the FP32 one.
+    unknown per step, is left out), so the roof is the FP32 one; likewise for
+    the COCG iterations of the mixed shifted solves.
     Advection-diffusion (BiCGStab, two stencil applications of 22 flop with
     the upwind terms per iteration): 70 per iteration + 28 per step (real);
     ~196 per iteration of the complex shifted solves.
@@ -267,7 +268,9 @@ def roofline_2d(cls, ms, launches, units, prec, adv=False, band_nx=0):
     step is one forward and one backward substitution of bandwidth nx, 4 nx
     flop per unknown; a shifted solve the same in complex arithmetic, 16 nx."""
     ns = units["ns"]
-    fp32 = prec == "mixed" and cls == "fine"
+    # on the mixed path the Krylov iterations of both F and the shifted
+    # solves run in FP32 (the FP64 refinement work is not counted)
+    fp32 = prec == "mixed"
     if band_nx and cls in ("fine", "cgc_solve"):
         if cls == "fine":
             flops = 4.0 * band_nx * ns * units["fine_steps"]
@@ -300,7 +303,7 @@ def roofline_entry(cls, ms, launches, units, prec, w, hbm_peak, peak_kind):
         return None
     if w.dim == 2:
         band_nx = w.nx if (prec == "fp64" and (w.nx <= 32 or METHOD2D[0] == 2)
-                           and METHOD2D[0] != 1) else 0
+                           and METHOD2D[0] not in (1, 3)) else 0
         return roofline_2d(cls, ms, launches, units, prec, w.advection > 0, band_nx)
     if w.reaction_kind:
         if cls != "fine":
@@ -1033,8 +1036,9 @@ def main():
     ap.add_argument("--samples", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
-    ap.add_argument("--method2d", type=int, default=0, choices=[0, 1, 2],
-                    help="2D linear solves: 0 auto, 1 Krylov, 2 banded LU")
+    ap.add_argument("--method2d", type=int, default=0, choices=[0, 1, 2, 3],
+                    help="2D linear solves: 0 auto, 1 Krylov, 2 banded LU, "
+                         "3 Krylov with every mixed system on a thread-block cluster")
     ap.add_argument("--offline", default="", metavar="MULTS",
                     help="offline-stage scan: training sets of these multiples of P, e.g. 1,2,8")
     ap.add_argument("--set", action="append", default=[], metavar="FIELD=VALUE",

@@ -150,6 +150,320 @@ __global__ void __launch_bounds__(128) k_fine_newton(
     if (itcount) atomicAdd(itcount, its);
 }
 
+// ---- G lanes per column
+// The same Newton backward-Euler steps with each column's rows split over G
+// lanes (lane g holds rows [g R, g R + R) of w and v in registers).  The
+// tridiagonal Newton system (I - dt grad f(w)) d = R of every iteration is
+// solved by the Thomas recurrences, each one split at the lane boundaries
+// and joined by a scan over the G lanes:
+//   pivots      piv_i = diag_i - lower_i upper_{i-1} / piv_{i-1}, a continued
+//               fraction: (p_i, q_i) = (diag_i p_{i-1} - lower_i upper_{i-1}
+//               q_{i-1}, p_{i-1}), piv = p / q; the lanes' 2 x 2 products are
+//               scanned (rescaled by powers of two, which is exact);
+//   forward     y_i = R_i - (lower_i / piv_{i-1}) y_{i-1}, affine maps scanned;
+//   backward    d_i = (y_i - upper_i d_{i+1}) / piv_i, affine maps scanned from
+//               the right.
+// One thread per column left the GPU with S N threads in all (8,192 for 256
+// samples x 32 intervals, under two warps per SM) and each of them a chain of
+// dependent FP64 operations; G lanes per column give G times the threads and
+// a chain G times shorter, for about twice the FP64 operations.  A Newton
+// iteration ends for the whole column at once (the lanes share max |d| and
+// max |w|); columns of one warp that converged earlier keep their w while
+// the others iterate.  Rows beyond nx are identity rows (d = 0, w = 0).
+namespace {
+
+__device__ __forceinline__ void m2_rescale(double& a, double& b, double& c, double& d) {
+    const double mx = fmax(fmax(fabs(a), fabs(b)), fmax(fabs(c), fabs(d)));
+    if (mx > 0.0 && (mx > 0x1p+64 || mx < 0x1p-64)) {
+        const int e = ilogb(mx);
+        a = scalbn(a, -e);
+        b = scalbn(b, -e);
+        c = scalbn(c, -e);
+        d = scalbn(d, -e);
+    }
+}
+
+// One Newton backward-Euler step of the column held by this lane group:
+// w (in/out) the iterate, v the start value.  Returns false where the
+// column's Newton iteration reached the cap or produced a non-finite step.
+template <int KIND, int G, int R>
+__device__ __forceinline__ bool newton_be_g(int nx, int g, const double (&wfv)[R + 1], double dt, double c,
+                            double f0, const double (&v)[R], double (&w)[R], unsigned long long* its) {
+    constexpr unsigned FULL = 0xffffffffu;
+    bool done = false, ok = true;
+    for (int it = 0; it < kNewtonMax; ++it) {
+        if (__all_sync(FULL, done)) break;
+        if (!done) ++*its;
+        double Rr[R], lo[R], up[R], ipv[R];
+        // residual and Jacobian rows; w beyond the grid is 0
+        double wprev = __shfl_up_sync(FULL, w[R - 1], 1, G);
+        double wnext = __shfl_down_sync(FULL, w[0], 1, G);
+        if (g == 0) wprev = 0.0;
+        if (g == G - 1) wnext = 0.0;
+        double dg[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            const int i = g * R + j;
+            const double wi = w[j];
+            const double wl = j > 0 ? w[j - 1] : wprev;
+            const double wr = j + 1 < R ? w[j + 1] : wnext;
+            if (i < nx) {
+                const double fl = dt * wfv[j], fr = dt * wfv[j + 1];
+                const double Aw = fl * (wi - wl) - fr * (wr - wi);
+                if (KIND == 1) {
+                    Rr[j] = wi + Aw + dt * c * (wi * wi * wi - wi) - v[j] - dt * f0;
+                    dg[j] = 1.0 + fl + fr + dt * c * (3.0 * wi * wi - 1.0);
+                    lo[j] = -fl;
+                    up[j] = -fr;
+                } else {
+                    const double dc = dt * c;
+                    Rr[j] = wi + Aw + dc * (eo_flux(wi, wr) - eo_flux(wl, wi)) - v[j] - dt * f0;
+                    dg[j] = 1.0 + fl + fr + dc * fabs(wi);
+                    lo[j] = -fl - dc * fmax(wl, 0.0);
+                    up[j] = -fr + dc * fmin(wr, 0.0);
+                }
+            } else {
+                Rr[j] = 0.0;
+                dg[j] = 1.0;
+                lo[j] = 0.0;
+                up[j] = 0.0;
+            }
+        }
+        // pivots: the lane's product of the maps M_i = [[dg_i, -lo_i up_{i-1}], [1, 0]]
+        double upl = __shfl_up_sync(FULL, up[R - 1], 1, G);   // up of the row before the lane
+        if (g == 0) upl = 0.0;
+        double t00 = 1.0, t01 = 0.0, t10 = 0.0, t11 = 1.0;
+        {
+            double upp = upl;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const double cc = -lo[j] * upp;
+                const double n00 = dg[j] * t00 + cc * t10, n01 = dg[j] * t01 + cc * t11;
+                t10 = t00;
+                t11 = t01;
+                t00 = n00;
+                t01 = n01;
+                m2_rescale(t00, t01, t10, t11);
+                upp = up[j];
+            }
+        }
+#pragma unroll
+        for (int d = 1; d < G; d <<= 1) {
+            const double b00 = __shfl_up_sync(FULL, t00, d, G), b01 = __shfl_up_sync(FULL, t01, d, G);
+            const double b10 = __shfl_up_sync(FULL, t10, d, G), b11 = __shfl_up_sync(FULL, t11, d, G);
+            if (g >= d) {
+                const double n00 = t00 * b00 + t01 * b10, n01 = t00 * b01 + t01 * b11;
+                const double n10 = t10 * b00 + t11 * b10, n11 = t10 * b01 + t11 * b11;
+                t00 = n00;
+                t01 = n01;
+                t10 = n10;
+                t11 = n11;
+                m2_rescale(t00, t01, t10, t11);
+            }
+        }
+        const double pp = __shfl_up_sync(FULL, t00, 1, G), qq = __shfl_up_sync(FULL, t10, 1, G);
+        double piv = (g > 0 && qq != 0.0) ? pp / qq : 1.0;   // pivot of the row before the lane
+        {
+            double upp = upl;
+#pragma unroll
+            for (int j = 0; j < R; ++j) {
+                const double m = lo[j] / piv;   // multiplier of row j (0 at the first row)
+                piv = dg[j] - m * upp;
+                ipv[j] = 1.0 / piv;
+                lo[j] = m;                      // lo now holds the multipliers
+                upp = up[j];
+            }
+        }
+        // forward: y_j = R_j - m_j y_{j-1}; the lane as y_out = a y_in + b
+        double a = 1.0, b = 0.0;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            a = -lo[j] * a;
+            b = Rr[j] - lo[j] * b;
+        }
+#pragma unroll
+        for (int d = 1; d < G; d <<= 1) {
+            const double pa = __shfl_up_sync(FULL, a, d, G), pb = __shfl_up_sync(FULL, b, d, G);
+            if (g >= d) {
+                b = fma(a, pb, b);
+                a *= pa;
+            }
+        }
+        double y = __shfl_up_sync(FULL, b, 1, G);
+        if (g == 0) y = 0.0;
+#pragma unroll
+        for (int j = 0; j < R; ++j) {
+            y = Rr[j] - lo[j] * y;
+            Rr[j] = y;                          // Rr now holds y
+        }
+        // backward: d_j = (y_j - up_j d_{j+1}) / piv_j; the lane as d_first = C d_in + E
+        double C = 1.0, E = 0.0;
+#pragma unroll
+        for (int j = R - 1; j >= 0; --j) {
+            const double cj = -up[j] * ipv[j], ej = Rr[j] * ipv[j];
+            E = fma(cj, E, ej);
+            C = cj * C;
+        }
+#pragma unroll
+        for (int d = 1; d < G; d <<= 1) {
+            const double nc = __shfl_down_sync(FULL, C, d, G), ne = __shfl_down_sync(FULL, E, d, G);
+            if (g + d < G) {
+                E = fma(C, ne, E);
+                C *= nc;
+            }
+        }
+        double dn = __shfl_down_sync(FULL, E, 1, G);
+        if (g == G - 1) dn = 0.0;
+        double dmax = 0.0, wmax = 0.0;
+#pragma unroll
+        for (int j = R - 1; j >= 0; --j) {
+            const double dj = (Rr[j] - up[j] * dn) * ipv[j];
+            dn = dj;
+            const double wn = done ? w[j] : w[j] - dj;
+            if (!done) w[j] = wn;
+            dmax = fmax(dmax, fabs(dj));
+            wmax = fmax(wmax, fabs(wn));
+        }
+#pragma unroll
+        for (int d = 1; d < G; d <<= 1) {
+            dmax = fmax(dmax, __shfl_xor_sync(FULL, dmax, d, G));
+            wmax = fmax(wmax, __shfl_xor_sync(FULL, wmax, d, G));
+        }
+        if (!done) {
+            if (!(dmax == dmax)) {
+                ok = false;
+                done = true;
+            } else if (dmax <= 1e-14 * fmax(1.0, wmax)) {
+                done = true;
+            }
+        }
+    }
+    return ok && done;
+}
+
+// mode 0: F per column (s, n) (and with jump, b = F - G(prev)) as
+// k_fine_newton; mode 1: the sequential fine solution per sample s, written
+// every J steps (as k_sequential_newton).
+template <int KIND, int G, int R>
+__global__ void __launch_bounds__(128) k_newton_g(
+    int64_t S, int N, int nx, int J, double dT, double alpha, double c, double f0, int jump,
+    int mode, const double* __restrict__ U, const double* __restrict__ u0,
+    const double* __restrict__ wf, double* __restrict__ out, const int* __restrict__ active,
+    int* __restrict__ ifail, unsigned long long* __restrict__ itcount) {
+    const int64_t t = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+    const int64_t col = t / G;
+    const int g = (int)(t - col * G);
+    const int64_t ncol = mode == 0 ? S * N : S;
+    // whole warps stay for the shuffles; a group past the end works on
+    // a copy of the last column and writes nothing
+    const bool real = col < ncol;
+    const int64_t cc = real ? col : ncol - 1;
+    const int64_t s = mode == 0 ? cc / N : cc;
+    const int n = mode == 0 ? (int)(cc - s * N) : 0;
+    const bool act = active == nullptr || active[s];
+    if (!__any_sync(0xffffffffu, real && act)) return;   // the whole warp is idle
+    double wfv[R + 1];
+#pragma unroll
+    for (int j = 0; j <= R; ++j) {
+        const int i = g * R + j;
+        wfv[j] = i <= nx ? wf[s * (nx + 1) + i] : 0.0;
+    }
+    const double* Us = U ? U + s * (int64_t)nx * N : nullptr;
+    double w[R], v[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) {
+        const int i = g * R + j;
+        w[j] = i < nx ? ((mode == 1 || n == 0) ? u0[i] : Us[(int64_t)i * N + n - 1]) : 0.0;
+    }
+    bool ok = true;
+    unsigned long long its = 0;
+    const double dt = dT / J;
+    const int nint = mode == 0 ? 1 : N;
+    for (int ni = 0; ni < nint; ++ni) {
+        for (int j = 0; j < J; ++j) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) v[q] = w[q];
+            ok &= newton_be_g<KIND, G, R>(nx, g, wfv, dt, c, f0, v, w, &its);
+        }
+        if (mode == 1 && real && act) {
+#pragma unroll
+            for (int q = 0; q < R; ++q) {
+                const int i = g * R + q;
+                if (i < nx) out[(s * (int64_t)nx + i) * N + ni] = w[q];
+            }
+        }
+    }
+    if (mode == 0 && jump) {
+        // G(prev): one step of dT from prev; F stays in w
+        double gv[R], gw[R];
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = g * R + q;
+            const double pv = i < nx ? (n == 0 ? alpha * Us[(int64_t)i * N + N - 1]
+                                               : Us[(int64_t)i * N + n - 1])
+                                     : 0.0;
+            gv[q] = pv;
+            gw[q] = pv;
+        }
+        ok &= newton_be_g<KIND, G, R>(nx, g, wfv, dT, c, f0, gv, gw, &its);
+#pragma unroll
+        for (int q = 0; q < R; ++q) w[q] -= gw[q];
+    }
+    if (mode == 0 && real && act) {
+#pragma unroll
+        for (int q = 0; q < R; ++q) {
+            const int i = g * R + q;
+            if (i < nx) out[(s * (int64_t)nx + i) * N + n] = w[q];
+        }
+    }
+    if (real && act && g == 0) {
+        if (!ok && ifail) ifail[s] = 1;
+        if (itcount) atomicAdd(itcount, its);
+    }
+}
+
+// Lanes per column and rows per lane for nx rows: G = 16 up to 128 rows,
+// else 32; R the smallest power of two with G R >= nx, at most 8 (a lane
+// holds ~9 R doubles; at R = 16 they spill).  R = 0 past 256 rows: the
+// thread-per-column kernel takes those.
+void newton_g_shape(int nx, int* G, int* R) {
+    *G = nx <= 128 ? 16 : 32;
+    *R = 0;
+    for (int r : {2, 4, 8})
+        if (*G * r >= nx) {
+            *R = r;
+            break;
+        }
+}
+
+template <int KIND>
+bool launch_newton_g(int64_t S, int N, int nx, int J, double dT, double alpha, double c, double f0,
+                     int jump, int mode, const double* U, const double* u0, const double* wf,
+                     double* out, const int* active, int* ifail, unsigned long long* itcount,
+                     cudaStream_t st) {
+    int G = 0, R = 0;
+    newton_g_shape(nx, &G, &R);
+    if (R == 0) return false;
+    const int64_t ncol = mode == 0 ? S * N : S;
+    const int64_t threads = ((ncol * G + 31) / 32) * 32;
+    const unsigned grid = (unsigned)((threads + 127) / 128);
+#define KLECGC_NG(GG, RR)                                                                      \
+    if (G == GG && R == RR) {                                                                  \
+        k_newton_g<KIND, GG, RR><<<grid, 128, 0, st>>>(S, N, nx, J, dT, alpha, c, f0, jump,    \
+                                                        mode, U, u0, wf, out, active, ifail,   \
+                                                        itcount);                              \
+        return true;                                                                           \
+    }
+    KLECGC_NG(16, 2)
+    KLECGC_NG(16, 4)
+    KLECGC_NG(16, 8)
+    KLECGC_NG(32, 8)
+#undef KLECGC_NG
+    return false;
+}
+
+}  // namespace
+
 // Host value of the kernels' c: the cubic coefficient (kind 1) or c/h (kind 2).
 static double kind_coef(int kind, int nx, double c) { return kind == 2 ? c * (nx + 1) : c; }
 
@@ -161,6 +475,12 @@ void launch_fine_newton(int kind, int64_t S, int N, int nx, int J, double dT, do
     if (n == 0) return;
     const int64_t NS = n * nx;
     const double ck = kind_coef(kind, nx, c);
+    // G lanes per column where the rows fit (nx <= 256)
+    if (kind == 2 ? launch_newton_g<2>(S, N, nx, J, dT, alpha, ck, f0, jump, 0, U, u0, wf, b,
+                                       active, ifail, itcount, st)
+                  : launch_newton_g<1>(S, N, nx, J, dT, alpha, ck, f0, jump, 0, U, u0, wf, b,
+                                       active, ifail, itcount, st))
+        return;
     // One warp per CTA: each thread runs a long dependent FP64 chain, and the
     // FP64 pipe of an SM saturates at a few warps, so a batch of a few
     // thousand columns is spread over all SMs (128-thread CTAs put 256
@@ -210,6 +530,11 @@ void launch_sequential_newton(int kind, int64_t S, int N, int nx, int J, double 
                               double* U, int* ifail, cudaStream_t st) {
     if (S == 0) return;
     const double ck = kind_coef(kind, nx, c);
+    if (kind == 2 ? launch_newton_g<2>(S, N, nx, J, dt * J, 0.0, ck, f0, 0, 1, nullptr, u0, wf, U,
+                                       nullptr, ifail, nullptr, st)
+                  : launch_newton_g<1>(S, N, nx, J, dt * J, 0.0, ck, f0, 0, 1, nullptr, u0, wf, U,
+                                       nullptr, ifail, nullptr, st))
+        return;
     const unsigned grid = (unsigned)((S + 31) / 32);   // one warp per CTA (see above)
     if (kind == 2)
         k_sequential_newton<2><<<grid, 32, 0, st>>>(S, N, nx, J, dt, ck, f0, u0, wf, scratch, U,
