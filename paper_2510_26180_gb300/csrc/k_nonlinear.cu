@@ -234,6 +234,9 @@ __device__ __forceinline__ bool newton_be_g(int nx, int g, const double (&wfv)[R
         if (g == 0) upl = 0.0;
         double t00 = 1.0, t01 = 0.0, t10 = 0.0, t11 = 1.0;
         {
+            // R <= 8 factors with entries ~1 + 2 dt a / h^2 stay inside the
+            // FP64 range unless dt a / h^2 exceeds ~1e30, so the lane's
+            // product is rescaled once, at its end
             double upp = upl;
 #pragma unroll
             for (int j = 0; j < R; ++j) {
@@ -243,9 +246,9 @@ __device__ __forceinline__ bool newton_be_g(int nx, int g, const double (&wfv)[R
                 t11 = t01;
                 t00 = n00;
                 t01 = n01;
-                m2_rescale(t00, t01, t10, t11);
                 upp = up[j];
             }
+            m2_rescale(t00, t01, t10, t11);
         }
 #pragma unroll
         for (int d = 1; d < G; d <<= 1) {
@@ -262,15 +265,16 @@ __device__ __forceinline__ bool newton_be_g(int nx, int g, const double (&wfv)[R
             }
         }
         const double pp = __shfl_up_sync(FULL, t00, 1, G), qq = __shfl_up_sync(FULL, t10, 1, G);
-        double piv = (g > 0 && qq != 0.0) ? pp / qq : 1.0;   // pivot of the row before the lane
+        // 1 / (pivot of the row before the lane); one division per row below
+        double iprev = (g > 0 && pp != 0.0) ? qq / pp : 1.0;
         {
             double upp = upl;
 #pragma unroll
             for (int j = 0; j < R; ++j) {
-                const double m = lo[j] / piv;   // multiplier of row j (0 at the first row)
-                piv = dg[j] - m * upp;
-                ipv[j] = 1.0 / piv;
-                lo[j] = m;                      // lo now holds the multipliers
+                const double m = lo[j] * iprev;   // multiplier of row j (unused at the first row)
+                iprev = 1.0 / (dg[j] - m * upp);
+                ipv[j] = iprev;
+                lo[j] = m;                        // lo now holds the multipliers
                 upp = up[j];
             }
         }
