@@ -26,7 +26,8 @@
 //
 // Each CTA keeps its system's weights, diagonal and Krylov vectors in shared
 // memory when they fit (else in a global slice of its own) and loops over
-// work items.  The two dot products of an iteration are fused into two block
+// work items.  The mixed-precision systems that do not fit one CTA go to the
+// thread-block-cluster kernels of k_2d_cluster.cu instead (plan_2d).  The two dot products of an iteration are fused into two block
 // reductions; every thread sums the per-warp partials in the same order, so
 // all threads take the same (uniform) convergence decision.  Iteration
 // counts are capped (maxit); a solve that reaches the cap sets ifail[s].
