@@ -45,7 +45,7 @@
 
 namespace klecgc {
 
-constexpr int kFluxEvery32r = 16;
+constexpr int kFluxEvery32r = 32;
 
 // Per-sample table: seven FP32 planes of [R][32] (row i = g R + j at index
 // j 32 + g): l, P, dinv, u, Hg, wd (the face left of row i), G, then the

@@ -16,7 +16,7 @@ compares it with the oracle's F in FP64.  Start values in flux form every step
 a contraction, so after J steps the error stays below J x 8 x 2^-24 relative
 (3e-5 at J = 64), and in practice, the roundings being independent, near
 sqrt(J) x 8 x 2^-24; the bar is 1e-5.  The increment form of the later
-iterations (flux form every 16th step) is covered by a whole mixed solve per
+iterations (flux form every 16th or 32nd step) is covered by a whole mixed solve per
 shape, which must reach U* to 1e-6 with iteration counts within one of the
 shared-memory kernel's."""
 import json

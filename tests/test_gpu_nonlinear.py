@@ -44,6 +44,28 @@ def test_nonlinear_reference_matches_oracle(name):
 
 
 @pytest.mark.parametrize("name", PROBLEMS)
+@pytest.mark.parametrize("nx", [17, 128, 200, 300])
+def test_nonlinear_reference_across_lane_shapes(name, nx):
+    """The Newton propagator splits a column over 16 lanes up to 128 rows,
+    32 lanes up to 256 (8 rows per lane, padded with identity rows) and
+    keeps one thread per column above: U* of each shape against the
+    oracle's sequential Newton solution."""
+    from oracle import nonlinear as nl
+    over = dict(nx=nx, N=8, J=4, M=3, gpc_degree=1, n_train=8)
+    solver, w = gpu_solver(name, **over)
+    st = oracle_setup_ac(name, **over)
+    S = 3
+    xi = draw_xi(S, w.M, 74)
+    U = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
+    solver.reference(T(xi), S, w.N, w.J, U)
+    for s in range(S):
+        ref = st.reference(xi[s])
+        refp = nl.fine_sequential(st.operator(xi[s], 4.0), st.u0, w.N, w.J, w.T)
+        d = rel(U[s].cpu().numpy(), ref)
+        assert d < max(1e-12, 4 * rel(refp, ref)), (nx, s, d)
+
+
+@pytest.mark.parametrize("name", PROBLEMS)
 @pytest.mark.parametrize("guess", ["gpc", "coarse"])
 def test_nonlinear_solve_matches_oracle(name, guess):
     import paper_2510_26180_gb300 as pkg
@@ -104,6 +126,35 @@ def _coarse(nl, op, u0, N, dT):
     for _ in range(N):
         v = nl.G(op, v, dT)
         yield v
+
+
+@pytest.mark.parametrize("name", PROBLEMS)
+def test_nonlinear_solve_with_32_lanes_per_column(name):
+    """Whole solves from the coarse start at nx = 200 (F and its jump on 32
+    lanes per column): iteration counts equal to the oracle's, iterates at
+    its floor."""
+    import paper_2510_26180_gb300 as pkg
+    from oracle import nonlinear as nl
+    over = dict(nx=200, N=8, J=4, M=3, gpc_degree=1, n_train=8)
+    solver, w = gpu_solver(name, **over)
+    st = oracle_setup_ac(name, **over)
+    S = 3
+    xi = draw_xi(S, w.M, 75)
+    U = torch.empty((S, w.N, w.nx), dtype=torch.float64, device=dev())
+    it = torch.empty(S, dtype=torch.int32, device=dev())
+    code = solver.solve(T(xi), S, w.T / w.N, w.J, w.N, w.alpha, w.tol, w.kmax, pkg.FP64,
+                        pkg.GUESS_COARSE, U, it)
+    assert code == 0
+    U, it = U.cpu().numpy(), it.cpu().numpy()
+    for s in range(S):
+        op = st.operator(xi[s])
+        U0 = np.stack(list(_coarse(nl, op, st.u0, w.N, w.T / w.N)))
+        Uo, ko, _ = st.solve_sample(xi[s], U0=U0)
+        Ud, _, _ = st.solve_sample(xi[s], U0=U0, cgc="dense")
+        Up, _, _ = st.solve_sample(xi[s], U0=U0, field_ulps=4.0)
+        floor = rel(Ud, Uo) + rel(Up, Uo)
+        assert it[s] == ko, (s, it[s], ko)
+        assert rel(U[s], Uo) < max(1e-12, 4 * floor), (s, rel(U[s], Uo), floor)
 
 
 def test_zero_reaction_matches_the_linear_solver():
