@@ -51,9 +51,9 @@ FP64_ALU_PEAK = 1.25                              # TFLOP/s, GB300 nominal FP64
 # without a capture reports traffic null.
 _PTS512 = 512 * 64 * 1023
 MEASURED_TRAFFIC_B_PER_POINT = {
-    "mixed": {"fine": 249.1e6 / _PTS512, "cgc_fwd": 1034.5e6 / _PTS512,
+    "mixed": {"fine": 247.7e6 / _PTS512, "cgc_fwd": 1034.5e6 / _PTS512,
               "cgc_solve": 1552.7e6 / _PTS512, "cgc_inv": 893.0e6 / _PTS512},
-    "mixed_defect": {"fine": 249.1e6 / _PTS512, "cgc_fwd": 1047.8e6 / _PTS512,
+    "mixed_defect": {"fine": 247.7e6 / _PTS512, "cgc_fwd": 1047.8e6 / _PTS512,
                      "cgc_solve": 726.5e6 / _PTS512, "cgc_inv": 750.4e6 / _PTS512},
 }
 
