@@ -46,16 +46,18 @@ FP64_ALU_PEAK = 1.25                              # TFLOP/s, GB300 nominal FP64
 # ncu capture each (dram__bytes_read.sum + dram__bytes_write.sum) on 512
 # samples of heat1d_nx1023 (33.52 M points per launch, every sample active),
 # divided by the points of the captured launch; the roofline's traffic scales
-# them to a launch by its points.  The fine kernel is k_fine32r (the shape the
-# autotuner picks there).  Valid while those kernels are unchanged; a class
-# without a capture reports traffic null.
+# them to a launch by its points.  The fine kernel's figure is per layout (the
+# first letter of the autotuner's choice: L = k_fine32r, P = k_fine32p).
+# Valid while those kernels are unchanged; a class or layout without a
+# capture reports traffic null.
 _PTS512 = 512 * 64 * 1023
 MEASURED_TRAFFIC_B_PER_POINT = {
-    "mixed": {"fine": 247.7e6 / _PTS512, "cgc_fwd": 1034.5e6 / _PTS512,
+    "mixed": {"cgc_fwd": 1034.5e6 / _PTS512,
               "cgc_solve": 1552.7e6 / _PTS512, "cgc_inv": 893.0e6 / _PTS512},
-    "mixed_defect": {"fine": 247.7e6 / _PTS512, "cgc_fwd": 1047.8e6 / _PTS512,
+    "mixed_defect": {"cgc_fwd": 1047.8e6 / _PTS512,
                      "cgc_solve": 726.5e6 / _PTS512, "cgc_inv": 750.4e6 / _PTS512},
 }
+MEASURED_FINE_TRAFFIC_B_PER_POINT = {"L": 247.7e6 / _PTS512, "P": 243.6e6 / _PTS512}
 
 
 METHOD2D = [0]   # the 2D solve method of this run (set in main)
@@ -667,13 +669,13 @@ def run_gpu(args, w):
     # the other precision variants on the same batch: the plain FP64 path (the
     # >= 5x comparison) and, beside the headline, the other mixed split; each
     # one untimed warm-up solve and one timed solve, with its own kernel split
-    # the fine kernel's measured traffic is that of k_fine32r: drop it when
-    # the autotuner picked another kernel for this shape
+    # the fine kernel's measured traffic, for the layout the autotuner picked
     tuned = solver.tuning_report()
-    fine_is_r = any(v.startswith("L") for k, v in tuned.items() if "|ms@" not in k)
-    if not fine_is_r:
+    picks = [v[:1] for k, v in tuned.items() if "|ms@" not in k and "|fine32|" in k]
+    fine_pt = MEASURED_FINE_TRAFFIC_B_PER_POINT.get(picks[0]) if len(picks) == 1 else None
+    if fine_pt is not None:
         for table in MEASURED_TRAFFIC_B_PER_POINT.values():
-            table.pop("fine", None)
+            table["fine"] = fine_pt
     hbm_peak, peak_kind = peaks()
     variants = {}
     if not args.skip_fp64:

@@ -452,8 +452,10 @@ klecgc_status klecgc_set_loop(klecgc_ctx* ctx, int32_t mode);
  * given GPU times every candidate launch shape of the FP32 fine propagator
  * ("W<W>R<R>": W warps per pair of intervals, R rows per lane, 32 W R >=
  * nx + 1, W = 0 the shared-memory kernel; "L<L>R<R>": one interval per warp
- * with the factors in registers, L intervals per warp in turn) on up to 512
- * of its samples and keeps the fastest; later solves reuse the choice.
+ * with the factors in registers, L intervals per warp in turn; "P1R<R>": one
+ * interval per warp, each lane's R rows as two halves swept together in
+ * packed FP32x2) on up to 512 of its samples and keeps the fastest; later
+ * solves reuse the choice.
  * Every shape computes the same backward-Euler steps; the shapes split the
  * rows of a system differently between lanes, so results agree to FP32
  * rounding of the fine propagator, not bit for bit: a solve is reproducible

@@ -16,7 +16,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 OUT = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT, "libklecgc.so")
-SOURCES = ["api.cu", "k_field.cu", "k_guess.cu", "k_fine.cu", "k_fine32.cu", "k_fine32w.cu", "k_fine32r.cu", "k_cgc.cu", "k_mlp.cu", "k_2d.cu", "k_2d_cluster.cu", "k_batch.cu", "k_tc.cu", "k_nonlinear.cu",
+SOURCES = ["api.cu", "k_field.cu", "k_guess.cu", "k_fine.cu", "k_fine32.cu", "k_fine32w.cu", "k_fine32r.cu", "k_fine32p.cu", "k_cgc.cu", "k_mlp.cu", "k_2d.cu", "k_2d_cluster.cu", "k_batch.cu", "k_tc.cu", "k_nonlinear.cu",
            "k_offline.cu", "k_band.cu", "noalloc.cu", "setup_host.cpp"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 

@@ -355,7 +355,8 @@ klecgc_status choose_fine32w(klecgc_ctx* ctx, int64_t S, int N, int nx, int J, d
     // candidate W = 0: k_fine32 (one warp per pair of intervals, the factors
     // in shared memory, R rows per lane by its own rule); W >= 1: k_fine32w;
     // L >= 1: k_fine32r (one interval per warp, factors in registers, L
-    // intervals per warp in turn)
+    // intervals per warp in turn); P: k_fine32p (one interval per warp, each
+    // lane's rows as two halves in packed FP32x2)
     const int R0 = fine32_rows_per_lane(nx);
     *out = {0, R0};
     std::vector<Fine32wShape> cands;
@@ -364,6 +365,7 @@ klecgc_status choose_fine32w(klecgc_ctx* ctx, int64_t S, int N, int nx, int J, d
         for (const Fine32wShape& c : fine32w_candidates(nx)) cands.push_back(c);
         for (int L : {1, 4})
             if (fine32r_supported(R0, L)) cands.push_back({0, R0, L});
+        if (fine32p_supported(R0)) cands.push_back({0, R0, 0, 1});
     }
     if (ctx->tune_mode == 0 || cands.size() < 2 || S == 0) return KLECGC_OK;
     const std::string key = tune_key(ctx, "fine32", nx, N, J);
@@ -377,6 +379,10 @@ klecgc_status choose_fine32w(klecgc_ctx* ctx, int64_t S, int N, int nx, int J, d
             *sh = {0, R, W};
             return R == R0 && fine32r_supported(R, W);
         }
+        if (std::sscanf(v.c_str(), "P%dR%d", &W, &R) == 2) {
+            *sh = {0, R, 0, 1};
+            return W == 1 && R == R0 && fine32p_supported(R);
+        }
         return false;
     };
     auto it = ctx->tuned.find(key);
@@ -384,7 +390,8 @@ klecgc_status choose_fine32w(klecgc_ctx* ctx, int64_t S, int N, int nx, int J, d
     const int64_t St = std::min<int64_t>(S, 512);
     size_t tab = R0 ? fine_table32_bytes(St, R0) : 0;
     for (auto& c : cands) {
-        if (c.L) tab = std::max(tab, fine_table32r_bytes(St, c.R));
+        if (c.P) tab = std::max(tab, fine_table32p_bytes(St, c.R));
+        else if (c.L) tab = std::max(tab, fine_table32r_bytes(St, c.R));
         else if (c.W) tab = std::max(tab, fine_table32w_bytes(St, c));
     }
     WS(float, tb, "tune_table", tab / sizeof(float));
@@ -399,8 +406,9 @@ klecgc_status choose_fine32w(klecgc_ctx* ctx, int64_t S, int N, int nx, int J, d
     float best = 0.f;
     Fine32wShape pick = *out;
     auto name = [](const Fine32wShape& c) {
-        return c.L ? "L" + std::to_string(c.L) + "R" + std::to_string(c.R)
-                   : "W" + std::to_string(c.W) + "R" + std::to_string(c.R);
+        return c.P   ? "P1R" + std::to_string(c.R)
+               : c.L ? "L" + std::to_string(c.L) + "R" + std::to_string(c.R)
+                     : "W" + std::to_string(c.W) + "R" + std::to_string(c.R);
     };
     std::string times;
     auto run = [&](const Fine32wShape& c) {
@@ -408,7 +416,9 @@ klecgc_status choose_fine32w(klecgc_ctx* ctx, int64_t S, int N, int nx, int J, d
                         act, st);
     };
     for (const Fine32wShape& c : cands) {
-        if (c.L)
+        if (c.P)
+            launch_fine_table32p(f64, St, nx, c.R, tb, st);
+        else if (c.L)
             launch_fine_table32r(f64, St, nx, c.R, tb, st);
         else if (c.W == 0)
             launch_fine_table32(a, St, nx, c.R, ctx->h, dt, ctx->prob.reaction, tb, st);
@@ -471,11 +481,14 @@ klecgc_status build_operators(klecgc_ctx* ctx, const double* xi_d, int64_t S, in
         Fine32wShape sh;
         if ((s = choose_fine32w(ctx, S, N, nx, J, dT / J, op->a, f64, st, &sh)) != KLECGC_OK)
             return s;
-        const size_t tbytes = sh.L   ? fine_table32r_bytes(S, sh.R)
+        const size_t tbytes = sh.P   ? fine_table32p_bytes(S, sh.R)
+                              : sh.L ? fine_table32r_bytes(S, sh.R)
                               : sh.W ? fine_table32w_bytes(S, sh)
                                      : fine_table32_bytes(S, sh.R);
         WS(float, tb, "tab32w", tbytes / sizeof(float));
-        if (sh.L)
+        if (sh.P)
+            ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_table32p(f64, S, nx, sh.R, tb, st); });
+        else if (sh.L)
             ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_table32r(f64, S, nx, sh.R, tb, st); });
         else if (sh.W)
             ctx->launch(KLECGC_K_FACTORS, st, [&] { launch_fine_table32w(f64, S, nx, sh, tb, st); });
@@ -2662,7 +2675,7 @@ klecgc_status batch_persistent(klecgc_ctx* c0, std::vector<SolveRun>& runs, int6
         C.iters = R.iters;
         C.status = R.status;
         C.delta = R.delta;
-        if (R.op.sh32.W != 0 || R.op.sh32.L != 0 || !C.R) return fail(KLECGC_E_CUDA, "batch: a class without the shared-memory fine kernel");
+        if (R.op.sh32.W != 0 || R.op.sh32.L != 0 || R.op.sh32.P != 0 || !C.R) return fail(KLECGC_E_CUDA, "batch: a class without the shared-memory fine kernel");
     }
     // task lists, longest first within each stage
     struct Group {

@@ -182,6 +182,7 @@ void launch_fine32(int64_t S, int N, int nx, int J, double dt, double react, dou
 struct Fine32wShape {
     int W, R;
     int L = 0;
+    int P = 0;   // 1: k_fine32p (halves of R rows in packed FP32x2, one interval per warp)
 };
 Fine32wShape fine32w_shape(int nx);
 std::vector<Fine32wShape> fine32w_candidates(int nx);
@@ -201,8 +202,16 @@ void launch_fine32r(int R, int L, int64_t S, int N, int nx, int J, double dt, do
                     double forcing, int in_mode, const double* U64, const float2* Udf,
                     const double* u0, const float* c32, const float* table, float* fout,
                     const int* active, cudaStream_t st);
-// Any of the three: sh.L >= 1 is k_fine32r; else sh.W == 0 is k_fine32 (table of launch_fine_table32 with
-// sh.R rows per lane), sh.W >= 1 is k_fine32w.
+size_t fine_table32p_bytes(int64_t S, int R);
+void launch_fine_table32p(const FineCoef64* fc, int64_t S, int nx, int R, float* table,
+                          cudaStream_t st);
+bool fine32p_supported(int R);
+void launch_fine32p(int R, int64_t S, int N, int nx, int J, double dt, double react,
+                    double forcing, int in_mode, const double* U64, const float2* Udf,
+                    const double* u0, const float* c32, const float* table, float* fout,
+                    const int* active, cudaStream_t st);
+// Any of the four: sh.P is k_fine32p; sh.L >= 1 is k_fine32r; else sh.W == 0 is k_fine32 (table of
+// launch_fine_table32 with sh.R rows per lane), sh.W >= 1 is k_fine32w.
 void launch_fine_any(Fine32wShape sh, int64_t S, int N, int nx, int J, double dt, double react,
                      double forcing, int in_mode, const double* U64, const float2* Udf,
                      const double* u0, const float* c32, const float* table, float* fout,

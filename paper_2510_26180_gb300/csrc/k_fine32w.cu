@@ -437,7 +437,10 @@ void launch_fine_any(Fine32wShape sh, int64_t S, int N, int nx, int J, double dt
                      double forcing, int in_mode, const double* U64, const float2* Udf,
                      const double* u0, const float* c32, const float* table, float* fout,
                      const int* active, cudaStream_t st) {
-    if (sh.L)
+    if (sh.P)
+        launch_fine32p(sh.R, S, N, nx, J, dt, react, forcing, in_mode, U64, Udf, u0, c32, table,
+                       fout, active, st);
+    else if (sh.L)
         launch_fine32r(sh.R, sh.L, S, N, nx, J, dt, react, forcing, in_mode, U64, Udf, u0, c32,
                        table, fout, active, st);
     else if (sh.W == 0)

@@ -5,7 +5,10 @@ subinterval), each forced in turn through the autotuner's cache file:
 * k_fine32 (W0R..): one warp per pair of intervals, factors in shared memory;
 * k_fine32w (W1.., W2.., W4..): factors in registers, W warps per pair;
 * k_fine32r (L1.., L4..): one interval per warp, factors in registers, the
-  backward sweep regrouped as x = X + yin P + zin G.
+  backward sweep regrouped as x = X + yin P + zin G;
+* k_fine32p (P1..): as k_fine32r with each lane's rows split into two halves
+  swept together in packed FP32x2 (another partition of the rows, so another
+  rounding, within the same bar).
 
 klecgc_fine_sweep returns r_n = (I + dT(A + cI)) F_n - prev_n in FP64; the
 test recovers F_n = (I + dT(A + cI))^{-1} (r_n + prev_n) with the oracle's
@@ -33,8 +36,8 @@ torch = pytest.importorskip("torch")
 
 SHAPES = {
     63: ["W0R2", "W1R2", "L1R2", "L4R2"],
-    511: ["W0R16", "W1R16", "W2R8", "L1R16", "L4R16"],
-    1023: ["W0R32", "W2R16", "W4R8", "L1R32", "L4R32"],
+    511: ["W0R16", "W1R16", "W2R8", "L1R16", "L4R16", "P1R16"],
+    1023: ["W0R32", "W2R16", "W4R8", "L1R32", "L4R32", "P1R32"],
 }
 SMALL = dict(M=2, gpc_degree=1, n_train=6)
 

@@ -17,8 +17,9 @@ torch = pytest.importorskip("torch")
 
 OVER = dict(nx=511, N=16, J=8)   # candidates: factors in shared memory (W0R16), in
                                  # registers on 1 warp x 16 rows or 2 warps x 8 rows, or
-                                 # one interval per warp (1 or 4 in turn) x 16 rows
-ALL = ("W0R16", "W1R16", "W2R8", "L1R16", "L4R16")
+                                 # one interval per warp (1 or 4 in turn) x 16 rows, or
+                                 # one interval per warp x 2 halves of 8 rows (packed)
+ALL = ("W0R16", "W1R16", "W2R8", "L1R16", "L4R16", "P1R16")
 
 
 def _solve(solver, w, xi, precision):
