@@ -576,6 +576,8 @@ def run_gpu(args, w):
         osetup, pool = oracle_pool(w, cores)
 
     solver = pkg.Solver(pkg.Problem.from_workload(w), draw_train(w))
+    if args.tuning_cache:
+        solver.set_tuning(1, args.tuning_cache)
     if w.dim == 2 and args.method2d:
         solver.set_2d_method(args.method2d)
     info = solver.info()
@@ -1038,6 +1040,10 @@ def main():
     ap.add_argument("--samples", type=int, default=0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--skip-fp64", action="store_true")
+    ap.add_argument("--tuning-cache", default="", metavar="PATH",
+                    help="the autotuner's JSON cache file: read before the first solve and "
+                         "written after tuning, so that a second run (e.g. under a profiler, "
+                         "whose overhead swamps the tuner's timings) reruns the same kernels")
     ap.add_argument("--method2d", type=int, default=0, choices=[0, 1, 2, 3],
                     help="2D linear solves: 0 auto, 1 Krylov, 2 banded LU, "
                          "3 Krylov with every mixed system on a thread-block cluster")
