@@ -246,6 +246,13 @@ def run_reference(args, w):
 
 
 # ---------------------------------------------------------------- GPU arm
+def fine_traffic_per_point(tuned):
+    """Measured DRAM bytes per point of the FP32 fine kernel the autotuner
+    picked (the report's one fine32 choice), else None."""
+    picks = [v[:1] for k, v in tuned.items() if "|ms@" not in k and "|fine32|" in k]
+    return MEASURED_FINE_TRAFFIC_B_PER_POINT.get(picks[0]) if len(picks) == 1 else None
+
+
 def traffic_per_launch(cls, prec, points, launches):
     """Measured DRAM bytes per launch (classes with an ncu capture), else None."""
     per_pt = MEASURED_TRAFFIC_B_PER_POINT.get(prec, {}).get(cls)
@@ -673,8 +680,7 @@ def run_gpu(args, w):
     # one untimed warm-up solve and one timed solve, with its own kernel split
     # the fine kernel's measured traffic, for the layout the autotuner picked
     tuned = solver.tuning_report()
-    picks = [v[:1] for k, v in tuned.items() if "|ms@" not in k and "|fine32|" in k]
-    fine_pt = MEASURED_FINE_TRAFFIC_B_PER_POINT.get(picks[0]) if len(picks) == 1 else None
+    fine_pt = fine_traffic_per_point(tuned)
     if fine_pt is not None:
         for table in MEASURED_TRAFFIC_B_PER_POINT.values():
             table["fine"] = fine_pt
