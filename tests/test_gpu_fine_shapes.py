@@ -36,6 +36,8 @@ torch = pytest.importorskip("torch")
 
 SHAPES = {
     63: ["W0R2", "W1R2", "L1R2", "L4R2"],
+    127: ["W0R4", "L1R4", "L4R4", "P1R4"],
+    255: ["W0R8", "L1R8", "L4R8", "P1R8"],
     511: ["W0R16", "W1R16", "W2R8", "L1R16", "L4R16", "P1R16"],
     1023: ["W0R32", "W2R16", "W4R8", "L1R32", "L4R32", "P1R32"],
 }
@@ -62,7 +64,7 @@ def _oracle_F(w, xi, Uin):
     return np.stack(out), st
 
 
-@pytest.mark.parametrize("nx,J", [(63, 16), (511, 16), (1023, 64)])
+@pytest.mark.parametrize("nx,J", [(63, 16), (127, 16), (255, 16), (511, 16), (1023, 64)])
 @pytest.mark.parametrize("react", [(0.0, 0.0), (0.7, 0.4)])
 def test_each_fine_shape_matches_the_oracle_F(nx, J, react, tmp_path):
     import paper_2510_26180_gb300 as pkg
